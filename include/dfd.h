@@ -1,0 +1,193 @@
+/*
+ * dfd.h -- C ABI of the GB300 discrete Frechet distance library (libdfd.so).
+ *
+ * The discrete Frechet distance (DFD) of two polygonal curves p (n points)
+ * and q (m points) in R^dim is the value M_{n,m} of the recurrence of Eq. 1
+ * of "Walking Your Frog Fast in 4 LoC" (Sec. 3):
+ *     M_ij = max( min(M_{i-1,j}, M_{i-1,j-1}, M_{i,j-1}), d_ij ),
+ * with d_ij = || p_i - q_j ||_2 and the first row / column taken as running
+ * maxima (Alg. 1, Alg. 3).  The library carries SQUARED distances d_ij^2
+ * through the recurrence and takes one square root at the end; because the
+ * recurrence only selects among its inputs (min and max), this returns
+ * exactly the square of the distance computed on d_ij (Sec. 3, Theorem 1
+ * holds for any nondecreasing ground measure).
+ *
+ * Conventions shared by every entry point:
+ *   - Curves are row-major arrays of n x dim coordinates (point i at
+ *     p + i*dim), either float32 (DFD_F32) or int32 (DFD_I32).
+ *   - Unless an entry point says otherwise, every pointer is a DEVICE
+ *     pointer on the context's device, the work is enqueued on `stream`
+ *     (a cudaStream_t passed as void*, NULL = the legacy default stream),
+ *     and the call returns without waiting.  The caller owns every buffer
+ *     and must keep it alive until the stream has passed the work.
+ *   - Outputs: out_dist receives the distance delta (float for DFD_F32,
+ *     double for DFD_I32); out_dist2 receives delta^2 as the recurrence
+ *     computed it (float for DFD_F32, int64_t for DFD_I32, exact).  Either
+ *     may be NULL, not both.
+ *   - float32 results: delta^2 is one of the float32 squared distances
+ *     d_ij^2 = fma-chain(t_k = p_k - q_k) (t_0*t_0 first, then
+ *     fma(t_k, t_k, acc) for k = 1..dim-1, round-to-nearest), so it is within
+ *     dim+1 float32 roundings of the exact value; delta = sqrtf(delta^2),
+ *     correctly rounded.  int32 results: delta^2 is exact; delta is the
+ *     correctly rounded double square root of (double)delta^2.
+ *   - int32 precondition: every |coordinate| <= 2^30 - 1 and
+ *     dim * (2 * max|coordinate|)^2 <= 2^63 - 1; otherwise DFD_ERR_RANGE
+ *     (checked on the device when the context's check_inputs option is on).
+ *   - float32 precondition: finite coordinates; otherwise DFD_ERR_NONFINITE
+ *     (checked on the device when check_inputs is on).
+ *   - Functions never abort the process.  Invalid host arguments return an
+ *     error status immediately and enqueue nothing.  Errors found on the
+ *     device (input checks, a bounded wait that ran out) are recorded in the
+ *     context's sticky device error word, reported by dfd_get_error().
+ *   - No CPU fallback exists: without a usable CUDA device every call that
+ *     computes returns DFD_ERR_CUDA.
+ */
+#ifndef DFD_H_
+#define DFD_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum dfd_status {
+  DFD_OK = 0,
+  DFD_ERR_INVALID_ARG = 1, /* bad pointer, size, dtype or dim */
+  DFD_ERR_RANGE = 2,       /* int32 coordinates outside the exact range */
+  DFD_ERR_NONFINITE = 3,   /* float32 coordinate is NaN or infinite */
+  DFD_ERR_OOM = 4,         /* device or pinned host allocation failed */
+  DFD_ERR_CUDA = 5,        /* a CUDA runtime call failed / no device */
+  DFD_ERR_TIMEOUT = 6,     /* a bounded device wait ran out (no hang, no trap) */
+  DFD_ERR_BUSY = 7,        /* resource limit reached, retry later */
+  DFD_ERR_CANCELLED = 8,   /* work was cancelled before it finished */
+  DFD_ERR_NOT_READY = 9,   /* result not available yet */
+  DFD_ERR_UNSUPPORTED = 10 /* configuration not provided by this build */
+} dfd_status;
+
+typedef enum dfd_dtype { DFD_F32 = 0, DFD_I32 = 1 } dfd_dtype;
+
+typedef struct dfd_context dfd_context;
+
+typedef struct dfd_options {
+  size_t struct_size;       /* sizeof(dfd_options), for forward compatibility */
+  size_t mem_budget_bytes;  /* device scratch budget; 0 = no limit */
+  int max_slots;            /* serving: concurrent requests admitted (0 = default) */
+  double wait_timeout_ms;   /* limit of every device-side spin wait (default 2000) */
+  int check_inputs;         /* 1 = validate coordinates on the device (default) */
+} dfd_options;
+
+/* Fill *opt with the defaults.  Returns DFD_ERR_INVALID_ARG for NULL. */
+dfd_status dfd_options_default(dfd_options* opt);
+
+/* Human-readable name of a status code (static string, never NULL). */
+const char* dfd_status_string(dfd_status s);
+
+/*
+ * Create a context on CUDA device `device` (opt NULL = defaults).  The
+ * context owns a grow-only device scratch area, a pinned host staging area
+ * and the device error word; it is not thread-safe (use one per host thread
+ * or serialise calls).  *out is set only on DFD_OK.
+ */
+dfd_status dfd_context_create(dfd_context** out, int device, const dfd_options* opt);
+
+/* Synchronise the device, free everything the context owns.  NULL is OK. */
+dfd_status dfd_context_destroy(dfd_context* ctx);
+
+/*
+ * Synchronise the device and return the sticky device error word
+ * (DFD_OK if no device-side error happened), then clear it.
+ */
+dfd_status dfd_get_error(dfd_context* ctx);
+
+/*
+ * Discrete Frechet distance of one pair of curves (Eq. 1, Alg. 5 semantics)
+ * on the whole GPU: a band wavefront over the (n x m) recurrence (rows of p
+ * in bands across CTAs, warps inside a band as a systolic pipeline over the
+ * columns), with O(n + m) device scratch owned by the context.
+ *   p: n x dim, q: m x dim (device, dtype), n >= 1, m >= 1, 1 <= dim <= 16.
+ *   out_dist / out_dist2: device pointers to one element each (see top).
+ */
+dfd_status dfd_pair(dfd_context* ctx, dfd_dtype dtype, int dim, const void* p, int64_t n, const void* q,
+                    int64_t m, void* out_dist, void* out_dist2, void* stream);
+
+/*
+ * The same distance by the plain per-pair reference form: one CTA computes
+ * the recurrence row by row (Alg. 2 / Alg. 5 order); within each row the
+ * dependence on the left neighbour is resolved by a block-wide scan of the
+ * clamp functions x -> max(d_j, min(a_j, x)) (the paper's maxmin step,
+ * Sec. 3, made associative by composing clamps).  Same arguments and
+ * results as dfd_pair; bit-identical to it.  Scratch: O(m).
+ */
+dfd_status dfd_pair_reference(dfd_context* ctx, dfd_dtype dtype, int dim, const void* p, int64_t n,
+                              const void* q, int64_t m, void* out_dist, void* out_dist2, void* stream);
+
+/*
+ * dfd_pair with HOST buffers: copies p and q to the device (through the
+ * context's pinned staging area), runs dfd_pair on the context's internal
+ * stream, copies the result back and waits for it.  p, q, out_dist and
+ * out_dist2 are host pointers (outputs may be NULL, not both).  Device
+ * errors are returned directly.
+ */
+dfd_status dfd_pair_host(dfd_context* ctx, dfd_dtype dtype, int dim, const void* p, int64_t n, const void* q,
+                         int64_t m, void* out_dist, void* out_dist2);
+
+/*
+ * Explicit launch shape for the band wavefront of dfd_pair (for tuning and
+ * measurement).  rows_per_lane in {2, 4, 6, 8}, warps in 1..16 (compute
+ * warps per CTA; one more communication warp is added), ctas in 1..#SMs
+ * (0 = min(#bands, #SMs)).  Unsupported shapes return DFD_ERR_UNSUPPORTED.
+ */
+typedef struct dfd_wave_shape {
+  int rows_per_lane;
+  int warps;
+  int ctas;
+} dfd_wave_shape;
+
+dfd_status dfd_pair_shaped(dfd_context* ctx, dfd_dtype dtype, int dim, const void* p, int64_t n, const void* q,
+                           int64_t m, void* out_dist, void* out_dist2, void* stream, const dfd_wave_shape* shape);
+
+/* The launch shape dfd_pair would choose for (dtype, dim, n, m). */
+dfd_status dfd_pair_plan(dfd_context* ctx, dfd_dtype dtype, int dim, int64_t n, int64_t m, dfd_wave_shape* shape);
+
+/*
+ * Measurement hooks (no counterpart in the paper).  With timing enabled the
+ * context records a CUDA event pair around the main kernel launch of every
+ * computing call, on that call's stream.  dfd_timing_last waits for the
+ * latest pair and returns its duration in milliseconds (DFD_ERR_NOT_READY
+ * if none was recorded since enabling).
+ */
+dfd_status dfd_timing_enable(dfd_context* ctx, int on);
+dfd_status dfd_timing_last(dfd_context* ctx, double* ms);
+
+/*
+ * Issue-rate measurement (the ALU roofline of the recurrence; the paper's
+ * Sec. 4 "sum of all d_ij" baseline is op 10).  Runs one kernel of many
+ * independent instruction chains on every SM and returns the measured
+ * throughput in thread-operations per clock per SM (cells per clock per SM
+ * for the cell mixes) and the SM clock it ran at (MHz).  op:
+ *   0 fma.f32   1 fma.f32x2   2 min.f32   3 min.f32 (3 inputs)   4 min.s32
+ *   5 min.s64   6 mad.wide.s32   7 shfl.sync.up
+ *   8 one float32 3-D cell (f32x2 distance + min3 + max)
+ *   9 one int32 2-D cell (int64 squares + 3 x 64-bit min/max)
+ *  10 one float32 3-D distance, summed instead of Eq. 1
+ * Synchronous.  DFD_ERR_INVALID_ARG for an unknown op.
+ */
+dfd_status dfd_microbench(dfd_context* ctx, int op, double* per_clk_per_sm, double* sm_mhz);
+
+/*
+ * Diagnostics for the failure path of the device waits (no counterpart in
+ * the paper): one CTA spins on a device flag that nothing ever sets, using
+ * the same bounded wait as the wavefront, with a limit of timeout_ms; the
+ * call synchronises and returns what the wait recorded -- DFD_ERR_TIMEOUT
+ * when the limit works -- and clears the error word.  Nothing hangs or
+ * traps; the context stays usable.
+ */
+dfd_status dfd_debug_bounded_wait(dfd_context* ctx, double timeout_ms);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DFD_H_ */

@@ -1,0 +1,469 @@
+// dfd_api.cu -- the C ABI (dfd.h): contexts, argument checks, dispatch.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include "dfd_device.cuh"
+#include "dfd_internal.h"
+
+namespace dfd {
+
+// ------------------------------------------------------------ declarations
+template <class V, int DK, int R>
+dfd_status wave_launch(dfd_context* ctx, int dim, const void* p, int64_t n, const void* q, int64_t m,
+                       void* out_dist, void* out_dist2, cudaStream_t s, int W, int ctas);
+
+#define DFD_WAVE_EXTERN(V, DK, R)                                                                              \
+  extern template dfd_status wave_launch<V, DK, R>(dfd_context*, int, const void*, int64_t, const void*, int64_t, \
+                                                   void*, void*, cudaStream_t, int, int);
+#define DFD_WAVE_EXTERN_R(V, DK) \
+  DFD_WAVE_EXTERN(V, DK, 2) DFD_WAVE_EXTERN(V, DK, 4) DFD_WAVE_EXTERN(V, DK, 6) DFD_WAVE_EXTERN(V, DK, 8)
+DFD_WAVE_EXTERN_R(F32, 2)
+DFD_WAVE_EXTERN_R(F32, 3)
+DFD_WAVE_EXTERN_R(F32, 4)
+DFD_WAVE_EXTERN_R(F32, 8)
+DFD_WAVE_EXTERN_R(F32, 16)
+DFD_WAVE_EXTERN_R(I32, 2)
+DFD_WAVE_EXTERN_R(I32, 3)
+DFD_WAVE_EXTERN_R(I32, 4)
+DFD_WAVE_EXTERN_R(I32, 8)
+DFD_WAVE_EXTERN_R(I32, 16)
+
+// ---------------------------------------------------------- scratch memory
+dfd_status ensure_scratch(dfd_context* ctx, size_t bytes) {
+  if (bytes <= ctx->scratch_bytes) return DFD_OK;
+  if (ctx->opt.mem_budget_bytes && bytes > ctx->opt.mem_budget_bytes) return DFD_ERR_OOM;
+  size_t want = std::max(bytes, ctx->scratch_bytes + ctx->scratch_bytes / 2);
+  if (ctx->opt.mem_budget_bytes) want = std::min(want, ctx->opt.mem_budget_bytes);
+  void* p = nullptr;
+  // cudaFree synchronises the device, so no in-flight kernel still uses the old area.
+  if (ctx->scratch) cudaFree(ctx->scratch);
+  ctx->scratch = nullptr;
+  ctx->scratch_bytes = 0;
+  cudaError_t e = cudaMalloc(&p, want);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return DFD_ERR_OOM;
+  }
+  ctx->scratch = p;
+  ctx->scratch_bytes = want;
+  return DFD_OK;
+}
+
+dfd_status ensure_pinned(dfd_context* ctx, size_t bytes) {
+  if (bytes <= ctx->pinned_bytes) return DFD_OK;
+  if (ctx->pinned) {
+    cudaStreamSynchronize(ctx->stream);
+    cudaFreeHost(ctx->pinned);
+  }
+  ctx->pinned = nullptr;
+  ctx->pinned_bytes = 0;
+  size_t want = std::max(bytes, (size_t)1 << 20);
+  void* p = nullptr;
+  if (cudaMallocHost(&p, want) != cudaSuccess) {
+    cudaGetLastError();
+    return DFD_ERR_OOM;
+  }
+  ctx->pinned = p;
+  ctx->pinned_bytes = want;
+  return DFD_OK;
+}
+
+// ------------------------------------------------------ input check kernels
+__global__ void check_f32_kernel(const float* x, int64_t count, int* err) {
+  bool bad = false;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x)
+    bad |= !isfinite(x[i]);
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) raise_error(err, DFD_ERR_NONFINITE);
+}
+
+__global__ void check_i32_kernel(const int32_t* x, int64_t count, int dim, int* err) {
+  // |c| <= 2^30 - 1 and dim * (2 max|c|)^2 <= 2^63 - 1
+  const long long lim30 = (1LL << 30) - 1;
+  const double lim = sqrt((double)LLONG_MAX / (double)dim) / 2.0;
+  bool bad = false;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
+    const long long v = x[i] < 0 ? -(long long)x[i] : (long long)x[i];
+    bad |= v > lim30 || (double)v > lim;
+  }
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) raise_error(err, DFD_ERR_RANGE);
+}
+
+dfd_status launch_check_inputs(dfd_dtype dtype, int dim, const void* x, int64_t count, int* err, cudaStream_t s) {
+  if (count <= 0) return DFD_OK;
+  const int threads = 256;
+  const int blocks = (int)std::min<int64_t>((count + threads - 1) / threads, 1024);
+  if (dtype == DFD_F32)
+    check_f32_kernel<<<blocks, threads, 0, s>>>(static_cast<const float*>(x), count, err);
+  else
+    check_i32_kernel<<<blocks, threads, 0, s>>>(static_cast<const int32_t*>(x), count, dim, err);
+  return cuda_status(cudaGetLastError());
+}
+
+// ------------------------------------------------------------- wave plans
+static bool shape_ok(const dfd_context* ctx, dfd_dtype dtype, int dim, int R, int W) {
+  // q chunks are 128 columns for dim <= 4 and 64 beyond; the q ring bounds
+  // how far the last warp may trail warp 0 (see wave::max_warps).
+  const int C = dim_class(dim) <= 4 ? 128 : 64;
+  const int wmax = ((16 - 1) * C - 31) / 64 + 1;
+  if (W < 1 || W > 16 || W > wmax) return false;
+  if (R != 2 && R != 4 && R != 6 && R != 8) return false;
+  (void)ctx;
+  (void)dtype;
+  return true;
+}
+
+dfd_status wave_plan(const dfd_context* ctx, dfd_dtype dtype, int dim, int64_t n, int64_t m, WaveShape* shape) {
+  // Cost model: every CTA runs one band at a time; a band of H = 32*W*R rows
+  // sweeps m columns; bands start one inter-band lag apart; an SM reaches
+  // its issue limit once W*R >= RSAT (enough independent rows to hide the
+  // per-row min/max latency).  Minimise the modelled completion time.
+  (void)dim;
+  const double RSAT = 48.0;
+  const int P = std::max(ctx->num_sms, 1);
+  double best = 1e300;
+  WaveShape bs;
+  const int Rs[4] = {8, 6, 4, 2};
+  for (int R : Rs) {
+    for (int W = 1; W <= 16; ++W) {
+      if (!shape_ok(ctx, dtype, dim, R, W)) continue;
+      const double H = 32.0 * W * R;
+      const double B = std::ceil((double)n / H);
+      const double waves = std::ceil(B / P);
+      const double lag = 64.0 * W + 96.0;
+      const double conc = std::min(B, (double)P);
+      const double cols = waves * ((double)m + 64.0 * W) + (conc - 1.0) * lag;
+      const double sat = std::min(1.0, W * R / RSAT);
+      const double t = cols * H / sat;
+      if (t < best * 0.999) {
+        best = t;
+        bs.R = R;
+        bs.W = W;
+        bs.ctas = (int)conc;
+      }
+    }
+  }
+  *shape = bs;
+  return DFD_OK;
+}
+
+dfd_status wave_run(dfd_context* ctx, dfd_dtype dtype, int dim, const void* p, int64_t n, const void* q, int64_t m,
+                    void* out_dist, void* out_dist2, cudaStream_t s, const WaveShape& sh) {
+  if (!shape_ok(ctx, dtype, dim, sh.R, sh.W)) return DFD_ERR_UNSUPPORTED;
+  const int dk = dim_class(dim);
+#define DFD_W_R(V, DK)                                                                       \
+  switch (sh.R) {                                                                            \
+    case 2: return wave_launch<V, DK, 2>(ctx, dim, p, n, q, m, out_dist, out_dist2, s, sh.W, sh.ctas); \
+    case 4: return wave_launch<V, DK, 4>(ctx, dim, p, n, q, m, out_dist, out_dist2, s, sh.W, sh.ctas); \
+    case 6: return wave_launch<V, DK, 6>(ctx, dim, p, n, q, m, out_dist, out_dist2, s, sh.W, sh.ctas); \
+    case 8: return wave_launch<V, DK, 8>(ctx, dim, p, n, q, m, out_dist, out_dist2, s, sh.W, sh.ctas); \
+    default: return DFD_ERR_UNSUPPORTED;                                                     \
+  }
+#define DFD_W_DK(V)              \
+  switch (dk) {                  \
+    case 2: DFD_W_R(V, 2)        \
+    case 3: DFD_W_R(V, 3)        \
+    case 4: DFD_W_R(V, 4)        \
+    case 8: DFD_W_R(V, 8)        \
+    case 16: DFD_W_R(V, 16)      \
+    default: return DFD_ERR_UNSUPPORTED; \
+  }
+  if (dtype == DFD_F32) {
+    DFD_W_DK(F32)
+  } else {
+    DFD_W_DK(I32)
+  }
+#undef DFD_W_DK
+#undef DFD_W_R
+}
+
+__global__ void bounded_wait_kernel(const unsigned long long* flag, int* err, unsigned long long timeout_ns) {
+  if (threadIdx.x == 0) wait_geq(flag, 1ull, err, timeout_ns);
+}
+
+}  // namespace dfd
+
+using namespace dfd;
+
+// ======================================================================= C ABI
+namespace {
+
+dfd_status check_pair_args(dfd_context* ctx, dfd_dtype dtype, int dim, const void* p, int64_t n, const void* q,
+                           int64_t m, const void* out_dist, const void* out_dist2) {
+  if (!ctx) return DFD_ERR_INVALID_ARG;
+  if (dtype != DFD_F32 && dtype != DFD_I32) return DFD_ERR_INVALID_ARG;
+  if (dim < 1 || !p || !q || n < 1 || m < 1) return DFD_ERR_INVALID_ARG;
+  if (!out_dist && !out_dist2) return DFD_ERR_INVALID_ARG;
+  if (dim > 16) return DFD_ERR_UNSUPPORTED;
+  if (m > (int64_t)1 << 29 || n > ((int64_t)1 << 40)) return DFD_ERR_UNSUPPORTED;
+  return DFD_OK;
+}
+
+dfd_status set_device(dfd_context* ctx) {
+  return cuda_status(cudaSetDevice(ctx->device));
+}
+
+dfd_status pre_checks(dfd_context* ctx, dfd_dtype dtype, int dim, const void* p, int64_t n, const void* q, int64_t m,
+                      cudaStream_t s) {
+  if (!ctx->opt.check_inputs) return DFD_OK;
+  dfd_status st = launch_check_inputs(dtype, dim, p, n * dim, ctx->d_err, s);
+  if (st != DFD_OK) return st;
+  return launch_check_inputs(dtype, dim, q, m * dim, ctx->d_err, s);
+}
+
+}  // namespace
+
+extern "C" {
+
+dfd_status dfd_options_default(dfd_options* opt) {
+  if (!opt) return DFD_ERR_INVALID_ARG;
+  std::memset(opt, 0, sizeof(*opt));
+  opt->struct_size = sizeof(dfd_options);
+  opt->mem_budget_bytes = 0;
+  opt->max_slots = 0;
+  opt->wait_timeout_ms = 2000.0;
+  opt->check_inputs = 1;
+  return DFD_OK;
+}
+
+const char* dfd_status_string(dfd_status s) {
+  switch (s) {
+    case DFD_OK: return "DFD_OK";
+    case DFD_ERR_INVALID_ARG: return "DFD_ERR_INVALID_ARG";
+    case DFD_ERR_RANGE: return "DFD_ERR_RANGE";
+    case DFD_ERR_NONFINITE: return "DFD_ERR_NONFINITE";
+    case DFD_ERR_OOM: return "DFD_ERR_OOM";
+    case DFD_ERR_CUDA: return "DFD_ERR_CUDA";
+    case DFD_ERR_TIMEOUT: return "DFD_ERR_TIMEOUT";
+    case DFD_ERR_BUSY: return "DFD_ERR_BUSY";
+    case DFD_ERR_CANCELLED: return "DFD_ERR_CANCELLED";
+    case DFD_ERR_NOT_READY: return "DFD_ERR_NOT_READY";
+    case DFD_ERR_UNSUPPORTED: return "DFD_ERR_UNSUPPORTED";
+  }
+  return "DFD_ERR_UNKNOWN";
+}
+
+dfd_status dfd_context_create(dfd_context** out, int device, const dfd_options* opt) {
+  if (!out) return DFD_ERR_INVALID_ARG;
+  *out = nullptr;
+  int count = 0;
+  if (cudaGetDeviceCount(&count) != cudaSuccess || count <= 0) {
+    cudaGetLastError();
+    return DFD_ERR_CUDA;
+  }
+  if (device < 0 || device >= count) return DFD_ERR_INVALID_ARG;
+  dfd_context* ctx = new (std::nothrow) dfd_context();
+  if (!ctx) return DFD_ERR_OOM;
+  dfd_options_default(&ctx->opt);
+  if (opt) {
+    if (opt->struct_size != sizeof(dfd_options)) {
+      delete ctx;
+      return DFD_ERR_INVALID_ARG;
+    }
+    ctx->opt = *opt;
+    if (ctx->opt.wait_timeout_ms <= 0) ctx->opt.wait_timeout_ms = 2000.0;
+  }
+  ctx->device = device;
+  dfd_status st = set_device(ctx);
+  if (st == DFD_OK) {
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) st = DFD_ERR_CUDA;
+    else {
+      ctx->num_sms = prop.multiProcessorCount;
+      ctx->smem_optin = prop.sharedMemPerBlockOptin;
+    }
+  }
+  if (st == DFD_OK && cudaMalloc(&ctx->d_err, 256) != cudaSuccess) st = DFD_ERR_OOM;
+  if (st == DFD_OK && cudaMemset(ctx->d_err, 0, 256) != cudaSuccess) st = DFD_ERR_CUDA;
+  if (st == DFD_OK && cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess) st = DFD_ERR_CUDA;
+  if (st != DFD_OK) {
+    cudaGetLastError();
+    if (ctx->d_err) cudaFree(ctx->d_err);
+    delete ctx;
+    return st;
+  }
+  *out = ctx;
+  return DFD_OK;
+}
+
+dfd_status dfd_context_destroy(dfd_context* ctx) {
+  if (!ctx) return DFD_OK;
+  cudaSetDevice(ctx->device);
+  cudaDeviceSynchronize();
+  if (ctx->stream) cudaStreamDestroy(ctx->stream);
+  if (ctx->ev0) cudaEventDestroy(ctx->ev0);
+  if (ctx->ev1) cudaEventDestroy(ctx->ev1);
+  if (ctx->scratch) cudaFree(ctx->scratch);
+  if (ctx->pinned) cudaFreeHost(ctx->pinned);
+  if (ctx->d_err) cudaFree(ctx->d_err);
+  cudaGetLastError();
+  delete ctx;
+  return DFD_OK;
+}
+
+dfd_status dfd_get_error(dfd_context* ctx) {
+  if (!ctx) return DFD_ERR_INVALID_ARG;
+  dfd_status st = set_device(ctx);
+  if (st != DFD_OK) return st;
+  if (cudaDeviceSynchronize() != cudaSuccess) {
+    cudaGetLastError();
+    return DFD_ERR_CUDA;
+  }
+  int v = 0;
+  if (cudaMemcpy(&v, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return DFD_ERR_CUDA;
+  if (v != 0 && cudaMemset(ctx->d_err, 0, sizeof(int)) != cudaSuccess) return DFD_ERR_CUDA;
+  return (dfd_status)v;
+}
+
+dfd_status dfd_timing_enable(dfd_context* ctx, int on) {
+  if (!ctx) return DFD_ERR_INVALID_ARG;
+  dfd_status st = set_device(ctx);
+  if (st != DFD_OK) return st;
+  if (on && !ctx->ev0) {
+    if (cudaEventCreate(&ctx->ev0) != cudaSuccess || cudaEventCreate(&ctx->ev1) != cudaSuccess) {
+      cudaGetLastError();
+      return DFD_ERR_CUDA;
+    }
+  }
+  ctx->timing = on != 0;
+  ctx->timed = false;
+  return DFD_OK;
+}
+
+dfd_status dfd_timing_last(dfd_context* ctx, double* ms) {
+  if (!ctx || !ms) return DFD_ERR_INVALID_ARG;
+  if (!ctx->timing || !ctx->timed) return DFD_ERR_NOT_READY;
+  if (cudaEventSynchronize(ctx->ev1) != cudaSuccess) {
+    cudaGetLastError();
+    return DFD_ERR_CUDA;
+  }
+  float f = 0.f;
+  if (cudaEventElapsedTime(&f, ctx->ev0, ctx->ev1) != cudaSuccess) {
+    cudaGetLastError();
+    return DFD_ERR_CUDA;
+  }
+  *ms = f;
+  return DFD_OK;
+}
+
+dfd_status dfd_debug_bounded_wait(dfd_context* ctx, double timeout_ms) {
+  if (!ctx || !(timeout_ms > 0) || timeout_ms > 60000.0) return DFD_ERR_INVALID_ARG;
+  dfd_status st = set_device(ctx);
+  if (st != DFD_OK) return st;
+  // ctx->d_err[0] is the error word; d_err[2..3] (8-byte aligned) is a flag
+  // that stays zero.
+  unsigned long long* flag = reinterpret_cast<unsigned long long*>(ctx->d_err + 2);
+  if (cudaMemsetAsync(flag, 0, sizeof(*flag), ctx->stream) != cudaSuccess) return DFD_ERR_CUDA;
+  bounded_wait_kernel<<<1, 32, 0, ctx->stream>>>(flag, ctx->d_err, (unsigned long long)(timeout_ms * 1.0e6));
+  if (cudaGetLastError() != cudaSuccess) return DFD_ERR_CUDA;
+  if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) {
+    cudaGetLastError();
+    return DFD_ERR_CUDA;
+  }
+  int v = 0;
+  if (cudaMemcpy(&v, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return DFD_ERR_CUDA;
+  cudaMemset(ctx->d_err, 0, sizeof(int));
+  return (dfd_status)v;
+}
+
+dfd_status dfd_pair_plan(dfd_context* ctx, dfd_dtype dtype, int dim, int64_t n, int64_t m, dfd_wave_shape* shape) {
+  if (!ctx || !shape || n < 1 || m < 1 || dim < 1) return DFD_ERR_INVALID_ARG;
+  WaveShape sh;
+  dfd_status st = wave_plan(ctx, dtype, dim, n, m, &sh);
+  if (st != DFD_OK) return st;
+  shape->rows_per_lane = sh.R;
+  shape->warps = sh.W;
+  shape->ctas = sh.ctas;
+  return DFD_OK;
+}
+
+dfd_status dfd_pair_shaped(dfd_context* ctx, dfd_dtype dtype, int dim, const void* p, int64_t n, const void* q,
+                           int64_t m, void* out_dist, void* out_dist2, void* stream, const dfd_wave_shape* shape) {
+  dfd_status st = check_pair_args(ctx, dtype, dim, p, n, q, m, out_dist, out_dist2);
+  if (st != DFD_OK) return st;
+  WaveShape sh;
+  if (shape) {
+    sh.R = shape->rows_per_lane;
+    sh.W = shape->warps;
+    sh.ctas = shape->ctas;
+    if (sh.ctas < 0 || sh.ctas > ctx->num_sms) return DFD_ERR_UNSUPPORTED;
+  } else {
+    wave_plan(ctx, dtype, dim, n, m, &sh);
+  }
+  if ((st = set_device(ctx)) != DFD_OK) return st;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if ((st = pre_checks(ctx, dtype, dim, p, n, q, m, s)) != DFD_OK) return st;
+  return wave_run(ctx, dtype, dim, p, n, q, m, out_dist, out_dist2, s, sh);
+}
+
+dfd_status dfd_pair(dfd_context* ctx, dfd_dtype dtype, int dim, const void* p, int64_t n, const void* q, int64_t m,
+                    void* out_dist, void* out_dist2, void* stream) {
+  return dfd_pair_shaped(ctx, dtype, dim, p, n, q, m, out_dist, out_dist2, stream, nullptr);
+}
+
+dfd_status dfd_pair_reference(dfd_context* ctx, dfd_dtype dtype, int dim, const void* p, int64_t n, const void* q,
+                              int64_t m, void* out_dist, void* out_dist2, void* stream) {
+  dfd_status st = check_pair_args(ctx, dtype, dim, p, n, q, m, out_dist, out_dist2);
+  if (st != DFD_OK) return st;
+  if ((st = set_device(ctx)) != DFD_OK) return st;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if ((st = pre_checks(ctx, dtype, dim, p, n, q, m, s)) != DFD_OK) return st;
+  return rowscan_run(ctx, dtype, dim, p, n, q, m, out_dist, out_dist2, s);
+}
+
+dfd_status dfd_pair_host(dfd_context* ctx, dfd_dtype dtype, int dim, const void* p, int64_t n, const void* q, int64_t m,
+                         void* out_dist, void* out_dist2) {
+  dfd_status st = check_pair_args(ctx, dtype, dim, p, n, q, m, out_dist, out_dist2);
+  if (st != DFD_OK) return st;
+  if ((st = set_device(ctx)) != DFD_OK) return st;
+  // Device layout of the staged inputs and results: [p | q | dist | dist2],
+  // carved from the pinned host area and from a second device buffer that
+  // sits after the wavefront's scratch (which it grows first).
+  const size_t pb = align_up((size_t)n * dim * 4, 256), qb = align_up((size_t)m * dim * 4, 256);
+  const size_t host_bytes = pb + qb + 256;
+  if ((st = ensure_pinned(ctx, host_bytes)) != DFD_OK) return st;
+  char* h = static_cast<char*>(ctx->pinned);
+  std::memcpy(h, p, (size_t)n * dim * 4);
+  std::memcpy(h + pb, q, (size_t)m * dim * 4);
+  void* dio = nullptr;
+  if (cudaMallocAsync(&dio, host_bytes, ctx->stream) != cudaSuccess) {
+    cudaGetLastError();
+    return DFD_ERR_OOM;
+  }
+  char* d = static_cast<char*>(dio);
+  cudaStream_t s = ctx->stream;
+  cudaMemcpyAsync(d, h, pb + qb, cudaMemcpyHostToDevice, s);
+  WaveShape sh;
+  wave_plan(ctx, dtype, dim, n, m, &sh);
+  if ((st = pre_checks(ctx, dtype, dim, d, n, d + pb, m, s)) == DFD_OK) {
+    char* dres = d + pb + qb;
+    st = wave_run(ctx, dtype, dim, d, n, d + pb, m, dres, dres + 8, s, sh);
+    if (st == DFD_OK) {
+      cudaMemcpyAsync(h + pb + qb, dres, 16, cudaMemcpyDeviceToHost, s);
+    }
+  }
+  cudaFreeAsync(dio, s);
+  if (cudaStreamSynchronize(s) != cudaSuccess) {
+    cudaGetLastError();
+    return DFD_ERR_CUDA;
+  }
+  if (st != DFD_OK) return st;
+  int err = 0;
+  cudaMemcpy(&err, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost);
+  if (err != 0) {
+    cudaMemset(ctx->d_err, 0, sizeof(int));
+    return (dfd_status)err;
+  }
+  const char* r = h + pb + qb;
+  if (dtype == DFD_F32) {
+    if (out_dist) std::memcpy(out_dist, r, 4);
+    if (out_dist2) std::memcpy(out_dist2, r + 8, 4);
+  } else {
+    if (out_dist) std::memcpy(out_dist, r, 8);
+    if (out_dist2) std::memcpy(out_dist2, r + 8, 8);
+  }
+  return DFD_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,86 @@
+// dfd_internal.h -- host-side internals shared by the library's translation units.
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <mutex>
+#include <cuda_runtime.h>
+
+#include "dfd.h"
+
+struct dfd_context {
+  int device = 0;
+  int num_sms = 0;
+  size_t smem_optin = 0;
+  dfd_options opt{};
+  int* d_err = nullptr;               // sticky device error word (+ spare control ints)
+  void* scratch = nullptr;            // grow-only device scratch
+  size_t scratch_bytes = 0;
+  void* pinned = nullptr;             // grow-only pinned host staging
+  size_t pinned_bytes = 0;
+  cudaStream_t stream = nullptr;      // internal stream (host-buffer entry points)
+  bool timing = false;                // record events around the main kernel
+  bool timed = false;                 // ev0/ev1 hold a recorded pair
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+};
+
+namespace dfd {
+
+// Status from a CUDA error, never throwing.
+inline dfd_status cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return DFD_OK;
+  if (e == cudaErrorMemoryAllocation) return DFD_ERR_OOM;
+  return DFD_ERR_CUDA;
+}
+
+// Grow the context scratch to at least `bytes`; 256-byte aligned.
+dfd_status ensure_scratch(dfd_context* ctx, size_t bytes);
+dfd_status ensure_pinned(dfd_context* ctx, size_t bytes);
+
+// Events around the main kernel of a call (measurement hooks).
+inline void timing_begin(dfd_context* ctx, cudaStream_t s) {
+  if (ctx->timing) cudaEventRecord(ctx->ev0, s);
+}
+inline void timing_end(dfd_context* ctx, cudaStream_t s) {
+  if (ctx->timing) {
+    cudaEventRecord(ctx->ev1, s);
+    ctx->timed = true;
+  }
+}
+
+inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+inline unsigned long long timeout_ns(const dfd_context* ctx) {
+  double ms = ctx->opt.wait_timeout_ms > 0 ? ctx->opt.wait_timeout_ms : 2000.0;
+  return (unsigned long long)(ms * 1.0e6);
+}
+
+// Kernel dimension class: 2, 3, 4, 8, 16 (coordinates beyond dim are zero,
+// which adds exact zeros to the squared distance).
+inline int dim_class(int dim) {
+  if (dim <= 2) return 2;
+  if (dim == 3) return 3;
+  if (dim == 4) return 4;
+  if (dim <= 8) return 8;
+  if (dim <= 16) return 16;
+  return 0;
+}
+
+// Input validation kernels: set DFD_ERR_NONFINITE / DFD_ERR_RANGE in *err.
+dfd_status launch_check_inputs(dfd_dtype dtype, int dim, const void* x, int64_t count, int* err,
+                               cudaStream_t s);
+
+// Band wavefront (K2).
+struct WaveShape {
+  int R = 4;      // rows per lane
+  int W = 4;      // compute warps per CTA
+  int ctas = 0;   // persistent CTAs (0 = auto)
+};
+dfd_status wave_plan(const dfd_context* ctx, dfd_dtype dtype, int dim, int64_t n, int64_t m, WaveShape* shape);
+dfd_status wave_run(dfd_context* ctx, dfd_dtype dtype, int dim, const void* p, int64_t n, const void* q,
+                    int64_t m, void* out_dist, void* out_dist2, cudaStream_t s, const WaveShape& shape);
+
+// Per-pair reference (K1): one CTA, row-by-row clamp scan.
+dfd_status rowscan_run(dfd_context* ctx, dfd_dtype dtype, int dim, const void* p, int64_t n, const void* q,
+                       int64_t m, void* out_dist, void* out_dist2, cudaStream_t s);
+
+}  // namespace dfd

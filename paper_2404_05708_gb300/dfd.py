@@ -1,0 +1,283 @@
+"""Thin Python binding of libdfd.so (include/dfd.h).
+
+Argument marshalling only: every step of the distance computation runs in
+the CUDA library.  If the library has not been built, or no CUDA device is
+usable, the calls raise; there is no CPU fallback.
+
+Low-level functions keep the C names and take raw integers (device
+pointers, sizes, a cudaStream_t handle).  ``Context`` wraps them for torch
+tensors: ``ctx.pair(p, q)`` with float32 or int32 CUDA tensors of shape
+``[n, dim]`` / ``[m, dim]`` returns ``(dist, dist2)`` tensors on the device.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "_build", "libdfd.so")
+
+DFD_F32, DFD_I32 = 0, 1
+STATUS = {
+    0: "DFD_OK", 1: "DFD_ERR_INVALID_ARG", 2: "DFD_ERR_RANGE", 3: "DFD_ERR_NONFINITE", 4: "DFD_ERR_OOM",
+    5: "DFD_ERR_CUDA", 6: "DFD_ERR_TIMEOUT", 7: "DFD_ERR_BUSY", 8: "DFD_ERR_CANCELLED", 9: "DFD_ERR_NOT_READY",
+    10: "DFD_ERR_UNSUPPORTED",
+}
+STATUS_CODE = {v: k for k, v in STATUS.items()}
+
+
+class DFDError(RuntimeError):
+    def __init__(self, status: int, where: str = ""):
+        self.status = int(status)
+        super().__init__(f"{where}: {STATUS.get(self.status, self.status)}")
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("struct_size", ctypes.c_size_t), ("mem_budget_bytes", ctypes.c_size_t),
+                ("max_slots", ctypes.c_int), ("wait_timeout_ms", ctypes.c_double), ("check_inputs", ctypes.c_int)]
+
+
+class WaveShape(ctypes.Structure):
+    _fields_ = [("rows_per_lane", ctypes.c_int), ("warps", ctypes.c_int), ("ctas", ctypes.c_int)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+_VP = ctypes.c_void_p
+_I64 = ctypes.c_int64
+_INT = ctypes.c_int
+
+# name -> argtypes (all return int status unless listed in _RESTYPE)
+_SIGS = {
+    "dfd_options_default": [ctypes.POINTER(Options)],
+    "dfd_status_string": [_INT],
+    "dfd_context_create": [ctypes.POINTER(_VP), _INT, ctypes.POINTER(Options)],
+    "dfd_context_destroy": [_VP],
+    "dfd_get_error": [_VP],
+    "dfd_pair": [_VP, _INT, _INT, _VP, _I64, _VP, _I64, _VP, _VP, _VP],
+    "dfd_pair_reference": [_VP, _INT, _INT, _VP, _I64, _VP, _I64, _VP, _VP, _VP],
+    "dfd_pair_host": [_VP, _INT, _INT, _VP, _I64, _VP, _I64, _VP, _VP],
+    "dfd_pair_shaped": [_VP, _INT, _INT, _VP, _I64, _VP, _I64, _VP, _VP, _VP, ctypes.POINTER(WaveShape)],
+    "dfd_pair_plan": [_VP, _INT, _INT, _I64, _I64, ctypes.POINTER(WaveShape)],
+    "dfd_debug_bounded_wait": [_VP, ctypes.c_double],
+    "dfd_timing_enable": [_VP, _INT],
+    "dfd_timing_last": [_VP, ctypes.POINTER(ctypes.c_double)],
+    "dfd_microbench": [_VP, _INT, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)],
+}
+
+MICRO_OPS = {"ffma": 0, "ffma2": 1, "fmnmx": 2, "fmnmx3": 3, "imnmx": 4, "imnmx64": 5, "imad_wide": 6,
+             "shfl": 7, "cell_f32_d3": 8, "cell_i32_d2": 9, "distonly_f32_d3": 10}
+_RESTYPE = {"dfd_status_string": ctypes.c_char_p}
+
+
+def declared_symbols():
+    return list(_SIGS)
+
+
+def load_library(path: str | None = None):
+    """Load libdfd.so (raises if it is missing: there is no fallback)."""
+    global _lib
+    with _lock:
+        if _lib is not None and path is None:
+            return _lib
+        p = path or LIB_PATH
+        if not os.path.exists(p):
+            raise RuntimeError(f"CUDA library not built: {p} (run __graft_entry__.build())")
+        lib = ctypes.CDLL(p)
+        for name, args in _SIGS.items():
+            f = getattr(lib, name, None)
+            if f is None:
+                continue
+            f.argtypes = args
+            f.restype = _RESTYPE.get(name, _INT)
+        if path is None:
+            _lib = lib
+        return lib
+
+
+def _check(st: int, where: str):
+    if st != 0:
+        raise DFDError(st, where)
+
+
+# ------------------------------------------------------------ C-named calls
+
+def dfd_options_default() -> Options:
+    o = Options()
+    _check(load_library().dfd_options_default(ctypes.byref(o)), "dfd_options_default")
+    return o
+
+
+def dfd_status_string(status: int) -> str:
+    return load_library().dfd_status_string(int(status)).decode()
+
+
+def dfd_context_create(device: int = 0, opt: Options | None = None) -> int:
+    h = _VP()
+    _check(load_library().dfd_context_create(ctypes.byref(h), int(device), ctypes.byref(opt) if opt else None),
+           "dfd_context_create")
+    return h.value
+
+
+def dfd_context_destroy(ctx: int) -> int:
+    return load_library().dfd_context_destroy(ctx)
+
+
+def dfd_get_error(ctx: int) -> int:
+    return load_library().dfd_get_error(ctx)
+
+
+def dfd_pair(ctx, dtype, dim, p, n, q, m, out_dist, out_dist2, stream) -> int:
+    return load_library().dfd_pair(ctx, dtype, dim, p, n, q, m, out_dist, out_dist2, stream)
+
+
+def dfd_pair_reference(ctx, dtype, dim, p, n, q, m, out_dist, out_dist2, stream) -> int:
+    return load_library().dfd_pair_reference(ctx, dtype, dim, p, n, q, m, out_dist, out_dist2, stream)
+
+
+def dfd_pair_host(ctx, dtype, dim, p, n, q, m, out_dist, out_dist2) -> int:
+    return load_library().dfd_pair_host(ctx, dtype, dim, p, n, q, m, out_dist, out_dist2)
+
+
+def dfd_pair_shaped(ctx, dtype, dim, p, n, q, m, out_dist, out_dist2, stream, shape: WaveShape | None) -> int:
+    return load_library().dfd_pair_shaped(ctx, dtype, dim, p, n, q, m, out_dist, out_dist2, stream,
+                                          ctypes.byref(shape) if shape is not None else None)
+
+
+def dfd_timing_enable(ctx, on: bool) -> int:
+    return load_library().dfd_timing_enable(ctx, 1 if on else 0)
+
+
+def dfd_timing_last(ctx) -> float:
+    ms = ctypes.c_double()
+    _check(load_library().dfd_timing_last(ctx, ctypes.byref(ms)), "dfd_timing_last")
+    return ms.value
+
+
+def dfd_microbench(ctx, op: int):
+    """(per-clock-per-SM rate, SM MHz) of one measurement kernel."""
+    r, mhz = ctypes.c_double(), ctypes.c_double()
+    _check(load_library().dfd_microbench(ctx, int(op), ctypes.byref(r), ctypes.byref(mhz)), "dfd_microbench")
+    return r.value, mhz.value
+
+
+def dfd_debug_bounded_wait(ctx, timeout_ms: float) -> int:
+    return load_library().dfd_debug_bounded_wait(ctx, float(timeout_ms))
+
+
+def dfd_pair_plan(ctx, dtype, dim, n, m) -> WaveShape:
+    s = WaveShape()
+    _check(load_library().dfd_pair_plan(ctx, dtype, dim, n, m, ctypes.byref(s)), "dfd_pair_plan")
+    return s
+
+
+# -------------------------------------------------------- torch convenience
+
+def _torch():
+    import torch
+    return torch
+
+
+def _dtype_code(t) -> int:
+    torch = _torch()
+    if t.dtype == torch.float32:
+        return DFD_F32
+    if t.dtype == torch.int32:
+        return DFD_I32
+    raise TypeError(f"curves must be float32 or int32, got {t.dtype}")
+
+
+def _curve(t):
+    if t.dim() == 1:
+        t = t.unsqueeze(1)
+    if t.dim() != 2:
+        raise ValueError("a curve is an [n, dim] tensor")
+    return t.contiguous()
+
+
+class Context:
+    """A libdfd context bound to one CUDA device."""
+
+    def __init__(self, device: int = 0, mem_budget_bytes: int = 0, wait_timeout_ms: float = 2000.0,
+                 check_inputs: bool = True):
+        opt = dfd_options_default()
+        opt.mem_budget_bytes = int(mem_budget_bytes)
+        opt.wait_timeout_ms = float(wait_timeout_ms)
+        opt.check_inputs = 1 if check_inputs else 0
+        self.device = int(device)
+        self.handle = dfd_context_create(self.device, opt)
+
+    def close(self):
+        if self.handle:
+            dfd_context_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def get_error(self) -> int:
+        return dfd_get_error(self.handle)
+
+    def _outs(self, dt, out_dist, out_dist2):
+        torch = _torch()
+        dev = torch.device("cuda", self.device)
+        if out_dist is None:
+            out_dist = torch.empty(1, dtype=torch.float32 if dt == DFD_F32 else torch.float64, device=dev)
+        if out_dist2 is None:
+            out_dist2 = torch.empty(1, dtype=torch.float32 if dt == DFD_F32 else torch.int64, device=dev)
+        return out_dist, out_dist2
+
+    def pair(self, p, q, out_dist=None, out_dist2=None, stream=None, shape=None, reference=False):
+        """delta and delta^2 of two device curves; enqueued on `stream` (default: current)."""
+        torch = _torch()
+        p, q = _curve(p), _curve(q)
+        dt = _dtype_code(p)
+        if _dtype_code(q) != dt or p.shape[1] != q.shape[1]:
+            raise ValueError("p and q must share dtype and dim")
+        out_dist, out_dist2 = self._outs(dt, out_dist, out_dist2)
+        s = stream if stream is not None else torch.cuda.current_stream(self.device).cuda_stream
+        args = (self.handle, dt, p.shape[1], p.data_ptr(), p.shape[0], q.data_ptr(), q.shape[0],
+                out_dist.data_ptr(), out_dist2.data_ptr(), s)
+        if reference:
+            st = dfd_pair_reference(*args)
+        elif shape is not None:
+            st = dfd_pair_shaped(*args, WaveShape(*shape))
+        else:
+            st = dfd_pair(*args)
+        _check(st, "dfd_pair")
+        return out_dist, out_dist2
+
+    def pair_host(self, p, q):
+        """delta and delta^2 of two host (numpy) curves; synchronous."""
+        import numpy as np
+        p = np.ascontiguousarray(p)
+        q = np.ascontiguousarray(q)
+        if p.ndim == 1:
+            p = p[:, None]
+        if q.ndim == 1:
+            q = q[:, None]
+        if p.dtype == np.float32:
+            dt, d1, d2 = DFD_F32, np.zeros(1, np.float32), np.zeros(1, np.float32)
+        elif p.dtype == np.int32:
+            dt, d1, d2 = DFD_I32, np.zeros(1, np.float64), np.zeros(1, np.int64)
+        else:
+            raise TypeError("curves must be float32 or int32")
+        st = dfd_pair_host(self.handle, dt, p.shape[1], p.ctypes.data, p.shape[0], q.ctypes.data, q.shape[0],
+                           d1.ctypes.data, d2.ctypes.data)
+        _check(st, "dfd_pair_host")
+        return d1[0], d2[0]
+
+    def plan(self, dtype: int, dim: int, n: int, m: int):
+        s = dfd_pair_plan(self.handle, dtype, dim, n, m)
+        return s.rows_per_lane, s.warps, s.ctas

@@ -34,3 +34,13 @@ def pytest_collection_modifyitems(config, items):
 def olib():
     import oracle
     return oracle.load()
+
+
+@pytest.fixture(scope="session")
+def dctx():
+    """A libdfd context on cuda:0 (builds the library first if needed)."""
+    from paper_2404_05708_gb300 import build, dfd
+    build.build()
+    ctx = dfd.Context(0)
+    yield ctx
+    ctx.close()

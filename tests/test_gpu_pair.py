@@ -1,0 +1,225 @@
+"""GPU parity of the single-pair entry points against the CPU oracle.
+
+float32: delta^2 from the GPU must be bit-identical to the float32 selection
+mirror (same squared-distance rounding, min/max never round) and within
+1e-6 relative of the float64 oracle; int32: delta^2 exact (int64).
+Tolerance derivation (float32): every d^2 carries at most dim+1 roundings of
+2^-24 relative each, the min/max network is monotone, so delta^2 is within
+(dim+1)*2^-24 relative of the exact value and delta within half of that plus
+one rounding of the square root: 3-D -> 1.8e-7, 16-D -> 5.7e-7 < 1e-6.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2404_05708_gb300 import workloads
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+REL_TOL = 1e-6
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def run(ctx, p, q, **kw):
+    d, d2 = ctx.pair(dev(p), dev(q), **kw)
+    torch.cuda.synchronize()
+    return d.item(), d2.item()
+
+
+def check_f32(ctx, p, q, **kw):
+    d, d2 = run(ctx, p, q, **kw)
+    mirror = float(oracle.dfd2_f32mirror(p, q))
+    ref = oracle.dfd2_linear(p, q)
+    assert d2 == mirror, (d2, mirror, p.shape, q.shape, kw)
+    if ref == 0.0:
+        assert d == 0.0
+    else:
+        assert abs(d - math.sqrt(ref)) <= REL_TOL * math.sqrt(ref), (d, math.sqrt(ref))
+    assert np.float32(d) == np.sqrt(np.float32(d2))
+    return d2
+
+
+def check_i32(ctx, p, q, **kw):
+    d, d2 = run(ctx, p, q, **kw)
+    ref = oracle.dfd2_linear(p, q)
+    assert d2 == ref, (d2, ref, p.shape, q.shape, kw)
+    assert d == math.sqrt(float(ref))
+    return d2
+
+
+def f32_walk(rng, n, dim, scale=1.0):
+    return np.cumsum(rng.normal(0, scale, size=(n, dim)), axis=0).astype(np.float32)
+
+
+def i32_walk(rng, n, dim, step=64):
+    return np.cumsum(rng.integers(-step, step + 1, size=(n, dim)), axis=0).astype(np.int32)
+
+
+# ----------------------------------------------------------- paper configs
+
+def test_pair_2000x1500_gaussian_walks(dctx):
+    p, q = workloads.gaussian_walk_pair(2000, 1500, dim=2)
+    a = check_f32(dctx, p, q)
+    b = check_f32(dctx, p, q, reference=True)
+    assert a == b
+
+
+def test_long_pair_full_size_against_stored_oracle(dctx):
+    """200,000 x 200,000 3-D pair in dfd_pair's own launch shape (the benchmarked one)."""
+    import hashlib
+    rec = json.load(open(os.path.join(HERE, "golden", "long_pair_200k.json")))
+    p, q = workloads.warped_long_pair(200_000, 200_000, dim=3, seed=3)
+    h = hashlib.sha256()
+    h.update(p.tobytes())
+    h.update(q.tobytes())
+    if h.hexdigest() != rec["sha256"]:
+        pytest.skip("regenerated curves differ from the stored record on this platform")
+    d, d2 = run(dctx, p, q)
+    assert abs(d - rec["delta_f64"]) <= REL_TOL * rec["delta_f64"], (d, rec["delta_f64"])
+    # symmetry and reversal at full size: bit-identical
+    assert run(dctx, q, p)[1] == d2
+    assert run(dctx, p[::-1].copy(), q[::-1].copy())[1] == d2
+
+
+def test_long_pair_full_size_translation_closed_form(dctx):
+    """q = p + t with exactly representable coordinates: delta^2 = |t|^2 exactly."""
+    rng = np.random.default_rng(30)
+    n = 200_000
+    p = np.cumsum(rng.integers(-1, 2, size=(n, 3)), axis=0).astype(np.float32)
+    t = np.array([3.0, -4.0, 12.0], np.float32)
+    d, d2 = run(dctx, p, p + t)
+    assert d2 == 169.0 and d == 13.0
+    pi = p.astype(np.int32)
+    d, d2 = run(dctx, pi, pi + t.astype(np.int32))
+    assert d2 == 169 and d == 13.0
+
+
+# ---------------------------------------------------------- shapes and tiles
+
+EDGE_N = [1, 2, 31, 32, 33, 63, 64, 65, 255, 256, 257, 1000]
+EDGE_M = [1, 2, 31, 32, 33, 95, 127, 128, 129, 300]
+
+
+@pytest.mark.parametrize("dtype", ["f32", "i32"])
+def test_small_pairs_tile_edges(dctx, dtype):
+    rng = np.random.default_rng(31)
+    for n in EDGE_N:
+        for m in EDGE_M:
+            dim = int(rng.choice([1, 2, 3]))
+            if dtype == "f32":
+                check_f32(dctx, f32_walk(rng, n, dim), f32_walk(rng, m, dim))
+            else:
+                check_i32(dctx, i32_walk(rng, n, dim), i32_walk(rng, m, dim))
+
+
+@pytest.mark.parametrize("dim", [1, 2, 3, 4, 5, 7, 8, 9, 13, 16])
+def test_dims(dctx, dim):
+    rng = np.random.default_rng(32 + dim)
+    n, m = int(rng.integers(300, 900)), int(rng.integers(300, 900))
+    check_f32(dctx, f32_walk(rng, n, dim), f32_walk(rng, m, dim))
+    check_f32(dctx, f32_walk(rng, n, dim), f32_walk(rng, m, dim), reference=True)
+    check_i32(dctx, i32_walk(rng, n, dim, 1000), i32_walk(rng, m, dim, 1000))
+
+
+@pytest.mark.parametrize("R", [2, 4, 6, 8])
+def test_explicit_wave_shapes(dctx, R):
+    """Several bands per CTA, several waves, single CTA: all bit-identical."""
+    rng = np.random.default_rng(40 + R)
+    p, q = f32_walk(rng, 3001, 3), f32_walk(rng, 2500, 3)
+    pi, qi = i32_walk(rng, 2777, 2), i32_walk(rng, 1999, 2)
+    want = float(oracle.dfd2_f32mirror(p, q))
+    want_i = oracle.dfd2_linear(pi, qi)
+    for W in (1, 2, 5, 16):
+        for ctas in (1, 3, 0):
+            assert run(dctx, p, q, shape=(R, W, ctas))[1] == want, (R, W, ctas)
+            assert run(dctx, pi, qi, shape=(R, W, ctas))[1] == want_i, (R, W, ctas)
+
+
+def test_reference_kernel_matches_oracle_int(dctx):
+    rng = np.random.default_rng(50)
+    for n, m in [(1, 1), (1, 700), (700, 1), (257, 513), (1200, 900)]:
+        p, q = i32_walk(rng, n, 2), i32_walk(rng, m, 2)
+        check_i32(dctx, p, q, reference=True)
+
+
+# ------------------------------------------------------------ edge cases
+
+def test_identity_symmetry_reversal_duplication(dctx):
+    rng = np.random.default_rng(51)
+    p, q = f32_walk(rng, 1500, 3), f32_walk(rng, 1100, 3)
+    assert run(dctx, p, p) == (0.0, 0.0)
+    base = run(dctx, p, q)[1]
+    assert run(dctx, q, p)[1] == base
+    assert run(dctx, p[::-1].copy(), q[::-1].copy())[1] == base
+    pd = np.insert(p, 700, p[700], axis=0)
+    assert run(dctx, pd, q)[1] == base
+
+
+def test_one_point_curves(dctx):
+    rng = np.random.default_rng(52)
+    q = i32_walk(rng, 5000, 2)
+    p = np.array([[7, -3]], np.int32)
+    want = int(np.max(np.sum((q.astype(np.int64) - p) ** 2, axis=1)))
+    assert run(dctx, p, q)[1] == want
+    assert run(dctx, q, p)[1] == want
+    assert run(dctx, p, p[:1])[1] == 0
+
+
+def test_int_extreme_coordinates(dctx):
+    big = (1 << 29) - 1
+    p = np.array([[big, -big], [-big, big], [0, 0]], np.int32)
+    q = np.array([[-big, big], [big, big]], np.int32)
+    check_i32(dctx, p, q)
+
+
+def test_host_entry_matches_device_entry(dctx):
+    p, q = workloads.gaussian_walk_pair(900, 1300, dim=3)
+    d_host, d2_host = dctx.pair_host(p, q)
+    assert float(d2_host) == run(dctx, p, q)[1]
+    pi, qi = i32_walk(np.random.default_rng(53), 800, 2), i32_walk(np.random.default_rng(54), 600, 2)
+    assert int(dctx.pair_host(pi, qi)[1]) == oracle.dfd2_linear(pi, qi)
+
+
+# ---------------------------------------------------------- error paths
+
+def test_invalid_arguments(dctx):
+    from paper_2404_05708_gb300 import dfd
+    p = dev(np.zeros((4, 2), np.float32))
+    o = torch.empty(1, device="cuda")
+    s = torch.cuda.current_stream().cuda_stream
+    assert dfd.dfd_pair(dctx.handle, 0, 2, p.data_ptr(), 0, p.data_ptr(), 4, o.data_ptr(), 0, s) == 1
+    assert dfd.dfd_pair(dctx.handle, 0, 0, p.data_ptr(), 4, p.data_ptr(), 4, o.data_ptr(), 0, s) == 1
+    assert dfd.dfd_pair(dctx.handle, 0, 2, p.data_ptr(), 4, p.data_ptr(), 4, 0, 0, s) == 1
+    assert dfd.dfd_pair(dctx.handle, 7, 2, p.data_ptr(), 4, p.data_ptr(), 4, o.data_ptr(), 0, s) == 1
+    assert dfd.dfd_pair(dctx.handle, 0, 17, p.data_ptr(), 1, p.data_ptr(), 1, o.data_ptr(), 0, s) == 10
+    assert dctx.get_error() == 0
+
+
+def test_device_input_checks(dctx):
+    p = np.zeros((10, 2), np.float32)
+    p[3, 1] = np.nan
+    run(dctx, p, np.zeros((5, 2), np.float32))
+    assert dctx.get_error() == 3          # DFD_ERR_NONFINITE, then cleared
+    assert dctx.get_error() == 0
+    pi = np.zeros((10, 2), np.int32)
+    pi[2, 0] = 1 << 30
+    run(dctx, pi, np.zeros((5, 2), np.int32))
+    assert dctx.get_error() == 2          # DFD_ERR_RANGE
+    # the context stays usable
+    check_f32(dctx, *workloads.gaussian_walk_pair(100, 120))
+
+
+def test_bounded_wait_times_out_without_hanging(dctx):
+    from paper_2404_05708_gb300 import dfd
+    assert dfd.dfd_debug_bounded_wait(dctx.handle, 5.0) == 6   # DFD_ERR_TIMEOUT
+    assert dctx.get_error() == 0
+    check_f32(dctx, *workloads.gaussian_walk_pair(64, 64))
