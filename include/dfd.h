@@ -166,12 +166,16 @@ dfd_status dfd_timing_last(dfd_context* ctx, double* ms);
  * Sec. 4 "sum of all d_ij" baseline is op 10).  Runs one kernel of many
  * independent instruction chains on every SM and returns the measured
  * throughput in thread-operations per clock per SM (cells per clock per SM
- * for the cell mixes) and the SM clock it ran at (MHz).  op:
+ * for the cell mixes; clocks per dependent operation for the latency ops)
+ * and the SM clock it ran at (MHz).  op:
  *   0 fma.f32   1 fma.f32x2   2 min.f32   3 min.f32 (3 inputs)   4 min.s32
  *   5 min.s64   6 mad.wide.s32   7 shfl.sync.up
  *   8 one float32 3-D cell (f32x2 distance + min3 + max)
  *   9 one int32 2-D cell (int64 squares + 3 x 64-bit min/max)
  *  10 one float32 3-D distance, summed instead of Eq. 1
+ *  latency (one warp per SM, clocks per dependent op):
+ *  11 min.f32   12 min3 -> max (one cell of the recurrence's chain)
+ *  13 shfl.sync.up   14 fma.f32x2   15 min.s64 -> max.s64
  * Synchronous.  DFD_ERR_INVALID_ARG for an unknown op.
  */
 dfd_status dfd_microbench(dfd_context* ctx, int op, double* per_clk_per_sm, double* sm_mhz);

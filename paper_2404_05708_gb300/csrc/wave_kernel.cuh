@@ -169,6 +169,22 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
 }
 
+// Predicated shared-memory store without a branch (keeps the unrolled
+// systolic block one basic block, so loads and distances of later steps can
+// be scheduled under the min/max chain of earlier ones).
+__device__ __forceinline__ void st_shared_if(float* p, float v, bool pred) {
+  asm volatile(
+      "{\n\t.reg .pred P;\n\tsetp.ne.u32 P, %2, 0;\n\t@P st.shared.f32 [%0], %1;\n\t}" ::"r"(smem_addr(p)), "f"(v),
+      "r"((unsigned)pred)
+      : "memory");
+}
+__device__ __forceinline__ void st_shared_if(long long* p, long long v, bool pred) {
+  asm volatile(
+      "{\n\t.reg .pred P;\n\tsetp.ne.u32 P, %2, 0;\n\t@P st.shared.s64 [%0], %1;\n\t}" ::"r"(smem_addr(p)), "l"(v),
+      "r"((unsigned)pred)
+      : "memory");
+}
+
 template <class T>
 __device__ __forceinline__ T ld_cg(const T* p) {
   return __ldcg(p);
@@ -264,11 +280,19 @@ __device__ __forceinline__ void compute_stripe(const Args& a, int w, int64_t ban
     __syncwarp();
     if (ld_volatile_smem(&ctl->abort)) break;
 
+    // The block's 32 ring inputs, one per lane (lane s holds column c0 + s);
+    // at step s lane 0 takes lane s's value.  Lane 31's outputs are gathered
+    // the same way (lane s keeps step s's) and stored after the block, so
+    // the unrolled block has no shared-memory store and no branch: later
+    // steps' q loads and distances can be scheduled under earlier chains.
+    const T in_blk = ring_in[(c0 + L) & (RING - 1)];
+    T out_blk = V::inf();
 #pragma unroll
     for (int s = 0; s < G; ++s) {
       const int col = c0 + s - L;
+      const T rin = __shfl_sync(0xffffffffu, in_blk, s);
       T u = __shfl_up_sync(0xffffffffu, bout, 1);
-      if (L == 0) u = ring_in[(c0 + s) & (RING - 1)];
+      u = (L == 0) ? rin : u;
       const int cq = max(col, 0);
       const unsigned slot = (gbase + (unsigned)(cq >> LOGC)) & (NQ - 1);
       const Rec* qp = qring + (size_t)slot * NPL * C + (cq & (C - 1));
@@ -285,7 +309,12 @@ __device__ __forceinline__ void compute_stripe(const Args& a, int w, int64_t ban
       }
       upp = u;
       bout = up;
-      if (L == 31 && col >= 0) ring_out[col & (RING - 1)] = bout;
+      const T b31 = __shfl_sync(0xffffffffu, bout, 31);
+      out_blk = (L == s) ? b31 : out_blk;
+    }
+    {
+      const int oc = c0 + L - 31;   // column lane 31 produced at step L
+      st_shared_if(ring_out + (oc & (RING - 1)), out_blk, oc >= 0);
     }
     __syncwarp();
     if (L == 31) st_release_cta(&ctl->prod[w + 1], c0 + G - 31);
@@ -390,7 +419,8 @@ __device__ __forceinline__ void comm_warp(const Args& a, int64_t band, unsigned 
         __syncwarp();
         if (L == 0) {
           st_release_cta(&ctl->cons[W], drained + 32);
-          __threadfence();
+          // The release orders the warp's row-buffer stores (made visible to
+          // lane 0 by __syncwarp) before the progress word at GPU scope.
           st_release_u64(&a.progress[band], (unsigned long long)need);
         }
         drained += 32;
