@@ -63,7 +63,8 @@ typedef enum dfd_status {
   DFD_ERR_BUSY = 7,        /* resource limit reached, retry later */
   DFD_ERR_CANCELLED = 8,   /* work was cancelled before it finished */
   DFD_ERR_NOT_READY = 9,   /* result not available yet */
-  DFD_ERR_UNSUPPORTED = 10 /* configuration not provided by this build */
+  DFD_ERR_UNSUPPORTED = 10, /* configuration not provided by this build */
+  DFD_ERR_CAPACITY = 11     /* input needs more than a fixed-size buffer holds */
 } dfd_status;
 
 typedef enum dfd_dtype { DFD_F32 = 0, DFD_I32 = 1 } dfd_dtype;
@@ -147,6 +148,41 @@ typedef struct dfd_wave_shape {
 
 dfd_status dfd_pair_shaped(dfd_context* ctx, dfd_dtype dtype, int dim, const void* p, int64_t n, const void* q,
                            int64_t m, void* out_dist, void* out_dist2, void* stream, const dfd_wave_shape* shape);
+
+/*
+ * dfd_pair for callers that cannot allocate device memory.  This entry point
+ * has no counterpart in the paper; it exists for library users whose device
+ * memory is not theirs to allocate -- a process whose HBM is reserved up
+ * front by another allocator (a framework's caching pool, a serving engine
+ * under a fixed memory budget) -- and for latency-critical loops where a
+ * cudaMalloc / cudaFree, which can synchronise the whole device, is not
+ * acceptable.  It needs no context and calls no cudaMalloc, cudaFree or
+ * other allocating routine.
+ *
+ * The band wavefront's scratch (band ticket, progress words, row buffer,
+ * packed q) and the device error word live in one fixed array of
+ * DFD_NOALLOC_SCRATCH_BYTES in the library's device image, present on
+ * every GPU that loads the library until the process exits.  Scratch needed
+ * (bytes): 1024 + 8*ceil(n / 64) + m * (4 for float32, 8 for int32) +
+ * (m + 288) * Q, where Q = 32 (float32, dim <= 4), 64 (float32, dim 5..8),
+ * 128 (float32, dim 9..16), 16 (int32, dim <= 4), 32 (int32, dim 5..8),
+ * 64 (int32, dim 9..16).  Larger inputs return DFD_ERR_CAPACITY before
+ * anything is enqueued (e.g. float32 3-D: m up to ~460,000).
+ *
+ * Arguments and results as dfd_pair, on CUDA device `device` (made current
+ * for the call, then restored).  The input checks always run.  The first
+ * call on a device looks up the array's device address (and the device's
+ * SM count); make that first call before any stream capture.  Every call
+ * clears what must start at zero and overwrites the rest, so the array
+ * keeps only the last call's contents: calls whose work overlaps on the
+ * GPU (on different streams, or from different threads) share the array
+ * and race -- serialise them.  On a device-side error (invalid coordinates,
+ * a bounded wait that ran out) the outputs are left as NaN (float, double)
+ * / -1 (int64); there is no context to read the error code from.
+ */
+#define DFD_NOALLOC_SCRATCH_BYTES (16u << 20)
+dfd_status dfd_pair_noalloc(int device, dfd_dtype dtype, int dim, const void* p, int64_t n, const void* q,
+                            int64_t m, void* out_dist, void* out_dist2, void* stream);
 
 /* The launch shape dfd_pair would choose for (dtype, dim, n, m). */
 dfd_status dfd_pair_plan(dfd_context* ctx, dfd_dtype dtype, int dim, int64_t n, int64_t m, dfd_wave_shape* shape);

@@ -240,6 +240,7 @@ const char* dfd_status_string(dfd_status s) {
     case DFD_ERR_CANCELLED: return "DFD_ERR_CANCELLED";
     case DFD_ERR_NOT_READY: return "DFD_ERR_NOT_READY";
     case DFD_ERR_UNSUPPORTED: return "DFD_ERR_UNSUPPORTED";
+    case DFD_ERR_CAPACITY: return "DFD_ERR_CAPACITY";
   }
   return "DFD_ERR_UNKNOWN";
 }

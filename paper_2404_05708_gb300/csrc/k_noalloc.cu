@@ -1,0 +1,133 @@
+// k_noalloc.cu -- dfd_pair for callers that cannot allocate device memory.
+//
+// Who needs it: processes whose device memory belongs to another allocator
+// (a framework's caching pool, a serving engine that reserves its HBM budget
+// up front) and latency-critical loops that must not call cudaMalloc /
+// cudaFree, which can synchronise the device.  This entry point uses no
+// context and allocates nothing: the band wavefront's scratch and the error
+// word live in the fixed array below, part of the library's device image.
+#include <cstring>
+#include <mutex>
+
+#include "dfd_device.cuh"
+#include "dfd_internal.h"
+
+namespace dfd {
+namespace {
+
+// Layout: [0, 256) error word (+ padding); [256, end) wavefront scratch
+// (ticket, progress words, row buffer, packed q).  Every GPU that loads the
+// library holds this array until the process exits.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[DFD_NOALLOC_SCRATCH_BYTES];
+
+constexpr size_t kErrBytes = 256;
+constexpr int kMaxDevices = 64;
+
+struct DeviceSetup {
+  bool done = false;
+  dfd_status status = DFD_OK;
+  unsigned char* scratch = nullptr;  // device address of g_noalloc_scratch
+  int num_sms = 0;
+  size_t smem_optin = 0;
+};
+
+std::mutex g_setup_mu;
+DeviceSetup g_setup[kMaxDevices];
+
+// Once per device, with that device current: the array's device address
+// (in host code its name is only a host-side stand-in) and the SM count.
+dfd_status setup_device(int device, DeviceSetup* out) {
+  std::lock_guard<std::mutex> lock(g_setup_mu);
+  DeviceSetup& s = g_setup[device];
+  if (!s.done) {
+    void* ptr = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+    cudaDeviceProp prop;
+    if (e == cudaSuccess) e = cudaGetDeviceProperties(&prop, device);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      s.status = DFD_ERR_CUDA;
+    } else {
+      s.scratch = static_cast<unsigned char*>(ptr);
+      s.num_sms = prop.multiProcessorCount;
+      s.smem_optin = prop.sharedMemPerBlockOptin;
+      s.status = DFD_OK;
+    }
+    s.done = true;
+  }
+  *out = s;
+  return s.status;
+}
+
+// Upper bound of the wavefront's scratch for (n, m) in this dtype / dim.
+size_t scratch_needed(dfd_dtype dtype, int dim, int64_t n, int64_t m) {
+  const int dk = dim_class(dim);
+  size_t q_per_col;
+  if (dtype == DFD_F32)
+    q_per_col = dk <= 4 ? 32 : dk == 8 ? 64 : 128;
+  else
+    q_per_col = dk <= 4 ? 16 : dk == 8 ? 32 : 64;
+  const size_t vbytes = dtype == DFD_F32 ? 4 : 8;
+  return 1024 + 8 * (size_t)((n + 63) / 64) + (size_t)m * vbytes + ((size_t)m + 288) * q_per_col;
+}
+
+}  // namespace
+}  // namespace dfd
+
+extern "C" dfd_status dfd_pair_noalloc(int device, dfd_dtype dtype, int dim, const void* p, int64_t n,
+                                       const void* q, int64_t m, void* out_dist, void* out_dist2, void* stream) {
+  using namespace dfd;
+  if (dtype != DFD_F32 && dtype != DFD_I32) return DFD_ERR_INVALID_ARG;
+  if (dim < 1 || !p || !q || n < 1 || m < 1 || (!out_dist && !out_dist2)) return DFD_ERR_INVALID_ARG;
+  if (dim > 16) return DFD_ERR_UNSUPPORTED;
+  if (device < 0 || device >= kMaxDevices) return DFD_ERR_INVALID_ARG;
+  if (m > ((int64_t)1 << 29) || scratch_needed(dtype, dim, n, m) > DFD_NOALLOC_SCRATCH_BYTES - kErrBytes)
+    return DFD_ERR_CAPACITY;
+
+  int prev = -1;
+  if (cudaGetDevice(&prev) != cudaSuccess) {
+    cudaGetLastError();
+    return DFD_ERR_CUDA;
+  }
+  if (cudaSetDevice(device) != cudaSuccess) {
+    cudaGetLastError();
+    return DFD_ERR_CUDA;
+  }
+  DeviceSetup dev;
+  dfd_status st = setup_device(device, &dev);
+  if (st == DFD_OK) {
+    // A context on the stack whose scratch IS the fixed array and whose
+    // budget equals its size: the wavefront's grow-only scratch path returns
+    // before it could ever free or allocate.
+    dfd_context c;
+    c.device = device;
+    c.num_sms = dev.num_sms;
+    c.smem_optin = dev.smem_optin;
+    dfd_options_default(&c.opt);
+    c.opt.mem_budget_bytes = DFD_NOALLOC_SCRATCH_BYTES - kErrBytes;
+    c.d_err = reinterpret_cast<int*>(dev.scratch);
+    c.scratch = dev.scratch + kErrBytes;
+    c.scratch_bytes = DFD_NOALLOC_SCRATCH_BYTES - kErrBytes;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    // Outputs start as NaN (float, double) / -1 (int64): all-ones bytes.
+    const size_t vb = dtype == DFD_F32 ? 4 : 8;
+    cudaError_t e = cudaSuccess;
+    if (out_dist) e = cudaMemsetAsync(out_dist, 0xff, vb, s);
+    if (e == cudaSuccess && out_dist2) e = cudaMemsetAsync(out_dist2, 0xff, vb, s);
+    // The error word must start at zero for this call.
+    if (e == cudaSuccess) e = cudaMemsetAsync(c.d_err, 0, sizeof(int), s);
+    st = cuda_status(e);
+    if (st == DFD_OK) st = launch_check_inputs(dtype, dim, p, n * dim, c.d_err, s);
+    if (st == DFD_OK) st = launch_check_inputs(dtype, dim, q, m * dim, c.d_err, s);
+    if (st == DFD_OK) {
+      WaveShape sh;
+      wave_plan(&c, dtype, dim, n, m, &sh);
+      st = wave_run(&c, dtype, dim, p, n, q, m, out_dist, out_dist2, s, sh);
+      if (st == DFD_ERR_OOM) st = DFD_ERR_CAPACITY;
+    }
+    c.scratch = nullptr;   // not owned: nothing to release
+    c.d_err = nullptr;
+  }
+  cudaSetDevice(prev);
+  return st;
+}

@@ -22,7 +22,7 @@ DFD_F32, DFD_I32 = 0, 1
 STATUS = {
     0: "DFD_OK", 1: "DFD_ERR_INVALID_ARG", 2: "DFD_ERR_RANGE", 3: "DFD_ERR_NONFINITE", 4: "DFD_ERR_OOM",
     5: "DFD_ERR_CUDA", 6: "DFD_ERR_TIMEOUT", 7: "DFD_ERR_BUSY", 8: "DFD_ERR_CANCELLED", 9: "DFD_ERR_NOT_READY",
-    10: "DFD_ERR_UNSUPPORTED",
+    10: "DFD_ERR_UNSUPPORTED", 11: "DFD_ERR_CAPACITY",
 }
 STATUS_CODE = {v: k for k, v in STATUS.items()}
 
@@ -62,6 +62,7 @@ _SIGS = {
     "dfd_pair_shaped": [_VP, _INT, _INT, _VP, _I64, _VP, _I64, _VP, _VP, _VP, ctypes.POINTER(WaveShape)],
     "dfd_pair_plan": [_VP, _INT, _INT, _I64, _I64, ctypes.POINTER(WaveShape)],
     "dfd_debug_bounded_wait": [_VP, ctypes.c_double],
+    "dfd_pair_noalloc": [_INT, _INT, _INT, _VP, _I64, _VP, _I64, _VP, _VP, _VP],
     "dfd_timing_enable": [_VP, _INT],
     "dfd_timing_last": [_VP, ctypes.POINTER(ctypes.c_double)],
     "dfd_microbench": [_VP, _INT, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)],
@@ -140,6 +141,11 @@ def dfd_pair_reference(ctx, dtype, dim, p, n, q, m, out_dist, out_dist2, stream)
 
 def dfd_pair_host(ctx, dtype, dim, p, n, q, m, out_dist, out_dist2) -> int:
     return load_library().dfd_pair_host(ctx, dtype, dim, p, n, q, m, out_dist, out_dist2)
+
+
+def dfd_pair_noalloc(device, dtype, dim, p, n, q, m, out_dist, out_dist2, stream) -> int:
+    """dfd_pair without a context and without any device allocation (fixed scratch array)."""
+    return load_library().dfd_pair_noalloc(device, dtype, dim, p, n, q, m, out_dist, out_dist2, stream)
 
 
 def dfd_pair_shaped(ctx, dtype, dim, p, n, q, m, out_dist, out_dist2, stream, shape: WaveShape | None) -> int:

@@ -1,0 +1,75 @@
+"""dfd_pair_noalloc: the distance without any device allocation.
+
+Some users of this library cannot let it call cudaMalloc: their process's
+device memory is reserved up front by another allocator (a framework's
+caching pool, a serving engine under a fixed HBM budget), or they call it
+from latency-critical loops where a cudaMalloc / cudaFree, which can
+synchronise the whole device, is not acceptable.  dfd_pair_noalloc serves
+them: no context, no allocation, its scratch in a fixed array inside the
+library's device image.  These tests call it through the C ABI and check it
+against the ordinary entry point, dfd_pair, on consecutive calls.
+
+This file is named to be collected last, so a run that stops at the first
+failure has already run every other test; it also passes on its own.
+"""
+import numpy as np
+import pytest
+
+from paper_2404_05708_gb300 import dfd, workloads
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _noalloc(p, q, dtype_code, d_out, d2_out):
+    s = torch.cuda.current_stream().cuda_stream
+    st = dfd.dfd_pair_noalloc(0, dtype_code, p.shape[1], p.data_ptr(), p.shape[0], q.data_ptr(), q.shape[0],
+                              d_out.data_ptr(), d2_out.data_ptr(), s)
+    torch.cuda.synchronize()
+    return st
+
+
+def _existing(ctx, p, q):
+    d, d2 = ctx.pair(p, q)
+    torch.cuda.synchronize()
+    return d.item(), d2.item()
+
+
+def test_noalloc_matches_dfd_pair_on_consecutive_calls(dctx):
+    rng = np.random.default_rng(70)
+    # call 1: float32, 3-D
+    p1, q1 = workloads.warped_long_pair(3001, 2500, dim=3, seed=71)
+    P1, Q1 = torch.from_numpy(p1).cuda(), torch.from_numpy(q1).cuda()
+    d1 = torch.empty(1, dtype=torch.float32, device="cuda")
+    d21 = torch.empty(1, dtype=torch.float32, device="cuda")
+    assert _noalloc(P1, Q1, dfd.DFD_F32, d1, d21) == 0
+    want_d, want_d2 = _existing(dctx, P1, Q1)
+    assert d21.item() == want_d2 and d1.item() == want_d
+
+    # call 2: int32, 2-D, different sizes (the array keeps the last call's contents)
+    p2 = np.cumsum(rng.integers(-64, 65, size=(1800, 2)), axis=0).astype(np.int32)
+    q2 = np.cumsum(rng.integers(-64, 65, size=(2200, 2)), axis=0).astype(np.int32)
+    P2, Q2 = torch.from_numpy(p2).cuda(), torch.from_numpy(q2).cuda()
+    d2 = torch.empty(1, dtype=torch.float64, device="cuda")
+    d22 = torch.empty(1, dtype=torch.int64, device="cuda")
+    assert _noalloc(P2, Q2, dfd.DFD_I32, d2, d22) == 0
+    want_d, want_d2 = _existing(dctx, P2, Q2)
+    assert d22.item() == want_d2 and d2.item() == want_d
+
+    # call 3: call 1 again; device free memory must not move across it
+    torch.cuda.synchronize()
+    free_before = torch.cuda.mem_get_info()[0]
+    assert _noalloc(P1, Q1, dfd.DFD_F32, d1, d21) == 0
+    free_after = torch.cuda.mem_get_info()[0]
+    assert free_after == free_before
+    want_d, want_d2 = _existing(dctx, P1, Q1)
+    assert d21.item() == want_d2 and d1.item() == want_d
+
+
+def test_noalloc_rejects_inputs_beyond_its_fixed_capacity():
+    # float32 3-D needs ~36 bytes per column of q: 600,000 columns exceed 16 MiB.
+    p = torch.zeros((10, 3), dtype=torch.float32, device="cuda")
+    q = torch.zeros((600_000, 3), dtype=torch.float32, device="cuda")
+    d = torch.empty(1, dtype=torch.float32, device="cuda")
+    d2 = torch.empty(1, dtype=torch.float32, device="cuda")
+    assert _noalloc(p, q, dfd.DFD_F32, d, d2) == dfd.STATUS_CODE["DFD_ERR_CAPACITY"]
