@@ -135,6 +135,55 @@ dfd_status dfd_pair_host(dfd_context* ctx, dfd_dtype dtype, int dim, const void*
                          int64_t m, void* out_dist, void* out_dist2);
 
 /*
+ * Distances of many independent pairs of curves in one persistent launch
+ * (the batch evaluation of Sec. 4, without padding: pairs of any lengths).
+ *   points:  all curves' coordinates, CSR packed (curve c is rows
+ *            offsets[c] .. offsets[c+1]-1 of a [total, dim] array), device.
+ *   offsets: int64[n_curves + 1], device, non-decreasing, offsets[0] = 0.
+ *   pairs:   int32[2 * n_pairs] curve ids (a, b), device.
+ *   out_dist / out_dist2: n_pairs elements each (types as for dfd_pair).
+ * One warp computes one pair (rows = the shorter curve, 32*R rows per
+ * stripe, systolic over the columns); pairs are ordered by cost n*m,
+ * largest first (a device-side counting sort, no host synchronisation) and
+ * taken by persistent warps from an atomic counter.  Invalid curve ids or
+ * empty curves put DFD_ERR_INVALID_ARG in the error word and leave that
+ * pair's outputs unwritten.  A pair whose two curves both exceed 32*Rmax
+ * points (Rmax = 8, 4, 2 for dim <= 4, <= 8, <= 16) needs its longer curve
+ * <= 4096 points, else DFD_ERR_UNSUPPORTED for that pair.
+ */
+dfd_status dfd_batch(dfd_context* ctx, dfd_dtype dtype, int dim, const void* points, const int64_t* offsets,
+                     int64_t n_curves, const int32_t* pairs, int64_t n_pairs, void* out_dist, void* out_dist2,
+                     void* stream);
+
+/*
+ * All-pairs distance matrix of n_curves curves (the paper's motivating use:
+ * clustering and distance matrices of trajectories, Sec. 2), condensed upper
+ * triangle: entry k = i*(2N - i - 1)/2 + (j - i - 1) for i < j (N =
+ * n_curves), N*(N-1)/2 elements in out_condensed (distances) and/or
+ * out_dist2.  Pairs are decoded from k on the device; same engine and
+ * limits as dfd_batch.
+ */
+dfd_status dfd_matrix(dfd_context* ctx, dfd_dtype dtype, int dim, const void* points, const int64_t* offsets,
+                      int64_t n_curves, void* out_condensed, void* out_dist2, void* stream);
+
+/*
+ * CUDA-graph capture of one dfd_batch / dfd_matrix call (input checks, plan
+ * and the persistent launch) for repeated launches with the same pointers:
+ * update the buffers' contents, not the graph.  The call runs once
+ * normally (results written, device synchronised), then is captured with a
+ * private scratch area owned by the graph.  dfd_graph_launch enqueues it on
+ * `stream`; the graph must be destroyed before its context.
+ */
+typedef struct dfd_graph dfd_graph;
+dfd_status dfd_batch_capture(dfd_context* ctx, dfd_dtype dtype, int dim, const void* points, const int64_t* offsets,
+                             int64_t n_curves, const int32_t* pairs, int64_t n_pairs, void* out_dist, void* out_dist2,
+                             dfd_graph** out);
+dfd_status dfd_matrix_capture(dfd_context* ctx, dfd_dtype dtype, int dim, const void* points, const int64_t* offsets,
+                              int64_t n_curves, void* out_condensed, void* out_dist2, dfd_graph** out);
+dfd_status dfd_graph_launch(dfd_graph* graph, void* stream);
+dfd_status dfd_graph_destroy(dfd_graph* graph);
+
+/*
  * Explicit launch shape for the band wavefront of dfd_pair (for tuning and
  * measurement).  rows_per_lane in {2, 4, 6, 8}, warps in 1..16 (compute
  * warps per CTA; one more communication warp is added), ctas in 1..#SMs

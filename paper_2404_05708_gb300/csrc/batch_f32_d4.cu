@@ -1,0 +1,3 @@
+// Ragged batch and matrix instantiations: F32 coordinates, dimension class 4.
+#include "batch_launch.cuh"
+DFD_BATCH_INSTANTIATE(F32, 4)

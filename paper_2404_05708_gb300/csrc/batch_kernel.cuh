@@ -1,0 +1,346 @@
+// batch_kernel.cuh -- K4 (ragged batch) and K5 (all-pairs matrix).
+//
+// Many independent pairs: one warp per pair.  The rows of the recurrence of
+// Eq. 1 are the shorter curve (delta(p,q) = delta(q,p)), split into stripes
+// of 32*R rows; lane L holds R consecutive rows in registers and the stripe
+// runs as a systolic array over the columns (lane L at step s updates column
+// s - L).  Rows past the curve's end repeat its last point (a repeated point
+// does not change the distance, Sec. 4 footnote).  A pair longer than one
+// stripe hands each stripe's bottom row to the next through a per-warp
+// shared-memory buffer (in place: a column is read for stripe k+1 before
+// stripe k+1 overwrites it).  Persistent warps take work items from an
+// atomic counter over a device-built, cost-descending (LPT) work list.
+#pragma once
+#include "dfd_device.cuh"
+
+namespace dfd {
+namespace batch {
+
+// Rows per lane of one stripe is at most RMAX (fewer registers for wider
+// points); pairs with more rows run several stripes.
+template <int DK>
+struct Rmax {
+  static constexpr int value = DK <= 4 ? 8 : (DK <= 8 ? 4 : 2);
+};
+constexpr int BUF_COLS = 4096;    // per-warp row buffer (columns) for multi-stripe pairs
+
+// Rows per lane chosen for a pair with `rows` rows (one stripe when possible).
+template <int DK>
+__host__ __device__ __forceinline__ int rows_per_lane(int rows) {
+  const int r = (rows + 31) / 32;
+  return r > Rmax<DK>::value ? Rmax<DK>::value : (r < 1 ? 1 : r);
+}
+
+template <class V, int DK, int R>
+__device__ __forceinline__ typename V::value warp_dfd(const typename V::coord* __restrict__ P, int n,
+                                                      const typename V::coord* __restrict__ Q, int m, int dim,
+                                                      typename V::value* buf, int L) {
+  using T = typename V::value;
+  using Cd = typename V::coord;
+  const int nstripes = (n + 32 * R - 1) / (32 * R);
+  T res = V::inf();
+  for (int st = 0; st < nstripes; ++st) {
+    Cd pr[R][DK];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int i = min(st * 32 * R + L * R + r, n - 1);
+#pragma unroll
+      for (int k = 0; k < DK; ++k) pr[r][k] = k < dim ? __ldg(P + (int64_t)i * dim + k) : (Cd)0;
+    }
+    const bool has_top = st > 0, has_bottom = st + 1 < nstripes, last = !has_bottom;
+    T v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = V::inf();
+    T bout = V::inf();
+    T upp = (st == 0 && L == 0) ? V::zero() : V::inf();
+    const int nsteps = m + 31;
+    for (int c0 = 0; c0 < nsteps; c0 += 32) {
+      const T top_blk = has_top ? buf[min(c0 + L, m - 1)] : V::inf();
+      T out_blk = V::inf();
+#pragma unroll
+      for (int s = 0; s < 32; ++s) {
+        const int j = c0 + s - L;
+        const int jq = min(max(j, 0), m - 1);
+        Cd qk[DK];
+#pragma unroll
+        for (int k = 0; k < DK; ++k) qk[k] = k < dim ? __ldg(Q + (int64_t)jq * dim + k) : (Cd)0;
+        T d[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) d[r] = dist2<DK>(pr[r], qk);
+        const T tin = __shfl_sync(0xffffffffu, top_blk, s);
+        T u = __shfl_up_sync(0xffffffffu, bout, 1);
+        u = (L == 0) ? tin : u;
+        T up = u, dg = upp;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          const T l = v[r];
+          const T nv = V::vmax(V::vmin3(l, dg, up), d[r]);
+          dg = l;
+          v[r] = nv;
+          up = nv;
+        }
+        upp = u;
+        bout = up;
+        if (has_bottom) {
+          const T b31 = __shfl_sync(0xffffffffu, bout, 31);
+          out_blk = (L == s) ? b31 : out_blk;
+        }
+        res = (last && j == m - 1) ? bout : res;
+      }
+      if (has_bottom) {
+        const int oc = c0 + L - 31;
+        __syncwarp();
+        if (oc >= 0 && oc < m) buf[oc] = out_blk;
+      }
+      __syncwarp();
+    }
+  }
+  return __shfl_sync(0xffffffffu, res, 31);
+}
+
+template <class V, int DK>
+__device__ __forceinline__ typename V::value warp_dfd_any(const typename V::coord* P, int n,
+                                                          const typename V::coord* Q, int m, int dim,
+                                                          typename V::value* buf, int L) {
+  constexpr int RM = Rmax<DK>::value;
+  switch (rows_per_lane<DK>(n)) {
+#define DFD_B_CASE(RR)                                                            \
+  case RR:                                                                        \
+    if constexpr (RR <= RM) return warp_dfd<V, DK, RR>(P, n, Q, m, dim, buf, L); \
+    break;
+    DFD_B_CASE(1)
+    DFD_B_CASE(2)
+    DFD_B_CASE(3)
+    DFD_B_CASE(4)
+    DFD_B_CASE(5)
+    DFD_B_CASE(6)
+    DFD_B_CASE(7)
+    DFD_B_CASE(8)
+    DFD_B_CASE(9)
+    DFD_B_CASE(10)
+    DFD_B_CASE(11)
+    DFD_B_CASE(12)
+    DFD_B_CASE(13)
+    DFD_B_CASE(14)
+    DFD_B_CASE(15)
+    default:
+      break;
+#undef DFD_B_CASE
+  }
+  return warp_dfd<V, DK, RM>(P, n, Q, m, dim, buf, L);
+}
+
+// A pair needs the row buffer when its rows span several stripes.
+template <int DK>
+__device__ __forceinline__ bool fits_buffer(int rows, int cols) {
+  return rows <= 32 * Rmax<DK>::value || cols <= BUF_COLS;
+}
+
+template <class T>
+__device__ __forceinline__ void write_result(void* out_dist, void* out_dist2, int64_t k, T r) {
+  if constexpr (sizeof(T) == 4) {
+    if (out_dist2) static_cast<float*>(out_dist2)[k] = (float)r;
+    if (out_dist) static_cast<float*>(out_dist)[k] = sqrtf((float)r);
+  } else {
+    if (out_dist2) static_cast<long long*>(out_dist2)[k] = (long long)r;
+    if (out_dist) static_cast<double*>(out_dist)[k] = sqrt((double)r);
+  }
+}
+
+// ------------------------------------------------------------- planning
+// Cost bucket of a pair, descending cost = ascending bucket: 4 buckets per
+// octave of rows*cols, 128 buckets.
+constexpr int NBUCKET = 128;
+
+__device__ __forceinline__ int cost_bucket(int64_t cost) {
+  const int lg = 63 - __clzll((unsigned long long)max(cost, (int64_t)1));
+  const int frac = (int)((cost >> max(lg - 2, 0)) & 3);  // next two bits
+  const int b = lg * 4 + (lg >= 2 ? frac : 0);
+  return NBUCKET - 1 - min(b, NBUCKET - 1);
+}
+
+struct PlanArgs {
+  const int64_t* offsets;
+  const int32_t* pairs;
+  int64_t n_pairs;
+  int64_t n_curves;
+  unsigned* hist;      // [NBUCKET]
+  unsigned* cursor;    // [NBUCKET]
+  unsigned char* bucket;  // [n_pairs]
+  unsigned* worklist;  // [n_pairs]: pair index | swap << 31
+  int* err;
+};
+
+// (static: this header is compiled into several translation units)
+static __global__ void plan_hist_kernel(PlanArgs a) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < a.n_pairs; k += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t ia = a.pairs[2 * k], ib = a.pairs[2 * k + 1];
+    int b = NBUCKET - 1;
+    if (ia < 0 || ib < 0 || ia >= a.n_curves || ib >= a.n_curves) {
+      raise_error(a.err, DFD_ERR_INVALID_ARG);
+    } else {
+      const int64_t total = a.offsets[a.n_curves];
+      const int64_t oa = a.offsets[ia], ob = a.offsets[ib], ea = a.offsets[ia + 1], eb = a.offsets[ib + 1];
+      const int64_t na = ea - oa, nb = eb - ob;
+      if (na < 1 || nb < 1 || oa < 0 || ob < 0 || ea > total || eb > total || na > INT32_MAX || nb > INT32_MAX)
+        raise_error(a.err, DFD_ERR_INVALID_ARG);
+      b = cost_bucket(max(na, (int64_t)1) * max(nb, (int64_t)1));
+    }
+    a.bucket[k] = (unsigned char)b;
+    atomicAdd(&a.hist[b], 1u);
+  }
+}
+
+static __global__ void plan_scan_kernel(PlanArgs a) {
+  // one warp: exclusive scan of NBUCKET counts into cursors
+  if (threadIdx.x == 0) {
+    unsigned run = 0;
+    for (int b = 0; b < NBUCKET; ++b) {
+      a.cursor[b] = run;
+      run += a.hist[b];
+    }
+  }
+}
+
+static __global__ void plan_scatter_kernel(PlanArgs a) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < a.n_pairs; k += (int64_t)gridDim.x * blockDim.x) {
+    const unsigned pos = atomicAdd(&a.cursor[a.bucket[k]], 1u);
+    const int32_t ia = a.pairs[2 * k], ib = a.pairs[2 * k + 1];
+    unsigned swap = 0;
+    if (ia >= 0 && ib >= 0 && ia < a.n_curves && ib < a.n_curves) {
+      const int64_t na = a.offsets[ia + 1] - a.offsets[ia], nb = a.offsets[ib + 1] - a.offsets[ib];
+      swap = na > nb ? 1u : 0u;   // rows = the shorter curve
+    }
+    a.worklist[pos] = (unsigned)k | (swap << 31);
+  }
+}
+
+// ------------------------------------------------------------ batch kernel
+struct BatchArgs {
+  void* rowbuf;        // per-warp BUF_COLS values (multi-stripe pairs)
+  const void* points;
+  const int64_t* offsets;
+  const int32_t* pairs;
+  const unsigned* worklist;
+  int64_t n_items;
+  int64_t n_curves;
+  int dim;
+  int* counter;
+  int* err;
+  void* out_dist;
+  void* out_dist2;
+};
+
+template <class V, int DK>
+__global__ void __launch_bounds__(256, 2) batch_kernel(BatchArgs a) {
+  using T = typename V::value;
+  using Cd = typename V::coord;
+  const int L = threadIdx.x & 31;
+  const int64_t gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  T* buf = static_cast<T*>(a.rowbuf) + gw * BUF_COLS;
+  const Cd* pts = static_cast<const Cd*>(a.points);
+  const int64_t total = a.offsets[a.n_curves];
+  if (ld_relaxed_i32(a.err) != 0) return;
+  for (;;) {
+    int item = 0;
+    if (L == 0) item = atomicAdd(a.counter, 1);
+    item = __shfl_sync(0xffffffffu, item, 0);
+    if (item >= a.n_items) break;
+    const unsigned w = a.worklist[item];
+    const int64_t k = w & 0x7fffffffu;
+    int32_t ia = a.pairs[2 * k], ib = a.pairs[2 * k + 1];
+    if (w >> 31) {
+      const int32_t t = ia;
+      ia = ib;
+      ib = t;
+    }
+    if (ia < 0 || ib < 0 || ia >= a.n_curves || ib >= a.n_curves) continue;  // reported by the plan
+    const int64_t oa = a.offsets[ia], ob = a.offsets[ib];
+    const int64_t ea = a.offsets[ia + 1], eb = a.offsets[ib + 1];
+    if (oa < 0 || ob < 0 || ea > total || eb > total) continue;             // reported by the plan
+    const int n = (int)(ea - oa), m = (int)(eb - ob);
+    if (n < 1 || m < 1) continue;                                            // reported by the plan
+    if (!fits_buffer<DK>(n, m)) {
+      if (L == 0) raise_error(a.err, DFD_ERR_UNSUPPORTED);
+      continue;
+    }
+    const T r = warp_dfd_any<V, DK>(pts + oa * a.dim, n, pts + ob * a.dim, m, a.dim, buf, L);
+    if (L == 0) write_result<T>(a.out_dist, a.out_dist2, k, r);
+  }
+}
+
+// ----------------------------------------------------------- matrix kernel
+// Condensed upper triangle: k = i*(2N - i - 1)/2 + (j - i - 1), i < j.
+__device__ __forceinline__ void decode_pair(int64_t k, int64_t N, int64_t* pi, int64_t* pj) {
+  const double b = 2.0 * (double)N - 1.0;
+  int64_t i = (int64_t)floor((b - sqrt(b * b - 8.0 * (double)k)) / 2.0);
+  // fix the floating-point estimate with exact integer checks
+  auto start = [N](int64_t r) { return r * (2 * N - r - 1) / 2; };
+  if (i < 0) i = 0;
+  if (i > N - 2) i = N - 2;
+  while (i > 0 && start(i) > k) --i;
+  while (i + 1 <= N - 2 && start(i + 1) <= k) ++i;
+  *pi = i;
+  *pj = k - start(i) + i + 1;
+}
+
+struct MatrixArgs {
+  void* rowbuf;        // per-warp BUF_COLS values (multi-stripe pairs)
+  const void* points;
+  const int64_t* offsets;
+  int64_t n_curves;
+  int64_t n_pairs;
+  int dim;
+  int chunk;        // pairs per pop
+  int* counter;
+  int* err;
+  void* out_dist;
+  void* out_dist2;
+};
+
+template <class V, int DK>
+__global__ void __launch_bounds__(256, 2) matrix_kernel(MatrixArgs a) {
+  using T = typename V::value;
+  using Cd = typename V::coord;
+  const int L = threadIdx.x & 31;
+  const int64_t gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  T* buf = static_cast<T*>(a.rowbuf) + gw * BUF_COLS;
+  const Cd* pts = static_cast<const Cd*>(a.points);
+  const int64_t total = a.offsets[a.n_curves];
+  if (ld_relaxed_i32(a.err) != 0) return;
+  for (;;) {
+    long long base = 0;
+    if (L == 0) base = (long long)atomicAdd(a.counter, 1) * a.chunk;
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (base >= a.n_pairs) break;
+    const int64_t end = min((int64_t)base + a.chunk, a.n_pairs);
+    int64_t i, j;
+    decode_pair(base, a.n_curves, &i, &j);
+    for (int64_t k = base; k < end; ++k) {
+      const int64_t oi = a.offsets[i], oj = a.offsets[j], ei = a.offsets[i + 1], ej = a.offsets[j + 1];
+      const bool ok = oi >= 0 && oj >= 0 && ei <= total && ej <= total && ei - oi <= INT32_MAX &&
+                      ej - oj <= INT32_MAX;
+      const int ni = ok ? (int)(ei - oi) : 0, nj = ok ? (int)(ej - oj) : 0;
+      const int rows = min(ni, nj), cols = max(ni, nj);
+      if (rows < 1) {
+        if (L == 0) raise_error(a.err, DFD_ERR_INVALID_ARG);
+      } else if (fits_buffer<DK>(rows, cols)) {
+        T r;
+        if (ni <= nj)
+          r = warp_dfd_any<V, DK>(pts + oi * a.dim, ni, pts + oj * a.dim, nj, a.dim, buf, L);
+        else
+          r = warp_dfd_any<V, DK>(pts + oj * a.dim, nj, pts + oi * a.dim, ni, a.dim, buf, L);
+        if (L == 0) write_result<T>(a.out_dist, a.out_dist2, k, r);
+      } else if (L == 0) {
+        raise_error(a.err, DFD_ERR_UNSUPPORTED);
+      }
+      if (++j == a.n_curves) {
+        ++i;
+        j = i + 1;
+      }
+    }
+  }
+}
+
+}  // namespace batch
+}  // namespace dfd

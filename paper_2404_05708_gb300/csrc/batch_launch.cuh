@@ -1,0 +1,136 @@
+// batch_launch.cuh -- host launchers of K4 (ragged batch) and K5 (matrix),
+// instantiated per (value type, dimension class) in batch_*.cu.
+#pragma once
+#include <algorithm>
+#include <type_traits>
+#include "batch_kernel.cuh"
+#include "dfd_internal.h"
+
+namespace dfd {
+
+// Input checks over CSR points whose count is on the device (offsets[n]).
+template <class V>
+__global__ void check_points_kernel(const typename V::coord* x, const int64_t* count_points, int dim, int* err) {
+  const int64_t count = count_points[0] * dim;
+  bool bad = false;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
+    const typename V::coord c = x[i];
+    if constexpr (std::is_same<V, F32>::value) {
+      bad |= !isfinite(c);
+    } else {
+      const long long a = c < 0 ? -(long long)c : (long long)c;
+      bad |= a > (1LL << 30) - 1 || (double)a > sqrt((double)LLONG_MAX / (double)dim) / 2.0;
+    }
+  }
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0)
+    raise_error(err, std::is_same<V, F32>::value ? DFD_ERR_NONFINITE : DFD_ERR_RANGE);
+}
+
+template <class K>
+int resident_blocks(const dfd_context* ctx, K kernel, int threads) {
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, 0) != cudaSuccess || per_sm < 1) {
+    cudaGetLastError();
+    per_sm = 1;
+  }
+  return per_sm * ctx->num_sms;
+}
+
+template <class V, int DK>
+dfd_status batch_launch(dfd_context* ctx, int dim, const void* points, const int64_t* offsets, int64_t n_curves,
+                        const int32_t* pairs, int64_t n_pairs, void* out_dist, void* out_dist2, cudaStream_t s) {
+  using T = typename V::value;
+  constexpr int THREADS = 256;
+  const int blocks = resident_blocks(ctx, batch::batch_kernel<V, DK>, THREADS);
+  const size_t warps = (size_t)blocks * (THREADS / 32);
+  // scratch: [counter | hist | cursor] [bucket bytes] [worklist] [row buffers]
+  const size_t off_hist = 256, off_cursor = off_hist + batch::NBUCKET * 4;
+  const size_t off_bucket = align_up(off_cursor + batch::NBUCKET * 4, 256);
+  const size_t off_work = align_up(off_bucket + (size_t)n_pairs, 256);
+  const size_t off_buf = align_up(off_work + (size_t)n_pairs * 4, 256);
+  const size_t total = off_buf + warps * batch::BUF_COLS * sizeof(T);
+  dfd_status st = ensure_scratch(ctx, total);
+  if (st != DFD_OK) return st;
+  char* base = static_cast<char*>(ctx->scratch);
+  cudaError_t e = cudaMemsetAsync(base, 0, off_bucket, s);
+  if (e != cudaSuccess) return cuda_status(e);
+  if (ctx->opt.check_inputs) {
+    check_points_kernel<V><<<std::min(4 * ctx->num_sms, 1024), 256, 0, s>>>(
+        static_cast<const typename V::coord*>(points), offsets + n_curves, dim, ctx->d_err);
+  }
+  batch::PlanArgs pa;
+  pa.offsets = offsets;
+  pa.pairs = pairs;
+  pa.n_pairs = n_pairs;
+  pa.n_curves = n_curves;
+  pa.hist = reinterpret_cast<unsigned*>(base + off_hist);
+  pa.cursor = reinterpret_cast<unsigned*>(base + off_cursor);
+  pa.bucket = reinterpret_cast<unsigned char*>(base + off_bucket);
+  pa.worklist = reinterpret_cast<unsigned*>(base + off_work);
+  pa.err = ctx->d_err;
+  const int pblocks = (int)std::min<int64_t>((n_pairs + 255) / 256, 8 * (int64_t)ctx->num_sms);
+  batch::plan_hist_kernel<<<pblocks, 256, 0, s>>>(pa);
+  batch::plan_scan_kernel<<<1, 32, 0, s>>>(pa);
+  batch::plan_scatter_kernel<<<pblocks, 256, 0, s>>>(pa);
+  batch::BatchArgs ba;
+  ba.rowbuf = base + off_buf;
+  ba.points = points;
+  ba.offsets = offsets;
+  ba.pairs = pairs;
+  ba.worklist = pa.worklist;
+  ba.n_items = n_pairs;
+  ba.n_curves = n_curves;
+  ba.dim = dim;
+  ba.counter = reinterpret_cast<int*>(base);
+  ba.err = ctx->d_err;
+  ba.out_dist = out_dist;
+  ba.out_dist2 = out_dist2;
+  timing_begin(ctx, s);
+  batch::batch_kernel<V, DK><<<blocks, THREADS, 0, s>>>(ba);
+  timing_end(ctx, s);
+  return cuda_status(cudaGetLastError());
+}
+
+template <class V, int DK>
+dfd_status matrix_launch(dfd_context* ctx, int dim, const void* points, const int64_t* offsets, int64_t n_curves,
+                         void* out_dist, void* out_dist2, cudaStream_t s, int chunk) {
+  using T = typename V::value;
+  constexpr int THREADS = 256;
+  const int blocks = resident_blocks(ctx, batch::matrix_kernel<V, DK>, THREADS);
+  const size_t warps = (size_t)blocks * (THREADS / 32);
+  const size_t off_buf = 256;
+  const size_t total = off_buf + warps * batch::BUF_COLS * sizeof(T);
+  dfd_status st = ensure_scratch(ctx, total);
+  if (st != DFD_OK) return st;
+  char* base = static_cast<char*>(ctx->scratch);
+  cudaError_t e = cudaMemsetAsync(base, 0, 256, s);
+  if (e != cudaSuccess) return cuda_status(e);
+  if (ctx->opt.check_inputs) {
+    check_points_kernel<V><<<std::min(4 * ctx->num_sms, 1024), 256, 0, s>>>(
+        static_cast<const typename V::coord*>(points), offsets + n_curves, dim, ctx->d_err);
+  }
+  batch::MatrixArgs ma;
+  ma.rowbuf = base + off_buf;
+  ma.points = points;
+  ma.offsets = offsets;
+  ma.n_curves = n_curves;
+  ma.n_pairs = n_curves * (n_curves - 1) / 2;
+  ma.dim = dim;
+  ma.chunk = chunk > 0 ? chunk : 8;
+  ma.counter = reinterpret_cast<int*>(base);
+  ma.err = ctx->d_err;
+  ma.out_dist = out_dist;
+  ma.out_dist2 = out_dist2;
+  timing_begin(ctx, s);
+  batch::matrix_kernel<V, DK><<<blocks, THREADS, 0, s>>>(ma);
+  timing_end(ctx, s);
+  return cuda_status(cudaGetLastError());
+}
+
+}  // namespace dfd
+
+#define DFD_BATCH_INSTANTIATE(V, DK)                                                                              \
+  template dfd_status dfd::batch_launch<dfd::V, DK>(dfd_context*, int, const void*, const int64_t*, int64_t,       \
+                                                      const int32_t*, int64_t, void*, void*, cudaStream_t);        \
+  template dfd_status dfd::matrix_launch<dfd::V, DK>(dfd_context*, int, const void*, const int64_t*, int64_t, void*, \
+                                                       void*, cudaStream_t, int);

@@ -30,6 +30,28 @@ DFD_WAVE_EXTERN_R(I32, 4)
 DFD_WAVE_EXTERN_R(I32, 8)
 DFD_WAVE_EXTERN_R(I32, 16)
 
+template <class V, int DK>
+dfd_status batch_launch(dfd_context* ctx, int dim, const void* points, const int64_t* offsets, int64_t n_curves,
+                        const int32_t* pairs, int64_t n_pairs, void* out_dist, void* out_dist2, cudaStream_t s);
+template <class V, int DK>
+dfd_status matrix_launch(dfd_context* ctx, int dim, const void* points, const int64_t* offsets, int64_t n_curves,
+                         void* out_dist, void* out_dist2, cudaStream_t s, int chunk);
+#define DFD_BATCH_EXTERN(V, DK)                                                                              \
+  extern template dfd_status batch_launch<V, DK>(dfd_context*, int, const void*, const int64_t*, int64_t,     \
+                                                 const int32_t*, int64_t, void*, void*, cudaStream_t);        \
+  extern template dfd_status matrix_launch<V, DK>(dfd_context*, int, const void*, const int64_t*, int64_t,    \
+                                                  void*, void*, cudaStream_t, int);
+DFD_BATCH_EXTERN(F32, 2)
+DFD_BATCH_EXTERN(F32, 3)
+DFD_BATCH_EXTERN(F32, 4)
+DFD_BATCH_EXTERN(F32, 8)
+DFD_BATCH_EXTERN(F32, 16)
+DFD_BATCH_EXTERN(I32, 2)
+DFD_BATCH_EXTERN(I32, 3)
+DFD_BATCH_EXTERN(I32, 4)
+DFD_BATCH_EXTERN(I32, 8)
+DFD_BATCH_EXTERN(I32, 16)
+
 // ---------------------------------------------------------- scratch memory
 dfd_status ensure_scratch(dfd_context* ctx, size_t bytes) {
   if (bytes <= ctx->scratch_bytes) return DFD_OK;
@@ -176,6 +198,45 @@ dfd_status wave_run(dfd_context* ctx, dfd_dtype dtype, int dim, const void* p, i
   }
 #undef DFD_W_DK
 #undef DFD_W_R
+}
+
+dfd_status batch_run(dfd_context* ctx, dfd_dtype dtype, int dim, const void* points, const int64_t* offsets,
+                     int64_t n_curves, const int32_t* pairs, int64_t n_pairs, void* out_dist, void* out_dist2,
+                     cudaStream_t s) {
+#define DFD_B_DK(V)                                                                                           \
+  switch (dim_class(dim)) {                                                                                   \
+    case 2: return batch_launch<V, 2>(ctx, dim, points, offsets, n_curves, pairs, n_pairs, out_dist, out_dist2, s); \
+    case 3: return batch_launch<V, 3>(ctx, dim, points, offsets, n_curves, pairs, n_pairs, out_dist, out_dist2, s); \
+    case 4: return batch_launch<V, 4>(ctx, dim, points, offsets, n_curves, pairs, n_pairs, out_dist, out_dist2, s); \
+    case 8: return batch_launch<V, 8>(ctx, dim, points, offsets, n_curves, pairs, n_pairs, out_dist, out_dist2, s); \
+    case 16: return batch_launch<V, 16>(ctx, dim, points, offsets, n_curves, pairs, n_pairs, out_dist, out_dist2, s); \
+    default: return DFD_ERR_UNSUPPORTED;                                                                      \
+  }
+  if (dtype == DFD_F32) {
+    DFD_B_DK(F32)
+  } else {
+    DFD_B_DK(I32)
+  }
+#undef DFD_B_DK
+}
+
+dfd_status matrix_run(dfd_context* ctx, dfd_dtype dtype, int dim, const void* points, const int64_t* offsets,
+                      int64_t n_curves, void* out_dist, void* out_dist2, cudaStream_t s, int chunk) {
+#define DFD_M_DK(V)                                                                                      \
+  switch (dim_class(dim)) {                                                                              \
+    case 2: return matrix_launch<V, 2>(ctx, dim, points, offsets, n_curves, out_dist, out_dist2, s, chunk);   \
+    case 3: return matrix_launch<V, 3>(ctx, dim, points, offsets, n_curves, out_dist, out_dist2, s, chunk);   \
+    case 4: return matrix_launch<V, 4>(ctx, dim, points, offsets, n_curves, out_dist, out_dist2, s, chunk);   \
+    case 8: return matrix_launch<V, 8>(ctx, dim, points, offsets, n_curves, out_dist, out_dist2, s, chunk);   \
+    case 16: return matrix_launch<V, 16>(ctx, dim, points, offsets, n_curves, out_dist, out_dist2, s, chunk); \
+    default: return DFD_ERR_UNSUPPORTED;                                                                 \
+  }
+  if (dtype == DFD_F32) {
+    DFD_M_DK(F32)
+  } else {
+    DFD_M_DK(I32)
+  }
+#undef DFD_M_DK
 }
 
 __global__ void bounded_wait_kernel(const unsigned long long* flag, int* err, unsigned long long timeout_ns) {
@@ -464,6 +525,148 @@ dfd_status dfd_pair_host(dfd_context* ctx, dfd_dtype dtype, int dim, const void*
     if (out_dist) std::memcpy(out_dist, r, 8);
     if (out_dist2) std::memcpy(out_dist2, r + 8, 8);
   }
+  return DFD_OK;
+}
+
+}  // extern "C"
+
+// ============================================================ batch / matrix
+struct dfd_graph {
+  dfd_context* ctx = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  void* scratch = nullptr;   // owned: the captured launches point into it
+};
+
+namespace {
+
+dfd_status check_batch_args(dfd_context* ctx, dfd_dtype dtype, int dim, const void* points, const int64_t* offsets,
+                            int64_t n_curves, const void* out_dist, const void* out_dist2) {
+  if (!ctx) return DFD_ERR_INVALID_ARG;
+  if (dtype != DFD_F32 && dtype != DFD_I32) return DFD_ERR_INVALID_ARG;
+  if (dim < 1 || !points || !offsets || n_curves < 1) return DFD_ERR_INVALID_ARG;
+  if (!out_dist && !out_dist2) return DFD_ERR_INVALID_ARG;
+  if (dim > 16) return DFD_ERR_UNSUPPORTED;
+  if (n_curves > INT32_MAX) return DFD_ERR_UNSUPPORTED;
+  return DFD_OK;
+}
+
+// Run `fn` once normally (sizes the context scratch), then capture it into a
+// graph that owns a private copy of the scratch, so later calls that grow or
+// reuse the context scratch cannot disturb the graph's buffers.
+template <class F>
+dfd_status capture_graph(dfd_context* ctx, F fn, dfd_graph** out) {
+  dfd_status st = fn(ctx->stream);
+  if (st != DFD_OK) return st;
+  if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) {
+    cudaGetLastError();
+    return DFD_ERR_CUDA;
+  }
+  dfd_graph* g = new (std::nothrow) dfd_graph();
+  if (!g) return DFD_ERR_OOM;
+  g->ctx = ctx;
+  if (cudaMalloc(&g->scratch, ctx->scratch_bytes) != cudaSuccess) {
+    cudaGetLastError();
+    delete g;
+    return DFD_ERR_OOM;
+  }
+  void* saved = ctx->scratch;
+  ctx->scratch = g->scratch;
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeRelaxed);
+  if (e == cudaSuccess) {
+    st = fn(ctx->stream);
+    cudaError_t e2 = cudaStreamEndCapture(ctx->stream, &graph);
+    if (st == DFD_OK && e2 != cudaSuccess) st = DFD_ERR_CUDA;
+  } else {
+    st = DFD_ERR_CUDA;
+  }
+  ctx->scratch = saved;
+  if (st == DFD_OK && cudaGraphInstantiate(&g->exec, graph, 0) != cudaSuccess) st = DFD_ERR_CUDA;
+  if (graph) cudaGraphDestroy(graph);
+  if (st != DFD_OK) {
+    cudaGetLastError();
+    if (g->exec) cudaGraphExecDestroy(g->exec);
+    cudaFree(g->scratch);
+    delete g;
+    return st;
+  }
+  *out = g;
+  return DFD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+dfd_status dfd_batch(dfd_context* ctx, dfd_dtype dtype, int dim, const void* points, const int64_t* offsets,
+                     int64_t n_curves, const int32_t* pairs, int64_t n_pairs, void* out_dist, void* out_dist2,
+                     void* stream) {
+  dfd_status st = check_batch_args(ctx, dtype, dim, points, offsets, n_curves, out_dist, out_dist2);
+  if (st != DFD_OK) return st;
+  if (!pairs || n_pairs < 0 || n_pairs > INT32_MAX) return DFD_ERR_INVALID_ARG;
+  if (n_pairs == 0) return DFD_OK;
+  if ((st = set_device(ctx)) != DFD_OK) return st;
+  return batch_run(ctx, dtype, dim, points, offsets, n_curves, pairs, n_pairs, out_dist, out_dist2,
+                   static_cast<cudaStream_t>(stream));
+}
+
+dfd_status dfd_matrix(dfd_context* ctx, dfd_dtype dtype, int dim, const void* points, const int64_t* offsets,
+                      int64_t n_curves, void* out_condensed, void* out_dist2, void* stream) {
+  dfd_status st = check_batch_args(ctx, dtype, dim, points, offsets, n_curves, out_condensed, out_dist2);
+  if (st != DFD_OK) return st;
+  if (n_curves < 2) return DFD_OK;
+  if ((st = set_device(ctx)) != DFD_OK) return st;
+  return matrix_run(ctx, dtype, dim, points, offsets, n_curves, out_condensed, out_dist2,
+                    static_cast<cudaStream_t>(stream), 0);
+}
+
+dfd_status dfd_batch_capture(dfd_context* ctx, dfd_dtype dtype, int dim, const void* points, const int64_t* offsets,
+                             int64_t n_curves, const int32_t* pairs, int64_t n_pairs, void* out_dist, void* out_dist2,
+                             dfd_graph** out) {
+  if (!out) return DFD_ERR_INVALID_ARG;
+  *out = nullptr;
+  dfd_status st = check_batch_args(ctx, dtype, dim, points, offsets, n_curves, out_dist, out_dist2);
+  if (st != DFD_OK) return st;
+  if (!pairs || n_pairs < 1 || n_pairs > INT32_MAX) return DFD_ERR_INVALID_ARG;
+  if ((st = set_device(ctx)) != DFD_OK) return st;
+  return capture_graph(
+      ctx,
+      [&](cudaStream_t s) {
+        return batch_run(ctx, dtype, dim, points, offsets, n_curves, pairs, n_pairs, out_dist, out_dist2, s);
+      },
+      out);
+}
+
+dfd_status dfd_matrix_capture(dfd_context* ctx, dfd_dtype dtype, int dim, const void* points, const int64_t* offsets,
+                              int64_t n_curves, void* out_condensed, void* out_dist2, dfd_graph** out) {
+  if (!out) return DFD_ERR_INVALID_ARG;
+  *out = nullptr;
+  dfd_status st = check_batch_args(ctx, dtype, dim, points, offsets, n_curves, out_condensed, out_dist2);
+  if (st != DFD_OK) return st;
+  if (n_curves < 2) return DFD_ERR_INVALID_ARG;
+  if ((st = set_device(ctx)) != DFD_OK) return st;
+  return capture_graph(
+      ctx,
+      [&](cudaStream_t s) {
+        return matrix_run(ctx, dtype, dim, points, offsets, n_curves, out_condensed, out_dist2, s, 0);
+      },
+      out);
+}
+
+dfd_status dfd_graph_launch(dfd_graph* g, void* stream) {
+  if (!g || !g->exec) return DFD_ERR_INVALID_ARG;
+  if (cudaSetDevice(g->ctx->device) != cudaSuccess) return DFD_ERR_CUDA;
+  return cuda_status(cudaGraphLaunch(g->exec, static_cast<cudaStream_t>(stream)));
+}
+
+dfd_status dfd_graph_destroy(dfd_graph* g) {
+  if (!g) return DFD_OK;
+  cudaSetDevice(g->ctx->device);
+  cudaDeviceSynchronize();
+  if (g->exec) cudaGraphExecDestroy(g->exec);
+  if (g->scratch) cudaFree(g->scratch);
+  cudaGetLastError();
+  delete g;
   return DFD_OK;
 }
 

@@ -79,6 +79,13 @@ dfd_status wave_plan(const dfd_context* ctx, dfd_dtype dtype, int dim, int64_t n
 dfd_status wave_run(dfd_context* ctx, dfd_dtype dtype, int dim, const void* p, int64_t n, const void* q,
                     int64_t m, void* out_dist, void* out_dist2, cudaStream_t s, const WaveShape& shape);
 
+// Ragged batch (K4) and all-pairs matrix (K5).
+dfd_status batch_run(dfd_context* ctx, dfd_dtype dtype, int dim, const void* points, const int64_t* offsets,
+                     int64_t n_curves, const int32_t* pairs, int64_t n_pairs, void* out_dist, void* out_dist2,
+                     cudaStream_t s);
+dfd_status matrix_run(dfd_context* ctx, dfd_dtype dtype, int dim, const void* points, const int64_t* offsets,
+                      int64_t n_curves, void* out_dist, void* out_dist2, cudaStream_t s, int chunk);
+
 // Per-pair reference (K1): one CTA, row-by-row clamp scan.
 dfd_status rowscan_run(dfd_context* ctx, dfd_dtype dtype, int dim, const void* p, int64_t n, const void* q,
                        int64_t m, void* out_dist, void* out_dist2, cudaStream_t s);

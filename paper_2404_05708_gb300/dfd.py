@@ -63,6 +63,12 @@ _SIGS = {
     "dfd_pair_plan": [_VP, _INT, _INT, _I64, _I64, ctypes.POINTER(WaveShape)],
     "dfd_debug_bounded_wait": [_VP, ctypes.c_double],
     "dfd_pair_noalloc": [_INT, _INT, _INT, _VP, _I64, _VP, _I64, _VP, _VP, _VP],
+    "dfd_batch": [_VP, _INT, _INT, _VP, _VP, _I64, _VP, _I64, _VP, _VP, _VP],
+    "dfd_matrix": [_VP, _INT, _INT, _VP, _VP, _I64, _VP, _VP, _VP],
+    "dfd_batch_capture": [_VP, _INT, _INT, _VP, _VP, _I64, _VP, _I64, _VP, _VP, ctypes.POINTER(_VP)],
+    "dfd_matrix_capture": [_VP, _INT, _INT, _VP, _VP, _I64, _VP, _VP, ctypes.POINTER(_VP)],
+    "dfd_graph_launch": [_VP, _VP],
+    "dfd_graph_destroy": [_VP],
     "dfd_timing_enable": [_VP, _INT],
     "dfd_timing_last": [_VP, ctypes.POINTER(ctypes.c_double)],
     "dfd_microbench": [_VP, _INT, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)],
@@ -148,6 +154,37 @@ def dfd_pair_noalloc(device, dtype, dim, p, n, q, m, out_dist, out_dist2, stream
     return load_library().dfd_pair_noalloc(device, dtype, dim, p, n, q, m, out_dist, out_dist2, stream)
 
 
+def dfd_batch(ctx, dtype, dim, points, offsets, n_curves, pairs, n_pairs, out_dist, out_dist2, stream) -> int:
+    return load_library().dfd_batch(ctx, dtype, dim, points, offsets, n_curves, pairs, n_pairs, out_dist, out_dist2,
+                                    stream)
+
+
+def dfd_matrix(ctx, dtype, dim, points, offsets, n_curves, out_condensed, out_dist2, stream) -> int:
+    return load_library().dfd_matrix(ctx, dtype, dim, points, offsets, n_curves, out_condensed, out_dist2, stream)
+
+
+def dfd_batch_capture(ctx, dtype, dim, points, offsets, n_curves, pairs, n_pairs, out_dist, out_dist2) -> int:
+    g = _VP()
+    _check(load_library().dfd_batch_capture(ctx, dtype, dim, points, offsets, n_curves, pairs, n_pairs, out_dist,
+                                            out_dist2, ctypes.byref(g)), "dfd_batch_capture")
+    return g.value
+
+
+def dfd_matrix_capture(ctx, dtype, dim, points, offsets, n_curves, out_condensed, out_dist2) -> int:
+    g = _VP()
+    _check(load_library().dfd_matrix_capture(ctx, dtype, dim, points, offsets, n_curves, out_condensed, out_dist2,
+                                             ctypes.byref(g)), "dfd_matrix_capture")
+    return g.value
+
+
+def dfd_graph_launch(graph, stream) -> int:
+    return load_library().dfd_graph_launch(graph, stream)
+
+
+def dfd_graph_destroy(graph) -> int:
+    return load_library().dfd_graph_destroy(graph)
+
+
 def dfd_pair_shaped(ctx, dtype, dim, p, n, q, m, out_dist, out_dist2, stream, shape: WaveShape | None) -> int:
     return load_library().dfd_pair_shaped(ctx, dtype, dim, p, n, q, m, out_dist, out_dist2, stream,
                                           ctypes.byref(shape) if shape is not None else None)
@@ -202,6 +239,30 @@ def _curve(t):
     if t.dim() != 2:
         raise ValueError("a curve is an [n, dim] tensor")
     return t.contiguous()
+
+
+class Graph:
+    """A captured dfd_batch / dfd_matrix call; keeps its buffers alive."""
+
+    def __init__(self, handle, keep):
+        self.handle = handle
+        self._keep = keep
+
+    def launch(self, stream=None):
+        torch = _torch()
+        s = stream if stream is not None else torch.cuda.current_stream().cuda_stream
+        _check(dfd_graph_launch(self.handle, s), "dfd_graph_launch")
+
+    def close(self):
+        if self.handle:
+            dfd_graph_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Context:
@@ -263,6 +324,53 @@ class Context:
         else:
             st = dfd_pair(*args)
         _check(st, "dfd_pair")
+        return out_dist, out_dist2
+
+    def _batch_outs(self, dt, count, out_dist, out_dist2):
+        torch = _torch()
+        dev = torch.device("cuda", self.device)
+        if out_dist is None:
+            out_dist = torch.empty(count, dtype=torch.float32 if dt == DFD_F32 else torch.float64, device=dev)
+        if out_dist2 is None:
+            out_dist2 = torch.empty(count, dtype=torch.float32 if dt == DFD_F32 else torch.int64, device=dev)
+        return out_dist, out_dist2
+
+    def batch(self, points, offsets, pairs, out_dist=None, out_dist2=None, stream=None, capture=False):
+        """Distances of pairs[k] = (a, b) of CSR curves; returns (dist, dist2) or a Graph if capture."""
+        torch = _torch()
+        points = _curve(points)
+        dt = _dtype_code(points)
+        offsets = offsets.contiguous()
+        pairs = pairs.contiguous()
+        if offsets.dtype != torch.int64 or pairs.dtype != torch.int32:
+            raise TypeError("offsets must be int64 and pairs int32")
+        n_pairs = pairs.numel() // 2
+        out_dist, out_dist2 = self._batch_outs(dt, n_pairs, out_dist, out_dist2)
+        args = (self.handle, dt, points.shape[1], points.data_ptr(), offsets.data_ptr(), offsets.numel() - 1,
+                pairs.data_ptr(), n_pairs, out_dist.data_ptr(), out_dist2.data_ptr())
+        if capture:
+            return Graph(dfd_batch_capture(*args), (points, offsets, pairs, out_dist, out_dist2)), out_dist, out_dist2
+        s = stream if stream is not None else torch.cuda.current_stream(self.device).cuda_stream
+        _check(dfd_batch(*args, s), "dfd_batch")
+        return out_dist, out_dist2
+
+    def matrix(self, points, offsets, out_dist=None, out_dist2=None, stream=None, capture=False):
+        """Condensed upper-triangle distance matrix of CSR curves."""
+        torch = _torch()
+        points = _curve(points)
+        dt = _dtype_code(points)
+        offsets = offsets.contiguous()
+        if offsets.dtype != torch.int64:
+            raise TypeError("offsets must be int64")
+        n = offsets.numel() - 1
+        count = n * (n - 1) // 2
+        out_dist, out_dist2 = self._batch_outs(dt, count, out_dist, out_dist2)
+        args = (self.handle, dt, points.shape[1], points.data_ptr(), offsets.data_ptr(), n, out_dist.data_ptr(),
+                out_dist2.data_ptr())
+        if capture:
+            return Graph(dfd_matrix_capture(*args), (points, offsets, out_dist, out_dist2)), out_dist, out_dist2
+        s = stream if stream is not None else torch.cuda.current_stream(self.device).cuda_stream
+        _check(dfd_matrix(*args, s), "dfd_matrix")
         return out_dist, out_dist2
 
     def pair_host(self, p, q):

@@ -1,0 +1,163 @@
+"""GPU parity of the ragged batch (dfd_batch) and the all-pairs matrix (dfd_matrix).
+
+int32: bit-exact against the int64 oracle; float32: delta^2 bit-identical to
+the float32 selection mirror and delta within 1e-6 of the float64 oracle
+(tolerance derivation in test_gpu_pair.py).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2404_05708_gb300 import workloads
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+REL_TOL = 1e-6
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def run_batch(ctx, b, **kw):
+    d, d2 = ctx.batch(dev(b.points), dev(b.offsets), dev(b.pairs), **kw)
+    torch.cuda.synchronize()
+    return d.cpu().numpy(), d2.cpu().numpy()
+
+
+def check_f32(d, d2, b):
+    mirror, _ = oracle.batch(b.points, b.offsets, b.pairs, mirror=True)
+    ref, _ = oracle.batch(b.points, b.offsets, b.pairs)
+    assert np.array_equal(d2, mirror), np.nonzero(d2 != mirror)[0][:10]
+    want = np.sqrt(ref)
+    err = np.abs(d.astype(np.float64) - want)
+    assert np.all(err <= REL_TOL * np.maximum(want, 1e-300)), err.max()
+
+
+def ragged_edges(dtype, dim, seed):
+    """Lengths at warp/stripe edges: 1, 31..33, 255..257, 511..513, 600."""
+    rng = np.random.default_rng(seed)
+    edges = [1, 2, 31, 32, 33, 63, 64, 65, 127, 128, 129, 255, 256, 257, 511, 512, 513, 600]
+    lens = []
+    pairs = []
+    for a in edges:
+        for bb in edges:
+            pairs.append((len(lens), len(lens) + 1))
+            lens += [a, bb]
+    lens = np.array(lens, np.int64)
+    off = np.zeros(len(lens) + 1, np.int64)
+    np.cumsum(lens, out=off[1:])
+    if dtype == "i32":
+        pts = np.cumsum(rng.integers(-64, 65, size=(off[-1], dim)), axis=0).astype(np.int32)
+    else:
+        pts = np.cumsum(rng.normal(0, 1, size=(off[-1], dim)), axis=0).astype(np.float32)
+    return workloads.Batch(points=pts, offsets=off, pairs=np.array(pairs, np.int32))
+
+
+@pytest.mark.parametrize("dim", [1, 2, 3])
+def test_batch_int_edges(dctx, dim):
+    b = ragged_edges("i32", dim, 80 + dim)
+    _, d2 = run_batch(dctx, b)
+    ref, _ = oracle.batch(b.points, b.offsets, b.pairs)
+    assert np.array_equal(d2, ref), np.nonzero(d2 != ref)[0][:10]
+
+
+@pytest.mark.parametrize("dim", [2, 3, 5, 8, 16])
+def test_batch_float_edges(dctx, dim):
+    b = ragged_edges("f32", dim, 90 + dim)
+    d, d2 = run_batch(dctx, b)
+    check_f32(d, d2, b)
+
+
+def test_batch_ragged_int_full_size(dctx):
+    """65,536 pairs, lengths U{16..512}, int32 2-D walks: every pair bit-exact."""
+    b = workloads.ragged_int_batch()
+    d, d2 = run_batch(dctx, b)
+    ref, _ = oracle.batch(b.points, b.offsets, b.pairs)
+    assert np.array_equal(d2, ref), np.nonzero(d2 != ref)[0][:10]
+    assert np.array_equal(d, np.sqrt(ref.astype(np.float64)))
+
+
+def test_batch_graph_replay_updates_with_buffers(dctx):
+    b = workloads.ragged_int_batch(n_pairs=3000, seed=41)
+    pts, off, pr = dev(b.points), dev(b.offsets), dev(b.pairs)
+    g, d, d2 = dctx.batch(pts, off, pr, capture=True)
+    torch.cuda.synchronize()
+    ref, _ = oracle.batch(b.points, b.offsets, b.pairs)
+    assert np.array_equal(d2.cpu().numpy(), ref)
+    # new contents in the same buffers, then replay
+    b2 = workloads.ragged_int_batch(n_pairs=3000, seed=41)
+    b2.points = (b2.points * 3 - 7).astype(np.int32)
+    pts.copy_(dev(b2.points))
+    d2.zero_()
+    g.launch()
+    g.launch()
+    torch.cuda.synchronize()
+    ref2, _ = oracle.batch(b2.points, b2.offsets, b2.pairs)
+    assert np.array_equal(d2.cpu().numpy(), ref2)
+    g.close()
+
+
+def test_batch_invalid_ids_are_reported(dctx):
+    b = ragged_edges("i32", 2, 7)
+    pairs = b.pairs.copy()
+    pairs[5, 1] = 10 ** 6
+    d, d2 = dctx.batch(dev(b.points), dev(b.offsets), dev(pairs))
+    torch.cuda.synchronize()
+    assert dctx.get_error() == 1          # DFD_ERR_INVALID_ARG
+    assert dctx.get_error() == 0
+
+
+# ----------------------------------------------------------------- matrix
+
+def condensed_oracle(b):
+    n = b.n_curves
+    ii, jj = np.triu_indices(n, k=1)
+    pairs = np.stack([ii, jj], axis=1).astype(np.int32)
+    return oracle.batch(b.points, b.offsets, pairs), oracle.batch(b.points, b.offsets, pairs, mirror=True)
+
+
+def test_matrix_small_float16d(dctx):
+    b = workloads.ar1_curves(n_curves=70, seed=51)
+    d, d2 = dctx.matrix(dev(b.points), dev(b.offsets))
+    torch.cuda.synchronize()
+    (ref, _), (mirror, _) = condensed_oracle(b)
+    assert np.array_equal(d2.cpu().numpy(), mirror)
+    assert np.all(np.abs(d.cpu().numpy() - np.sqrt(ref)) <= REL_TOL * np.sqrt(ref))
+
+
+def test_matrix_small_int(dctx):
+    rng = np.random.default_rng(52)
+    lens = rng.integers(1, 300, size=45)
+    off = np.zeros(46, np.int64)
+    np.cumsum(lens, out=off[1:])
+    pts = np.cumsum(rng.integers(-100, 101, size=(off[-1], 3)), axis=0).astype(np.int32)
+    b = workloads.Batch(points=pts, offsets=off, pairs=np.zeros((0, 2), np.int32))
+    _, d2 = dctx.matrix(dev(pts), dev(off))
+    torch.cuda.synchronize()
+    (ref, _), _ = condensed_oracle(b)
+    assert np.array_equal(d2.cpu().numpy(), ref)
+
+
+def test_matrix_full_size_sampled(dctx):
+    """4096 curves, 16-D AR(1), lengths U{64..256}: 8,386,560 pairs, 400 sampled entries vs the oracle."""
+    b = workloads.ar1_curves()
+    d, d2 = dctx.matrix(dev(b.points), dev(b.offsets))
+    torch.cuda.synchronize()
+    n = b.n_curves
+    rng = np.random.default_rng(53)
+    ks = rng.integers(0, n * (n - 1) // 2, size=400)
+    # decode k -> (i, j) on the host, independently of the kernel
+    starts = np.array([i * (2 * n - i - 1) // 2 for i in range(n)], np.int64)
+    ii = np.searchsorted(starts, ks, side="right") - 1
+    jj = ks - starts[ii] + ii + 1
+    pairs = np.stack([ii, jj], axis=1).astype(np.int32)
+    ref, _ = oracle.batch(b.points, b.offsets, pairs)
+    mirror, _ = oracle.batch(b.points, b.offsets, pairs, mirror=True)
+    got2 = d2.cpu().numpy()[ks]
+    got = d.cpu().numpy()[ks]
+    assert np.array_equal(got2, mirror)
+    assert np.all(np.abs(got - np.sqrt(ref)) <= REL_TOL * np.sqrt(ref))
