@@ -1,8 +1,8 @@
 #!/usr/bin/env python3
 """Benchmark of the discrete Frechet distance hot path on GB300.
 
-Workload (the single-GPU configuration the headline metric is quoted on):
-one long pair of 3-D float32 curves, n = m = 200,000, q a time-warped,
+Default workload (the single-GPU configuration the headline metric is quoted
+on): one long pair of 3-D float32 curves, n = m = 200,000, q a time-warped,
 jittered copy of the Gaussian random walk p (seeded, synthetic).  A step is
 one complete distance computation through ``dfd_pair`` (the band wavefront,
 all 4.0e10 cells of Eq. 1).  ``value`` = cells / second / 1e9 (GCUPS) with
@@ -11,18 +11,21 @@ the curves already resident in HBM; ``e2e`` = the same metric through
 inside the timed region).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+    python bench.py --workload batch    # 65,536 ragged int32 2-D pairs, one graph launch per step
+    python bench.py --workload matrix   # all pairs of 4096 16-D AR(1) curves, one graph launch per step
+    python bench.py --workload pair2k   # one 2000 x 1500 2-D pair
 
-Under torchrun (N > 1) every rank computes its own replica of the pair (the
-single pair does not shard: replicas only); value = all ranks' cells / the
-slowest rank's time.  ``--impl reference`` times the CPU oracle (float64
-Alg. 5) on host cores on a bounded prefix of the same pair.
+Under torchrun (N > 1) the single long pair runs as replicas (one per rank);
+the batch and matrix workloads shard their pairs across ranks (no
+collective).  value = all ranks' cells / the slowest rank's time.
+``--impl reference`` times the CPU oracle (float64 / int64 Alg. 5) on host
+cores on a bounded sample of the same workload.
 """
 from __future__ import annotations
 
 import argparse
 import hashlib
 import json
-import math
 import os
 import statistics
 import subprocess
@@ -39,7 +42,7 @@ N_POINTS = 200_000
 DIM = 3
 SEED = 3
 L2_FLUSH_BYTES = 256 << 20
-CPU_SAMPLE = 50_000          # cpu_baseline: prefix p[:a], q[:a]
+CPU_SAMPLE = 50_000          # cpu_baseline of the long pair: prefix p[:a], q[:a]
 REF_SAMPLE = 20_000          # --impl reference: prefix per step
 
 # dram__bytes_read.sum + dram__bytes_write.sum per launch of the wavefront
@@ -48,9 +51,9 @@ REF_SAMPLE = 20_000          # --impl reference: prefix per step
 TRAFFIC_BY_KERNEL_SHA: dict = {}
 
 
-def kernel_sha() -> str:
+def kernel_sha(files=("wave_kernel.cuh", "wave_launch.cuh", "dfd_device.cuh")) -> str:
     h = hashlib.sha256()
-    for f in ("wave_kernel.cuh", "wave_launch.cuh", "dfd_device.cuh"):
+    for f in files:
         with open(os.path.join(ROOT, "paper_2404_05708_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -62,6 +65,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="long", choices=["long", "batch", "matrix", "pair2k"])
     ap.add_argument("--n", type=int, default=N_POINTS)
     ap.add_argument("--m", type=int, default=N_POINTS)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -125,35 +129,318 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+# --------------------------------------------------------------- workloads
+class LongPair:
+    """One long 3-D float32 pair through dfd_pair (band wavefront)."""
+    micro_op = "cell_f32_d3"
+    dtype = "f32"
+    launches_per_step = 4          # 2 input checks, q packing, wavefront
+
+    def __init__(self, args, ctx, dfd, torch, workloads, rank, world):
+        self.n, self.m = args.n, args.m
+        self.p_np, self.q_np = workloads.warped_long_pair(self.n, self.m, dim=DIM, seed=SEED)
+        self.p = torch.from_numpy(self.p_np).cuda()
+        self.q = torch.from_numpy(self.q_np).cuda()
+        self.ctx, self.torch = ctx, torch
+        self.d = torch.empty(1, dtype=torch.float32, device="cuda")
+        self.d2 = torch.empty(1, dtype=torch.float32, device="cuda")
+        self.cells = self.n * self.m
+        shape = ctx.plan(0, DIM, self.n, self.m)
+        self.config = {"workload": f"long pair {self.n}x{self.m}, {DIM}-D float32 warped random walk (seed {SEED})",
+                       "n": self.n, "m": self.m, "dim": DIM, "cells_per_step": self.cells,
+                       "launch_shape": {"rows_per_lane": shape[0], "warps": shape[1], "ctas": shape[2]},
+                       "kernel_sha": kernel_sha()}
+        self.h2d = (self.n + self.m) * DIM * 4
+        self.d2h = 16
+
+    def step(self):
+        self.ctx.pair(self.p, self.q, self.d, self.d2)
+
+    def e2e_step(self):
+        return self.ctx.pair_host(self.p_np, self.q_np)
+
+    def verify(self):
+        gold_path = os.path.join(ROOT, "tests", "golden", "long_pair_200k.json")
+        if self.n != N_POINTS or self.m != N_POINTS or not os.path.exists(gold_path):
+            return None
+        rec = json.load(open(gold_path))
+        h = hashlib.sha256()
+        h.update(self.p_np.tobytes())
+        h.update(self.q_np.tobytes())
+        if h.hexdigest() != rec["sha256"]:
+            return None
+        got = float(self.d.item())
+        return abs(got - rec["delta_f64"]) <= 1e-6 * rec["delta_f64"]
+
+    def cpu_baseline(self):
+        import oracle
+        a = min(CPU_SAMPLE, self.n, self.m)
+        ps, qs = self.p_np[:a].copy(), self.q_np[:a].copy()
+        oracle.load()
+        t0 = time.perf_counter()
+        oracle.dfd2_linear(ps, qs)
+        dt = time.perf_counter() - t0
+        return {"value": a * a / dt / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+                "sample": f"prefix p[:{a}], q[:{a}] of the same pair, Alg. 5 float64, one thread, {dt:.1f} s"}
+
+    def per_pair(self):
+        return None
+
+
+class Pair2k(LongPair):
+    """One 2000 x 1500 2-D float32 pair (Gaussian walks)."""
+    micro_op = "cell_f32_d3"
+
+    def __init__(self, args, ctx, dfd, torch, workloads, rank, world):
+        self.n, self.m = 2000, 1500
+        self.p_np, self.q_np = workloads.gaussian_walk_pair(self.n, self.m, dim=2)
+        self.p = torch.from_numpy(self.p_np).cuda()
+        self.q = torch.from_numpy(self.q_np).cuda()
+        self.ctx, self.torch = ctx, torch
+        self.d = torch.empty(1, dtype=torch.float32, device="cuda")
+        self.d2 = torch.empty(1, dtype=torch.float32, device="cuda")
+        self.cells = self.n * self.m
+        self.config = {"workload": "pair 2000x1500, 2-D float32 Gaussian walks (seeds 1, 2)", "n": self.n,
+                       "m": self.m, "dim": 2, "cells_per_step": self.cells}
+        self.h2d = (self.n + self.m) * 2 * 4
+        self.d2h = 16
+
+    def verify(self):
+        import oracle
+        import math
+        return abs(float(self.d.item()) - math.sqrt(oracle.dfd2_linear(self.p_np, self.q_np))) <= \
+            1e-6 * float(self.d.item())
+
+    def cpu_baseline(self):
+        import oracle
+        oracle.load()
+        t0 = time.perf_counter()
+        k = 0
+        while time.perf_counter() - t0 < 10.0:
+            oracle.dfd2_linear(self.p_np, self.q_np)
+            k += 1
+        dt = time.perf_counter() - t0
+        return {"value": k * self.cells / dt / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+                "sample": f"the full pair, {k} times, Alg. 5 float64, one thread"}
+
+    def per_pair(self):
+        torch = self.torch
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        self.ctx.pair(self.p, self.q, reference=True)
+        torch.cuda.synchronize()
+        ev0.record()
+        for _ in range(5):
+            self.ctx.pair(self.p, self.q, reference=True)
+        ev1.record()
+        torch.cuda.synchronize()
+        return {"per_pair_reference_gcups": 5 * self.cells / (ev0.elapsed_time(ev1) * 1e-3) / 1e9}
+
+
+class _Many:
+    """Shared logic of the batch and matrix workloads (pairs sharded over ranks)."""
+
+    def e2e_step(self):
+        torch = self.torch
+        self.pts_dev.copy_(self.pts_host, non_blocking=True)
+        self.graph.launch()
+        self.out_host.copy_(self.out2, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+        return self.out_host
+
+    def step(self):
+        self.graph.launch()
+
+
+class Batch(_Many):
+    """65,536 ragged int32 2-D pairs, lengths U{16..512}, one captured graph per step."""
+    micro_op = "cell_i32_d2"
+    dtype = "i32"
+    launches_per_step = 5          # input check, 3 plan kernels, persistent batch kernel
+
+    def __init__(self, args, ctx, dfd, torch, workloads, rank, world):
+        b = workloads.ragged_int_batch()
+        pairs = b.pairs[rank::world].copy()
+        self.b, self.pairs_np = b, pairs
+        self.ctx, self.torch = ctx, torch
+        ln = b.lengths()
+        self.cells = int(np.sum(ln[pairs[:, 0]] * ln[pairs[:, 1]]))
+        self.pts_host = torch.from_numpy(b.points).pin_memory()
+        self.pts_dev = torch.from_numpy(b.points).cuda()
+        self.off = torch.from_numpy(b.offsets).cuda()
+        self.pairs = torch.from_numpy(pairs).cuda()
+        self.graph, self.out, self.out2 = ctx.batch(self.pts_dev, self.off, self.pairs, capture=True)
+        self.out_host = torch.empty_like(self.out2, device="cpu").pin_memory()
+        self.config = {"workload": "ragged batch, 65,536 pairs of int32 2-D random walks, lengths U{16..512} "
+                                   "(seed 4), one persistent launch per step in a captured CUDA graph",
+                       "n_pairs": int(pairs.shape[0]), "dim": 2, "cells_per_step": self.cells,
+                       "kernel_sha": kernel_sha(("batch_kernel.cuh", "batch_launch.cuh", "dfd_device.cuh"))}
+        self.h2d = b.points.nbytes
+        self.d2h = self.out2.numel() * 8
+
+    def verify(self):
+        import oracle
+        idx = np.random.default_rng(0).choice(self.pairs_np.shape[0], size=512, replace=False)
+        ref, _ = oracle.batch(self.b.points, self.b.offsets, self.pairs_np[idx])
+        return bool(np.array_equal(self.out2.cpu().numpy()[idx], ref))
+
+    def cpu_baseline(self):
+        import oracle
+        oracle.load()
+        n = 8192
+        t0 = time.perf_counter()
+        _, used = oracle.batch(self.b.points, self.b.offsets, self.pairs_np[:n])
+        dt = time.perf_counter() - t0
+        ln = self.b.lengths()
+        cells = int(np.sum(ln[self.pairs_np[:n, 0]] * ln[self.pairs_np[:n, 1]]))
+        return {"value": cells / dt / 1e9, "unit": UNIT, "cores": used, "kind": "oracle",
+                "sample": f"first {n} pairs of the batch, Alg. 5 int64, {used} threads, {dt:.1f} s"}
+
+    def per_pair(self):
+        """The same pairs one launch each, back to back on one stream (sample of 512)."""
+        torch = self.torch
+        ln = self.b.lengths()
+        idx = np.random.default_rng(1).choice(self.pairs_np.shape[0], size=512, replace=False)
+        curves = []
+        cells = 0
+        for k in idx:
+            a, c = self.pairs_np[k]
+            pa = self.pts_dev[self.b.offsets[a]:self.b.offsets[a + 1]]
+            pc = self.pts_dev[self.b.offsets[c]:self.b.offsets[c + 1]]
+            curves.append((pa, pc))
+            cells += int(ln[a] * ln[c])
+        out = {}
+        for name, kw in (("per_pair_reference_gcups", {"reference": True}), ("per_pair_wave_gcups", {})):
+            for pa, pc in curves[:8]:
+                self.ctx.pair(pa, pc, **kw)
+            torch.cuda.synchronize()
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ev0.record()
+            for pa, pc in curves:
+                self.ctx.pair(pa, pc, **kw)
+            ev1.record()
+            torch.cuda.synchronize()
+            out[name] = cells / (ev0.elapsed_time(ev1) * 1e-3) / 1e9
+        return out
+
+
+class Matrix(_Many):
+    """All-pairs condensed matrix of 4096 16-D float32 AR(1) curves, lengths U{64..256}."""
+    micro_op = "cell_f32_d16"
+    dtype = "f32"
+    launches_per_step = 2          # input check, persistent matrix kernel
+
+    def __init__(self, args, ctx, dfd, torch, workloads, rank, world):
+        if world > 1:
+            raise SystemExit("the matrix workload runs on one GPU")
+        b = workloads.ar1_curves()
+        self.b = b
+        self.ctx, self.torch = ctx, torch
+        ln = b.lengths().astype(np.int64)
+        tot = int(ln.sum())
+        self.cells = int((tot * tot - int(np.sum(ln * ln))) // 2)
+        self.pts_host = torch.from_numpy(b.points).pin_memory()
+        self.pts_dev = torch.from_numpy(b.points).cuda()
+        self.off = torch.from_numpy(b.offsets).cuda()
+        self.graph, self.out, self.out2 = ctx.matrix(self.pts_dev, self.off, capture=True)
+        self.out_host = torch.empty_like(self.out2, device="cpu").pin_memory()
+        n = b.n_curves
+        self.config = {"workload": "all-pairs matrix (upper triangle) of 4096 float32 16-D AR(1) curves "
+                                   "(phi 0.95), lengths U{64..256} (seed 5), one launch per step in a CUDA graph",
+                       "n_curves": n, "n_pairs": n * (n - 1) // 2, "dim": 16, "cells_per_step": self.cells,
+                       "kernel_sha": kernel_sha(("batch_kernel.cuh", "batch_launch.cuh", "dfd_device.cuh"))}
+        self.h2d = b.points.nbytes
+        self.d2h = self.out2.numel() * 4
+
+    def verify(self):
+        import oracle
+        n = self.b.n_curves
+        rng = np.random.default_rng(2)
+        ks = rng.integers(0, n * (n - 1) // 2, size=128)
+        starts = np.array([i * (2 * n - i - 1) // 2 for i in range(n)], np.int64)
+        ii = np.searchsorted(starts, ks, side="right") - 1
+        jj = ks - starts[ii] + ii + 1
+        mirror, _ = oracle.batch(self.b.points, self.b.offsets, np.stack([ii, jj], 1).astype(np.int32), mirror=True)
+        return bool(np.array_equal(self.out2.cpu().numpy()[ks], mirror))
+
+    def cpu_baseline(self):
+        import oracle
+        oracle.load()
+        rng = np.random.default_rng(3)
+        n = self.b.n_curves
+        pairs = np.stack([rng.integers(0, n, 20000), rng.integers(0, n, 20000)], 1).astype(np.int32)
+        t0 = time.perf_counter()
+        _, used = oracle.batch(self.b.points, self.b.offsets, pairs)
+        dt = time.perf_counter() - t0
+        ln = self.b.lengths()
+        cells = int(np.sum(ln[pairs[:, 0]] * ln[pairs[:, 1]]))
+        return {"value": cells / dt / 1e9, "unit": UNIT, "cores": used, "kind": "oracle",
+                "sample": f"20,000 random pairs of the 4096 curves, Alg. 5 float64, {used} threads, {dt:.1f} s"}
+
+    def per_pair(self):
+        return None
+
+
+WORKLOADS = {"long": LongPair, "pair2k": Pair2k, "batch": Batch, "matrix": Matrix}
+
+
 # -------------------------------------------------------------- reference
 def run_reference(args):
-    """CPU oracle (float64 Alg. 5) on host cores, bounded prefix per step."""
+    """CPU oracle on host cores, bounded sample per step."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
     import oracle
     from paper_2404_05708_gb300 import workloads
-    p, q = workloads.warped_long_pair(args.n, args.m, dim=DIM, seed=SEED)
-    a = min(REF_SAMPLE, args.n, args.m)
-    ps, qs = p[:a].copy(), q[:a].copy()
     oracle.load()
-    for _ in range(args.warmup):
-        oracle.dfd2_linear(ps, qs)
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        oracle.dfd2_linear(ps, qs)
-    dt = time.perf_counter() - t0
-    cells = a * a * args.steps
-    v = cells / dt / 1e9
-    sample = f"prefix p[:{a}], q[:{a}] of the {args.n}x{args.m} pair per step (Alg. 5, float64, 1 thread)"
+    if args.workload in ("long", "pair2k"):
+        if args.workload == "long":
+            p, q = workloads.warped_long_pair(args.n, args.m, dim=DIM, seed=SEED)
+            a = min(REF_SAMPLE, args.n, args.m)
+            ps, qs = p[:a].copy(), q[:a].copy()
+            sample = f"prefix p[:{a}], q[:{a}] of the {args.n}x{args.m} pair per step (Alg. 5, float64, 1 thread)"
+            cfg = {"workload": f"long pair {args.n}x{args.m}, {DIM}-D float32 warped random walk",
+                   "n": args.n, "m": args.m, "dim": DIM}
+        else:
+            ps, qs = workloads.gaussian_walk_pair(2000, 1500, dim=2)
+            sample = "the full 2000x1500 pair per step (Alg. 5, float64, 1 thread)"
+            cfg = {"workload": "pair 2000x1500, 2-D float32 Gaussian walks", "n": 2000, "m": 1500, "dim": 2}
+        cells_step = ps.shape[0] * qs.shape[0]
+        for _ in range(args.warmup):
+            oracle.dfd2_linear(ps, qs)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            oracle.dfd2_linear(ps, qs)
+        dt = time.perf_counter() - t0
+        cores, dtype = 1, "f64"
+    else:
+        if args.workload == "batch":
+            b = workloads.ragged_int_batch()
+            pairs = b.pairs[:4096]
+            dtype = "int64"
+            cfg = {"workload": "ragged batch, 65,536 pairs of int32 2-D random walks", "dim": 2}
+            sample = "first 4096 pairs of the batch per step (Alg. 5, int64, all host threads)"
+        else:
+            b = workloads.ar1_curves()
+            rng = np.random.default_rng(3)
+            pairs = np.stack([rng.integers(0, 4096, 4096), rng.integers(0, 4096, 4096)], 1).astype(np.int32)
+            dtype = "f64"
+            cfg = {"workload": "all-pairs matrix of 4096 float32 16-D AR(1) curves", "dim": 16}
+            sample = "4096 random pairs per step (Alg. 5, float64, all host threads)"
+        ln = b.lengths()
+        cells_step = int(np.sum(ln[pairs[:, 0]] * ln[pairs[:, 1]]))
+        for _ in range(args.warmup):
+            oracle.batch(b.points, b.offsets, pairs)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            _, cores = oracle.batch(b.points, b.offsets, pairs)
+        dt = time.perf_counter() - t0
+    v = cells_step * args.steps / dt / 1e9
     out = {
         "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"long pair {args.n}x{args.m}, {DIM}-D float32 warped random walk", "n": args.n,
-                   "m": args.m, "dim": DIM},
+        "scaling": "weak", "vs_baseline": None, "dtype": dtype, "data": "synthetic", "config": cfg,
         "impl": "reference",
-        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(out))
@@ -161,24 +448,11 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------------ ours
-def cpu_baseline_leg(p, q):
-    import oracle
-    a = min(CPU_SAMPLE, p.shape[0], q.shape[0])
-    ps, qs = p[:a].copy(), q[:a].copy()
-    oracle.load()
-    t0 = time.perf_counter()
-    oracle.dfd2_linear(ps, qs)
-    dt = time.perf_counter() - t0
-    return {"value": a * a / dt / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"prefix p[:{a}], q[:{a}] of the same pair, Alg. 5 float64, one thread, {dt:.1f} s"}
-
-
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
 
-    import numpy as np
     import torch
     import torch.distributed as dist
     from paper_2404_05708_gb300 import build, dfd, workloads
@@ -195,23 +469,17 @@ def main():
     if world > 1:
         dist.barrier()
 
-    n, m = args.n, args.m
-    p_np, q_np = workloads.warped_long_pair(n, m, dim=DIM, seed=SEED)
-    p = torch.from_numpy(p_np).cuda()
-    q = torch.from_numpy(q_np).cuda()
     ctx = dfd.Context(local)
     dfd.dfd_timing_enable(ctx.handle, True)
-    d_out = torch.empty(1, dtype=torch.float32, device="cuda")
-    d2_out = torch.empty(1, dtype=torch.float32, device="cuda")
+    wl = WORKLOADS[args.workload](args, ctx, dfd, torch, workloads, rank, world)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
 
     for _ in range(args.warmup):
         flush.zero_()
-        ctx.pair(p, q, d_out, d2_out)
+        wl.step()
     torch.cuda.synchronize()
 
-    gpu_id = None
     try:
         gpu_id = "GPU-" + str(torch.cuda.get_device_properties(local).uuid).replace("GPU-", "")
     except Exception:
@@ -227,9 +495,10 @@ def main():
     for k in range(args.steps):
         flush.zero_()                       # L2 flush outside the timed events
         ev[k][0].record(stream)
-        ctx.pair(p, q, d_out, d2_out)
+        wl.step()
         ev[k][1].record(stream)
-        kernel_ms.append(dfd.dfd_timing_last(ctx.handle))
+        if args.workload in ("long", "pair2k"):
+            kernel_ms.append(dfd.dfd_timing_last(ctx.handle))
     torch.cuda.synchronize()
     step_ms = [a.elapsed_time(b) for a, b in ev]
     total_ms = sum(step_ms)
@@ -237,19 +506,22 @@ def main():
         t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         total_ms = float(t.item())
+        c = torch.tensor([wl.cells], device="cuda", dtype=torch.float64)
+        dist.all_reduce(c, op=dist.ReduceOp.SUM)
+        total_cells = float(c.item())
         dist.barrier()
+    else:
+        total_cells = float(wl.cells)
     torch.cuda.synchronize()
     clocks = sampler.stop()
+    value = total_cells * args.steps / (total_ms * 1e-3) / 1e9
+    verified = wl.verify()
 
-    cells_per_step = n * m
-    value = world * cells_per_step * args.steps / (total_ms * 1e-3) / 1e9
-    got_d = float(d_out.item())
-
-    # end to end through the host-buffer entry point
+    # end to end through the public API with host buffers
     e2e_times = []
     for k in range(args.warmup + args.steps):
         t0 = time.perf_counter()
-        dh, _ = ctx.pair_host(p_np, q_np)
+        wl.e2e_step()
         if k >= args.warmup:
             e2e_times.append(time.perf_counter() - t0)
     e2e_total = sum(e2e_times)
@@ -257,60 +529,51 @@ def main():
         t = torch.tensor([e2e_total], device="cuda", dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_total = float(t.item())
-    e2e_value = world * cells_per_step * args.steps / e2e_total / 1e9
+    e2e_value = total_cells * args.steps / e2e_total / 1e9
 
-    # parity of the timed result against the stored oracle value
-    verified = None
-    gold_path = os.path.join(ROOT, "tests", "golden", "long_pair_200k.json")
-    if n == N_POINTS and m == N_POINTS and os.path.exists(gold_path):
-        rec = json.load(open(gold_path))
-        h = hashlib.sha256()
-        h.update(p_np.tobytes())
-        h.update(q_np.tobytes())
-        if h.hexdigest() == rec["sha256"]:
-            verified = abs(got_d - rec["delta_f64"]) <= 1e-6 * rec["delta_f64"] and float(dh) == got_d
-
-    # ALU roofline: measured issue rate of one cell's instruction mix
-    cell_rate, mb_mhz = dfd.dfd_microbench(ctx.handle, dfd.MICRO_OPS["cell_f32_d3"])
+    # ALU roofline: measured issue rate of the workload's cell instruction mix
+    cell_rate, mb_mhz = dfd.dfd_microbench(ctx.handle, dfd.MICRO_OPS[wl.micro_op])
     sms = torch.cuda.get_device_properties(local).multi_processor_count
     clk = clocks["sm_mhz"] if clocks else mb_mhz
     peak = cell_rate * sms * clk * 1e6 / 1e9
-    kern_avg = sum(kernel_ms) / len(kernel_ms)
-    achieved = cells_per_step / (kern_avg * 1e-3) / 1e9
-    sha = kernel_sha()
+    kern_avg = (sum(kernel_ms) / len(kernel_ms)) if kernel_ms else total_ms / args.steps
+    achieved = wl.cells / (kern_avg * 1e-3) / 1e9
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gcell/s", "frac": achieved / peak,
-                "traffic": TRAFFIC_BY_KERNEL_SHA.get(sha),
-                "peak_basis": f"measured cell-mix rate {cell_rate:.2f} cells/clk/SM x {sms} SMs x {clk:.0f} MHz"}
+                "traffic": TRAFFIC_BY_KERNEL_SHA.get(wl.config.get("kernel_sha")),
+                "peak_basis": f"measured {wl.micro_op} mix {cell_rate:.2f} cells/clk/SM x {sms} SMs x {clk:.0f} MHz"}
+    if not kernel_ms:
+        roofline["timing"] = "whole captured graph per step (plan + persistent kernel)"
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline_leg(p_np, q_np)
+        cpu = wl.cpu_baseline()
+    extra = wl.per_pair() if rank == 0 else None
 
-    shape = ctx.plan(dfd.DFD_F32, DIM, n, m)
+    cfg = dict(wl.config)
+    cfg.update({"parallelism": (f"dp{world} (pairs sharded)" if args.workload == "batch" else "replicas")
+                if world > 1 else "single",
+                "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MB write)", "verified_vs_oracle": verified})
+    if extra:
+        cfg["per_pair"] = extra
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": f"long pair {n}x{m}, {DIM}-D float32 warped random walk (seed {SEED})",
-                   "n": n, "m": m, "dim": DIM, "cells_per_step": cells_per_step,
-                   "parallelism": "replicas" if world > 1 else "single",
-                   "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MB write)",
-                   "launch_shape": {"rows_per_lane": shape[0], "warps": shape[1], "ctas": shape[2]},
-                   "verified_vs_oracle": verified, "kernel_sha": sha},
-        "roofline": roofline,
-        "cpu_baseline": cpu,
-        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": (n + m) * DIM * 4,
-                "d2h_bytes_per_step": 16},
-        "gpu_launches": 4 * args.steps,
+        "scaling": "strong" if args.workload == "batch" else "weak", "vs_baseline": None, "dtype": wl.dtype,
+        "data": "synthetic", "config": cfg, "roofline": roofline, "cpu_baseline": cpu,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": wl.h2d, "d2h_bytes_per_step": wl.d2h},
+        "gpu_launches": wl.launches_per_step * args.steps,
         "clocks": clocks,
     }
     if rank == 0:
         print(json.dumps(out))
+    del wl
     ctx.close()
     if world > 1:
         dist.destroy_process_group()
     return 0
 
+
+import numpy as np  # noqa: E402  (workload classes use it)
 
 if __name__ == "__main__":
     sys.exit(main())

@@ -38,14 +38,15 @@ enum MicroOp {
   MB_LAT_SHFL = 13,        // latency: dependent shfl.up chain
   MB_LAT_FFMA2 = 14,       // latency: dependent fma.f32x2 chain
   MB_LAT_MNMX64 = 15,      // latency: dependent min.s64 -> max.s64 (int cell chain)
-  MB_COUNT = 16
+  MB_MIX_F32D16 = 16,      // one float32 16-D cell: 16 sub + 16 fma/mul + min3 + max (scalar)
+  MB_COUNT = 17
 };
 
-__host__ __device__ constexpr bool is_latency(int op) { return op >= MB_LAT_FMNMX; }
+__host__ __device__ constexpr bool is_latency(int op) { return op >= MB_LAT_FMNMX && op <= MB_LAT_MNMX64; }
 
 // operations (thread-instructions, cells, or dependent ops) per iteration
 __host__ __device__ constexpr int ops_per_iter(int op) {
-  return op == MB_MIX_F32D3 ? 16 : op == MB_MIX_I32D2 ? 8 : op == MB_DISTONLY_F32D3 ? 16 : 8;
+  return op == MB_MIX_F32D3 ? 16 : op == MB_MIX_I32D2 ? 8 : op == MB_DISTONLY_F32D3 ? 16 : op == MB_MIX_F32D16 ? 2 : 8;
 }
 
 template <int OP>
@@ -83,6 +84,22 @@ __global__ void __launch_bounds__(MB_THREADS) micro_kernel(float seed, unsigned 
     } else if constexpr (OP == MB_LAT_FFMA2) {
 #pragma unroll
       for (int k = 0; k < 8; ++k) asm volatile("fma.rn.f32x2 %0, %0, %1, %1;" : "+l"(u[0]) : "l"(cu));
+    } else if constexpr (OP == MB_MIX_F32D16) {
+      // two independent 16-D cells per iteration (coordinates loop-carried)
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        float acc, t;
+        asm volatile("sub.rn.f32 %0, %1, %2;" : "=f"(t) : "f"(f[c]), "f"(c1));
+        asm volatile("mul.rn.f32 %0, %1, %1;" : "=f"(acc) : "f"(t));
+#pragma unroll
+        for (int k = 1; k < 16; ++k) {
+          asm volatile("sub.rn.f32 %0, %1, %2;" : "=f"(t) : "f"(f[(c + k) & 7]), "f"(c2));
+          asm volatile("fma.rn.f32 %0, %1, %1, %0;" : "+f"(acc) : "f"(t));
+        }
+        asm volatile("min.f32 %0, %0, %1, %2;" : "+f"(f[c + 4]) : "f"(c1), "f"(c2));
+        asm volatile("max.f32 %0, %0, %1;" : "+f"(f[c + 4]) : "f"(acc));
+        f[c] = acc;
+      }
     } else if constexpr (OP == MB_LAT_MNMX64) {
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
@@ -229,6 +246,7 @@ extern "C" dfd_status dfd_microbench(dfd_context* ctx, int op, double* result, d
     case MB_LAT_SHFL: return run_op<MB_LAT_SHFL>(ctx, result, sm_mhz);
     case MB_LAT_FFMA2: return run_op<MB_LAT_FFMA2>(ctx, result, sm_mhz);
     case MB_LAT_MNMX64: return run_op<MB_LAT_MNMX64>(ctx, result, sm_mhz);
+    case MB_MIX_F32D16: return run_op<MB_MIX_F32D16>(ctx, result, sm_mhz);
     default: return DFD_ERR_INVALID_ARG;
   }
 }
