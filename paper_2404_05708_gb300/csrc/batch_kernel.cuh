@@ -11,6 +11,7 @@
 // stripe k+1 overwrites it).  Persistent warps take work items from an
 // atomic counter over a device-built, cost-descending (LPT) work list.
 #pragma once
+#include <type_traits>
 #include "dfd_device.cuh"
 
 namespace dfd {
@@ -31,10 +32,53 @@ __host__ __device__ __forceinline__ int rows_per_lane(int rows) {
   return r > Rmax<DK>::value ? Rmax<DK>::value : (r < 1 ? 1 : r);
 }
 
+// Point j of a curve into registers, coordinates past dim zero.  With `vec`
+// (dim == DK in {2, 4, 8, 16} and 16-byte aligned curves, checked by the
+// host) one 8- or 16-byte load per 2 or 4 coordinates.
+template <class Cd, int DK>
+__device__ __forceinline__ void load_point(const Cd* __restrict__ Q, int j, int dim, bool vec, Cd (&qk)[DK]) {
+  if constexpr (DK == 2) {
+    if (vec) {
+      if constexpr (sizeof(Cd) == 4 && std::is_same<Cd, float>::value) {
+        const float2 t = __ldg(reinterpret_cast<const float2*>(Q) + j);
+        qk[0] = t.x;
+        qk[1] = t.y;
+      } else {
+        const int2 t = __ldg(reinterpret_cast<const int2*>(Q) + j);
+        qk[0] = t.x;
+        qk[1] = t.y;
+      }
+      return;
+    }
+  } else if constexpr (DK % 4 == 0) {
+    if (vec) {
+#pragma unroll
+      for (int c = 0; c < DK / 4; ++c) {
+        if constexpr (std::is_same<Cd, float>::value) {
+          const float4 t = __ldg(reinterpret_cast<const float4*>(Q) + (int64_t)j * (DK / 4) + c);
+          qk[4 * c] = t.x;
+          qk[4 * c + 1] = t.y;
+          qk[4 * c + 2] = t.z;
+          qk[4 * c + 3] = t.w;
+        } else {
+          const int4 t = __ldg(reinterpret_cast<const int4*>(Q) + (int64_t)j * (DK / 4) + c);
+          qk[4 * c] = t.x;
+          qk[4 * c + 1] = t.y;
+          qk[4 * c + 2] = t.z;
+          qk[4 * c + 3] = t.w;
+        }
+      }
+      return;
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < DK; ++k) qk[k] = k < dim ? __ldg(Q + (int64_t)j * dim + k) : (Cd)0;
+}
+
 template <class V, int DK, int R>
 __device__ __forceinline__ typename V::value warp_dfd(const typename V::coord* __restrict__ P, int n,
                                                       const typename V::coord* __restrict__ Q, int m, int dim,
-                                                      typename V::value* buf, int L) {
+                                                      bool vec, typename V::value* buf, int L) {
   using T = typename V::value;
   using Cd = typename V::coord;
   const int nstripes = (n + 32 * R - 1) / (32 * R);
@@ -57,13 +101,15 @@ __device__ __forceinline__ typename V::value warp_dfd(const typename V::coord* _
     for (int c0 = 0; c0 < nsteps; c0 += 32) {
       const T top_blk = has_top ? buf[min(c0 + L, m - 1)] : V::inf();
       T out_blk = V::inf();
-#pragma unroll
+      // 4 steps unrolled (not 32): a kernel holds every R variant, and warps
+      // running different variants side by side must not thrash the
+      // instruction cache.
+#pragma unroll 4
       for (int s = 0; s < 32; ++s) {
         const int j = c0 + s - L;
         const int jq = min(max(j, 0), m - 1);
         Cd qk[DK];
-#pragma unroll
-        for (int k = 0; k < DK; ++k) qk[k] = k < dim ? __ldg(Q + (int64_t)jq * dim + k) : (Cd)0;
+        load_point<Cd, DK>(Q, jq, dim, vec, qk);
         T d[R];
 #pragma unroll
         for (int r = 0; r < R; ++r) d[r] = dist2<DK>(pr[r], qk);
@@ -100,13 +146,13 @@ __device__ __forceinline__ typename V::value warp_dfd(const typename V::coord* _
 
 template <class V, int DK>
 __device__ __forceinline__ typename V::value warp_dfd_any(const typename V::coord* P, int n,
-                                                          const typename V::coord* Q, int m, int dim,
+                                                          const typename V::coord* Q, int m, int dim, bool vec,
                                                           typename V::value* buf, int L) {
   constexpr int RM = Rmax<DK>::value;
   switch (rows_per_lane<DK>(n)) {
 #define DFD_B_CASE(RR)                                                            \
   case RR:                                                                        \
-    if constexpr (RR <= RM) return warp_dfd<V, DK, RR>(P, n, Q, m, dim, buf, L); \
+    if constexpr (RR <= RM) return warp_dfd<V, DK, RR>(P, n, Q, m, dim, vec, buf, L); \
     break;
     DFD_B_CASE(1)
     DFD_B_CASE(2)
@@ -127,7 +173,7 @@ __device__ __forceinline__ typename V::value warp_dfd_any(const typename V::coor
       break;
 #undef DFD_B_CASE
   }
-  return warp_dfd<V, DK, RM>(P, n, Q, m, dim, buf, L);
+  return warp_dfd<V, DK, RM>(P, n, Q, m, dim, vec, buf, L);
 }
 
 // A pair needs the row buffer when its rows span several stripes.
@@ -148,15 +194,19 @@ __device__ __forceinline__ void write_result(void* out_dist, void* out_dist2, in
 }
 
 // ------------------------------------------------------------- planning
-// Cost bucket of a pair, descending cost = ascending bucket: 4 buckets per
-// octave of rows*cols, 128 buckets.
-constexpr int NBUCKET = 128;
+// Work order: by code variant first (rows per lane R, then the number of
+// stripes), largest first, then by column count, largest first (LPT within
+// a variant).  Warps resident together then mostly run the same variant,
+// and the costliest pairs start first.  16 variant classes x 16 column
+// buckets of 256.
+constexpr int NBUCKET = 256;
 
-__device__ __forceinline__ int cost_bucket(int64_t cost) {
-  const int lg = 63 - __clzll((unsigned long long)max(cost, (int64_t)1));
-  const int frac = (int)((cost >> max(lg - 2, 0)) & 3);  // next two bits
-  const int b = lg * 4 + (lg >= 2 ? frac : 0);
-  return NBUCKET - 1 - min(b, NBUCKET - 1);
+__device__ __forceinline__ int cost_bucket(int64_t rows, int64_t cols, int rmax) {
+  const int64_t per_stripe = 32 * (int64_t)rmax;
+  const int64_t stripes = (rows + per_stripe - 1) / per_stripe;
+  const int cls = stripes > 1 ? rmax + (int)min(stripes - 1, (int64_t)6) : (int)((rows + 31) / 32);
+  const int sub = 15 - (int)min((int64_t)15, (cols - 1) / 256);
+  return (15 - min(cls, 15)) * 16 + sub;
 }
 
 struct PlanArgs {
@@ -169,6 +219,7 @@ struct PlanArgs {
   unsigned char* bucket;  // [n_pairs]
   unsigned* worklist;  // [n_pairs]: pair index | swap << 31
   int* err;
+  int rmax;            // rows per lane of one stripe for this dimension class
 };
 
 // (static: this header is compiled into several translation units)
@@ -184,7 +235,7 @@ static __global__ void plan_hist_kernel(PlanArgs a) {
       const int64_t na = ea - oa, nb = eb - ob;
       if (na < 1 || nb < 1 || oa < 0 || ob < 0 || ea > total || eb > total || na > INT32_MAX || nb > INT32_MAX)
         raise_error(a.err, DFD_ERR_INVALID_ARG);
-      b = cost_bucket(max(na, (int64_t)1) * max(nb, (int64_t)1));
+      b = cost_bucket(max(min(na, nb), (int64_t)1), max(max(na, nb), (int64_t)1), a.rmax);
     }
     a.bucket[k] = (unsigned char)b;
     atomicAdd(&a.hist[b], 1u);
@@ -225,6 +276,7 @@ struct BatchArgs {
   int64_t n_items;
   int64_t n_curves;
   int dim;
+  int vec;             // 1: vector point loads allowed (dim == DK, 16-byte aligned points)
   int* counter;
   int* err;
   void* out_dist;
@@ -264,7 +316,7 @@ __global__ void __launch_bounds__(256, 2) batch_kernel(BatchArgs a) {
       if (L == 0) raise_error(a.err, DFD_ERR_UNSUPPORTED);
       continue;
     }
-    const T r = warp_dfd_any<V, DK>(pts + oa * a.dim, n, pts + ob * a.dim, m, a.dim, buf, L);
+    const T r = warp_dfd_any<V, DK>(pts + oa * a.dim, n, pts + ob * a.dim, m, a.dim, a.vec != 0, buf, L);
     if (L == 0) write_result<T>(a.out_dist, a.out_dist2, k, r);
   }
 }
@@ -291,6 +343,7 @@ struct MatrixArgs {
   int64_t n_curves;
   int64_t n_pairs;
   int dim;
+  int vec;             // 1: vector point loads allowed (dim == DK, 16-byte aligned points)
   int chunk;        // pairs per pop
   int* counter;
   int* err;
@@ -327,9 +380,9 @@ __global__ void __launch_bounds__(256, 2) matrix_kernel(MatrixArgs a) {
       } else if (fits_buffer<DK>(rows, cols)) {
         T r;
         if (ni <= nj)
-          r = warp_dfd_any<V, DK>(pts + oi * a.dim, ni, pts + oj * a.dim, nj, a.dim, buf, L);
+          r = warp_dfd_any<V, DK>(pts + oi * a.dim, ni, pts + oj * a.dim, nj, a.dim, a.vec != 0, buf, L);
         else
-          r = warp_dfd_any<V, DK>(pts + oj * a.dim, nj, pts + oi * a.dim, ni, a.dim, buf, L);
+          r = warp_dfd_any<V, DK>(pts + oj * a.dim, nj, pts + oi * a.dim, ni, a.dim, a.vec != 0, buf, L);
         if (L == 0) write_result<T>(a.out_dist, a.out_dist2, k, r);
       } else if (L == 0) {
         raise_error(a.err, DFD_ERR_UNSUPPORTED);

@@ -26,6 +26,17 @@ __global__ void check_points_kernel(const typename V::coord* x, const int64_t* c
     raise_error(err, std::is_same<V, F32>::value ? DFD_ERR_NONFINITE : DFD_ERR_RANGE);
 }
 
+// Vector point loads need dim == DK in {2, 4, 8, 16} and aligned points
+// (8 bytes for 2-D, 16 bytes otherwise; every curve then starts aligned too).
+template <int DK>
+int vector_loads_ok(const void* points, int dim) {
+  const uintptr_t a = reinterpret_cast<uintptr_t>(points);
+  if (dim != DK) return 0;
+  if (DK == 2) return a % 8 == 0;
+  if (DK % 4 == 0) return a % 16 == 0;
+  return 0;
+}
+
 template <class K>
 int resident_blocks(const dfd_context* ctx, K kernel, int threads) {
   int per_sm = 0;
@@ -68,6 +79,7 @@ dfd_status batch_launch(dfd_context* ctx, int dim, const void* points, const int
   pa.bucket = reinterpret_cast<unsigned char*>(base + off_bucket);
   pa.worklist = reinterpret_cast<unsigned*>(base + off_work);
   pa.err = ctx->d_err;
+  pa.rmax = batch::Rmax<DK>::value;
   const int pblocks = (int)std::min<int64_t>((n_pairs + 255) / 256, 8 * (int64_t)ctx->num_sms);
   batch::plan_hist_kernel<<<pblocks, 256, 0, s>>>(pa);
   batch::plan_scan_kernel<<<1, 32, 0, s>>>(pa);
@@ -81,6 +93,7 @@ dfd_status batch_launch(dfd_context* ctx, int dim, const void* points, const int
   ba.n_items = n_pairs;
   ba.n_curves = n_curves;
   ba.dim = dim;
+  ba.vec = vector_loads_ok<DK>(points, dim);
   ba.counter = reinterpret_cast<int*>(base);
   ba.err = ctx->d_err;
   ba.out_dist = out_dist;
@@ -116,6 +129,7 @@ dfd_status matrix_launch(dfd_context* ctx, int dim, const void* points, const in
   ma.n_curves = n_curves;
   ma.n_pairs = n_curves * (n_curves - 1) / 2;
   ma.dim = dim;
+  ma.vec = vector_loads_ok<DK>(points, dim);
   ma.chunk = chunk > 0 ? chunk : 8;
   ma.counter = reinterpret_cast<int*>(base);
   ma.err = ctx->d_err;

@@ -85,7 +85,8 @@ __global__ void __launch_bounds__(MB_THREADS) micro_kernel(float seed, unsigned 
 #pragma unroll
       for (int k = 0; k < 8; ++k) asm volatile("fma.rn.f32x2 %0, %0, %1, %1;" : "+l"(u[0]) : "l"(cu));
     } else if constexpr (OP == MB_MIX_F32D16) {
-      // two independent 16-D cells per iteration (coordinates loop-carried)
+      // two independent 16-D cells per iteration (coordinates loop-carried,
+      // 16 distinct subtrahends so no subtraction can be merged)
 #pragma unroll
       for (int c = 0; c < 2; ++c) {
         float acc, t;
@@ -93,7 +94,7 @@ __global__ void __launch_bounds__(MB_THREADS) micro_kernel(float seed, unsigned 
         asm volatile("mul.rn.f32 %0, %1, %1;" : "=f"(acc) : "f"(t));
 #pragma unroll
         for (int k = 1; k < 16; ++k) {
-          asm volatile("sub.rn.f32 %0, %1, %2;" : "=f"(t) : "f"(f[(c + k) & 7]), "f"(c2));
+          asm volatile("sub.rn.f32 %0, %1, %2;" : "=f"(t) : "f"(f[c]), "f"(c2 + (float)k));
           asm volatile("fma.rn.f32 %0, %1, %1, %0;" : "+f"(acc) : "f"(t));
         }
         asm volatile("min.f32 %0, %0, %1, %2;" : "+f"(f[c + 4]) : "f"(c1), "f"(c2));
