@@ -184,6 +184,64 @@ dfd_status dfd_graph_launch(dfd_graph* graph, void* stream);
 dfd_status dfd_graph_destroy(dfd_graph* graph);
 
 /*
+ * Serving: query-vs-candidates searches (Sec. 4's batch of curves against
+ * one reference curve, as a request stream) with continuous batching.
+ *
+ * Candidate curves (float32) are uploaded once and stay resident on the
+ * device.  dfd_server_submit (any host thread, non-blocking) queues a
+ * request: one query curve and k candidate ids; the k distances are written
+ * to host_out[0..k) before dfd_server_wait returns DFD_OK.  A scheduler
+ * thread admits requests in arrival order while fewer than max_slots are
+ * running and the device arena (mem_budget_bytes) holds their query (O(n));
+ * it runs ticks -- one persistent launch per point dimension over pairs from
+ * every admitted request, costliest first, up to tick_cells cells -- and a
+ * pair longer than one row stripe advances at most stripes_per_tick stripes
+ * per tick, its O(m) bottom row kept in the arena between ticks (the prefix
+ * property of Sec. 3).  Requests that arrive while others run join the next
+ * tick; two ticks are in flight.  Each distance is bit-identical to
+ * dfd_pair's for the same two curves, whatever else is in the tick.
+ * Ownership: submit copies the query and ids; host_out must stay valid
+ * until wait returns OK or CANCELLED.  A ticket is released by the wait that
+ * returns its final status.  Destroy the server before its context.
+ */
+typedef struct dfd_server dfd_server;
+typedef struct dfd_server_options {
+  size_t struct_size;        /* sizeof(dfd_server_options) */
+  size_t mem_budget_bytes;   /* device arena for queries and row states (default 1 GiB) */
+  int max_slots;             /* requests running at once (default 256) */
+  double tick_cells;         /* cells per tick (default 2e9) */
+  int stripes_per_tick;      /* row stripes a long pair advances per tick (default 4) */
+} dfd_server_options;
+typedef struct dfd_serving_stats {
+  uint64_t completed, cancelled, ticks;
+  double cells;              /* cells of completed requests */
+  double p50_ms, p99_ms, mean_ms;   /* latency: completion - arrival */
+  double gpu_busy_ms;        /* device time of all ticks */
+  double gcups_busy;         /* cells / gpu_busy_ms */
+  double gcups_wall;         /* cells / (last completion - first arrival) */
+  size_t arena_used_bytes;
+} dfd_serving_stats;
+
+dfd_status dfd_server_options_default(dfd_server_options* opt);
+dfd_status dfd_server_create(dfd_context* ctx, const dfd_server_options* opt, dfd_server** out);
+dfd_status dfd_server_destroy(dfd_server* server);
+/* Append n_curves candidates of dimension dim (host CSR arrays, offsets[0] = 0);
+   *first_id receives the id of the first one (ids are per dimension). */
+dfd_status dfd_server_add_candidates(dfd_server* server, int dim, const float* host_points,
+                                     const int64_t* host_offsets, int64_t n_curves, int64_t* first_id);
+/* arrival_s: the request's arrival time on the dfd_server_now clock (latency is
+   measured from it; < 0 = now). */
+dfd_status dfd_server_submit(dfd_server* server, int dim, const float* host_query, int64_t n,
+                             const int64_t* cand_ids, int64_t k, float* host_out, double arrival_s, uint64_t* ticket);
+/* DFD_OK / DFD_ERR_CANCELLED (final), DFD_ERR_NOT_READY on timeout (timeout_ms < 0: no limit). */
+dfd_status dfd_server_wait(dfd_server* server, uint64_t ticket, double timeout_ms);
+dfd_status dfd_server_cancel(dfd_server* server, uint64_t ticket);
+dfd_status dfd_server_stats(dfd_server* server, dfd_serving_stats* out);
+dfd_status dfd_server_stats_reset(dfd_server* server);
+/* The server's clock in seconds (monotonic). */
+double dfd_server_now(dfd_server* server);
+
+/*
  * Explicit launch shape for the band wavefront of dfd_pair (for tuning and
  * measurement).  rows_per_lane in {2, 4, 6, 8}, warps in 1..16 (compute
  * warps per CTA; one more communication warp is added), ctas in 1..#SMs

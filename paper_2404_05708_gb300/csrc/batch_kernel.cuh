@@ -75,15 +75,22 @@ __device__ __forceinline__ void load_point(const Cd* __restrict__ Q, int j, int 
   for (int k = 0; k < DK; ++k) qk[k] = k < dim ? __ldg(Q + (int64_t)j * dim + k) : (Cd)0;
 }
 
+// Stripes [st_begin, st_end) of the pair (all of them by default).  `buf`
+// holds the bottom row of stripe st_begin - 1 on entry (when st_begin > 0)
+// and of stripe st_end - 1 on exit (when st_end < #stripes): this is the
+// O(m) row state that lets a long pair pause between serving ticks (row i of
+// the recurrence summarises rows 1..i, Sec. 3).  Returns delta^2 when the
+// last stripe ran, +inf otherwise.
 template <class V, int DK, int R>
 __device__ __forceinline__ typename V::value warp_dfd(const typename V::coord* __restrict__ P, int n,
                                                       const typename V::coord* __restrict__ Q, int m, int dim,
-                                                      bool vec, typename V::value* buf, int L) {
+                                                      bool vec, typename V::value* buf, int L, int st_begin = 0,
+                                                      int st_end = 1 << 30) {
   using T = typename V::value;
   using Cd = typename V::coord;
   const int nstripes = (n + 32 * R - 1) / (32 * R);
   T res = V::inf();
-  for (int st = 0; st < nstripes; ++st) {
+  for (int st = st_begin; st < min(st_end, nstripes); ++st) {
     Cd pr[R][DK];
 #pragma unroll
     for (int r = 0; r < R; ++r) {
@@ -147,12 +154,13 @@ __device__ __forceinline__ typename V::value warp_dfd(const typename V::coord* _
 template <class V, int DK>
 __device__ __forceinline__ typename V::value warp_dfd_any(const typename V::coord* P, int n,
                                                           const typename V::coord* Q, int m, int dim, bool vec,
-                                                          typename V::value* buf, int L) {
+                                                          typename V::value* buf, int L, int st_begin = 0,
+                                                          int st_end = 1 << 30) {
   constexpr int RM = Rmax<DK>::value;
   switch (rows_per_lane<DK>(n)) {
-#define DFD_B_CASE(RR)                                                            \
-  case RR:                                                                        \
-    if constexpr (RR <= RM) return warp_dfd<V, DK, RR>(P, n, Q, m, dim, vec, buf, L); \
+#define DFD_B_CASE(RR)                                                                                 \
+  case RR:                                                                                             \
+    if constexpr (RR < RM) return warp_dfd<V, DK, RR>(P, n, Q, m, dim, vec, buf, L, st_begin, st_end); \
     break;
     DFD_B_CASE(1)
     DFD_B_CASE(2)
@@ -161,19 +169,18 @@ __device__ __forceinline__ typename V::value warp_dfd_any(const typename V::coor
     DFD_B_CASE(5)
     DFD_B_CASE(6)
     DFD_B_CASE(7)
-    DFD_B_CASE(8)
-    DFD_B_CASE(9)
-    DFD_B_CASE(10)
-    DFD_B_CASE(11)
-    DFD_B_CASE(12)
-    DFD_B_CASE(13)
-    DFD_B_CASE(14)
-    DFD_B_CASE(15)
     default:
       break;
 #undef DFD_B_CASE
   }
-  return warp_dfd<V, DK, RM>(P, n, Q, m, dim, vec, buf, L);
+  return warp_dfd<V, DK, RM>(P, n, Q, m, dim, vec, buf, L, st_begin, st_end);
+}
+
+// Number of stripes warp_dfd_any uses for a pair with `rows` rows.
+template <int DK>
+__host__ __device__ __forceinline__ int num_stripes(int rows) {
+  const int r = rows_per_lane<DK>(rows);
+  return (rows + 32 * r - 1) / (32 * r);
 }
 
 // A pair needs the row buffer when its rows span several stripes.

@@ -42,6 +42,18 @@ class WaveShape(ctypes.Structure):
     _fields_ = [("rows_per_lane", ctypes.c_int), ("warps", ctypes.c_int), ("ctas", ctypes.c_int)]
 
 
+class ServerOptions(ctypes.Structure):
+    _fields_ = [("struct_size", ctypes.c_size_t), ("mem_budget_bytes", ctypes.c_size_t), ("max_slots", ctypes.c_int),
+                ("tick_cells", ctypes.c_double), ("stripes_per_tick", ctypes.c_int)]
+
+
+class ServingStats(ctypes.Structure):
+    _fields_ = [("completed", ctypes.c_uint64), ("cancelled", ctypes.c_uint64), ("ticks", ctypes.c_uint64),
+                ("cells", ctypes.c_double), ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double),
+                ("mean_ms", ctypes.c_double), ("gpu_busy_ms", ctypes.c_double), ("gcups_busy", ctypes.c_double),
+                ("gcups_wall", ctypes.c_double), ("arena_used_bytes", ctypes.c_size_t)]
+
+
 _lock = threading.Lock()
 _lib = None
 
@@ -69,6 +81,16 @@ _SIGS = {
     "dfd_matrix_capture": [_VP, _INT, _INT, _VP, _VP, _I64, _VP, _VP, ctypes.POINTER(_VP)],
     "dfd_graph_launch": [_VP, _VP],
     "dfd_graph_destroy": [_VP],
+    "dfd_server_options_default": [ctypes.POINTER(ServerOptions)],
+    "dfd_server_create": [_VP, ctypes.POINTER(ServerOptions), ctypes.POINTER(_VP)],
+    "dfd_server_destroy": [_VP],
+    "dfd_server_add_candidates": [_VP, _INT, _VP, _VP, _I64, ctypes.POINTER(_I64)],
+    "dfd_server_submit": [_VP, _INT, _VP, _I64, _VP, _I64, _VP, ctypes.c_double, ctypes.POINTER(ctypes.c_uint64)],
+    "dfd_server_wait": [_VP, ctypes.c_uint64, ctypes.c_double],
+    "dfd_server_cancel": [_VP, ctypes.c_uint64],
+    "dfd_server_stats": [_VP, ctypes.POINTER(ServingStats)],
+    "dfd_server_stats_reset": [_VP],
+    "dfd_server_now": [_VP],
     "dfd_timing_enable": [_VP, _INT],
     "dfd_timing_last": [_VP, ctypes.POINTER(ctypes.c_double)],
     "dfd_microbench": [_VP, _INT, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)],
@@ -78,7 +100,7 @@ MICRO_OPS = {"ffma": 0, "ffma2": 1, "fmnmx": 2, "fmnmx3": 3, "imnmx": 4, "imnmx6
              "shfl": 7, "cell_f32_d3": 8, "cell_i32_d2": 9, "distonly_f32_d3": 10,
              "lat_fmnmx": 11, "lat_cell": 12, "lat_shfl": 13, "lat_ffma2": 14, "lat_mnmx64": 15,
              "cell_f32_d16": 16}
-_RESTYPE = {"dfd_status_string": ctypes.c_char_p}
+_RESTYPE = {"dfd_status_string": ctypes.c_char_p, "dfd_server_now": ctypes.c_double}
 
 
 def declared_symbols():
@@ -240,6 +262,125 @@ def _curve(t):
     if t.dim() != 2:
         raise ValueError("a curve is an [n, dim] tensor")
     return t.contiguous()
+
+
+def dfd_server_create(ctx, opt: ServerOptions) -> int:
+    h = _VP()
+    _check(load_library().dfd_server_create(ctx, ctypes.byref(opt), ctypes.byref(h)), "dfd_server_create")
+    return h.value
+
+
+def dfd_server_options_default() -> ServerOptions:
+    o = ServerOptions()
+    _check(load_library().dfd_server_options_default(ctypes.byref(o)), "dfd_server_options_default")
+    return o
+
+
+def dfd_server_destroy(server) -> int:
+    return load_library().dfd_server_destroy(server)
+
+
+def dfd_server_add_candidates(server, dim, points, offsets, n_curves) -> int:
+    first = _I64()
+    _check(load_library().dfd_server_add_candidates(server, dim, points, offsets, n_curves, ctypes.byref(first)),
+           "dfd_server_add_candidates")
+    return first.value
+
+
+def dfd_server_submit(server, dim, query, n, cand_ids, k, out, arrival_s=-1.0) -> int:
+    t = ctypes.c_uint64()
+    _check(load_library().dfd_server_submit(server, dim, query, n, cand_ids, k, out, float(arrival_s),
+                                            ctypes.byref(t)), "dfd_server_submit")
+    return t.value
+
+
+def dfd_server_wait(server, ticket, timeout_ms=-1.0) -> int:
+    return load_library().dfd_server_wait(server, ticket, float(timeout_ms))
+
+
+def dfd_server_cancel(server, ticket) -> int:
+    return load_library().dfd_server_cancel(server, ticket)
+
+
+def dfd_server_stats(server) -> ServingStats:
+    st = ServingStats()
+    _check(load_library().dfd_server_stats(server, ctypes.byref(st)), "dfd_server_stats")
+    return st
+
+
+def dfd_server_stats_reset(server) -> int:
+    return load_library().dfd_server_stats_reset(server)
+
+
+def dfd_server_now(server) -> float:
+    return load_library().dfd_server_now(server)
+
+
+class Server:
+    """Continuous-batching search server (query vs resident candidates)."""
+
+    def __init__(self, ctx: "Context", mem_budget_bytes: int = 1 << 30, max_slots: int = 256,
+                 tick_cells: float = 2e9, stripes_per_tick: int = 4):
+        opt = dfd_server_options_default()
+        opt.mem_budget_bytes = int(mem_budget_bytes)
+        opt.max_slots = int(max_slots)
+        opt.tick_cells = float(tick_cells)
+        opt.stripes_per_tick = int(stripes_per_tick)
+        self.ctx = ctx
+        self.handle = dfd_server_create(ctx.handle, opt)
+        self._keep = {}
+
+    def add_candidates(self, points, offsets) -> int:
+        import numpy as np
+        points = np.ascontiguousarray(points, np.float32)
+        offsets = np.ascontiguousarray(offsets, np.int64)
+        return dfd_server_add_candidates(self.handle, points.shape[1], points.ctypes.data, offsets.ctypes.data,
+                                         offsets.shape[0] - 1)
+
+    def submit(self, query, cand_ids, out=None, arrival_s=-1.0) -> int:
+        import numpy as np
+        query = np.ascontiguousarray(query, np.float32)
+        if query.ndim == 1:
+            query = query[:, None]
+        cand_ids = np.ascontiguousarray(cand_ids, np.int64)
+        if out is None:
+            out = np.zeros(cand_ids.shape[0], np.float32)
+        t = dfd_server_submit(self.handle, query.shape[1], query.ctypes.data, query.shape[0], cand_ids.ctypes.data,
+                              cand_ids.shape[0], out.ctypes.data, arrival_s)
+        self._keep[t] = out
+        return t
+
+    def wait(self, ticket, timeout_ms=-1.0):
+        """(status, out array); the out array is final when status is 0."""
+        st = dfd_server_wait(self.handle, ticket, timeout_ms)
+        out = self._keep.get(ticket)
+        if st != STATUS_CODE["DFD_ERR_NOT_READY"]:
+            self._keep.pop(ticket, None)
+        return st, out
+
+    def cancel(self, ticket) -> int:
+        return dfd_server_cancel(self.handle, ticket)
+
+    def stats(self) -> dict:
+        s = dfd_server_stats(self.handle)
+        return {f: getattr(s, f) for f, _ in ServingStats._fields_}
+
+    def reset_stats(self):
+        dfd_server_stats_reset(self.handle)
+
+    def now(self) -> float:
+        return dfd_server_now(self.handle)
+
+    def close(self):
+        if self.handle:
+            dfd_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Graph:

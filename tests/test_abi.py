@@ -15,7 +15,7 @@ def declared_in_headers():
     for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
         src = open(h).read()
         src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-        names |= set(re.findall(r"^\s*(?:dfd_status|const char\s*\*)\s+(dfd_\w+)\s*\(", src, flags=re.M))
+        names |= set(re.findall(r"^\s*(?:dfd_status|const char\s*\*|double)\s+(dfd_\w+)\s*\(", src, flags=re.M))
     return names
 
 
