@@ -260,8 +260,9 @@ class Batch(_Many):
     launches_per_step = 5          # input check, 3 plan kernels, persistent batch kernel
 
     def __init__(self, args, ctx, dfd, torch, workloads, rank, world):
+        from paper_2404_05708_gb300 import shard
         b = workloads.ragged_int_batch()
-        pairs = b.pairs[rank::world].copy()
+        pairs = b.pairs[shard.shard_pairs(b.lengths(), b.pairs, rank, world)].copy()
         self.b, self.pairs_np = b, pairs
         self.ctx, self.torch = ctx, torch
         ln = b.lengths()
