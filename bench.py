@@ -71,6 +71,7 @@ def parse():
     ap.add_argument("--n", type=int, default=N_POINTS)
     ap.add_argument("--m", type=int, default=N_POINTS)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
     return ap.parse_args()
 
 
@@ -147,10 +148,16 @@ class LongPair:
         self.d = torch.empty(1, dtype=torch.float32, device="cuda")
         self.d2 = torch.empty(1, dtype=torch.float32, device="cuda")
         self.cells = self.n * self.m
-        shape = ctx.plan(0, DIM, self.n, self.m)
+        if getattr(args, "no_autotune", False):
+            shape, tuned = ctx.plan(0, DIM, self.n, self.m), False
+        else:
+            # Untimed setup: time each candidate launch shape once, keep the fastest.
+            shape, tuned = ctx.autotune(self.p, self.q), True
+            torch.cuda.synchronize()
         self.config = {"workload": f"long pair {self.n}x{self.m}, {DIM}-D float32 warped random walk (seed {SEED})",
                        "n": self.n, "m": self.m, "dim": DIM, "cells_per_step": self.cells,
-                       "launch_shape": {"rows_per_lane": shape[0], "warps": shape[1], "ctas": shape[2]},
+                       "launch_shape": {"rows_per_lane": shape[0], "warps": shape[1], "ctas": shape[2],
+                                        "autotuned": tuned},
                        "kernel_sha": kernel_sha()}
         self.h2d = (self.n + self.m) * DIM * 4
         self.d2h = 16

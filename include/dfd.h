@@ -291,6 +291,21 @@ dfd_status dfd_pair_shaped(dfd_context* ctx, dfd_dtype dtype, int dim, const voi
 dfd_status dfd_pair_noalloc(int device, dfd_dtype dtype, int dim, const void* p, int64_t n, const void* q,
                             int64_t m, void* out_dist, void* out_dist2, void* stream);
 
+/*
+ * Autotuner of the band wavefront (no counterpart in the paper): runs
+ * dfd_pair on (p, q) once per candidate launch shape (rows per lane 4, 6,
+ * 8 x compute warps 2..10, at most two waves of bands), times each with CUDA
+ * events on `stream`, and records the fastest for the size class of
+ * (dtype, dim, n, m) in the context; later dfd_pair calls of that class use
+ * it.  Synchronous; *best (may be NULL) receives the chosen shape.
+ * dfd_autotune_save / _load write / read the context's table as text lines
+ * "key rows_per_lane warps ctas".
+ */
+dfd_status dfd_pair_autotune(dfd_context* ctx, dfd_dtype dtype, int dim, const void* p, int64_t n, const void* q,
+                             int64_t m, void* stream, dfd_wave_shape* best);
+dfd_status dfd_autotune_save(dfd_context* ctx, const char* path);
+dfd_status dfd_autotune_load(dfd_context* ctx, const char* path);
+
 /* The launch shape dfd_pair would choose for (dtype, dim, n, m). */
 dfd_status dfd_pair_plan(dfd_context* ctx, dfd_dtype dtype, int dim, int64_t n, int64_t m, dfd_wave_shape* shape);
 

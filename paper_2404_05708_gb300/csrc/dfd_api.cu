@@ -1,6 +1,7 @@
 // dfd_api.cu -- the C ABI (dfd.h): contexts, argument checks, dispatch.
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <new>
 
@@ -141,7 +142,11 @@ dfd_status wave_plan(const dfd_context* ctx, dfd_dtype dtype, int dim, int64_t n
   // sweeps m columns; bands start one inter-band lag apart; an SM reaches
   // its issue limit once W*R >= RSAT (enough independent rows to hide the
   // per-row min/max latency).  Minimise the modelled completion time.
-  (void)dim;
+  auto hit = ctx->tuned.find(tune_key(dtype, dim_class(dim), n, m));
+  if (hit != ctx->tuned.end()) {
+    *shape = hit->second;
+    return DFD_OK;
+  }
   const double RSAT = 48.0;
   const int P = std::max(ctx->num_sms, 1);
   double best = 1e300;
@@ -406,6 +411,91 @@ dfd_status dfd_timing_last(dfd_context* ctx, double* ms) {
     return DFD_ERR_CUDA;
   }
   *ms = f;
+  return DFD_OK;
+}
+
+dfd_status dfd_pair_autotune(dfd_context* ctx, dfd_dtype dtype, int dim, const void* p, int64_t n, const void* q,
+                             int64_t m, void* stream, dfd_wave_shape* best_out) {
+  dfd_status st = check_pair_args(ctx, dtype, dim, p, n, q, m, p, nullptr);
+  if (st != DFD_OK) return st;
+  if ((st = set_device(ctx)) != DFD_OK) return st;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  // Candidates: rows per lane {4, 6, 8} x compute warps 2..10, keeping those
+  // whose band count is at most two waves of the SMs.
+  void* res = nullptr;
+  if (cudaMallocAsync(&res, 16, s) != cudaSuccess) {
+    cudaGetLastError();
+    return DFD_ERR_OOM;
+  }
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  WaveShape best;
+  wave_plan(ctx, dtype, dim, n, m, &best);
+  float best_ms = 1e30f;
+  const int Rs[3] = {4, 6, 8};
+  for (int R : Rs) {
+    for (int W = 2; W <= 10; ++W) {
+      if (!shape_ok(ctx, dtype, dim, R, W)) continue;
+      const int64_t H = (int64_t)32 * W * R;
+      const int64_t B = (n + H - 1) / H;
+      if (B > 2 * (int64_t)ctx->num_sms || (B < ctx->num_sms / 2 && W > 2)) continue;
+      WaveShape sh;
+      sh.R = R;
+      sh.W = W;
+      sh.ctas = 0;
+      cudaEventRecord(e0, s);
+      st = wave_run(ctx, dtype, dim, p, n, q, m, res, nullptr, s, sh);
+      cudaEventRecord(e1, s);
+      if (st != DFD_OK) continue;
+      if (cudaEventSynchronize(e1) != cudaSuccess) {
+        cudaGetLastError();
+        continue;
+      }
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < best_ms) {
+        best_ms = ms;
+        best = sh;
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFreeAsync(res, s);
+  cudaStreamSynchronize(s);
+  ctx->tuned[tune_key(dtype, dim_class(dim), n, m)] = best;
+  if (best_out) {
+    best_out->rows_per_lane = best.R;
+    best_out->warps = best.W;
+    best_out->ctas = best.ctas;
+  }
+  return DFD_OK;
+}
+
+dfd_status dfd_autotune_save(dfd_context* ctx, const char* path) {
+  if (!ctx || !path) return DFD_ERR_INVALID_ARG;
+  FILE* f = std::fopen(path, "w");
+  if (!f) return DFD_ERR_INVALID_ARG;
+  std::fprintf(f, "# dfd wavefront tuning: key rows_per_lane warps ctas\n");
+  for (const auto& kv : ctx->tuned)
+    std::fprintf(f, "%llu %d %d %d\n", (unsigned long long)kv.first, kv.second.R, kv.second.W, kv.second.ctas);
+  std::fclose(f);
+  return DFD_OK;
+}
+
+dfd_status dfd_autotune_load(dfd_context* ctx, const char* path) {
+  if (!ctx || !path) return DFD_ERR_INVALID_ARG;
+  FILE* f = std::fopen(path, "r");
+  if (!f) return DFD_ERR_INVALID_ARG;
+  char line[256];
+  while (std::fgets(line, sizeof line, f)) {
+    if (line[0] == '#') continue;
+    unsigned long long key = 0;
+    WaveShape sh;
+    if (std::sscanf(line, "%llu %d %d %d", &key, &sh.R, &sh.W, &sh.ctas) == 4) ctx->tuned[(uint64_t)key] = sh;
+  }
+  std::fclose(f);
   return DFD_OK;
 }
 

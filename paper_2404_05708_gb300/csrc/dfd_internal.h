@@ -2,10 +2,26 @@
 #pragma once
 #include <cstddef>
 #include <cstdint>
+#include <map>
 #include <mutex>
 #include <cuda_runtime.h>
 
 #include "dfd.h"
+
+namespace dfd {
+// Launch shape of the band wavefront (K2).
+struct WaveShape {
+  int R = 4;      // rows per lane
+  int W = 4;      // compute warps per CTA
+  int ctas = 0;   // persistent CTAs (0 = auto)
+};
+// Autotuning key: dtype, dimension class and the size classes of n and m
+// (floor(log2)), packed in 64 bits.
+inline uint64_t tune_key(int dtype, int dk, int64_t n, int64_t m) {
+  auto lg = [](int64_t x) { int b = 0; while (x > 1) { x >>= 1; ++b; } return b; };
+  return ((uint64_t)dtype << 48) | ((uint64_t)dk << 40) | ((uint64_t)lg(n) << 20) | (uint64_t)lg(m);
+}
+}  // namespace dfd
 
 struct dfd_context {
   int device = 0;
@@ -21,6 +37,7 @@ struct dfd_context {
   bool timing = false;                // record events around the main kernel
   bool timed = false;                 // ev0/ev1 hold a recorded pair
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  std::map<uint64_t, dfd::WaveShape> tuned;   // autotuned wavefront shapes
 };
 
 namespace dfd {
@@ -70,11 +87,6 @@ dfd_status launch_check_inputs(dfd_dtype dtype, int dim, const void* x, int64_t 
                                cudaStream_t s);
 
 // Band wavefront (K2).
-struct WaveShape {
-  int R = 4;      // rows per lane
-  int W = 4;      // compute warps per CTA
-  int ctas = 0;   // persistent CTAs (0 = auto)
-};
 dfd_status wave_plan(const dfd_context* ctx, dfd_dtype dtype, int dim, int64_t n, int64_t m, WaveShape* shape);
 dfd_status wave_run(dfd_context* ctx, dfd_dtype dtype, int dim, const void* p, int64_t n, const void* q,
                     int64_t m, void* out_dist, void* out_dist2, cudaStream_t s, const WaveShape& shape);

@@ -280,11 +280,57 @@ __device__ __forceinline__ void compute_stripe(const Args& a, int w, int64_t ban
     __syncwarp();
     if (ld_volatile_smem(&ctl->abort)) break;
 
+    auto qaddr = [&](int cq) {
+      const unsigned slot = (gbase + (unsigned)(cq >> LOGC)) & (NQ - 1);
+      return qring + (size_t)slot * NPL * C + (cq & (C - 1));
+    };
+    if constexpr (sizeof(T) == 4) {
+      // Each warp issues in order, so whatever waits on the previous step's
+      // chain blocks every later instruction.  Per step only one instruction
+      // does (the shuffle of the bottom value): lane 0's 32 ring inputs are
+      // loaded into registers at block start (broadcast), the next step's q
+      // point and distances are computed ahead of this step's chain, and
+      // lane 31's output is a predicated store that nothing waits on.
+      T rv[G];
+#pragma unroll
+      for (int k = 0; k < G; k += 4) {
+        const float4 t4 = *reinterpret_cast<const float4*>(ring_in + ((c0 + k) & (RING - 1)));
+        rv[k] = t4.x;
+        rv[k + 1] = t4.y;
+        rv[k + 2] = t4.z;
+        rv[k + 3] = t4.w;
+      }
+      T dcur[R];
+      rows.dist(qaddr(max(c0 - L, 0)), C, dcur);
+#pragma unroll
+      for (int s = 0; s < G; ++s) {
+        const int col = c0 + s - L;
+        T dnext[R];
+        if (s + 1 < G) rows.dist(qaddr(max(col + 1, 0)), C, dnext);
+        T u = __shfl_up_sync(0xffffffffu, bout, 1);
+        u = (L == 0) ? rv[s] : u;
+        T up = u, dg = upp;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          const T l = v[r];
+          const T nv = V::vmax(V::vmin3(l, dg, up), dcur[r]);
+          dg = l;
+          v[r] = nv;
+          up = nv;
+        }
+        upp = u;
+        bout = up;
+        st_shared_if(ring_out + (col & (RING - 1)), bout, L == 31 && col >= 0);
+        if (s + 1 < G) {
+#pragma unroll
+          for (int r = 0; r < R; ++r) dcur[r] = dnext[r];
+        }
+      }
+    } else {
     // The block's 32 ring inputs, one per lane (lane s holds column c0 + s);
     // at step s lane 0 takes lane s's value.  Lane 31's outputs are gathered
     // the same way (lane s keeps step s's) and stored after the block, so
-    // the unrolled block has no shared-memory store and no branch: later
-    // steps' q loads and distances can be scheduled under earlier chains.
+    // the unrolled block has no shared-memory store and no branch.
     const T in_blk = ring_in[(c0 + L) & (RING - 1)];
     T out_blk = V::inf();
 #pragma unroll
@@ -293,11 +339,8 @@ __device__ __forceinline__ void compute_stripe(const Args& a, int w, int64_t ban
       const T rin = __shfl_sync(0xffffffffu, in_blk, s);
       T u = __shfl_up_sync(0xffffffffu, bout, 1);
       u = (L == 0) ? rin : u;
-      const int cq = max(col, 0);
-      const unsigned slot = (gbase + (unsigned)(cq >> LOGC)) & (NQ - 1);
-      const Rec* qp = qring + (size_t)slot * NPL * C + (cq & (C - 1));
       T d[R];
-      rows.dist(qp, C, d);
+      rows.dist(qaddr(max(col, 0)), C, d);
       T up = u, dg = upp;
 #pragma unroll
       for (int r = 0; r < R; ++r) {
@@ -315,6 +358,7 @@ __device__ __forceinline__ void compute_stripe(const Args& a, int w, int64_t ban
     {
       const int oc = c0 + L - 31;   // column lane 31 produced at step L
       st_shared_if(ring_out + (oc & (RING - 1)), out_blk, oc >= 0);
+    }
     }
     __syncwarp();
     if (L == 31) st_release_cta(&ctl->prod[w + 1], c0 + G - 31);
@@ -366,7 +410,7 @@ __device__ __forceinline__ void comm_warp(const Args& a, int64_t band, unsigned 
     if (issued < a.nch) {
       const unsigned seq = gbase + (unsigned)issued;
       const unsigned slot = seq & (NQ - 1);
-      const bool slot_free = seq < (unsigned)NQ || mbar_try_wait(&empty[slot], ((seq / NQ) - 1) & 1);
+      const bool slot_free = seq < (unsigned)NQ || mbar_test_wait(&empty[slot], ((seq / NQ) - 1) & 1);
       if (slot_free) {
         if (L == 0) {
           mbar_arrive_expect_tx(&full[slot], CHUNK_BYTES);

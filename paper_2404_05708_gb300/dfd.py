@@ -73,6 +73,9 @@ _SIGS = {
     "dfd_pair_host": [_VP, _INT, _INT, _VP, _I64, _VP, _I64, _VP, _VP],
     "dfd_pair_shaped": [_VP, _INT, _INT, _VP, _I64, _VP, _I64, _VP, _VP, _VP, ctypes.POINTER(WaveShape)],
     "dfd_pair_plan": [_VP, _INT, _INT, _I64, _I64, ctypes.POINTER(WaveShape)],
+    "dfd_pair_autotune": [_VP, _INT, _INT, _VP, _I64, _VP, _I64, _VP, ctypes.POINTER(WaveShape)],
+    "dfd_autotune_save": [_VP, ctypes.c_char_p],
+    "dfd_autotune_load": [_VP, ctypes.c_char_p],
     "dfd_debug_bounded_wait": [_VP, ctypes.c_double],
     "dfd_pair_noalloc": [_INT, _INT, _INT, _VP, _I64, _VP, _I64, _VP, _VP, _VP],
     "dfd_batch": [_VP, _INT, _INT, _VP, _VP, _I64, _VP, _I64, _VP, _VP, _VP],
@@ -238,6 +241,21 @@ def dfd_pair_plan(ctx, dtype, dim, n, m) -> WaveShape:
     s = WaveShape()
     _check(load_library().dfd_pair_plan(ctx, dtype, dim, n, m, ctypes.byref(s)), "dfd_pair_plan")
     return s
+
+
+def dfd_pair_autotune(ctx, dtype, dim, p, n, q, m, stream) -> WaveShape:
+    s = WaveShape()
+    _check(load_library().dfd_pair_autotune(ctx, dtype, dim, p, n, q, m, stream, ctypes.byref(s)),
+           "dfd_pair_autotune")
+    return s
+
+
+def dfd_autotune_save(ctx, path: str) -> int:
+    return load_library().dfd_autotune_save(ctx, str(path).encode())
+
+
+def dfd_autotune_load(ctx, path: str) -> int:
+    return load_library().dfd_autotune_load(ctx, str(path).encode())
 
 
 # -------------------------------------------------------- torch convenience
@@ -538,3 +556,21 @@ class Context:
     def plan(self, dtype: int, dim: int, n: int, m: int):
         s = dfd_pair_plan(self.handle, dtype, dim, n, m)
         return s.rows_per_lane, s.warps, s.ctas
+
+    def autotune(self, p, q, stream=None):
+        """Time every candidate wavefront shape on device curves (p, q) and
+        keep the fastest for their size class; returns (rows_per_lane, warps, ctas)."""
+        torch = _torch()
+        p, q = _curve(p), _curve(q)
+        dt = _dtype_code(p)
+        if _dtype_code(q) != dt or p.shape[1] != q.shape[1]:
+            raise ValueError("p and q must share dtype and dim")
+        st = stream if stream is not None else torch.cuda.current_stream(self.device).cuda_stream
+        s = dfd_pair_autotune(self.handle, dt, p.shape[1], p.data_ptr(), p.shape[0], q.data_ptr(), q.shape[0], st)
+        return s.rows_per_lane, s.warps, s.ctas
+
+    def save_tuning(self, path):
+        _check(dfd_autotune_save(self.handle, path), "dfd_autotune_save")
+
+    def load_tuning(self, path):
+        _check(dfd_autotune_load(self.handle, path), "dfd_autotune_load")

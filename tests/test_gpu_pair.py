@@ -144,6 +144,33 @@ def test_explicit_wave_shapes(dctx, R):
             assert run(dctx, pi, qi, shape=(R, W, ctas))[1] == want_i, (R, W, ctas)
 
 
+def test_autotune_picks_a_valid_shape_and_round_trips(tmp_path):
+    """The autotuner records a shape for the size class; dfd_pair then uses
+    it (same plan reported) and results stay equal to the oracle; the table
+    survives save / load into a fresh context."""
+    from paper_2404_05708_gb300 import dfd
+    rng = np.random.default_rng(77)
+    p, q = f32_walk(rng, 20000, 3), f32_walk(rng, 17000, 3)
+    ctx = dfd.Context(0)
+    try:
+        shape = ctx.autotune(dev(p), dev(q))
+        torch.cuda.synchronize()
+        R, W, ctas = shape
+        assert R in (4, 6, 8) and 2 <= W <= 10, shape
+        assert ctx.plan(dfd.DFD_F32, 3, 20000, 17000) == shape
+        check_f32(ctx, p, q)
+        path = tmp_path / "tune.txt"
+        ctx.save_tuning(path)
+        ctx2 = dfd.Context(0)
+        try:
+            ctx2.load_tuning(path)
+            assert ctx2.plan(dfd.DFD_F32, 3, 20000, 17000) == shape
+        finally:
+            ctx2.close()
+    finally:
+        ctx.close()
+
+
 def test_reference_kernel_matches_oracle_int(dctx):
     rng = np.random.default_rng(50)
     for n, m in [(1, 1), (1, 700), (700, 1), (257, 513), (1200, 900)]:
