@@ -72,6 +72,8 @@ def parse():
     ap.add_argument("--m", type=int, default=N_POINTS)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--shape", default="", help="long pair: fixed launch shape R,W,ctas (no autotune)")
+    ap.add_argument("--pairs", type=int, default=0, help="batch: number of pairs (default 65,536)")
     return ap.parse_args()
 
 
@@ -148,7 +150,10 @@ class LongPair:
         self.d = torch.empty(1, dtype=torch.float32, device="cuda")
         self.d2 = torch.empty(1, dtype=torch.float32, device="cuda")
         self.cells = self.n * self.m
-        if getattr(args, "no_autotune", False):
+        if args.shape:
+            shape, tuned = tuple(int(x) for x in args.shape.split(",")), False
+            self.shape = shape
+        elif getattr(args, "no_autotune", False):
             shape, tuned = ctx.plan(0, DIM, self.n, self.m), False
         else:
             # Untimed setup: time each candidate launch shape once, keep the fastest.
@@ -162,8 +167,10 @@ class LongPair:
         self.h2d = (self.n + self.m) * DIM * 4
         self.d2h = 16
 
+    shape = None
+
     def step(self):
-        self.ctx.pair(self.p, self.q, self.d, self.d2)
+        self.ctx.pair(self.p, self.q, self.d, self.d2, shape=self.shape)
 
     def e2e_step(self):
         return self.ctx.pair_host(self.p_np, self.q_np)
@@ -268,7 +275,7 @@ class Batch(_Many):
 
     def __init__(self, args, ctx, dfd, torch, workloads, rank, world):
         from paper_2404_05708_gb300 import shard
-        b = workloads.ragged_int_batch()
+        b = workloads.ragged_int_batch(n_pairs=args.pairs) if args.pairs else workloads.ragged_int_batch()
         pairs = b.pairs[shard.shard_pairs(b.lengths(), b.pairs, rank, world)].copy()
         self.b, self.pairs_np = b, pairs
         self.ctx, self.torch = ctx, torch
@@ -280,7 +287,7 @@ class Batch(_Many):
         self.pairs = torch.from_numpy(pairs).cuda()
         self.graph, self.out, self.out2 = ctx.batch(self.pts_dev, self.off, self.pairs, capture=True)
         self.out_host = torch.empty_like(self.out2, device="cpu").pin_memory()
-        self.config = {"workload": "ragged batch, 65,536 pairs of int32 2-D random walks, lengths U{16..512} "
+        self.config = {"workload": f"ragged batch, {b.pairs.shape[0]:,} pairs of int32 2-D random walks, lengths U{{16..512}} "
                                    "(seed 4), one persistent launch per step in a captured CUDA graph",
                        "n_pairs": int(pairs.shape[0]), "dim": 2, "cells_per_step": self.cells,
                        "kernel_sha": kernel_sha(("batch_kernel.cuh", "batch_launch.cuh", "dfd_device.cuh"))}

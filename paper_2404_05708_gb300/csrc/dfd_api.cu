@@ -7,6 +7,7 @@
 
 #include "dfd_device.cuh"
 #include "dfd_internal.h"
+#include "wave_shape.h"
 
 namespace dfd {
 
@@ -126,28 +127,26 @@ dfd_status launch_check_inputs(dfd_dtype dtype, int dim, const void* x, int64_t 
 
 // ------------------------------------------------------------- wave plans
 static bool shape_ok(const dfd_context* ctx, dfd_dtype dtype, int dim, int R, int W) {
-  // q chunks are 128 columns for dim <= 4 and 64 beyond; the q ring bounds
-  // how far the last warp may trail warp 0 (see wave::max_warps).
-  const int C = dim_class(dim) <= 4 ? 128 : 64;
-  const int wmax = ((16 - 1) * C - 31) / 64 + 1;
-  if (W < 1 || W > 16 || W > wmax) return false;
-  if (R != 2 && R != 4 && R != 6 && R != 8) return false;
+  // The q ring bounds how far the last warp may trail warp 0, the register
+  // file how many warps of R rows a CTA can hold (wave_shape.h).
   (void)ctx;
-  (void)dtype;
-  return true;
+  const int dk = dim_class(dim);
+  return dk > 0 && wave::shape_supported(dtype == DFD_F32, dk, R, W);
 }
 
 dfd_status wave_plan(const dfd_context* ctx, dfd_dtype dtype, int dim, int64_t n, int64_t m, WaveShape* shape) {
   // Cost model: every CTA runs one band at a time; a band of H = 32*W*R rows
-  // sweeps m columns; bands start one inter-band lag apart; an SM reaches
-  // its issue limit once W*R >= RSAT (enough independent rows to hide the
-  // per-row min/max latency).  Minimise the modelled completion time.
+  // sweeps m columns plus its internal skew; bands start one inter-band lag
+  // apart (W warps, each trailing the one above by 32*K + G columns); an SM
+  // reaches its issue limit once W*R >= RSAT rows (enough independent cells
+  // to hide the min/max latency; fewer with skewed float32 lanes, whose
+  // step chain is two cells).  Minimise the modelled completion time.
   auto hit = ctx->tuned.find(tune_key(dtype, dim_class(dim), n, m));
   if (hit != ctx->tuned.end()) {
     *shape = hit->second;
     return DFD_OK;
   }
-  const double RSAT = 48.0;
+  const double RSAT = dtype == DFD_F32 ? 24.0 : 48.0;
   const int P = std::max(ctx->num_sms, 1);
   double best = 1e300;
   WaveShape bs;
@@ -158,9 +157,11 @@ dfd_status wave_plan(const dfd_context* ctx, dfd_dtype dtype, int dim, int64_t n
       const double H = 32.0 * W * R;
       const double B = std::ceil((double)n / H);
       const double waves = std::ceil(B / P);
-      const double lag = 64.0 * W + 96.0;
+      const double K = dtype == DFD_F32 ? R / 2 : 1;
+      const double wlag = 32.0 * K + 32.0;
+      const double lag = wlag * W + 96.0;
       const double conc = std::min(B, (double)P);
-      const double cols = waves * ((double)m + 64.0 * W) + (conc - 1.0) * lag;
+      const double cols = waves * ((double)m + wlag * W) + (conc - 1.0) * lag;
       const double sat = std::min(1.0, W * R / RSAT);
       const double t = cols * H / sat;
       if (t < best * 0.999) {

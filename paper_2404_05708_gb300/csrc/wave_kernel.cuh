@@ -24,25 +24,38 @@
 #pragma once
 #include <type_traits>
 #include "dfd_device.cuh"
+#include "wave_shape.h"
 
 namespace dfd {
 namespace wave {
 
-constexpr int G = 32;        // systolic steps between synchronisations
-constexpr int RING = 256;    // columns held by each inter-warp ring (power of 2)
-constexpr int NQ = 16;       // q chunk slots (power of 2)
-
 template <int DK>
 struct ChunkCols {
-  static constexpr int value = DK <= 4 ? 128 : 64;  // q columns per TMA chunk
+  static constexpr int value = chunk_cols(DK);
 };
 
-// With every ring saturated, warp w+1 trails warp w by two G-blocks, so the
-// last of W warps trails warp 0 by 2*G*(W-1) columns plus its 31-lane skew.
-// The q ring must hold that window, or warp 0 could wait for a slot that
-// only the last warp can free:  (NQ - 1) * C >= 2*G*(W-1) + 31.
-__host__ __device__ constexpr int max_warps(int C) {
-  return ((NQ - 1) * C - 31) / (2 * G) + 1;
+// Column skew between neighbouring lanes.  float32 lanes hold K = R/2 row
+// pairs and pair h runs h columns behind pair 0, so the K pairs of one step
+// are independent (the "up" of pair h is pair h-1's value from the step
+// before); lane L+1 runs K columns behind lane L.  int32 lanes keep all R
+// rows in one column (K = 1).
+template <class V, int R>
+struct Skew {
+  static constexpr int value = skew(std::is_same<V, F32>::value, R);
+};
+
+// Compute warps per CTA the register file allows (the kernel's launch bound).
+template <class V, int DK, int R>
+struct kMaxWarps {
+  static constexpr int value = max_warps_regs(std::is_same<V, F32>::value, DK, R);
+};
+
+// Position of column cc (0 <= cc < C) inside a packed q chunk plane: lanes
+// K columns apart read records K * 16 bytes apart, which for even K maps
+// several lanes to one bank group, so chunks are stored by column residue
+// mod TR = K ([cc mod TR][cc / TR]) for K in {2, 4} (TR = 1 otherwise).
+__host__ __device__ __forceinline__ int qpos(int cc, int TR, int C) {
+  return TR > 1 ? (cc & (TR - 1)) * (C / TR) + cc / TR : cc;
 }
 
 struct Args {
@@ -88,6 +101,26 @@ struct Rows<F32, DK, R> {
         pp[h][k] = pack2(a, b);
       }
     }
+  }
+
+  // Rows 2h, 2h+1 against one q point given as its NPL packed planes.
+  // (h must be a compile-time constant after unrolling.)
+  __device__ __forceinline__ void dist_pair(int h, const float4 (&t)[NPL], float& d0, float& d1) const {
+    unsigned long long qk[DK];
+#pragma unroll
+    for (int c = 0; c < NPL; ++c) {
+      qk[2 * c] = pack2(t[c].x, t[c].y);
+      if (2 * c + 1 < DK) qk[2 * c + 1] = pack2(t[c].z, t[c].w);
+    }
+    const unsigned long long u0 = sub2(pp[h][0], qk[0]);
+    unsigned long long acc = mul2(u0, u0);
+#pragma unroll
+    for (int k = 1; k < DK; ++k) {
+      const unsigned long long u = sub2(pp[h][k], qk[k]);
+      acc = fma2(u, u, acc);
+    }
+    d0 = lo2(acc);
+    d1 = hi2(acc);
   }
 
   __device__ __forceinline__ void dist(const Rec* qp, int plane_stride, float d[R]) const {
@@ -185,6 +218,16 @@ __device__ __forceinline__ void st_shared_if(long long* p, long long v, bool pre
       : "memory");
 }
 
+// Four-float variant (16-byte aligned address).  No "memory" clobber: the
+// ring it writes is published by a later st.release (asm volatile, kept in
+// order), and q / ring loads of later steps may be scheduled across it.
+__device__ __forceinline__ void st_shared_if4(float* p, float4 v, bool pred) {
+  asm volatile(
+      "{\n\t.reg .pred P;\n\tsetp.ne.u32 P, %5, 0;\n\t@P st.shared.v4.f32 [%0], {%1, %2, %3, %4};\n\t}" ::"r"(
+          smem_addr(p)),
+      "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w), "r"((unsigned)pred));
+}
+
 template <class T>
 __device__ __forceinline__ T ld_cg(const T* p) {
   return __ldcg(p);
@@ -231,7 +274,138 @@ struct Layout {
   static __host__ __device__ size_t bytes(int W) { return ctl_off(W) + sizeof(Ctl); }
 };
 
+// ----------------------------------------------------------- ring indexing
+// Inter-warp rings hold column c at index (c + 3) mod RING: lane 31 emits
+// column c0 + s - (32K - 1) at step s and 32K - 1 = 3 (mod 4), so the four
+// outputs of steps 4t..4t+3 land in one aligned 16-byte slot.
+__device__ __forceinline__ int ridx(int c) { return (c + 3) & (RING - 1); }
+
+// q ring: NQ chunks of C columns, plane-major ([plane][NQ*C] records); for
+// lane skew K in {2, 4} each plane is further split by column residue mod
+// TR = K ([plane][residue][NQ*C/TR]), so the 32 lanes of a step (K columns
+// apart) read 32 consecutive records.  x is the column's position in the
+// band-stream (chunk sequence * C + column), taken mod the ring size.
+template <class V, int R>
+struct QTrans {
+  static constexpr int value = (Skew<V, R>::value == 2 || Skew<V, R>::value == 4) ? Skew<V, R>::value : 1;
+};
+
 // ----------------------------------------------------------- compute warp
+// float32: one G-step block of the skewed systolic stripe.  At step s pair h
+// of lane L updates column c0 + s - K*L - h (rows 2h, 2h+1 of the lane):
+//   row 2h:   up = pair h-1's bottom value of the previous step, diag = that
+//             of the step before (lane L-1's bottom row by shuffle for h = 0,
+//             the ring above for lane 0), left = its own previous value;
+//   row 2h+1: up = row 2h of this step, diag / left = the previous values.
+// The K pairs of a step are independent, so the only chain a step carries
+// is two cells long.  Pair 0's q record is loaded two steps ahead and slides
+// to pair h after h steps in registers; the shuffle for the next step is
+// issued as soon as the bottom pair is done.
+template <int DK, int R>
+struct SkewState {
+  static constexpr int K = R / 2;
+  static constexpr int NPL = (DK + 1) / 2;
+  float v0[K], v1[K], pv1[K];   // rows 2h, 2h+1 now; row 2h+1 one step ago
+  float dcur[K][2];             // distances of the coming step
+  float4 win[K][NPL];           // win[j]: pair 0's record j steps ago (j < K-1 used)
+  float4 nrec1[NPL];            // pair 0's record of the coming step + 1
+  float upp;                    // lane's diagonal input
+  float ush;                    // lane L-1's bottom value, shuffled for the coming step
+};
+
+template <int DK, int R>
+__device__ __forceinline__ void skew_block(const Rows<F32, DK, R>& rows, SkewState<DK, R>& st, const float* ring_in,
+                                           float* ring_out, const float4* qring, unsigned xbase, int c0, int L) {
+  constexpr int K = R / 2;
+  constexpr int NPL = (DK + 1) / 2;
+  constexpr int C = ChunkCols<DK>::value;
+  constexpr int NQC = NQ * C;
+  constexpr int TR = (K == 2 || K == 4) ? K : 1;
+  constexpr int SK = 32 * K - 1;
+  // Lane 0's inputs from the ring above: columns c0..c0+31 at indices
+  // c0+3..c0+34 (9 aligned float4 loads, broadcast).
+  float rin[36];
+#pragma unroll
+  for (int k = 0; k < 36; k += 4) {
+    const float4 t4 = *reinterpret_cast<const float4*>(ring_in + ((c0 + k) & (RING - 1)));
+    rin[k] = t4.x;
+    rin[k + 1] = t4.y;
+    rin[k + 2] = t4.z;
+    rin[k + 3] = t4.w;
+  }
+  float u = (L == 0) ? rin[3] : st.ush;
+  // Stream position of pair 0's column at step 0 of this block; X = 0 mod TR.
+  const unsigned X = xbase + (unsigned)(c0 - K * L);
+  const unsigned Xq = X / TR;
+  float obuf[4];
+#pragma unroll
+  for (int s = 0; s < G; ++s) {
+    // (1) pair 0's record for step s + 2
+    float4 nrec2[NPL];
+    {
+      const int res = (s + 2) % TR;
+      const unsigned idx = (Xq + (unsigned)((s + 2) / TR)) & (unsigned)(NQC / TR - 1);
+      const float4* qp = qring + res * (NQC / TR) + idx;
+#pragma unroll
+      for (int c = 0; c < NPL; ++c) nrec2[c] = qp[c * NQC];
+    }
+    // (2) the bottom pair first, then the shuffle for step s + 1
+    float unext;
+    {
+      constexpr int h = K - 1;
+      const int hp = h > 0 ? h - 1 : 0;
+      const float up0 = h > 0 ? st.v1[hp] : u;
+      const float dg0 = h > 0 ? st.pv1[hp] : st.upp;
+      const float n0 = F32::vmax(F32::vmin3(st.v0[h], dg0, up0), st.dcur[h][0]);
+      const float n1 = F32::vmax(F32::vmin3(st.v1[h], st.v0[h], n0), st.dcur[h][1]);
+      st.pv1[h] = st.v1[h];
+      st.v0[h] = n0;
+      st.v1[h] = n1;
+      unext = __shfl_up_sync(0xffffffffu, n1, 1);
+      obuf[s & 3] = n1;
+    }
+    // (3) the other pairs (pair 0 takes the shuffled / ring value)
+#pragma unroll
+    for (int h = K - 2; h >= 0; --h) {
+      const int hp = h > 0 ? h - 1 : 0;
+      const float up0 = h > 0 ? st.v1[hp] : u;
+      const float dg0 = h > 0 ? st.pv1[hp] : st.upp;
+      const float n0 = F32::vmax(F32::vmin3(st.v0[h], dg0, up0), st.dcur[h][0]);
+      const float n1 = F32::vmax(F32::vmin3(st.v1[h], st.v0[h], n0), st.dcur[h][1]);
+      st.pv1[h] = st.v1[h];
+      st.v0[h] = n0;
+      st.v1[h] = n1;
+    }
+    st.upp = u;
+    // (4) distances of step s + 1
+    rows.dist_pair(0, st.nrec1, st.dcur[0][0], st.dcur[0][1]);
+#pragma unroll
+    for (int h = 1; h < K; ++h) rows.dist_pair(h, st.win[h - 1], st.dcur[h][0], st.dcur[h][1]);
+    // (5) lane 31's bottom values, four steps per store
+    if ((s & 3) == 3) {
+      const int c_last = c0 + s - SK;   // column of this step's output
+      st_shared_if4(ring_out + ridx(c_last - 3), make_float4(obuf[0], obuf[1], obuf[2], obuf[3]),
+                    L == 31 && c_last >= 0);
+    }
+    // (6) slide the records
+#pragma unroll
+    for (int j = K - 2; j > 0; --j) {
+#pragma unroll
+      for (int c = 0; c < NPL; ++c) st.win[j][c] = st.win[j - 1][c];
+    }
+#pragma unroll
+    for (int c = 0; c < NPL; ++c) {
+      st.win[0][c] = st.nrec1[c];
+      st.nrec1[c] = nrec2[c];
+    }
+    if (s + 1 < G) {
+      u = (L == 0) ? rin[s + 4] : unext;
+    } else {
+      st.ush = unext;
+    }
+  }
+}
+
 template <class V, int DK, int R>
 __device__ __forceinline__ void compute_stripe(const Args& a, int w, int64_t band, unsigned gbase,
                                                unsigned char* smem) {
@@ -240,7 +414,10 @@ __device__ __forceinline__ void compute_stripe(const Args& a, int w, int64_t ban
   using Rec = typename Lay::Rec;
   constexpr int C = Lay::C;
   constexpr int NPL = Lay::NPL;
-  constexpr int LOGC = C == 128 ? 7 : 6;
+  constexpr int NQC = NQ * C;
+  constexpr int K = Skew<V, R>::value;
+  constexpr int SK = 32 * K - 1;
+  constexpr bool kSkew = std::is_same<V, F32>::value;
   const int L = threadIdx.x & 31;
   const int W = (int)(blockDim.x >> 5) - 1;
   const Rec* qring = reinterpret_cast<const Rec*>(smem);
@@ -257,114 +434,131 @@ __device__ __forceinline__ void compute_stripe(const Args& a, int w, int64_t ban
   const int64_t rend = min(rb0 + a.H, a.n);
   rows.load(static_cast<const Coord*>(a.p), rb0 + (int64_t)(w * 32 + L) * R, rend - 1, a.dim);
 
+  const bool corner = band == 0 && w == 0 && L == 0;
+  const unsigned xbase = gbase * (unsigned)C;   // stream position of the band's column 0
+  // int32 state: R rows in one column.
   T v[R];
 #pragma unroll
   for (int r = 0; r < R; ++r) v[r] = V::inf();
   T bout = V::inf();
-  T upp = (band == 0 && w == 0 && L == 0) ? V::zero() : V::inf();
+  T upp = corner ? V::zero() : V::inf();
+  // float32 state: skewed pairs.
+  using SS = SkewState<DK, (kSkew ? R : 2)>;
+  SS ss;
+  if constexpr (kSkew) {
+#pragma unroll
+    for (int h = 0; h < SS::K; ++h) ss.v0[h] = ss.v1[h] = ss.pv1[h] = V::inf();
+    ss.upp = corner ? 0.f : V::inf();
+    ss.ush = V::inf();
+  }
   const int m = (int)a.m;
-  int qdone = 0;
+  int qdone = 0, qready = 0;
 
   for (int blk = 0; blk < a.nblk; ++blk) {
     const int c0 = blk * G;
-    bool ok = true;
-    if (L == 0) ok = spin_smem_geq(&ctl->prod[w], min(c0 + G, m), ctl, a.err, a.timeout_ns);
-    if (L == 31) ok = spin_smem_geq(&ctl->cons[w + 1], c0 + G - 31 - RING, ctl, a.err, a.timeout_ns);
-    if ((c0 & (C - 1)) == 0) {
-      const unsigned seq = gbase + (unsigned)(c0 >> LOGC);
-      if (!mbar_wait(&full[seq & (NQ - 1)], (seq / NQ) & 1, a.err, a.timeout_ns)) {
-        *reinterpret_cast<volatile int*>(&ctl->abort) = 1;
+    // One uniform check of both ring counters and the abort flag; spin
+    // (bounded) only when one of them is not there yet.
+    const int need_in = min(c0 + G, m);
+    const int need_out = c0 + G - SK - RING;
+    {
+      const int pv = ld_acquire_cta(&ctl->prod[w]);
+      const int cv = ld_acquire_cta(&ctl->cons[w + 1]);
+      const int ab = ld_volatile_smem(&ctl->abort);
+      if (pv < need_in || cv < need_out || ab) {
+        if (L == 0) spin_smem_geq(&ctl->prod[w], need_in, ctl, a.err, a.timeout_ns);
+        if (L == 31) spin_smem_geq(&ctl->cons[w + 1], need_out, ctl, a.err, a.timeout_ns);
+        __syncwarp();
+        if (ld_volatile_smem(&ctl->abort)) break;
       }
     }
-    (void)ok;
-    __syncwarp();
-    if (ld_volatile_smem(&ctl->abort)) break;
-
-    auto qaddr = [&](int cq) {
-      const unsigned slot = (gbase + (unsigned)(cq >> LOGC)) & (NQ - 1);
-      return qring + (size_t)slot * NPL * C + (cq & (C - 1));
-    };
-    if constexpr (sizeof(T) == 4) {
-      // Each warp issues in order, so whatever waits on the previous step's
-      // chain blocks every later instruction.  Per step only one instruction
-      // does (the shuffle of the bottom value): lane 0's 32 ring inputs are
-      // loaded into registers at block start (broadcast), the next step's q
-      // point and distances are computed ahead of this step's chain, and
-      // lane 31's output is a predicated store that nothing waits on.
-      T rv[G];
-#pragma unroll
-      for (int k = 0; k < G; k += 4) {
-        const float4 t4 = *reinterpret_cast<const float4*>(ring_in + ((c0 + k) & (RING - 1)));
-        rv[k] = t4.x;
-        rv[k + 1] = t4.y;
-        rv[k + 2] = t4.z;
-        rv[k + 3] = t4.w;
+    // q chunks through the one holding column c0 + G + 1 (the last steps'
+    // look-ahead reads it).
+    const int qneed = min((c0 + G + 1) / C + 1, a.nch);
+    if (qready < qneed) {
+      bool qok = true;
+      while (qready < qneed) {
+        const unsigned seq = gbase + (unsigned)qready;
+        if (!mbar_wait(&full[seq & (NQ - 1)], (seq / NQ) & 1, a.err, a.timeout_ns)) {
+          *reinterpret_cast<volatile int*>(&ctl->abort) = 1;
+          qok = false;
+          break;
+        }
+        ++qready;
       }
-      T dcur[R];
-      rows.dist(qaddr(max(c0 - L, 0)), C, dcur);
+      if (!qok) break;
+    }
+
+    if constexpr (kSkew) {
+      const float4* qr = reinterpret_cast<const float4*>(qring);
+      if (blk == 0) {
+        // Step 0 and step 1 records of pair 0 (columns -K*L and 1 - K*L;
+        // negative columns read stale records and only ever produce +inf).
+        constexpr int TRk = QTrans<V, R>::value;
+        auto rec_at = [&](unsigned x, float4 (&r)[NPL]) {
+          const float4* qp = qr + (x % TRk) * (NQC / TRk) + ((x / TRk) & (unsigned)(NQC / TRk - 1));
+#pragma unroll
+          for (int c = 0; c < NPL; ++c) r[c] = qp[c * NQC];
+        };
+        float4 r0[NPL];
+        rec_at(xbase - (unsigned)(K * L), r0);
+        rec_at(xbase + 1u - (unsigned)(K * L), ss.nrec1);
+#pragma unroll
+        for (int h = 0; h < SS::K; ++h) {
+#pragma unroll
+          for (int c = 0; c < NPL; ++c) ss.win[h][c] = r0[c];
+        }
+        rows.dist_pair(0, r0, ss.dcur[0][0], ss.dcur[0][1]);
+#pragma unroll
+        for (int h = 1; h < SS::K; ++h) {
+          ss.dcur[h][0] = ss.dcur[0][0];
+          ss.dcur[h][1] = ss.dcur[0][1];
+        }
+      }
+      skew_block<DK, (kSkew ? R : 2)>(reinterpret_cast<const Rows<F32, DK, (kSkew ? R : 2)>&>(rows), ss,
+                                      reinterpret_cast<const float*>(ring_in), reinterpret_cast<float*>(ring_out),
+                                      qr, xbase, c0, L);
+    } else {
+      auto qaddr = [&](int cq) { return qring + ((xbase + (unsigned)cq) & (unsigned)(NQC - 1)); };
+      // The block's 32 ring inputs, one per lane (lane s holds column c0 + s);
+      // at step s lane 0 takes lane s's value.  Lane 31's outputs are gathered
+      // the same way (lane s keeps step s's) and stored after the block, so
+      // the unrolled block has no shared-memory store and no branch.
+      const T in_blk = ring_in[ridx(c0 + L)];
+      T out_blk = V::inf();
 #pragma unroll
       for (int s = 0; s < G; ++s) {
         const int col = c0 + s - L;
-        T dnext[R];
-        if (s + 1 < G) rows.dist(qaddr(max(col + 1, 0)), C, dnext);
+        const T rin = __shfl_sync(0xffffffffu, in_blk, s);
         T u = __shfl_up_sync(0xffffffffu, bout, 1);
-        u = (L == 0) ? rv[s] : u;
+        u = (L == 0) ? rin : u;
+        T d[R];
+        rows.dist(qaddr(max(col, 0)), NQC, d);
         T up = u, dg = upp;
 #pragma unroll
         for (int r = 0; r < R; ++r) {
           const T l = v[r];
-          const T nv = V::vmax(V::vmin3(l, dg, up), dcur[r]);
+          const T nv = V::vmax(V::vmin3(l, dg, up), d[r]);
           dg = l;
           v[r] = nv;
           up = nv;
         }
         upp = u;
         bout = up;
-        st_shared_if(ring_out + (col & (RING - 1)), bout, L == 31 && col >= 0);
-        if (s + 1 < G) {
-#pragma unroll
-          for (int r = 0; r < R; ++r) dcur[r] = dnext[r];
-        }
+        const T b31 = __shfl_sync(0xffffffffu, bout, 31);
+        out_blk = (L == s) ? b31 : out_blk;
       }
-    } else {
-    // The block's 32 ring inputs, one per lane (lane s holds column c0 + s);
-    // at step s lane 0 takes lane s's value.  Lane 31's outputs are gathered
-    // the same way (lane s keeps step s's) and stored after the block, so
-    // the unrolled block has no shared-memory store and no branch.
-    const T in_blk = ring_in[(c0 + L) & (RING - 1)];
-    T out_blk = V::inf();
-#pragma unroll
-    for (int s = 0; s < G; ++s) {
-      const int col = c0 + s - L;
-      const T rin = __shfl_sync(0xffffffffu, in_blk, s);
-      T u = __shfl_up_sync(0xffffffffu, bout, 1);
-      u = (L == 0) ? rin : u;
-      T d[R];
-      rows.dist(qaddr(max(col, 0)), C, d);
-      T up = u, dg = upp;
-#pragma unroll
-      for (int r = 0; r < R; ++r) {
-        const T l = v[r];
-        const T nv = V::vmax(V::vmin3(l, dg, up), d[r]);
-        dg = l;
-        v[r] = nv;
-        up = nv;
+      {
+        const int oc = c0 + L - 31;   // column lane 31 produced at step L
+        st_shared_if(ring_out + ridx(oc), out_blk, oc >= 0);
       }
-      upp = u;
-      bout = up;
-      const T b31 = __shfl_sync(0xffffffffu, bout, 31);
-      out_blk = (L == s) ? b31 : out_blk;
-    }
-    {
-      const int oc = c0 + L - 31;   // column lane 31 produced at step L
-      st_shared_if(ring_out + (oc & (RING - 1)), out_blk, oc >= 0);
-    }
     }
     __syncwarp();
-    if (L == 31) st_release_cta(&ctl->prod[w + 1], c0 + G - 31);
+    if (L == 31) st_release_cta(&ctl->prod[w + 1], c0 + G - SK);
     if (L == 0) st_release_cta(&ctl->cons[w], c0 + G);
-    // q chunks no lane of this warp will read again: columns < c0 + G - 31.
-    const int consumed = max(0, c0 + G - 31) >> LOGC;
+    // q chunks no lane of this warp will read again: the next read is lane
+    // 31's first one in the next block (float32: the look-ahead of step 2).
+    const int first_unread = c0 + G - 31 * K + (kSkew ? 2 : 0);
+    const int consumed = max(0, first_unread) / C;
     while (qdone < consumed && qdone < a.nch) {
       if (L == 0) mbar_arrive(&empty[(gbase + (unsigned)qdone) & (NQ - 1)]);
       ++qdone;
@@ -386,6 +580,8 @@ __device__ __forceinline__ void comm_warp(const Args& a, int64_t band, unsigned 
   constexpr int C = Lay::C;
   constexpr int NPL = Lay::NPL;
   constexpr unsigned CHUNK_BYTES = (unsigned)(NPL * C * sizeof(Rec));
+  constexpr int NQC = NQ * C;
+  constexpr int TR = QTrans<V, R>::value;
   const int L = threadIdx.x & 31;
   const int W = (int)(blockDim.x >> 5) - 1;
   Rec* qring = reinterpret_cast<Rec*>(smem);
@@ -414,7 +610,16 @@ __device__ __forceinline__ void comm_warp(const Args& a, int64_t band, unsigned 
       if (slot_free) {
         if (L == 0) {
           mbar_arrive_expect_tx(&full[slot], CHUNK_BYTES);
-          tma_load_1d(qring + (size_t)slot * NPL * C, qpk + (size_t)issued * NPL * C, CHUNK_BYTES, &full[slot]);
+          // One copy per plane and column residue (the ring layout of QTrans).
+#pragma unroll
+          for (int pl = 0; pl < NPL; ++pl) {
+#pragma unroll
+            for (int r = 0; r < TR; ++r) {
+              tma_load_1d(qring + (size_t)pl * NQC + (size_t)r * (NQC / TR) + (size_t)slot * (C / TR),
+                          qpk + ((size_t)issued * NPL + pl) * C + (size_t)r * (C / TR),
+                          (unsigned)((C / TR) * sizeof(Rec)), &full[slot]);
+            }
+          }
         }
         ++issued;
         progressed = true;
@@ -435,7 +640,7 @@ __device__ __forceinline__ void comm_warp(const Args& a, int64_t band, unsigned 
         const int col = filled + L;
         T val = V::inf();
         if (band > 0 && col < m) val = ld_cg(rowbuf + col);
-        ring0[col & (RING - 1)] = val;
+        ring0[ridx(col)] = val;
         __syncwarp();
         if (L == 0) st_release_cta(&ctl->prod[0], filled + 32);
         filled += 32;
@@ -448,7 +653,7 @@ __device__ __forceinline__ void comm_warp(const Args& a, int64_t band, unsigned 
       if (ld_acquire_cta(&ctl->prod[W]) >= need) {
         const int col = drained + L;
         if (col < m) {
-          const T val = ringW[col & (RING - 1)];
+          const T val = ringW[ridx(col)];
           st_cg(rowbuf + col, val);
           if (band == a.nbands - 1 && col == m - 1) {
             if constexpr (sizeof(T) == 4) {
@@ -502,7 +707,7 @@ __device__ __forceinline__ void comm_warp(const Args& a, int64_t band, unsigned 
 
 // ------------------------------------------------------------------ kernel
 template <class V, int DK, int R>
-__global__ void __launch_bounds__(17 * 32, 1) wave_kernel(Args a) {
+__global__ void __launch_bounds__((kMaxWarps<V, DK, R>::value + 1) * 32, 1) wave_kernel(Args a) {
   using Lay = Layout<V, DK, R>;
   using T = typename V::value;
   extern __shared__ __align__(128) unsigned char smem[];
@@ -554,10 +759,11 @@ __global__ void __launch_bounds__(17 * 32, 1) wave_kernel(Args a) {
 
 // --------------------------------------------------------- q packing kernel
 // Writes the per-band q stream: nch chunks of C columns, NPL 16-byte planes
-// per column, columns past m repeat q_{m-1} (a repeated point does not change
-// the distance, Sec. 4 footnote; they are never read into the result).
+// per column, each plane in the column order qpos(., TR, C); columns past m
+// repeat q_{m-1} (a repeated point does not change the distance, Sec. 4
+// footnote; they are never read into the result).
 template <class V, int DK>
-__global__ void pack_q_kernel(const typename V::coord* q, int64_t m, int dim, int nch, void* out) {
+__global__ void pack_q_kernel(const typename V::coord* q, int64_t m, int dim, int nch, int TR, void* out) {
   constexpr int C = ChunkCols<DK>::value;
   using Rows_ = Rows<V, DK, 2>;
   constexpr int NPL = Rows_::NPL;
@@ -585,7 +791,7 @@ __global__ void pack_q_kernel(const typename V::coord* q, int64_t m, int dim, in
       r.z = k + 2 < dim ? qj[k + 2] : 0;
       r.w = k + 3 < dim ? qj[k + 3] : 0;
     }
-    o[idx] = r;
+    o[chunk * (C * NPL) + plane * C + qpos(jj, TR, C)] = r;
   }
 }
 

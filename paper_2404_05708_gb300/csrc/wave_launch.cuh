@@ -2,6 +2,7 @@
 // per (value type, dimension class, rows per lane) in wave_*.cu.
 #pragma once
 #include <algorithm>
+#include <type_traits>
 #include "dfd_internal.h"
 #include "wave_kernel.cuh"
 
@@ -14,13 +15,19 @@ dfd_status wave_launch(dfd_context* ctx, int dim, const void* p, int64_t n, cons
   using T = typename V::value;
   using Rec = typename Lay::Rec;
   constexpr int C = Lay::C;
-  if (W < 1 || W > 16 || W > wave::max_warps(C)) return DFD_ERR_UNSUPPORTED;
+  constexpr int K = wave::Skew<V, R>::value;
+  if constexpr (wave::kMaxWarps<V, DK, R>::value < 1) {
+    return DFD_ERR_UNSUPPORTED;   // R rows of DK coordinates do not fit one lane's registers
+  } else {
+  if (!wave::shape_supported(std::is_same<V, F32>::value, DK, R, W)) return DFD_ERR_UNSUPPORTED;
   const int64_t H = (int64_t)W * 32 * R;
   const int64_t nbands = (n + H - 1) / H;
-  const int64_t nblk64 = (m + 31 + wave::G - 1) / wave::G;
+  // Lane 31's bottom row reaches column m - 1 at step m - 1 + 32*K - 1.
+  const int64_t nblk64 = (m + 32 * K - 1 + wave::G - 1) / wave::G;
   if (nblk64 * wave::G > (int64_t)INT32_MAX / 2) return DFD_ERR_UNSUPPORTED;
   const int nblk = (int)nblk64;
-  const int nch = (nblk * wave::G + C - 1) / C;
+  // The look-ahead of the last steps reads columns up to nblk*G + 1.
+  const int nch = (nblk * wave::G + 2 + C - 1) / C;
 
   const size_t off_prog = 256;
   const size_t off_row = align_up(off_prog + (size_t)nbands * sizeof(unsigned long long), 256);
@@ -37,7 +44,7 @@ dfd_status wave_launch(dfd_context* ctx, int dim, const void* p, int64_t n, cons
     const int threads = 256;
     const int blocks = (int)std::min<int64_t>((recs + threads - 1) / threads, 4 * (int64_t)ctx->num_sms);
     wave::pack_q_kernel<V, DK><<<blocks, threads, 0, s>>>(static_cast<const typename V::coord*>(q), m, dim, nch,
-                                                         base + off_q);
+                                                         wave::QTrans<V, R>::value, base + off_q);
   }
   const size_t smem = Lay::bytes(W);
   if (smem > ctx->smem_optin) return DFD_ERR_UNSUPPORTED;
@@ -67,6 +74,7 @@ dfd_status wave_launch(dfd_context* ctx, int dim, const void* p, int64_t n, cons
   wave::wave_kernel<V, DK, R><<<grid, (W + 1) * 32, smem, s>>>(a);
   timing_end(ctx, s);
   return cuda_status(cudaGetLastError());
+  }
 }
 
 }  // namespace dfd

@@ -1,0 +1,51 @@
+// wave_shape.h -- launch-shape limits of the band wavefront (K2), shared by
+// the kernel (launch bounds) and the host (shape checks, planner).
+#pragma once
+
+namespace dfd {
+namespace wave {
+
+constexpr int G = 32;        // systolic steps between synchronisations
+constexpr int RING = 256;    // columns held by each inter-warp ring (power of 2)
+constexpr int NQ = 16;       // q chunk slots (power of 2)
+
+// q columns per TMA chunk.
+constexpr int chunk_cols(int dk) { return dk <= 4 ? 128 : 64; }
+
+// Column skew between neighbouring lanes: float32 lanes hold R/2 skewed row
+// pairs, int32 lanes keep their R rows in one column.
+constexpr int skew(bool f32, int R) { return f32 ? R / 2 : 1; }
+
+// Deadlock bound of the q ring.  Warp w+1 needs columns that warp w emits
+// 32*K - 1 columns late and publishes per G-block, so it trails warp w by at
+// most 32*K + G columns; lane 31 of the last warp reads 31*K columns behind
+// its lane 0, and warp 0 waits for the chunks one block ahead (the q
+// look-ahead reaches two columns past the block).  Every chunk warp 0 can
+// wait for must fit in the ring beside the oldest one the last warp may
+// still read:
+//   (NQ - 1) * C >= (W - 1) * (32*K + G) + 31*K + G + 2.
+constexpr int max_warps_ring(int C, int K) { return ((NQ - 1) * C - 31 * K - G - 2) / (32 * K + G) + 1; }
+
+// Registers a compute lane needs (points, row state, q records in flight,
+// the block's ring inputs, addressing), an estimate calibrated on ptxas.
+constexpr int reg_estimate(bool f32, int dk, int R) {
+  return f32 ? 48 + R * dk + (R / 2) * ((dk + 1) / 2) * 4 + 2 * R + 3 * (R / 2) + G
+             : 48 + R * dk + 4 * R + ((dk + 3) / 4) * 4;
+}
+
+// Compute warps per CTA the register file allows (with the communication
+// warp, one CTA per SM); 0 if even one warp would not fit in 255 registers.
+constexpr int max_warps_regs(bool f32, int dk, int R) {
+  return reg_estimate(f32, dk, R) > 248 ? 0
+         : (65536 / (32 * ((reg_estimate(f32, dk, R) + 7) / 8 * 8)) - 1) > 16
+             ? 16
+             : 65536 / (32 * ((reg_estimate(f32, dk, R) + 7) / 8 * 8)) - 1;
+}
+
+constexpr bool shape_supported(bool f32, int dk, int R, int W) {
+  return (R == 2 || R == 4 || R == 6 || R == 8) && W >= 1 && W <= max_warps_regs(f32, dk, R) &&
+         W <= max_warps_ring(chunk_cols(dk), skew(f32, R));
+}
+
+}  // namespace wave
+}  // namespace dfd

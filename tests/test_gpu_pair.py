@@ -138,7 +138,7 @@ def test_explicit_wave_shapes(dctx, R):
     pi, qi = i32_walk(rng, 2777, 2), i32_walk(rng, 1999, 2)
     want = float(oracle.dfd2_f32mirror(p, q))
     want_i = oracle.dfd2_linear(pi, qi)
-    for W in (1, 2, 5, 16):
+    for W in (1, 2, 5, 7, 11):
         for ctas in (1, 3, 0):
             assert run(dctx, p, q, shape=(R, W, ctas))[1] == want, (R, W, ctas)
             assert run(dctx, pi, qi, shape=(R, W, ctas))[1] == want_i, (R, W, ctas)
@@ -169,6 +169,22 @@ def test_autotune_picks_a_valid_shape_and_round_trips(tmp_path):
             ctx2.close()
     finally:
         ctx.close()
+
+
+def test_unsupported_wave_shapes_are_refused(dctx):
+    """Shapes outside the register / q-ring limits return DFD_ERR_UNSUPPORTED
+    (no launch); 16-D float32 lanes cannot hold 8 rows."""
+    from paper_2404_05708_gb300 import dfd
+    rng = np.random.default_rng(5)
+    p, q = f32_walk(rng, 300, 3), f32_walk(rng, 200, 3)
+    for shape in ((8, 16, 0), (3, 2, 0), (8, 0, 0)):
+        with pytest.raises(dfd.DFDError) as e:
+            run(dctx, p, q, shape=shape)
+        assert e.value.status == dfd.STATUS_CODE["DFD_ERR_UNSUPPORTED"]
+    p16, q16 = f32_walk(rng, 300, 16), f32_walk(rng, 200, 16)
+    with pytest.raises(dfd.DFDError):
+        run(dctx, p16, q16, shape=(8, 2, 0))
+    dctx.get_error()
 
 
 def test_reference_kernel_matches_oracle_int(dctx):
