@@ -597,6 +597,7 @@ __device__ __forceinline__ void comm_warp(const Args& a, int64_t band, unsigned 
   const int m = (int)a.m;
   const int fill_end = a.nblk * G;
   int issued = 0, filled = 0, drained = 0;
+  unsigned long long pub = 0;   // columns of the band above known published
   unsigned long long t_idle = globaltimer_ns();
   bool aborted = false;
 
@@ -625,55 +626,71 @@ __device__ __forceinline__ void comm_warp(const Args& a, int64_t band, unsigned 
         progressed = true;
       }
     }
-    // (2) top ring of the band, 32 columns at a time
-    if (filled < fill_end && ld_acquire_cta(&ctl->cons[0]) >= filled + 32 - RING) {
-      bool avail = true;
-      const int need = min(filled + 32, m);
-      if (band > 0 && need > 0) {
-        unsigned long long pv = 0;
-        if (L == 0) pv = ld_acquire_u64(&a.progress[band - 1]);
-        pv = __shfl_sync(0xffffffffu, pv, 0);
-        __syncwarp();
-        avail = pv >= (unsigned long long)need;
+    // (2) top ring of the band: every 32-column unit that the band above
+    // has published (acquire; re-polled only when the cached value falls
+    // short) and the ring has room for, up to 4 units per L2 round trip.
+    if (filled < fill_end) {
+      const int room = ld_acquire_cta(&ctl->cons[0]) + RING - filled;
+      int ready = fill_end - filled;
+      if (band > 0) {
+        if (pub < (unsigned long long)min(filled + 32, m)) {
+          unsigned long long pv = 0;
+          if (L == 0) pv = ld_acquire_u64(&a.progress[band - 1]);
+          pub = __shfl_sync(0xffffffffu, pv, 0);
+        }
+        // Columns past m are +inf padding, ready once column m - 1 is.
+        ready = pub >= (unsigned long long)m ? fill_end - filled : (int)pub - filled;
       }
-      if (avail) {
-        const int col = filled + L;
-        T val = V::inf();
-        if (band > 0 && col < m) val = ld_cg(rowbuf + col);
-        ring0[ridx(col)] = val;
+      const int units = min(min(ready, room) >> 5, 4);
+      if (units > 0) {
+        __syncwarp();   // order the lanes' loads after lane 0's acquire
+        T val[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const int col = filled + 32 * k + L;
+          val[k] = V::inf();
+          if (k < units && band > 0 && col < m) val[k] = ld_cg(rowbuf + col);
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+          if (k < units) ring0[ridx(filled + 32 * k + L)] = val[k];
         __syncwarp();
-        if (L == 0) st_release_cta(&ctl->prod[0], filled + 32);
-        filled += 32;
+        filled += 32 * units;
+        if (L == 0) st_release_cta(&ctl->prod[0], filled);
         progressed = true;
       }
     }
-    // (3) drain the bottom ring to the global row buffer and publish it
+    // (3) drain the bottom ring to the global row buffer and publish it,
+    // up to 4 units of 32 columns per release.
     if (drained < m) {
-      const int need = min(drained + 32, m);
-      if (ld_acquire_cta(&ctl->prod[W]) >= need) {
-        const int col = drained + L;
-        if (col < m) {
-          const T val = ringW[ridx(col)];
-          st_cg(rowbuf + col, val);
-          if (band == a.nbands - 1 && col == m - 1) {
-            if constexpr (sizeof(T) == 4) {
-              if (a.out_dist2) static_cast<float*>(a.out_dist2)[0] = (float)val;
-              if (a.out_dist) static_cast<float*>(a.out_dist)[0] = sqrtf((float)val);
-            } else {
-              if (a.out_dist2) static_cast<long long*>(a.out_dist2)[0] = (long long)val;
-              if (a.out_dist) static_cast<double*>(a.out_dist)[0] = sqrt((double)val);
+      const int pw = min(ld_acquire_cta(&ctl->prod[W]), m);
+      const int units = min((pw - drained + (pw == m ? 31 : 0)) >> 5, 4);
+      if (units > 0) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const int col = drained + 32 * k + L;
+          if (k < units && col < m) {
+            const T val = ringW[ridx(col)];
+            st_cg(rowbuf + col, val);
+            if (band == a.nbands - 1 && col == m - 1) {
+              if constexpr (sizeof(T) == 4) {
+                if (a.out_dist2) static_cast<float*>(a.out_dist2)[0] = (float)val;
+                if (a.out_dist) static_cast<float*>(a.out_dist)[0] = sqrtf((float)val);
+              } else {
+                if (a.out_dist2) static_cast<long long*>(a.out_dist2)[0] = (long long)val;
+                if (a.out_dist) static_cast<double*>(a.out_dist)[0] = sqrt((double)val);
+              }
             }
           }
         }
         __syncwarp();
+        drained = min(drained + 32 * units, m);
         if (L == 0) {
-          st_release_cta(&ctl->cons[W], drained + 32);
+          st_release_cta(&ctl->cons[W], drained);
           // The release orders the warp's row-buffer stores (made visible to
           // lane 0 by __syncwarp) before the progress word at GPU scope.
-          st_release_u64(&a.progress[band], (unsigned long long)need);
+          st_release_u64(&a.progress[band], (unsigned long long)drained);
         }
-        drained += 32;
-        if (drained > m) drained = m;
         progressed = true;
       }
     }
