@@ -349,32 +349,28 @@ __device__ __forceinline__ void skew_block(const Rows<F32, DK, R>& rows, SkewSta
 #pragma unroll
       for (int c = 0; c < NPL; ++c) nrec2[c] = qp[c * NQC];
     }
-    // (2) the bottom pair first, then the shuffle for step s + 1
+    // (2) the first rows of all pairs (independent), then the second rows
+    // with the bottom pair first, so the shuffle for step s + 1 leaves early
     float unext;
     {
-      constexpr int h = K - 1;
-      const int hp = h > 0 ? h - 1 : 0;
-      const float up0 = h > 0 ? st.v1[hp] : u;
-      const float dg0 = h > 0 ? st.pv1[hp] : st.upp;
-      const float n0 = F32::vmax(F32::vmin3(st.v0[h], dg0, up0), st.dcur[h][0]);
-      const float n1 = F32::vmax(F32::vmin3(st.v1[h], st.v0[h], n0), st.dcur[h][1]);
-      st.pv1[h] = st.v1[h];
-      st.v0[h] = n0;
-      st.v1[h] = n1;
-      unext = __shfl_up_sync(0xffffffffu, n1, 1);
-      obuf[s & 3] = n1;
-    }
-    // (3) the other pairs (pair 0 takes the shuffled / ring value)
+      float n0[K], n1[K];
 #pragma unroll
-    for (int h = K - 2; h >= 0; --h) {
-      const int hp = h > 0 ? h - 1 : 0;
-      const float up0 = h > 0 ? st.v1[hp] : u;
-      const float dg0 = h > 0 ? st.pv1[hp] : st.upp;
-      const float n0 = F32::vmax(F32::vmin3(st.v0[h], dg0, up0), st.dcur[h][0]);
-      const float n1 = F32::vmax(F32::vmin3(st.v1[h], st.v0[h], n0), st.dcur[h][1]);
-      st.pv1[h] = st.v1[h];
-      st.v0[h] = n0;
-      st.v1[h] = n1;
+      for (int h = K - 1; h >= 0; --h) {
+        const int hp = h > 0 ? h - 1 : 0;
+        const float up0 = h > 0 ? st.v1[hp] : u;   // pair 0: lane L-1 / ring above
+        const float dg0 = h > 0 ? st.pv1[hp] : st.upp;
+        n0[h] = F32::vmax(F32::vmin3(st.v0[h], dg0, up0), st.dcur[h][0]);
+      }
+#pragma unroll
+      for (int h = K - 1; h >= 0; --h) n1[h] = F32::vmax(F32::vmin3(st.v1[h], st.v0[h], n0[h]), st.dcur[h][1]);
+      unext = __shfl_up_sync(0xffffffffu, n1[K - 1], 1);
+      obuf[s & 3] = n1[K - 1];
+#pragma unroll
+      for (int h = 0; h < K; ++h) {
+        st.pv1[h] = st.v1[h];
+        st.v0[h] = n0[h];
+        st.v1[h] = n1[h];
+      }
     }
     st.upp = u;
     // (4) distances of step s + 1
