@@ -119,7 +119,7 @@ __device__ __forceinline__ typename V::value warp_dfd(const typename V::coord* _
         load_point<Cd, DK>(Q, jq, dim, vec, qk);
         T d[R];
 #pragma unroll
-        for (int r = 0; r < R; ++r) d[r] = dist2<DK>(pr[r], qk);
+        for (int r = 0; r < R; ++r) d[r] = vdist2<V, DK>(pr[r], qk);
         const T tin = __shfl_sync(0xffffffffu, top_blk, s);
         T u = __shfl_up_sync(0xffffffffu, bout, 1);
         u = (L == 0) ? tin : u;
@@ -189,15 +189,84 @@ __device__ __forceinline__ bool fits_buffer(int rows, int cols) {
   return rows <= 32 * Rmax<DK>::value || cols <= BUF_COLS;
 }
 
-template <class T>
-__device__ __forceinline__ void write_result(void* out_dist, void* out_dist2, int64_t k, T r) {
-  if constexpr (sizeof(T) == 4) {
-    if (out_dist2) static_cast<float*>(out_dist2)[k] = (float)r;
-    if (out_dist) static_cast<float*>(out_dist)[k] = sqrtf((float)r);
+template <class V>
+__device__ __forceinline__ void write_result(void* out_dist, void* out_dist2, int64_t k, typename V::value r) {
+  if constexpr (std::is_same<V, F32>::value) {
+    if (out_dist2) static_cast<float*>(out_dist2)[k] = r;
+    if (out_dist) static_cast<float*>(out_dist)[k] = sqrtf(r);
   } else {
-    if (out_dist2) static_cast<long long*>(out_dist2)[k] = (long long)r;
-    if (out_dist) static_cast<double*>(out_dist)[k] = sqrt((double)r);
+    long long v;
+    if constexpr (std::is_same<V, I32B>::value)
+      v = (long long)__float_as_uint(r);
+    else
+      v = (long long)r;
+    if (out_dist2) static_cast<long long*>(out_dist2)[k] = v;
+    if (out_dist) static_cast<double*>(out_dist)[k] = sqrt((double)v);
   }
+}
+
+// int32 pairs whose bounding boxes keep every squared distance exact in
+// uint32 (below the first float NaN pattern) run as I32B.  bbox holds per
+// curve and coordinate (min, max).
+__device__ __forceinline__ bool narrow_pair(const int* __restrict__ bbox, int dk, int64_t ia, int64_t ib) {
+  unsigned long long s = 0;
+  for (int k = 0; k < dk; ++k) {
+    const long long lo = min(bbox[(ia * dk + k) * 2], bbox[(ib * dk + k) * 2]);
+    const long long hi = max(bbox[(ia * dk + k) * 2 + 1], bbox[(ib * dk + k) * 2 + 1]);
+    const unsigned long long r = (unsigned long long)(hi - lo);
+    if (r > kI32BMaxRange) return false;
+    s += r * r;
+  }
+  return s <= kI32BMaxD2;
+}
+
+// Per-curve bounding boxes (one warp per curve) of int32 points, and the
+// coordinate range check (|c| <= lim) when `check` is set.
+template <int DK>
+__global__ void curve_bbox_kernel(const int32_t* __restrict__ pts, const int64_t* __restrict__ offsets,
+                                  int64_t n_curves, int dim, int vec, int check, long long lim, int* bbox, int* err) {
+  const int L = threadIdx.x & 31;
+  const int64_t total = offsets[n_curves];
+  bool bad = false;
+  for (int64_t c = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < n_curves;
+       c += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+    const int64_t o = offsets[c], e = offsets[c + 1];
+    int lo[DK], hi[DK];
+#pragma unroll
+    for (int k = 0; k < DK; ++k) {
+      lo[k] = INT_MAX;
+      hi[k] = INT_MIN;
+    }
+    if (o >= 0 && e <= total && o < e) {
+      const int32_t* Q = pts + o * dim;
+      for (int64_t j = L; j < e - o; j += 32) {
+        int32_t qk[DK];
+        load_point<int32_t, DK>(Q, (int)j, dim, vec != 0, qk);
+#pragma unroll
+        for (int k = 0; k < DK; ++k) {
+          lo[k] = min(lo[k], qk[k]);
+          hi[k] = max(hi[k], qk[k]);
+          if (check && k < dim) bad |= qk[k] < -lim || qk[k] > lim;
+        }
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < DK; ++k) {
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) {
+        lo[k] = min(lo[k], __shfl_xor_sync(0xffffffffu, lo[k], off));
+        hi[k] = max(hi[k], __shfl_xor_sync(0xffffffffu, hi[k], off));
+      }
+    }
+    if (L == 0) {
+#pragma unroll
+      for (int k = 0; k < DK; ++k) {
+        bbox[(c * DK + k) * 2] = lo[k];
+        bbox[(c * DK + k) * 2 + 1] = hi[k];
+      }
+    }
+  }
+  if (__any_sync(0xffffffffu, bad) && L == 0) raise_error(err, DFD_ERR_RANGE);
 }
 
 // ------------------------------------------------------------- planning
@@ -205,8 +274,11 @@ __device__ __forceinline__ void write_result(void* out_dist, void* out_dist2, in
 // stripes), largest first, then by column count, largest first (LPT within
 // a variant).  Warps resident together then mostly run the same variant,
 // and the costliest pairs start first.  16 variant classes x 16 column
-// buckets of 256.
-constexpr int NBUCKET = 256;
+// buckets of 256 per value class; int32 pairs come in two value classes
+// (exact int64 first, then exact uint32 bits, I32B).
+constexpr int NBUCKET1 = 256;
+constexpr int NBUCKET = 2 * NBUCKET1;
+constexpr unsigned kNarrowBit = 1u << 30;   // worklist: pair index | narrow << 30 | swap << 31
 
 __device__ __forceinline__ int cost_bucket(int64_t rows, int64_t cols, int rmax) {
   const int64_t per_stripe = 32 * (int64_t)rmax;
@@ -223,8 +295,10 @@ struct PlanArgs {
   int64_t n_curves;
   unsigned* hist;      // [NBUCKET]
   unsigned* cursor;    // [NBUCKET]
-  unsigned char* bucket;  // [n_pairs]
-  unsigned* worklist;  // [n_pairs]: pair index | swap << 31
+  unsigned short* bucket;  // [n_pairs]
+  unsigned* worklist;  // [n_pairs]: pair index | narrow << 30 | swap << 31
+  const int* bbox;     // int32 batches: per curve and coordinate (min, max); else null
+  int dk;              // coordinates per bbox entry
   int* err;
   int rmax;            // rows per lane of one stripe for this dimension class
 };
@@ -233,7 +307,7 @@ struct PlanArgs {
 static __global__ void plan_hist_kernel(PlanArgs a) {
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < a.n_pairs; k += (int64_t)gridDim.x * blockDim.x) {
     const int32_t ia = a.pairs[2 * k], ib = a.pairs[2 * k + 1];
-    int b = NBUCKET - 1;
+    int b = NBUCKET1 - 1;   // invalid pairs: last of the int64 class (skipped by the kernel)
     if (ia < 0 || ib < 0 || ia >= a.n_curves || ib >= a.n_curves) {
       raise_error(a.err, DFD_ERR_INVALID_ARG);
     } else {
@@ -243,8 +317,9 @@ static __global__ void plan_hist_kernel(PlanArgs a) {
       if (na < 1 || nb < 1 || oa < 0 || ob < 0 || ea > total || eb > total || na > INT32_MAX || nb > INT32_MAX)
         raise_error(a.err, DFD_ERR_INVALID_ARG);
       b = cost_bucket(max(min(na, nb), (int64_t)1), max(max(na, nb), (int64_t)1), a.rmax);
+      if (a.bbox && narrow_pair(a.bbox, a.dk, ia, ib)) b += NBUCKET1;
     }
-    a.bucket[k] = (unsigned char)b;
+    a.bucket[k] = (unsigned short)b;
     atomicAdd(&a.hist[b], 1u);
   }
 }
@@ -269,7 +344,8 @@ static __global__ void plan_scatter_kernel(PlanArgs a) {
       const int64_t na = a.offsets[ia + 1] - a.offsets[ia], nb = a.offsets[ib + 1] - a.offsets[ib];
       swap = na > nb ? 1u : 0u;   // rows = the shorter curve
     }
-    a.worklist[pos] = (unsigned)k | (swap << 31);
+    const unsigned narrow = a.bucket[k] >= NBUCKET1 ? kNarrowBit : 0u;
+    a.worklist[pos] = (unsigned)k | narrow | (swap << 31);
   }
 }
 
@@ -306,7 +382,7 @@ __global__ void __launch_bounds__(256, 2) batch_kernel(BatchArgs a) {
     item = __shfl_sync(0xffffffffu, item, 0);
     if (item >= a.n_items) break;
     const unsigned w = a.worklist[item];
-    const int64_t k = w & 0x7fffffffu;
+    const int64_t k = w & (kNarrowBit - 1);
     int32_t ia = a.pairs[2 * k], ib = a.pairs[2 * k + 1];
     if (w >> 31) {
       const int32_t t = ia;
@@ -323,8 +399,16 @@ __global__ void __launch_bounds__(256, 2) batch_kernel(BatchArgs a) {
       if (L == 0) raise_error(a.err, DFD_ERR_UNSUPPORTED);
       continue;
     }
+    if constexpr (std::is_same<V, I32>::value) {
+      if (w & kNarrowBit) {
+        const float r = warp_dfd_any<I32B, DK>(pts + oa * a.dim, n, pts + ob * a.dim, m, a.dim, a.vec != 0,
+                                               reinterpret_cast<float*>(buf), L);
+        if (L == 0) write_result<I32B>(a.out_dist, a.out_dist2, k, r);
+        continue;
+      }
+    }
     const T r = warp_dfd_any<V, DK>(pts + oa * a.dim, n, pts + ob * a.dim, m, a.dim, a.vec != 0, buf, L);
-    if (L == 0) write_result<T>(a.out_dist, a.out_dist2, k, r);
+    if (L == 0) write_result<V>(a.out_dist, a.out_dist2, k, r);
   }
 }
 
@@ -352,6 +436,7 @@ struct MatrixArgs {
   int dim;
   int vec;             // 1: vector point loads allowed (dim == DK, 16-byte aligned points)
   int chunk;        // pairs per pop
+  const int* bbox;  // int32 matrices: per curve and coordinate (min, max); else null
   int* counter;
   int* err;
   void* out_dist;
@@ -385,12 +470,20 @@ __global__ void __launch_bounds__(256, 2) matrix_kernel(MatrixArgs a) {
       if (rows < 1) {
         if (L == 0) raise_error(a.err, DFD_ERR_INVALID_ARG);
       } else if (fits_buffer<DK>(rows, cols)) {
-        T r;
-        if (ni <= nj)
-          r = warp_dfd_any<V, DK>(pts + oi * a.dim, ni, pts + oj * a.dim, nj, a.dim, a.vec != 0, buf, L);
-        else
-          r = warp_dfd_any<V, DK>(pts + oj * a.dim, nj, pts + oi * a.dim, ni, a.dim, a.vec != 0, buf, L);
-        if (L == 0) write_result<T>(a.out_dist, a.out_dist2, k, r);
+        const int64_t ia = ni <= nj ? i : j, ib = ni <= nj ? j : i;
+        const int64_t oa = ni <= nj ? oi : oj, ob = ni <= nj ? oj : oi;
+        bool narrow = false;
+        if constexpr (std::is_same<V, I32>::value) narrow = a.bbox && narrow_pair(a.bbox, DK, ia, ib);
+        if (narrow) {
+          if constexpr (std::is_same<V, I32>::value) {
+            const float r = warp_dfd_any<I32B, DK>(pts + oa * a.dim, rows, pts + ob * a.dim, cols, a.dim,
+                                                   a.vec != 0, reinterpret_cast<float*>(buf), L);
+            if (L == 0) write_result<I32B>(a.out_dist, a.out_dist2, k, r);
+          }
+        } else {
+          const T r = warp_dfd_any<V, DK>(pts + oa * a.dim, rows, pts + ob * a.dim, cols, a.dim, a.vec != 0, buf, L);
+          if (L == 0) write_result<V>(a.out_dist, a.out_dist2, k, r);
+        }
       } else if (L == 0) {
         raise_error(a.err, DFD_ERR_UNSUPPORTED);
       }

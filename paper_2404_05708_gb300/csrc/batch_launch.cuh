@@ -2,28 +2,24 @@
 // instantiated per (value type, dimension class) in batch_*.cu.
 #pragma once
 #include <algorithm>
+#include <climits>
+#include <cmath>
 #include <type_traits>
 #include "batch_kernel.cuh"
 #include "dfd_internal.h"
 
 namespace dfd {
 
-// Input checks over CSR points whose count is on the device (offsets[n]).
+// float32 input check over CSR points whose count is on the device
+// (offsets[n]); int32 batches are checked by the bounding-box kernel.
 template <class V>
 __global__ void check_points_kernel(const typename V::coord* x, const int64_t* count_points, int dim, int* err) {
+  static_assert(std::is_same<V, F32>::value, "float32 only");
   const int64_t count = count_points[0] * dim;
   bool bad = false;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
-    const typename V::coord c = x[i];
-    if constexpr (std::is_same<V, F32>::value) {
-      bad |= !isfinite(c);
-    } else {
-      const long long a = c < 0 ? -(long long)c : (long long)c;
-      bad |= a > (1LL << 30) - 1 || (double)a > sqrt((double)LLONG_MAX / (double)dim) / 2.0;
-    }
-  }
-  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0)
-    raise_error(err, std::is_same<V, F32>::value ? DFD_ERR_NONFINITE : DFD_ERR_RANGE);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x)
+    bad |= !isfinite(x[i]);
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) raise_error(err, DFD_ERR_NONFINITE);
 }
 
 // Vector point loads need dim == DK in {2, 4, 8, 16} and aligned points
@@ -35,6 +31,25 @@ int vector_loads_ok(const void* points, int dim) {
   if (DK == 2) return a % 8 == 0;
   if (DK % 4 == 0) return a % 16 == 0;
   return 0;
+}
+
+// Largest |coordinate| of an int32 curve: |p_k - q_k| <= 2 * lim must keep
+// dim squares summing below 2^63 (and every difference in int32).
+inline long long int32_coord_limit(int dim) {
+  const double l = std::floor(std::sqrt((double)LLONG_MAX / (double)dim) / 2.0);
+  return std::min<long long>((1LL << 30) - 1, (long long)l);
+}
+
+// Per-curve bounding boxes (and, with input checks on, the coordinate
+// range check) of an int32 CSR batch.
+template <int DK>
+void launch_curve_bbox(dfd_context* ctx, const void* points, const int64_t* offsets, int64_t n_curves, int dim,
+                       int* bbox, cudaStream_t s) {
+  const int64_t warps_needed = n_curves;
+  const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((warps_needed + 7) / 8, 16 * (int64_t)ctx->num_sms));
+  batch::curve_bbox_kernel<DK><<<blocks, 256, 0, s>>>(static_cast<const int32_t*>(points), offsets, n_curves, dim,
+                                                      vector_loads_ok<DK>(points, dim), ctx->opt.check_inputs ? 1 : 0,
+                                                      int32_coord_limit(dim), bbox, ctx->d_err);
 }
 
 template <class K>
@@ -54,18 +69,24 @@ dfd_status batch_launch(dfd_context* ctx, int dim, const void* points, const int
   constexpr int THREADS = 256;
   const int blocks = resident_blocks(ctx, batch::batch_kernel<V, DK>, THREADS);
   const size_t warps = (size_t)blocks * (THREADS / 32);
-  // scratch: [counter | hist | cursor] [bucket bytes] [worklist] [row buffers]
+  constexpr bool kInt = std::is_same<V, I32>::value;
+  if (n_pairs >= (int64_t)batch::kNarrowBit) return DFD_ERR_UNSUPPORTED;
+  // scratch: [counter | hist | cursor] [bucket] [worklist] [bbox] [row buffers]
   const size_t off_hist = 256, off_cursor = off_hist + batch::NBUCKET * 4;
   const size_t off_bucket = align_up(off_cursor + batch::NBUCKET * 4, 256);
-  const size_t off_work = align_up(off_bucket + (size_t)n_pairs, 256);
-  const size_t off_buf = align_up(off_work + (size_t)n_pairs * 4, 256);
+  const size_t off_work = align_up(off_bucket + (size_t)n_pairs * 2, 256);
+  const size_t off_bbox = align_up(off_work + (size_t)n_pairs * 4, 256);
+  const size_t off_buf = align_up(off_bbox + (kInt ? (size_t)n_curves * DK * 2 * 4 : 0), 256);
   const size_t total = off_buf + warps * batch::BUF_COLS * sizeof(T);
   dfd_status st = ensure_scratch(ctx, total);
   if (st != DFD_OK) return st;
   char* base = static_cast<char*>(ctx->scratch);
   cudaError_t e = cudaMemsetAsync(base, 0, off_bucket, s);
   if (e != cudaSuccess) return cuda_status(e);
-  if (ctx->opt.check_inputs) {
+  int* bbox = kInt ? reinterpret_cast<int*>(base + off_bbox) : nullptr;
+  if constexpr (kInt) {
+    launch_curve_bbox<DK>(ctx, points, offsets, n_curves, dim, bbox, s);
+  } else if (ctx->opt.check_inputs) {
     check_points_kernel<V><<<std::min(4 * ctx->num_sms, 1024), 256, 0, s>>>(
         static_cast<const typename V::coord*>(points), offsets + n_curves, dim, ctx->d_err);
   }
@@ -76,8 +97,10 @@ dfd_status batch_launch(dfd_context* ctx, int dim, const void* points, const int
   pa.n_curves = n_curves;
   pa.hist = reinterpret_cast<unsigned*>(base + off_hist);
   pa.cursor = reinterpret_cast<unsigned*>(base + off_cursor);
-  pa.bucket = reinterpret_cast<unsigned char*>(base + off_bucket);
+  pa.bucket = reinterpret_cast<unsigned short*>(base + off_bucket);
   pa.worklist = reinterpret_cast<unsigned*>(base + off_work);
+  pa.bbox = bbox;
+  pa.dk = DK;
   pa.err = ctx->d_err;
   pa.rmax = batch::Rmax<DK>::value;
   const int pblocks = (int)std::min<int64_t>((n_pairs + 255) / 256, 8 * (int64_t)ctx->num_sms);
@@ -111,14 +134,19 @@ dfd_status matrix_launch(dfd_context* ctx, int dim, const void* points, const in
   constexpr int THREADS = 256;
   const int blocks = resident_blocks(ctx, batch::matrix_kernel<V, DK>, THREADS);
   const size_t warps = (size_t)blocks * (THREADS / 32);
-  const size_t off_buf = 256;
+  constexpr bool kInt = std::is_same<V, I32>::value;
+  const size_t off_bbox = 256;
+  const size_t off_buf = align_up(off_bbox + (kInt ? (size_t)n_curves * DK * 2 * 4 : 0), 256);
   const size_t total = off_buf + warps * batch::BUF_COLS * sizeof(T);
   dfd_status st = ensure_scratch(ctx, total);
   if (st != DFD_OK) return st;
   char* base = static_cast<char*>(ctx->scratch);
   cudaError_t e = cudaMemsetAsync(base, 0, 256, s);
   if (e != cudaSuccess) return cuda_status(e);
-  if (ctx->opt.check_inputs) {
+  int* bbox = kInt ? reinterpret_cast<int*>(base + off_bbox) : nullptr;
+  if constexpr (kInt) {
+    launch_curve_bbox<DK>(ctx, points, offsets, n_curves, dim, bbox, s);
+  } else if (ctx->opt.check_inputs) {
     check_points_kernel<V><<<std::min(4 * ctx->num_sms, 1024), 256, 0, s>>>(
         static_cast<const typename V::coord*>(points), offsets + n_curves, dim, ctx->d_err);
   }
@@ -131,6 +159,7 @@ dfd_status matrix_launch(dfd_context* ctx, int dim, const void* points, const in
   ma.dim = dim;
   ma.vec = vector_loads_ok<DK>(points, dim);
   ma.chunk = chunk > 0 ? chunk : 8;
+  ma.bbox = bbox;
   ma.counter = reinterpret_cast<int*>(base);
   ma.err = ctx->d_err;
   ma.out_dist = out_dist;

@@ -102,14 +102,12 @@ __global__ void check_f32_kernel(const float* x, int64_t count, int* err) {
   if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) raise_error(err, DFD_ERR_NONFINITE);
 }
 
-__global__ void check_i32_kernel(const int32_t* x, int64_t count, int dim, int* err) {
-  // |c| <= 2^30 - 1 and dim * (2 max|c|)^2 <= 2^63 - 1
-  const long long lim30 = (1LL << 30) - 1;
-  const double lim = sqrt((double)LLONG_MAX / (double)dim) / 2.0;
+__global__ void check_i32_kernel(const int32_t* x, int64_t count, long long lim, int* err) {
+  // |c| <= lim = min(2^30 - 1, sqrt((2^63 - 1) / dim) / 2), computed on the host
   bool bad = false;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
     const long long v = x[i] < 0 ? -(long long)x[i] : (long long)x[i];
-    bad |= v > lim30 || (double)v > lim;
+    bad |= v > lim;
   }
   if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) raise_error(err, DFD_ERR_RANGE);
 }
@@ -121,7 +119,10 @@ dfd_status launch_check_inputs(dfd_dtype dtype, int dim, const void* x, int64_t 
   if (dtype == DFD_F32)
     check_f32_kernel<<<blocks, threads, 0, s>>>(static_cast<const float*>(x), count, err);
   else
-    check_i32_kernel<<<blocks, threads, 0, s>>>(static_cast<const int32_t*>(x), count, dim, err);
+    check_i32_kernel<<<blocks, threads, 0, s>>>(
+        static_cast<const int32_t*>(x), count,
+        std::min<long long>((1LL << 30) - 1, (long long)std::floor(std::sqrt((double)LLONG_MAX / (double)dim) / 2.0)),
+        err);
   return cuda_status(cudaGetLastError());
 }
 

@@ -7,6 +7,7 @@
 #pragma once
 #include <cstdint>
 #include <climits>
+#include <type_traits>
 #include <cuda_runtime.h>
 
 #include "dfd_status.h"
@@ -42,6 +43,34 @@ struct I32 {
   __device__ __forceinline__ static value vmin3(value a, value b, value c) { return vmin(vmin(a, b), c); }
 };
 
+// I32B: int32 coordinates whose squared distances are known (from the
+// pair's bounding boxes) to stay below 0x7F800000.  The squared distance is
+// computed exactly in uint32 and carried as the float with those bits: for
+// such non-negative patterns the float order is the integer order, so the
+// recurrence (pure selection) runs on float min/max (full rate, 3-input
+// min) and returns the exact int64 value's bit pattern.  +inf (0x7F800000)
+// is above every value.
+struct I32B {
+  using coord = int32_t;
+  using value = float;
+  __device__ __forceinline__ static value inf() { return __int_as_float(0x7f800000); }
+  __device__ __forceinline__ static value ninf() { return __int_as_float(0xff800000); }
+  __device__ __forceinline__ static value zero() { return 0.0f; }
+  __device__ __forceinline__ static value vmin(value a, value b) { return fminf(a, b); }
+  __device__ __forceinline__ static value vmax(value a, value b) { return fmaxf(a, b); }
+  __device__ __forceinline__ static value vmin3(value a, value b, value c) {
+    value r;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+  }
+};
+
+// Largest bounding-box range per coordinate (and sum of squared ranges) for
+// which a pair may use I32B: every |p_k - q_k| <= 46340 keeps each square in
+// int32 and the sum below the first NaN pattern.
+constexpr unsigned kI32BMaxRange = 46340u;
+constexpr unsigned long long kI32BMaxD2 = 0x7f7fffffull;
+
 // ---------------------------------------------------------- ground distance
 // Squared Euclidean distance.  float32: t_k = p_k - q_k rounded, then
 // acc = t_0*t_0, acc = fma(t_k, t_k, acc) for k = 1..D-1, each op rounded to
@@ -70,6 +99,23 @@ __device__ __forceinline__ long long dist2(const int32_t* p, const int32_t* q) {
     acc += (long long)u * (long long)u;
   }
   return acc;
+}
+
+// Squared distance in the value type of V (F32: float, I32: exact int64,
+// I32B: exact uint32 bits as a float).
+template <class V, int D>
+__device__ __forceinline__ typename V::value vdist2(const typename V::coord* p, const typename V::coord* q) {
+  if constexpr (std::is_same<V, I32B>::value) {
+    unsigned acc = 0;
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      const unsigned t = (unsigned)(p[k] - q[k]);
+      acc += t * t;   // |p_k - q_k| <= 46340: each square < 2^31, the sum < 0x7F800000
+    }
+    return __uint_as_float(acc);
+  } else {
+    return dist2<D>(p, q);
+  }
 }
 
 // Packed float32x2 arithmetic (two independent lanes in one 64-bit register),

@@ -65,6 +65,75 @@ def test_batch_int_edges(dctx, dim):
     assert np.array_equal(d2, ref), np.nonzero(d2 != ref)[0][:10]
 
 
+def value_class_batch(dim, seed):
+    """int32 pairs on both sides of the exact-uint32 class bound: union
+    bounding boxes with one coordinate range near 46340 (int64 class: its
+    square alone passes the bound), squared ranges summing just below /
+    above 0x7F7FFFFF, wide curves (|c| near 2^28) that only the int64 path
+    can take, and ordinary narrow pairs of one or several row stripes."""
+    rng = np.random.default_rng(seed)
+    curves, pairs = [], []
+
+    def walk(n, step, start):
+        return (np.cumsum(rng.integers(-step, step + 1, size=(n, dim)), axis=0) + start).astype(np.int64)
+
+    def add_pair(a, b):
+        pairs.append((len(curves), len(curves) + 1))
+        curves.extend([a, b])
+
+    for span in (46339, 46340, 46341, 46342):
+        for n, m in ((40, 70), (300, 33), (513, 257)):
+            a = walk(n, 50, 0)
+            b = walk(m, 50, 0)
+            a[0, 0], b[-1, 0] = -span // 2, span - span // 2   # fixes the union range of coordinate 0
+            a[:, 0] = np.clip(a[:, 0], -span // 2, span - span // 2)
+            b[:, 0] = np.clip(b[:, 0], -span // 2, span - span // 2)
+            add_pair(a, b)
+    # sum of squared ranges around the limit (each range < 46340)
+    r = int(math.isqrt(0x7F7FFFFF // dim))
+    for delta in (-1, 0, 1, 2):
+        a = walk(64, 20, 0)
+        b = walk(96, 20, 0)
+        for k in range(dim):
+            lo, hi = -(r // 2), r - r // 2 + (delta if k == 0 else 0)
+            a[:, k] = np.clip(a[:, k], lo, hi)
+            b[:, k] = np.clip(b[:, k], lo, hi)
+            a[0, k], b[-1, k] = lo, hi
+        add_pair(a, b)
+    for n, m in ((50, 60), (400, 700)):
+        add_pair(walk(n, 1 << 20, 1 << 28), walk(m, 1 << 20, -(1 << 28)))
+    # ordinary narrow pairs, one and several row stripes
+    for n, m in ((1, 5), (32, 33), (257, 300), (600, 900), (1000, 40)):
+        add_pair(walk(n, 64, 0), walk(m, 64, 0))
+    lens = np.array([len(c) for c in curves], np.int64)
+    off = np.zeros(len(curves) + 1, np.int64)
+    np.cumsum(lens, out=off[1:])
+    pts = np.concatenate(curves).astype(np.int32)
+    return workloads.Batch(points=pts, offsets=off, pairs=np.array(pairs, np.int32))
+
+
+@pytest.mark.parametrize("dim", [1, 2, 3, 4])
+def test_batch_int_value_classes_bit_exact(dctx, dim):
+    """Pairs on both sides of the uint32-bits class bound (and far beyond)
+    give the int64 oracle's values bit for bit, through the batch and the
+    matrix entry points."""
+    b = value_class_batch(dim, 30 + dim)
+    ref, _ = oracle.batch(b.points, b.offsets, b.pairs)
+    d, d2 = run_batch(dctx, b)
+    assert np.array_equal(d2, ref), np.nonzero(d2 != ref)[0][:10]
+    assert np.all(d == np.sqrt(ref.astype(np.float64)))
+    # the matrix over the last 24 curves mixes both classes
+    nc = 24
+    c0 = len(b.offsets) - 1 - nc
+    sub = workloads.Batch(points=b.points[b.offsets[c0]:], offsets=b.offsets[c0:] - b.offsets[c0],
+                          pairs=np.zeros((0, 2), np.int32))
+    md, md2 = dctx.matrix(dev(sub.points), dev(sub.offsets))
+    torch.cuda.synchronize()
+    iu = np.triu_indices(nc, 1)
+    want, _ = oracle.batch(sub.points, sub.offsets, np.stack(iu, 1).astype(np.int32))
+    assert np.array_equal(md2.cpu().numpy(), want)
+
+
 @pytest.mark.parametrize("dim", [2, 3, 5, 8, 16])
 def test_batch_float_edges(dctx, dim):
     b = ragged_edges("f32", dim, 90 + dim)
