@@ -335,6 +335,8 @@ dfd_status dfd_timing_last(dfd_context* ctx, double* ms);
  *  11 min.f32   12 min3 -> max (one cell of the recurrence's chain)
  *  13 shfl.sync.up   14 fma.f32x2   15 min.s64 -> max.s64
  *  16 one float32 16-D cell (scalar: 16 sub + 16 mul/fma + min3 + max)
+ *  17 one int32 2-D cell carried as uint32 bits (2 sub, mul.lo, mad.lo,
+ *     3-input float min + float max), cells / clock / SM
  * Synchronous.  DFD_ERR_INVALID_ARG for an unknown op.
  */
 dfd_status dfd_microbench(dfd_context* ctx, int op, double* per_clk_per_sm, double* sm_mhz);

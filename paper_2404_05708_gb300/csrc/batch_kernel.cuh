@@ -18,10 +18,16 @@ namespace dfd {
 namespace batch {
 
 // Rows per lane of one stripe is at most RMAX (fewer registers for wider
-// points); pairs with more rows run several stripes.
+// points: a lane's R rows form one dependent chain per step, so wide points
+// keep R small and occupancy at two 256-thread CTAs per SM); pairs with
+// more rows run several stripes.
 template <int DK>
 struct Rmax {
   static constexpr int value = DK <= 4 ? 8 : (DK <= 8 ? 4 : 2);
+};
+template <int DK>
+struct kBlocksPerSM {
+  static constexpr int value = 2;
 };
 constexpr int BUF_COLS = 4096;    // per-warp row buffer (columns) for multi-stripe pairs
 
@@ -367,7 +373,7 @@ struct BatchArgs {
 };
 
 template <class V, int DK>
-__global__ void __launch_bounds__(256, 2) batch_kernel(BatchArgs a) {
+__global__ void __launch_bounds__(256, kBlocksPerSM<DK>::value) batch_kernel(BatchArgs a) {
   using T = typename V::value;
   using Cd = typename V::coord;
   const int L = threadIdx.x & 31;
@@ -444,7 +450,7 @@ struct MatrixArgs {
 };
 
 template <class V, int DK>
-__global__ void __launch_bounds__(256, 2) matrix_kernel(MatrixArgs a) {
+__global__ void __launch_bounds__(256, kBlocksPerSM<DK>::value) matrix_kernel(MatrixArgs a) {
   using T = typename V::value;
   using Cd = typename V::coord;
   const int L = threadIdx.x & 31;

@@ -39,7 +39,8 @@ enum MicroOp {
   MB_LAT_FFMA2 = 14,       // latency: dependent fma.f32x2 chain
   MB_LAT_MNMX64 = 15,      // latency: dependent min.s64 -> max.s64 (int cell chain)
   MB_MIX_F32D16 = 16,      // one float32 16-D cell: 16 sub + 16 fma/mul + min3 + max (scalar)
-  MB_COUNT = 17
+  MB_MIX_I32B_D2 = 17,     // one int32 2-D cell in uint32 bits: 2 sub, mul.lo, mad.lo, min3.f32 + max.f32
+  MB_COUNT = 18
 };
 
 __host__ __device__ constexpr bool is_latency(int op) { return op >= MB_LAT_FMNMX && op <= MB_LAT_MNMX64; }
@@ -143,6 +144,16 @@ __global__ void __launch_bounds__(MB_THREADS) micro_kernel(float seed, unsigned 
           asm volatile("max.f32 %0, %0, %1;" : "+f"(f[k]) : "f"(lo));
           asm volatile("min.f32 %0, %0, %1, %2;" : "+f"(f[(k + 4) & 7]) : "f"(c1), "f"(c2));
           asm volatile("max.f32 %0, %0, %1;" : "+f"(f[(k + 4) & 7]) : "f"(hi));
+        } else if constexpr (OP == MB_MIX_I32B_D2) {
+          int dx, dy;
+          unsigned d2;
+          asm volatile("sub.s32 %0, %1, %2;" : "=r"(dx) : "r"(iv[k]), "r"(it));
+          asm volatile("sub.s32 %0, %1, %2;" : "=r"(dy) : "r"(iv[(k + 1) & 7]), "r"(it));
+          iv[k] = dy;
+          asm volatile("mul.lo.u32 %0, %1, %1;" : "=r"(d2) : "r"(dx));
+          asm volatile("mad.lo.u32 %0, %1, %1, %0;" : "+r"(d2) : "r"(dy));
+          asm volatile("min.f32 %0, %0, %1, %2;" : "+f"(f[k]) : "f"(f[(k + 1) & 7]), "f"(f[(k + 2) & 7]));
+          asm volatile("max.f32 %0, %0, %1;" : "+f"(f[k]) : "f"(__uint_as_float(d2)));
         } else if constexpr (OP == MB_MIX_I32D2) {
           long long d2;
           int dx, dy;
@@ -248,6 +259,7 @@ extern "C" dfd_status dfd_microbench(dfd_context* ctx, int op, double* result, d
     case MB_LAT_FFMA2: return run_op<MB_LAT_FFMA2>(ctx, result, sm_mhz);
     case MB_LAT_MNMX64: return run_op<MB_LAT_MNMX64>(ctx, result, sm_mhz);
     case MB_MIX_F32D16: return run_op<MB_MIX_F32D16>(ctx, result, sm_mhz);
+    case MB_MIX_I32B_D2: return run_op<MB_MIX_I32B_D2>(ctx, result, sm_mhz);
     default: return DFD_ERR_INVALID_ARG;
   }
 }

@@ -43,7 +43,7 @@ struct Item {
 };
 
 template <int DK>
-__global__ void __launch_bounds__(256, 2) serve_kernel(const Item* items, int n_items, int dim, int vec,
+__global__ void __launch_bounds__(256, batch::kBlocksPerSM<DK>::value) serve_kernel(const Item* items, int n_items, int dim, int vec,
                                                        int* counter, float* out) {
   const int L = threadIdx.x & 31;
   for (;;) {
