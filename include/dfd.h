@@ -156,6 +156,55 @@ dfd_status dfd_batch(dfd_context* ctx, dfd_dtype dtype, int dim, const void* poi
                      void* stream);
 
 /*
+ * Threshold decision for many pairs (the decision form of the problem,
+ * Sec. 2: is delta(p, q) <= eps?) with early abandon.  M never decreases
+ * along a monotone path's prefix bottleneck, so delta^2 >= min of M over any
+ * set of cells every path must enter; once such a set of the running
+ * recurrence exceeds eps^2 the pair is abandoned (the heuristics that avoid
+ * full computations, Sec. 5).  Same inputs, engine and limits as dfd_batch,
+ * plus:
+ *   eps2:       per-pair squared thresholds, device (float for DFD_F32,
+ *               int64 for DFD_I32), or NULL to use eps2_all for every pair
+ *               (compared as: float32 delta^2 <= the largest float <=
+ *               eps2_all; int32 delta^2 <= floor(eps2_all)).
+ *   out_dist2:  n_pairs, the exact delta^2 of pairs computed to the end,
+ *               +inf (float) / INT64_MAX (int64) for abandoned ones; may be
+ *               NULL if out_within is given.
+ *   out_within: int32[n_pairs], 1 if delta^2 <= eps^2 else 0; may be NULL.
+ *   abandoned:  device uint64 counter incremented per abandoned pair; may
+ *               be NULL.
+ * Ties (delta^2 == eps^2) are never abandoned.
+ */
+dfd_status dfd_batch_decide(dfd_context* ctx, dfd_dtype dtype, int dim, const void* points, const int64_t* offsets,
+                            int64_t n_curves, const int32_t* pairs, int64_t n_pairs, const void* eps2,
+                            double eps2_all, void* out_dist2, int32_t* out_within, unsigned long long* abandoned,
+                            void* stream);
+
+/*
+ * Exact k nearest neighbours of one query curve among candidate curves
+ * (float32), by discrete Frechet distance, with early abandon: a candidate
+ * stops as soon as a cut of its running recurrence exceeds the current
+ * k-th best delta^2 (see dfd_batch_decide), so only the survivors are
+ * computed to the end.
+ *   query:     n x dim float32, device.
+ *   points / offsets / n_curves: candidate curves, CSR as for dfd_batch.
+ *   cand:      int32[n_cand] candidate curve ids, device, or NULL to use
+ *              curves 0 .. n_cand-1.
+ *   k:         1 .. 1024.
+ *   out_ids:   int32[k] candidate curve ids, ascending by (delta^2, position
+ *              in cand), -1 past n_cand; out_dist2 / out_dist: float[k]
+ *              delta^2 / delta (+inf past n_cand).  Any may be NULL, not all.
+ *   abandoned: device uint64, set to the number of abandoned candidates
+ *              (may be NULL).
+ * The results equal the k smallest of the exact float32 delta^2 of every
+ * candidate, ties broken by position.  Invalid ids / empty candidates set
+ * DFD_ERR_INVALID_ARG in the error word and are skipped.
+ */
+dfd_status dfd_knn(dfd_context* ctx, int dim, const float* query, int64_t n, const float* points,
+                   const int64_t* offsets, int64_t n_curves, const int32_t* cand, int64_t n_cand, int k,
+                   int32_t* out_ids, float* out_dist2, float* out_dist, unsigned long long* abandoned, void* stream);
+
+/*
  * All-pairs distance matrix of n_curves curves (the paper's motivating use:
  * clustering and distance matrices of trajectories, Sec. 2), condensed upper
  * triangle: entry k = i*(2N - i - 1)/2 + (j - i - 1) for i < j (N =

@@ -87,11 +87,52 @@ __device__ __forceinline__ void load_point(const Cd* __restrict__ Q, int j, int 
 // O(m) row state that lets a long pair pause between serving ticks (row i of
 // the recurrence summarises rows 1..i, Sec. 3).  Returns delta^2 when the
 // last stripe ran, +inf otherwise.
-template <class V, int DK, int R>
+// Early abandon (decider and k-NN forms).  Along any monotone path the
+// bottleneck of its prefix ending at a cell is at least M of that cell, so
+// delta >= min over any set of cells that every path from (0,0) to
+// (n-1,m-1) must enter.  After each 32-step block of a single-stripe pair
+// the lanes' current cells (one column per lane, lane L at column s - L)
+// together with, for each lane, the left neighbour of the upper lane's
+// bottom cell (the lane's `upp`, which a diagonal step could otherwise slip
+// past) form such a set while lane 0 has not passed the last column: a path
+// starts left of it in row 0 and must reach column m-1 in the last row.  A
+// pair whose minimum there exceeds the limit has delta^2 above it and is
+// abandoned; ties never abandon.  (One stripe of a taller pair is not such
+// a set: a path may pass left of it and leave through the stripe's bottom
+// row, so multi-stripe pairs are always computed to the end.)
+template <class V>
+struct NoAbandon {
+  static constexpr bool on = false;
+  bool hit = false;
+  __device__ __forceinline__ typename V::value limit() const { return V::inf(); }
+};
+
+// A fixed limit, or one read (lane 0, relaxed, broadcast) from device memory
+// each time it is checked: the k-NN search lowers it while warps run.
+template <class V>
+struct AbandonAbove {
+  static constexpr bool on = true;
+  typename V::value fixed;
+  const unsigned* live_bits;   // k-NN: current limit as float bits (float values only), else null
+  bool hit = false;
+  __device__ __forceinline__ typename V::value limit() const {
+    if constexpr (sizeof(typename V::value) == 4) {
+      if (live_bits) {
+        unsigned b = 0;
+        if ((threadIdx.x & 31) == 0) b = (unsigned)ld_relaxed_i32(reinterpret_cast<const int*>(live_bits));
+        b = __shfl_sync(0xffffffffu, b, 0);
+        return __uint_as_float(b);
+      }
+    }
+    return fixed;
+  }
+};
+
+template <class V, int DK, int R, class AB = NoAbandon<V>>
 __device__ __forceinline__ typename V::value warp_dfd(const typename V::coord* __restrict__ P, int n,
                                                       const typename V::coord* __restrict__ Q, int m, int dim,
                                                       bool vec, typename V::value* buf, int L, int st_begin = 0,
-                                                      int st_end = 1 << 30) {
+                                                      int st_end = 1 << 30, AB* ab = nullptr) {
   using T = typename V::value;
   using Cd = typename V::coord;
   const int nstripes = (n + 32 * R - 1) / (32 * R);
@@ -152,21 +193,35 @@ __device__ __forceinline__ typename V::value warp_dfd(const typename V::coord* _
         if (oc >= 0 && oc < m) buf[oc] = out_blk;
       }
       __syncwarp();
+      if constexpr (AB::on) {
+        // (a cut of the whole grid only when this stripe is the whole grid)
+        if (!has_top && !has_bottom && c0 + 31 <= m - 1) {
+          T cut = upp;
+#pragma unroll
+          for (int r = 0; r < R; ++r) cut = V::vmin(cut, v[r]);
+#pragma unroll
+          for (int off = 16; off > 0; off >>= 1) cut = V::vmin(cut, __shfl_xor_sync(0xffffffffu, cut, off));
+          if (cut > ab->limit()) {
+            ab->hit = true;
+            return V::inf();
+          }
+        }
+      }
     }
   }
   return __shfl_sync(0xffffffffu, res, 31);
 }
 
-template <class V, int DK>
+template <class V, int DK, class AB = NoAbandon<V>>
 __device__ __forceinline__ typename V::value warp_dfd_any(const typename V::coord* P, int n,
                                                           const typename V::coord* Q, int m, int dim, bool vec,
                                                           typename V::value* buf, int L, int st_begin = 0,
-                                                          int st_end = 1 << 30) {
+                                                          int st_end = 1 << 30, AB* ab = nullptr) {
   constexpr int RM = Rmax<DK>::value;
   switch (rows_per_lane<DK>(n)) {
-#define DFD_B_CASE(RR)                                                                                 \
-  case RR:                                                                                             \
-    if constexpr (RR < RM) return warp_dfd<V, DK, RR>(P, n, Q, m, dim, vec, buf, L, st_begin, st_end); \
+#define DFD_B_CASE(RR)                                                                                       \
+  case RR:                                                                                                   \
+    if constexpr (RR < RM) return warp_dfd<V, DK, RR, AB>(P, n, Q, m, dim, vec, buf, L, st_begin, st_end, ab); \
     break;
     DFD_B_CASE(1)
     DFD_B_CASE(2)
@@ -179,7 +234,7 @@ __device__ __forceinline__ typename V::value warp_dfd_any(const typename V::coor
       break;
 #undef DFD_B_CASE
   }
-  return warp_dfd<V, DK, RM>(P, n, Q, m, dim, vec, buf, L, st_begin, st_end);
+  return warp_dfd<V, DK, RM, AB>(P, n, Q, m, dim, vec, buf, L, st_begin, st_end, ab);
 }
 
 // Number of stripes warp_dfd_any uses for a pair with `rows` rows.
@@ -415,6 +470,107 @@ __global__ void __launch_bounds__(256, kBlocksPerSM<DK>::value) batch_kernel(Bat
     }
     const T r = warp_dfd_any<V, DK>(pts + oa * a.dim, n, pts + ob * a.dim, m, a.dim, a.vec != 0, buf, L);
     if (L == 0) write_result<V>(a.out_dist, a.out_dist2, k, r);
+  }
+}
+
+// ----------------------------------------------------------- decider kernel
+// Threshold decision per pair: within[k] = (delta^2 <= eps2_k), with early
+// abandon once a cut of the recurrence exceeds eps2_k.  dist2[k] is the
+// exact delta^2 of pairs computed to the end and +inf (float) / INT64_MAX
+// (int32) for abandoned ones.
+struct DecideArgs {
+  BatchArgs b;
+  const void* eps2;        // per pair (float / int64), or null: eps2_f / eps2_i for all
+  float eps2_f;
+  long long eps2_i;
+  int* within;             // [n_pairs] 1 / 0 (may be null)
+  unsigned long long* abandoned;   // pairs abandoned (may be null)
+};
+
+// The limit in the value domain of the uint32-bits class.
+__device__ __forceinline__ float bits_limit(long long e) {
+  if (e < 0) return __int_as_float(0xff800000);
+  if (e >= 0x7f800000LL) return __int_as_float(0x7f800000);
+  return __uint_as_float((unsigned)e);
+}
+
+template <class V, int DK>
+__global__ void __launch_bounds__(256, kBlocksPerSM<DK>::value) decide_kernel(DecideArgs d) {
+  using T = typename V::value;
+  using Cd = typename V::coord;
+  const BatchArgs& a = d.b;
+  const int L = threadIdx.x & 31;
+  const int64_t gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  T* buf = static_cast<T*>(a.rowbuf) + gw * BUF_COLS;
+  const Cd* pts = static_cast<const Cd*>(a.points);
+  const int64_t total = a.offsets[a.n_curves];
+  if (ld_relaxed_i32(a.err) != 0) return;
+  for (;;) {
+    int item = 0;
+    if (L == 0) item = atomicAdd(a.counter, 1);
+    item = __shfl_sync(0xffffffffu, item, 0);
+    if (item >= a.n_items) break;
+    const unsigned w = a.worklist[item];
+    const int64_t k = w & (kNarrowBit - 1);
+    int32_t ia = a.pairs[2 * k], ib = a.pairs[2 * k + 1];
+    if (w >> 31) {
+      const int32_t t = ia;
+      ia = ib;
+      ib = t;
+    }
+    if (ia < 0 || ib < 0 || ia >= a.n_curves || ib >= a.n_curves) continue;
+    const int64_t oa = a.offsets[ia], ob = a.offsets[ib];
+    const int64_t ea = a.offsets[ia + 1], eb = a.offsets[ib + 1];
+    if (oa < 0 || ob < 0 || ea > total || eb > total) continue;
+    const int n = (int)(ea - oa), m = (int)(eb - ob);
+    if (n < 1 || m < 1) continue;
+    if (!fits_buffer<DK>(n, m)) {
+      if (L == 0) raise_error(a.err, DFD_ERR_UNSUPPORTED);
+      continue;
+    }
+    bool hit = false, within = false;
+    long long exact = 0;
+    float exact_f = 0.f;
+    if constexpr (std::is_same<V, F32>::value) {
+      AbandonAbove<F32> ab;
+      ab.fixed = d.eps2 ? static_cast<const float*>(d.eps2)[k] : d.eps2_f;
+      ab.live_bits = nullptr;
+      const float r = warp_dfd_any<F32, DK, AbandonAbove<F32>>(pts + oa * a.dim, n, pts + ob * a.dim, m, a.dim,
+                                                               a.vec != 0, buf, L, 0, 1 << 30, &ab);
+      hit = ab.hit;
+      exact_f = r;
+      within = !hit && r <= ab.fixed;
+    } else {
+      const long long e = d.eps2 ? static_cast<const long long*>(d.eps2)[k] : d.eps2_i;
+      if (w & kNarrowBit) {
+        AbandonAbove<I32B> ab;
+        ab.fixed = bits_limit(e);
+        ab.live_bits = nullptr;
+        const float r = warp_dfd_any<I32B, DK, AbandonAbove<I32B>>(pts + oa * a.dim, n, pts + ob * a.dim, m, a.dim,
+                                                                   a.vec != 0, reinterpret_cast<float*>(buf), L, 0,
+                                                                   1 << 30, &ab);
+        hit = ab.hit;
+        exact = (long long)__float_as_uint(r);
+      } else {
+        AbandonAbove<I32> ab;
+        ab.fixed = e;
+        ab.live_bits = nullptr;
+        exact = warp_dfd_any<I32, DK, AbandonAbove<I32>>(pts + oa * a.dim, n, pts + ob * a.dim, m, a.dim,
+                                                         a.vec != 0, buf, L, 0, 1 << 30, &ab);
+        hit = ab.hit;
+      }
+      within = !hit && exact <= e;
+    }
+    if (L == 0) {
+      if (d.within) d.within[k] = within ? 1 : 0;
+      if (a.out_dist2) {
+        if constexpr (std::is_same<V, F32>::value)
+          static_cast<float*>(a.out_dist2)[k] = hit ? __int_as_float(0x7f800000) : exact_f;
+        else
+          static_cast<long long*>(a.out_dist2)[k] = hit ? LLONG_MAX : exact;
+      }
+      if (hit && d.abandoned) atomicAdd(d.abandoned, 1ull);
+    }
   }
 }
 

@@ -62,12 +62,14 @@ int resident_blocks(const dfd_context* ctx, K kernel, int threads) {
   return per_sm * ctx->num_sms;
 }
 
+// Scratch, input checks (and int32 bounding boxes) and the device-built
+// LPT work list shared by the batch and decider kernels; `blocks` persistent
+// CTAs of 256 threads will run the work list.
 template <class V, int DK>
-dfd_status batch_launch(dfd_context* ctx, int dim, const void* points, const int64_t* offsets, int64_t n_curves,
-                        const int32_t* pairs, int64_t n_pairs, void* out_dist, void* out_dist2, cudaStream_t s) {
+dfd_status batch_prepare(dfd_context* ctx, int dim, const void* points, const int64_t* offsets, int64_t n_curves,
+                         const int32_t* pairs, int64_t n_pairs, cudaStream_t s, int blocks, batch::BatchArgs* ba) {
   using T = typename V::value;
   constexpr int THREADS = 256;
-  const int blocks = resident_blocks(ctx, batch::batch_kernel<V, DK>, THREADS);
   const size_t warps = (size_t)blocks * (THREADS / 32);
   constexpr bool kInt = std::is_same<V, I32>::value;
   if (n_pairs >= (int64_t)batch::kNarrowBit) return DFD_ERR_UNSUPPORTED;
@@ -107,22 +109,53 @@ dfd_status batch_launch(dfd_context* ctx, int dim, const void* points, const int
   batch::plan_hist_kernel<<<pblocks, 256, 0, s>>>(pa);
   batch::plan_scan_kernel<<<1, 32, 0, s>>>(pa);
   batch::plan_scatter_kernel<<<pblocks, 256, 0, s>>>(pa);
+  ba->rowbuf = base + off_buf;
+  ba->points = points;
+  ba->offsets = offsets;
+  ba->pairs = pairs;
+  ba->worklist = pa.worklist;
+  ba->n_items = n_pairs;
+  ba->n_curves = n_curves;
+  ba->dim = dim;
+  ba->vec = vector_loads_ok<DK>(points, dim);
+  ba->counter = reinterpret_cast<int*>(base);
+  ba->err = ctx->d_err;
+  ba->out_dist = nullptr;
+  ba->out_dist2 = nullptr;
+  return cuda_status(cudaGetLastError());
+}
+
+template <class V, int DK>
+dfd_status batch_launch(dfd_context* ctx, int dim, const void* points, const int64_t* offsets, int64_t n_curves,
+                        const int32_t* pairs, int64_t n_pairs, void* out_dist, void* out_dist2, cudaStream_t s) {
+  const int blocks = resident_blocks(ctx, batch::batch_kernel<V, DK>, 256);
   batch::BatchArgs ba;
-  ba.rowbuf = base + off_buf;
-  ba.points = points;
-  ba.offsets = offsets;
-  ba.pairs = pairs;
-  ba.worklist = pa.worklist;
-  ba.n_items = n_pairs;
-  ba.n_curves = n_curves;
-  ba.dim = dim;
-  ba.vec = vector_loads_ok<DK>(points, dim);
-  ba.counter = reinterpret_cast<int*>(base);
-  ba.err = ctx->d_err;
+  dfd_status st = batch_prepare<V, DK>(ctx, dim, points, offsets, n_curves, pairs, n_pairs, s, blocks, &ba);
+  if (st != DFD_OK) return st;
   ba.out_dist = out_dist;
   ba.out_dist2 = out_dist2;
   timing_begin(ctx, s);
-  batch::batch_kernel<V, DK><<<blocks, THREADS, 0, s>>>(ba);
+  batch::batch_kernel<V, DK><<<blocks, 256, 0, s>>>(ba);
+  timing_end(ctx, s);
+  return cuda_status(cudaGetLastError());
+}
+
+template <class V, int DK>
+dfd_status decide_launch(dfd_context* ctx, int dim, const void* points, const int64_t* offsets, int64_t n_curves,
+                         const int32_t* pairs, int64_t n_pairs, const void* eps2, double eps2_all, void* out_dist2,
+                         int32_t* out_within, unsigned long long* abandoned, cudaStream_t s) {
+  const int blocks = resident_blocks(ctx, batch::decide_kernel<V, DK>, 256);
+  batch::DecideArgs d;
+  dfd_status st = batch_prepare<V, DK>(ctx, dim, points, offsets, n_curves, pairs, n_pairs, s, blocks, &d.b);
+  if (st != DFD_OK) return st;
+  d.b.out_dist2 = out_dist2;
+  d.eps2 = eps2;
+  d.eps2_f = (float)eps2_all;
+  d.eps2_i = eps2_all >= 9.2e18 ? LLONG_MAX : (long long)std::floor(eps2_all);
+  d.within = out_within;
+  d.abandoned = abandoned;
+  timing_begin(ctx, s);
+  batch::decide_kernel<V, DK><<<blocks, 256, 0, s>>>(d);
   timing_end(ctx, s);
   return cuda_status(cudaGetLastError());
 }
@@ -175,5 +208,8 @@ dfd_status matrix_launch(dfd_context* ctx, int dim, const void* points, const in
 #define DFD_BATCH_INSTANTIATE(V, DK)                                                                              \
   template dfd_status dfd::batch_launch<dfd::V, DK>(dfd_context*, int, const void*, const int64_t*, int64_t,       \
                                                       const int32_t*, int64_t, void*, void*, cudaStream_t);        \
+  template dfd_status dfd::decide_launch<dfd::V, DK>(dfd_context*, int, const void*, const int64_t*, int64_t,      \
+                                                       const int32_t*, int64_t, const void*, double, void*, int32_t*, \
+                                                       unsigned long long*, cudaStream_t);                            \
   template dfd_status dfd::matrix_launch<dfd::V, DK>(dfd_context*, int, const void*, const int64_t*, int64_t, void*, \
                                                        void*, cudaStream_t, int);

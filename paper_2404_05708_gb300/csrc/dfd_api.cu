@@ -38,9 +38,16 @@ dfd_status batch_launch(dfd_context* ctx, int dim, const void* points, const int
 template <class V, int DK>
 dfd_status matrix_launch(dfd_context* ctx, int dim, const void* points, const int64_t* offsets, int64_t n_curves,
                          void* out_dist, void* out_dist2, cudaStream_t s, int chunk);
+template <class V, int DK>
+dfd_status decide_launch(dfd_context* ctx, int dim, const void* points, const int64_t* offsets, int64_t n_curves,
+                         const int32_t* pairs, int64_t n_pairs, const void* eps2, double eps2_all, void* out_dist2,
+                         int32_t* out_within, unsigned long long* abandoned, cudaStream_t s);
 #define DFD_BATCH_EXTERN(V, DK)                                                                              \
   extern template dfd_status batch_launch<V, DK>(dfd_context*, int, const void*, const int64_t*, int64_t,     \
                                                  const int32_t*, int64_t, void*, void*, cudaStream_t);        \
+  extern template dfd_status decide_launch<V, DK>(dfd_context*, int, const void*, const int64_t*, int64_t,    \
+                                                  const int32_t*, int64_t, const void*, double, void*,        \
+                                                  int32_t*, unsigned long long*, cudaStream_t);               \
   extern template dfd_status matrix_launch<V, DK>(dfd_context*, int, const void*, const int64_t*, int64_t,    \
                                                   void*, void*, cudaStream_t, int);
 DFD_BATCH_EXTERN(F32, 2)
@@ -225,6 +232,31 @@ dfd_status batch_run(dfd_context* ctx, dfd_dtype dtype, int dim, const void* poi
     DFD_B_DK(I32)
   }
 #undef DFD_B_DK
+}
+
+static dfd_status decide_run(dfd_context* ctx, dfd_dtype dtype, int dim, const void* points, const int64_t* offsets,
+                             int64_t n_curves, const int32_t* pairs, int64_t n_pairs, const void* eps2,
+                             double eps2_all, void* out_dist2, int32_t* within, unsigned long long* abandoned,
+                             cudaStream_t s) {
+#define DFD_D_CALL(V, DK) \
+  return decide_launch<V, DK>(ctx, dim, points, offsets, n_curves, pairs, n_pairs, eps2, eps2_all, out_dist2, within, \
+                              abandoned, s)
+#define DFD_D_DK(V)                \
+  switch (dim_class(dim)) {        \
+    case 2: DFD_D_CALL(V, 2);      \
+    case 3: DFD_D_CALL(V, 3);      \
+    case 4: DFD_D_CALL(V, 4);      \
+    case 8: DFD_D_CALL(V, 8);      \
+    case 16: DFD_D_CALL(V, 16);    \
+    default: return DFD_ERR_UNSUPPORTED; \
+  }
+  if (dtype == DFD_F32) {
+    DFD_D_DK(F32)
+  } else {
+    DFD_D_DK(I32)
+  }
+#undef DFD_D_DK
+#undef DFD_D_CALL
 }
 
 dfd_status matrix_run(dfd_context* ctx, dfd_dtype dtype, int dim, const void* points, const int64_t* offsets,
@@ -700,6 +732,28 @@ dfd_status dfd_batch(dfd_context* ctx, dfd_dtype dtype, int dim, const void* poi
   if ((st = set_device(ctx)) != DFD_OK) return st;
   return batch_run(ctx, dtype, dim, points, offsets, n_curves, pairs, n_pairs, out_dist, out_dist2,
                    static_cast<cudaStream_t>(stream));
+}
+
+dfd_status dfd_batch_decide(dfd_context* ctx, dfd_dtype dtype, int dim, const void* points, const int64_t* offsets,
+                            int64_t n_curves, const int32_t* pairs, int64_t n_pairs, const void* eps2,
+                            double eps2_all, void* out_dist2, int32_t* out_within, unsigned long long* abandoned,
+                            void* stream) {
+  dfd_status st = check_batch_args(ctx, dtype, dim, points, offsets, n_curves, out_within ? (void*)out_within : out_dist2,
+                                   out_dist2);
+  if (st != DFD_OK) return st;
+  if (!pairs || n_pairs < 0 || n_pairs > INT32_MAX) return DFD_ERR_INVALID_ARG;
+  if (!eps2 && std::isnan(eps2_all)) return DFD_ERR_INVALID_ARG;
+  if (n_pairs == 0) return DFD_OK;
+  if ((st = set_device(ctx)) != DFD_OK) return st;
+  double e = eps2_all;
+  if (dtype == DFD_F32 && !eps2 && std::isfinite(e)) {
+    // largest float <= eps2_all, so that (float) delta^2 <= it  <=>  delta^2 <= eps2_all
+    float f = (float)e;
+    if ((double)f > e) f = std::nextafter(f, -INFINITY);
+    e = (double)f;
+  }
+  return decide_run(ctx, dtype, dim, points, offsets, n_curves, pairs, n_pairs, eps2, e, out_dist2, out_within,
+                    abandoned, static_cast<cudaStream_t>(stream));
 }
 
 dfd_status dfd_matrix(dfd_context* ctx, dfd_dtype dtype, int dim, const void* points, const int64_t* offsets,

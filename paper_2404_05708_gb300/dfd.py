@@ -80,6 +80,8 @@ _SIGS = {
     "dfd_pair_noalloc": [_INT, _INT, _INT, _VP, _I64, _VP, _I64, _VP, _VP, _VP],
     "dfd_batch": [_VP, _INT, _INT, _VP, _VP, _I64, _VP, _I64, _VP, _VP, _VP],
     "dfd_matrix": [_VP, _INT, _INT, _VP, _VP, _I64, _VP, _VP, _VP],
+    "dfd_batch_decide": [_VP, _INT, _INT, _VP, _VP, _I64, _VP, _I64, _VP, ctypes.c_double, _VP, _VP, _VP, _VP],
+    "dfd_knn": [_VP, _INT, _VP, _I64, _VP, _VP, _I64, _VP, _I64, _INT, _VP, _VP, _VP, _VP, _VP],
     "dfd_batch_capture": [_VP, _INT, _INT, _VP, _VP, _I64, _VP, _I64, _VP, _VP, ctypes.POINTER(_VP)],
     "dfd_matrix_capture": [_VP, _INT, _INT, _VP, _VP, _I64, _VP, _VP, ctypes.POINTER(_VP)],
     "dfd_graph_launch": [_VP, _VP],
@@ -187,6 +189,18 @@ def dfd_batch(ctx, dtype, dim, points, offsets, n_curves, pairs, n_pairs, out_di
 
 def dfd_matrix(ctx, dtype, dim, points, offsets, n_curves, out_condensed, out_dist2, stream) -> int:
     return load_library().dfd_matrix(ctx, dtype, dim, points, offsets, n_curves, out_condensed, out_dist2, stream)
+
+
+def dfd_batch_decide(ctx, dtype, dim, points, offsets, n_curves, pairs, n_pairs, eps2, eps2_all, out_dist2,
+                     out_within, abandoned, stream) -> int:
+    return load_library().dfd_batch_decide(ctx, dtype, dim, points, offsets, n_curves, pairs, n_pairs, eps2,
+                                           float(eps2_all), out_dist2, out_within, abandoned, stream)
+
+
+def dfd_knn(ctx, dim, query, n, points, offsets, n_curves, cand, n_cand, k, out_ids, out_dist2, out_dist, abandoned,
+            stream) -> int:
+    return load_library().dfd_knn(ctx, dim, query, n, points, offsets, n_curves, cand, n_cand, k, out_ids, out_dist2,
+                                  out_dist, abandoned, stream)
 
 
 def dfd_batch_capture(ctx, dtype, dim, points, offsets, n_curves, pairs, n_pairs, out_dist, out_dist2) -> int:
@@ -513,6 +527,66 @@ class Context:
         s = stream if stream is not None else torch.cuda.current_stream(self.device).cuda_stream
         _check(dfd_batch(*args, s), "dfd_batch")
         return out_dist, out_dist2
+
+    def decide(self, points, offsets, pairs, eps2, out_dist2=None, out_within=None, stream=None):
+        """Threshold decision delta^2 <= eps2 per pair with early abandon.  eps2 is a
+        number (all pairs) or a device tensor (float32 / int64 per pair).
+        Returns (dist2, within, abandoned): exact delta^2 of pairs computed to
+        the end (+inf / INT64_MAX when abandoned), 0/1 flags, abandoned count."""
+        torch = _torch()
+        points = _curve(points)
+        dt = _dtype_code(points)
+        offsets, pairs = offsets.contiguous(), pairs.contiguous()
+        if offsets.dtype != torch.int64 or pairs.dtype != torch.int32:
+            raise TypeError("offsets must be int64 and pairs int32")
+        n_pairs = pairs.numel() // 2
+        dev = points.device
+        if out_dist2 is None:
+            out_dist2 = torch.empty(n_pairs, dtype=torch.float32 if dt == DFD_F32 else torch.int64, device=dev)
+        if out_within is None:
+            out_within = torch.empty(n_pairs, dtype=torch.int32, device=dev)
+        ab = torch.zeros(1, dtype=torch.int64, device=dev)
+        if isinstance(eps2, (int, float)):
+            eps_ptr, eps_all = None, float(eps2)
+        else:
+            want = torch.float32 if dt == DFD_F32 else torch.int64
+            eps2 = eps2.contiguous()
+            if eps2.dtype != want or eps2.numel() != n_pairs:
+                raise TypeError(f"eps2 must be {want} with one value per pair")
+            eps_ptr, eps_all = eps2.data_ptr(), 0.0
+        s = stream if stream is not None else torch.cuda.current_stream(self.device).cuda_stream
+        st = dfd_batch_decide(self.handle, dt, points.shape[1], points.data_ptr(), offsets.data_ptr(),
+                              offsets.numel() - 1, pairs.data_ptr(), n_pairs, eps_ptr, eps_all, out_dist2.data_ptr(),
+                              out_within.data_ptr(), ab.data_ptr(), s)
+        _check(st, "dfd_batch_decide")
+        return out_dist2, out_within, ab
+
+    def knn(self, query, points, offsets, k, cand=None, stream=None):
+        """k nearest candidates of a float32 query curve.  Returns (ids, dist2,
+        abandoned): int32[k], float32[k] ascending, device counter."""
+        torch = _torch()
+        query, points = _curve(query), _curve(points)
+        if query.dtype != torch.float32 or points.dtype != torch.float32 or query.shape[1] != points.shape[1]:
+            raise TypeError("query and candidates must be float32 curves of one dim")
+        offsets = offsets.contiguous()
+        if offsets.dtype != torch.int64:
+            raise TypeError("offsets must be int64")
+        n_curves = offsets.numel() - 1
+        if cand is not None:
+            cand = cand.contiguous()
+            if cand.dtype != torch.int32:
+                raise TypeError("cand must be int32")
+        n_cand = cand.numel() if cand is not None else n_curves
+        dev = points.device
+        ids = torch.empty(k, dtype=torch.int32, device=dev)
+        d2 = torch.empty(k, dtype=torch.float32, device=dev)
+        ab = torch.zeros(1, dtype=torch.int64, device=dev)
+        s = stream if stream is not None else torch.cuda.current_stream(self.device).cuda_stream
+        st = dfd_knn(self.handle, query.shape[1], query.data_ptr(), query.shape[0], points.data_ptr(),
+                     offsets.data_ptr(), n_curves, cand.data_ptr() if cand is not None else None, n_cand, int(k),
+                     ids.data_ptr(), d2.data_ptr(), None, ab.data_ptr(), s)
+        _check(st, "dfd_knn")
+        return ids, d2, ab
 
     def matrix(self, points, offsets, out_dist=None, out_dist2=None, stream=None, capture=False):
         """Condensed upper-triangle distance matrix of CSR curves."""
