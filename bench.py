@@ -65,7 +65,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="long", choices=["long", "batch", "matrix", "pair2k", "serve"])
+    ap.add_argument("--workload", default="long", choices=["long", "batch", "matrix", "pair2k", "serve", "knn"])
     ap.add_argument("--rates", default="100,300,1000,3000,10000")
     ap.add_argument("--serve-seconds", type=float, default=2.0)
     ap.add_argument("--n", type=int, default=N_POINTS)
@@ -415,7 +415,108 @@ class Matrix(_Many):
         return None
 
 
-WORKLOADS = {"long": LongPair, "pair2k": Pair2k, "batch": Batch, "matrix": Matrix}
+class Knn:
+    """Exact k-NN (k = 10) of a float32 2-D query curve among the 2^16-curve
+    serving pool, with early abandon; one query per step (8 queries cycled).
+    `value` counts every candidate's n*m cells (the work the search answers
+    for), so pruning shows as a higher rate; config holds the abandoned
+    fraction and the time dfd_batch needs to compute every distance."""
+    micro_op = "cell_f32_d3"
+    dtype = "f32"
+    launches_per_step = 5          # 2 input checks, init, search, sort
+
+    def __init__(self, args, ctx, dfd, torch, workloads, rank, world):
+        self.k = 10
+        pool = workloads.serving_pool(dim=2, seed=8)
+        qs = workloads.serving_pool(n_curves=8, dim=2, seed=99)
+        self.pool, self.qs = pool, qs
+        self.ctx, self.torch = ctx, torch
+        self.pts = torch.from_numpy(pool.points).cuda()
+        self.off = torch.from_numpy(pool.offsets).cuda()
+        self.q_host = [torch.from_numpy(qs.curve(i).copy()).pin_memory() for i in range(8)]
+        self.q_dev = [q.cuda() for q in self.q_host]
+        plen = int(pool.lengths().sum())
+        self.cells_q = [int(len(q)) * plen for q in self.q_host]
+        self.it = 0
+        self.cells = int(np.mean(self.cells_q))
+        # full computation of every distance for the same query (comparison)
+        allp = torch.cat([self.q_dev[0], self.pts])
+        allo = torch.cat([torch.zeros(1, dtype=torch.int64, device="cuda"), self.off + len(self.q_dev[0])])
+        pairs = torch.stack([torch.zeros(pool.n_curves, dtype=torch.int32),
+                             torch.arange(1, pool.n_curves + 1, dtype=torch.int32)], 1).cuda()
+        ctx.batch(allp, allo, pairs)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(True), torch.cuda.Event(True)
+        e0.record()
+        d, d2 = ctx.batch(allp, allo, pairs)
+        e1.record()
+        torch.cuda.synchronize()
+        self.full_ms = e0.elapsed_time(e1)
+        self.full_top = torch.sort(d2)[0][: self.k].cpu().numpy()
+        ids, kd2, ab = ctx.knn(self.q_dev[0], self.pts, self.off, self.k)
+        torch.cuda.synchronize()
+        self.ab_frac = int(ab.item()) / pool.n_curves
+        self.match_full = bool(np.array_equal(kd2.cpu().numpy(), self.full_top))
+        self.config = {"workload": "exact k-NN (k = 10) of a float32 2-D query among 2^16 resident Gaussian-walk "
+                                   "candidates, lognormal lengths median 256 (seeds 8, 99), early abandon",
+                       "k": self.k, "n_candidates": pool.n_curves, "cells_per_step": self.cells,
+                       "abandoned_fraction": round(self.ab_frac, 4),
+                       "full_batch_ms_same_query": round(self.full_ms, 3),
+                       "kernel_sha": kernel_sha(("batch_kernel.cuh", "knn.cu", "dfd_device.cuh"))}
+        self.h2d = int(self.q_host[0].numel() * 4)
+        self.d2h = self.k * 8
+
+    def step(self):
+        i = self.it % 8
+        self.it += 1
+        self.ctx.knn(self.q_dev[i], self.pts, self.off, self.k)
+
+    def e2e_step(self):
+        i = self.it % 8
+        self.it += 1
+        q = self.q_dev[i]
+        q.copy_(self.q_host[i], non_blocking=True)
+        ids, d2, _ = self.ctx.knn(q, self.pts, self.off, self.k)
+        return ids.cpu(), d2.cpu()
+
+    def verify(self):
+        # k-NN of query 1 among the first 2048 candidates against the oracle,
+        # and query 0's k-NN against the full GPU computation of all distances
+        import oracle
+        torch = self.torch
+        sub = 2048
+        cand = torch.arange(sub, dtype=torch.int32, device="cuda")
+        ids, d2, _ = self.ctx.knn(self.q_dev[1], self.pts, self.off, self.k, cand=cand)
+        qn = self.qs.curve(1)
+        allp = np.concatenate([qn, self.pool.points[: self.pool.offsets[sub]]])
+        allo = np.concatenate([[0], self.pool.offsets[: sub + 1] + len(qn)])
+        pairs = np.stack([np.zeros(sub, np.int32), np.arange(1, sub + 1, dtype=np.int32)], 1)
+        want, _ = oracle.batch(allp, allo, pairs, mirror=True)
+        order = np.lexsort((np.arange(sub), want))[: self.k]
+        ok = np.array_equal(ids.cpu().numpy(), order) and np.array_equal(d2.cpu().numpy(), want[order])
+        return bool(ok and self.match_full)
+
+    def cpu_baseline(self):
+        import oracle
+        qn = self.qs.curve(0)
+        sub = 64
+        allp = np.concatenate([qn, self.pool.points[: self.pool.offsets[sub]]])
+        allo = np.concatenate([[0], self.pool.offsets[: sub + 1] + len(qn)])
+        pairs = np.stack([np.zeros(sub, np.int32), np.arange(1, sub + 1, dtype=np.int32)], 1)
+        oracle.load()
+        t0 = time.perf_counter()
+        oracle.batch(allp, allo, pairs, nthreads=1)
+        dt = time.perf_counter() - t0
+        cells = len(qn) * int(self.pool.offsets[sub])
+        return {"value": cells / dt / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+                "sample": f"query 0 against the first {sub} candidates, all distances (no pruning), Alg. 5 float64, "
+                          f"one thread, {dt:.1f} s"}
+
+    def per_pair(self):
+        return None
+
+
+WORKLOADS = {"long": LongPair, "pair2k": Pair2k, "batch": Batch, "matrix": Matrix, "knn": Knn}
 
 
 def run_serving(args):

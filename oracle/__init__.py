@@ -74,6 +74,8 @@ def _declare(lib):
     lib.dfo_batch_i64.argtypes = [_I32P, _I64P, _I32P, c_i64, c_int, _I64P, c_int]
     lib.dfo_batch_f32mirror.restype = c_int
     lib.dfo_batch_f32mirror.argtypes = [_F32P, _I64P, _I32P, c_i64, c_int, _F32P, c_int]
+    lib.dfo_dtw_f32mirror.restype = ctypes.c_float
+    lib.dfo_dtw_f32mirror.argtypes = [_F32P, c_i64, _F32P, c_i64, c_int]
     lib.dfo_levenshtein.restype = ctypes.c_int64
     lib.dfo_levenshtein.argtypes = [_I32P, c_i64, _I32P, c_i64]
     return lib
@@ -161,6 +163,13 @@ def dtw(p, q, lib=None):
     lib = lib or load()
     p, q, _ = _prep(np.asarray(p, np.float32), np.asarray(q, np.float32))
     return float(lib.dfo_dtw_f64(_ptr(p, _F32P), p.shape[0], _ptr(q, _F32P), q.shape[0], p.shape[1]))
+
+
+def dtw_f32mirror(p, q, lib=None):
+    """DTW in float32, one rounding per cell (the GPU kernel's order)."""
+    lib = lib or load()
+    p, q, _ = _prep(np.asarray(p, np.float32), np.asarray(q, np.float32))
+    return float(lib.dfo_dtw_f32mirror(_ptr(p, _F32P), p.shape[0], _ptr(q, _F32P), q.shape[0], p.shape[1]))
 
 
 def levenshtein(a, b, lib=None):

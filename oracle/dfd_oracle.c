@@ -37,6 +37,7 @@
  *                   below); a selection check, not a precision reference
  *   dfo_batch_*     Alg. 5 over a list of (a, b) curve pairs, threaded
  *   dfo_dtw_*       the DTW variant of the appendix (max replaced by +)
+ *   dfo_dtw_f32mirror  DTW in float32, one rounding per cell (GPU selection mirror)
  *   dfo_levenshtein Wagner-Fischer edit distance (the appendix's third
  *                   variant; textbook definition, see DESIGN notes)
  *
@@ -443,6 +444,33 @@ double dfo_dtw_f64(const float* p, int64_t n, const float* q, int64_t m, int dim
         }
     }
     double r = v[m - 1];
+    free(v);
+    return r;
+}
+
+/*
+ * DTW in float32 with a fixed evaluation order, the selection mirror of the
+ * GPU kernel: the ground cost is d2_f32 (the squared-distance order above)
+ * and each cell is one float32 addition after an exact minimum,
+ * D_ij = fl(min(min(D_{i-1,j}, D_{i-1,j-1}), D_{i,j-1}) + c_ij).  Any
+ * evaluation order with one rounding per cell gives this value bit for bit.
+ */
+float dfo_dtw_f32mirror(const float* p, int64_t n, const float* q, int64_t m, int dim) {
+    float* v = (float*)malloc((size_t)m * sizeof(float));
+    if (!v) return -1.0f;
+    v[0] = d2_f32(p, q, dim);
+    for (int64_t j = 1; j < m; ++j) v[j] = v[j - 1] + d2_f32(p, q + j * dim, dim);
+    for (int64_t i = 1; i < n; ++i) {
+        const float* pi = p + i * dim;
+        float diag = v[0];
+        v[0] = v[0] + d2_f32(pi, q, dim);
+        for (int64_t j = 1; j < m; ++j) {
+            float up = v[j];
+            v[j] = fminf(fminf(up, diag), v[j - 1]) + d2_f32(pi, q + j * dim, dim);
+            diag = up;
+        }
+    }
+    float r = v[m - 1];
     free(v);
     return r;
 }

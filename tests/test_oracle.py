@@ -207,6 +207,36 @@ def test_dtw_bruteforce():
         assert oracle.dtw(p, q) == _dtw_brute(p, q)
 
 
+def test_dtw_f32mirror_exact_on_integers_and_bounded_otherwise():
+    """The float32 DTW mirror equals the float64 DTW (pinned by brute force
+    above) exactly when every value is an integer below 2^24, and is within
+    the summation bound otherwise: a path has at most n+m-1 non-negative
+    terms, each with dim+1 roundings, plus one rounding per addition."""
+    rng = np.random.default_rng(19)
+    for _ in range(40):
+        n, m = int(rng.integers(1, 40)), int(rng.integers(1, 40))
+        p = rand_int_curve(rng, n, 2).astype(np.float32)
+        q = rand_int_curve(rng, m, 2).astype(np.float32)
+        assert oracle.dtw_f32mirror(p, q) == oracle.dtw(p, q)
+    for dim in (1, 3, 16):
+        for _ in range(10):
+            n, m = int(rng.integers(1, 300)), int(rng.integers(1, 300))
+            p = np.cumsum(rng.normal(size=(n, dim)), 0).astype(np.float32)
+            q = np.cumsum(rng.normal(size=(m, dim)), 0).astype(np.float32)
+            ref = oracle.dtw(p, q)
+            bound = (n + m + dim + 2) * 2.0 ** -24 * ref
+            assert abs(oracle.dtw_f32mirror(p, q) - ref) <= bound
+
+
+def test_dtw_f32mirror_planted_mistake_is_caught():
+    """A DTW cell that kept the maximum of the Frechet recurrence instead of
+    the sum would not match: the mirror differs from the Frechet mirror."""
+    rng = np.random.default_rng(20)
+    p = rand_int_curve(rng, 12, 2).astype(np.float32)
+    q = rand_int_curve(rng, 9, 2).astype(np.float32)
+    assert oracle.dtw_f32mirror(p, q) > oracle.dfd2_f32mirror(p, q)
+
+
 def test_levenshtein_known_and_brute():
     enc = lambda s: np.array([ord(c) for c in s], np.int32)
     assert oracle.levenshtein(enc("kitten"), enc("sitting")) == 3
