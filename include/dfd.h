@@ -182,10 +182,12 @@ dfd_status dfd_batch_decide(dfd_context* ctx, dfd_dtype dtype, int dim, const vo
 
 /*
  * Exact k nearest neighbours of one query curve among candidate curves
- * (float32), by discrete Frechet distance, with early abandon: a candidate
- * stops as soon as a cut of its running recurrence exceeds the current
- * k-th best delta^2 (see dfd_batch_decide), so only the survivors are
- * computed to the end.
+ * (float32), by discrete Frechet distance, with early abandon: candidates
+ * are searched in ascending order of the endpoint bound max(d(p_1,q_1),
+ * d(p_n,q_m))^2 <= delta^2 (every coupling contains both end pairs), skipped
+ * when that bound exceeds the current k-th best, and otherwise stopped as
+ * soon as a cut of the running recurrence exceeds it (see
+ * dfd_batch_decide), so only the survivors are computed to the end.
  *   query:     n x dim float32, device.
  *   points / offsets / n_curves: candidate curves, CSR as for dfd_batch.
  *   cand:      int32[n_cand] candidate curve ids, device, or NULL to use
@@ -194,15 +196,38 @@ dfd_status dfd_batch_decide(dfd_context* ctx, dfd_dtype dtype, int dim, const vo
  *   out_ids:   int32[k] candidate curve ids, ascending by (delta^2, position
  *              in cand), -1 past n_cand; out_dist2 / out_dist: float[k]
  *              delta^2 / delta (+inf past n_cand).  Any may be NULL, not all.
- *   abandoned: device uint64, set to the number of abandoned candidates
- *              (may be NULL).
+ *   abandoned: device uint64, set to the number of candidates abandoned
+ *              or skipped by their endpoint bound (may be NULL).
+ *   evaluated: device uint64, set to the number of recurrence cells
+ *              actually evaluated (may be NULL).
  * The results equal the k smallest of the exact float32 delta^2 of every
  * candidate, ties broken by position.  Invalid ids / empty candidates set
  * DFD_ERR_INVALID_ARG in the error word and are skipped.
  */
 dfd_status dfd_knn(dfd_context* ctx, int dim, const float* query, int64_t n, const float* points,
                    const int64_t* offsets, int64_t n_curves, const int32_t* cand, int64_t n_cand, int k,
-                   int32_t* out_ids, float* out_dist2, float* out_dist, unsigned long long* abandoned, void* stream);
+                   int32_t* out_ids, float* out_dist2, float* out_dist, unsigned long long* abandoned,
+                   unsigned long long* evaluated, void* stream);
+
+/*
+ * The appendix variants of the recurrence (DTW and the Levenshtein
+ * distance), many pairs per launch on the batch engine (same inputs, order
+ * and limits as dfd_batch):
+ *   DFD_VARIANT_DTW: dtype DFD_F32, 1 <= dim <= 16; out = float[n_pairs],
+ *     D_{n,m} of D_ij = fl(min(D_{i-1,j}, D_{i-1,j-1}, D_{i,j-1}) + c_ij)
+ *     with c_ij the float32 squared distance of dfd_pair and the first row /
+ *     column as running sums; one rounding per cell, so the value is fixed
+ *     (within (n+m+dim+2) * 2^-24 relative of the exact sum).
+ *   DFD_VARIANT_LEVENSHTEIN: dtype DFD_I32, dim = 1 (one int32 symbol per
+ *     position); out = int64[n_pairs], the unit-cost edit distance (the
+ *     textbook table, E_{i,0} = i, E_{0,j} = j).
+ * Other dtype / dim combinations return DFD_ERR_INVALID_ARG.
+ */
+typedef enum dfd_variant { DFD_VARIANT_DTW = 1, DFD_VARIANT_LEVENSHTEIN = 2 } dfd_variant;
+
+dfd_status dfd_batch_variant(dfd_context* ctx, dfd_variant variant, dfd_dtype dtype, int dim, const void* points,
+                             const int64_t* offsets, int64_t n_curves, const int32_t* pairs, int64_t n_pairs,
+                             void* out, void* stream);
 
 /*
  * All-pairs distance matrix of n_curves curves (the paper's motivating use:

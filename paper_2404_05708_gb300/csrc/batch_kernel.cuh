@@ -115,6 +115,7 @@ struct AbandonAbove {
   typename V::value fixed;
   const unsigned* live_bits;   // k-NN: current limit as float bits (float values only), else null
   bool hit = false;
+  int cols_done = 0;           // columns of the (single) stripe swept when abandoned
   __device__ __forceinline__ typename V::value limit() const {
     if constexpr (sizeof(typename V::value) == 4) {
       if (live_bits) {
@@ -203,6 +204,7 @@ __device__ __forceinline__ typename V::value warp_dfd(const typename V::coord* _
           for (int off = 16; off > 0; off >>= 1) cut = V::vmin(cut, __shfl_xor_sync(0xffffffffu, cut, off));
           if (cut > ab->limit()) {
             ab->hit = true;
+            ab->cols_done = c0 + 32;
             return V::inf();
           }
         }

@@ -43,7 +43,20 @@ struct KnnArgs {
   float* rowbuf;               // per-warp BUF_COLS floats
   unsigned long long* abandoned;
   unsigned long long* computed;
+  unsigned long long* evaluated;   // cells of the recurrence actually evaluated (may be null)
+  unsigned* lb;                // [n_cand] endpoint lower bound (float bits) per position
+  unsigned* order;             // [n_cand] positions, ascending lower bound
+  unsigned* hist;              // [NB] counting-sort buckets
 };
+
+// Counting sort of the candidates by their endpoint lower bound: every
+// coupling path contains (0,0) and (n-1,m-1), so delta^2 >= the larger of
+// those two squared distances (computed in the kernels' float32 order, so
+// the bound holds bit for bit).  Searching near candidates first lowers the
+// limit early, and a candidate whose bound already exceeds the limit is
+// skipped without running the recurrence.
+constexpr int NB = 8192;   // buckets on the top bits of the bound's float bits
+__device__ __forceinline__ unsigned lb_bucket(unsigned bits) { return min(bits >> 18, (unsigned)NB - 1); }
 
 // Warp-wide largest key of the k slots and its index.
 __device__ __forceinline__ void topk_max(const KnnArgs& a, int L, unsigned long long* mx, int* mi) {
@@ -88,6 +101,68 @@ __device__ __forceinline__ void topk_insert(const KnnArgs& a, unsigned long long
 }
 
 template <int DK>
+__global__ void knn_lb_kernel(KnnArgs a) {
+  const int64_t total = a.offsets[a.n_curves];
+  float q0[DK], q1[DK];
+#pragma unroll
+  for (int k = 0; k < DK; ++k) {
+    q0[k] = k < a.dim ? a.query[k] : 0.f;
+    q1[k] = k < a.dim ? a.query[(int64_t)(a.n - 1) * a.dim + k] : 0.f;
+  }
+  for (int64_t it = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; it < a.n_cand;
+       it += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t id = a.cand ? a.cand[it] : it;
+    unsigned bits = 0;   // invalid candidates: bound 0 (the search reports them)
+    if (id >= 0 && id < a.n_curves) {
+      const int64_t o = a.offsets[id], e = a.offsets[id + 1];
+      if (o >= 0 && e <= total && e > o) {
+        float c0[DK], c1[DK];
+#pragma unroll
+        for (int k = 0; k < DK; ++k) {
+          c0[k] = k < a.dim ? a.points[o * a.dim + k] : 0.f;
+          c1[k] = k < a.dim ? a.points[(e - 1) * a.dim + k] : 0.f;
+        }
+        bits = __float_as_uint(fmaxf(dist2<DK>(q0, c0), dist2<DK>(q1, c1)));
+      }
+    }
+    a.lb[it] = bits;
+    atomicAdd(a.hist + lb_bucket(bits), 1u);
+  }
+}
+
+// Exclusive scan of the NB bucket counts (one block of 1024 threads).
+__global__ void __launch_bounds__(1024) knn_scan_kernel(unsigned* hist) {
+  __shared__ unsigned part[1024];
+  constexpr int PER = NB / 1024;
+  unsigned loc[PER], sum = 0;
+#pragma unroll
+  for (int i = 0; i < PER; ++i) {
+    loc[i] = hist[threadIdx.x * PER + i];
+    sum += loc[i];
+  }
+  part[threadIdx.x] = sum;
+  __syncthreads();
+  for (int off = 1; off < 1024; off <<= 1) {
+    const unsigned v = threadIdx.x >= off ? part[threadIdx.x - off] : 0u;
+    __syncthreads();
+    part[threadIdx.x] += v;
+    __syncthreads();
+  }
+  unsigned run = part[threadIdx.x] - sum;
+#pragma unroll
+  for (int i = 0; i < PER; ++i) {
+    hist[threadIdx.x * PER + i] = run;
+    run += loc[i];
+  }
+}
+
+__global__ void knn_scatter_kernel(KnnArgs a) {
+  for (int64_t it = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; it < a.n_cand;
+       it += (int64_t)gridDim.x * blockDim.x)
+    a.order[atomicAdd(a.hist + lb_bucket(a.lb[it]), 1u)] = (unsigned)it;
+}
+
+template <int DK>
 __global__ void __launch_bounds__(256, batch::kBlocksPerSM<DK>::value) knn_kernel(KnnArgs a) {
   const int L = threadIdx.x & 31;
   const int64_t gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -99,6 +174,15 @@ __global__ void __launch_bounds__(256, batch::kBlocksPerSM<DK>::value) knn_kerne
     if (L == 0) item = atomicAdd(a.counter, 1);
     item = __shfl_sync(0xffffffffu, item, 0);
     if (item >= a.n_cand) break;
+    item = (int)a.order[item];   // nearest endpoint bound first
+    {
+      // Positions come in ascending bucket order: once a bucket's lower edge
+      // exceeds the limit, no later candidate can enter the k best.
+      unsigned lim = 0;
+      if (L == 0) lim = (unsigned)ld_relaxed_i32(reinterpret_cast<const int*>(a.limit));
+      lim = __shfl_sync(0xffffffffu, lim, 0);
+      if ((lb_bucket(a.lb[item]) << 18) > lim) break;
+    }
     const int64_t id = a.cand ? a.cand[item] : item;
     if (id < 0 || id >= a.n_curves) {
       if (L == 0) raise_error(a.err, DFD_ERR_INVALID_ARG);
@@ -110,6 +194,12 @@ __global__ void __launch_bounds__(256, batch::kBlocksPerSM<DK>::value) knn_kerne
       continue;
     }
     const int m = (int)(e - o);
+    {
+      unsigned lim = 0;
+      if (L == 0) lim = (unsigned)ld_relaxed_i32(reinterpret_cast<const int*>(a.limit));
+      lim = __shfl_sync(0xffffffffu, lim, 0);
+      if (a.lb[item] > lim) continue;   // delta^2 >= bound > k-th best: no recurrence needed
+    }
     const float* C = a.points + o * a.dim;
     const bool query_rows = a.n <= m;
     const int rows = query_rows ? a.n : m, cols = query_rows ? m : a.n;
@@ -124,10 +214,9 @@ __global__ void __launch_bounds__(256, batch::kBlocksPerSM<DK>::value) knn_kerne
                                      a.query, a.n, C, m, a.dim, a.vec != 0, buf, L, 0, 1 << 30, &ab)
                                : batch::warp_dfd_any<F32, DK, batch::AbandonAbove<F32>>(
                                      C, m, a.query, a.n, a.dim, a.vec != 0, buf, L, 0, 1 << 30, &ab);
-    if (ab.hit) {
-      if (L == 0 && a.abandoned) atomicAdd(a.abandoned, 1ull);
-      continue;
-    }
+    if (L == 0 && a.evaluated)
+      atomicAdd(a.evaluated, (unsigned long long)rows * (unsigned long long)(ab.hit ? min(ab.cols_done, cols) : cols));
+    if (ab.hit) continue;
     if (L == 0 && a.computed) atomicAdd(a.computed, 1ull);
     const unsigned bits = __float_as_uint(r);
     unsigned lim = 0;
@@ -139,20 +228,24 @@ __global__ void __launch_bounds__(256, batch::kBlocksPerSM<DK>::value) knn_kerne
 }
 
 __global__ void knn_init_kernel(unsigned long long* topk, int k, unsigned* limit, int* counter,
-                                unsigned long long* abandoned, unsigned long long* computed) {
+                                unsigned long long* abandoned, unsigned long long* computed,
+                                unsigned long long* evaluated) {
   for (int j = threadIdx.x; j < k; j += blockDim.x) topk[j] = kEmpty;
   if (threadIdx.x == 0) {
     *limit = 0x7f800000u;
     *counter = 0;
     *computed = 0;
     if (abandoned) *abandoned = 0;
+    if (evaluated) *evaluated = 0;
   }
 }
 
 // Sort the k keys ascending (bitonic, one block) and write ids / distances.
 __global__ void __launch_bounds__(KMAX) knn_finish_kernel(const unsigned long long* topk, int k,
                                                           const int32_t* cand, int32_t* out_ids, float* out_dist2,
-                                                          float* out_dist) {
+                                                          float* out_dist, const unsigned long long* computed,
+                                                          int64_t n_cand, unsigned long long* abandoned) {
+  if (threadIdx.x == 0 && abandoned) *abandoned = (unsigned long long)n_cand - *computed;
   __shared__ unsigned long long s[KMAX];
   int size = 1;
   while (size < k) size <<= 1;
@@ -189,10 +282,13 @@ template <int DK>
 dfd_status knn_launch(dfd_context* ctx, int dim, const float* query, int n, const float* points,
                       const int64_t* offsets, int64_t n_curves, const int32_t* cand, int64_t n_cand, int k,
                       int32_t* out_ids, float* out_dist2, float* out_dist, unsigned long long* abandoned,
-                      cudaStream_t s) {
+                      unsigned long long* evaluated, cudaStream_t s) {
   const int blocks = resident_blocks(ctx, knn_kernel<DK>, 256);
   const size_t warps = (size_t)blocks * 8;
-  const size_t off_topk = 256, off_buf = align_up(off_topk + (size_t)k * 8, 256);
+  const size_t off_topk = 256, off_hist = align_up(off_topk + (size_t)k * 8, 256);
+  const size_t off_lb = align_up(off_hist + (size_t)NB * 4, 256);
+  const size_t off_order = align_up(off_lb + (size_t)n_cand * 4, 256);
+  const size_t off_buf = align_up(off_order + (size_t)n_cand * 4, 256);
   const size_t total = off_buf + warps * batch::BUF_COLS * sizeof(float);
   dfd_status st = ensure_scratch(ctx, total);
   if (st != DFD_OK) return st;
@@ -221,11 +317,21 @@ dfd_status knn_launch(dfd_context* ctx, int dim, const float* query, int n, cons
   a.err = ctx->d_err;
   a.rowbuf = reinterpret_cast<float*>(base + off_buf);
   a.abandoned = abandoned;
-  knn_init_kernel<<<1, 256, 0, s>>>(a.topk, k, a.limit, a.counter, abandoned, a.computed);
+  a.evaluated = evaluated;
+  a.hist = reinterpret_cast<unsigned*>(base + off_hist);
+  a.lb = reinterpret_cast<unsigned*>(base + off_lb);
+  a.order = reinterpret_cast<unsigned*>(base + off_order);
+  knn_init_kernel<<<1, 256, 0, s>>>(a.topk, k, a.limit, a.counter, abandoned, a.computed, evaluated);
+  cudaError_t e = cudaMemsetAsync(a.hist, 0, (size_t)NB * 4, s);
+  if (e != cudaSuccess) return cuda_status(e);
+  const int lblocks = (int)std::max<int64_t>(1, std::min<int64_t>((n_cand + 255) / 256, 4 * (int64_t)ctx->num_sms));
+  knn_lb_kernel<DK><<<lblocks, 256, 0, s>>>(a);
+  knn_scan_kernel<<<1, 1024, 0, s>>>(a.hist);
+  knn_scatter_kernel<<<lblocks, 256, 0, s>>>(a);
   timing_begin(ctx, s);
   knn_kernel<DK><<<blocks, 256, 0, s>>>(a);
   timing_end(ctx, s);
-  knn_finish_kernel<<<1, KMAX, 0, s>>>(a.topk, k, cand, out_ids, out_dist2, out_dist);
+  knn_finish_kernel<<<1, KMAX, 0, s>>>(a.topk, k, cand, out_ids, out_dist2, out_dist, a.computed, n_cand, abandoned);
   return cuda_status(cudaGetLastError());
 }
 
@@ -237,7 +343,7 @@ using namespace dfd;
 extern "C" dfd_status dfd_knn(dfd_context* ctx, int dim, const float* query, int64_t n, const float* points,
                               const int64_t* offsets, int64_t n_curves, const int32_t* cand, int64_t n_cand, int k,
                               int32_t* out_ids, float* out_dist2, float* out_dist, unsigned long long* abandoned,
-                              void* stream) {
+                              unsigned long long* evaluated, void* stream) {
   if (!ctx || !query || !points || !offsets || n < 1 || n > INT32_MAX || n_curves < 1 || n_curves > INT32_MAX)
     return DFD_ERR_INVALID_ARG;
   if (dim < 1 || k < 1 || n_cand < 0 || n_cand > INT32_MAX || (!cand && n_cand > n_curves))
@@ -250,11 +356,11 @@ extern "C" dfd_status dfd_knn(dfd_context* ctx, int dim, const float* query, int
   }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   switch (dim_class(dim)) {
-    case 2: return knn::knn_launch<2>(ctx, dim, query, (int)n, points, offsets, n_curves, cand, n_cand, k, out_ids, out_dist2, out_dist, abandoned, s);
-    case 3: return knn::knn_launch<3>(ctx, dim, query, (int)n, points, offsets, n_curves, cand, n_cand, k, out_ids, out_dist2, out_dist, abandoned, s);
-    case 4: return knn::knn_launch<4>(ctx, dim, query, (int)n, points, offsets, n_curves, cand, n_cand, k, out_ids, out_dist2, out_dist, abandoned, s);
-    case 8: return knn::knn_launch<8>(ctx, dim, query, (int)n, points, offsets, n_curves, cand, n_cand, k, out_ids, out_dist2, out_dist, abandoned, s);
-    case 16: return knn::knn_launch<16>(ctx, dim, query, (int)n, points, offsets, n_curves, cand, n_cand, k, out_ids, out_dist2, out_dist, abandoned, s);
+    case 2: return knn::knn_launch<2>(ctx, dim, query, (int)n, points, offsets, n_curves, cand, n_cand, k, out_ids, out_dist2, out_dist, abandoned, evaluated, s);
+    case 3: return knn::knn_launch<3>(ctx, dim, query, (int)n, points, offsets, n_curves, cand, n_cand, k, out_ids, out_dist2, out_dist, abandoned, evaluated, s);
+    case 4: return knn::knn_launch<4>(ctx, dim, query, (int)n, points, offsets, n_curves, cand, n_cand, k, out_ids, out_dist2, out_dist, abandoned, evaluated, s);
+    case 8: return knn::knn_launch<8>(ctx, dim, query, (int)n, points, offsets, n_curves, cand, n_cand, k, out_ids, out_dist2, out_dist, abandoned, evaluated, s);
+    case 16: return knn::knn_launch<16>(ctx, dim, query, (int)n, points, offsets, n_curves, cand, n_cand, k, out_ids, out_dist2, out_dist, abandoned, evaluated, s);
     default: return DFD_ERR_UNSUPPORTED;
   }
 }

@@ -1,0 +1,251 @@
+// variants.cu -- the appendix variants of the recurrence on the batch engine:
+// DTW (the Frechet recurrence with the outer max replaced by a sum) and the
+// Levenshtein distance (unit-cost edit distance), many pairs per launch.
+//
+// Same lane layout as the Frechet batch kernel (one warp per pair, rows =
+// the shorter sequence in stripes of 32*R, lane L at step s on column
+// s - L, stripes handing their bottom row through a per-warp buffer) and
+// the same device-built LPT work list; only the cell rule and the
+// boundaries differ:
+//   DTW:          D_ij = fl(min(D_{i-1,j}, D_{i-1,j-1}, D_{i,j-1}) + c_ij),
+//                 c_ij the float32 squared distance, boundaries +inf,
+//                 corner 0 (the running sums of the first row / column);
+//   Levenshtein:  E_ij = min(min(E_{i-1,j}, E_{i,j-1}) + 1,
+//                            E_{i-1,j-1} + [a_i != b_j]),
+//                 boundaries E_{i,-1} = i + 1, E_{-1,j} = j + 1, corner 0
+//                 (the textbook table; the appendix listing's start
+//                 differs by one and is read as this).
+// Unlike the Frechet distance neither is invariant under repeating a point,
+// so the result is read at row n - 1 (the padding rows of the last stripe
+// are computed and ignored).
+#include <algorithm>
+#include "batch_launch.cuh"
+#include "dfd_internal.h"
+
+namespace dfd {
+namespace variant {
+
+struct DtwOp {
+  using V = F32;
+  using coord = float;
+  using value = float;
+  static constexpr bool lev = false;
+};
+struct LevOp {
+  using V = I32;
+  using coord = int32_t;
+  using value = int;
+  static constexpr bool lev = true;
+};
+
+template <class Op, int DK, int R>
+__device__ __forceinline__ typename Op::value warp_var(const typename Op::coord* __restrict__ P, int n,
+                                                       const typename Op::coord* __restrict__ Q, int m, int dim,
+                                                       bool vec, typename Op::value* buf, int L) {
+  using T = typename Op::value;
+  using Cd = typename Op::coord;
+  const T INF = Op::lev ? (T)0x3fffffff : (T)__int_as_float(0x7f800000);
+  const int nstripes = (n + 32 * R - 1) / (32 * R);
+  T res = 0;
+  for (int st = 0; st < nstripes; ++st) {
+    Cd pr[R][DK];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int i = min(st * 32 * R + L * R + r, n - 1);
+#pragma unroll
+      for (int k = 0; k < DK; ++k) pr[r][k] = k < dim ? __ldg(P + (int64_t)i * dim + k) : (Cd)0;
+    }
+    const bool has_top = st > 0, has_bottom = st + 1 < nstripes, last = !has_bottom;
+    const int row0 = st * 32 * R + L * R;   // global row of the lane's first row
+    T v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = Op::lev ? (T)(row0 + r + 1) : INF;
+    T bout = v[R - 1];
+    T upp = Op::lev ? (T)row0 : ((st == 0 && L == 0) ? (T)0 : INF);
+    // lane and register of row n - 1 (last stripe)
+    const int li = n - 1 - st * 32 * R;
+    const int lres = li / R, rres = li % R;
+    const int nsteps = m + 31;
+    for (int c0 = 0; c0 < nsteps; c0 += 32) {
+      T top_blk;
+      if (has_top)
+        top_blk = buf[min(c0 + L, m - 1)];
+      else
+        top_blk = Op::lev ? (T)(c0 + L + 1) : INF;
+      T out_blk = INF;
+#pragma unroll 4
+      for (int s = 0; s < 32; ++s) {
+        const int j = c0 + s - L;
+        const int jq = min(max(j, 0), m - 1);
+        Cd qk[DK];
+        batch::load_point<Cd, DK>(Q, jq, dim, vec, qk);
+        T d[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          if constexpr (Op::lev) {
+            bool diff = false;
+#pragma unroll
+            for (int k = 0; k < DK; ++k) diff |= pr[r][k] != qk[k];
+            d[r] = diff ? 1 : 0;
+          } else {
+            d[r] = dist2<DK>(pr[r], qk);
+          }
+        }
+        const T tin = __shfl_sync(0xffffffffu, top_blk, s);
+        T u = __shfl_up_sync(0xffffffffu, bout, 1);
+        u = (L == 0) ? tin : u;
+        T up = u, dg = upp;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          const T l = v[r];
+          T nv;
+          if constexpr (Op::lev) {
+            nv = min(min(l, up) + 1, dg + d[r]);
+            nv = j < 0 ? l : nv;   // columns left of the table keep the boundary E_{i,-1}
+          } else {
+            nv = __fadd_rn(F32::vmin3(l, dg, up), d[r]);
+          }
+          dg = l;
+          v[r] = nv;
+          up = nv;
+        }
+        upp = u;
+        bout = up;
+        if (has_bottom) {
+          const T b31 = __shfl_sync(0xffffffffu, bout, 31);
+          out_blk = (L == s) ? b31 : out_blk;
+        }
+        if (last && L == lres && j == m - 1) {
+#pragma unroll
+          for (int r = 0; r < R; ++r)
+            if (r == rres) res = v[r];
+        }
+      }
+      if (has_bottom) {
+        const int oc = c0 + L - 31;
+        __syncwarp();
+        if (oc >= 0 && oc < m) buf[oc] = out_blk;
+      }
+      __syncwarp();
+    }
+    if (last) res = __shfl_sync(0xffffffffu, res, lres);
+  }
+  return res;
+}
+
+template <class Op, int DK>
+__device__ __forceinline__ typename Op::value warp_var_any(const typename Op::coord* P, int n,
+                                                           const typename Op::coord* Q, int m, int dim, bool vec,
+                                                           typename Op::value* buf, int L) {
+  constexpr int RM = batch::Rmax<DK>::value;
+  switch (batch::rows_per_lane<DK>(n)) {
+#define DFD_V_CASE(RR) \
+  case RR:             \
+    if constexpr (RR < RM) return warp_var<Op, DK, RR>(P, n, Q, m, dim, vec, buf, L); \
+    break;
+    DFD_V_CASE(1)
+    DFD_V_CASE(2)
+    DFD_V_CASE(3)
+    DFD_V_CASE(4)
+    DFD_V_CASE(5)
+    DFD_V_CASE(6)
+    DFD_V_CASE(7)
+    default:
+      break;
+#undef DFD_V_CASE
+  }
+  return warp_var<Op, DK, RM>(P, n, Q, m, dim, vec, buf, L);
+}
+
+template <class Op, int DK>
+__global__ void __launch_bounds__(256, batch::kBlocksPerSM<DK>::value) variant_kernel(batch::BatchArgs a) {
+  using T = typename Op::value;
+  using Cd = typename Op::coord;
+  const int L = threadIdx.x & 31;
+  const int64_t gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  T* buf = static_cast<T*>(a.rowbuf) + gw * batch::BUF_COLS;
+  const Cd* pts = static_cast<const Cd*>(a.points);
+  const int64_t total = a.offsets[a.n_curves];
+  if (ld_relaxed_i32(a.err) != 0) return;
+  for (;;) {
+    int item = 0;
+    if (L == 0) item = atomicAdd(a.counter, 1);
+    item = __shfl_sync(0xffffffffu, item, 0);
+    if (item >= a.n_items) break;
+    const unsigned w = a.worklist[item];
+    const int64_t k = w & (batch::kNarrowBit - 1);
+    int32_t ia = a.pairs[2 * k], ib = a.pairs[2 * k + 1];
+    if (w >> 31) {
+      const int32_t t = ia;
+      ia = ib;
+      ib = t;
+    }
+    if (ia < 0 || ib < 0 || ia >= a.n_curves || ib >= a.n_curves) continue;  // reported by the plan
+    const int64_t oa = a.offsets[ia], ob = a.offsets[ib];
+    const int64_t ea = a.offsets[ia + 1], eb = a.offsets[ib + 1];
+    if (oa < 0 || ob < 0 || ea > total || eb > total) continue;
+    const int n = (int)(ea - oa), m = (int)(eb - ob);
+    if (n < 1 || m < 1) continue;
+    if (!batch::fits_buffer<DK>(n, m)) {
+      if (L == 0) raise_error(a.err, DFD_ERR_UNSUPPORTED);
+      continue;
+    }
+    const T r = warp_var_any<Op, DK>(pts + oa * a.dim, n, pts + ob * a.dim, m, a.dim, a.vec != 0, buf, L);
+    if (L == 0) {
+      if constexpr (Op::lev)
+        static_cast<long long*>(a.out_dist2)[k] = (long long)r;
+      else
+        static_cast<float*>(a.out_dist2)[k] = r;
+    }
+  }
+}
+
+template <class Op, int DK>
+dfd_status variant_launch(dfd_context* ctx, int dim, const void* points, const int64_t* offsets, int64_t n_curves,
+                          const int32_t* pairs, int64_t n_pairs, void* out, cudaStream_t s) {
+  const int blocks = resident_blocks(ctx, variant_kernel<Op, DK>, 256);
+  batch::BatchArgs ba;
+  dfd_status st = batch_prepare<typename Op::V, DK>(ctx, dim, points, offsets, n_curves, pairs, n_pairs, s, blocks, &ba);
+  if (st != DFD_OK) return st;
+  ba.out_dist2 = out;
+  timing_begin(ctx, s);
+  variant_kernel<Op, DK><<<blocks, 256, 0, s>>>(ba);
+  timing_end(ctx, s);
+  return cuda_status(cudaGetLastError());
+}
+
+}  // namespace variant
+}  // namespace dfd
+
+using namespace dfd;
+
+extern "C" dfd_status dfd_batch_variant(dfd_context* ctx, dfd_variant var, dfd_dtype dtype, int dim,
+                                        const void* points, const int64_t* offsets, int64_t n_curves,
+                                        const int32_t* pairs, int64_t n_pairs, void* out, void* stream) {
+  if (!ctx || !points || !offsets || !pairs || !out || n_curves < 1 || n_pairs < 0) return DFD_ERR_INVALID_ARG;
+  if (n_curves > INT32_MAX || n_pairs > INT32_MAX) return DFD_ERR_UNSUPPORTED;
+  if (var == DFD_VARIANT_DTW) {
+    if (dtype != DFD_F32 || dim < 1) return DFD_ERR_INVALID_ARG;
+    if (dim > 16) return DFD_ERR_UNSUPPORTED;
+  } else if (var == DFD_VARIANT_LEVENSHTEIN) {
+    if (dtype != DFD_I32 || dim != 1) return DFD_ERR_INVALID_ARG;
+  } else {
+    return DFD_ERR_INVALID_ARG;
+  }
+  if (n_pairs == 0) return DFD_OK;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) {
+    cudaGetLastError();
+    return DFD_ERR_CUDA;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (var == DFD_VARIANT_LEVENSHTEIN)
+    return variant::variant_launch<variant::LevOp, 2>(ctx, dim, points, offsets, n_curves, pairs, n_pairs, out, s);
+  switch (dim_class(dim)) {
+    case 2: return variant::variant_launch<variant::DtwOp, 2>(ctx, dim, points, offsets, n_curves, pairs, n_pairs, out, s);
+    case 3: return variant::variant_launch<variant::DtwOp, 3>(ctx, dim, points, offsets, n_curves, pairs, n_pairs, out, s);
+    case 4: return variant::variant_launch<variant::DtwOp, 4>(ctx, dim, points, offsets, n_curves, pairs, n_pairs, out, s);
+    case 8: return variant::variant_launch<variant::DtwOp, 8>(ctx, dim, points, offsets, n_curves, pairs, n_pairs, out, s);
+    case 16: return variant::variant_launch<variant::DtwOp, 16>(ctx, dim, points, offsets, n_curves, pairs, n_pairs, out, s);
+    default: return DFD_ERR_UNSUPPORTED;
+  }
+}

@@ -19,6 +19,7 @@ PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(PKG, "_build", "libdfd.so")
 
 DFD_F32, DFD_I32 = 0, 1
+DFD_VARIANT_DTW, DFD_VARIANT_LEVENSHTEIN = 1, 2
 STATUS = {
     0: "DFD_OK", 1: "DFD_ERR_INVALID_ARG", 2: "DFD_ERR_RANGE", 3: "DFD_ERR_NONFINITE", 4: "DFD_ERR_OOM",
     5: "DFD_ERR_CUDA", 6: "DFD_ERR_TIMEOUT", 7: "DFD_ERR_BUSY", 8: "DFD_ERR_CANCELLED", 9: "DFD_ERR_NOT_READY",
@@ -81,7 +82,8 @@ _SIGS = {
     "dfd_batch": [_VP, _INT, _INT, _VP, _VP, _I64, _VP, _I64, _VP, _VP, _VP],
     "dfd_matrix": [_VP, _INT, _INT, _VP, _VP, _I64, _VP, _VP, _VP],
     "dfd_batch_decide": [_VP, _INT, _INT, _VP, _VP, _I64, _VP, _I64, _VP, ctypes.c_double, _VP, _VP, _VP, _VP],
-    "dfd_knn": [_VP, _INT, _VP, _I64, _VP, _VP, _I64, _VP, _I64, _INT, _VP, _VP, _VP, _VP, _VP],
+    "dfd_batch_variant": [_VP, _INT, _INT, _INT, _VP, _VP, _I64, _VP, _I64, _VP, _VP],
+    "dfd_knn": [_VP, _INT, _VP, _I64, _VP, _VP, _I64, _VP, _I64, _INT, _VP, _VP, _VP, _VP, _VP, _VP],
     "dfd_batch_capture": [_VP, _INT, _INT, _VP, _VP, _I64, _VP, _I64, _VP, _VP, ctypes.POINTER(_VP)],
     "dfd_matrix_capture": [_VP, _INT, _INT, _VP, _VP, _I64, _VP, _VP, ctypes.POINTER(_VP)],
     "dfd_graph_launch": [_VP, _VP],
@@ -197,10 +199,15 @@ def dfd_batch_decide(ctx, dtype, dim, points, offsets, n_curves, pairs, n_pairs,
                                            float(eps2_all), out_dist2, out_within, abandoned, stream)
 
 
+def dfd_batch_variant(ctx, variant, dtype, dim, points, offsets, n_curves, pairs, n_pairs, out, stream) -> int:
+    return load_library().dfd_batch_variant(ctx, variant, dtype, dim, points, offsets, n_curves, pairs, n_pairs, out,
+                                            stream)
+
+
 def dfd_knn(ctx, dim, query, n, points, offsets, n_curves, cand, n_cand, k, out_ids, out_dist2, out_dist, abandoned,
-            stream) -> int:
+            evaluated, stream) -> int:
     return load_library().dfd_knn(ctx, dim, query, n, points, offsets, n_curves, cand, n_cand, k, out_ids, out_dist2,
-                                  out_dist, abandoned, stream)
+                                  out_dist, abandoned, evaluated, stream)
 
 
 def dfd_batch_capture(ctx, dtype, dim, points, offsets, n_curves, pairs, n_pairs, out_dist, out_dist2) -> int:
@@ -561,9 +568,36 @@ class Context:
         _check(st, "dfd_batch_decide")
         return out_dist2, out_within, ab
 
+    def dtw(self, points, offsets, pairs, out=None, stream=None):
+        """DTW (appendix variant, squared-distance ground cost) of float32 CSR pairs."""
+        return self._variant(DFD_VARIANT_DTW, points, offsets, pairs, out, stream)
+
+    def levenshtein(self, symbols, offsets, pairs, out=None, stream=None):
+        """Edit distance of int32 symbol sequences (CSR, one symbol per position)."""
+        return self._variant(DFD_VARIANT_LEVENSHTEIN, symbols, offsets, pairs, out, stream)
+
+    def _variant(self, var, points, offsets, pairs, out, stream):
+        torch = _torch()
+        points = points.reshape(-1, 1) if points.dim() == 1 else points
+        points = _curve(points)
+        dt = _dtype_code(points)
+        offsets, pairs = offsets.contiguous(), pairs.contiguous()
+        if offsets.dtype != torch.int64 or pairs.dtype != torch.int32:
+            raise TypeError("offsets must be int64 and pairs int32")
+        n_pairs = pairs.numel() // 2
+        if out is None:
+            out = torch.empty(n_pairs, dtype=torch.float32 if var == DFD_VARIANT_DTW else torch.int64,
+                              device=points.device)
+        s = stream if stream is not None else torch.cuda.current_stream(self.device).cuda_stream
+        st = dfd_batch_variant(self.handle, var, dt, points.shape[1], points.data_ptr(), offsets.data_ptr(),
+                               offsets.numel() - 1, pairs.data_ptr(), n_pairs, out.data_ptr(), s)
+        _check(st, "dfd_batch_variant")
+        return out
+
     def knn(self, query, points, offsets, k, cand=None, stream=None):
         """k nearest candidates of a float32 query curve.  Returns (ids, dist2,
-        abandoned): int32[k], float32[k] ascending, device counter."""
+        counters): int32[k], float32[k] ascending, device int64[2] = (candidates
+        abandoned or skipped, recurrence cells evaluated)."""
         torch = _torch()
         query, points = _curve(query), _curve(points)
         if query.dtype != torch.float32 or points.dtype != torch.float32 or query.shape[1] != points.shape[1]:
@@ -580,11 +614,11 @@ class Context:
         dev = points.device
         ids = torch.empty(k, dtype=torch.int32, device=dev)
         d2 = torch.empty(k, dtype=torch.float32, device=dev)
-        ab = torch.zeros(1, dtype=torch.int64, device=dev)
+        ab = torch.zeros(2, dtype=torch.int64, device=dev)   # [abandoned, cells evaluated]
         s = stream if stream is not None else torch.cuda.current_stream(self.device).cuda_stream
         st = dfd_knn(self.handle, query.shape[1], query.data_ptr(), query.shape[0], points.data_ptr(),
                      offsets.data_ptr(), n_curves, cand.data_ptr() if cand is not None else None, n_cand, int(k),
-                     ids.data_ptr(), d2.data_ptr(), None, ab.data_ptr(), s)
+                     ids.data_ptr(), d2.data_ptr(), None, ab.data_ptr(), ab.data_ptr() + 8, s)
         _check(st, "dfd_knn")
         return ids, d2, ab
 

@@ -129,8 +129,11 @@ def test_knn_matches_brute_force(dctx, dim, k):
     torch.cuda.synchronize()
     assert np.array_equal(ids.cpu().numpy(), want_ids), (ids.cpu().numpy()[:10], want_ids[:10])
     assert np.array_equal(d2.cpu().numpy(), want_d2)
+    n_ab, evaluated = (int(x) for x in ab.cpu().numpy())
+    total_cells = len(qry) * int(off[-1])
+    assert 0 < evaluated <= total_cells
     if k <= 64:
-        assert int(ab.item()) > 0   # small k prunes
+        assert n_ab > 0 and evaluated < total_cells   # small k prunes
 
 
 def test_knn_candidate_subset_ties_and_padding(dctx):
