@@ -153,6 +153,10 @@ __device__ __forceinline__ typename V::value warp_dfd(const typename V::coord* _
     T bout = V::inf();
     T upp = (st == 0 && L == 0) ? V::zero() : V::inf();
     const int nsteps = m + 31;
+    // q point of the coming step, loaded one step ahead (the load's latency
+    // stays off the step's chain)
+    Cd qk[DK];
+    load_point<Cd, DK>(Q, 0, dim, vec, qk);
     for (int c0 = 0; c0 < nsteps; c0 += 32) {
       const T top_blk = has_top ? buf[min(c0 + L, m - 1)] : V::inf();
       T out_blk = V::inf();
@@ -162,9 +166,8 @@ __device__ __forceinline__ typename V::value warp_dfd(const typename V::coord* _
 #pragma unroll 4
       for (int s = 0; s < 32; ++s) {
         const int j = c0 + s - L;
-        const int jq = min(max(j, 0), m - 1);
-        Cd qk[DK];
-        load_point<Cd, DK>(Q, jq, dim, vec, qk);
+        Cd qn[DK];
+        load_point<Cd, DK>(Q, min(max(j + 1, 0), m - 1), dim, vec, qn);
         T d[R];
 #pragma unroll
         for (int r = 0; r < R; ++r) d[r] = vdist2<V, DK>(pr[r], qk);
@@ -186,7 +189,8 @@ __device__ __forceinline__ typename V::value warp_dfd(const typename V::coord* _
           const T b31 = __shfl_sync(0xffffffffu, bout, 31);
           out_blk = (L == s) ? b31 : out_blk;
         }
-        res = (last && j == m - 1) ? bout : res;
+#pragma unroll
+        for (int k = 0; k < DK; ++k) qk[k] = qn[k];
       }
       if (has_bottom) {
         const int oc = c0 + L - 31;
@@ -210,6 +214,10 @@ __device__ __forceinline__ typename V::value warp_dfd(const typename V::coord* _
         }
       }
     }
+    // Lane 31's bottom row has swept past column m - 1 over q padded by
+    // repeating its last point, which leaves the value unchanged (Sec. 4
+    // footnote): its last value is delta^2.
+    if (last) res = bout;
   }
   return __shfl_sync(0xffffffffu, res, 31);
 }
