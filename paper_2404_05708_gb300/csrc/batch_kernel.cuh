@@ -146,6 +146,17 @@ __device__ __forceinline__ typename V::value warp_dfd(const typename V::coord* _
 #pragma unroll
       for (int k = 0; k < DK; ++k) pr[r][k] = k < dim ? __ldg(P + (int64_t)i * dim + k) : (Cd)0;
     }
+    // float32: rows packed in pairs, two cells per f32x2 instruction (the
+    // same per-element rounding as the scalar order; odd R: last row scalar)
+    constexpr bool kPack = std::is_same<V, F32>::value && R >= 2;
+    unsigned long long pp[kPack ? R / 2 : 1][DK];
+    if constexpr (kPack) {
+#pragma unroll
+      for (int h = 0; h < R / 2; ++h) {
+#pragma unroll
+        for (int k = 0; k < DK; ++k) pp[h][k] = pack2(pr[2 * h][k], pr[2 * h + 1][k]);
+      }
+    }
     const bool has_top = st > 0, has_bottom = st + 1 < nstripes, last = !has_bottom;
     T v[R];
 #pragma unroll
@@ -169,8 +180,27 @@ __device__ __forceinline__ typename V::value warp_dfd(const typename V::coord* _
         Cd qn[DK];
         load_point<Cd, DK>(Q, min(max(j + 1, 0), m - 1), dim, vec, qn);
         T d[R];
+        if constexpr (kPack) {
+          unsigned long long qd[DK];
 #pragma unroll
-        for (int r = 0; r < R; ++r) d[r] = vdist2<V, DK>(pr[r], qk);
+          for (int k = 0; k < DK; ++k) qd[k] = pack2(qk[k], qk[k]);
+#pragma unroll
+          for (int h = 0; h < R / 2; ++h) {
+            const unsigned long long t0 = sub2(pp[h][0], qd[0]);
+            unsigned long long acc = mul2(t0, t0);
+#pragma unroll
+            for (int k = 1; k < DK; ++k) {
+              const unsigned long long t = sub2(pp[h][k], qd[k]);
+              acc = fma2(t, t, acc);
+            }
+            d[2 * h] = lo2(acc);
+            d[2 * h + 1] = hi2(acc);
+          }
+          if constexpr ((R & 1) != 0) d[R - 1] = vdist2<V, DK>(pr[R - 1], qk);
+        } else {
+#pragma unroll
+          for (int r = 0; r < R; ++r) d[r] = vdist2<V, DK>(pr[r], qk);
+        }
         const T tin = __shfl_sync(0xffffffffu, top_blk, s);
         T u = __shfl_up_sync(0xffffffffu, bout, 1);
         u = (L == 0) ? tin : u;
