@@ -29,6 +29,18 @@ template <int DK>
 struct kBlocksPerSM {
   static constexpr int value = 2;
 };
+
+// Wide points (dim class >= 8) stream through a per-warp shared-memory ring
+// of 64 q points instead of per-lane L1/L2 loads: the warp loads the next 32
+// points cooperatively one block ahead (one point per lane, coalesced) and
+// every step reads them from shared memory, plane-major ([16-byte plane][64
+// points]) so that lanes one column apart read consecutive records.
+template <int DK>
+struct QStage {
+  static constexpr bool on = DK >= 8;
+  static constexpr int NPL = (DK + 3) / 4;
+  static constexpr int RECS = on ? NPL * 64 : 1;   // uint4 records per warp
+};
 constexpr int BUF_COLS = 4096;    // per-warp row buffer (columns) for multi-stripe pairs
 
 // Rows per lane chosen for a pair with `rows` rows (one stripe when possible).
@@ -133,7 +145,8 @@ template <class V, int DK, int R, class AB = NoAbandon<V>>
 __device__ __forceinline__ typename V::value warp_dfd(const typename V::coord* __restrict__ P, int n,
                                                       const typename V::coord* __restrict__ Q, int m, int dim,
                                                       bool vec, typename V::value* buf, int L, int st_begin = 0,
-                                                      int st_end = 1 << 30, AB* ab = nullptr) {
+                                                      int st_end = 1 << 30, AB* ab = nullptr,
+                                                      uint4* stage = nullptr) {
   using T = typename V::value;
   using Cd = typename V::coord;
   const int nstripes = (n + 32 * R - 1) / (32 * R);
@@ -167,10 +180,40 @@ __device__ __forceinline__ typename V::value warp_dfd(const typename V::coord* _
     // q point of the coming step, loaded one step ahead (the load's latency
     // stays off the step's chain)
     Cd qk[DK];
-    load_point<Cd, DK>(Q, 0, dim, vec, qk);
+    Cd qpre[QStage<DK>::on ? DK : 1];   // staged form: this lane's point of the next block
+    if constexpr (QStage<DK>::on) {
+      load_point<Cd, DK>(Q, min(L, m - 1), dim, vec, qpre);
+    } else {
+      load_point<Cd, DK>(Q, 0, dim, vec, qk);
+    }
     for (int c0 = 0; c0 < nsteps; c0 += 32) {
       const T top_blk = has_top ? buf[min(c0 + L, m - 1)] : V::inf();
       T out_blk = V::inf();
+      if constexpr (QStage<DK>::on) {
+        // columns c0 .. c0+31 into ring slots (c & 63); the ring then holds
+        // c0-32 .. c0+31, every column this block's lanes read
+        __syncwarp();
+#pragma unroll
+        for (int c = 0; c < QStage<DK>::NPL; ++c) {
+          uint4 r;
+          r.x = *reinterpret_cast<const unsigned*>(&qpre[4 * c]);
+          r.y = 4 * c + 1 < DK ? *reinterpret_cast<const unsigned*>(&qpre[4 * c + 1]) : 0u;
+          r.z = 4 * c + 2 < DK ? *reinterpret_cast<const unsigned*>(&qpre[4 * c + 2]) : 0u;
+          r.w = 4 * c + 3 < DK ? *reinterpret_cast<const unsigned*>(&qpre[4 * c + 3]) : 0u;
+          stage[c * 64 + ((c0 + L) & 63)] = r;
+        }
+        __syncwarp();
+        load_point<Cd, DK>(Q, min(c0 + 32 + L, m - 1), dim, vec, qpre);   // next block, in flight
+        const int j0 = min(max(c0 - L, 0), m - 1);
+#pragma unroll
+        for (int c = 0; c < QStage<DK>::NPL; ++c) {
+          const uint4 r = stage[c * 64 + (j0 & 63)];
+          qk[4 * c] = *reinterpret_cast<const Cd*>(&r.x);
+          if (4 * c + 1 < DK) qk[4 * c + 1] = *reinterpret_cast<const Cd*>(&r.y);
+          if (4 * c + 2 < DK) qk[4 * c + 2] = *reinterpret_cast<const Cd*>(&r.z);
+          if (4 * c + 3 < DK) qk[4 * c + 3] = *reinterpret_cast<const Cd*>(&r.w);
+        }
+      }
       // 4 steps unrolled (not 32): a kernel holds every R variant, and warps
       // running different variants side by side must not thrash the
       // instruction cache.
@@ -178,7 +221,21 @@ __device__ __forceinline__ typename V::value warp_dfd(const typename V::coord* _
       for (int s = 0; s < 32; ++s) {
         const int j = c0 + s - L;
         Cd qn[DK];
-        load_point<Cd, DK>(Q, min(max(j + 1, 0), m - 1), dim, vec, qn);
+        if constexpr (QStage<DK>::on) {
+          if (s + 1 < 32) {
+            const int jn = min(max(j + 1, 0), m - 1);
+#pragma unroll
+            for (int c = 0; c < QStage<DK>::NPL; ++c) {
+              const uint4 r = stage[c * 64 + (jn & 63)];
+              qn[4 * c] = *reinterpret_cast<const Cd*>(&r.x);
+              if (4 * c + 1 < DK) qn[4 * c + 1] = *reinterpret_cast<const Cd*>(&r.y);
+              if (4 * c + 2 < DK) qn[4 * c + 2] = *reinterpret_cast<const Cd*>(&r.z);
+              if (4 * c + 3 < DK) qn[4 * c + 3] = *reinterpret_cast<const Cd*>(&r.w);
+            }
+          }
+        } else {
+          load_point<Cd, DK>(Q, min(max(j + 1, 0), m - 1), dim, vec, qn);
+        }
         T d[R];
         if constexpr (kPack) {
           unsigned long long qd[DK];
@@ -256,12 +313,13 @@ template <class V, int DK, class AB = NoAbandon<V>>
 __device__ __forceinline__ typename V::value warp_dfd_any(const typename V::coord* P, int n,
                                                           const typename V::coord* Q, int m, int dim, bool vec,
                                                           typename V::value* buf, int L, int st_begin = 0,
-                                                          int st_end = 1 << 30, AB* ab = nullptr) {
+                                                          int st_end = 1 << 30, AB* ab = nullptr,
+                                                          uint4* stage = nullptr) {
   constexpr int RM = Rmax<DK>::value;
   switch (rows_per_lane<DK>(n)) {
 #define DFD_B_CASE(RR)                                                                                       \
   case RR:                                                                                                   \
-    if constexpr (RR < RM) return warp_dfd<V, DK, RR, AB>(P, n, Q, m, dim, vec, buf, L, st_begin, st_end, ab); \
+    if constexpr (RR < RM) return warp_dfd<V, DK, RR, AB>(P, n, Q, m, dim, vec, buf, L, st_begin, st_end, ab, stage); \
     break;
     DFD_B_CASE(1)
     DFD_B_CASE(2)
@@ -274,7 +332,7 @@ __device__ __forceinline__ typename V::value warp_dfd_any(const typename V::coor
       break;
 #undef DFD_B_CASE
   }
-  return warp_dfd<V, DK, RM, AB>(P, n, Q, m, dim, vec, buf, L, st_begin, st_end, ab);
+  return warp_dfd<V, DK, RM, AB>(P, n, Q, m, dim, vec, buf, L, st_begin, st_end, ab, stage);
 }
 
 // Number of stripes warp_dfd_any uses for a pair with `rows` rows.
@@ -471,6 +529,8 @@ template <class V, int DK>
 __global__ void __launch_bounds__(256, kBlocksPerSM<DK>::value) batch_kernel(BatchArgs a) {
   using T = typename V::value;
   using Cd = typename V::coord;
+  __shared__ uint4 stage_sm[8][QStage<DK>::RECS];
+  uint4* stage = stage_sm[threadIdx.x >> 5];
   const int L = threadIdx.x & 31;
   const int64_t gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   T* buf = static_cast<T*>(a.rowbuf) + gw * BUF_COLS;
@@ -503,12 +563,14 @@ __global__ void __launch_bounds__(256, kBlocksPerSM<DK>::value) batch_kernel(Bat
     if constexpr (std::is_same<V, I32>::value) {
       if (w & kNarrowBit) {
         const float r = warp_dfd_any<I32B, DK>(pts + oa * a.dim, n, pts + ob * a.dim, m, a.dim, a.vec != 0,
-                                               reinterpret_cast<float*>(buf), L);
+                                               reinterpret_cast<float*>(buf), L, 0, 1 << 30,
+                                               static_cast<NoAbandon<I32B>*>(nullptr), stage);
         if (L == 0) write_result<I32B>(a.out_dist, a.out_dist2, k, r);
         continue;
       }
     }
-    const T r = warp_dfd_any<V, DK>(pts + oa * a.dim, n, pts + ob * a.dim, m, a.dim, a.vec != 0, buf, L);
+    const T r = warp_dfd_any<V, DK>(pts + oa * a.dim, n, pts + ob * a.dim, m, a.dim, a.vec != 0, buf, L, 0, 1 << 30,
+                                    static_cast<NoAbandon<V>*>(nullptr), stage);
     if (L == 0) write_result<V>(a.out_dist, a.out_dist2, k, r);
   }
 }
@@ -538,6 +600,8 @@ template <class V, int DK>
 __global__ void __launch_bounds__(256, kBlocksPerSM<DK>::value) decide_kernel(DecideArgs d) {
   using T = typename V::value;
   using Cd = typename V::coord;
+  __shared__ uint4 stage_sm[8][QStage<DK>::RECS];
+  uint4* stage = stage_sm[threadIdx.x >> 5];
   const BatchArgs& a = d.b;
   const int L = threadIdx.x & 31;
   const int64_t gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -576,7 +640,7 @@ __global__ void __launch_bounds__(256, kBlocksPerSM<DK>::value) decide_kernel(De
       ab.fixed = d.eps2 ? static_cast<const float*>(d.eps2)[k] : d.eps2_f;
       ab.live_bits = nullptr;
       const float r = warp_dfd_any<F32, DK, AbandonAbove<F32>>(pts + oa * a.dim, n, pts + ob * a.dim, m, a.dim,
-                                                               a.vec != 0, buf, L, 0, 1 << 30, &ab);
+                                                               a.vec != 0, buf, L, 0, 1 << 30, &ab, stage);
       hit = ab.hit;
       exact_f = r;
       within = !hit && r <= ab.fixed;
@@ -588,7 +652,7 @@ __global__ void __launch_bounds__(256, kBlocksPerSM<DK>::value) decide_kernel(De
         ab.live_bits = nullptr;
         const float r = warp_dfd_any<I32B, DK, AbandonAbove<I32B>>(pts + oa * a.dim, n, pts + ob * a.dim, m, a.dim,
                                                                    a.vec != 0, reinterpret_cast<float*>(buf), L, 0,
-                                                                   1 << 30, &ab);
+                                                                   1 << 30, &ab, stage);
         hit = ab.hit;
         exact = (long long)__float_as_uint(r);
       } else {
@@ -596,7 +660,7 @@ __global__ void __launch_bounds__(256, kBlocksPerSM<DK>::value) decide_kernel(De
         ab.fixed = e;
         ab.live_bits = nullptr;
         exact = warp_dfd_any<I32, DK, AbandonAbove<I32>>(pts + oa * a.dim, n, pts + ob * a.dim, m, a.dim,
-                                                         a.vec != 0, buf, L, 0, 1 << 30, &ab);
+                                                         a.vec != 0, buf, L, 0, 1 << 30, &ab, stage);
         hit = ab.hit;
       }
       within = !hit && exact <= e;
@@ -649,6 +713,8 @@ template <class V, int DK>
 __global__ void __launch_bounds__(256, kBlocksPerSM<DK>::value) matrix_kernel(MatrixArgs a) {
   using T = typename V::value;
   using Cd = typename V::coord;
+  __shared__ uint4 stage_sm[8][QStage<DK>::RECS];
+  uint4* stage = stage_sm[threadIdx.x >> 5];
   const int L = threadIdx.x & 31;
   const int64_t gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   T* buf = static_cast<T*>(a.rowbuf) + gw * BUF_COLS;
@@ -679,11 +745,13 @@ __global__ void __launch_bounds__(256, kBlocksPerSM<DK>::value) matrix_kernel(Ma
         if (narrow) {
           if constexpr (std::is_same<V, I32>::value) {
             const float r = warp_dfd_any<I32B, DK>(pts + oa * a.dim, rows, pts + ob * a.dim, cols, a.dim,
-                                                   a.vec != 0, reinterpret_cast<float*>(buf), L);
+                                                   a.vec != 0, reinterpret_cast<float*>(buf), L, 0, 1 << 30,
+                                                   static_cast<NoAbandon<I32B>*>(nullptr), stage);
             if (L == 0) write_result<I32B>(a.out_dist, a.out_dist2, k, r);
           }
         } else {
-          const T r = warp_dfd_any<V, DK>(pts + oa * a.dim, rows, pts + ob * a.dim, cols, a.dim, a.vec != 0, buf, L);
+          const T r = warp_dfd_any<V, DK>(pts + oa * a.dim, rows, pts + ob * a.dim, cols, a.dim, a.vec != 0, buf, L,
+                                          0, 1 << 30, static_cast<NoAbandon<V>*>(nullptr), stage);
           if (L == 0) write_result<V>(a.out_dist, a.out_dist2, k, r);
         }
       } else if (L == 0) {

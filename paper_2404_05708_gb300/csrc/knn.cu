@@ -164,6 +164,8 @@ __global__ void knn_scatter_kernel(KnnArgs a) {
 
 template <int DK>
 __global__ void __launch_bounds__(256, batch::kBlocksPerSM<DK>::value) knn_kernel(KnnArgs a) {
+  __shared__ uint4 stage_sm[8][batch::QStage<DK>::RECS];
+  uint4* stage = stage_sm[threadIdx.x >> 5];
   const int L = threadIdx.x & 31;
   const int64_t gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   float* buf = a.rowbuf + gw * batch::BUF_COLS;
@@ -211,9 +213,9 @@ __global__ void __launch_bounds__(256, batch::kBlocksPerSM<DK>::value) knn_kerne
     ab.fixed = __int_as_float(0x7f800000);
     ab.live_bits = a.limit;
     const float r = query_rows ? batch::warp_dfd_any<F32, DK, batch::AbandonAbove<F32>>(
-                                     a.query, a.n, C, m, a.dim, a.vec != 0, buf, L, 0, 1 << 30, &ab)
+                                     a.query, a.n, C, m, a.dim, a.vec != 0, buf, L, 0, 1 << 30, &ab, stage)
                                : batch::warp_dfd_any<F32, DK, batch::AbandonAbove<F32>>(
-                                     C, m, a.query, a.n, a.dim, a.vec != 0, buf, L, 0, 1 << 30, &ab);
+                                     C, m, a.query, a.n, a.dim, a.vec != 0, buf, L, 0, 1 << 30, &ab, stage);
     if (L == 0 && a.evaluated)
       atomicAdd(a.evaluated, (unsigned long long)rows * (unsigned long long)(ab.hit ? min(ab.cols_done, cols) : cols));
     if (ab.hit) continue;

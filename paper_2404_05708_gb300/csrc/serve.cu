@@ -45,6 +45,8 @@ struct Item {
 template <int DK>
 __global__ void __launch_bounds__(256, batch::kBlocksPerSM<DK>::value) serve_kernel(const Item* items, int n_items, int dim, int vec,
                                                        int* counter, float* out) {
+  __shared__ uint4 stage_sm[8][batch::QStage<DK>::RECS];
+  uint4* stage = stage_sm[threadIdx.x >> 5];
   const int L = threadIdx.x & 31;
   for (;;) {
     int i = 0;
@@ -52,7 +54,8 @@ __global__ void __launch_bounds__(256, batch::kBlocksPerSM<DK>::value) serve_ker
     i = __shfl_sync(0xffffffffu, i, 0);
     if (i >= n_items) break;
     const Item it = items[i];
-    const float r = batch::warp_dfd_any<F32, DK>(it.P, it.n, it.Q, it.m, dim, vec != 0, it.state, L, it.s0, it.s1);
+    const float r = batch::warp_dfd_any<F32, DK>(it.P, it.n, it.Q, it.m, dim, vec != 0, it.state, L, it.s0, it.s1,
+                                                 static_cast<batch::NoAbandon<F32>*>(nullptr), stage);
     if (L == 0 && it.out >= 0) out[it.out] = sqrtf(r);
   }
 }
