@@ -230,6 +230,23 @@ dfd_status dfd_batch_variant(dfd_context* ctx, dfd_variant variant, dfd_dtype dt
                              void* out, void* stream);
 
 /*
+ * Monte Carlo distance samples of two uncertain float32 curves (the
+ * application to uncertain curves named in Sec. 5).  Sample s uses
+ *   p_s[i][k] = fl(p[i][k] + sigma_p * noise_p[s][i][k]),
+ *   q_s[j][k] = fl(q[j][k] + sigma_q * noise_q[s][j][k])   (one rounding, fmaf),
+ * and out_dist2[s] / out_dist[s] receive delta_s^2 / delta_s exactly as
+ * dfd_batch computes them (any of the two may be NULL, not both).
+ *   p: n x dim, q: m x dim, noise_p: n_samples x n x dim, noise_q:
+ *   n_samples x m x dim, all device float32; the noise is the caller's (a
+ *   sample is reproducible bit for bit).
+ * The samples are built in stream-ordered device memory (cudaMallocAsync,
+ * freed in order after the launch) and computed in one batch launch.
+ */
+dfd_status dfd_mc_pair(dfd_context* ctx, int dim, const float* p, int64_t n, const float* q, int64_t m,
+                       const float* noise_p, const float* noise_q, float sigma_p, float sigma_q, int64_t n_samples,
+                       float* out_dist2, float* out_dist, void* stream);
+
+/*
  * All-pairs distance matrix of n_curves curves (the paper's motivating use:
  * clustering and distance matrices of trajectories, Sec. 2), condensed upper
  * triangle: entry k = i*(2N - i - 1)/2 + (j - i - 1) for i < j (N =

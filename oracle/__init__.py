@@ -74,6 +74,8 @@ def _declare(lib):
     lib.dfo_batch_i64.argtypes = [_I32P, _I64P, _I32P, c_i64, c_int, _I64P, c_int]
     lib.dfo_batch_f32mirror.restype = c_int
     lib.dfo_batch_f32mirror.argtypes = [_F32P, _I64P, _I32P, c_i64, c_int, _F32P, c_int]
+    lib.dfo_perturb_f32.restype = None
+    lib.dfo_perturb_f32.argtypes = [_F32P, _F32P, ctypes.c_float, c_i64, _F32P]
     lib.dfo_dtw_f32mirror.restype = ctypes.c_float
     lib.dfo_dtw_f32mirror.argtypes = [_F32P, c_i64, _F32P, c_i64, c_int]
     lib.dfo_levenshtein.restype = ctypes.c_int64
@@ -170,6 +172,18 @@ def dtw_f32mirror(p, q, lib=None):
     lib = lib or load()
     p, q, _ = _prep(np.asarray(p, np.float32), np.asarray(q, np.float32))
     return float(lib.dfo_dtw_f32mirror(_ptr(p, _F32P), p.shape[0], _ptr(q, _F32P), q.shape[0], p.shape[1]))
+
+
+def perturb(x, z, sigma, lib=None):
+    """x + sigma * z per coordinate, one float32 rounding (uncertain-curve samples)."""
+    lib = lib or load()
+    x = np.ascontiguousarray(x, np.float32)
+    z = np.ascontiguousarray(z, np.float32)
+    if x.shape != z.shape:
+        raise ValueError("x and z must have one shape")
+    out = np.empty_like(x)
+    lib.dfo_perturb_f32(_ptr(x, _F32P), _ptr(z, _F32P), float(sigma), x.size, _ptr(out, _F32P))
+    return out
 
 
 def levenshtein(a, b, lib=None):

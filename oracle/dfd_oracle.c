@@ -38,6 +38,7 @@
  *   dfo_batch_*     Alg. 5 over a list of (a, b) curve pairs, threaded
  *   dfo_dtw_*       the DTW variant of the appendix (max replaced by +)
  *   dfo_dtw_f32mirror  DTW in float32, one rounding per cell (GPU selection mirror)
+ *   dfo_perturb_f32    x + sigma * z with one rounding (Monte Carlo samples)
  *   dfo_levenshtein Wagner-Fischer edit distance (the appendix's third
  *                   variant; textbook definition, see DESIGN notes)
  *
@@ -473,6 +474,15 @@ float dfo_dtw_f32mirror(const float* p, int64_t n, const float* q, int64_t m, in
     float r = v[m - 1];
     free(v);
     return r;
+}
+
+/*
+ * Perturbed coordinates of an uncertain curve (Monte Carlo sampling, the
+ * application named in Sec. 5): out_i = x_i + sigma * z_i with one rounding
+ * (C99 fmaf), z the caller's noise.
+ */
+void dfo_perturb_f32(const float* x, const float* z, float sigma, int64_t count, float* out) {
+    for (int64_t i = 0; i < count; ++i) out[i] = fmaf(sigma, z[i], x[i]);
 }
 
 /*

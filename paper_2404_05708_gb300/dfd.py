@@ -82,6 +82,7 @@ _SIGS = {
     "dfd_batch": [_VP, _INT, _INT, _VP, _VP, _I64, _VP, _I64, _VP, _VP, _VP],
     "dfd_matrix": [_VP, _INT, _INT, _VP, _VP, _I64, _VP, _VP, _VP],
     "dfd_batch_decide": [_VP, _INT, _INT, _VP, _VP, _I64, _VP, _I64, _VP, ctypes.c_double, _VP, _VP, _VP, _VP],
+    "dfd_mc_pair": [_VP, _INT, _VP, _I64, _VP, _I64, _VP, _VP, ctypes.c_float, ctypes.c_float, _I64, _VP, _VP, _VP],
     "dfd_batch_variant": [_VP, _INT, _INT, _INT, _VP, _VP, _I64, _VP, _I64, _VP, _VP],
     "dfd_knn": [_VP, _INT, _VP, _I64, _VP, _VP, _I64, _VP, _I64, _INT, _VP, _VP, _VP, _VP, _VP, _VP],
     "dfd_batch_capture": [_VP, _INT, _INT, _VP, _VP, _I64, _VP, _I64, _VP, _VP, ctypes.POINTER(_VP)],
@@ -197,6 +198,12 @@ def dfd_batch_decide(ctx, dtype, dim, points, offsets, n_curves, pairs, n_pairs,
                      out_within, abandoned, stream) -> int:
     return load_library().dfd_batch_decide(ctx, dtype, dim, points, offsets, n_curves, pairs, n_pairs, eps2,
                                            float(eps2_all), out_dist2, out_within, abandoned, stream)
+
+
+def dfd_mc_pair(ctx, dim, p, n, q, m, noise_p, noise_q, sigma_p, sigma_q, n_samples, out_dist2, out_dist,
+                stream) -> int:
+    return load_library().dfd_mc_pair(ctx, dim, p, n, q, m, noise_p, noise_q, float(sigma_p), float(sigma_q),
+                                      n_samples, out_dist2, out_dist, stream)
 
 
 def dfd_batch_variant(ctx, variant, dtype, dim, points, offsets, n_curves, pairs, n_pairs, out, stream) -> int:
@@ -567,6 +574,27 @@ class Context:
                               out_within.data_ptr(), ab.data_ptr(), s)
         _check(st, "dfd_batch_decide")
         return out_dist2, out_within, ab
+
+    def mc_pair(self, p, q, noise_p, noise_q, sigma_p, sigma_q, stream=None):
+        """Monte Carlo samples of delta for uncertain float32 curves: returns
+        (dist, dist2), float32[n_samples], sample s perturbing p and q by
+        sigma * noise[s] (noise_p: [S, n, dim], noise_q: [S, m, dim])."""
+        torch = _torch()
+        p, q = _curve(p), _curve(q)
+        noise_p, noise_q = noise_p.contiguous(), noise_q.contiguous()
+        if p.dtype != torch.float32 or q.dtype != torch.float32 or noise_p.dtype != torch.float32 or \
+                noise_q.dtype != torch.float32:
+            raise TypeError("curves and noise must be float32")
+        S = noise_p.shape[0]
+        if tuple(noise_p.shape) != (S, p.shape[0], p.shape[1]) or tuple(noise_q.shape) != (S, q.shape[0], q.shape[1]):
+            raise ValueError("noise_p must be [S, n, dim] and noise_q [S, m, dim]")
+        d = torch.empty(S, dtype=torch.float32, device=p.device)
+        d2 = torch.empty(S, dtype=torch.float32, device=p.device)
+        s = stream if stream is not None else torch.cuda.current_stream(self.device).cuda_stream
+        st = dfd_mc_pair(self.handle, p.shape[1], p.data_ptr(), p.shape[0], q.data_ptr(), q.shape[0],
+                         noise_p.data_ptr(), noise_q.data_ptr(), sigma_p, sigma_q, S, d2.data_ptr(), d.data_ptr(), s)
+        _check(st, "dfd_mc_pair")
+        return d, d2
 
     def dtw(self, points, offsets, pairs, out=None, stream=None):
         """DTW (appendix variant, squared-distance ground cost) of float32 CSR pairs."""

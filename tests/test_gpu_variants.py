@@ -80,3 +80,27 @@ def test_variant_argument_errors(dctx):
         dctx.dtw(dev(pts), dev(off), dev(pairs))            # DTW needs float32
     with pytest.raises(dfd.DFDError):
         dctx.levenshtein(dev(pts), dev(off), dev(pairs))    # Levenshtein needs one symbol per position
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_mc_pair_samples_match_oracle(dctx, dim):
+    """Each Monte Carlo sample equals the oracle's float32 mirror on the
+    oracle's own perturbation (one rounding) of the same noise."""
+    rng = np.random.default_rng(90 + dim)
+    n, m, S = 300, 200, 40
+    p = np.cumsum(rng.normal(size=(n, dim)), 0).astype(np.float32)
+    q = np.cumsum(rng.normal(size=(m, dim)), 0).astype(np.float32)
+    zp = rng.normal(size=(S, n, dim)).astype(np.float32)
+    zq = rng.normal(size=(S, m, dim)).astype(np.float32)
+    sp, sq = 0.3, 0.7
+    d, d2 = dctx.mc_pair(dev(p), dev(q), dev(zp), dev(zq), sp, sq)
+    torch.cuda.synchronize()
+    d2 = d2.cpu().numpy()
+    for s in range(S):
+        ps = oracle.perturb(p, zp[s], sp)
+        qs = oracle.perturb(q, zq[s], sq)
+        assert d2[s] == np.float32(oracle.dfd2_f32mirror(ps, qs)), s
+    # sigma = 0: every sample is the unperturbed distance
+    d0, d20 = dctx.mc_pair(dev(p), dev(q), dev(zp[:3]), dev(zq[:3]), 0.0, 0.0)
+    torch.cuda.synchronize()
+    assert np.all(d20.cpu().numpy() == np.float32(oracle.dfd2_f32mirror(p, q)))

@@ -237,6 +237,28 @@ def test_dtw_f32mirror_planted_mistake_is_caught():
     assert oracle.dtw_f32mirror(p, q) > oracle.dfd2_f32mirror(p, q)
 
 
+def test_perturb_single_rounding():
+    """x + sigma*z with one rounding: exact where the exact value is a
+    float32; where the float64 sum of x and the (exact) float64 product is
+    itself exact, equal to that sum rounded once to float32."""
+    rng = np.random.default_rng(23)
+    x = rng.integers(-1000, 1000, size=500).astype(np.float32)
+    z = rng.integers(-64, 64, size=500).astype(np.float32) / np.float32(8)
+    out = oracle.perturb(x, z, 0.25)
+    assert np.array_equal(out, x + np.float32(0.25) * z)      # all exact
+    x = rng.normal(size=2000).astype(np.float32)
+    z = rng.normal(size=2000).astype(np.float32)
+    sigma = np.float32(0.3)
+    prod = z.astype(np.float64) * np.float64(sigma)            # exact in float64
+    s64 = x.astype(np.float64) + prod
+    exact = (s64 - x.astype(np.float64)) == prod                # the float64 sum did not round
+    assert exact.sum() > 100
+    assert np.array_equal(oracle.perturb(x, z, sigma)[exact], s64[exact].astype(np.float32))
+    # planted mistake: two roundings (product first) differ somewhere
+    two = (np.float32(sigma) * z) + x
+    assert not np.array_equal(two, oracle.perturb(x, z, sigma))
+
+
 def test_levenshtein_known_and_brute():
     enc = lambda s: np.array([ord(c) for c in s], np.int32)
     assert oracle.levenshtein(enc("kitten"), enc("sitting")) == 3
