@@ -55,6 +55,17 @@ REF_SAMPLE = 20_000          # --impl reference: prefix per step
 TRAFFIC_BY_KERNEL_SHA: dict = {"5703067a15fc0880": 9429568}
 
 
+def long_workload(n, m):
+    return f"long pair {n}x{m}, {DIM}-D float32 warped random walk (seed {SEED})"
+
+
+PAIR2K_WORKLOAD = "pair 2000x1500, 2-D float32 Gaussian walks (seeds 1, 2)"
+BATCH_WORKLOAD = ("ragged batch, {n:,} pairs of int32 2-D random walks, lengths U{{16..512}} (seed 4), "
+                  "one persistent launch per step in a captured CUDA graph")
+MATRIX_WORKLOAD = ("all-pairs matrix (upper triangle) of 4096 float32 16-D AR(1) curves (phi 0.95), "
+                   "lengths U{64..256} (seed 5), one launch per step in a CUDA graph")
+
+
 def kernel_sha(files=("wave_kernel.cuh", "wave_launch.cuh", "wave_shape.h", "dfd_device.cuh")) -> str:
     h = hashlib.sha256()
     for f in files:
@@ -163,7 +174,7 @@ class LongPair:
             # Untimed setup: time each candidate launch shape once, keep the fastest.
             shape, tuned = ctx.autotune(self.p, self.q), True
             torch.cuda.synchronize()
-        self.config = {"workload": f"long pair {self.n}x{self.m}, {DIM}-D float32 warped random walk (seed {SEED})",
+        self.config = {"workload": long_workload(self.n, self.m),
                        "n": self.n, "m": self.m, "dim": DIM, "cells_per_step": self.cells,
                        "launch_shape": {"rows_per_lane": shape[0], "warps": shape[1], "ctas": shape[2],
                                         "autotuned": tuned},
@@ -220,7 +231,7 @@ class Pair2k(LongPair):
         self.d = torch.empty(1, dtype=torch.float32, device="cuda")
         self.d2 = torch.empty(1, dtype=torch.float32, device="cuda")
         self.cells = self.n * self.m
-        self.config = {"workload": "pair 2000x1500, 2-D float32 Gaussian walks (seeds 1, 2)", "n": self.n,
+        self.config = {"workload": PAIR2K_WORKLOAD, "n": self.n,
                        "m": self.m, "dim": 2, "cells_per_step": self.cells}
         self.h2d = (self.n + self.m) * 2 * 4
         self.d2h = 16
@@ -301,8 +312,7 @@ class Batch(_Many):
         self.pairs = torch.from_numpy(pairs).cuda()
         self.graph, self.out, self.out2 = ctx.batch(self.pts_dev, self.off, self.pairs, capture=True)
         self.out_host = torch.empty_like(self.out2, device="cpu").pin_memory()
-        self.config = {"workload": f"ragged batch, {b.pairs.shape[0]:,} pairs of int32 2-D random walks, lengths U{{16..512}} "
-                                   "(seed 4), one persistent launch per step in a captured CUDA graph",
+        self.config = {"workload": BATCH_WORKLOAD.format(n=b.pairs.shape[0]),
                        "n_pairs": int(pairs.shape[0]), "dim": 2, "cells_per_step": self.cells,
                        "kernel_sha": kernel_sha(("batch_kernel.cuh", "batch_launch.cuh", "dfd_device.cuh"))}
         self.h2d = b.points.nbytes
@@ -383,8 +393,7 @@ class Matrix(_Many):
         self.graph, self.out, self.out2 = ctx.matrix(self.pts_dev, self.off, capture=True)
         self.out_host = torch.empty_like(self.out2, device="cpu").pin_memory()
         n = b.n_curves
-        self.config = {"workload": "all-pairs matrix (upper triangle) of 4096 float32 16-D AR(1) curves "
-                                   "(phi 0.95), lengths U{64..256} (seed 5), one launch per step in a CUDA graph",
+        self.config = {"workload": MATRIX_WORKLOAD,
                        "n_curves": n, "n_pairs": n * (n - 1) // 2, "dim": 16, "cells_per_step": self.cells,
                        "kernel_sha": kernel_sha(("batch_kernel.cuh", "batch_launch.cuh", "dfd_device.cuh"))}
         self.h2d = b.points.nbytes
@@ -604,12 +613,12 @@ def run_reference(args):
             a = min(REF_SAMPLE, args.n, args.m)
             ps, qs = p[:a].copy(), q[:a].copy()
             sample = f"prefix p[:{a}], q[:{a}] of the {args.n}x{args.m} pair per step (Alg. 5, float64, 1 thread)"
-            cfg = {"workload": f"long pair {args.n}x{args.m}, {DIM}-D float32 warped random walk",
-                   "n": args.n, "m": args.m, "dim": DIM}
+            cfg = {"workload": long_workload(args.n, args.m), "n": args.n, "m": args.m, "dim": DIM,
+                   "cells_per_step": args.n * args.m}
         else:
             ps, qs = workloads.gaussian_walk_pair(2000, 1500, dim=2)
             sample = "the full 2000x1500 pair per step (Alg. 5, float64, 1 thread)"
-            cfg = {"workload": "pair 2000x1500, 2-D float32 Gaussian walks", "n": 2000, "m": 1500, "dim": 2}
+            cfg = {"workload": PAIR2K_WORKLOAD, "n": 2000, "m": 1500, "dim": 2, "cells_per_step": 2000 * 1500}
         cells_step = ps.shape[0] * qs.shape[0]
         for _ in range(args.warmup):
             oracle.dfd2_linear(ps, qs)
@@ -623,14 +632,17 @@ def run_reference(args):
             b = workloads.ragged_int_batch()
             pairs = b.pairs[:4096]
             dtype = "int64"
-            cfg = {"workload": "ragged batch, 65,536 pairs of int32 2-D random walks", "dim": 2}
+            cfg = {"workload": BATCH_WORKLOAD.format(n=b.pairs.shape[0]), "n_pairs": int(b.pairs.shape[0]), "dim": 2,
+                   "cells_per_step": int(np.sum(b.lengths()[b.pairs[:, 0]] * b.lengths()[b.pairs[:, 1]]))}
             sample = "first 4096 pairs of the batch per step (Alg. 5, int64, all host threads)"
         else:
             b = workloads.ar1_curves()
             rng = np.random.default_rng(3)
             pairs = np.stack([rng.integers(0, 4096, 4096), rng.integers(0, 4096, 4096)], 1).astype(np.int32)
             dtype = "f64"
-            cfg = {"workload": "all-pairs matrix of 4096 float32 16-D AR(1) curves", "dim": 16}
+            ln_all = b.lengths().astype(np.int64)
+            cfg = {"workload": MATRIX_WORKLOAD, "n_curves": 4096, "n_pairs": 4096 * 4095 // 2, "dim": 16,
+                   "cells_per_step": int((ln_all.sum() ** 2 - (ln_all ** 2).sum()) // 2)}
             sample = "4096 random pairs per step (Alg. 5, float64, all host threads)"
         ln = b.lengths()
         cells_step = int(np.sum(ln[pairs[:, 0]] * ln[pairs[:, 1]]))
