@@ -63,7 +63,7 @@ typedef enum dfd_status {
   DFD_ERR_BUSY = 7,        /* resource limit reached, retry later */
   DFD_ERR_CANCELLED = 8,   /* work was cancelled before it finished */
   DFD_ERR_NOT_READY = 9,   /* result not available yet */
-  DFD_ERR_UNSUPPORTED = 10, /* configuration not provided by this build */
+  DFD_ERR_UNSUPPORTED = 10, /* configuration the library does not support */
   DFD_ERR_CAPACITY = 11     /* input needs more than a fixed-size buffer holds */
 } dfd_status;
 
