@@ -108,10 +108,10 @@ __device__ __forceinline__ void load_point(const Cd* __restrict__ Q, int j, int 
 // bottom cell (the lane's `upp`, which a diagonal step could otherwise slip
 // past) form such a set while lane 0 has not passed the last column: a path
 // starts left of it in row 0 and must reach column m-1 in the last row.  A
-// pair whose minimum there exceeds the limit has delta^2 above it and is
-// abandoned; ties never abandon.  (One stripe of a taller pair is not such
-// a set: a path may pass left of it and leave through the stripe's bottom
-// row, so multi-stripe pairs are always computed to the end.)
+// stripe of a taller pair adds the cells through which a path can avoid its
+// frontier (see bmin / sufb in warp_dfd).  A pair whose minimum there
+// exceeds the limit has delta^2 above it and is abandoned; ties never
+// abandon.
 template <class V>
 struct NoAbandon {
   static constexpr bool on = false;
@@ -176,6 +176,43 @@ __device__ __forceinline__ typename V::value warp_dfd(const typename V::coord* _
     for (int r = 0; r < R; ++r) v[r] = V::inf();
     T bout = V::inf();
     T upp = (st == 0 && L == 0) ? V::zero() : V::inf();
+    // Early abandon of a multi-stripe pair: the stripe's frontier cut is
+    // completed by (a) the cells of the stripe's bottom row already swept
+    // (`bmin`, lane 31: a path passing left of the frontier leaves through
+    // them) and (b) the previous stripe's bottom row from lane 0's column on
+    // (a path entering right of the frontier comes through it), kept as
+    // suffix minima per 32-column block (`sufb`, block L + 32t on lane L).
+    T bmin = V::inf();
+    T sufb[AB::on ? BUF_COLS / 1024 : 1];
+    if constexpr (AB::on) {
+#pragma unroll
+      for (int t = 0; t < BUF_COLS / 1024; ++t) sufb[t] = V::inf();
+      if (has_top) {
+        const int nb = (m + 31) / 32;
+        for (int b = 0; b < nb; ++b) {
+          const int c = 32 * b + L;
+          T x = c < m ? buf[c] : V::inf();
+#pragma unroll
+          for (int off = 16; off > 0; off >>= 1) x = V::vmin(x, __shfl_xor_sync(0xffffffffu, x, off));
+#pragma unroll
+          for (int t = 0; t < BUF_COLS / 1024; ++t)
+            if (L == (b & 31) && t == (b >> 5)) sufb[t] = x;
+        }
+        T carry = V::inf();   // minimum over the blocks of higher t
+#pragma unroll
+        for (int t = BUF_COLS / 1024 - 1; t >= 0; --t) {
+          T x = sufb[t];
+#pragma unroll
+          for (int off = 1; off < 32; off <<= 1) {
+            const T y = __shfl_down_sync(0xffffffffu, x, off);
+            if (L + off < 32) x = V::vmin(x, y);
+          }
+          x = V::vmin(x, carry);
+          carry = __shfl_sync(0xffffffffu, x, 0);
+          sufb[t] = x;
+        }
+      }
+    }
     const int nsteps = m + 31;
     // q point of the coming step, loaded one step ahead (the load's latency
     // stays off the step's chain)
@@ -272,6 +309,7 @@ __device__ __forceinline__ typename V::value warp_dfd(const typename V::coord* _
         }
         upp = u;
         bout = up;
+        if constexpr (AB::on) bmin = V::vmin(bmin, bout);
         if (has_bottom) {
           const T b31 = __shfl_sync(0xffffffffu, bout, 31);
           out_blk = (L == s) ? b31 : out_blk;
@@ -286,13 +324,25 @@ __device__ __forceinline__ typename V::value warp_dfd(const typename V::coord* _
       }
       __syncwarp();
       if constexpr (AB::on) {
-        // (a cut of the whole grid only when this stripe is the whole grid)
-        if (!has_top && !has_bottom && c0 + 31 <= m - 1) {
+        if (c0 + 31 <= m - 1) {
           T cut = upp;
 #pragma unroll
           for (int r = 0; r < R; ++r) cut = V::vmin(cut, v[r]);
 #pragma unroll
           for (int off = 16; off > 0; off >>= 1) cut = V::vmin(cut, __shfl_xor_sync(0xffffffffu, cut, off));
+          if (has_bottom) cut = V::vmin(cut, __shfl_sync(0xffffffffu, bmin, 31));
+          if (has_top) {
+            // previous stripe's bottom row from column c0 + 31 on: that column
+            // (lane 31's top value of this block) and the blocks after it
+            const int nb = c0 / 32 + 1;
+            T sv = V::inf();
+#pragma unroll
+            for (int t = 0; t < BUF_COLS / 1024; ++t)
+              if (t == (nb >> 5)) sv = sufb[t];
+            sv = __shfl_sync(0xffffffffu, sv, nb & 31);
+            if (nb >= (m + 31) / 32) sv = V::inf();
+            cut = V::vmin(cut, V::vmin(sv, __shfl_sync(0xffffffffu, top_blk, 31)));
+          }
           if (cut > ab->limit()) {
             ab->hit = true;
             ab->cols_done = c0 + 32;
