@@ -62,8 +62,8 @@ def long_workload(n, m):
 PAIR2K_WORKLOAD = "pair 2000x1500, 2-D float32 Gaussian walks (seeds 1, 2)"
 BATCH_WORKLOAD = ("ragged batch, {n:,} pairs of int32 2-D random walks, lengths U{{16..512}} (seed 4), "
                   "one persistent launch per step in a captured CUDA graph")
-MATRIX_WORKLOAD = ("all-pairs matrix (upper triangle) of 4096 float32 16-D AR(1) curves (phi 0.95), "
-                   "lengths U{64..256} (seed 5), one launch per step in a CUDA graph")
+MATRIX_WORKLOAD = ("all-pairs matrix (upper triangle) of {n} float32 16-D AR(1) curves (phi 0.95), "
+                   "lengths U{{64..256}} (seed 5), one launch per step in a CUDA graph")
 
 
 def kernel_sha(files=("wave_kernel.cuh", "wave_launch.cuh", "wave_shape.h", "dfd_device.cuh")) -> str:
@@ -89,6 +89,7 @@ def parse():
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--shape", default="", help="long pair: fixed launch shape R,W,ctas (no autotune)")
     ap.add_argument("--pairs", type=int, default=0, help="batch: number of pairs (default 65,536)")
+    ap.add_argument("--curves", type=int, default=0, help="matrix: number of curves (default 4096)")
     return ap.parse_args()
 
 
@@ -381,7 +382,7 @@ class Matrix(_Many):
     def __init__(self, args, ctx, dfd, torch, workloads, rank, world):
         if world > 1:
             raise SystemExit("the matrix workload runs on one GPU")
-        b = workloads.ar1_curves()
+        b = workloads.ar1_curves(n_curves=args.curves) if args.curves else workloads.ar1_curves()
         self.b = b
         self.ctx, self.torch = ctx, torch
         ln = b.lengths().astype(np.int64)
@@ -393,7 +394,7 @@ class Matrix(_Many):
         self.graph, self.out, self.out2 = ctx.matrix(self.pts_dev, self.off, capture=True)
         self.out_host = torch.empty_like(self.out2, device="cpu").pin_memory()
         n = b.n_curves
-        self.config = {"workload": MATRIX_WORKLOAD,
+        self.config = {"workload": MATRIX_WORKLOAD.format(n=n),
                        "n_curves": n, "n_pairs": n * (n - 1) // 2, "dim": 16, "cells_per_step": self.cells,
                        "kernel_sha": kernel_sha(("batch_kernel.cuh", "batch_launch.cuh", "dfd_device.cuh"))}
         self.h2d = b.points.nbytes
@@ -641,7 +642,7 @@ def run_reference(args):
             pairs = np.stack([rng.integers(0, 4096, 4096), rng.integers(0, 4096, 4096)], 1).astype(np.int32)
             dtype = "f64"
             ln_all = b.lengths().astype(np.int64)
-            cfg = {"workload": MATRIX_WORKLOAD, "n_curves": 4096, "n_pairs": 4096 * 4095 // 2, "dim": 16,
+            cfg = {"workload": MATRIX_WORKLOAD.format(n=4096), "n_curves": 4096, "n_pairs": 4096 * 4095 // 2, "dim": 16,
                    "cells_per_step": int((ln_all.sum() ** 2 - (ln_all ** 2).sum()) // 2)}
             sample = "4096 random pairs per step (Alg. 5, float64, all host threads)"
         ln = b.lengths()
