@@ -30,14 +30,15 @@ struct kBlocksPerSM {
   static constexpr int value = 2;
 };
 
-// Wide points (dim class >= 8) stream through a per-warp shared-memory ring
-// of 64 q points instead of per-lane L1/L2 loads: the warp loads the next 32
-// points cooperatively one block ahead (one point per lane, coalesced) and
-// every step reads them from shared memory, plane-major ([16-byte plane][64
-// points]) so that lanes one column apart read consecutive records.
+// q streams through a per-warp shared-memory ring of 64 points instead of
+// per-lane L1/L2 loads: the warp loads the next 32 points cooperatively one
+// block ahead (one point per lane, coalesced) and every step reads them from
+// shared memory, plane-major ([16-byte plane][64 points]) so that lanes one
+// column apart read consecutive records.  (Per-lane loads left lane 0
+// waiting on L2 for every new point.)
 template <int DK>
 struct QStage {
-  static constexpr bool on = DK >= 8;
+  static constexpr bool on = true;
   static constexpr int NPL = (DK + 3) / 4;
   static constexpr int RECS = on ? NPL * 64 : 1;   // uint4 records per warp
 };
@@ -448,6 +449,7 @@ __global__ void curve_bbox_kernel(const int32_t* __restrict__ pts, const int64_t
     }
     if (o >= 0 && e <= total && o < e) {
       const int32_t* Q = pts + o * dim;
+#pragma unroll 4
       for (int64_t j = L; j < e - o; j += 32) {
         int32_t qk[DK];
         load_point<int32_t, DK>(Q, (int)j, dim, vec != 0, qk);
