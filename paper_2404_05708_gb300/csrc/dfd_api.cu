@@ -461,9 +461,13 @@ dfd_status dfd_pair_autotune(dfd_context* ctx, dfd_dtype dtype, int dim, const v
     cudaGetLastError();
     return DFD_ERR_OOM;
   }
-  cudaEvent_t e0, e1;
-  cudaEventCreate(&e0);
-  cudaEventCreate(&e1);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    cudaGetLastError();
+    if (e0) cudaEventDestroy(e0);
+    cudaFreeAsync(res, s);
+    return DFD_ERR_CUDA;
+  }
   WaveShape best;
   wave_plan(ctx, dtype, dim, n, m, &best);
   float best_ms = 1e30f;

@@ -66,3 +66,19 @@ def test_no_cpu_fallback_without_device(lib):
     with pytest.raises(dfd.DFDError) as e:
         dfd.dfd_context_create(0)
     assert e.value.status == dfd.STATUS_CODE["DFD_ERR_CUDA"]
+
+
+def test_entry_points_reject_null_context_without_touching_a_device(lib):
+    """Host-side validation: every computing entry point returns
+    DFD_ERR_INVALID_ARG for a NULL context before any CUDA call."""
+    inv = dfd.STATUS_CODE["DFD_ERR_INVALID_ARG"]
+    dummy = 0x1000   # never dereferenced: the NULL context is rejected first
+    assert dfd.dfd_pair(None, dfd.DFD_F32, 2, dummy, 4, dummy, 4, dummy, dummy, None) == inv
+    assert dfd.dfd_batch(None, dfd.DFD_F32, 2, dummy, dummy, 2, dummy, 1, dummy, dummy, None) == inv
+    assert dfd.dfd_matrix(None, dfd.DFD_F32, 2, dummy, dummy, 3, dummy, dummy, None) == inv
+    assert dfd.dfd_batch_decide(None, dfd.DFD_F32, 2, dummy, dummy, 2, dummy, 1, None, 1.0, dummy, dummy,
+                                None, None) == inv
+    assert dfd.dfd_knn(None, 2, dummy, 4, dummy, dummy, 2, None, 2, 1, dummy, dummy, None, None, None, None) == inv
+    assert dfd.dfd_batch_variant(None, dfd.DFD_VARIANT_DTW, dfd.DFD_F32, 2, dummy, dummy, 2, dummy, 1, dummy,
+                                 None) == inv
+    assert dfd.dfd_mc_pair(None, 2, dummy, 4, dummy, 4, dummy, dummy, 0.1, 0.1, 1, dummy, dummy, None) == inv
