@@ -83,6 +83,8 @@ def parse():
     ap.add_argument("--workload", default="long", choices=["long", "batch", "matrix", "pair2k", "serve", "knn"])
     ap.add_argument("--rates", default="100,300,1000,3000,10000")
     ap.add_argument("--serve-seconds", type=float, default=2.0)
+    ap.add_argument("--tick-cells", type=float, default=2e9, help="serve: cell budget of one tick")
+    ap.add_argument("--stripes-per-tick", type=int, default=4, help="serve: row stripes a long pair advances per tick")
     ap.add_argument("--n", type=int, default=N_POINTS)
     ap.add_argument("--m", type=int, default=N_POINTS)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -557,7 +559,8 @@ def run_serving(args):
     torch.cuda.set_device(0)
     ctx = dfd.Context(0)
     pools = {d: workloads.serving_pool(dim=d, seed=6 + d) for d in (2, 3)}
-    srv = dfd.Server(ctx, mem_budget_bytes=4 << 30, max_slots=512, tick_cells=2e9, stripes_per_tick=4)
+    srv = dfd.Server(ctx, mem_budget_bytes=4 << 30, max_slots=512, tick_cells=args.tick_cells,
+                     stripes_per_tick=args.stripes_per_tick)
     for d in (2, 3):
         srv.add_candidates(pools[d].points, pools[d].offsets)
     rates = [float(r) for r in args.rates.split(",")]

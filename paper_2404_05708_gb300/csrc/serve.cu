@@ -194,6 +194,8 @@ struct dfd_server {
   std::unordered_map<uint64_t, std::unique_ptr<Request>> requests;
   uint64_t next_ticket = 1;
   Tick ticks[2];
+  std::vector<int> sort_count, sort_key;   // build_tick's counting sort (reused buffers)
+  std::vector<Item> sort_items;
   int next_tick = 0;
   std::deque<Tick*> inflight;
   std::thread worker;
@@ -350,11 +352,30 @@ void build_tick(dfd_server* s, Tick& t) {
     while (r->next_pair < (int64_t)r->pairs.size() && r->pairs[r->next_pair].issued >= r->pairs[r->next_pair].nst)
       r->next_pair++;
   }
-  // one launch per dimension; costliest items first inside it (LPT)
-  std::stable_sort(t.items.begin(), t.items.end(), [](const Item& a, const Item& b) {
-    if (a.dim != b.dim) return a.dim < b.dim;
-    return (double)(a.s1 - a.s0) * a.m * std::min(a.n, 256) > (double)(b.s1 - b.s0) * b.m * std::min(b.n, 256);
-  });
+  // One launch per dimension; costliest items first inside it (LPT by
+  // power-of-two cost classes): a counting sort, linear in the items, where
+  // a comparison sort of every pair was the scheduler's largest per-pair cost.
+  constexpr int NCLS = 48;
+  const size_t n_it = t.items.size();
+  if (n_it > 1) {
+    std::vector<int>& cnt = s->sort_count;
+    cnt.assign((MAX_DIM + 1) * NCLS + 1, 0);
+    std::vector<int>& key = s->sort_key;
+    key.resize(n_it);
+    for (size_t i = 0; i < n_it; ++i) {
+      const Item& it = t.items[i];
+      const unsigned long long c =
+          (unsigned long long)(it.s1 - it.s0) * (unsigned long long)it.m * (unsigned long long)std::min(it.n, 256);
+      const int b = c > 1 ? std::min(NCLS - 1, 63 - __builtin_clzll(c)) : 0;
+      key[i] = std::min(it.dim, MAX_DIM) * NCLS + (NCLS - 1 - b);
+      ++cnt[key[i] + 1];
+    }
+    for (size_t k = 1; k < cnt.size(); ++k) cnt[k] += cnt[k - 1];
+    std::vector<Item>& out = s->sort_items;
+    out.resize(n_it);
+    for (size_t i = 0; i < n_it; ++i) out[cnt[key[i]]++] = t.items[i];
+    t.items.swap(out);
+  }
 }
 
 void launch_tick(dfd_server* s, Tick& t) {
