@@ -81,10 +81,10 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="long", choices=["long", "batch", "matrix", "pair2k", "serve", "knn"])
-    ap.add_argument("--rates", default="100,300,1000,3000,10000")
+    ap.add_argument("--rates", default="100,1000,3000,10000,20000,30000")
     ap.add_argument("--serve-seconds", type=float, default=2.0)
-    ap.add_argument("--tick-cells", type=float, default=2e9, help="serve: cell budget of one tick")
-    ap.add_argument("--stripes-per-tick", type=int, default=4, help="serve: row stripes a long pair advances per tick")
+    ap.add_argument("--tick-cells", type=float, default=4e9, help="serve: cell budget of one tick")
+    ap.add_argument("--stripes-per-tick", type=int, default=8, help="serve: row stripes a long pair advances per tick")
     ap.add_argument("--n", type=int, default=N_POINTS)
     ap.add_argument("--m", type=int, default=N_POINTS)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -596,7 +596,8 @@ def run_serving(args):
            "higher_is_better": True, "dtype": "f32", "data": "synthetic",
            "config": {"workload": "serving: Poisson stream of query-vs-k-candidates requests (dims 2, 3; "
                                   "lognormal lengths median 256 clipped [32, 4096]; k ~ U{1..1024}) against "
-                                  "2^16 resident candidates per dim"},
+                                  "2^16 resident candidates per dim",
+                      "tick_cells": args.tick_cells, "stripes_per_tick": args.stripes_per_tick},
            "serving": sweep}
     print(json.dumps(out))
     return 0

@@ -283,25 +283,30 @@ dfd_status dfd_graph_destroy(dfd_graph* graph);
  * request: one query curve and k candidate ids; the k distances are written
  * to host_out[0..k) before dfd_server_wait returns DFD_OK.  A scheduler
  * thread admits requests in arrival order while fewer than max_slots are
- * running and the device arena (mem_budget_bytes) holds their query (O(n));
- * it runs ticks -- one persistent launch per point dimension over pairs from
- * every admitted request, costliest first, up to tick_cells cells -- and a
- * pair longer than one row stripe advances at most stripes_per_tick stripes
- * per tick, its O(m) bottom row kept in the arena between ticks (the prefix
+ * running and the device arena (mem_budget_bytes) holds their query and
+ * candidate ids (O(n + k)); it runs ticks -- one persistent launch per point
+ * dimension over pairs from every admitted request, oldest request first,
+ * costliest pairs first inside a launch, up to tick_cells cells.  Pairs that
+ * finish within a tick are expanded from per-request ranges on the device;
+ * a pair with more than stripes_per_tick row stripes (or a multi-stripe pair
+ * wider than 4096 points) advances at most stripes_per_tick stripes per
+ * tick, its O(m) bottom row kept in the arena between ticks (the prefix
  * property of Sec. 3).  Requests that arrive while others run join the next
  * tick; two ticks are in flight.  Each distance is bit-identical to
  * dfd_pair's for the same two curves, whatever else is in the tick.
  * Ownership: submit copies the query and ids; host_out must stay valid
  * until wait returns OK or CANCELLED.  A ticket is released by the wait that
  * returns its final status.  Destroy the server before its context.
+ * Limits: at most INT32_MAX candidates per dimension; a request whose query
+ * and ids exceed 32 MiB of staging returns DFD_ERR_CAPACITY from submit.
  */
 typedef struct dfd_server dfd_server;
 typedef struct dfd_server_options {
   size_t struct_size;        /* sizeof(dfd_server_options) */
-  size_t mem_budget_bytes;   /* device arena for queries and row states (default 1 GiB) */
+  size_t mem_budget_bytes;   /* device arena for queries, candidate ids and row states (default 1 GiB) */
   int max_slots;             /* requests running at once (default 256) */
-  double tick_cells;         /* cells per tick (default 2e9) */
-  int stripes_per_tick;      /* row stripes a long pair advances per tick (default 4) */
+  double tick_cells;         /* cells per tick (default 4e9) */
+  int stripes_per_tick;      /* row stripes a long pair advances per tick (default 8) */
 } dfd_server_options;
 typedef struct dfd_serving_stats {
   uint64_t completed, cancelled, ticks;

@@ -2,15 +2,28 @@
 //
 // Requests (a query curve and k candidate ids from a device-resident pool)
 // arrive from any host thread.  A scheduler thread admits them while slots
-// and device memory allow (a request's footprint is its query, O(n), plus an
-// O(m) row state for each long pair in flight), and runs ticks: each tick is
-// one persistent launch (per point dimension present) over (query,
-// candidate) pairs drawn from every admitted request, costliest first, up to
-// a cell budget.  Pairs longer than one stripe advance a few row stripes per
+// and device memory allow (a request's footprint is its query and candidate
+// ids, O(n + k), plus an O(m) row state for each long pair in flight), and
+// runs ticks: each tick is one persistent launch per point dimension present
+// over (query, candidate) pairs drawn from every admitted request, oldest
+// request first, up to a cell budget.
+//
+// Admission sorts a request's pairs by cost class (power-of-two cell count).
+// Pairs that finish within one tick are handed to a tick as slices -- a run
+// of consecutive positions in that order, one class per slice -- and
+// expanded into pairs on the device: a warp takes a global pair index and
+// finds its slice by a 32-way search of the slices' prefix sums.  So the
+// host's work per tick grows with the requests, not with the pairs.  Only
+// long pairs (more row stripes than a tick runs, or a row state wider than a
+// warp's buffer) go out one by one as items: they advance a few stripes per
 // tick and keep their bottom row in device memory between ticks (row i of
 // the recurrence summarises rows 1..i, Sec. 3), so a long pair never blocks
-// the requests that arrive behind it.  Two ticks are in flight at a time:
-// while the GPU runs tick t the host prepares tick t+1 and retires t-1.
+// the requests behind it.  Inside a launch the items come first, then the
+// slices in decreasing cost class (largest first, LPT).  Two ticks are in
+// flight, each on its own stream: while tick t drains its last warps, tick
+// t+1's blocks already take the SMs it frees (a long pair is in at most one
+// tick in flight, so the two never share a row state), and the host
+// prepares the next tick while it retires the oldest.
 #include <algorithm>
 #include <atomic>
 #include <chrono>
@@ -32,6 +45,7 @@
 namespace dfd {
 namespace serve {
 
+// One long pair's stripes [s0, s1).
 struct Item {
   const float* P;   // rows curve (device)
   const float* Q;   // column curve (device)
@@ -42,21 +56,91 @@ struct Item {
   int dim;          // point dimension (items are grouped by it)
 };
 
+// `count` pairs of one request, expanded on the device: pair li compares the
+// query with candidate cids[li] and writes its distance to out[out_base + li].
+struct Slice {
+  const float* query;     // device, n x dim
+  const int32_t* cids;    // device, candidate ids of the slice's pairs
+  int n;                  // query points
+  int count;              // pairs
+  int out_base;           // output slot of the slice's first pair
+  int pad;
+};
+
+struct ServeArgs {
+  const Item* items;      // long pairs (first in the launch's index space)
+  int n_items;
+  int n_slices;
+  const Slice* slices;
+  const int* prefix;      // n_slices + 1 pair-count prefix sums (relative to prefix[0])
+  const float* pool;      // candidate points of this dim (device)
+  const int64_t* offsets; // candidate c spans points [offsets[c], offsets[c + 1])
+  int dim, vec;
+  int* counter;
+  float* out;
+  float* rowbuf;          // batch::BUF_COLS values per warp (multi-stripe short pairs)
+};
+
 template <int DK>
-__global__ void __launch_bounds__(256, batch::kBlocksPerSM<DK>::value) serve_kernel(const Item* items, int n_items, int dim, int vec,
-                                                       int* counter, float* out) {
+__global__ void __launch_bounds__(256, batch::kBlocksPerSM<DK>::value) serve_kernel(ServeArgs a) {
   __shared__ uint4 stage_sm[8][batch::QStage<DK>::RECS];
   uint4* stage = stage_sm[threadIdx.x >> 5];
   const int L = threadIdx.x & 31;
+  const int64_t gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  float* buf = a.rowbuf + gw * batch::BUF_COLS;
+  const int base = a.n_slices > 0 ? a.prefix[0] : 0;
+  const int total = a.n_items + (a.n_slices > 0 ? a.prefix[a.n_slices] - base : 0);
   for (;;) {
     int i = 0;
-    if (L == 0) i = atomicAdd(counter, 1);
+    if (L == 0) i = atomicAdd(a.counter, 1);
     i = __shfl_sync(0xffffffffu, i, 0);
-    if (i >= n_items) break;
-    const Item it = items[i];
-    const float r = batch::warp_dfd_any<F32, DK>(it.P, it.n, it.Q, it.m, dim, vec != 0, it.state, L, it.s0, it.s1,
+    if (i >= total) break;
+    const float *P, *Q;
+    float* state;
+    int n, m, s0 = 0, s1 = 1 << 30, out;
+    if (i < a.n_items) {
+      const Item it = a.items[i];
+      P = it.P;
+      Q = it.Q;
+      state = it.state;
+      n = it.n;
+      m = it.m;
+      s0 = it.s0;
+      s1 = it.s1;
+      out = it.out;
+    } else {
+      // the slice holding pair j: prefix[lo] - base <= j < prefix[hi] - base,
+      // narrowed 32-fold per round (one probe per lane)
+      const int j = i - a.n_items;
+      int lo = 0, hi = a.n_slices;
+      while (hi - lo > 1) {
+        const int step = (hi - lo + 31) >> 5;
+        const int p = lo + L * step;
+        const bool le = p < hi && a.prefix[p] - base <= j;
+        const int cnt = __popc(__ballot_sync(0xffffffffu, le));   // >= 1: position lo qualifies
+        lo += (cnt - 1) * step;
+        hi = min(hi, lo + step);
+      }
+      const Slice sl = a.slices[lo];
+      const int li = j - (a.prefix[lo] - base);
+      const int64_t o = a.offsets[sl.cids[li]];
+      const int len = (int)(a.offsets[sl.cids[li] + 1] - o);
+      const float* C = a.pool + o * a.dim;
+      const bool qrows = sl.n <= len;
+      P = qrows ? sl.query : C;
+      Q = qrows ? C : sl.query;
+      n = qrows ? sl.n : len;
+      m = qrows ? len : sl.n;
+      state = buf;
+      out = sl.out_base + li;
+      if (batch::num_stripes<DK>(n) > 1 && m > batch::BUF_COLS) {   // admission makes such pairs items
+        if (L == 0) a.out[out] = -1.f;
+        continue;
+      }
+    }
+    const float r = batch::warp_dfd_any<F32, DK>(P, n, Q, m, a.dim, a.vec != 0, state, L, s0, s1,
                                                  static_cast<batch::NoAbandon<F32>*>(nullptr), stage);
-    if (L == 0 && it.out >= 0) out[it.out] = sqrtf(r);
+    if (L == 0 && out >= 0) a.out[out] = sqrtf(r);
   }
 }
 
@@ -120,18 +204,29 @@ class Arena {
 };
 
 struct Pool {
-  float* points = nullptr;   // device
+  float* points = nullptr;        // device
+  int64_t* d_offsets = nullptr;   // device copy of `offsets`
   std::vector<int64_t> offsets{0};
   ~Pool() {
     if (points) cudaFree(points);
+    if (d_offsets) cudaFree(d_offsets);
   }
 };
 
-struct PairState {
+// A pair that spans ticks.
+struct LongPair {
+  int k = 0;                  // pair index in the request
   int rows = 0, cols = 0, nst = 1;
   bool query_is_rows = true;
   int issued = 0;             // stripes issued to ticks
+  bool busy = false;          // in a tick in flight
   size_t state_off = SIZE_MAX;
+};
+
+// A run of a request's cost-sorted short pairs that share one cost class.
+struct ClassRun {
+  int begin;                  // first position in `order`
+  int cls;                    // rank: 0 = costliest class
 };
 
 struct Request {
@@ -145,35 +240,72 @@ struct Request {
   dfd_status status = DFD_ERR_NOT_READY;
   bool cancelled = false;
   size_t q_off = SIZE_MAX;
-  std::vector<PairState> pairs;
+  size_t cid_off = SIZE_MAX, cid_bytes = 0;   // candidate ids of the short pairs (int32, in `order`)
+  std::vector<int32_t> order;       // short pairs (indices into ids), costliest class first
+  std::vector<double> cells_pre;    // cells of order[0 .. i)
+  std::vector<ClassRun> runs;
+  std::vector<LongPair> longs;
+  int64_t next_short = 0;     // positions of `order` before it are in a slice
+  size_t next_long = 0;       // long pairs before it have every stripe issued
   int64_t remaining = 0;      // pairs without a result
-  int64_t next_pair = 0;      // pairs before it have every stripe issued
-  int inflight = 0;           // items of this request in ticks not yet retired
+  int inflight = 0;           // items and slices of this request in ticks not yet retired
   double cells = 0;
 };
 
+// Host record of a slice.
+struct SliceRec {
+  Slice d;
+  Request* r;
+  int first;                  // position of the slice's first pair in r->order
+  int key;                    // dim * NCLS + class rank
+};
+
+// A tick's launches alternate between its two streams (forked after the
+// tick's copies, joined before its results are read back), so the launches
+// of different point dimensions overlap like consecutive ticks do.
+constexpr int NSTREAM = 2;
+
 struct Tick {
+  cudaStream_t stream[NSTREAM] = {};
+  float* rowbuf[NSTREAM] = {};   // per-warp row buffers of the launches on each stream
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  std::vector<LongPair*> longs_issued;
   std::vector<Item> items;
-  std::vector<std::pair<Request*, int>> outs;   // output slot -> (request, pair)
+  std::vector<std::pair<Request*, int>> outs;   // item output slot -> (request, pair)
   std::vector<Request*> members;                // one entry per item
-  Item* h_items = nullptr;    // pinned
+  std::vector<SliceRec> slices;
+  std::vector<int> prefix;                      // pair-count prefix sums of `slices`
+  size_t n_outs = 0;          // item outputs, then the slices' pairs
+  char* h_desc = nullptr;     // pinned: items | slices | prefix
+  char* d_desc = nullptr;
+  size_t cap_desc = 0;
+  size_t off_slices = 0, off_prefix = 0, desc_bytes = 0;
   float* h_out = nullptr;     // pinned
-  Item* d_items = nullptr;
   float* d_out = nullptr;
+  size_t cap_out = 0;
   int* d_counter = nullptr;   // one counter per launch (one launch per dim)
-  size_t cap_items = 0;
-  char* h_stage = nullptr;    // pinned staging of the queries admitted with this tick
+  char* h_stage = nullptr;    // pinned staging of the queries and ids admitted with this tick
   size_t stage_used = 0;
   struct Upload {
     size_t arena_off, stage_off, bytes;
   };
   std::vector<Upload> uploads;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  cudaEvent_t ev_up = nullptr;   // this tick's uploads (and every earlier tick's) are done
   double cells = 0;
 };
 
 constexpr int MAX_DIM = 16;
-constexpr size_t STAGE_BYTES = (size_t)32 << 20;   // pinned query staging per tick
+constexpr int NTICK = 3;        // tick slots; at most NTICK - 1 in flight
+constexpr int NCLS = 48;                           // cost classes: floor(log2(cells))
+constexpr size_t STAGE_BYTES = (size_t)32 << 20;   // pinned query / id staging per tick
+
+inline int cost_rank(unsigned long long cells) {   // 0 for the costliest class
+  const int b = cells > 1 ? std::min(NCLS - 1, 63 - __builtin_clzll(cells)) : 0;
+  return NCLS - 1 - b;
+}
+
+inline size_t align16(size_t b) { return (b + 15) / 16 * 16; }
 
 }  // namespace serve
 }  // namespace dfd
@@ -184,7 +316,6 @@ using namespace dfd::serve;
 struct dfd_server {
   dfd_context* ctx = nullptr;
   dfd_server_options opt{};
-  cudaStream_t stream = nullptr;
   Arena arena;
   std::unordered_map<int, std::unique_ptr<Pool>> pools;   // by dim
   std::mutex mu;
@@ -193,9 +324,12 @@ struct dfd_server {
   std::vector<Request*> active;
   std::unordered_map<uint64_t, std::unique_ptr<Request>> requests;
   uint64_t next_ticket = 1;
-  Tick ticks[2];
-  std::vector<int> sort_count, sort_key;   // build_tick's counting sort (reused buffers)
+  Tick ticks[NTICK];
+  Tick* last_launched = nullptr;
+  Tick* last_retired = nullptr;
+  std::vector<int> sort_count, sort_key;   // counting sorts (reused buffers)
   std::vector<Item> sort_items;
+  std::vector<SliceRec> sort_slices;
   int next_tick = 0;
   std::deque<Tick*> inflight;
   std::thread worker;
@@ -209,26 +343,36 @@ struct dfd_server {
 
 namespace {
 
-bool ensure_tick_capacity(Tick& t, size_t items) {
-  if (items <= t.cap_items) return true;
-  const size_t cap = std::max(items, t.cap_items * 2 + 1024);
-  if (t.h_items) cudaFreeHost(t.h_items);
-  if (t.h_out) cudaFreeHost(t.h_out);
-  if (t.d_items) cudaFree(t.d_items);
-  if (t.d_out) cudaFree(t.d_out);
-  t.h_items = nullptr;
-  t.h_out = nullptr;
-  t.d_items = nullptr;
-  t.d_out = nullptr;
-  t.cap_items = 0;
-  if (cudaMallocHost(&t.h_items, cap * sizeof(Item)) != cudaSuccess ||
-      cudaMallocHost(&t.h_out, cap * sizeof(float)) != cudaSuccess ||
-      cudaMalloc(&t.d_items, cap * sizeof(Item)) != cudaSuccess ||
-      cudaMalloc(&t.d_out, cap * sizeof(float)) != cudaSuccess) {
-    cudaGetLastError();
-    return false;
+// Warps of the widest tick launch: blocks are capped at two per SM.
+inline size_t max_tick_warps(const dfd_server* s) { return (size_t)2 * s->ctx->num_sms * 8; }
+
+bool ensure_tick_capacity(Tick& t, size_t desc_bytes, size_t outs) {
+  if (desc_bytes > t.cap_desc) {
+    const size_t cap = std::max(desc_bytes, t.cap_desc * 2 + (64 << 10));
+    if (t.h_desc) cudaFreeHost(t.h_desc);
+    if (t.d_desc) cudaFree(t.d_desc);
+    t.h_desc = t.d_desc = nullptr;
+    t.cap_desc = 0;
+    if (cudaMallocHost(&t.h_desc, cap) != cudaSuccess || cudaMalloc(&t.d_desc, cap) != cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    t.cap_desc = cap;
   }
-  t.cap_items = cap;
+  if (outs > t.cap_out) {
+    const size_t cap = std::max(outs, t.cap_out * 2 + 4096);
+    if (t.h_out) cudaFreeHost(t.h_out);
+    if (t.d_out) cudaFree(t.d_out);
+    t.h_out = nullptr;
+    t.d_out = nullptr;
+    t.cap_out = 0;
+    if (cudaMallocHost(&t.h_out, cap * sizeof(float)) != cudaSuccess ||
+        cudaMalloc(&t.d_out, cap * sizeof(float)) != cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    t.cap_out = cap;
+  }
   return true;
 }
 
@@ -247,7 +391,11 @@ void release_request_memory(dfd_server* s, Request* r) {
     s->arena.release(r->q_off, (size_t)r->n * r->dim * sizeof(float));
     r->q_off = SIZE_MAX;
   }
-  for (auto& p : r->pairs) {
+  if (r->cid_off != SIZE_MAX) {
+    s->arena.release(r->cid_off, r->cid_bytes);
+    r->cid_off = SIZE_MAX;
+  }
+  for (auto& p : r->longs) {
     if (p.state_off != SIZE_MAX) {
       s->arena.release(p.state_off, (size_t)p.cols * sizeof(float));
       p.state_off = SIZE_MAX;
@@ -272,9 +420,63 @@ void finish_request(dfd_server* s, Request* r, dfd_status st, double t) {
   s->cv_done.notify_all();
 }
 
+// Split a request's pairs into long pairs and short pairs, the short ones in
+// decreasing cost class (a counting sort), with their cell prefix sums and
+// class runs; the candidate ids in that order go to `cid_stage`.
+void plan_request(dfd_server* s, Request* r, int32_t* cid_stage) {
+  const int max_st = s->opt.stripes_per_tick > 0 ? s->opt.stripes_per_tick : 8;
+  const Pool& pool = *s->pools[r->dim];
+  const int k = (int)r->ids.size();
+  std::vector<int>& key = s->sort_key;
+  std::vector<int>& cnt = s->sort_count;
+  key.resize(k);
+  cnt.assign(NCLS + 1, 0);
+  r->longs.clear();
+  r->cells = 0;
+  for (int x = 0; x < k; ++x) {
+    const int64_t c = r->ids[x];
+    const int len = (int)(pool.offsets[c + 1] - pool.offsets[c]);
+    const int rows = std::min(r->n, len), cols = std::max(r->n, len);
+    const int nst = stripes_for(r->dim, rows);
+    r->cells += (double)rows * cols;
+    if (nst > max_st || (nst > 1 && cols > batch::BUF_COLS)) {
+      LongPair lp;
+      lp.k = x;
+      lp.rows = rows;
+      lp.cols = cols;
+      lp.nst = nst;
+      lp.query_is_rows = r->n <= len;
+      r->longs.push_back(lp);
+      key[x] = -1;
+    } else {
+      key[x] = cost_rank((unsigned long long)rows * (unsigned long long)cols);
+      ++cnt[key[x] + 1];
+    }
+  }
+  for (int c = 1; c <= NCLS; ++c) cnt[c] += cnt[c - 1];
+  const int n_short = cnt[NCLS];
+  r->runs.clear();
+  for (int c = 0; c < NCLS; ++c)
+    if (cnt[c + 1] > cnt[c]) r->runs.push_back({cnt[c], c});
+  r->order.resize(n_short);
+  for (int x = 0; x < k; ++x)
+    if (key[x] >= 0) r->order[cnt[key[x]]++] = x;
+  r->cells_pre.resize(n_short + 1);
+  r->cells_pre[0] = 0;
+  for (int y = 0; y < n_short; ++y) {
+    const int64_t c = r->ids[r->order[y]];
+    const int len = (int)(pool.offsets[c + 1] - pool.offsets[c]);
+    r->cells_pre[y + 1] = r->cells_pre[y] + (double)r->n * len;
+    cid_stage[y] = (int32_t)c;
+  }
+  r->next_short = 0;
+  r->next_long = 0;
+  r->remaining = k;
+}
+
 // Admit pending requests in arrival order while slots and memory allow; the
-// admitted queries are staged in the tick's pinned buffer and copied to the
-// device ahead of the tick's kernels (stream order).
+// admitted queries and candidate ids are staged in the tick's pinned buffer
+// and copied to the device ahead of the tick's kernels (stream order).
 void admit(dfd_server* s, Tick& t) {
   const int max_slots = s->opt.max_slots > 0 ? s->opt.max_slots : 256;
   t.uploads.clear();
@@ -282,52 +484,53 @@ void admit(dfd_server* s, Tick& t) {
   while (!s->pending.empty() && (int)s->active.size() < max_slots) {
     Request* r = s->pending.front();
     const size_t qb = (size_t)r->n * r->dim * sizeof(float);
-    if (t.stage_used + qb > STAGE_BYTES) break;   // the next tick takes it
+    const size_t ib = std::max<size_t>(r->ids.size() * sizeof(int32_t), 16);
+    if (t.stage_used + align16(qb) + align16(ib) > STAGE_BYTES) break;   // the next tick takes it
     const size_t off = s->arena.alloc(qb);
-    if (off == SIZE_MAX) break;                   // wait for running requests to release memory
+    if (off == SIZE_MAX) break;                    // wait for running requests to release memory
+    const size_t coff = s->arena.alloc(ib);
+    if (coff == SIZE_MAX) {
+      s->arena.release(off, qb);
+      break;
+    }
     s->pending.pop_front();
     r->q_off = off;
+    r->cid_off = coff;
+    r->cid_bytes = ib;
     std::memcpy(t.h_stage + t.stage_used, r->query.data(), qb);
     t.uploads.push_back({off, t.stage_used, qb});
-    t.stage_used += (qb + 15) / 16 * 16;
-    Pool& pool = *s->pools[r->dim];
-    r->pairs.resize(r->ids.size());
-    for (size_t k = 0; k < r->ids.size(); ++k) {
-      const int64_t c = r->ids[k];
-      const int len = (int)(pool.offsets[c + 1] - pool.offsets[c]);
-      PairState& p = r->pairs[k];
-      p.query_is_rows = r->n <= len;
-      p.rows = std::min(r->n, len);
-      p.cols = std::max(r->n, len);
-      p.nst = stripes_for(r->dim, p.rows);
-      r->cells += (double)p.rows * p.cols;
-    }
-    r->remaining = (int64_t)r->ids.size();
+    t.stage_used += align16(qb);
+    plan_request(s, r, reinterpret_cast<int32_t*>(t.h_stage + t.stage_used));
+    if (!r->order.empty()) t.uploads.push_back({coff, t.stage_used, r->order.size() * sizeof(int32_t)});
+    t.stage_used += align16(ib);
     s->active.push_back(r);
   }
 }
 
-// Fill `t` with the next slice of work of the admitted requests (oldest first).
+// Fill `t` with the next work of the admitted requests (oldest first): the
+// long pairs' next stripes, then a run of the short pairs.
 void build_tick(dfd_server* s, Tick& t) {
   t.items.clear();
   t.outs.clear();
   t.members.clear();
+  t.slices.clear();
+  t.longs_issued.clear();
   t.cells = 0;
-  const double budget = s->opt.tick_cells > 0 ? s->opt.tick_cells : 2.0e9;
-  const int max_st = s->opt.stripes_per_tick > 0 ? s->opt.stripes_per_tick : 4;
+  const double budget = s->opt.tick_cells > 0 ? s->opt.tick_cells : 4.0e9;
+  const int max_st = s->opt.stripes_per_tick > 0 ? s->opt.stripes_per_tick : 8;
   for (Request* r : s->active) {
     if (t.cells >= budget) break;
     if (r->cancelled) continue;
     Pool& pool = *s->pools[r->dim];
     const float* qdev = reinterpret_cast<const float*>(s->arena.ptr(r->q_off));
-    for (int64_t k = r->next_pair; k < (int64_t)r->pairs.size() && t.cells < budget; ++k) {
-      PairState& p = r->pairs[k];
-      if (p.issued >= p.nst) continue;
+    for (size_t x = r->next_long; x < r->longs.size() && t.cells < budget; ++x) {
+      LongPair& p = r->longs[x];
+      if (p.issued >= p.nst || p.busy) continue;
       if (p.nst > 1 && p.state_off == SIZE_MAX) {
         p.state_off = s->arena.alloc((size_t)p.cols * sizeof(float));
         if (p.state_off == SIZE_MAX) continue;   // no room for its row state in this tick
       }
-      const float* cdev = pool.points + pool.offsets[r->ids[k]] * r->dim;
+      const float* cdev = pool.points + pool.offsets[r->ids[p.k]] * r->dim;
       Item it;
       it.P = p.query_is_rows ? qdev : cdev;
       it.Q = p.query_is_rows ? cdev : qdev;
@@ -339,23 +542,54 @@ void build_tick(dfd_server* s, Tick& t) {
       it.dim = r->dim;
       if (it.s1 == p.nst) {
         it.out = (int)t.outs.size();
-        t.outs.emplace_back(r, (int)k);
+        t.outs.emplace_back(r, p.k);
       } else {
         it.out = -1;
       }
       t.cells += (double)(it.s1 - it.s0) / p.nst * p.rows * (double)p.cols;
       p.issued = it.s1;
+      p.busy = true;
+      t.longs_issued.push_back(&p);
       t.items.push_back(it);
       t.members.push_back(r);
       r->inflight++;
     }
-    while (r->next_pair < (int64_t)r->pairs.size() && r->pairs[r->next_pair].issued >= r->pairs[r->next_pair].nst)
-      r->next_pair++;
+    while (r->next_long < r->longs.size() && r->longs[r->next_long].issued >= r->longs[r->next_long].nst)
+      r->next_long++;
+    const int64_t n_short = (int64_t)r->order.size();
+    if (r->next_short < n_short && t.cells < budget) {
+      // the longest run of positions whose cells fit the budget left (at least one)
+      const double* cp = r->cells_pre.data();
+      const double want = cp[r->next_short] + (budget - t.cells);
+      int64_t e = std::upper_bound(cp + r->next_short + 1, cp + n_short + 1, want) - cp - 1;
+      e = std::max<int64_t>(e, r->next_short + 1);
+      t.cells += cp[e] - cp[r->next_short];
+      const int32_t* cids = reinterpret_cast<const int32_t*>(s->arena.ptr(r->cid_off));
+      // one slice per class run inside [next_short, e)
+      auto run = std::upper_bound(r->runs.begin(), r->runs.end(), (int)r->next_short,
+                                  [](int pos, const ClassRun& c) { return pos < c.begin; }) - 1;
+      for (int64_t a = r->next_short; a < e; ++run) {
+        const int64_t run_end = (run + 1 == r->runs.end()) ? n_short : (run + 1)->begin;
+        const int64_t b = std::min(e, run_end);
+        SliceRec sr;
+        sr.d.query = qdev;
+        sr.d.cids = cids + a;
+        sr.d.n = r->n;
+        sr.d.count = (int)(b - a);
+        sr.d.out_base = 0;
+        sr.d.pad = 0;
+        sr.r = r;
+        sr.first = (int)a;
+        sr.key = std::min(r->dim, MAX_DIM) * NCLS + run->cls;
+        t.slices.push_back(sr);
+        r->inflight++;
+        a = b;
+      }
+      r->next_short = e;
+    }
   }
-  // One launch per dimension; costliest items first inside it (LPT by
-  // power-of-two cost classes): a counting sort, linear in the items, where
-  // a comparison sort of every pair was the scheduler's largest per-pair cost.
-  constexpr int NCLS = 48;
+  // One launch per dimension; inside it the items costliest first, then the
+  // slices costliest class first (counting sorts, linear in the items).
   const size_t n_it = t.items.size();
   if (n_it > 1) {
     std::vector<int>& cnt = s->sort_count;
@@ -364,10 +598,9 @@ void build_tick(dfd_server* s, Tick& t) {
     key.resize(n_it);
     for (size_t i = 0; i < n_it; ++i) {
       const Item& it = t.items[i];
-      const unsigned long long c =
-          (unsigned long long)(it.s1 - it.s0) * (unsigned long long)it.m * (unsigned long long)std::min(it.n, 256);
-      const int b = c > 1 ? std::min(NCLS - 1, 63 - __builtin_clzll(c)) : 0;
-      key[i] = std::min(it.dim, MAX_DIM) * NCLS + (NCLS - 1 - b);
+      key[i] = std::min(it.dim, MAX_DIM) * NCLS +
+               cost_rank((unsigned long long)(it.s1 - it.s0) * (unsigned long long)it.m *
+                         (unsigned long long)std::min(it.n, 256));
       ++cnt[key[i] + 1];
     }
     for (size_t k = 1; k < cnt.size(); ++k) cnt[k] += cnt[k - 1];
@@ -376,30 +609,83 @@ void build_tick(dfd_server* s, Tick& t) {
     for (size_t i = 0; i < n_it; ++i) out[cnt[key[i]]++] = t.items[i];
     t.items.swap(out);
   }
+  const size_t n_sl = t.slices.size();
+  if (n_sl > 1) {
+    std::vector<int>& cnt = s->sort_count;
+    cnt.assign((MAX_DIM + 1) * NCLS + 1, 0);
+    for (const SliceRec& sr : t.slices) ++cnt[sr.key + 1];
+    for (size_t k = 1; k < cnt.size(); ++k) cnt[k] += cnt[k - 1];
+    std::vector<SliceRec>& out = s->sort_slices;
+    out.resize(n_sl);
+    for (const SliceRec& sr : t.slices) out[cnt[sr.key]++] = sr;
+    t.slices.swap(out);
+  }
+  t.prefix.resize(n_sl + 1);
+  t.prefix[0] = 0;
+  const int n_item_outs = (int)t.outs.size();
+  for (size_t j = 0; j < n_sl; ++j) {
+    t.slices[j].d.out_base = n_item_outs + t.prefix[j];
+    t.prefix[j + 1] = t.prefix[j] + t.slices[j].d.count;
+  }
+  t.n_outs = (size_t)n_item_outs + t.prefix[n_sl];
+  t.off_slices = align16(n_it * sizeof(Item));
+  t.off_prefix = t.off_slices + align16(n_sl * sizeof(Slice));
+  t.desc_bytes = t.off_prefix + (n_sl + 1) * sizeof(int);
 }
 
 void launch_tick(dfd_server* s, Tick& t) {
-  const size_t n = t.items.size();
-  if (n) std::memcpy(t.h_items, t.items.data(), n * sizeof(Item));
-  cudaEventRecord(t.ev0, s->stream);
+  const size_t n_it = t.items.size(), n_sl = t.slices.size();
+  if (n_it) std::memcpy(t.h_desc, t.items.data(), n_it * sizeof(Item));
+  Slice* hs = reinterpret_cast<Slice*>(t.h_desc + t.off_slices);
+  for (size_t j = 0; j < n_sl; ++j) hs[j] = t.slices[j].d;
+  std::memcpy(t.h_desc + t.off_prefix, t.prefix.data(), (n_sl + 1) * sizeof(int));
+  cudaStream_t st = t.stream[0];
+  cudaEventRecord(t.ev0, st);
+  // queries and ids admitted with earlier ticks were uploaded on their
+  // streams: order this tick after those copies (not after their kernels)
+  if (s->last_launched) cudaStreamWaitEvent(st, s->last_launched->ev_up, 0);
   for (const auto& u : t.uploads)
-    cudaMemcpyAsync(s->arena.ptr(u.arena_off), t.h_stage + u.stage_off, u.bytes, cudaMemcpyHostToDevice, s->stream);
-  if (n) cudaMemcpyAsync(t.d_items, t.h_items, n * sizeof(Item), cudaMemcpyHostToDevice, s->stream);
-  cudaMemsetAsync(t.d_counter, 0, (MAX_DIM + 1) * sizeof(int), s->stream);
-  size_t b = 0;
-  while (b < n) {
-    size_t e = b;
-    const int dim = t.items[b].dim;
-    while (e < n && t.items[e].dim == dim) ++e;
+    cudaMemcpyAsync(s->arena.ptr(u.arena_off), t.h_stage + u.stage_off, u.bytes, cudaMemcpyHostToDevice, st);
+  cudaEventRecord(t.ev_up, st);
+  if (n_it || n_sl) cudaMemcpyAsync(t.d_desc, t.h_desc, t.desc_bytes, cudaMemcpyHostToDevice, st);
+  cudaMemsetAsync(t.d_counter, 0, (MAX_DIM + 1) * sizeof(int), st);
+  cudaEventRecord(t.ev_fork, st);   // the tick's inputs are in place
+  const Item* d_items = reinterpret_cast<const Item*>(t.d_desc);
+  const Slice* d_slices = reinterpret_cast<const Slice*>(t.d_desc + t.off_slices);
+  const int* d_prefix = reinterpret_cast<const int*>(t.d_desc + t.off_prefix);
+  int n_launch = 0;
+  size_t ib = 0, sb = 0;
+  while (ib < n_it || sb < n_sl) {
+    // items and slices are both sorted by dim: take the smaller dim next
+    const int di = ib < n_it ? t.items[ib].dim : MAX_DIM + 1;
+    const int ds = sb < n_sl ? t.slices[sb].r->dim : MAX_DIM + 1;
+    const int dim = std::min(di, ds);
+    size_t ie = ib, se = sb;
+    while (ie < n_it && t.items[ie].dim == dim) ++ie;
+    while (se < n_sl && t.slices[se].r->dim == dim) ++se;
+    const int lane = n_launch++ % NSTREAM;
+    cudaStream_t ls = t.stream[lane];
+    if (n_launch == 2) cudaStreamWaitEvent(ls, t.ev_fork, 0);
+    ServeArgs a;
+    a.items = d_items + ib;
+    a.n_items = (int)(ie - ib);
+    a.n_slices = (int)(se - sb);
+    a.slices = d_slices + sb;
+    a.prefix = d_prefix + sb;
+    const Pool& pool = *s->pools[dim];
+    a.pool = pool.points;
+    a.offsets = pool.d_offsets;
+    a.dim = dim;
     const int dk = dim_class(dim);
-    const int vec = (dim == dk && dk != 3) ? 1 : 0;
-    const int count = (int)(e - b);
-    const int blocks = std::max(1, std::min((count + 7) / 8, 2 * s->ctx->num_sms));
-    const Item* items = t.d_items + b;
-    int* counter = t.d_counter + dim;
-#define DFD_SERVE_CASE(K)                                                                                   \
-  case K:                                                                                                   \
-    serve_kernel<K><<<blocks, 256, 0, s->stream>>>(items, count, dim, vec, counter, t.d_out);              \
+    a.vec = (dim == dk && dk != 3) ? 1 : 0;
+    a.counter = t.d_counter + dim;
+    a.out = t.d_out;
+    a.rowbuf = t.rowbuf[lane];
+    const int64_t count = (int64_t)a.n_items + (t.prefix[se] - t.prefix[sb]);
+    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((count + 7) / 8, 2 * (int64_t)s->ctx->num_sms));
+#define DFD_SERVE_CASE(K)                                 \
+  case K:                                                 \
+    serve_kernel<K><<<blocks, 256, 0, ls>>>(a);           \
     break;
     switch (dk) {
       DFD_SERVE_CASE(2)
@@ -411,26 +697,55 @@ void launch_tick(dfd_server* s, Tick& t) {
         break;
     }
 #undef DFD_SERVE_CASE
-    b = e;
+    ib = ie;
+    sb = se;
   }
-  if (!t.outs.empty())
-    cudaMemcpyAsync(t.h_out, t.d_out, t.outs.size() * sizeof(float), cudaMemcpyDeviceToHost, s->stream);
-  cudaEventRecord(t.ev1, s->stream);
+  if (n_launch > 1) {
+    cudaEventRecord(t.ev_join, t.stream[1]);
+    cudaStreamWaitEvent(st, t.ev_join, 0);
+  }
+  if (t.n_outs)
+    cudaMemcpyAsync(t.h_out, t.d_out, t.n_outs * sizeof(float), cudaMemcpyDeviceToHost, st);
+  cudaEventRecord(t.ev1, st);
+  s->last_launched = &t;
   if (cudaGetLastError() != cudaSuccess) s->fatal = DFD_ERR_CUDA;
 }
 
 // Caller holds s->mu; the tick's ev1 has completed.
 void retire_tick(dfd_server* s, Tick& t) {
   const double now = now_s();
-  float ms = 0.f;
-  if (cudaEventElapsedTime(&ms, t.ev0, t.ev1) == cudaSuccess) s->busy_ms += ms;
+  // device busy time: the union of the tick intervals (consecutive ticks
+  // overlap; the previous tick's slot is not reused while this one retires)
+  float ms = 0.f, ov = 0.f;
+  if (cudaEventElapsedTime(&ms, t.ev0, t.ev1) == cudaSuccess) {
+    if (!s->last_retired || cudaEventElapsedTime(&ov, t.ev0, s->last_retired->ev1) != cudaSuccess) ov = 0.f;
+    s->busy_ms += ms - std::min(ms, std::max(ov, 0.f));
+  }
+  cudaGetLastError();
+  s->last_retired = &t;
   s->n_ticks++;
+  for (LongPair* p : t.longs_issued) p->busy = false;
   for (size_t i = 0; i < t.outs.size(); ++i) {
     Request* r = t.outs[i].first;
     if (!r->cancelled && r->host_out) r->host_out[t.outs[i].second] = t.h_out[i];
     r->remaining--;
   }
   for (Request* r : t.members) r->inflight--;
+  bool bad = false;
+  for (const SliceRec& sr : t.slices) {
+    Request* r = sr.r;
+    const float* v = t.h_out + sr.d.out_base;
+    const int32_t* ord = r->order.data() + sr.first;
+    if (!r->cancelled && r->host_out) {
+      for (int li = 0; li < sr.d.count; ++li) {
+        bad |= v[li] < 0.f;
+        r->host_out[ord[li]] = v[li];
+      }
+    }
+    r->remaining -= sr.d.count;
+    r->inflight--;
+  }
+  if (bad && s->fatal == DFD_OK) s->fatal = DFD_ERR_CAPACITY;   // a pair the kernel refused (not planned so)
   // completion: every pair has a result, or a cancelled request has nothing in flight
   std::vector<Request*> done;
   for (Request* r : s->active) {
@@ -445,21 +760,21 @@ void worker_loop(dfd_server* s) {
   while (!s->stop) {
     Tick& t = s->ticks[s->next_tick];
     bool launched = false;
-    if (s->inflight.size() < 2) {
+    if (s->inflight.size() < NTICK - 1) {
       admit(s, t);
       build_tick(s, t);
-      if (!t.items.empty() || !t.uploads.empty()) {
-        if (!ensure_tick_capacity(t, t.items.size())) {
+      if (!t.items.empty() || !t.slices.empty() || !t.uploads.empty()) {
+        if (!ensure_tick_capacity(t, t.desc_bytes, t.n_outs)) {
           s->fatal = DFD_ERR_OOM;
         } else {
           launch_tick(s, t);
           s->inflight.push_back(&t);
-          s->next_tick ^= 1;
+          s->next_tick = (s->next_tick + 1) % NTICK;
           launched = true;
         }
       }
     }
-    if (!s->inflight.empty() && (s->inflight.size() >= 2 || !launched)) {
+    if (!s->inflight.empty() && (s->inflight.size() >= NTICK - 1 || !launched)) {
       Tick* old = s->inflight.front();
       lk.unlock();
       cudaEventSynchronize(old->ev1);
@@ -500,8 +815,8 @@ dfd_status dfd_server_options_default(dfd_server_options* o) {
   o->struct_size = sizeof(dfd_server_options);
   o->mem_budget_bytes = (size_t)1 << 30;
   o->max_slots = 256;
-  o->tick_cells = 2.0e9;
-  o->stripes_per_tick = 4;
+  o->tick_cells = 4.0e9;
+  o->stripes_per_tick = 8;
   return DFD_OK;
 }
 
@@ -520,10 +835,16 @@ dfd_status dfd_server_create(dfd_context* ctx, const dfd_server_options* opt, df
   if (!s) return DFD_ERR_OOM;
   s->ctx = ctx;
   s->opt = o;
-  bool ok = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) == cudaSuccess;
-  ok = ok && s->arena.init(o.mem_budget_bytes);
+  bool ok = s->arena.init(o.mem_budget_bytes);
   for (auto& t : s->ticks) {
+    for (int k = 0; k < NSTREAM; ++k) {
+      ok = ok && cudaStreamCreateWithFlags(&t.stream[k], cudaStreamNonBlocking) == cudaSuccess;
+      ok = ok && cudaMalloc(&t.rowbuf[k], max_tick_warps(s) * batch::BUF_COLS * sizeof(float)) == cudaSuccess;
+    }
+    ok = ok && cudaEventCreateWithFlags(&t.ev_fork, cudaEventDisableTiming) == cudaSuccess;
+    ok = ok && cudaEventCreateWithFlags(&t.ev_join, cudaEventDisableTiming) == cudaSuccess;
     ok = ok && cudaEventCreate(&t.ev0) == cudaSuccess && cudaEventCreate(&t.ev1) == cudaSuccess;
+    ok = ok && cudaEventCreateWithFlags(&t.ev_up, cudaEventDisableTiming) == cudaSuccess;
     ok = ok && cudaMalloc(&t.d_counter, (MAX_DIM + 1) * sizeof(int)) == cudaSuccess;
     ok = ok && cudaMallocHost(&t.h_stage, STAGE_BYTES) == cudaSuccess;
   }
@@ -546,18 +867,26 @@ dfd_status dfd_server_destroy(dfd_server* s) {
   }
   if (s->worker.joinable()) s->worker.join();
   cudaSetDevice(s->ctx->device);
-  if (s->stream) cudaStreamSynchronize(s->stream);
+  for (auto& t : s->ticks)
+    for (cudaStream_t x : t.stream)
+      if (x) cudaStreamSynchronize(x);
   for (auto& t : s->ticks) {
-    if (t.h_items) cudaFreeHost(t.h_items);
+    if (t.h_desc) cudaFreeHost(t.h_desc);
     if (t.h_out) cudaFreeHost(t.h_out);
-    if (t.d_items) cudaFree(t.d_items);
+    if (t.d_desc) cudaFree(t.d_desc);
     if (t.d_out) cudaFree(t.d_out);
     if (t.d_counter) cudaFree(t.d_counter);
     if (t.h_stage) cudaFreeHost(t.h_stage);
     if (t.ev0) cudaEventDestroy(t.ev0);
     if (t.ev1) cudaEventDestroy(t.ev1);
+    if (t.ev_up) cudaEventDestroy(t.ev_up);
+    if (t.ev_fork) cudaEventDestroy(t.ev_fork);
+    if (t.ev_join) cudaEventDestroy(t.ev_join);
+    for (int k = 0; k < NSTREAM; ++k) {
+      if (t.rowbuf[k]) cudaFree(t.rowbuf[k]);
+      if (t.stream[k]) cudaStreamDestroy(t.stream[k]);
+    }
   }
-  if (s->stream) cudaStreamDestroy(s->stream);
   cudaGetLastError();
   delete s;
   return DFD_OK;
@@ -580,21 +909,35 @@ dfd_status dfd_server_add_candidates(dfd_server* s, int dim, const float* host_p
   auto& slot = s->pools[dim];
   if (!slot) slot.reset(new Pool());
   Pool& pool = *slot;
+  if ((int64_t)pool.offsets.size() - 1 + n_curves > INT32_MAX) return DFD_ERR_UNSUPPORTED;   // ids travel as int32
   const int64_t old_pts = pool.offsets.back();
-  // grow: new device array with old + new points (the worker is not using the
-  // pool while we hold the lock, and the copy below is ordered on its stream)
+  // grow: new device arrays with old + new curves (the worker launches no
+  // tick while we hold the lock; the ticks in flight finish before the old
+  // arrays are freed, and the copies finish before the lock is released)
   float* grown = nullptr;
   if (cudaMalloc(&grown, (size_t)(old_pts + npts) * dim * sizeof(float)) != cudaSuccess) {
     cudaGetLastError();
     return DFD_ERR_OOM;
   }
-  cudaStreamSynchronize(s->stream);
+  for (auto& t : s->ticks)   // ticks in flight read the old arrays
+    for (cudaStream_t x : t.stream) cudaStreamSynchronize(x);
   if (pool.points) cudaMemcpy(grown, pool.points, (size_t)old_pts * dim * sizeof(float), cudaMemcpyDeviceToDevice);
   cudaMemcpy(grown + old_pts * dim, host_points, (size_t)npts * dim * sizeof(float), cudaMemcpyHostToDevice);
   if (pool.points) cudaFree(pool.points);
   pool.points = grown;
-  if (first_id) *first_id = (int64_t)pool.offsets.size() - 1;
+  const size_t old_curves = pool.offsets.size() - 1;
   for (int64_t c = 0; c < n_curves; ++c) pool.offsets.push_back(old_pts + host_offsets[c + 1]);
+  int64_t* offs = nullptr;
+  if (cudaMalloc(&offs, pool.offsets.size() * sizeof(int64_t)) != cudaSuccess) {
+    cudaGetLastError();
+    pool.offsets.resize(old_curves + 1);
+    return DFD_ERR_OOM;
+  }
+  cudaMemcpy(offs, pool.offsets.data(), pool.offsets.size() * sizeof(int64_t), cudaMemcpyHostToDevice);
+  cudaStreamSynchronize(0);
+  if (pool.d_offsets) cudaFree(pool.d_offsets);
+  pool.d_offsets = offs;
+  if (first_id) *first_id = (int64_t)old_curves;
   return cudaGetLastError() == cudaSuccess ? DFD_OK : DFD_ERR_CUDA;
 }
 
@@ -621,6 +964,8 @@ dfd_status dfd_server_submit(dfd_server* s, int dim, const float* host_query, in
     if (cand_ids[i] < 0 || cand_ids[i] >= ncand) return DFD_ERR_INVALID_ARG;
   const size_t qb = (size_t)n * dim * sizeof(float);
   if (qb > s->opt.mem_budget_bytes / 2) return DFD_ERR_BUSY;   // never admissible
+  if (align16(qb) + align16(std::max<size_t>((size_t)k * sizeof(int32_t), 16)) > STAGE_BYTES)
+    return DFD_ERR_CAPACITY;
   r->ticket = s->next_ticket++;
   *ticket = r->ticket;
   if (s->t_first < 0) s->t_first = r->t_arrival;

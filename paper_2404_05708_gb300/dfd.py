@@ -366,7 +366,7 @@ class Server:
     """Continuous-batching search server (query vs resident candidates)."""
 
     def __init__(self, ctx: "Context", mem_budget_bytes: int = 1 << 30, max_slots: int = 256,
-                 tick_cells: float = 2e9, stripes_per_tick: int = 4):
+                 tick_cells: float = 4e9, stripes_per_tick: int = 8):
         opt = dfd_server_options_default()
         opt.mem_budget_bytes = int(mem_budget_bytes)
         opt.max_slots = int(max_slots)

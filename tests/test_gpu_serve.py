@@ -90,6 +90,48 @@ def test_alone_equals_in_mix_and_oracle(dctx):
     srv.close()
 
 
+def mixed_pool(dim, seed, n=240):
+    """Mostly short curves, one in ten longer than a warp's 4096-point row buffer."""
+    rng = np.random.default_rng(seed)
+    lens = np.where(rng.random(n) < 0.1, rng.integers(4097, 4400, n), rng.integers(8, 600, n))
+    off = np.concatenate([[0], np.cumsum(lens)]).astype(np.int64)
+    pts = np.cumsum(rng.normal(0, 1, size=(int(off[-1]), dim)), axis=0).astype(np.float32)
+    return workloads.Batch(points=pts, offsets=off, pairs=np.zeros((0, 2), np.int32))
+
+
+def test_slices_across_ticks_classes_and_long_pairs(dctx):
+    # short pairs go out as per-request slices (one per cost class, split at
+    # tick boundaries), multi-stripe short pairs use the warp row buffer, and
+    # pairs with more stripes than a tick runs -- or wider than the buffer --
+    # go out as items; every result must equal the float32 mirror bit for bit
+    pl = {d: mixed_pool(d, seed=40 + d) for d in (2, 3)}
+    srv = make_server(dctx, pl, tick_cells=3e7, stripes_per_tick=3, max_slots=1024)
+    rng = np.random.default_rng(11)
+    reqs = []
+    for i in range(160):
+        d = int(rng.choice([2, 3]))
+        u = rng.random()
+        n = int(rng.integers(8, 500)) if u < 0.6 else int(rng.integers(500, 1100)) if u < 0.95 else \
+            int(rng.integers(4100, 4300))
+        q = np.cumsum(rng.normal(0, 1, size=(n, d)), axis=0).astype(np.float32)
+        k = int(rng.integers(1, 48)) if n < 4000 else 6
+        ids = rng.integers(0, len(pl[d].offsets) - 1, size=k).astype(np.int64)
+        reqs.append((q, ids))
+    tickets = [srv.submit(a, b) for a, b in reqs]
+    for tk, (a, b) in zip(tickets, reqs):
+        st, out = srv.wait(tk, timeout_ms=120000)
+        assert st == 0
+        bb = pl[a.shape[1]]
+        pts = np.concatenate([a, bb.points])
+        off = np.concatenate([[0], a.shape[0] + bb.offsets]).astype(np.int64)
+        pairs = np.stack([np.zeros_like(b), b + 1], 1).astype(np.int32)
+        mirror, _ = oracle.batch(pts, off, pairs, mirror=True)
+        assert np.array_equal(out, np.sqrt(mirror.astype(np.float32)))
+    s = srv.stats()
+    assert s["completed"] == len(reqs) and s["ticks"] > 1
+    srv.close()
+
+
 def test_small_memory_budget_and_few_slots_still_finish(dctx):
     pl = pools(n=300, seed=110, hi=600)
     srv = make_server(dctx, pl, mem_budget_bytes=1 << 20, max_slots=3, tick_cells=2e6, stripes_per_tick=2)
