@@ -30,18 +30,70 @@ struct kBlocksPerSM {
   static constexpr int value = 2;
 };
 
-// q streams through a per-warp shared-memory ring of 64 points instead of
-// per-lane L1/L2 loads: the warp loads the next 32 points cooperatively one
-// block ahead (one point per lane, coalesced) and every step reads them from
-// shared memory, plane-major ([16-byte plane][64 points]) so that lanes one
-// column apart read consecutive records.  (Per-lane loads left lane 0
-// waiting on L2 for every new point.)
+// q streams through a per-warp shared-memory window instead of per-lane
+// L1/L2 loads: the warp loads the next 32 points cooperatively one block
+// ahead (one point per lane, coalesced) and every step reads them from
+// shared memory.  During the block of columns c0 .. c0+31 the window holds
+// columns c0-32 .. c0+31 in slots 0 .. 63, so lane L reads column
+// c0 + s - L from slot 32 + s - L: one load per 16-byte plane at a fixed
+// offset from a per-lane base, no index arithmetic per step.  Planes are
+// stored plane-major ([plane][64 slots]) so lanes one column apart read
+// consecutive records.  (Per-lane loads left lane 0 waiting on L2 for every
+// new point.)  After the planes, 16 records hold the stripe's bottom row of
+// the current block (lane 31 stores one value per step).
 template <int DK>
 struct QStage {
   static constexpr bool on = true;
   static constexpr int NPL = (DK + 3) / 4;
-  static constexpr int RECS = on ? NPL * 64 : 1;   // uint4 records per warp
+  static constexpr int RECS = NPL * 64 + 16;   // uint4 records per warp
 };
+
+// Form of a column's record in the window.
+//   kRaw:  the coordinates, 4 per plane.
+//   kDup:  float32 points of dim class 2 as (x, x, y, y): the operand of the
+//          packed row pairs, read as is.
+//   kNorm: uint32-bits points of dim class <= 3 as (-2x, -2y, -2z, |q|^2),
+//          mod 2^32.  With |p|^2 per row, d^2 = |p|^2 + |q|^2 - 2 p.q is
+//          three integer instructions a cell instead of four, and exact: the
+//          arithmetic is modulo 2^32 and the true d^2 is below 2^31.
+enum QRecKind { kRaw = 0, kDup = 1, kNorm = 2 };
+template <class V, int DK>
+struct QRec {
+  static constexpr int kind = (std::is_same<V, F32>::value && DK == 2)   ? kDup
+                              : (std::is_same<V, I32B>::value && DK <= 3) ? kNorm
+                                                                         : kRaw;
+  static constexpr int NPL = QStage<DK>::NPL;   // 1 for kDup and kNorm
+};
+
+// Plane c of the record of point q.
+template <class V, int DK>
+__device__ __forceinline__ uint4 make_qrec(const typename V::coord (&q)[DK], int c) {
+  uint4 r;
+  if constexpr (QRec<V, DK>::kind == kDup) {
+    r.x = r.y = __float_as_uint(q[0]);
+    r.z = r.w = __float_as_uint(q[1]);
+  } else if constexpr (QRec<V, DK>::kind == kNorm) {
+    unsigned n2 = 0;
+#pragma unroll
+    for (int k = 0; k < DK; ++k) n2 += (unsigned)q[k] * (unsigned)q[k];
+    r.x = 0u - 2u * (unsigned)q[0];
+    r.y = DK > 1 ? 0u - 2u * (unsigned)q[DK > 1 ? 1 : 0] : 0u;
+    r.z = DK > 2 ? 0u - 2u * (unsigned)q[DK > 2 ? 2 : 0] : 0u;
+    r.w = n2;
+  } else {
+    unsigned w[4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      const int k = 4 * c + t;
+      w[t] = 0u;
+#pragma unroll
+      for (int kk = 0; kk < DK; ++kk)
+        if (kk == k) w[t] = *reinterpret_cast<const unsigned*>(&q[kk]);
+    }
+    r = make_uint4(w[0], w[1], w[2], w[3]);
+  }
+  return r;
+}
 constexpr int BUF_COLS = 4096;    // per-warp row buffer (columns) for multi-stripe pairs
 
 // Rows per lane chosen for a pair with `rows` rows (one stripe when possible).
@@ -215,86 +267,105 @@ __device__ __forceinline__ typename V::value warp_dfd(const typename V::coord* _
       }
     }
     const int nsteps = m + 31;
-    // q point of the coming step, loaded one step ahead (the load's latency
-    // stays off the step's chain)
-    Cd qk[DK];
-    Cd qpre[QStage<DK>::on ? DK : 1];   // staged form: this lane's point of the next block
-    if constexpr (QStage<DK>::on) {
-      load_point<Cd, DK>(Q, min(L, m - 1), dim, vec, qpre);
-    } else {
-      load_point<Cd, DK>(Q, 0, dim, vec, qk);
+    using QR = QRec<V, DK>;
+    constexpr int NPL = QR::NPL;
+    // |p|^2 per row (kNorm)
+    unsigned pn[QR::kind == kNorm ? R : 1];
+    if constexpr (QR::kind == kNorm) {
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        unsigned acc = 0;
+#pragma unroll
+        for (int k = 0; k < DK; ++k) acc += (unsigned)pr[r][k] * (unsigned)pr[r][k];
+        pn[r] = acc;
+      }
     }
+    // this lane's point of the coming block (in flight during the block before)
+    Cd qpre[DK];
+    load_point<Cd, DK>(Q, min(L, m - 1), dim, vec, qpre);
+    const uint4* sb = stage + (32 - L);   // column c0 + s - L of the window is sb[s]
+    T* outb = reinterpret_cast<T*>(stage + NPL * 64);
     for (int c0 = 0; c0 < nsteps; c0 += 32) {
       const T top_blk = has_top ? buf[min(c0 + L, m - 1)] : V::inf();
-      T out_blk = V::inf();
-      if constexpr (QStage<DK>::on) {
-        // columns c0 .. c0+31 into ring slots (c & 63); the ring then holds
-        // c0-32 .. c0+31, every column this block's lanes read
-        __syncwarp();
+      // slide the window: the block before's columns (slot 32 + L, written
+      // by this lane) move to slot L, this block's column to slot 32 + L
+      __syncwarp();
 #pragma unroll
-        for (int c = 0; c < QStage<DK>::NPL; ++c) {
-          uint4 r;
-          r.x = *reinterpret_cast<const unsigned*>(&qpre[4 * c]);
-          r.y = 4 * c + 1 < DK ? *reinterpret_cast<const unsigned*>(&qpre[4 * c + 1]) : 0u;
-          r.z = 4 * c + 2 < DK ? *reinterpret_cast<const unsigned*>(&qpre[4 * c + 2]) : 0u;
-          r.w = 4 * c + 3 < DK ? *reinterpret_cast<const unsigned*>(&qpre[4 * c + 3]) : 0u;
-          stage[c * 64 + ((c0 + L) & 63)] = r;
-        }
-        __syncwarp();
-        load_point<Cd, DK>(Q, min(c0 + 32 + L, m - 1), dim, vec, qpre);   // next block, in flight
-        const int j0 = min(max(c0 - L, 0), m - 1);
-#pragma unroll
-        for (int c = 0; c < QStage<DK>::NPL; ++c) {
-          const uint4 r = stage[c * 64 + (j0 & 63)];
-          qk[4 * c] = *reinterpret_cast<const Cd*>(&r.x);
-          if (4 * c + 1 < DK) qk[4 * c + 1] = *reinterpret_cast<const Cd*>(&r.y);
-          if (4 * c + 2 < DK) qk[4 * c + 2] = *reinterpret_cast<const Cd*>(&r.z);
-          if (4 * c + 3 < DK) qk[4 * c + 3] = *reinterpret_cast<const Cd*>(&r.w);
-        }
+      for (int c = 0; c < NPL; ++c) {
+        stage[c * 64 + L] = c0 > 0 ? stage[c * 64 + 32 + L] : make_qrec<V, DK>(qpre, c);
+        stage[c * 64 + 32 + L] = make_qrec<V, DK>(qpre, c);
       }
+      __syncwarp();
+      load_point<Cd, DK>(Q, min(c0 + 32 + L, m - 1), dim, vec, qpre);   // next block, in flight
+      uint4 qr[NPL];
+#pragma unroll
+      for (int c = 0; c < NPL; ++c) qr[c] = sb[c * 64];
       // 4 steps unrolled (not 32): a kernel holds every R variant, and warps
       // running different variants side by side must not thrash the
       // instruction cache.
 #pragma unroll 4
       for (int s = 0; s < 32; ++s) {
-        const int j = c0 + s - L;
-        Cd qn[DK];
-        if constexpr (QStage<DK>::on) {
-          if (s + 1 < 32) {
-            const int jn = min(max(j + 1, 0), m - 1);
+        uint4 qn[NPL];   // the next step's record, read one step ahead
+        if (s + 1 < 32) {
 #pragma unroll
-            for (int c = 0; c < QStage<DK>::NPL; ++c) {
-              const uint4 r = stage[c * 64 + (jn & 63)];
-              qn[4 * c] = *reinterpret_cast<const Cd*>(&r.x);
-              if (4 * c + 1 < DK) qn[4 * c + 1] = *reinterpret_cast<const Cd*>(&r.y);
-              if (4 * c + 2 < DK) qn[4 * c + 2] = *reinterpret_cast<const Cd*>(&r.z);
-              if (4 * c + 3 < DK) qn[4 * c + 3] = *reinterpret_cast<const Cd*>(&r.w);
-            }
-          }
-        } else {
-          load_point<Cd, DK>(Q, min(max(j + 1, 0), m - 1), dim, vec, qn);
+          for (int c = 0; c < NPL; ++c) qn[c] = sb[c * 64 + s + 1];
         }
         T d[R];
-        if constexpr (kPack) {
-          unsigned long long qd[DK];
+        if constexpr (QR::kind == kNorm) {
 #pragma unroll
-          for (int k = 0; k < DK; ++k) qd[k] = pack2(qk[k], qk[k]);
+          for (int r = 0; r < R; ++r) {
+            unsigned acc = pn[r] + qr[0].w;
+            acc += (unsigned)pr[r][0] * qr[0].x;
+            if (DK > 1) acc += (unsigned)pr[r][1] * qr[0].y;
+            if (DK > 2) acc += (unsigned)pr[r][2 < DK ? 2 : 0] * qr[0].z;
+            d[r] = __uint_as_float(acc);
+          }
+        } else if constexpr (QR::kind == kDup) {
+          unsigned long long qd[2];
+          qd[0] = ((unsigned long long)qr[0].y << 32) | qr[0].x;
+          qd[1] = ((unsigned long long)qr[0].w << 32) | qr[0].z;
 #pragma unroll
           for (int h = 0; h < R / 2; ++h) {
             const unsigned long long t0 = sub2(pp[h][0], qd[0]);
-            unsigned long long acc = mul2(t0, t0);
-#pragma unroll
-            for (int k = 1; k < DK; ++k) {
-              const unsigned long long t = sub2(pp[h][k], qd[k]);
-              acc = fma2(t, t, acc);
-            }
+            const unsigned long long t1 = sub2(pp[h][1], qd[1]);
+            const unsigned long long acc = fma2(t1, t1, mul2(t0, t0));
             d[2 * h] = lo2(acc);
             d[2 * h + 1] = hi2(acc);
           }
-          if constexpr ((R & 1) != 0) d[R - 1] = vdist2<V, DK>(pr[R - 1], qk);
+          if constexpr ((R & 1) != 0) {
+            const Cd qk[DK] = {__uint_as_float(qr[0].x), __uint_as_float(qr[0].z)};
+            d[R - 1] = vdist2<V, DK>(pr[R - 1], qk);
+          }
         } else {
+          Cd qk[DK];
 #pragma unroll
-          for (int r = 0; r < R; ++r) d[r] = vdist2<V, DK>(pr[r], qk);
+          for (int c = 0; c < NPL; ++c) {
+            qk[4 * c] = *reinterpret_cast<const Cd*>(&qr[c].x);
+            if (4 * c + 1 < DK) qk[4 * c + 1] = *reinterpret_cast<const Cd*>(&qr[c].y);
+            if (4 * c + 2 < DK) qk[4 * c + 2] = *reinterpret_cast<const Cd*>(&qr[c].z);
+            if (4 * c + 3 < DK) qk[4 * c + 3] = *reinterpret_cast<const Cd*>(&qr[c].w);
+          }
+          if constexpr (kPack) {
+            unsigned long long qd[DK];
+#pragma unroll
+            for (int k = 0; k < DK; ++k) qd[k] = pack2(qk[k], qk[k]);
+#pragma unroll
+            for (int h = 0; h < R / 2; ++h) {
+              const unsigned long long t0 = sub2(pp[h][0], qd[0]);
+              unsigned long long acc = mul2(t0, t0);
+#pragma unroll
+              for (int k = 1; k < DK; ++k) {
+                const unsigned long long t = sub2(pp[h][k], qd[k]);
+                acc = fma2(t, t, acc);
+              }
+              d[2 * h] = lo2(acc);
+              d[2 * h + 1] = hi2(acc);
+            }
+            if constexpr ((R & 1) != 0) d[R - 1] = vdist2<V, DK>(pr[R - 1], qk);
+          } else {
+#pragma unroll
+            for (int r = 0; r < R; ++r) d[r] = vdist2<V, DK>(pr[r], qk);
+          }
         }
         const T tin = __shfl_sync(0xffffffffu, top_blk, s);
         T u = __shfl_up_sync(0xffffffffu, bout, 1);
@@ -311,19 +382,15 @@ __device__ __forceinline__ typename V::value warp_dfd(const typename V::coord* _
         upp = u;
         bout = up;
         if constexpr (AB::on) bmin = V::vmin(bmin, bout);
-        if (has_bottom) {
-          const T b31 = __shfl_sync(0xffffffffu, bout, 31);
-          out_blk = (L == s) ? b31 : out_blk;
-        }
+        if (has_bottom && L == 31) outb[s] = bout;   // column c0 + s - 31 of the stripe's bottom row
 #pragma unroll
-        for (int k = 0; k < DK; ++k) qk[k] = qn[k];
-      }
-      if (has_bottom) {
-        const int oc = c0 + L - 31;
-        __syncwarp();
-        if (oc >= 0 && oc < m) buf[oc] = out_blk;
+        for (int c = 0; c < NPL; ++c) qr[c] = qn[c];
       }
       __syncwarp();
+      if (has_bottom) {
+        const int oc = c0 + L - 31;
+        if (oc >= 0 && oc < m) buf[oc] = outb[L];
+      }
       if constexpr (AB::on) {
         if (c0 + 31 <= m - 1) {
           T cut = upp;
