@@ -96,11 +96,16 @@ __device__ __forceinline__ uint4 make_qrec(const typename V::coord (&q)[DK], int
 }
 constexpr int BUF_COLS = 4096;    // per-warp row buffer (columns) for multi-stripe pairs
 
-// Rows per lane chosen for a pair with `rows` rows (one stripe when possible).
+// Rows per lane chosen for a pair with `rows` rows: the fewest stripes
+// (one when rows <= 32 * Rmax), with the rows spread evenly over them, so a
+// pair of 300 rows runs two stripes of 160 rows rather than two of 256.
 template <int DK>
 __host__ __device__ __forceinline__ int rows_per_lane(int rows) {
-  const int r = (rows + 31) / 32;
-  return r > Rmax<DK>::value ? Rmax<DK>::value : (r < 1 ? 1 : r);
+  constexpr int RM = Rmax<DK>::value;
+  if (rows <= 32) return 1;
+  const int st = (rows + 32 * RM - 1) / (32 * RM);
+  const int r = (rows + 32 * st - 1) / (32 * st);
+  return r > RM ? RM : r;
 }
 
 // Point j of a curve into registers, coordinates past dim zero.  With `vec`
