@@ -260,6 +260,20 @@ __device__ __forceinline__ bool spin_smem_geq(const int* cnt, int need, Ctl* ctl
   }
 }
 
+// Records mirrored past the end of each q ring row (see QRow).
+constexpr int kQMirror = 64;
+
+// q ring row geometry: a row (one plane and column residue) holds NQ*C/TR
+// records followed by a mirror of its first kQMirror records, so the 34
+// records a 32-step block reads from any start are contiguous and a step
+// addresses its record at a fixed offset from the block's base.
+template <int C, int TR>
+struct QRow {
+  static constexpr int RING_LEN = NQ * C / TR;      // records of the ring proper
+  static constexpr int LEN = RING_LEN + kQMirror;   // records per row
+  static constexpr int PLANE = TR * LEN;            // records per plane
+};
+
 template <class V, int DK, int R>
 struct Layout {
   using Rows_ = Rows<V, DK, R>;
@@ -267,7 +281,9 @@ struct Layout {
   using T = typename V::value;
   static constexpr int C = ChunkCols<DK>::value;
   static constexpr int NPL = Rows_::NPL;
-  static constexpr size_t q_bytes = (size_t)NQ * NPL * C * sizeof(Rec);
+  static constexpr int TR = (Skew<V, R>::value == 2 || Skew<V, R>::value == 4) ? Skew<V, R>::value : 1;
+  using QR = QRow<C, TR>;
+  static constexpr size_t q_bytes = (size_t)NPL * QR::PLANE * sizeof(Rec);
   static constexpr size_t bar_off = q_bytes;
   static constexpr size_t ring_off = bar_off + 2 * NQ * sizeof(uint64_t);
   static __host__ __device__ size_t ctl_off(int W) { return ring_off + (size_t)(W + 1) * RING * sizeof(T); }
@@ -319,8 +335,8 @@ __device__ __forceinline__ void skew_block(const Rows<F32, DK, R>& rows, SkewSta
   constexpr int K = R / 2;
   constexpr int NPL = (DK + 1) / 2;
   constexpr int C = ChunkCols<DK>::value;
-  constexpr int NQC = NQ * C;
   constexpr int TR = (K == 2 || K == 4) ? K : 1;
+  using QR = QRow<C, TR>;
   constexpr int SK = 32 * K - 1;
   // Lane 0's inputs from the ring above: columns c0..c0+31 at indices
   // c0+3..c0+34 (9 aligned float4 loads, broadcast).
@@ -336,18 +352,18 @@ __device__ __forceinline__ void skew_block(const Rows<F32, DK, R>& rows, SkewSta
   float u = (L == 0) ? rin[3] : st.ush;
   // Stream position of pair 0's column at step 0 of this block; X = 0 mod TR.
   const unsigned X = xbase + (unsigned)(c0 - K * L);
-  const unsigned Xq = X / TR;
+  // the block's records start at ring position Xq mod the row length and
+  // run on into the mirror: fixed offsets from one base
+  const float4* qb = qring + ((X / TR) & (unsigned)(QR::RING_LEN - 1));
   float obuf[4];
 #pragma unroll
   for (int s = 0; s < G; ++s) {
     // (1) pair 0's record for step s + 2
     float4 nrec2[NPL];
     {
-      const int res = (s + 2) % TR;
-      const unsigned idx = (Xq + (unsigned)((s + 2) / TR)) & (unsigned)(NQC / TR - 1);
-      const float4* qp = qring + res * (NQC / TR) + idx;
+      const float4* qp = qb + ((s + 2) % TR) * QR::LEN + (s + 2) / TR;
 #pragma unroll
-      for (int c = 0; c < NPL; ++c) nrec2[c] = qp[c * NQC];
+      for (int c = 0; c < NPL; ++c) nrec2[c] = qp[c * QR::PLANE];
     }
     // (2) the first rows of all pairs (independent), then the second rows
     // with the bottom pair first, so the shuffle for step s + 1 leaves early
@@ -489,11 +505,12 @@ __device__ __forceinline__ void compute_stripe(const Args& a, int w, int64_t ban
       if (blk == 0) {
         // Step 0 and step 1 records of pair 0 (columns -K*L and 1 - K*L;
         // negative columns read stale records and only ever produce +inf).
-        constexpr int TRk = QTrans<V, R>::value;
+        constexpr int TRk = Lay::TR;
+        using QRk = typename Lay::QR;
         auto rec_at = [&](unsigned x, float4 (&r)[NPL]) {
-          const float4* qp = qr + (x % TRk) * (NQC / TRk) + ((x / TRk) & (unsigned)(NQC / TRk - 1));
+          const float4* qp = qr + (x % TRk) * QRk::LEN + ((x / TRk) & (unsigned)(QRk::RING_LEN - 1));
 #pragma unroll
-          for (int c = 0; c < NPL; ++c) r[c] = qp[c * NQC];
+          for (int c = 0; c < NPL; ++c) r[c] = qp[c * QRk::PLANE];
         };
         float4 r0[NPL];
         rec_at(xbase - (unsigned)(K * L), r0);
@@ -528,7 +545,7 @@ __device__ __forceinline__ void compute_stripe(const Args& a, int w, int64_t ban
         T u = __shfl_up_sync(0xffffffffu, bout, 1);
         u = (L == 0) ? rin : u;
         T d[R];
-        rows.dist(qaddr(max(col, 0)), NQC, d);
+        rows.dist(qaddr(max(col, 0)), Lay::QR::PLANE, d);
         T up = u, dg = upp;
 #pragma unroll
         for (int r = 0; r < R; ++r) {
@@ -576,8 +593,9 @@ __device__ __forceinline__ void comm_warp(const Args& a, int64_t band, unsigned 
   constexpr int C = Lay::C;
   constexpr int NPL = Lay::NPL;
   constexpr unsigned CHUNK_BYTES = (unsigned)(NPL * C * sizeof(Rec));
-  constexpr int NQC = NQ * C;
-  constexpr int TR = QTrans<V, R>::value;
+  constexpr int TR = Lay::TR;
+  using QR = typename Lay::QR;
+  static_assert(QTrans<V, R>::value == TR, "q ring residue split");
   const int L = threadIdx.x & 31;
   const int W = (int)(blockDim.x >> 5) - 1;
   Rec* qring = reinterpret_cast<Rec*>(smem);
@@ -606,15 +624,19 @@ __device__ __forceinline__ void comm_warp(const Args& a, int64_t band, unsigned 
       const bool slot_free = seq < (unsigned)NQ || mbar_test_wait(&empty[slot], ((seq / NQ) - 1) & 1);
       if (slot_free) {
         if (L == 0) {
-          mbar_arrive_expect_tx(&full[slot], CHUNK_BYTES);
+          // The first slots' leading records also go to the rows' mirrors.
+          const int mir0 = (int)slot * (C / TR);
+          const int nmir = mir0 < kQMirror ? min(C / TR, kQMirror - mir0) : 0;
+          mbar_arrive_expect_tx(&full[slot], CHUNK_BYTES + (unsigned)(NPL * TR * nmir * sizeof(Rec)));
           // One copy per plane and column residue (the ring layout of QTrans).
 #pragma unroll
           for (int pl = 0; pl < NPL; ++pl) {
 #pragma unroll
             for (int r = 0; r < TR; ++r) {
-              tma_load_1d(qring + (size_t)pl * NQC + (size_t)r * (NQC / TR) + (size_t)slot * (C / TR),
-                          qpk + ((size_t)issued * NPL + pl) * C + (size_t)r * (C / TR),
-                          (unsigned)((C / TR) * sizeof(Rec)), &full[slot]);
+              Rec* row = qring + (size_t)pl * QR::PLANE + (size_t)r * QR::LEN;
+              const Rec* src = qpk + ((size_t)issued * NPL + pl) * C + (size_t)r * (C / TR);
+              tma_load_1d(row + (size_t)slot * (C / TR), src, (unsigned)((C / TR) * sizeof(Rec)), &full[slot]);
+              if (nmir > 0) tma_load_1d(row + QR::RING_LEN + mir0, src, (unsigned)(nmir * sizeof(Rec)), &full[slot]);
             }
           }
         }
