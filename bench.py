@@ -45,14 +45,14 @@ L2_FLUSH_BYTES = 256 << 20
 CPU_SAMPLE = 50_000          # cpu_baseline of the long pair: prefix p[:a], q[:a]
 REF_SAMPLE = 20_000          # --impl reference: prefix per step
 
-# dram__bytes_read.sum + dram__bytes_write.sum per launch of the wavefront
-# kernel, keyed by the SHA-256 of the kernel source it was captured on
-# (reported as null when the kernel has changed since).
 # DRAM bytes (read + write) per launch of the main kernel, from an ncu launch
 # list of the benchmark command (gpu__time_duration.sum, dram__bytes_read.sum,
 # dram__bytes_write.sum: one pass), keyed by the hash of the kernel sources it
 # was taken on; any later source change reports null.
-TRAFFIC_BY_KERNEL_SHA: dict = {"5703067a15fc0880": 9429568}
+TRAFFIC_BY_KERNEL_SHA: dict = {
+    "7beb7b6acc1cc579": 9360230,     # wave_kernel<F32, 3, 6>, long pair 200,000^2
+    "025a8d5c1e61fa57": 289575749,   # batch_kernel<I32, 2>, ragged batch of 65,536 pairs
+}
 
 
 def long_workload(n, m):
