@@ -17,17 +17,21 @@
 namespace dfd {
 namespace batch {
 
-// Rows per lane of one stripe is at most RMAX (fewer registers for wider
-// points: a lane's R rows form one dependent chain per step, so wide points
-// keep R small and occupancy at two 256-thread CTAs per SM); pairs with
-// more rows run several stripes.
+// Rows per lane of one stripe is at most Rmax: 8 for points of up to 4
+// coordinates and 4 beyond (a lane's R rows form one dependent chain per
+// step).  Points of dim class 16 hold their packed rows in up to 172
+// registers, so those kernels run one 256-thread CTA per SM: each step's
+// four q planes then serve four rows instead of two, and a pair needs half
+// the stripes (16-D matrix: 0.59 Tcell/s, was 0.49 with two rows and two
+// CTAs per SM).  Other classes run two CTAs per SM.  Pairs with more rows
+// run several stripes.
 template <int DK>
 struct Rmax {
-  static constexpr int value = DK <= 4 ? 8 : (DK <= 8 ? 4 : 2);
+  static constexpr int value = DK <= 4 ? 8 : 4;
 };
 template <int DK>
 struct kBlocksPerSM {
-  static constexpr int value = 2;
+  static constexpr int value = DK >= 16 ? 1 : 2;
 };
 
 // q streams through a per-warp shared-memory window instead of per-lane
