@@ -38,9 +38,12 @@ def check_f32(d, d2, b):
 
 
 def ragged_edges(dtype, dim, seed):
-    """Lengths at warp/stripe edges: 1, 31..33, 255..257, 511..513, 600."""
+    """Lengths at warp/stripe edges (1, 31..33, 127..129, 255..257, 511..513)
+    and lengths whose rows are spread over several stripes of fewer than
+    32 * Rmax rows (160, 300, 384, 385, 600, 767, 769, 1000)."""
     rng = np.random.default_rng(seed)
-    edges = [1, 2, 31, 32, 33, 63, 64, 65, 127, 128, 129, 255, 256, 257, 511, 512, 513, 600]
+    edges = [1, 2, 31, 32, 33, 63, 64, 65, 127, 128, 129, 160, 255, 256, 257, 300, 384, 385, 511, 512, 513, 600,
+             767, 769, 1000]
     lens = []
     pairs = []
     for a in edges:
