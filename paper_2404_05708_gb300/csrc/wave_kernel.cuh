@@ -202,6 +202,27 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
 }
 
+// A block's publication: one fence for the whole warp, then each counter
+// store under a predicate.  The fence followed by a relaxed store is a
+// release; __syncwarp before it has made the other lanes' ring stores
+// visible to the storing lane.  (One fence and no divergent branch, where
+// a release store per lane took two of each.)
+__device__ __forceinline__ void fence_acq_rel_cta() { asm volatile("fence.acq_rel.cta;" ::: "memory"); }
+__device__ __forceinline__ void st_relaxed_cta_if(int* p, int v, bool pred) {
+  asm volatile(
+      "{\n\t.reg .pred P;\n\tsetp.ne.u32 P, %2, 0;\n\t@P st.relaxed.cta.shared::cta.s32 [%0], %1;\n\t}" ::"r"(
+          smem_addr(p)),
+      "r"(v), "r"((unsigned)pred)
+      : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_if(uint64_t* bar, bool pred) {
+  asm volatile(
+      "{\n\t.reg .pred P;\n\tsetp.ne.u32 P, %1, 0;\n\t@P mbarrier.arrive.shared::cta.b64 _, [%0];\n\t}" ::"r"(
+          smem_addr(bar)),
+      "r"((unsigned)pred)
+      : "memory");
+}
+
 // Predicated shared-memory store without a branch (keeps the unrolled
 // systolic block one basic block, so loads and distances of later steps can
 // be scheduled under the min/max chain of earlier ones).
@@ -566,16 +587,18 @@ __device__ __forceinline__ void compute_stripe(const Args& a, int w, int64_t ban
       }
     }
     __syncwarp();
-    if (L == 31) st_release_cta(&ctl->prod[w + 1], c0 + G - SK);
-    if (L == 0) st_release_cta(&ctl->cons[w], c0 + G);
+    fence_acq_rel_cta();
+    st_relaxed_cta_if(&ctl->prod[w + 1], c0 + G - SK, L == 31);
+    st_relaxed_cta_if(&ctl->cons[w], c0 + G, L == 0);
     // q chunks no lane of this warp will read again: the next read is lane
     // 31's first one in the next block (float32: the look-ahead of step 2).
+    // A block of G <= C columns finishes at most one chunk.
+    static_assert(G <= C, "one chunk release per block");
     const int first_unread = c0 + G - 31 * K + (kSkew ? 2 : 0);
-    const int consumed = max(0, first_unread) / C;
-    while (qdone < consumed && qdone < a.nch) {
-      if (L == 0) mbar_arrive(&empty[(gbase + (unsigned)qdone) & (NQ - 1)]);
-      ++qdone;
-    }
+    const int consumed = min(max(0, first_unread) / C, a.nch);
+    const bool release = qdone < consumed;
+    mbar_arrive_if(&empty[(gbase + (unsigned)qdone) & (NQ - 1)], release && L == 0);
+    qdone += release ? 1 : 0;
   }
   __syncwarp();
   while (qdone < a.nch) {
