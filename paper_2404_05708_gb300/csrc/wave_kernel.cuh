@@ -75,6 +75,30 @@ struct Args {
   void* out_dist;
   void* out_dist2;
   unsigned long long timeout_ns;
+  int64_t pstep;          // elements from one row of p to the next
+  // Optional second problem in the same launch (nprob == 2): the last n_b
+  // rows of the pair taken backwards (p_b points at the last row, row
+  // stride -pstep) against q reversed (its own packed stream qpk_b), with
+  // its own row buffer and progress words.  Tickets alternate between the
+  // two problems.
+  int nprob;
+  const void* p_b;
+  int64_t n_b;
+  int64_t nbands_b;
+  const void* qpk_b;
+  void* rowbuf_b;
+  unsigned long long* progress_b;
+};
+
+// The fields of Args that differ between the two problems of a launch.
+struct Prob {
+  const void* p;
+  int64_t n;
+  int64_t pstep;
+  const void* qpk;
+  void* rowbuf;
+  unsigned long long* progress;
+  int64_t nbands;
 };
 
 // ------------------------------------------------ rows held by one lane
@@ -90,14 +114,14 @@ struct Rows<F32, DK, R> {
   using Rec = float4;
   unsigned long long pp[R / 2][DK];
 
-  __device__ __forceinline__ void load(const float* P, int64_t r0, int64_t rlast, int dim) {
+  __device__ __forceinline__ void load(const float* P, int64_t r0, int64_t rlast, int dim, int64_t pstep) {
 #pragma unroll
     for (int h = 0; h < R / 2; ++h) {
       const int64_t i0 = min(r0 + 2 * h, rlast), i1 = min(r0 + 2 * h + 1, rlast);
 #pragma unroll
       for (int k = 0; k < DK; ++k) {
-        const float a = k < dim ? P[i0 * dim + k] : 0.f;
-        const float b = k < dim ? P[i1 * dim + k] : 0.f;
+        const float a = k < dim ? P[i0 * pstep + k] : 0.f;
+        const float b = k < dim ? P[i1 * pstep + k] : 0.f;
         pp[h][k] = pack2(a, b);
       }
     }
@@ -153,12 +177,12 @@ struct Rows<I32, DK, R> {
   using Rec = int4;
   int pr[R][DK];
 
-  __device__ __forceinline__ void load(const int32_t* P, int64_t r0, int64_t rlast, int dim) {
+  __device__ __forceinline__ void load(const int32_t* P, int64_t r0, int64_t rlast, int dim, int64_t pstep) {
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       const int64_t i = min(r0 + r, rlast);
 #pragma unroll
-      for (int k = 0; k < DK; ++k) pr[r][k] = k < dim ? P[i * dim + k] : 0;
+      for (int k = 0; k < DK; ++k) pr[r][k] = k < dim ? P[i * pstep + k] : 0;
     }
   }
 
@@ -440,7 +464,7 @@ __device__ __forceinline__ void skew_block(const Rows<F32, DK, R>& rows, SkewSta
 }
 
 template <class V, int DK, int R>
-__device__ __forceinline__ void compute_stripe(const Args& a, int w, int64_t band, unsigned gbase,
+__device__ __forceinline__ void compute_stripe(const Args& a, const Prob& pb, int w, int64_t band, unsigned gbase,
                                                unsigned char* smem) {
   using Lay = Layout<V, DK, R>;
   using T = typename V::value;
@@ -464,8 +488,8 @@ __device__ __forceinline__ void compute_stripe(const Args& a, int w, int64_t ban
   using Coord = typename V::coord;
   Rows<V, DK, R> rows;
   const int64_t rb0 = band * a.H;
-  const int64_t rend = min(rb0 + a.H, a.n);
-  rows.load(static_cast<const Coord*>(a.p), rb0 + (int64_t)(w * 32 + L) * R, rend - 1, a.dim);
+  const int64_t rend = min(rb0 + a.H, pb.n);
+  rows.load(static_cast<const Coord*>(pb.p), rb0 + (int64_t)(w * 32 + L) * R, rend - 1, a.dim, pb.pstep);
 
   const bool corner = band == 0 && w == 0 && L == 0;
   const unsigned xbase = gbase * (unsigned)C;   // stream position of the band's column 0
@@ -489,65 +513,68 @@ __device__ __forceinline__ void compute_stripe(const Args& a, int w, int64_t ban
 
   for (int blk = 0; blk < a.nblk; ++blk) {
     const int c0 = blk * G;
-    // One uniform check of both ring counters and the abort flag; spin
-    // (bounded) only when one of them is not there yet.
+    // One uniform check of both ring counters, the abort flag and the q
+    // chunks through the one holding column c0 + G + 1 (the last steps'
+    // look-ahead reads it); the slow path (a wait, or the first block,
+    // which always waits for its first chunk) handles them one by one.
     const int need_in = min(c0 + G, m);
     const int need_out = c0 + G - SK - RING;
+    const int qneed = min((c0 + G + 1) / C + 1, a.nch);
+    const float4* qr = reinterpret_cast<const float4*>(qring);
     {
       const int pv = ld_acquire_cta(&ctl->prod[w]);
       const int cv = ld_acquire_cta(&ctl->cons[w + 1]);
       const int ab = ld_volatile_smem(&ctl->abort);
-      if (pv < need_in || cv < need_out || ab) {
-        if (L == 0) spin_smem_geq(&ctl->prod[w], need_in, ctl, a.err, a.timeout_ns);
-        if (L == 31) spin_smem_geq(&ctl->cons[w + 1], need_out, ctl, a.err, a.timeout_ns);
-        __syncwarp();
-        if (ld_volatile_smem(&ctl->abort)) break;
-      }
-    }
-    // q chunks through the one holding column c0 + G + 1 (the last steps'
-    // look-ahead reads it).
-    const int qneed = min((c0 + G + 1) / C + 1, a.nch);
-    if (qready < qneed) {
-      bool qok = true;
-      while (qready < qneed) {
-        const unsigned seq = gbase + (unsigned)qready;
-        if (!mbar_wait(&full[seq & (NQ - 1)], (seq / NQ) & 1, a.err, a.timeout_ns)) {
-          *reinterpret_cast<volatile int*>(&ctl->abort) = 1;
-          qok = false;
-          break;
+      if (pv < need_in || cv < need_out || ab || qready < qneed) {
+        if (pv < need_in || cv < need_out || ab) {
+          // spin (bounded) only on the counter that is not there yet
+          if (L == 0) spin_smem_geq(&ctl->prod[w], need_in, ctl, a.err, a.timeout_ns);
+          if (L == 31) spin_smem_geq(&ctl->cons[w + 1], need_out, ctl, a.err, a.timeout_ns);
+          __syncwarp();
+          if (ld_volatile_smem(&ctl->abort)) break;
         }
-        ++qready;
+        bool qok = true;
+        while (qready < qneed) {
+          const unsigned seq = gbase + (unsigned)qready;
+          if (!mbar_wait(&full[seq & (NQ - 1)], (seq / NQ) & 1, a.err, a.timeout_ns)) {
+            *reinterpret_cast<volatile int*>(&ctl->abort) = 1;
+            qok = false;
+            break;
+          }
+          ++qready;
+        }
+        if (!qok) break;
+        if constexpr (kSkew) {
+          if (blk == 0) {
+            // Step 0 and step 1 records of pair 0 (columns -K*L and 1 - K*L;
+            // negative columns read stale records and only ever produce +inf).
+            constexpr int TRk = Lay::TR;
+            using QRk = typename Lay::QR;
+            auto rec_at = [&](unsigned x, float4 (&r)[NPL]) {
+              const float4* qp = qr + (x % TRk) * QRk::LEN + ((x / TRk) & (unsigned)(QRk::RING_LEN - 1));
+#pragma unroll
+              for (int c = 0; c < NPL; ++c) r[c] = qp[c * QRk::PLANE];
+            };
+            float4 r0[NPL];
+            rec_at(xbase - (unsigned)(K * L), r0);
+            rec_at(xbase + 1u - (unsigned)(K * L), ss.nrec1);
+#pragma unroll
+            for (int h = 0; h < SS::K; ++h) {
+#pragma unroll
+              for (int c = 0; c < NPL; ++c) ss.win[h][c] = r0[c];
+            }
+            rows.dist_pair(0, r0, ss.dcur[0][0], ss.dcur[0][1]);
+#pragma unroll
+            for (int h = 1; h < SS::K; ++h) {
+              ss.dcur[h][0] = ss.dcur[0][0];
+              ss.dcur[h][1] = ss.dcur[0][1];
+            }
+          }
+        }
       }
-      if (!qok) break;
     }
 
     if constexpr (kSkew) {
-      const float4* qr = reinterpret_cast<const float4*>(qring);
-      if (blk == 0) {
-        // Step 0 and step 1 records of pair 0 (columns -K*L and 1 - K*L;
-        // negative columns read stale records and only ever produce +inf).
-        constexpr int TRk = Lay::TR;
-        using QRk = typename Lay::QR;
-        auto rec_at = [&](unsigned x, float4 (&r)[NPL]) {
-          const float4* qp = qr + (x % TRk) * QRk::LEN + ((x / TRk) & (unsigned)(QRk::RING_LEN - 1));
-#pragma unroll
-          for (int c = 0; c < NPL; ++c) r[c] = qp[c * QRk::PLANE];
-        };
-        float4 r0[NPL];
-        rec_at(xbase - (unsigned)(K * L), r0);
-        rec_at(xbase + 1u - (unsigned)(K * L), ss.nrec1);
-#pragma unroll
-        for (int h = 0; h < SS::K; ++h) {
-#pragma unroll
-          for (int c = 0; c < NPL; ++c) ss.win[h][c] = r0[c];
-        }
-        rows.dist_pair(0, r0, ss.dcur[0][0], ss.dcur[0][1]);
-#pragma unroll
-        for (int h = 1; h < SS::K; ++h) {
-          ss.dcur[h][0] = ss.dcur[0][0];
-          ss.dcur[h][1] = ss.dcur[0][1];
-        }
-      }
       skew_block<DK, (kSkew ? R : 2)>(reinterpret_cast<const Rows<F32, DK, (kSkew ? R : 2)>&>(rows), ss,
                                       reinterpret_cast<const float*>(ring_in), reinterpret_cast<float*>(ring_out),
                                       qr, xbase, c0, L);
@@ -609,7 +636,8 @@ __device__ __forceinline__ void compute_stripe(const Args& a, int w, int64_t ban
 
 // ------------------------------------------------------- communication warp
 template <class V, int DK, int R>
-__device__ __forceinline__ void comm_warp(const Args& a, int64_t band, unsigned gbase, unsigned char* smem) {
+__device__ __forceinline__ void comm_warp(const Args& a, const Prob& pb, int64_t band, unsigned gbase,
+                                          unsigned char* smem) {
   using Lay = Layout<V, DK, R>;
   using T = typename V::value;
   using Rec = typename Lay::Rec;
@@ -628,8 +656,8 @@ __device__ __forceinline__ void comm_warp(const Args& a, int64_t band, unsigned 
   Ctl* ctl = reinterpret_cast<Ctl*>(smem + Lay::ctl_off(W));
   T* ring0 = rings;
   const T* ringW = rings + (size_t)W * RING;
-  const Rec* qpk = static_cast<const Rec*>(a.qpk);
-  T* rowbuf = static_cast<T*>(a.rowbuf);
+  const Rec* qpk = static_cast<const Rec*>(pb.qpk);
+  T* rowbuf = static_cast<T*>(pb.rowbuf);
 
   const int m = (int)a.m;
   const int fill_end = a.nblk * G;
@@ -676,7 +704,7 @@ __device__ __forceinline__ void comm_warp(const Args& a, int64_t band, unsigned 
       if (band > 0) {
         if (pub < (unsigned long long)min(filled + 32, m)) {
           unsigned long long pv = 0;
-          if (L == 0) pv = ld_acquire_u64(&a.progress[band - 1]);
+          if (L == 0) pv = ld_acquire_u64(&pb.progress[band - 1]);
           pub = __shfl_sync(0xffffffffu, pv, 0);
         }
         // Columns past m are +inf padding, ready once column m - 1 is.
@@ -713,7 +741,7 @@ __device__ __forceinline__ void comm_warp(const Args& a, int64_t band, unsigned 
           if (k < units && col < m) {
             const T val = ringW[ridx(col)];
             st_cg(rowbuf + col, val);
-            if (band == a.nbands - 1 && col == m - 1) {
+            if (band == pb.nbands - 1 && col == m - 1) {
               if constexpr (sizeof(T) == 4) {
                 if (a.out_dist2) static_cast<float*>(a.out_dist2)[0] = (float)val;
                 if (a.out_dist) static_cast<float*>(a.out_dist)[0] = sqrtf((float)val);
@@ -730,7 +758,7 @@ __device__ __forceinline__ void comm_warp(const Args& a, int64_t band, unsigned 
           st_release_cta(&ctl->cons[W], drained);
           // The release orders the warp's row-buffer stores (made visible to
           // lane 0 by __syncwarp) before the progress word at GPU scope.
-          st_release_u64(&a.progress[band], (unsigned long long)drained);
+          st_release_u64(&pb.progress[band], (unsigned long long)drained);
         }
         progressed = true;
       }
@@ -803,12 +831,24 @@ __global__ void __launch_bounds__((kMaxWarps<V, DK, R>::value + 1) * 32, 1) wave
       }
     }
     __syncthreads();
-    const int64_t band = ctl->band;
-    if (band >= a.nbands) break;
+    const int t = ctl->band;
+    const int prob = a.nprob == 2 ? (t & 1) : 0;
+    const int64_t band = a.nprob == 2 ? (int64_t)(t >> 1) : (int64_t)t;
+    if (band >= max(a.nbands, a.nprob == 2 ? a.nbands_b : (int64_t)0)) break;
+    Prob pb;
+    if (prob == 0) {
+      pb = Prob{a.p, a.n, a.pstep, a.qpk, a.rowbuf, a.progress, a.nbands};
+    } else {
+      pb = Prob{a.p_b, a.n_b, -a.pstep, a.qpk_b, a.rowbuf_b, a.progress_b, a.nbands_b};
+    }
+    if (band >= pb.nbands) {   // this problem has one band fewer than the other
+      __syncthreads();
+      continue;
+    }
     if (warp == W)
-      comm_warp<V, DK, R>(a, band, gbase, smem);
+      comm_warp<V, DK, R>(a, pb, band, gbase, smem);
     else
-      compute_stripe<V, DK, R>(a, warp, band, gbase, smem);
+      compute_stripe<V, DK, R>(a, pb, warp, band, gbase, smem);
     gbase += (unsigned)a.nch;
     __syncthreads();
     if (ctl->abort) break;
@@ -819,9 +859,10 @@ __global__ void __launch_bounds__((kMaxWarps<V, DK, R>::value + 1) * 32, 1) wave
 // Writes the per-band q stream: nch chunks of C columns, NPL 16-byte planes
 // per column, each plane in the column order qpos(., TR, C); columns past m
 // repeat q_{m-1} (a repeated point does not change the distance, Sec. 4
-// footnote; they are never read into the result).
+// footnote; they are never read into the result).  With `rev` the stream is
+// that of q reversed (column j is q_{m-1-j}).
 template <class V, int DK>
-__global__ void pack_q_kernel(const typename V::coord* q, int64_t m, int dim, int nch, int TR, void* out) {
+__global__ void pack_q_kernel(const typename V::coord* q, int64_t m, int dim, int nch, int TR, int rev, void* out) {
   constexpr int C = ChunkCols<DK>::value;
   using Rows_ = Rows<V, DK, 2>;
   constexpr int NPL = Rows_::NPL;
@@ -834,7 +875,8 @@ __global__ void pack_q_kernel(const typename V::coord* q, int64_t m, int dim, in
     const int rem = (int)(idx % (C * NPL));
     const int plane = rem / C;
     const int jj = rem % C;
-    const int64_t j = min(chunk * C + jj, m - 1);
+    const int64_t jc = min(chunk * C + jj, m - 1);
+    const int64_t j = rev ? m - 1 - jc : jc;   // the reversed problem's column jc is q's column m-1-jc
     const typename V::coord* qj = q + j * dim;
     Rec r;
     if constexpr (std::is_same<V, F32>::value) {
@@ -850,6 +892,49 @@ __global__ void pack_q_kernel(const typename V::coord* q, int64_t m, int dim, in
       r.w = k + 3 < dim ? qj[k + 3] : 0;
     }
     o[chunk * (C * NPL) + plane * C + qpos(jj, TR, C)] = r;
+  }
+}
+
+// ------------------------------------------------------------ combine
+// Two wavefronts meet between rows n1-1 and n1: F[j] = M[n1-1][j] of the
+// forward problem, and B[j], the bottleneck of the best path from (n1, j)
+// to (n-1, m-1), is the backward problem's bottom row read in reverse
+// (rowbuf_b[m-1-j]).  Every monotone path crosses from row n1-1 to row n1
+// once, by a vertical step (to column j) or a diagonal one (to j+1), so
+// delta^2 = min_j max(F[j], min(B[j], B[j+1])): a selection among the same
+// squared distances, bit-identical to the single wavefront's result.  One
+// CTA, a block-wide min.
+template <class V>
+__global__ void combine_kernel(const void* rowbuf_f, const void* rowbuf_b, int64_t m, void* out_dist,
+                               void* out_dist2) {
+  using T = typename V::value;
+  const T* F = static_cast<const T*>(rowbuf_f);
+  const T* B = static_cast<const T*>(rowbuf_b);
+  T best = V::inf();
+  for (int64_t j = threadIdx.x; j < m; j += blockDim.x) {
+    const T bj = B[m - 1 - j];
+    const T bj1 = j + 1 < m ? B[m - 2 - j] : V::inf();
+    best = V::vmin(best, V::vmax(F[j], V::vmin(bj, bj1)));
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) best = V::vmin(best, __shfl_xor_sync(0xffffffffu, best, off));
+  __shared__ T part[32];
+  const int warp = threadIdx.x >> 5, L = threadIdx.x & 31;
+  if (L == 0) part[warp] = best;
+  __syncthreads();
+  if (warp == 0) {
+    T x = L < (int)(blockDim.x >> 5) ? part[L] : V::inf();
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) x = V::vmin(x, __shfl_xor_sync(0xffffffffu, x, off));
+    if (L == 0) {
+      if constexpr (sizeof(T) == 4) {
+        if (out_dist2) static_cast<float*>(out_dist2)[0] = (float)x;
+        if (out_dist) static_cast<float*>(out_dist)[0] = sqrtf((float)x);
+      } else {
+        if (out_dist2) static_cast<long long*>(out_dist2)[0] = (long long)x;
+        if (out_dist) static_cast<double*>(out_dist)[0] = sqrt((double)x);
+      }
+    }
   }
 }
 

@@ -21,20 +21,47 @@ dfd_status wave_launch(dfd_context* ctx, int dim, const void* p, int64_t n, cons
   } else {
   if (!wave::shape_supported(std::is_same<V, F32>::value, DK, R, W)) return DFD_ERR_UNSUPPORTED;
   const int64_t H = (int64_t)W * 32 * R;
-  const int64_t nbands = (n + H - 1) / H;
+  const int64_t nbands_all = (n + H - 1) / H;
   // Lane 31's bottom row reaches column m - 1 at step m - 1 + 32*K - 1.
   const int64_t nblk64 = (m + 32 * K - 1 + wave::G - 1) / wave::G;
   if (nblk64 * wave::G > (int64_t)INT32_MAX / 2) return DFD_ERR_UNSUPPORTED;
   const int nblk = (int)nblk64;
   // The look-ahead of the last steps reads columns up to nblk*G + 1.
   const int nch = (nblk * wave::G + 2 + C - 1) / C;
+  const size_t q_bytes = (size_t)nch * Lay::NPL * C * sizeof(Rec);
 
-  const size_t off_prog = 256;
-  const size_t off_row = align_up(off_prog + (size_t)nbands * sizeof(unsigned long long), 256);
-  const size_t off_q = align_up(off_row + (size_t)m * sizeof(T), 256);
-  const size_t total = off_q + (size_t)nch * Lay::NPL * C * sizeof(Rec);
-  dfd_status st = ensure_scratch(ctx, total);
+  // Two wavefronts when the pair has two bands or more: the first
+  // ceil(#bands / 2) bands forward from (0, 0), the remaining rows backward
+  // from (n-1, m-1) on both curves reversed, met by combine_kernel.  Each
+  // front starts its own chain of bands, so the launch waits for half as
+  // many band start-up lags.  The scratch doubles (two row buffers, two
+  // packed q streams); where it cannot grow (a fixed scratch array), one
+  // forward wavefront runs.
+  auto layout = [&](bool two, size_t* off_prog_b, size_t* off_row, size_t* off_row_b, size_t* off_q,
+                    size_t* off_q_b, int64_t nb0, int64_t nb1) {
+    const size_t off_prog = 256;
+    *off_prog_b = align_up(off_prog + (size_t)nb0 * sizeof(unsigned long long), 256);
+    *off_row = align_up(*off_prog_b + (two ? (size_t)nb1 * sizeof(unsigned long long) : 0), 256);
+    *off_row_b = align_up(*off_row + (size_t)m * sizeof(T), 256);
+    *off_q = align_up(*off_row_b + (two ? (size_t)m * sizeof(T) : 0), 256);
+    *off_q_b = align_up(*off_q + q_bytes, 256);
+    return *off_q_b + (two ? q_bytes : 0);
+  };
+  bool two = nbands_all >= 2;
+  const int64_t n1_split = ((nbands_all + 1) / 2) * H;   // forward rows when split (< n for two bands or more)
+  size_t off_prog_b, off_row, off_row_b, off_q, off_q_b;
+  dfd_status st = DFD_OK;
+  if (two) {
+    st = ensure_scratch(ctx, layout(true, &off_prog_b, &off_row, &off_row_b, &off_q, &off_q_b,
+                                    (nbands_all + 1) / 2, (n - n1_split + H - 1) / H));
+    if (st != DFD_OK) two = false;
+  }
+  if (!two) st = ensure_scratch(ctx, layout(false, &off_prog_b, &off_row, &off_row_b, &off_q, &off_q_b, nbands_all, 0));
   if (st != DFD_OK) return st;
+  const int64_t n1 = two ? n1_split : n;   // rows of the forward problem
+  const int64_t n2 = n - n1;               // rows of the backward problem (0: one front)
+  const int64_t nb0 = (n1 + H - 1) / H;
+  const int64_t nb1 = (n2 + H - 1) / H;
   char* base = static_cast<char*>(ctx->scratch);
 
   cudaError_t e = cudaMemsetAsync(base, 0, off_row, s);
@@ -43,35 +70,47 @@ dfd_status wave_launch(dfd_context* ctx, int dim, const void* p, int64_t n, cons
     const int64_t recs = (int64_t)nch * C * Lay::NPL;
     const int threads = 256;
     const int blocks = (int)std::min<int64_t>((recs + threads - 1) / threads, 4 * (int64_t)ctx->num_sms);
-    wave::pack_q_kernel<V, DK><<<blocks, threads, 0, s>>>(static_cast<const typename V::coord*>(q), m, dim, nch,
-                                                         wave::QTrans<V, R>::value, base + off_q);
+    for (int r = 0; r < (two ? 2 : 1); ++r)
+      wave::pack_q_kernel<V, DK><<<blocks, threads, 0, s>>>(static_cast<const typename V::coord*>(q), m, dim, nch,
+                                                           wave::QTrans<V, R>::value, r, base + (r ? off_q_b : off_q));
   }
   const size_t smem = Lay::bytes(W);
   if (smem > ctx->smem_optin) return DFD_ERR_UNSUPPORTED;
   e = cudaFuncSetAttribute(wave::wave_kernel<V, DK, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return cuda_status(e);
 
+  using Coord = typename V::coord;
   wave::Args a;
   a.p = p;
-  a.n = n;
+  a.n = two ? n1 : n;
   a.dim = dim;
   a.qpk = base + off_q;
   a.m = m;
   a.nch = nch;
   a.nblk = nblk;
   a.H = H;
-  a.nbands = nbands;
+  a.nbands = nb0;
   a.rowbuf = base + off_row;
-  a.progress = reinterpret_cast<unsigned long long*>(base + off_prog);
+  a.progress = reinterpret_cast<unsigned long long*>(base + 256);
   a.ticket = reinterpret_cast<int*>(base);
   a.err = ctx->d_err;
-  a.out_dist = out_dist;
-  a.out_dist2 = out_dist2;
+  a.out_dist = two ? nullptr : out_dist;     // two fronts: combine_kernel writes the result
+  a.out_dist2 = two ? nullptr : out_dist2;
   a.timeout_ns = timeout_ns(ctx);
+  a.pstep = dim;
+  a.nprob = two ? 2 : 1;
+  a.p_b = two ? static_cast<const void*>(static_cast<const Coord*>(p) + (n - 1) * (int64_t)dim) : nullptr;
+  a.n_b = n2;
+  a.nbands_b = nb1;
+  a.qpk_b = two ? base + off_q_b : nullptr;
+  a.rowbuf_b = two ? base + off_row_b : nullptr;
+  a.progress_b = reinterpret_cast<unsigned long long*>(base + off_prog_b);
+  const int64_t nbands = nb0 + nb1;
   int grid = ctas > 0 ? ctas : ctx->num_sms;
   grid = (int)std::min<int64_t>(grid, nbands);
   timing_begin(ctx, s);
   wave::wave_kernel<V, DK, R><<<grid, (W + 1) * 32, smem, s>>>(a);
+  if (two) wave::combine_kernel<V><<<1, 1024, 0, s>>>(a.rowbuf, a.rowbuf_b, m, out_dist, out_dist2);
   timing_end(ctx, s);
   return cuda_status(cudaGetLastError());
   }
