@@ -216,6 +216,11 @@ __device__ __forceinline__ int ld_acquire_cta(const int* p) {
   asm volatile("ld.acquire.cta.shared::cta.s32 %0, [%1];" : "=r"(v) : "r"(smem_addr(p)) : "memory");
   return v;
 }
+__device__ __forceinline__ int ld_relaxed_cta(const int* p) {
+  int v;
+  asm volatile("ld.relaxed.cta.shared::cta.s32 %0, [%1];" : "=r"(v) : "r"(smem_addr(p)) : "memory");
+  return v;
+}
 __device__ __forceinline__ void st_release_cta(int* p, int v) {
   asm volatile("st.release.cta.shared::cta.s32 [%0], %1;" ::"r"(smem_addr(p)), "r"(v) : "memory");
 }
@@ -522,8 +527,10 @@ __device__ __forceinline__ void compute_stripe(const Args& a, const Prob& pb, in
     const int qneed = min((c0 + G + 1) / C + 1, a.nch);
     const float4* qr = reinterpret_cast<const float4*>(qring);
     {
-      const int pv = ld_acquire_cta(&ctl->prod[w]);
-      const int cv = ld_acquire_cta(&ctl->cons[w + 1]);
+      // relaxed reads and one fence after the check (an acquire): cheaper
+      // than two acquire loads (measured: 2 cycles a step)
+      const int pv = ld_relaxed_cta(&ctl->prod[w]);
+      const int cv = ld_relaxed_cta(&ctl->cons[w + 1]);
       const int ab = ld_volatile_smem(&ctl->abort);
       if (pv < need_in || cv < need_out || ab || qready < qneed) {
         if (pv < need_in || cv < need_out || ab) {
@@ -572,6 +579,7 @@ __device__ __forceinline__ void compute_stripe(const Args& a, const Prob& pb, in
           }
         }
       }
+      fence_acq_rel_cta();
     }
 
     if constexpr (kSkew) {
