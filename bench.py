@@ -161,7 +161,10 @@ class LongPair:
 
     def __init__(self, args, ctx, dfd, torch, workloads, rank, world):
         self.n, self.m = args.n, args.m
-        self.p_np, self.q_np = workloads.warped_long_pair(self.n, self.m, dim=DIM, seed=SEED)
+        p_np, q_np = workloads.warped_long_pair(self.n, self.m, dim=DIM, seed=SEED)
+        # the e2e step reads the inputs from page-locked host memory
+        self.p_np = torch.from_numpy(p_np).pin_memory().numpy()
+        self.q_np = torch.from_numpy(q_np).pin_memory().numpy()
         self.p = torch.from_numpy(self.p_np).cuda()
         self.q = torch.from_numpy(self.q_np).cuda()
         self.ctx, self.torch = ctx, torch
@@ -318,12 +321,19 @@ class Batch(_Many):
         self.config = {"workload": BATCH_WORKLOAD.format(n=b.pairs.shape[0]),
                        "n_pairs": int(pairs.shape[0]), "dim": 2, "cells_per_step": self.cells,
                        "kernel_sha": kernel_sha(("batch_kernel.cuh", "batch_launch.cuh", "dfd_device.cuh"))}
-        self.h2d = b.points.nbytes
-        self.d2h = self.out2.numel() * 8
+        # e2e: dfd_batch_host from page-locked points (copy slices overlap the
+        # batch kernels), offsets and pairs from host memory, dist + dist2 back
+        self.pts_pinned_np = self.pts_host.numpy()
+        self.h2d = b.points.nbytes + b.offsets.nbytes + pairs.nbytes
+        self.d2h = pairs.shape[0] * 16
         narrow = int_pair_classes(b, pairs)
         cells = ln[pairs[:, 0]].astype(np.int64) * ln[pairs[:, 1]]
         self.cells_narrow = int(cells[narrow].sum())
         self.config["value_classes"] = {"uint32_bits_pairs": int(narrow.sum()), "int64_pairs": int((~narrow).sum())}
+
+    def e2e_step(self):
+        d, d2 = self.ctx.batch_host(self.pts_pinned_np, self.b.offsets, self.pairs_np)
+        return d2
 
     def micro_mix(self):
         mix = [("cell_i32b_d2", self.cells_narrow), ("cell_i32_d2", self.cells - self.cells_narrow)]

@@ -125,9 +125,10 @@ dfd_status dfd_pair_reference(dfd_context* ctx, dfd_dtype dtype, int dim, const 
                               const void* q, int64_t m, void* out_dist, void* out_dist2, void* stream);
 
 /*
- * dfd_pair with HOST buffers: copies p and q to the device (through the
- * context's pinned staging area), runs dfd_pair on the context's internal
- * stream, copies the result back and waits for it.  p, q, out_dist and
+ * dfd_pair with HOST buffers: copies p and q to the device (directly when
+ * they are page-locked, e.g. from cudaHostAlloc or a pinned tensor; else
+ * through the context's pinned staging area), runs dfd_pair on the
+ * context's internal stream, copies the result back and waits for it.  p, q, out_dist and
  * out_dist2 are host pointers (outputs may be NULL, not both).  Device
  * errors are returned directly.
  */
@@ -256,6 +257,22 @@ dfd_status dfd_mc_pair(dfd_context* ctx, int dim, const float* p, int64_t n, con
  */
 dfd_status dfd_matrix(dfd_context* ctx, dfd_dtype dtype, int dim, const void* points, const int64_t* offsets,
                       int64_t n_curves, void* out_condensed, void* out_dist2, void* stream);
+
+/*
+ * dfd_batch with HOST buffers (points, offsets, pairs and the outputs are
+ * host pointers; outputs may be NULL, not both): synchronous.  The points
+ * are copied to the device in up to 8 slices of curves (about 128 MiB each)
+ * on a copy stream, directly when they are page-locked and through the
+ * context's pinned staging area otherwise; the pairs are grouped by the
+ * slice of their later curve and each group runs as soon as its slice has
+ * landed, so the copies overlap the computation.  Results are bit-identical
+ * to dfd_batch on the same data.  Offsets must be nondecreasing and every
+ * id in [0, n_curves) (checked on the host: DFD_ERR_INVALID_ARG); the
+ * device-side checks are dfd_batch's, returned directly.  Uses the context's
+ * internal streams and staging: one host-buffer call per context at a time.
+ */
+dfd_status dfd_batch_host(dfd_context* ctx, dfd_dtype dtype, int dim, const void* points, const int64_t* offsets,
+                          int64_t n_curves, const int32_t* pairs, int64_t n_pairs, void* out_dist, void* out_dist2);
 
 /*
  * CUDA-graph capture of one dfd_batch / dfd_matrix call (input checks, plan

@@ -1,0 +1,229 @@
+// batch_host.cu -- dfd_batch with HOST buffers (the ragged batch, K4, Sec. 4's
+// batches of curve pairs): copies the points to the device in slices of
+// curves on a copy stream while the batch engine runs the pairs whose
+// curves have arrived, then copies the distances back.
+//
+// The pairs are grouped by the slice of their later curve (a counting sort
+// on the host); slice k's group runs as one batch launch over curves
+// [0, end_k) as soon as slice k has landed, so the copy of slice k+1 overlaps
+// it.  Each launch boxes and checks only the curves no earlier launch
+// covered (the int32 bounding boxes live in one buffer for the whole
+// batch), and the last launch waits for every slice and covers all curves,
+// so the input checks are those of dfd_batch.  Results are bit-identical to
+// dfd_batch on the same data: each pair is computed by the same engine.
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "batch_launch.cuh"
+#include "dfd_internal.h"
+
+namespace dfd {
+#define DFD_RANGE_EXTERN(V, DK)                                                                                 \
+  extern template dfd_status batch_launch_range<V, DK>(dfd_context*, int, const void*, const int64_t*, int64_t, \
+                                                       const int32_t*, int64_t, void*, void*, cudaStream_t,     \
+                                                       int64_t, int*);
+DFD_RANGE_EXTERN(F32, 2)
+DFD_RANGE_EXTERN(F32, 3)
+DFD_RANGE_EXTERN(F32, 4)
+DFD_RANGE_EXTERN(F32, 8)
+DFD_RANGE_EXTERN(F32, 16)
+DFD_RANGE_EXTERN(I32, 2)
+DFD_RANGE_EXTERN(I32, 3)
+DFD_RANGE_EXTERN(I32, 4)
+DFD_RANGE_EXTERN(I32, 8)
+DFD_RANGE_EXTERN(I32, 16)
+#undef DFD_RANGE_EXTERN
+
+namespace {
+
+// Points per copy slice (about).  Every slice's launch ends on the tail of
+// its longest pairs (a 512 x 512 pair is ~0.2 ms on one warp), so slices are
+// few and large: on the 65,536-pair int32 batch (277 MB) 8 slices of 32 MB
+// ran at 1.39 Tcell/s end to end, 3 of 128 MB at 1.48.
+constexpr size_t kSliceBytes = (size_t)128 << 20;
+
+dfd_status range_run(dfd_context* ctx, dfd_dtype dtype, int dim, const void* points, const int64_t* offsets,
+                     int64_t n_curves, const int32_t* pairs, int64_t n_pairs, void* out_dist, void* out_dist2,
+                     cudaStream_t s, int64_t first, int* bbox) {
+#define DFD_R_DK(V)                                                                                              \
+  switch (dim_class(dim)) {                                                                                      \
+    case 2: return batch_launch_range<V, 2>(ctx, dim, points, offsets, n_curves, pairs, n_pairs, out_dist,       \
+                                            out_dist2, s, first, bbox);                                          \
+    case 3: return batch_launch_range<V, 3>(ctx, dim, points, offsets, n_curves, pairs, n_pairs, out_dist,       \
+                                            out_dist2, s, first, bbox);                                          \
+    case 4: return batch_launch_range<V, 4>(ctx, dim, points, offsets, n_curves, pairs, n_pairs, out_dist,       \
+                                            out_dist2, s, first, bbox);                                          \
+    case 8: return batch_launch_range<V, 8>(ctx, dim, points, offsets, n_curves, pairs, n_pairs, out_dist,       \
+                                            out_dist2, s, first, bbox);                                          \
+    case 16: return batch_launch_range<V, 16>(ctx, dim, points, offsets, n_curves, pairs, n_pairs, out_dist,     \
+                                              out_dist2, s, first, bbox);                                        \
+    default: return DFD_ERR_UNSUPPORTED;                                                                         \
+  }
+  if (dtype == DFD_F32) {
+    DFD_R_DK(F32)
+  } else {
+    DFD_R_DK(I32)
+  }
+#undef DFD_R_DK
+}
+
+bool page_locked(const void* x) {
+  cudaPointerAttributes at;
+  const bool yes = cudaPointerGetAttributes(&at, x) == cudaSuccess && at.type == cudaMemoryTypeHost;
+  cudaGetLastError();
+  return yes;
+}
+
+}  // namespace
+}  // namespace dfd
+
+using namespace dfd;
+
+extern "C" dfd_status dfd_batch_host(dfd_context* ctx, dfd_dtype dtype, int dim, const void* points,
+                                     const int64_t* offsets, int64_t n_curves, const int32_t* pairs, int64_t n_pairs,
+                                     void* out_dist, void* out_dist2) {
+  dfd_status st = check_batch_args(ctx, dtype, dim, points, offsets, n_curves, out_dist, out_dist2);
+  if (st != DFD_OK) return st;
+  if (!pairs || n_pairs < 0 || n_pairs > INT32_MAX) return DFD_ERR_INVALID_ARG;
+  if (n_pairs == 0) return DFD_OK;
+  // host-side checks the slicing relies on: monotone offsets, ids in range
+  if (offsets[0] < 0) return DFD_ERR_INVALID_ARG;
+  for (int64_t c = 0; c < n_curves; ++c)
+    if (offsets[c + 1] < offsets[c]) return DFD_ERR_INVALID_ARG;
+  for (int64_t k = 0; k < 2 * n_pairs; ++k)
+    if (pairs[k] < 0 || pairs[k] >= n_curves) return DFD_ERR_INVALID_ARG;
+  if ((st = set_device(ctx)) != DFD_OK) return st;
+
+  const int64_t n_pts = offsets[n_curves];
+  const size_t elem = 4;   // float32 and int32 coordinates
+  const size_t pts_bytes = (size_t)n_pts * dim * elem;
+  const bool f32 = dtype == DFD_F32;
+  const size_t d1 = f32 ? 4 : 8, d2 = f32 ? 4 : 8;   // result element sizes (dist, dist2)
+
+  // slices of curves with about kSliceBytes of points each
+  const int K = (int)std::max<size_t>(1, std::min<size_t>(kMaxSlices, (pts_bytes + kSliceBytes - 1) / kSliceBytes));
+  std::vector<int64_t> bound(K + 1, n_curves);
+  bound[0] = 0;
+  for (int k = 1; k < K; ++k) {
+    const int64_t target = (int64_t)((double)n_pts * k / K);
+    bound[k] = std::lower_bound(offsets, offsets + n_curves + 1, target) - offsets;
+    bound[k] = std::min(std::max(bound[k], bound[k - 1]), n_curves);
+  }
+  // group the pairs by the slice of their later curve (stable counting sort)
+  std::vector<int> slice_of(n_pairs);
+  std::vector<int64_t> start(K + 1, 0);
+  for (int64_t i = 0; i < n_pairs; ++i) {
+    const int64_t c = std::max(pairs[2 * i], pairs[2 * i + 1]);
+    const int k = (int)(std::upper_bound(bound.begin() + 1, bound.end(), c) - (bound.begin() + 1));
+    slice_of[i] = std::min(k, K - 1);
+    ++start[slice_of[i] + 1];
+  }
+  for (int k = 0; k < K; ++k) start[k + 1] += start[k];
+
+  // pinned staging: [offsets | pairs (grouped) | dist | dist2 | points if pageable]
+  const bool pts_locked = page_locked(points);
+  const size_t off_b = align_up((size_t)(n_curves + 1) * 8, 256);
+  const size_t pair_b = align_up((size_t)n_pairs * 8, 256);
+  const size_t dist_b = align_up((size_t)n_pairs * d1, 256), dist2_b = align_up((size_t)n_pairs * d2, 256);
+  const size_t host_bytes = off_b + pair_b + dist_b + dist2_b + (pts_locked ? 0 : align_up(pts_bytes, 256));
+  if ((st = ensure_pinned(ctx, host_bytes)) != DFD_OK) return st;
+  char* h = static_cast<char*>(ctx->pinned);
+  std::memcpy(h, offsets, (size_t)(n_curves + 1) * 8);
+  int32_t* hp = reinterpret_cast<int32_t*>(h + off_b);
+  std::vector<int32_t> perm(n_pairs);   // grouped position -> caller's pair index
+  {
+    std::vector<int64_t> cur(start.begin(), start.end() - 1);
+    for (int64_t i = 0; i < n_pairs; ++i) {
+      const int64_t pos = cur[slice_of[i]]++;
+      perm[pos] = (int32_t)i;
+      hp[2 * pos] = pairs[2 * i];
+      hp[2 * pos + 1] = pairs[2 * i + 1];
+    }
+  }
+  char* h_pts = pts_locked ? nullptr : h + off_b + pair_b + dist_b + dist2_b;
+  if (!pts_locked) std::memcpy(h_pts, points, pts_bytes);
+  const char* src_pts = pts_locked ? static_cast<const char*>(points) : h_pts;
+
+  // device (the context's staging buffer): [points | offsets | pairs | bbox | dist | dist2]
+  const size_t bbox_b = f32 ? 0 : align_up((size_t)n_curves * dim_class(dim) * 2 * 4, 256);
+  const size_t dev_bytes = align_up(pts_bytes, 256) + off_b + pair_b + bbox_b + dist_b + dist2_b;
+  cudaStream_t s = ctx->stream;
+  if (!ctx->copy_stream) {
+    if (cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaGetLastError();
+      ctx->copy_stream = nullptr;
+      return DFD_ERR_CUDA;
+    }
+    for (auto& e : ctx->slice_ev) {
+      if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        return DFD_ERR_CUDA;
+      }
+    }
+  }
+  if ((st = ensure_io(ctx, dev_bytes)) != DFD_OK) return st;
+  char* d = static_cast<char*>(ctx->io);
+  char* d_pts = d;
+  int64_t* d_off = reinterpret_cast<int64_t*>(d + align_up(pts_bytes, 256));
+  int32_t* d_pairs = reinterpret_cast<int32_t*>(reinterpret_cast<char*>(d_off) + off_b);
+  int* d_bbox = f32 ? nullptr : reinterpret_cast<int*>(reinterpret_cast<char*>(d_pairs) + pair_b);
+  char* d_dist = reinterpret_cast<char*>(d_pairs) + pair_b + bbox_b;
+  char* d_dist2 = d_dist + dist_b;
+
+  cudaMemcpyAsync(d_off, h, (size_t)(n_curves + 1) * 8, cudaMemcpyHostToDevice, s);
+  cudaMemcpyAsync(d_pairs, hp, (size_t)n_pairs * 8, cudaMemcpyHostToDevice, s);
+  // the copy stream starts after the previous work on s (which may still
+  // read the staging buffer's earlier contents)
+  cudaEventRecord(ctx->slice_ev[kMaxSlices], s);
+  cudaStreamWaitEvent(ctx->copy_stream, ctx->slice_ev[kMaxSlices], 0);
+  for (int k = 0; k < K; ++k) {
+    const size_t b0 = (size_t)(k == 0 ? 0 : offsets[bound[k]]) * dim * elem;
+    const size_t b1 = (size_t)(k + 1 == K ? n_pts : offsets[bound[k + 1]]) * dim * elem;
+    if (b1 > b0) cudaMemcpyAsync(d_pts + b0, src_pts + b0, b1 - b0, cudaMemcpyHostToDevice, ctx->copy_stream);
+    cudaEventRecord(ctx->slice_ev[k], ctx->copy_stream);
+  }
+  int last = 0;   // the last slice with pairs: it waits for every slice and covers all curves
+  for (int k = 0; k < K; ++k)
+    if (start[k + 1] > start[k]) last = k;
+  int64_t covered = 0;   // curves boxed / checked so far
+  for (int k = 0; k <= last && st == DFD_OK; ++k) {
+    const int64_t cnt = start[k + 1] - start[k];
+    if (cnt == 0) continue;
+    const bool final_launch = k == last;
+    for (int j = (final_launch ? 0 : k); j <= (final_launch ? K - 1 : k); ++j)
+      cudaStreamWaitEvent(s, ctx->slice_ev[j], 0);
+    const int64_t upto = final_launch ? n_curves : bound[k + 1];
+    st = range_run(ctx, dtype, dim, d_pts, d_off, upto, d_pairs + 2 * start[k], cnt,
+                   out_dist ? d_dist + start[k] * d1 : nullptr, out_dist2 ? d_dist2 + start[k] * d2 : nullptr, s,
+                   covered, d_bbox);
+    covered = upto;
+  }
+  if (st == DFD_OK) {
+    if (out_dist) cudaMemcpyAsync(h + off_b + pair_b, d_dist, (size_t)n_pairs * d1, cudaMemcpyDeviceToHost, s);
+    if (out_dist2)
+      cudaMemcpyAsync(h + off_b + pair_b + dist_b, d_dist2, (size_t)n_pairs * d2, cudaMemcpyDeviceToHost, s);
+  }
+  // s is ordered after every slice copy, whether or not a launch ran, so
+  // the synchronisation below covers the copy stream too
+  for (int k = 0; k < K; ++k) cudaStreamWaitEvent(s, ctx->slice_ev[k], 0);
+  if (cudaStreamSynchronize(s) != cudaSuccess) {
+    cudaGetLastError();
+    return DFD_ERR_CUDA;
+  }
+  if (st != DFD_OK) return st;
+  int err = 0;
+  cudaMemcpy(&err, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost);
+  if (err != 0) {
+    cudaMemset(ctx->d_err, 0, sizeof(int));
+    return (dfd_status)err;
+  }
+  const char* r1 = h + off_b + pair_b;
+  const char* r2 = r1 + dist_b;
+  for (int64_t pos = 0; pos < n_pairs; ++pos) {
+    const int64_t i = perm[pos];
+    if (out_dist) std::memcpy(static_cast<char*>(out_dist) + i * d1, r1 + pos * d1, d1);
+    if (out_dist2) std::memcpy(static_cast<char*>(out_dist2) + i * d2, r2 + pos * d2, d2);
+  }
+  return DFD_OK;
+}

@@ -507,14 +507,16 @@ __device__ __forceinline__ bool narrow_pair(const int* __restrict__ bbox, int dk
 }
 
 // Per-curve bounding boxes (one warp per curve) of int32 points, and the
-// coordinate range check (|c| <= lim) when `check` is set.
+// coordinate range check (|c| <= lim) when `check` is set, for curves
+// [first, n_curves).
 template <int DK>
 __global__ void curve_bbox_kernel(const int32_t* __restrict__ pts, const int64_t* __restrict__ offsets,
-                                  int64_t n_curves, int dim, int vec, int check, long long lim, int* bbox, int* err) {
+                                  int64_t first, int64_t n_curves, int dim, int vec, int check, long long lim,
+                                  int* bbox, int* err) {
   const int L = threadIdx.x & 31;
   const int64_t total = offsets[n_curves];
   bool bad = false;
-  for (int64_t c = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < n_curves;
+  for (int64_t c = first + (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5); c < n_curves;
        c += ((int64_t)gridDim.x * blockDim.x) >> 5) {
     const int64_t o = offsets[c], e = offsets[c + 1];
     int lo[DK], hi[DK];

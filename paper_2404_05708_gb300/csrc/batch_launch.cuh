@@ -10,14 +10,17 @@
 
 namespace dfd {
 
-// float32 input check over CSR points whose count is on the device
-// (offsets[n]); int32 batches are checked by the bounding-box kernel.
+// float32 input check over CSR points [begin[0], end[0]) (point indices on
+// the device: offsets[first], offsets[n]); int32 batches are checked by the
+// bounding-box kernel.
 template <class V>
-__global__ void check_points_kernel(const typename V::coord* x, const int64_t* count_points, int dim, int* err) {
+__global__ void check_points_kernel(const typename V::coord* x, const int64_t* begin, const int64_t* end, int dim,
+                                    int* err) {
   static_assert(std::is_same<V, F32>::value, "float32 only");
-  const int64_t count = count_points[0] * dim;
+  const int64_t count = end[0] * dim;
   bool bad = false;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x)
+  for (int64_t i = begin[0] * dim + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count;
+       i += (int64_t)gridDim.x * blockDim.x)
     bad |= !isfinite(x[i]);
   if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) raise_error(err, DFD_ERR_NONFINITE);
 }
@@ -41,15 +44,17 @@ inline long long int32_coord_limit(int dim) {
 }
 
 // Per-curve bounding boxes (and, with input checks on, the coordinate
-// range check) of an int32 CSR batch.
+// range check) of curves [first, n_curves) of an int32 CSR batch.
 template <int DK>
 void launch_curve_bbox(dfd_context* ctx, const void* points, const int64_t* offsets, int64_t n_curves, int dim,
-                       int* bbox, cudaStream_t s) {
-  const int64_t warps_needed = n_curves;
+                       int* bbox, cudaStream_t s, int64_t first = 0) {
+  const int64_t warps_needed = n_curves - first;
+  if (warps_needed < 1) return;
   const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((warps_needed + 7) / 8, 16 * (int64_t)ctx->num_sms));
-  batch::curve_bbox_kernel<DK><<<blocks, 256, 0, s>>>(static_cast<const int32_t*>(points), offsets, n_curves, dim,
-                                                      vector_loads_ok<DK>(points, dim), ctx->opt.check_inputs ? 1 : 0,
-                                                      int32_coord_limit(dim), bbox, ctx->d_err);
+  batch::curve_bbox_kernel<DK><<<blocks, 256, 0, s>>>(static_cast<const int32_t*>(points), offsets, first, n_curves,
+                                                      dim, vector_loads_ok<DK>(points, dim),
+                                                      ctx->opt.check_inputs ? 1 : 0, int32_coord_limit(dim), bbox,
+                                                      ctx->d_err);
 }
 
 template <class K>
@@ -65,9 +70,14 @@ int resident_blocks(const dfd_context* ctx, K kernel, int threads) {
 // Scratch, input checks (and int32 bounding boxes) and the device-built
 // LPT work list shared by the batch and decider kernels; `blocks` persistent
 // CTAs of 256 threads will run the work list.
+// With `bbox_ext` (int32 batches) the per-curve boxes live in the caller's
+// buffer and only curves [first_curve, n_curves) are boxed and checked
+// (float32: only their points are checked): a batch run in slices of
+// curves, each slice covering the curves no earlier slice covered.
 template <class V, int DK>
 dfd_status batch_prepare(dfd_context* ctx, int dim, const void* points, const int64_t* offsets, int64_t n_curves,
-                         const int32_t* pairs, int64_t n_pairs, cudaStream_t s, int blocks, batch::BatchArgs* ba) {
+                         const int32_t* pairs, int64_t n_pairs, cudaStream_t s, int blocks, batch::BatchArgs* ba,
+                         int64_t first_curve = 0, int* bbox_ext = nullptr) {
   using T = typename V::value;
   constexpr int THREADS = 256;
   const size_t warps = (size_t)blocks * (THREADS / 32);
@@ -78,19 +88,19 @@ dfd_status batch_prepare(dfd_context* ctx, int dim, const void* points, const in
   const size_t off_bucket = align_up(off_cursor + batch::NBUCKET * 4, 256);
   const size_t off_work = align_up(off_bucket + (size_t)n_pairs * 2, 256);
   const size_t off_bbox = align_up(off_work + (size_t)n_pairs * 4, 256);
-  const size_t off_buf = align_up(off_bbox + (kInt ? (size_t)n_curves * DK * 2 * 4 : 0), 256);
+  const size_t off_buf = align_up(off_bbox + (kInt && !bbox_ext ? (size_t)n_curves * DK * 2 * 4 : 0), 256);
   const size_t total = off_buf + warps * batch::BUF_COLS * sizeof(T);
   dfd_status st = ensure_scratch(ctx, total);
   if (st != DFD_OK) return st;
   char* base = static_cast<char*>(ctx->scratch);
   cudaError_t e = cudaMemsetAsync(base, 0, off_bucket, s);
   if (e != cudaSuccess) return cuda_status(e);
-  int* bbox = kInt ? reinterpret_cast<int*>(base + off_bbox) : nullptr;
+  int* bbox = kInt ? (bbox_ext ? bbox_ext : reinterpret_cast<int*>(base + off_bbox)) : nullptr;
   if constexpr (kInt) {
-    launch_curve_bbox<DK>(ctx, points, offsets, n_curves, dim, bbox, s);
-  } else if (ctx->opt.check_inputs) {
+    launch_curve_bbox<DK>(ctx, points, offsets, n_curves, dim, bbox, s, bbox_ext ? first_curve : 0);
+  } else if (ctx->opt.check_inputs && n_curves > first_curve) {
     check_points_kernel<V><<<std::min(4 * ctx->num_sms, 1024), 256, 0, s>>>(
-        static_cast<const typename V::coord*>(points), offsets + n_curves, dim, ctx->d_err);
+        static_cast<const typename V::coord*>(points), offsets + first_curve, offsets + n_curves, dim, ctx->d_err);
   }
   batch::PlanArgs pa;
   pa.offsets = offsets;
@@ -126,11 +136,13 @@ dfd_status batch_prepare(dfd_context* ctx, int dim, const void* points, const in
 }
 
 template <class V, int DK>
-dfd_status batch_launch(dfd_context* ctx, int dim, const void* points, const int64_t* offsets, int64_t n_curves,
-                        const int32_t* pairs, int64_t n_pairs, void* out_dist, void* out_dist2, cudaStream_t s) {
+dfd_status batch_launch_range(dfd_context* ctx, int dim, const void* points, const int64_t* offsets,
+                              int64_t n_curves, const int32_t* pairs, int64_t n_pairs, void* out_dist,
+                              void* out_dist2, cudaStream_t s, int64_t first_curve, int* bbox_ext) {
   const int blocks = resident_blocks(ctx, batch::batch_kernel<V, DK>, 256);
   batch::BatchArgs ba;
-  dfd_status st = batch_prepare<V, DK>(ctx, dim, points, offsets, n_curves, pairs, n_pairs, s, blocks, &ba);
+  dfd_status st = batch_prepare<V, DK>(ctx, dim, points, offsets, n_curves, pairs, n_pairs, s, blocks, &ba,
+                                       first_curve, bbox_ext);
   if (st != DFD_OK) return st;
   ba.out_dist = out_dist;
   ba.out_dist2 = out_dist2;
@@ -138,6 +150,13 @@ dfd_status batch_launch(dfd_context* ctx, int dim, const void* points, const int
   batch::batch_kernel<V, DK><<<blocks, 256, 0, s>>>(ba);
   timing_end(ctx, s);
   return cuda_status(cudaGetLastError());
+}
+
+template <class V, int DK>
+dfd_status batch_launch(dfd_context* ctx, int dim, const void* points, const int64_t* offsets, int64_t n_curves,
+                        const int32_t* pairs, int64_t n_pairs, void* out_dist, void* out_dist2, cudaStream_t s) {
+  return batch_launch_range<V, DK>(ctx, dim, points, offsets, n_curves, pairs, n_pairs, out_dist, out_dist2, s, 0,
+                                   nullptr);
 }
 
 template <class V, int DK>
@@ -181,7 +200,7 @@ dfd_status matrix_launch(dfd_context* ctx, int dim, const void* points, const in
     launch_curve_bbox<DK>(ctx, points, offsets, n_curves, dim, bbox, s);
   } else if (ctx->opt.check_inputs) {
     check_points_kernel<V><<<std::min(4 * ctx->num_sms, 1024), 256, 0, s>>>(
-        static_cast<const typename V::coord*>(points), offsets + n_curves, dim, ctx->d_err);
+        static_cast<const typename V::coord*>(points), offsets, offsets + n_curves, dim, ctx->d_err);
   }
   batch::MatrixArgs ma;
   ma.rowbuf = base + off_buf;
@@ -208,6 +227,9 @@ dfd_status matrix_launch(dfd_context* ctx, int dim, const void* points, const in
 #define DFD_BATCH_INSTANTIATE(V, DK)                                                                              \
   template dfd_status dfd::batch_launch<dfd::V, DK>(dfd_context*, int, const void*, const int64_t*, int64_t,       \
                                                       const int32_t*, int64_t, void*, void*, cudaStream_t);        \
+  template dfd_status dfd::batch_launch_range<dfd::V, DK>(dfd_context*, int, const void*, const int64_t*, int64_t, \
+                                                            const int32_t*, int64_t, void*, void*, cudaStream_t,      \
+                                                            int64_t, int*);                                           \
   template dfd_status dfd::decide_launch<dfd::V, DK>(dfd_context*, int, const void*, const int64_t*, int64_t,      \
                                                        const int32_t*, int64_t, const void*, double, void*, int32_t*, \
                                                        unsigned long long*, cudaStream_t);                            \

@@ -82,6 +82,28 @@ dfd_status ensure_scratch(dfd_context* ctx, size_t bytes) {
   return DFD_OK;
 }
 
+// Device buffer of the host-buffer entry points (inputs and results staged
+// on the device); grow-only, so repeated calls map no new memory.  Those
+// calls are synchronous, so nothing still uses the old buffer on growth.
+dfd_status ensure_io(dfd_context* ctx, size_t bytes) {
+  if (bytes <= ctx->io_bytes) return DFD_OK;
+  if (ctx->io) {
+    cudaStreamSynchronize(ctx->stream);
+    cudaFree(ctx->io);
+  }
+  ctx->io = nullptr;
+  ctx->io_bytes = 0;
+  const size_t want = std::max(bytes, ctx->io_bytes + ctx->io_bytes / 2);
+  void* p = nullptr;
+  if (cudaMalloc(&p, want) != cudaSuccess) {
+    cudaGetLastError();
+    return DFD_ERR_OOM;
+  }
+  ctx->io = p;
+  ctx->io_bytes = want;
+  return DFD_OK;
+}
+
 dfd_status ensure_pinned(dfd_context* ctx, size_t bytes) {
   if (bytes <= ctx->pinned_bytes) return DFD_OK;
   if (ctx->pinned) {
@@ -284,6 +306,19 @@ __global__ void bounded_wait_kernel(const unsigned long long* flag, int* err, un
 
 }  // namespace dfd
 
+dfd_status dfd::set_device(dfd_context* ctx) { return cuda_status(cudaSetDevice(ctx->device)); }
+
+dfd_status dfd::check_batch_args(dfd_context* ctx, dfd_dtype dtype, int dim, const void* points, const int64_t* offsets,
+                            int64_t n_curves, const void* out_dist, const void* out_dist2) {
+  if (!ctx) return DFD_ERR_INVALID_ARG;
+  if (dtype != DFD_F32 && dtype != DFD_I32) return DFD_ERR_INVALID_ARG;
+  if (dim < 1 || !points || !offsets || n_curves < 1) return DFD_ERR_INVALID_ARG;
+  if (!out_dist && !out_dist2) return DFD_ERR_INVALID_ARG;
+  if (dim > 16) return DFD_ERR_UNSUPPORTED;
+  if (n_curves > INT32_MAX) return DFD_ERR_UNSUPPORTED;
+  return DFD_OK;
+}
+
 using namespace dfd;
 
 // ======================================================================= C ABI
@@ -300,9 +335,6 @@ dfd_status check_pair_args(dfd_context* ctx, dfd_dtype dtype, int dim, const voi
   return DFD_OK;
 }
 
-dfd_status set_device(dfd_context* ctx) {
-  return cuda_status(cudaSetDevice(ctx->device));
-}
 
 dfd_status pre_checks(dfd_context* ctx, dfd_dtype dtype, int dim, const void* p, int64_t n, const void* q, int64_t m,
                       cudaStream_t s) {
@@ -393,9 +425,13 @@ dfd_status dfd_context_destroy(dfd_context* ctx) {
   cudaSetDevice(ctx->device);
   cudaDeviceSynchronize();
   if (ctx->stream) cudaStreamDestroy(ctx->stream);
+  if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
+  for (cudaEvent_t e : ctx->slice_ev)
+    if (e) cudaEventDestroy(e);
   if (ctx->ev0) cudaEventDestroy(ctx->ev0);
   if (ctx->ev1) cudaEventDestroy(ctx->ev1);
   if (ctx->scratch) cudaFree(ctx->scratch);
+  if (ctx->io) cudaFree(ctx->io);
   if (ctx->pinned) cudaFreeHost(ctx->pinned);
   if (ctx->d_err) cudaFree(ctx->d_err);
   cudaGetLastError();
@@ -609,21 +645,27 @@ dfd_status dfd_pair_host(dfd_context* ctx, dfd_dtype dtype, int dim, const void*
   if ((st = set_device(ctx)) != DFD_OK) return st;
   // Device layout of the staged inputs and results: [p | q | dist | dist2],
   // carved from the pinned host area and from a second device buffer that
-  // sits after the wavefront's scratch (which it grows first).
+  // sits after the wavefront's scratch (which it grows first).  Inputs the
+  // caller already holds in page-locked memory are copied to the device
+  // directly; pageable ones go through the pinned area first.
   const size_t pb = align_up((size_t)n * dim * 4, 256), qb = align_up((size_t)m * dim * 4, 256);
   const size_t host_bytes = pb + qb + 256;
   if ((st = ensure_pinned(ctx, host_bytes)) != DFD_OK) return st;
   char* h = static_cast<char*>(ctx->pinned);
-  std::memcpy(h, p, (size_t)n * dim * 4);
-  std::memcpy(h + pb, q, (size_t)m * dim * 4);
-  void* dio = nullptr;
-  if (cudaMallocAsync(&dio, host_bytes, ctx->stream) != cudaSuccess) {
+  auto page_locked = [](const void* x) {
+    cudaPointerAttributes at;
+    const bool yes = cudaPointerGetAttributes(&at, x) == cudaSuccess && at.type == cudaMemoryTypeHost;
     cudaGetLastError();
-    return DFD_ERR_OOM;
-  }
-  char* d = static_cast<char*>(dio);
+    return yes;
+  };
+  const bool p_locked = page_locked(p), q_locked = page_locked(q);
+  if (!p_locked) std::memcpy(h, p, (size_t)n * dim * 4);
+  if (!q_locked) std::memcpy(h + pb, q, (size_t)m * dim * 4);
+  if ((st = ensure_io(ctx, host_bytes)) != DFD_OK) return st;
+  char* d = static_cast<char*>(ctx->io);
   cudaStream_t s = ctx->stream;
-  cudaMemcpyAsync(d, h, pb + qb, cudaMemcpyHostToDevice, s);
+  cudaMemcpyAsync(d, p_locked ? p : h, (size_t)n * dim * 4, cudaMemcpyHostToDevice, s);
+  cudaMemcpyAsync(d + pb, q_locked ? q : h + pb, (size_t)m * dim * 4, cudaMemcpyHostToDevice, s);
   WaveShape sh;
   wave_plan(ctx, dtype, dim, n, m, &sh);
   if ((st = pre_checks(ctx, dtype, dim, d, n, d + pb, m, s)) == DFD_OK) {
@@ -633,7 +675,6 @@ dfd_status dfd_pair_host(dfd_context* ctx, dfd_dtype dtype, int dim, const void*
       cudaMemcpyAsync(h + pb + qb, dres, 16, cudaMemcpyDeviceToHost, s);
     }
   }
-  cudaFreeAsync(dio, s);
   if (cudaStreamSynchronize(s) != cudaSuccess) {
     cudaGetLastError();
     return DFD_ERR_CUDA;
@@ -667,16 +708,6 @@ struct dfd_graph {
 
 namespace {
 
-dfd_status check_batch_args(dfd_context* ctx, dfd_dtype dtype, int dim, const void* points, const int64_t* offsets,
-                            int64_t n_curves, const void* out_dist, const void* out_dist2) {
-  if (!ctx) return DFD_ERR_INVALID_ARG;
-  if (dtype != DFD_F32 && dtype != DFD_I32) return DFD_ERR_INVALID_ARG;
-  if (dim < 1 || !points || !offsets || n_curves < 1) return DFD_ERR_INVALID_ARG;
-  if (!out_dist && !out_dist2) return DFD_ERR_INVALID_ARG;
-  if (dim > 16) return DFD_ERR_UNSUPPORTED;
-  if (n_curves > INT32_MAX) return DFD_ERR_UNSUPPORTED;
-  return DFD_OK;
-}
 
 // Run `fn` once normally (sizes the context scratch), then capture it into a
 // graph that owns a private copy of the scratch, so later calls that grow or

@@ -23,6 +23,10 @@ inline uint64_t tune_key(int dtype, int dk, int64_t n, int64_t m) {
 }
 }  // namespace dfd
 
+namespace dfd {
+constexpr int kMaxSlices = 8;   // dfd_batch_host: copy slices of the points
+}
+
 struct dfd_context {
   int device = 0;
   int num_sms = 0;
@@ -33,11 +37,15 @@ struct dfd_context {
   size_t scratch_bytes = 0;
   void* pinned = nullptr;             // grow-only pinned host staging
   size_t pinned_bytes = 0;
+  void* io = nullptr;                 // grow-only device staging of the host-buffer entry points
+  size_t io_bytes = 0;
   cudaStream_t stream = nullptr;      // internal stream (host-buffer entry points)
   bool timing = false;                // record events around the main kernel
   bool timed = false;                 // ev0/ev1 hold a recorded pair
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   std::map<uint64_t, dfd::WaveShape> tuned;   // autotuned wavefront shapes
+  cudaStream_t copy_stream = nullptr;         // dfd_batch_host: point slices (created on first use)
+  cudaEvent_t slice_ev[dfd::kMaxSlices + 1] = {};   // one per slice, and one for the allocation
 };
 
 namespace dfd {
@@ -52,6 +60,7 @@ inline dfd_status cuda_status(cudaError_t e) {
 // Grow the context scratch to at least `bytes`; 256-byte aligned.
 dfd_status ensure_scratch(dfd_context* ctx, size_t bytes);
 dfd_status ensure_pinned(dfd_context* ctx, size_t bytes);
+dfd_status ensure_io(dfd_context* ctx, size_t bytes);
 
 // Events around the main kernel of a call (measurement hooks).
 inline void timing_begin(dfd_context* ctx, cudaStream_t s) {
@@ -81,6 +90,12 @@ inline int dim_class(int dim) {
   if (dim <= 16) return 16;
   return 0;
 }
+
+// Make the context's device current.
+dfd_status set_device(dfd_context* ctx);
+// Host-side argument checks shared by the batch entry points.
+dfd_status check_batch_args(dfd_context* ctx, dfd_dtype dtype, int dim, const void* points, const int64_t* offsets,
+                            int64_t n_curves, const void* out_dist, const void* out_dist2);
 
 // Input validation kernels: set DFD_ERR_NONFINITE / DFD_ERR_RANGE in *err.
 dfd_status launch_check_inputs(dfd_dtype dtype, int dim, const void* x, int64_t count, int* err,

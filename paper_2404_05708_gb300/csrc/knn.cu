@@ -298,7 +298,7 @@ dfd_status knn_launch(dfd_context* ctx, int dim, const float* query, int n, cons
   if (ctx->opt.check_inputs) {
     st = launch_check_inputs(DFD_F32, dim, query, (int64_t)n * dim, ctx->d_err, s);
     if (st != DFD_OK) return st;
-    check_points_kernel<F32><<<std::min(4 * ctx->num_sms, 1024), 256, 0, s>>>(points, offsets + n_curves, dim,
+    check_points_kernel<F32><<<std::min(4 * ctx->num_sms, 1024), 256, 0, s>>>(points, offsets, offsets + n_curves, dim,
                                                                              ctx->d_err);
   }
   KnnArgs a;

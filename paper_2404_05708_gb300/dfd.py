@@ -80,6 +80,7 @@ _SIGS = {
     "dfd_debug_bounded_wait": [_VP, ctypes.c_double],
     "dfd_pair_noalloc": [_INT, _INT, _INT, _VP, _I64, _VP, _I64, _VP, _VP, _VP],
     "dfd_batch": [_VP, _INT, _INT, _VP, _VP, _I64, _VP, _I64, _VP, _VP, _VP],
+    "dfd_batch_host": [_VP, _INT, _INT, _VP, _VP, _I64, _VP, _I64, _VP, _VP],
     "dfd_matrix": [_VP, _INT, _INT, _VP, _VP, _I64, _VP, _VP, _VP],
     "dfd_batch_decide": [_VP, _INT, _INT, _VP, _VP, _I64, _VP, _I64, _VP, ctypes.c_double, _VP, _VP, _VP, _VP],
     "dfd_mc_pair": [_VP, _INT, _VP, _I64, _VP, _I64, _VP, _VP, ctypes.c_float, ctypes.c_float, _I64, _VP, _VP, _VP],
@@ -178,6 +179,11 @@ def dfd_pair_reference(ctx, dtype, dim, p, n, q, m, out_dist, out_dist2, stream)
 
 def dfd_pair_host(ctx, dtype, dim, p, n, q, m, out_dist, out_dist2) -> int:
     return load_library().dfd_pair_host(ctx, dtype, dim, p, n, q, m, out_dist, out_dist2)
+
+
+def dfd_batch_host(ctx, dtype, dim, points, offsets, n_curves, pairs, n_pairs, out_dist, out_dist2) -> int:
+    return load_library().dfd_batch_host(ctx, dtype, dim, points, offsets, n_curves, pairs, n_pairs, out_dist,
+                                         out_dist2)
 
 
 def dfd_pair_noalloc(device, dtype, dim, p, n, q, m, out_dist, out_dist2, stream) -> int:
@@ -541,6 +547,32 @@ class Context:
         s = stream if stream is not None else torch.cuda.current_stream(self.device).cuda_stream
         _check(dfd_batch(*args, s), "dfd_batch")
         return out_dist, out_dist2
+
+    def batch_host(self, points, offsets, pairs, out_dist=None, out_dist2=None):
+        """dfd_batch on host (numpy) arrays, synchronous; returns (dist, dist2).
+        Page-locked points (e.g. a pinned tensor's numpy view) are copied to the
+        device directly, slice by slice, overlapping the computation."""
+        import numpy as np
+        points = np.ascontiguousarray(points)
+        if points.ndim == 1:
+            points = points[:, None]
+        offsets = np.ascontiguousarray(offsets, dtype=np.int64)
+        pairs = np.ascontiguousarray(pairs, dtype=np.int32)
+        n_pairs = pairs.size // 2
+        if points.dtype == np.float32:
+            dt = DFD_F32
+            d1 = out_dist if out_dist is not None else np.zeros(n_pairs, np.float32)
+            d2 = out_dist2 if out_dist2 is not None else np.zeros(n_pairs, np.float32)
+        elif points.dtype == np.int32:
+            dt = DFD_I32
+            d1 = out_dist if out_dist is not None else np.zeros(n_pairs, np.float64)
+            d2 = out_dist2 if out_dist2 is not None else np.zeros(n_pairs, np.int64)
+        else:
+            raise TypeError("curves must be float32 or int32")
+        _check(dfd_batch_host(self.handle, dt, points.shape[1], points.ctypes.data, offsets.ctypes.data,
+                              offsets.size - 1, pairs.ctypes.data, n_pairs, d1.ctypes.data, d2.ctypes.data),
+               "dfd_batch_host")
+        return d1, d2
 
     def decide(self, points, offsets, pairs, eps2, out_dist2=None, out_within=None, stream=None):
         """Threshold decision delta^2 <= eps2 per pair with early abandon.  eps2 is a

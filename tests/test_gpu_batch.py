@@ -153,6 +153,47 @@ def test_batch_ragged_int_full_size(dctx):
     assert np.array_equal(d, np.sqrt(ref.astype(np.float64)))
 
 
+def test_batch_host_equals_device_batch(dctx):
+    """dfd_batch_host (points copied in slices, pairs run per slice) equals
+    dfd_batch bit for bit, from page-locked and from pageable points."""
+    b = workloads.ragged_int_batch()   # 277 MB of points: 8 copy slices
+    d_dev, d2_dev = run_batch(dctx, b)
+    pinned = torch.from_numpy(b.points).pin_memory().numpy()
+    for pts in (pinned, b.points):
+        d, d2 = dctx.batch_host(pts, b.offsets, b.pairs)
+        assert np.array_equal(d2, d2_dev), np.nonzero(d2 != d2_dev)[0][:10]
+        assert np.array_equal(d, d_dev)
+
+
+def test_batch_host_slices_without_pairs_and_checks():
+    """Pairs that reference only late curves (early copy slices run no
+    launch) still see every curve boxed and checked: results equal
+    dfd_batch's, and a NaN in a curve no pair references is rejected as by
+    dfd_batch."""
+    from paper_2404_05708_gb300 import dfd
+    ctx = dfd.Context(0)
+    rng = np.random.default_rng(21)
+    lens = rng.integers(200, 700, size=30000)
+    off = np.concatenate([[0], np.cumsum(lens)]).astype(np.int64)
+    pts = np.cumsum(rng.normal(0, 1, size=(int(off[-1]), 2)), axis=0).astype(np.float32)   # ~108 MB
+    hi = np.arange(27000, 30000)
+    pairs = np.stack([rng.choice(hi, 600), rng.choice(hi, 600)], 1).astype(np.int32)
+    pairs = np.concatenate([pairs, [[0, 29999], [5, 12]]]).astype(np.int32)
+    b = workloads.Batch(points=pts, offsets=off, pairs=pairs)
+    d_dev, d2_dev = run_batch(ctx, b)
+    d, d2 = ctx.batch_host(pts, off, pairs)
+    assert np.array_equal(d2, d2_dev) and np.array_equal(d, d_dev)
+    mirror, _ = oracle.batch(pts, off, pairs[-2:], mirror=True)
+    assert np.array_equal(d2[-2:], mirror)
+    bad = pts.copy()
+    bad[off[100] + 3, 1] = np.nan   # curve 100: in no pair
+    with pytest.raises(dfd.DFDError):
+        ctx.batch_host(bad, off, pairs[:600])
+    with pytest.raises(dfd.DFDError):
+        ctx.batch_host(pts, off, np.array([[0, 30000]], np.int32))   # id out of range: host check
+    ctx.close()
+
+
 def test_batch_graph_replay_updates_with_buffers(dctx):
     b = workloads.ragged_int_batch(n_pairs=3000, seed=41)
     pts, off, pr = dev(b.points), dev(b.offsets), dev(b.pairs)
