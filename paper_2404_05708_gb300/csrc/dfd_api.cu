@@ -167,10 +167,13 @@ static bool shape_ok(const dfd_context* ctx, dfd_dtype dtype, int dim, int R, in
 dfd_status wave_plan(const dfd_context* ctx, dfd_dtype dtype, int dim, int64_t n, int64_t m, WaveShape* shape) {
   // Cost model: every CTA runs one band at a time; a band of H = 32*W*R rows
   // sweeps m columns plus its internal skew; bands start one inter-band lag
-  // apart (W warps, each trailing the one above by 32*K + G columns); an SM
-  // reaches its issue limit once W*R >= RSAT rows (enough independent cells
-  // to hide the min/max latency; fewer with skewed float32 lanes, whose
-  // step chain is two cells).  Minimise the modelled completion time.
+  // apart (W warps, each trailing the one above by 32*K + G columns), and a
+  // pair of two bands or more runs as two fronts, each its own chain of
+  // bands.  float32: a step costs the cycles measured for one band of each R
+  // alone (in place, one compute warp per SM sub-partition: 73, 69, 74, 117
+  // for R = 2, 4, 6, 8), times the compute warps sharing a sub-partition;
+  // int32: an SM reaches its issue limit once W*R >= 48 rows.  Minimise the
+  // modelled completion time.
   auto hit = ctx->tuned.find(tune_key(dtype, dim_class(dim), n, m));
   if (hit != ctx->tuned.end()) {
     *shape = hit->second;
@@ -191,9 +194,16 @@ dfd_status wave_plan(const dfd_context* ctx, dfd_dtype dtype, int dim, int64_t n
       const double wlag = 32.0 * K + 32.0;
       const double lag = wlag * W + 96.0;
       const double conc = std::min(B, (double)P);
-      const double cols = waves * ((double)m + wlag * W) + (conc - 1.0) * lag;
-      const double sat = std::min(1.0, W * R / RSAT);
-      const double t = cols * H / sat;
+      const double chain = B >= 2 ? std::ceil(conc / 2.0) - 1.0 : 0.0;   // bands of one front started in turn
+      const double cols = waves * ((double)m + wlag * W) + chain * lag;
+      double t;
+      if (dtype == DFD_F32) {
+        const double step = R == 2 ? 73.0 : R == 4 ? 69.0 : R == 6 ? 74.0 : 117.0;
+        t = cols * step * std::ceil(W / 4.0);
+      } else {
+        const double sat = std::min(1.0, W * R / RSAT);
+        t = cols * H / sat;
+      }
       if (t < best * 0.999) {
         best = t;
         bs.R = R;
