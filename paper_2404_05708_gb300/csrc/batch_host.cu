@@ -38,9 +38,9 @@ DFD_RANGE_EXTERN(I32, 16)
 namespace {
 
 // Points per copy slice (about).  Every slice's launch ends on the tail of
-// its longest pairs (a 512 x 512 pair is ~0.2 ms on one warp), so slices are
-// few and large: on the 65,536-pair int32 batch (277 MB) 8 slices of 32 MB
-// ran at 1.39 Tcell/s end to end, 3 of 128 MB at 1.48.
+// its longest pairs, and the first slice's copy is not overlapped: on the
+// 65,536-pair int32 batch (277 MB) 3 slices of 128 MB ran at 1.75 Tcell/s
+// end to end, 6 of 48 MB at 1.67 (one launch after one copy: 1.52).
 constexpr size_t kSliceBytes = (size_t)128 << 20;
 
 dfd_status range_run(dfd_context* ctx, dfd_dtype dtype, int dim, const void* points, const int64_t* offsets,
@@ -87,12 +87,10 @@ extern "C" dfd_status dfd_batch_host(dfd_context* ctx, dfd_dtype dtype, int dim,
   if (st != DFD_OK) return st;
   if (!pairs || n_pairs < 0 || n_pairs > INT32_MAX) return DFD_ERR_INVALID_ARG;
   if (n_pairs == 0) return DFD_OK;
-  // host-side checks the slicing relies on: monotone offsets, ids in range
+  // host-side check the slicing relies on: monotone offsets
   if (offsets[0] < 0) return DFD_ERR_INVALID_ARG;
   for (int64_t c = 0; c < n_curves; ++c)
     if (offsets[c + 1] < offsets[c]) return DFD_ERR_INVALID_ARG;
-  for (int64_t k = 0; k < 2 * n_pairs; ++k)
-    if (pairs[k] < 0 || pairs[k] >= n_curves) return DFD_ERR_INVALID_ARG;
   if ((st = set_device(ctx)) != DFD_OK) return st;
 
   const int64_t n_pts = offsets[n_curves];
@@ -110,16 +108,6 @@ extern "C" dfd_status dfd_batch_host(dfd_context* ctx, dfd_dtype dtype, int dim,
     bound[k] = std::lower_bound(offsets, offsets + n_curves + 1, target) - offsets;
     bound[k] = std::min(std::max(bound[k], bound[k - 1]), n_curves);
   }
-  // group the pairs by the slice of their later curve (stable counting sort)
-  std::vector<int> slice_of(n_pairs);
-  std::vector<int64_t> start(K + 1, 0);
-  for (int64_t i = 0; i < n_pairs; ++i) {
-    const int64_t c = std::max(pairs[2 * i], pairs[2 * i + 1]);
-    const int k = (int)(std::upper_bound(bound.begin() + 1, bound.end(), c) - (bound.begin() + 1));
-    slice_of[i] = std::min(k, K - 1);
-    ++start[slice_of[i] + 1];
-  }
-  for (int k = 0; k < K; ++k) start[k + 1] += start[k];
 
   // pinned staging: [offsets | pairs (grouped) | dist | dist2 | points if pageable]
   const bool pts_locked = page_locked(points);
@@ -129,18 +117,6 @@ extern "C" dfd_status dfd_batch_host(dfd_context* ctx, dfd_dtype dtype, int dim,
   const size_t host_bytes = off_b + pair_b + dist_b + dist2_b + (pts_locked ? 0 : align_up(pts_bytes, 256));
   if ((st = ensure_pinned(ctx, host_bytes)) != DFD_OK) return st;
   char* h = static_cast<char*>(ctx->pinned);
-  std::memcpy(h, offsets, (size_t)(n_curves + 1) * 8);
-  int32_t* hp = reinterpret_cast<int32_t*>(h + off_b);
-  std::vector<int32_t> perm(n_pairs);   // grouped position -> caller's pair index
-  {
-    std::vector<int64_t> cur(start.begin(), start.end() - 1);
-    for (int64_t i = 0; i < n_pairs; ++i) {
-      const int64_t pos = cur[slice_of[i]]++;
-      perm[pos] = (int32_t)i;
-      hp[2 * pos] = pairs[2 * i];
-      hp[2 * pos + 1] = pairs[2 * i + 1];
-    }
-  }
   char* h_pts = pts_locked ? nullptr : h + off_b + pair_b + dist_b + dist2_b;
   if (!pts_locked) std::memcpy(h_pts, points, pts_bytes);
   const char* src_pts = pts_locked ? static_cast<const char*>(points) : h_pts;
@@ -148,6 +124,14 @@ extern "C" dfd_status dfd_batch_host(dfd_context* ctx, dfd_dtype dtype, int dim,
   // device (the context's staging buffer): [points | offsets | pairs | bbox | dist | dist2]
   const size_t bbox_b = f32 ? 0 : align_up((size_t)n_curves * dim_class(dim) * 2 * 4, 256);
   const size_t dev_bytes = align_up(pts_bytes, 256) + off_b + pair_b + bbox_b + dist_b + dist2_b;
+  if ((st = ensure_io(ctx, dev_bytes)) != DFD_OK) return st;
+  char* d = static_cast<char*>(ctx->io);
+  char* d_pts = d;
+  int64_t* d_off = reinterpret_cast<int64_t*>(d + align_up(pts_bytes, 256));
+  int32_t* d_pairs = reinterpret_cast<int32_t*>(reinterpret_cast<char*>(d_off) + off_b);
+  int* d_bbox = f32 ? nullptr : reinterpret_cast<int*>(reinterpret_cast<char*>(d_pairs) + pair_b);
+  char* d_dist = reinterpret_cast<char*>(d_pairs) + pair_b + bbox_b;
+  char* d_dist2 = d_dist + dist_b;
   cudaStream_t s = ctx->stream;
   if (!ctx->copy_stream) {
     if (cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking) != cudaSuccess) {
@@ -162,27 +146,68 @@ extern "C" dfd_status dfd_batch_host(dfd_context* ctx, dfd_dtype dtype, int dim,
       }
     }
   }
-  if ((st = ensure_io(ctx, dev_bytes)) != DFD_OK) return st;
-  char* d = static_cast<char*>(ctx->io);
-  char* d_pts = d;
-  int64_t* d_off = reinterpret_cast<int64_t*>(d + align_up(pts_bytes, 256));
-  int32_t* d_pairs = reinterpret_cast<int32_t*>(reinterpret_cast<char*>(d_off) + off_b);
-  int* d_bbox = f32 ? nullptr : reinterpret_cast<int*>(reinterpret_cast<char*>(d_pairs) + pair_b);
-  char* d_dist = reinterpret_cast<char*>(d_pairs) + pair_b + bbox_b;
-  char* d_dist2 = d_dist + dist_b;
 
-  cudaMemcpyAsync(d_off, h, (size_t)(n_curves + 1) * 8, cudaMemcpyHostToDevice, s);
-  cudaMemcpyAsync(d_pairs, hp, (size_t)n_pairs * 8, cudaMemcpyHostToDevice, s);
-  // the copy stream starts after the previous work on s (which may still
-  // read the staging buffer's earlier contents)
-  cudaEventRecord(ctx->slice_ev[kMaxSlices], s);
-  cudaStreamWaitEvent(ctx->copy_stream, ctx->slice_ev[kMaxSlices], 0);
-  for (int k = 0; k < K; ++k) {
+  // Every host-to-device copy goes through the copy stream, in the order
+  // the launches need it (copies in one direction are served in order):
+  // slice 0, then the offsets and the grouped pairs, then the other slices.
+  cudaStream_t cs = ctx->copy_stream;
+  auto copy_slice = [&](int k) {
     const size_t b0 = (size_t)(k == 0 ? 0 : offsets[bound[k]]) * dim * elem;
     const size_t b1 = (size_t)(k + 1 == K ? n_pts : offsets[bound[k + 1]]) * dim * elem;
-    if (b1 > b0) cudaMemcpyAsync(d_pts + b0, src_pts + b0, b1 - b0, cudaMemcpyHostToDevice, ctx->copy_stream);
-    cudaEventRecord(ctx->slice_ev[k], ctx->copy_stream);
+    if (b1 > b0) cudaMemcpyAsync(d_pts + b0, src_pts + b0, b1 - b0, cudaMemcpyHostToDevice, cs);
+    cudaEventRecord(ctx->slice_ev[k], cs);
+  };
+  // 1. slice 0 first (after the previous work on s, which may still read
+  // the staging buffer's earlier contents)
+  cudaEventRecord(ctx->slice_ev[kMaxSlices], s);
+  cudaStreamWaitEvent(cs, ctx->slice_ev[kMaxSlices], 0);
+  copy_slice(0);
+
+  // 2. on the host meanwhile: check the ids and group the pairs by the slice
+  // of their later curve (stable counting sort)
+  std::vector<int> slice_of(n_pairs);
+  std::vector<int64_t> start(K + 1, 0);
+  bool bad_id = false;
+  for (int64_t i = 0; i < n_pairs; ++i) {
+    const int32_t ia = pairs[2 * i], ib = pairs[2 * i + 1];
+    if (ia < 0 || ib < 0 || ia >= n_curves || ib >= n_curves) {
+      bad_id = true;
+      break;
+    }
+    const int64_t c = std::max(ia, ib);
+    int k = 0;
+    while (k + 1 < K && c >= bound[k + 1]) ++k;
+    slice_of[i] = k;
+    ++start[k + 1];
   }
+  if (bad_id) {
+    // the copy reads the caller's buffer: let it finish before returning
+    cudaStreamSynchronize(cs);
+    cudaGetLastError();
+    return DFD_ERR_INVALID_ARG;
+  }
+  for (int k = 0; k < K; ++k) start[k + 1] += start[k];
+  std::memcpy(h, offsets, (size_t)(n_curves + 1) * 8);
+  int32_t* hp = reinterpret_cast<int32_t*>(h + off_b);
+  std::vector<int32_t> perm(n_pairs);   // grouped position -> caller's pair index
+  {
+    std::vector<int64_t> cur(start.begin(), start.end() - 1);
+    for (int64_t i = 0; i < n_pairs; ++i) {
+      const int64_t pos = cur[slice_of[i]]++;
+      perm[pos] = (int32_t)i;
+      hp[2 * pos] = pairs[2 * i];
+      hp[2 * pos + 1] = pairs[2 * i + 1];
+    }
+  }
+
+  // 3. the offsets and pairs, then the other slices; each slice's pairs run
+  // as soon as the slice has landed (slice k's event follows the offsets
+  // and pairs for k >= 1; slice 0's launch also waits for them)
+  cudaMemcpyAsync(d_off, h, (size_t)(n_curves + 1) * 8, cudaMemcpyHostToDevice, cs);
+  cudaMemcpyAsync(d_pairs, hp, (size_t)n_pairs * 8, cudaMemcpyHostToDevice, cs);
+  cudaEventRecord(ctx->slice_ev[kMaxSlices], cs);
+  cudaStreamWaitEvent(s, ctx->slice_ev[kMaxSlices], 0);
+  for (int k = 1; k < K; ++k) copy_slice(k);
   int last = 0;   // the last slice with pairs: it waits for every slice and covers all curves
   for (int k = 0; k < K; ++k)
     if (start[k + 1] > start[k]) last = k;
@@ -218,12 +243,31 @@ extern "C" dfd_status dfd_batch_host(dfd_context* ctx, dfd_dtype dtype, int dim,
     cudaMemset(ctx->d_err, 0, sizeof(int));
     return (dfd_status)err;
   }
+  // 4. results back in the caller's pair order
   const char* r1 = h + off_b + pair_b;
   const char* r2 = r1 + dist_b;
-  for (int64_t pos = 0; pos < n_pairs; ++pos) {
-    const int64_t i = perm[pos];
-    if (out_dist) std::memcpy(static_cast<char*>(out_dist) + i * d1, r1 + pos * d1, d1);
-    if (out_dist2) std::memcpy(static_cast<char*>(out_dist2) + i * d2, r2 + pos * d2, d2);
+  if (f32) {
+    if (out_dist) {
+      const float* a = reinterpret_cast<const float*>(r1);
+      float* o = static_cast<float*>(out_dist);
+      for (int64_t pos = 0; pos < n_pairs; ++pos) o[perm[pos]] = a[pos];
+    }
+    if (out_dist2) {
+      const float* a = reinterpret_cast<const float*>(r2);
+      float* o = static_cast<float*>(out_dist2);
+      for (int64_t pos = 0; pos < n_pairs; ++pos) o[perm[pos]] = a[pos];
+    }
+  } else {
+    if (out_dist) {
+      const double* a = reinterpret_cast<const double*>(r1);
+      double* o = static_cast<double*>(out_dist);
+      for (int64_t pos = 0; pos < n_pairs; ++pos) o[perm[pos]] = a[pos];
+    }
+    if (out_dist2) {
+      const long long* a = reinterpret_cast<const long long*>(r2);
+      long long* o = static_cast<long long*>(out_dist2);
+      for (int64_t pos = 0; pos < n_pairs; ++pos) o[perm[pos]] = a[pos];
+    }
   }
   return DFD_OK;
 }

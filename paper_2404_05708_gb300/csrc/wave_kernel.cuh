@@ -910,16 +910,19 @@ __global__ void pack_q_kernel(const typename V::coord* q, int64_t m, int dim, in
 // (rowbuf_b[m-1-j]).  Every monotone path crosses from row n1-1 to row n1
 // once, by a vertical step (to column j) or a diagonal one (to j+1), so
 // delta^2 = min_j max(F[j], min(B[j], B[j+1])): a selection among the same
-// squared distances, bit-identical to the single wavefront's result.  One
-// CTA, a block-wide min.
+// squared distances, bit-identical to the single wavefront's result.
+// Each CTA reduces a stretch of columns; the values are non-negative, so
+// their bit patterns order like the values and the CTAs merge by an atomic
+// max of the complemented bits in `word` (zero before the launch); the last
+// CTA to finish (`count`, zero before the launch) writes the result.
 template <class V>
-__global__ void combine_kernel(const void* rowbuf_f, const void* rowbuf_b, int64_t m, void* out_dist,
-                               void* out_dist2) {
+__global__ void combine_kernel(const void* rowbuf_f, const void* rowbuf_b, int64_t m, unsigned long long* word,
+                               unsigned* count, void* out_dist, void* out_dist2) {
   using T = typename V::value;
   const T* F = static_cast<const T*>(rowbuf_f);
   const T* B = static_cast<const T*>(rowbuf_b);
   T best = V::inf();
-  for (int64_t j = threadIdx.x; j < m; j += blockDim.x) {
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < m; j += (int64_t)gridDim.x * blockDim.x) {
     const T bj = B[m - 1 - j];
     const T bj1 = j + 1 < m ? B[m - 2 - j] : V::inf();
     best = V::vmin(best, V::vmax(F[j], V::vmin(bj, bj1)));
@@ -935,12 +938,24 @@ __global__ void combine_kernel(const void* rowbuf_f, const void* rowbuf_b, int64
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) x = V::vmin(x, __shfl_xor_sync(0xffffffffu, x, off));
     if (L == 0) {
-      if constexpr (sizeof(T) == 4) {
-        if (out_dist2) static_cast<float*>(out_dist2)[0] = (float)x;
-        if (out_dist) static_cast<float*>(out_dist)[0] = sqrtf((float)x);
-      } else {
-        if (out_dist2) static_cast<long long*>(out_dist2)[0] = (long long)x;
-        if (out_dist) static_cast<double*>(out_dist)[0] = sqrt((double)x);
+      unsigned long long bits;
+      if constexpr (sizeof(T) == 4)
+        bits = __float_as_uint((float)x);
+      else
+        bits = (unsigned long long)(long long)x;
+      atomicMax(word, ~bits);
+      __threadfence();
+      if (atomicAdd(count, 1u) == gridDim.x - 1) {
+        const unsigned long long mb = ~atomicAdd(word, 0ull);
+        if constexpr (sizeof(T) == 4) {
+          const float r = __uint_as_float((unsigned)mb);
+          if (out_dist2) static_cast<float*>(out_dist2)[0] = r;
+          if (out_dist) static_cast<float*>(out_dist)[0] = sqrtf(r);
+        } else {
+          const long long r = (long long)mb;
+          if (out_dist2) static_cast<long long*>(out_dist2)[0] = r;
+          if (out_dist) static_cast<double*>(out_dist)[0] = sqrt((double)r);
+        }
       }
     }
   }

@@ -110,7 +110,13 @@ dfd_status wave_launch(dfd_context* ctx, int dim, const void* p, int64_t n, cons
   grid = (int)std::min<int64_t>(grid, nbands);
   timing_begin(ctx, s);
   wave::wave_kernel<V, DK, R><<<grid, (W + 1) * 32, smem, s>>>(a);
-  if (two) wave::combine_kernel<V><<<1, 1024, 0, s>>>(a.rowbuf, a.rowbuf_b, m, out_dist, out_dist2);
+  if (two) {
+    // the merge words sit after the ticket in the zeroed scratch header
+    const int cblocks = (int)std::max<int64_t>(1, std::min<int64_t>((m + 1023) / 1024, ctx->num_sms));
+    wave::combine_kernel<V><<<cblocks, 256, 0, s>>>(a.rowbuf, a.rowbuf_b, m,
+                                                    reinterpret_cast<unsigned long long*>(base + 16),
+                                                    reinterpret_cast<unsigned*>(base + 8), out_dist, out_dist2);
+  }
   timing_end(ctx, s);
   return cuda_status(cudaGetLastError());
   }
