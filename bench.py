@@ -50,8 +50,8 @@ REF_SAMPLE = 20_000          # --impl reference: prefix per step
 # dram__bytes_write.sum: one pass), keyed by the hash of the kernel sources it
 # was taken on; any later source change reports null.
 TRAFFIC_BY_KERNEL_SHA: dict = {
-    "7beb7b6acc1cc579": 9360230,     # wave_kernel<F32, 3, 6>, long pair 200,000^2
-    "025a8d5c1e61fa57": 289575749,   # batch_kernel<I32, 2>, ragged batch of 65,536 pairs
+    "749cd1d4954ccfcf": 15845811,    # wave_kernel<F32, 3, 6>, long pair 200,000^2 (two fronts)
+    "3ad2e1b0da564fd5": 289500000,   # batch_kernel<I32, 2>, ragged batch of 65,536 pairs (graph launches)
 }
 
 
