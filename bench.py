@@ -80,7 +80,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="long", choices=["long", "batch", "matrix", "pair2k", "serve", "knn"])
+    ap.add_argument("--workload", default="long", choices=["long", "batch", "matrix", "pair2k", "serve", "knn", "next"])
     ap.add_argument("--rates", default="100,1000,3000,10000,20000,30000")
     ap.add_argument("--serve-seconds", type=float, default=2.0)
     ap.add_argument("--tick-cells", type=float, default=4e9, help="serve: cell budget of one tick")
@@ -617,6 +617,124 @@ def run_serving(args):
     return 0
 
 
+def run_next(args):
+    """The rows after the hot path, each on seeded synthetic inputs, timed
+    with CUDA events over --steps launches after --warmup, verified on a
+    sample against the oracle, with its roofline against the measured cell
+    mix of its own recurrence:
+
+    decider  dfd_batch_decide on the ragged int32 batch (65,536 pairs, the
+             batch workload) with eps^2 = the median delta^2 of its first
+             2,048 pairs; rate over all candidate cells, abandoned share.
+    dtw      DTW of 16,384 float32 2-D Gaussian-walk pairs, lengths U{16..512}.
+    lev      Levenshtein distance of 16,384 pairs of int32 symbol sequences
+             over {0..3}, lengths U{16..512}.
+    mc       4,096 Monte Carlo samples of one pair of 512-point 2-D walks,
+             both curves perturbed by 0.05 * N(0, 1) per coordinate.
+    """
+    import torch
+    import oracle
+    from paper_2404_05708_gb300 import build, dfd, workloads
+    build.build()
+    oracle.load()
+    torch.cuda.set_device(0)
+    ctx = dfd.Context(0)
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    steps, warmup = max(args.steps, 3), max(args.warmup, 3)
+
+    def timed(fn):
+        for _ in range(warmup):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / steps
+
+    def roof(op, cells, ms):
+        rate, mhz = dfd.dfd_microbench(ctx.handle, dfd.MICRO_OPS[op])
+        peak = rate * sms * mhz * 1e6 / 1e9
+        ach = cells / (ms * 1e-3) / 1e9
+        return {"bound": "alu", "achieved": ach, "peak": peak, "unit": "Gcell/s", "frac": ach / peak,
+                "peak_basis": f"measured mix {op} {rate:.2f} cells/clk/SM x {sms} SMs x {mhz:.0f} MHz"}
+
+    def ragged(n_pairs, seed, gen):
+        rng = np.random.default_rng(seed)
+        lens = rng.integers(16, 513, size=2 * n_pairs)
+        off = np.concatenate([[0], np.cumsum(lens)]).astype(np.int64)
+        pts = gen(rng, int(off[-1]))
+        pairs = np.arange(2 * n_pairs, dtype=np.int32).reshape(-1, 2)
+        return pts, off, pairs, lens
+
+    rows = []
+    # decider
+    b = workloads.ragged_int_batch()
+    ln = b.lengths()
+    cells = int(np.sum(ln[b.pairs[:, 0]] * ln[b.pairs[:, 1]]))
+    ref, _ = oracle.batch(b.points, b.offsets, b.pairs[:2048])
+    eps2 = float(np.median(ref))
+    P, O, Q = (torch.from_numpy(x).cuda() for x in (b.points, b.offsets, b.pairs))
+    out = {}
+    def dec():
+        out["r"] = ctx.decide(P, O, Q, eps2)
+    ms = timed(dec)
+    d2, within, ab = out["r"]
+    ok = bool(np.array_equal(within[:2048].cpu().numpy().astype(bool), ref <= eps2))
+    rows.append({"row": "decider", "pairs": int(b.pairs.shape[0]), "cells_per_step": cells, "ms": ms,
+                 "gcups_all_cells": cells / (ms * 1e-3) / 1e9, "eps2": eps2,
+                 "abandoned": int(ab.item()) / b.pairs.shape[0], "verified_vs_oracle": ok})
+    # DTW
+    pts, off, pairs, lens = ragged(16384, 11, lambda rng, n: np.cumsum(rng.normal(0, 1, size=(n, 2)), axis=0)
+                                   .astype(np.float32))
+    cells = int(np.sum(lens[0::2] * lens[1::2]))
+    P, O, Q = (torch.from_numpy(x).cuda() for x in (pts, off, pairs))
+    ms = timed(lambda: out.__setitem__("r", ctx.dtw(P, O, Q)))
+    got = out["r"][:256].cpu().numpy()
+    want = np.array([oracle.dtw_f32mirror(pts[off[2 * i]:off[2 * i + 1]], pts[off[2 * i + 1]:off[2 * i + 2]])
+                     for i in range(256)], np.float32)
+    rows.append({"row": "dtw", "pairs": 16384, "cells_per_step": cells, "ms": ms,
+                 "gcups": cells / (ms * 1e-3) / 1e9, "verified_vs_oracle": bool(np.array_equal(got, want)),
+                 "roofline": roof("cell_dtw_f32_d2", cells, ms)})
+    # Levenshtein
+    sym, off, pairs, lens = ragged(16384, 12, lambda rng, n: rng.integers(0, 4, size=(n, 1)).astype(np.int32))
+    cells = int(np.sum(lens[0::2] * lens[1::2]))
+    P, O, Q = (torch.from_numpy(x).cuda() for x in (sym, off, pairs))
+    ms = timed(lambda: out.__setitem__("r", ctx.levenshtein(P, O, Q)))
+    got = out["r"][:256].cpu().numpy()
+    want = np.array([oracle.levenshtein(sym[off[2 * i]:off[2 * i + 1], 0], sym[off[2 * i + 1]:off[2 * i + 2], 0])
+                     for i in range(256)], np.int64)
+    rows.append({"row": "levenshtein", "pairs": 16384, "cells_per_step": cells, "ms": ms,
+                 "gcups": cells / (ms * 1e-3) / 1e9, "verified_vs_oracle": bool(np.array_equal(got, want)),
+                 "roofline": roof("cell_lev_i32", cells, ms)})
+    # Monte Carlo
+    rng = np.random.default_rng(13)
+    p = np.cumsum(rng.normal(0, 1, size=(512, 2)), axis=0).astype(np.float32)
+    q = np.cumsum(rng.normal(0, 1, size=(512, 2)), axis=0).astype(np.float32)
+    S = 4096
+    zp = rng.normal(0, 1, size=(S, 512, 2)).astype(np.float32)
+    zq = rng.normal(0, 1, size=(S, 512, 2)).astype(np.float32)
+    Pd, Qd, Zp, Zq = (torch.from_numpy(x).cuda() for x in (p, q, zp, zq))
+    ms = timed(lambda: out.__setitem__("r", ctx.mc_pair(Pd, Qd, Zp, Zq, 0.05, 0.05)))
+    d2 = out["r"][1].cpu().numpy()
+    ok = all(d2[s] == np.float32(oracle.dfd2_f32mirror(oracle.perturb(p, zp[s], 0.05), oracle.perturb(q, zq[s], 0.05)))
+             for s in (0, 1, 2047, 4095))
+    cells = S * 512 * 512
+    rows.append({"row": "monte_carlo", "samples": S, "cells_per_step": cells, "ms": ms,
+                 "gcups": cells / (ms * 1e-3) / 1e9, "verified_vs_oracle": bool(ok),
+                 "roofline": roof("cell_f32_d2", cells, ms)})
+    ctx.close()
+    out_line = {"metric": METRIC, "value": rows[1]["gcups"], "unit": UNIT, "n_gpus": 1, "steps": steps,
+                "warmup": warmup, "higher_is_better": True, "dtype": "mixed", "data": "synthetic",
+                "config": {"workload": "rows after the hot path: early-abandon decider, DTW, Levenshtein, "
+                                       "Monte Carlo samples (value: DTW)"},
+                "rows": rows}
+    print(json.dumps(out_line))
+    return 0
+
+
 # -------------------------------------------------------------- reference
 def run_reference(args):
     """CPU oracle on host cores, bounded sample per step."""
@@ -691,6 +809,8 @@ def main():
         return run_reference(args)
     if args.workload == "serve":
         return run_serving(args)
+    if args.workload == "next":
+        return run_next(args)
 
     import torch
     import torch.distributed as dist

@@ -450,6 +450,10 @@ dfd_status dfd_timing_last(dfd_context* ctx, double* ms);
  *  16 one float32 16-D cell (scalar: 16 sub + 16 mul/fma + min3 + max)
  *  17 one int32 2-D cell carried as uint32 bits (2 sub, mul.lo, mad.lo,
  *     3-input float min + float max), cells / clock / SM
+ *  18 one float32 2-D DTW cell (2 sub, mul, fma, 3-input min, add)
+ *  19 one Levenshtein cell (compare + select, min, add, add, min, the
+ *     column mask's select)
+ *  20 one float32 2-D cell (f32x2 distance + min3 + max)
  * Synchronous.  DFD_ERR_INVALID_ARG for an unknown op.
  */
 dfd_status dfd_microbench(dfd_context* ctx, int op, double* per_clk_per_sm, double* sm_mhz);

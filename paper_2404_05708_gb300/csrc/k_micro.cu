@@ -40,14 +40,18 @@ enum MicroOp {
   MB_LAT_MNMX64 = 15,      // latency: dependent min.s64 -> max.s64 (int cell chain)
   MB_MIX_F32D16 = 16,      // one float32 16-D cell: 16 sub + 16 fma/mul + min3 + max (scalar)
   MB_MIX_I32B_D2 = 17,     // one int32 2-D cell in uint32 bits: 2 sub, mul.lo, mad.lo, min3.f32 + max.f32
-  MB_COUNT = 18
+  MB_MIX_DTW_F32D2 = 18,   // one float32 2-D DTW cell: sub, mul, sub, fma, min3.f32, add
+  MB_MIX_LEV_I32 = 19,     // one Levenshtein cell: compare + select, min, add, add, min, column mask select
+  MB_MIX_F32D2 = 20,       // one float32 2-D cell: 2 f32x2 (per 2 cells: 2 sub, mul, fma) + min3 + max
+  MB_COUNT = 21
 };
 
 __host__ __device__ constexpr bool is_latency(int op) { return op >= MB_LAT_FMNMX && op <= MB_LAT_MNMX64; }
 
 // operations (thread-instructions, cells, or dependent ops) per iteration
 __host__ __device__ constexpr int ops_per_iter(int op) {
-  return op == MB_MIX_F32D3 ? 16 : op == MB_MIX_I32D2 ? 8 : op == MB_DISTONLY_F32D3 ? 16 : op == MB_MIX_F32D16 ? 2 : 8;
+  return op == MB_MIX_F32D3 || op == MB_MIX_F32D2 ? 16
+         : op == MB_MIX_I32D2 ? 8 : op == MB_DISTONLY_F32D3 ? 16 : op == MB_MIX_F32D16 ? 2 : 8;
 }
 
 template <int OP>
@@ -144,6 +148,41 @@ __global__ void __launch_bounds__(MB_THREADS) micro_kernel(float seed, unsigned 
           asm volatile("max.f32 %0, %0, %1;" : "+f"(f[k]) : "f"(lo));
           asm volatile("min.f32 %0, %0, %1, %2;" : "+f"(f[(k + 4) & 7]) : "f"(c1), "f"(c2));
           asm volatile("max.f32 %0, %0, %1;" : "+f"(f[(k + 4) & 7]) : "f"(hi));
+        } else if constexpr (OP == MB_MIX_F32D2) {
+          // two cells (a row pair) per k: 2 sub2 + mul2 + fma2, then min3 + max per cell
+          unsigned long long t0_, t1_, acc;
+          asm volatile("sub.rn.f32x2 %0, %1, %2;" : "=l"(t0_) : "l"(u[k]), "l"(cu));
+          asm volatile("sub.rn.f32x2 %0, %1, %2;" : "=l"(t1_) : "l"(u[k]), "l"(u[(k + 1) & 7]));
+          asm volatile("mul.rn.f32x2 %0, %1, %1;" : "=l"(acc) : "l"(t0_));
+          asm volatile("fma.rn.f32x2 %0, %1, %1, %0;" : "+l"(acc) : "l"(t1_));
+          u[k] = acc;
+          const float lo = lo2(acc), hi = hi2(acc);
+          asm volatile("min.f32 %0, %0, %1, %2;" : "+f"(f[k]) : "f"(c1), "f"(c2));
+          asm volatile("max.f32 %0, %0, %1;" : "+f"(f[k]) : "f"(lo));
+          asm volatile("min.f32 %0, %0, %1, %2;" : "+f"(f[(k + 4) & 7]) : "f"(c1), "f"(c2));
+          asm volatile("max.f32 %0, %0, %1;" : "+f"(f[(k + 4) & 7]) : "f"(hi));
+        } else if constexpr (OP == MB_MIX_DTW_F32D2) {
+          // the point coordinates are loop-carried (rewritten below), so no
+          // distance can be hoisted out of the loop
+          float t, acc;
+          asm volatile("sub.rn.f32 %0, %1, %2;" : "=f"(t) : "f"(f[k]), "f"(c1));
+          asm volatile("mul.rn.f32 %0, %1, %1;" : "=f"(acc) : "f"(t));
+          asm volatile("sub.rn.f32 %0, %1, %2;" : "=f"(t) : "f"(f[(k + 1) & 7]), "f"(c2));
+          asm volatile("fma.rn.f32 %0, %1, %1, %0;" : "+f"(acc) : "f"(t));
+          float mn;
+          asm volatile("min.f32 %0, %1, %2, %3;" : "=f"(mn) : "f"(f[k]), "f"(f[(k + 2) & 7]), "f"(f[(k + 3) & 7]));
+          asm volatile("add.rn.f32 %0, %1, %2;" : "=f"(f[k]) : "f"(mn), "f"(acc));
+        } else if constexpr (OP == MB_MIX_LEV_I32) {
+          int dd, t0, t1;
+          asm volatile("{\n\t.reg .pred P;\n\tsetp.ne.s32 P, %1, %2;\n\tselp.s32 %0, 1, 0, P;\n\t}"
+                       : "=r"(dd) : "r"(iv[k]), "r"(it));
+          asm volatile("min.s32 %0, %1, %2;" : "=r"(t0) : "r"(iv[k]), "r"(iv[(k + 1) & 7]));
+          asm volatile("add.s32 %0, %0, 1;" : "+r"(t0));
+          asm volatile("add.s32 %0, %1, %2;" : "=r"(t1) : "r"(iv[(k + 2) & 7]), "r"(dd));
+          asm volatile("min.s32 %0, %0, %1;" : "+r"(t0) : "r"(t1));
+          asm volatile("{\n\t.reg .pred Q;\n\tsetp.lt.s32 Q, %2, 0;\n\tselp.s32 %0, %1, %0, Q;\n\t}"
+                       : "+r"(t0) : "r"(iv[k]), "r"(iv[(k + 3) & 7]));
+          iv[k] = t0;
         } else if constexpr (OP == MB_MIX_I32B_D2) {
           int dx, dy;
           unsigned d2;
@@ -260,6 +299,9 @@ extern "C" dfd_status dfd_microbench(dfd_context* ctx, int op, double* result, d
     case MB_LAT_MNMX64: return run_op<MB_LAT_MNMX64>(ctx, result, sm_mhz);
     case MB_MIX_F32D16: return run_op<MB_MIX_F32D16>(ctx, result, sm_mhz);
     case MB_MIX_I32B_D2: return run_op<MB_MIX_I32B_D2>(ctx, result, sm_mhz);
+    case MB_MIX_DTW_F32D2: return run_op<MB_MIX_DTW_F32D2>(ctx, result, sm_mhz);
+    case MB_MIX_LEV_I32: return run_op<MB_MIX_LEV_I32>(ctx, result, sm_mhz);
+    case MB_MIX_F32D2: return run_op<MB_MIX_F32D2>(ctx, result, sm_mhz);
     default: return DFD_ERR_INVALID_ARG;
   }
 }

@@ -108,7 +108,8 @@ _SIGS = {
 MICRO_OPS = {"ffma": 0, "ffma2": 1, "fmnmx": 2, "fmnmx3": 3, "imnmx": 4, "imnmx64": 5, "imad_wide": 6,
              "shfl": 7, "cell_f32_d3": 8, "cell_i32_d2": 9, "distonly_f32_d3": 10,
              "lat_fmnmx": 11, "lat_cell": 12, "lat_shfl": 13, "lat_ffma2": 14, "lat_mnmx64": 15,
-             "cell_f32_d16": 16, "cell_i32b_d2": 17}
+             "cell_f32_d16": 16, "cell_i32b_d2": 17, "cell_dtw_f32_d2": 18, "cell_lev_i32": 19,
+             "cell_f32_d2": 20}
 _RESTYPE = {"dfd_status_string": ctypes.c_char_p, "dfd_server_now": ctypes.c_double}
 
 
