@@ -41,9 +41,12 @@ struct LevOp {
 template <class Op, int DK, int R>
 __device__ __forceinline__ typename Op::value warp_var(const typename Op::coord* __restrict__ P, int n,
                                                        const typename Op::coord* __restrict__ Q, int m, int dim,
-                                                       bool vec, typename Op::value* buf, int L) {
+                                                       bool vec, typename Op::value* buf, int L, uint4* stage) {
   using T = typename Op::value;
   using Cd = typename Op::coord;
+  using V = typename Op::V;
+  using QR = batch::QRec<V, DK>;
+  constexpr int NPL = QR::NPL;
   const T INF = Op::lev ? (T)0x3fffffff : (T)__int_as_float(0x7f800000);
   const int nstripes = (n + 32 * R - 1) / (32 * R);
   T res = 0;
@@ -54,6 +57,17 @@ __device__ __forceinline__ typename Op::value warp_var(const typename Op::coord*
       const int i = min(st * 32 * R + L * R + r, n - 1);
 #pragma unroll
       for (int k = 0; k < DK; ++k) pr[r][k] = k < dim ? __ldg(P + (int64_t)i * dim + k) : (Cd)0;
+    }
+    // DTW: rows packed in pairs, two distances per f32x2 instruction (the
+    // per-element rounding of the scalar order)
+    constexpr bool kPack = !Op::lev && R >= 2;
+    unsigned long long pp[kPack ? R / 2 : 1][DK];
+    if constexpr (kPack) {
+#pragma unroll
+      for (int h = 0; h < R / 2; ++h) {
+#pragma unroll
+        for (int k = 0; k < DK; ++k) pp[h][k] = pack2(pr[2 * h][k], pr[2 * h + 1][k]);
+      }
     }
     const bool has_top = st > 0, has_bottom = st + 1 < nstripes, last = !has_bottom;
     const int row0 = st * 32 * R + L * R;   // global row of the lane's first row
@@ -66,29 +80,99 @@ __device__ __forceinline__ typename Op::value warp_var(const typename Op::coord*
     const int li = n - 1 - st * 32 * R;
     const int lres = li / R, rres = li % R;
     const int nsteps = m + 31;
+    // q through the per-warp window of the batch engine (columns c0-32 ..
+    // c0+31 in slots 0..63 during the block of c0, one record load per step)
+    Cd qpre[DK];
+    batch::load_point<Cd, DK>(Q, min(L, m - 1), dim, vec, qpre);
+    const uint4* sb = stage + (32 - L);
+    T* outb = reinterpret_cast<T*>(stage + NPL * 64);
     for (int c0 = 0; c0 < nsteps; c0 += 32) {
       T top_blk;
       if (has_top)
         top_blk = buf[min(c0 + L, m - 1)];
       else
         top_blk = Op::lev ? (T)(c0 + L + 1) : INF;
-      T out_blk = INF;
+      __syncwarp();
+#pragma unroll
+      for (int c = 0; c < NPL; ++c) {
+        stage[c * 64 + L] = c0 > 0 ? stage[c * 64 + 32 + L] : batch::make_qrec<V, DK>(qpre, c);
+        stage[c * 64 + 32 + L] = batch::make_qrec<V, DK>(qpre, c);
+      }
+      __syncwarp();
+      batch::load_point<Cd, DK>(Q, min(c0 + 32 + L, m - 1), dim, vec, qpre);
+      uint4 qr[NPL];
+#pragma unroll
+      for (int c = 0; c < NPL; ++c) qr[c] = sb[c * 64];
 #pragma unroll 4
       for (int s = 0; s < 32; ++s) {
         const int j = c0 + s - L;
-        const int jq = min(max(j, 0), m - 1);
-        Cd qk[DK];
-        batch::load_point<Cd, DK>(Q, jq, dim, vec, qk);
-        T d[R];
+        uint4 qn[NPL];
+        if (s + 1 < 32) {
 #pragma unroll
-        for (int r = 0; r < R; ++r) {
-          if constexpr (Op::lev) {
+          for (int c = 0; c < NPL; ++c) qn[c] = sb[c * 64 + s + 1];
+        }
+        T d[R];
+        if constexpr (Op::lev) {
+          Cd qk[DK];
+#pragma unroll
+          for (int c = 0; c < NPL; ++c) {
+            qk[4 * c] = *reinterpret_cast<const Cd*>(&qr[c].x);
+            if (4 * c + 1 < DK) qk[4 * c + 1] = *reinterpret_cast<const Cd*>(&qr[c].y);
+            if (4 * c + 2 < DK) qk[4 * c + 2] = *reinterpret_cast<const Cd*>(&qr[c].z);
+            if (4 * c + 3 < DK) qk[4 * c + 3] = *reinterpret_cast<const Cd*>(&qr[c].w);
+          }
+#pragma unroll
+          for (int r = 0; r < R; ++r) {
             bool diff = false;
 #pragma unroll
-            for (int k = 0; k < DK; ++k) diff |= pr[r][k] != qk[k];
+            for (int k = 0; k < DK; ++k) diff |= pr[r][k] != qk[k];   // coordinates past dim are 0 on both sides
             d[r] = diff ? 1 : 0;
+          }
+        } else if constexpr (QR::kind == batch::kDup) {
+          unsigned long long qd[2];
+          qd[0] = ((unsigned long long)qr[0].y << 32) | qr[0].x;
+          qd[1] = ((unsigned long long)qr[0].w << 32) | qr[0].z;
+#pragma unroll
+          for (int h = 0; h < R / 2; ++h) {
+            const unsigned long long t0 = sub2(pp[h][0], qd[0]);
+            const unsigned long long t1 = sub2(pp[h][1], qd[1]);
+            const unsigned long long acc = fma2(t1, t1, mul2(t0, t0));
+            d[2 * h] = lo2(acc);
+            d[2 * h + 1] = hi2(acc);
+          }
+          if constexpr ((R & 1) != 0) {
+            const Cd qk[DK] = {__uint_as_float(qr[0].x), __uint_as_float(qr[0].z)};
+            d[R - 1] = dist2<DK>(pr[R - 1], qk);
+          }
+        } else {
+          Cd qk[DK];
+#pragma unroll
+          for (int c = 0; c < NPL; ++c) {
+            qk[4 * c] = *reinterpret_cast<const Cd*>(&qr[c].x);
+            if (4 * c + 1 < DK) qk[4 * c + 1] = *reinterpret_cast<const Cd*>(&qr[c].y);
+            if (4 * c + 2 < DK) qk[4 * c + 2] = *reinterpret_cast<const Cd*>(&qr[c].z);
+            if (4 * c + 3 < DK) qk[4 * c + 3] = *reinterpret_cast<const Cd*>(&qr[c].w);
+          }
+          if constexpr (kPack) {
+            unsigned long long qd[DK];
+#pragma unroll
+            for (int k = 0; k < DK; ++k) qd[k] = pack2(qk[k], qk[k]);
+#pragma unroll
+            for (int h = 0; h < R / 2; ++h) {
+              const unsigned long long t0 = sub2(pp[h][0], qd[0]);
+              unsigned long long acc = mul2(t0, t0);
+#pragma unroll
+              for (int k = 1; k < DK; ++k) {
+                const unsigned long long t = sub2(pp[h][k], qd[k]);
+                acc = fma2(t, t, acc);
+              }
+              d[2 * h] = lo2(acc);
+              d[2 * h + 1] = hi2(acc);
+            }
+            if constexpr ((R & 1) != 0) d[R - 1] = dist2<DK>(pr[R - 1], qk);
           } else {
-            d[r] = dist2<DK>(pr[r], qk);
+#pragma unroll
+            for (int r = 0; r < R; ++r) d[r] = dist2<DK>(pr[r], qk);
           }
         }
         const T tin = __shfl_sync(0xffffffffu, top_blk, s);
@@ -111,22 +195,20 @@ __device__ __forceinline__ typename Op::value warp_var(const typename Op::coord*
         }
         upp = u;
         bout = up;
-        if (has_bottom) {
-          const T b31 = __shfl_sync(0xffffffffu, bout, 31);
-          out_blk = (L == s) ? b31 : out_blk;
-        }
+        if (has_bottom && L == 31) outb[s] = bout;   // column c0 + s - 31 of the stripe's bottom row
         if (last && L == lres && j == m - 1) {
 #pragma unroll
           for (int r = 0; r < R; ++r)
             if (r == rres) res = v[r];
         }
-      }
-      if (has_bottom) {
-        const int oc = c0 + L - 31;
-        __syncwarp();
-        if (oc >= 0 && oc < m) buf[oc] = out_blk;
+#pragma unroll
+        for (int c = 0; c < NPL; ++c) qr[c] = qn[c];
       }
       __syncwarp();
+      if (has_bottom) {
+        const int oc = c0 + L - 31;
+        if (oc >= 0 && oc < m) buf[oc] = outb[L];
+      }
     }
     if (last) res = __shfl_sync(0xffffffffu, res, lres);
   }
@@ -136,12 +218,12 @@ __device__ __forceinline__ typename Op::value warp_var(const typename Op::coord*
 template <class Op, int DK>
 __device__ __forceinline__ typename Op::value warp_var_any(const typename Op::coord* P, int n,
                                                            const typename Op::coord* Q, int m, int dim, bool vec,
-                                                           typename Op::value* buf, int L) {
+                                                           typename Op::value* buf, int L, uint4* stage) {
   constexpr int RM = batch::Rmax<DK>::value;
   switch (batch::rows_per_lane<DK>(n)) {
 #define DFD_V_CASE(RR) \
   case RR:             \
-    if constexpr (RR < RM) return warp_var<Op, DK, RR>(P, n, Q, m, dim, vec, buf, L); \
+    if constexpr (RR < RM) return warp_var<Op, DK, RR>(P, n, Q, m, dim, vec, buf, L, stage); \
     break;
     DFD_V_CASE(1)
     DFD_V_CASE(2)
@@ -154,13 +236,15 @@ __device__ __forceinline__ typename Op::value warp_var_any(const typename Op::co
       break;
 #undef DFD_V_CASE
   }
-  return warp_var<Op, DK, RM>(P, n, Q, m, dim, vec, buf, L);
+  return warp_var<Op, DK, RM>(P, n, Q, m, dim, vec, buf, L, stage);
 }
 
 template <class Op, int DK>
 __global__ void __launch_bounds__(256, batch::kBlocksPerSM<DK>::value) variant_kernel(batch::BatchArgs a) {
   using T = typename Op::value;
   using Cd = typename Op::coord;
+  __shared__ uint4 stage_sm[8][batch::QStage<DK>::RECS];
+  uint4* stage = stage_sm[threadIdx.x >> 5];
   const int L = threadIdx.x & 31;
   const int64_t gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   T* buf = static_cast<T*>(a.rowbuf) + gw * batch::BUF_COLS;
@@ -190,7 +274,7 @@ __global__ void __launch_bounds__(256, batch::kBlocksPerSM<DK>::value) variant_k
       if (L == 0) raise_error(a.err, DFD_ERR_UNSUPPORTED);
       continue;
     }
-    const T r = warp_var_any<Op, DK>(pts + oa * a.dim, n, pts + ob * a.dim, m, a.dim, a.vec != 0, buf, L);
+    const T r = warp_var_any<Op, DK>(pts + oa * a.dim, n, pts + ob * a.dim, m, a.dim, a.vec != 0, buf, L, stage);
     if (L == 0) {
       if constexpr (Op::lev)
         static_cast<long long*>(a.out_dist2)[k] = (long long)r;
