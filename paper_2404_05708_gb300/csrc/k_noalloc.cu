@@ -68,7 +68,10 @@ size_t scratch_needed(dfd_dtype dtype, int dim, int64_t n, int64_t m) {
   else
     q_per_col = dk <= 4 ? 16 : dk == 8 ? 32 : 64;
   const size_t vbytes = dtype == DFD_F32 ? 4 : 8;
-  return 1024 + 8 * (size_t)((n + 63) / 64) + (size_t)m * vbytes + ((size_t)m + 288) * q_per_col;
+  // packed q: m columns plus the skew and block padding, rounded up to whole
+  // chunks of up to 512 columns (one front; two fronts are used only when
+  // their doubled scratch also fits, else the wavefront runs one)
+  return 1024 + 8 * (size_t)((n + 63) / 64) + (size_t)m * vbytes + ((size_t)m + 1024) * q_per_col;
 }
 
 }  // namespace

@@ -181,6 +181,44 @@ def test_f32_mirror_exact_on_exact_inputs_and_close_otherwise():
         assert abs(got - ref) <= 6 * 2.0 ** -24 * ref
 
 
+def _rows_dp(d):
+    """All rows of Eq. 1 over a matrix of ground distances (plain loops)."""
+    n, m = d.shape
+    M = np.empty((n, m))
+    for i in range(n):
+        for j in range(m):
+            if i == 0 and j == 0:
+                M[i, j] = d[i, j]
+                continue
+            best = math.inf
+            if i > 0:
+                best = min(best, M[i - 1, j])
+            if j > 0:
+                best = min(best, M[i, j - 1])
+            if i > 0 and j > 0:
+                best = min(best, M[i - 1, j - 1])
+            M[i, j] = max(best, d[i, j])
+    return M
+
+
+def test_meeting_in_the_middle_identity():
+    """The two-front wavefront's combine: with F the last row of the DP over
+    rows 0..n1-1 and B the last row of the DP over the remaining rows with
+    both curves reversed (read back in forward column order), the oracle's
+    delta^2 equals min_j max(F[j], min(B[j], B[j+1])) for every split."""
+    rng = np.random.default_rng(17)
+    for _ in range(60):
+        n, m = int(rng.integers(2, 12)), int(rng.integers(1, 12))
+        p, q = rand_int_curve(rng, n, 2), rand_int_curve(rng, m, 2)
+        want = oracle.dfd2_linear(p, q)
+        d = ((p[:, None, :].astype(np.int64) - q[None, :, :]) ** 2).sum(-1).astype(float)
+        for n1 in range(1, n):
+            F = _rows_dp(d[:n1])[-1]
+            B = _rows_dp(d[n1:][::-1, ::-1])[-1][::-1]
+            Bn = np.append(B[1:], math.inf)
+            assert np.min(np.maximum(F, np.minimum(B, Bn))) == want, (n, m, n1)
+
+
 def test_batch_driver_matches_single_calls():
     from paper_2404_05708_gb300 import workloads
     b = workloads.ragged_int_batch(n_pairs=64, len_lo=1, len_hi=40, seed=21)

@@ -66,6 +66,24 @@ def test_noalloc_matches_dfd_pair_on_consecutive_calls(dctx):
     assert d21.item() == want_d2 and d1.item() == want_d
 
 
+def test_noalloc_falls_back_to_one_front(dctx):
+    """300,000 columns of 3-D float32: one front's scratch fits the fixed
+    array, two fronts' (two packed q streams) does not, so the wavefront
+    runs one front; q = p + t gives delta^2 = |t|^2 exactly."""
+    rng = np.random.default_rng(72)
+    n = 300_000
+    p = np.cumsum(rng.integers(-1, 2, size=(n, 3)), axis=0).astype(np.float32)
+    t = np.array([3.0, -4.0, 12.0], np.float32)
+    P, Q = torch.from_numpy(p).cuda(), torch.from_numpy(p + t).cuda()
+    d = torch.empty(1, dtype=torch.float32, device="cuda")
+    d2 = torch.empty(1, dtype=torch.float32, device="cuda")
+    assert _noalloc(P, Q, dfd.DFD_F32, d, d2) == 0
+    torch.cuda.synchronize()
+    assert d2.item() == 169.0 and d.item() == 13.0
+    e, e2 = dctx.pair(P, Q)   # the context path runs two fronts
+    assert e2.item() == d2.item() and e.item() == d.item()
+
+
 def test_noalloc_rejects_inputs_beyond_its_fixed_capacity():
     # float32 3-D needs ~36 bytes per column of q: 600,000 columns exceed 16 MiB.
     p = torch.zeros((10, 3), dtype=torch.float32, device="cuda")
