@@ -14,7 +14,9 @@
 //                            E_{i-1,j-1} + [a_i != b_j]),
 //                 boundaries E_{i,-1} = i + 1, E_{-1,j} = j + 1, corner 0
 //                 (the textbook table; the appendix listing's start
-//                 differs by one and is read as this).
+//                 differs by one and is read as this); the columns left of
+//                 the table (the systolic ramp) see a symbol that differs
+//                 from every real one, which keeps them at E_{i,-1}.
 // Unlike the Frechet distance neither is invariant under repeating a point,
 // so the result is read at row n - 1 (the padding rows of the last stripe
 // are computed and ignored).
@@ -95,7 +97,16 @@ __device__ __forceinline__ typename Op::value warp_var(const typename Op::coord*
       __syncwarp();
 #pragma unroll
       for (int c = 0; c < NPL; ++c) {
-        stage[c * 64 + L] = c0 > 0 ? stage[c * 64 + 32 + L] : batch::make_qrec<V, DK>(qpre, c);
+        uint4 lower = c0 > 0 ? stage[c * 64 + 32 + L] : batch::make_qrec<V, DK>(qpre, c);
+        // Levenshtein: columns left of the table (the first block's lower
+        // window) read a symbol with second coordinate 1, which differs from
+        // every real symbol (dim 1: second coordinate 0).  With d = 1 there the
+        // cell rule reproduces the boundary E_{i,-1} = i + 1 exactly
+        // (min(min(i+1, i) + 1, i + 1)), so no per-cell mask is needed.
+        if constexpr (Op::lev) {
+          if (c0 == 0 && c == 0) lower.y = 1u;
+        }
+        stage[c * 64 + L] = lower;
         stage[c * 64 + 32 + L] = batch::make_qrec<V, DK>(qpre, c);
       }
       __syncwarp();
@@ -184,8 +195,7 @@ __device__ __forceinline__ typename Op::value warp_var(const typename Op::coord*
           const T l = v[r];
           T nv;
           if constexpr (Op::lev) {
-            nv = min(min(l, up) + 1, dg + d[r]);
-            nv = j < 0 ? l : nv;   // columns left of the table keep the boundary E_{i,-1}
+            nv = min(min(l, up) + 1, dg + d[r]);   // columns left of the table keep E_{i,-1} (sentinel symbol)
           } else {
             nv = __fadd_rn(F32::vmin3(l, dg, up), d[r]);
           }
