@@ -106,7 +106,11 @@ dfd_status dfd_get_error(dfd_context* ctx);
  * Discrete Frechet distance of one pair of curves (Eq. 1, Alg. 5 semantics)
  * on the whole GPU: a band wavefront over the (n x m) recurrence (rows of p
  * in bands across CTAs, warps inside a band as a systolic pipeline over the
- * columns), with O(n + m) device scratch owned by the context.
+ * columns), with O(n + m) device scratch owned by the context.  A pair of two
+ * bands or more runs as two fronts in one launch -- forward over the first
+ * half of the bands and backward over the rest (both curves reversed) --
+ * whose last rows a final pass combines (min over the crossing steps of the
+ * max of both sides): the same value, bit for bit.
  *   p: n x dim, q: m x dim (device, dtype), n >= 1, m >= 1, 1 <= dim <= 16.
  *   out_dist / out_dist2: device pointers to one element each (see top).
  */
