@@ -847,6 +847,9 @@ dfd_status dfd_server_create(dfd_context* ctx, const dfd_server_options* opt, df
     ok = ok && cudaEventCreateWithFlags(&t.ev_up, cudaEventDisableTiming) == cudaSuccess;
     ok = ok && cudaMalloc(&t.d_counter, (MAX_DIM + 1) * sizeof(int)) == cudaSuccess;
     ok = ok && cudaMallocHost(&t.h_stage, STAGE_BYTES) == cudaSuccess;
+    // descriptors and results for ticks of up to ~256K pairs from the start:
+    // growing them later allocates (synchronising) inside a tick's latency
+    ok = ok && ensure_tick_capacity(t, (size_t)1 << 20, (size_t)1 << 18);
   }
   if (!ok) {
     cudaGetLastError();
