@@ -263,6 +263,26 @@ dfd_status dfd_matrix(dfd_context* ctx, dfd_dtype dtype, int dim, const void* po
                       int64_t n_curves, void* out_condensed, void* out_dist2, void* stream);
 
 /*
+ * Packing autotuner of the ragged batch (the "sophisticated scheduling" the
+ * paper leaves open, Sec. 4): which pair each warp takes next.  Order 0
+ * (default) hands out pairs grouped by code variant (rows per lane, stripes)
+ * and, inside a variant, by columns, largest first; order 1 hands them out by
+ * estimated cost alone (stripes x rows per lane x (columns + 31)), largest
+ * first.  Both compute every pair identically; only the timing differs.
+ * dfd_batch_autotune runs dfd_batch on the arguments with each order (one
+ * untimed and three timed runs, CUDA events on `stream`, synchronous),
+ * records the faster for (dtype, dim class) in the context -- later
+ * dfd_batch, dfd_batch_capture, dfd_batch_host and dfd_batch_decide calls
+ * of that class use it -- and writes it to *best_order (may be NULL).  The
+ * outputs hold the batch's results afterwards.  dfd_batch_set_order sets
+ * the order directly (0 or 1).
+ */
+dfd_status dfd_batch_autotune(dfd_context* ctx, dfd_dtype dtype, int dim, const void* points, const int64_t* offsets,
+                              int64_t n_curves, const int32_t* pairs, int64_t n_pairs, void* out_dist,
+                              void* out_dist2, int* best_order, void* stream);
+dfd_status dfd_batch_set_order(dfd_context* ctx, dfd_dtype dtype, int dim, int order);
+
+/*
  * dfd_batch with HOST buffers (points, offsets, pairs and the outputs are
  * host pointers; outputs may be NULL, not both): synchronous.  The points
  * are copied to the device in up to 8 slices of curves (about 128 MiB each)

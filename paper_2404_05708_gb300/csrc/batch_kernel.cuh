@@ -577,7 +577,23 @@ __device__ __forceinline__ int cost_bucket(int64_t rows, int64_t cols, int rmax)
   return (15 - min(cls, 15)) * 16 + sub;
 }
 
+// The packing order the autotuner can pick instead (order 1): pairs by
+// estimated cost alone, largest first -- stripes x rows per lane x (columns +
+// the 31-step ramp), on a log scale of 1/8 octave -- whatever their code
+// variant.  Either order computes every pair the same way; only the
+// assignment of pairs to warps over time differs.
+__device__ __forceinline__ int cost_bucket_lpt(int64_t rows, int64_t cols, int rmax) {
+  const int64_t per_stripe = 32 * (int64_t)rmax;
+  const int64_t st = (rows + per_stripe - 1) / per_stripe;
+  const int64_t r = rows <= 32 ? 1 : min((int64_t)rmax, (rows + 32 * st - 1) / (32 * st));
+  const unsigned long long cost = (unsigned long long)(st * r) * (unsigned long long)(cols + 31);   // >= 32
+  const int msb = 63 - __clzll((long long)cost);
+  const int b = 8 * msb + (int)((cost >> (msb - 3)) & 7);
+  return NBUCKET1 - 1 - min(NBUCKET1 - 1, b);
+}
+
 struct PlanArgs {
+  int order;           // 0: variant-major buckets (cost_bucket), 1: cost-descending (cost_bucket_lpt)
   const int64_t* offsets;
   const int32_t* pairs;
   int64_t n_pairs;
@@ -605,7 +621,8 @@ static __global__ void plan_hist_kernel(PlanArgs a) {
       const int64_t na = ea - oa, nb = eb - ob;
       if (na < 1 || nb < 1 || oa < 0 || ob < 0 || ea > total || eb > total || na > INT32_MAX || nb > INT32_MAX)
         raise_error(a.err, DFD_ERR_INVALID_ARG);
-      b = cost_bucket(max(min(na, nb), (int64_t)1), max(max(na, nb), (int64_t)1), a.rmax);
+      const int64_t rows = max(min(na, nb), (int64_t)1), cols = max(max(na, nb), (int64_t)1);
+      b = a.order ? cost_bucket_lpt(rows, cols, a.rmax) : cost_bucket(rows, cols, a.rmax);
       if (a.bbox && narrow_pair(a.bbox, a.dk, ia, ib)) b += NBUCKET1;
     }
     a.bucket[k] = (unsigned short)b;

@@ -115,6 +115,7 @@ dfd_status batch_prepare(dfd_context* ctx, int dim, const void* points, const in
   pa.dk = DK;
   pa.err = ctx->d_err;
   pa.rmax = batch::Rmax<DK>::value;
+  pa.order = ctx->batch_order[std::is_same<V, F32>::value ? 0 : 1][dim_class_index(DK)];
   const int pblocks = (int)std::min<int64_t>((n_pairs + 255) / 256, 8 * (int64_t)ctx->num_sms);
   batch::plan_hist_kernel<<<pblocks, 256, 0, s>>>(pa);
   batch::plan_scan_kernel<<<1, 32, 0, s>>>(pa);

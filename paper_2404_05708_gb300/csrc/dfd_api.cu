@@ -779,6 +779,61 @@ dfd_status dfd_batch(dfd_context* ctx, dfd_dtype dtype, int dim, const void* poi
                    static_cast<cudaStream_t>(stream));
 }
 
+dfd_status dfd_batch_set_order(dfd_context* ctx, dfd_dtype dtype, int dim, int order) {
+  if (!ctx || (dtype != DFD_F32 && dtype != DFD_I32) || dim < 1 || (order != 0 && order != 1))
+    return DFD_ERR_INVALID_ARG;
+  if (dim > 16) return DFD_ERR_UNSUPPORTED;
+  ctx->batch_order[dtype == DFD_F32 ? 0 : 1][dim_class_index(dim_class(dim))] = (signed char)order;
+  return DFD_OK;
+}
+
+dfd_status dfd_batch_autotune(dfd_context* ctx, dfd_dtype dtype, int dim, const void* points, const int64_t* offsets,
+                              int64_t n_curves, const int32_t* pairs, int64_t n_pairs, void* out_dist,
+                              void* out_dist2, int* best_order, void* stream) {
+  dfd_status st = check_batch_args(ctx, dtype, dim, points, offsets, n_curves, out_dist, out_dist2);
+  if (st != DFD_OK) return st;
+  if (!pairs || n_pairs < 0 || n_pairs > INT32_MAX) return DFD_ERR_INVALID_ARG;
+  if ((st = set_device(ctx)) != DFD_OK) return st;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  signed char& slot = ctx->batch_order[dtype == DFD_F32 ? 0 : 1][dim_class_index(dim_class(dim))];
+  const signed char keep = slot;
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) {
+    cudaGetLastError();
+    return DFD_ERR_CUDA;
+  }
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaGetLastError();
+    cudaEventDestroy(e0);
+    return DFD_ERR_CUDA;
+  }
+  float best_ms = 0.f;
+  int best = keep;
+  for (int order = 0; order < 2 && st == DFD_OK && n_pairs > 0; ++order) {
+    slot = (signed char)order;
+    // one untimed run (sizes the scratch), then three timed
+    st = batch_run(ctx, dtype, dim, points, offsets, n_curves, pairs, n_pairs, out_dist, out_dist2, s);
+    if (st != DFD_OK) break;
+    cudaEventRecord(e0, s);
+    for (int r = 0; r < 3 && st == DFD_OK; ++r)
+      st = batch_run(ctx, dtype, dim, points, offsets, n_curves, pairs, n_pairs, out_dist, out_dist2, s);
+    cudaEventRecord(e1, s);
+    float ms = 0.f;
+    if (st == DFD_OK && (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+      st = DFD_ERR_CUDA;
+    if (st == DFD_OK && (order == 0 || ms < best_ms)) {
+      best_ms = ms;
+      best = order;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaGetLastError();
+  slot = (signed char)(st == DFD_OK ? best : keep);
+  if (best_order) *best_order = slot;
+  return st;
+}
+
 dfd_status dfd_batch_decide(dfd_context* ctx, dfd_dtype dtype, int dim, const void* points, const int64_t* offsets,
                             int64_t n_curves, const int32_t* pairs, int64_t n_pairs, const void* eps2,
                             double eps2_all, void* out_dist2, int32_t* out_within, unsigned long long* abandoned,

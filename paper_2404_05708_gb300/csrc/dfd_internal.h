@@ -44,6 +44,7 @@ struct dfd_context {
   bool timed = false;                 // ev0/ev1 hold a recorded pair
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   std::map<uint64_t, dfd::WaveShape> tuned;   // autotuned wavefront shapes
+  signed char batch_order[2][5] = {};         // batch packing order per (float32 / int32, dim class 2,3,4,8,16)
   cudaStream_t copy_stream = nullptr;         // dfd_batch_host: point slices (created on first use)
   cudaEvent_t slice_ev[dfd::kMaxSlices + 1] = {};   // one per slice, and one for the allocation
 };
@@ -82,6 +83,9 @@ inline unsigned long long timeout_ns(const dfd_context* ctx) {
 
 // Kernel dimension class: 2, 3, 4, 8, 16 (coordinates beyond dim are zero,
 // which adds exact zeros to the squared distance).
+// Index of a dim class (2, 3, 4, 8, 16) in per-class tables.
+inline int dim_class_index(int dk) { return dk == 2 ? 0 : dk == 3 ? 1 : dk == 4 ? 2 : dk == 8 ? 3 : 4; }
+
 inline int dim_class(int dim) {
   if (dim <= 2) return 2;
   if (dim == 3) return 3;

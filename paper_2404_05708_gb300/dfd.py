@@ -81,6 +81,8 @@ _SIGS = {
     "dfd_pair_noalloc": [_INT, _INT, _INT, _VP, _I64, _VP, _I64, _VP, _VP, _VP],
     "dfd_batch": [_VP, _INT, _INT, _VP, _VP, _I64, _VP, _I64, _VP, _VP, _VP],
     "dfd_batch_host": [_VP, _INT, _INT, _VP, _VP, _I64, _VP, _I64, _VP, _VP],
+    "dfd_batch_autotune": [_VP, _INT, _INT, _VP, _VP, _I64, _VP, _I64, _VP, _VP, ctypes.POINTER(ctypes.c_int), _VP],
+    "dfd_batch_set_order": [_VP, _INT, _INT, _INT],
     "dfd_matrix": [_VP, _INT, _INT, _VP, _VP, _I64, _VP, _VP, _VP],
     "dfd_batch_decide": [_VP, _INT, _INT, _VP, _VP, _I64, _VP, _I64, _VP, ctypes.c_double, _VP, _VP, _VP, _VP],
     "dfd_mc_pair": [_VP, _INT, _VP, _I64, _VP, _I64, _VP, _VP, ctypes.c_float, ctypes.c_float, _I64, _VP, _VP, _VP],
@@ -548,6 +550,29 @@ class Context:
         s = stream if stream is not None else torch.cuda.current_stream(self.device).cuda_stream
         _check(dfd_batch(*args, s), "dfd_batch")
         return out_dist, out_dist2
+
+    def batch_autotune(self, points, offsets, pairs, stream=None):
+        """Time both packing orders of the ragged batch on these pairs (device
+        tensors), keep the faster for their (dtype, dim class); returns it (0 or 1)."""
+        torch = _torch()
+        points = _curve(points)
+        dt = _dtype_code(points)
+        offsets, pairs = offsets.contiguous(), pairs.contiguous()
+        if offsets.dtype != torch.int64 or pairs.dtype != torch.int32:
+            raise TypeError("offsets must be int64 and pairs int32")
+        n_pairs = pairs.numel() // 2
+        out_dist, out_dist2 = self._batch_outs(dt, n_pairs, None, None)
+        best = ctypes.c_int(0)
+        s = stream if stream is not None else torch.cuda.current_stream(self.device).cuda_stream
+        _check(load_library().dfd_batch_autotune(self.handle, dt, points.shape[1], points.data_ptr(),
+                                                 offsets.data_ptr(), offsets.numel() - 1, pairs.data_ptr(), n_pairs,
+                                                 out_dist.data_ptr(), out_dist2.data_ptr(), ctypes.byref(best), s),
+               "dfd_batch_autotune")
+        return best.value
+
+    def set_batch_order(self, dtype: int, dim: int, order: int):
+        """Set the ragged batch's packing order (0 variant-major, 1 cost-descending)."""
+        _check(load_library().dfd_batch_set_order(self.handle, dtype, dim, order), "dfd_batch_set_order")
 
     def batch_host(self, points, offsets, pairs, out_dist=None, out_dist2=None):
         """dfd_batch on host (numpy) arrays, synchronous; returns (dist, dist2).

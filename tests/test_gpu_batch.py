@@ -194,6 +194,29 @@ def test_batch_host_slices_without_pairs_and_checks():
     ctx.close()
 
 
+@pytest.mark.parametrize("dtype,dim", [("i32", 2), ("f32", 3)])
+def test_batch_packing_orders_agree_and_autotune(dctx, dtype, dim):
+    """Both packing orders give identical results; the autotuner keeps one."""
+    from paper_2404_05708_gb300 import dfd
+    code = dfd.DFD_I32 if dtype == "i32" else dfd.DFD_F32
+    b = ragged_edges(dtype, dim, 140 + dim)
+    outs = []
+    for order in (0, 1):
+        dctx.set_batch_order(code, dim, order)
+        outs.append(run_batch(dctx, b))
+    assert np.array_equal(outs[0][1], outs[1][1]) and np.array_equal(outs[0][0], outs[1][0])
+    best = dctx.batch_autotune(dev(b.points), dev(b.offsets), dev(b.pairs))
+    assert best in (0, 1)
+    d, d2 = run_batch(dctx, b)
+    assert np.array_equal(d2, outs[0][1])
+    if dtype == "i32":
+        ref, _ = oracle.batch(b.points, b.offsets, b.pairs)
+        assert np.array_equal(d2, ref)
+    else:
+        check_f32(d, d2, b)
+    dctx.set_batch_order(code, dim, 0)
+
+
 def test_batch_graph_replay_updates_with_buffers(dctx):
     b = workloads.ragged_int_batch(n_pairs=3000, seed=41)
     pts, off, pr = dev(b.points), dev(b.offsets), dev(b.pairs)
