@@ -508,17 +508,38 @@ __device__ __forceinline__ bool narrow_pair(const int* __restrict__ bbox, int dk
 
 // Per-curve bounding boxes (one warp per curve) of int32 points, and the
 // coordinate range check (|c| <= lim) when `check` is set, for curves
-// [first, n_curves).
+// [first, n_curves).  Every lane issues BoxLoads<DK> point loads per round
+// before it reduces any, so a round of 32 * BoxLoads points costs one memory
+// round trip (indices past the curve's end read its last point again, which
+// changes neither the box nor the check), and the next curve's offsets are
+// read while the current curve is reduced.  (A loop of one load per
+// iteration left each warp waiting on DRAM for every 32 points: 2 TB/s.)
 template <int DK>
+struct BoxLoads {
+  static constexpr int value = DK <= 2 ? 8 : DK <= 4 ? 4 : DK <= 8 ? 2 : 1;
+};
+
+template <int DK, bool VEC>
 __global__ void curve_bbox_kernel(const int32_t* __restrict__ pts, const int64_t* __restrict__ offsets,
-                                  int64_t first, int64_t n_curves, int dim, int vec, int check, long long lim,
-                                  int* bbox, int* err) {
+                                  int64_t first, int64_t n_curves, int dim, int check, long long lim, int* bbox,
+                                  int* err) {
+  constexpr int NL = BoxLoads<DK>::value;
   const int L = threadIdx.x & 31;
   const int64_t total = offsets[n_curves];
+  const int64_t wstride = ((int64_t)gridDim.x * blockDim.x) >> 5;
   bool bad = false;
-  for (int64_t c = first + (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5); c < n_curves;
-       c += ((int64_t)gridDim.x * blockDim.x) >> 5) {
-    const int64_t o = offsets[c], e = offsets[c + 1];
+  int64_t c = first + (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  int64_t o = 0, e = 0;
+  if (c < n_curves) {
+    o = offsets[c];
+    e = offsets[c + 1];
+  }
+  for (; c < n_curves; c += wstride) {
+    int64_t on = 0, en = 0;
+    if (c + wstride < n_curves) {
+      on = offsets[c + wstride];
+      en = offsets[c + wstride + 1];
+    }
     int lo[DK], hi[DK];
 #pragma unroll
     for (int k = 0; k < DK; ++k) {
@@ -526,16 +547,21 @@ __global__ void curve_bbox_kernel(const int32_t* __restrict__ pts, const int64_t
       hi[k] = INT_MIN;
     }
     if (o >= 0 && e <= total && o < e) {
-      const int32_t* Q = pts + o * dim;
-#pragma unroll 4
-      for (int64_t j = L; j < e - o; j += 32) {
-        int32_t qk[DK];
-        load_point<int32_t, DK>(Q, (int)j, dim, vec != 0, qk);
+      const int64_t len = e - o;
+      for (int64_t j0 = 0; j0 < len; j0 += 32 * NL) {
+        const int32_t* Q = pts + (o + j0) * dim;
+        const int last = (int)min(len - 1 - j0, (int64_t)(32 * NL - 1));
+        int32_t qk[NL][DK];
 #pragma unroll
-        for (int k = 0; k < DK; ++k) {
-          lo[k] = min(lo[k], qk[k]);
-          hi[k] = max(hi[k], qk[k]);
-          if (check && k < dim) bad |= qk[k] < -lim || qk[k] > lim;
+        for (int u = 0; u < NL; ++u) load_point<int32_t, DK>(Q, min(32 * u + L, last), dim, VEC, qk[u]);
+#pragma unroll
+        for (int u = 0; u < NL; ++u) {
+#pragma unroll
+          for (int k = 0; k < DK; ++k) {
+            lo[k] = min(lo[k], qk[u][k]);
+            hi[k] = max(hi[k], qk[u][k]);
+            if (check && k < dim) bad |= qk[u][k] < -lim || qk[u][k] > lim;
+          }
         }
       }
     }
@@ -554,6 +580,8 @@ __global__ void curve_bbox_kernel(const int32_t* __restrict__ pts, const int64_t
         bbox[(c * DK + k) * 2 + 1] = hi[k];
       }
     }
+    o = on;
+    e = en;
   }
   if (__any_sync(0xffffffffu, bad) && L == 0) raise_error(err, DFD_ERR_RANGE);
 }
@@ -608,49 +636,89 @@ struct PlanArgs {
   int rmax;            // rows per lane of one stripe for this dimension class
 };
 
+// The counting sort's atomics are aggregated per warp: the lanes of a warp
+// that fall in one bucket add their count with one atomic (hist) or take
+// consecutive slots from one (scatter), since a batch's pairs crowd into a
+// few buckets.  Each warp walks the pairs 32 at a time with all lanes
+// together, so the match covers the whole warp.
 // (static: this header is compiled into several translation units)
 static __global__ void plan_hist_kernel(PlanArgs a) {
-  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < a.n_pairs; k += (int64_t)gridDim.x * blockDim.x) {
-    const int32_t ia = a.pairs[2 * k], ib = a.pairs[2 * k + 1];
-    int b = NBUCKET1 - 1;   // invalid pairs: last of the int64 class (skipped by the kernel)
-    if (ia < 0 || ib < 0 || ia >= a.n_curves || ib >= a.n_curves) {
-      raise_error(a.err, DFD_ERR_INVALID_ARG);
-    } else {
-      const int64_t total = a.offsets[a.n_curves];
-      const int64_t oa = a.offsets[ia], ob = a.offsets[ib], ea = a.offsets[ia + 1], eb = a.offsets[ib + 1];
-      const int64_t na = ea - oa, nb = eb - ob;
-      if (na < 1 || nb < 1 || oa < 0 || ob < 0 || ea > total || eb > total || na > INT32_MAX || nb > INT32_MAX)
+  const int L = threadIdx.x & 31;
+  const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t wstride = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t k0 = 32 * w0; k0 < a.n_pairs; k0 += 32 * wstride) {
+    const int64_t k = k0 + L;
+    int b = -1;
+    if (k < a.n_pairs) {
+      const int32_t ia = a.pairs[2 * k], ib = a.pairs[2 * k + 1];
+      b = NBUCKET1 - 1;   // invalid pairs: last of the int64 class (skipped by the kernel)
+      if (ia < 0 || ib < 0 || ia >= a.n_curves || ib >= a.n_curves) {
         raise_error(a.err, DFD_ERR_INVALID_ARG);
-      const int64_t rows = max(min(na, nb), (int64_t)1), cols = max(max(na, nb), (int64_t)1);
-      b = a.order ? cost_bucket_lpt(rows, cols, a.rmax) : cost_bucket(rows, cols, a.rmax);
-      if (a.bbox && narrow_pair(a.bbox, a.dk, ia, ib)) b += NBUCKET1;
+      } else {
+        const int64_t total = a.offsets[a.n_curves];
+        const int64_t oa = a.offsets[ia], ob = a.offsets[ib], ea = a.offsets[ia + 1], eb = a.offsets[ib + 1];
+        const int64_t na = ea - oa, nb = eb - ob;
+        if (na < 1 || nb < 1 || oa < 0 || ob < 0 || ea > total || eb > total || na > INT32_MAX || nb > INT32_MAX)
+          raise_error(a.err, DFD_ERR_INVALID_ARG);
+        const int64_t rows = max(min(na, nb), (int64_t)1), cols = max(max(na, nb), (int64_t)1);
+        b = a.order ? cost_bucket_lpt(rows, cols, a.rmax) : cost_bucket(rows, cols, a.rmax);
+        if (a.bbox && narrow_pair(a.bbox, a.dk, ia, ib)) b += NBUCKET1;
+      }
+      a.bucket[k] = (unsigned short)b;
     }
-    a.bucket[k] = (unsigned short)b;
-    atomicAdd(&a.hist[b], 1u);
+    const unsigned peers = __match_any_sync(0xffffffffu, b);
+    if (b >= 0 && L == __ffs(peers) - 1) atomicAdd(&a.hist[b], (unsigned)__popc(peers));
   }
 }
 
+// One block of NBUCKET threads: exclusive scan of the bucket counts into
+// the cursors (a shuffle scan per warp, then over the warp totals).
 static __global__ void plan_scan_kernel(PlanArgs a) {
-  // one warp: exclusive scan of NBUCKET counts into cursors
-  if (threadIdx.x == 0) {
-    unsigned run = 0;
-    for (int b = 0; b < NBUCKET; ++b) {
-      a.cursor[b] = run;
-      run += a.hist[b];
-    }
+  static_assert(NBUCKET % 32 == 0 && NBUCKET / 32 <= 32 && NBUCKET <= 1024, "one block, one warp of warp totals");
+  __shared__ unsigned wsum[NBUCKET / 32];
+  const int b = threadIdx.x, L = b & 31, w = b >> 5;
+  const unsigned x = a.hist[b];
+  unsigned inc = x;
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const unsigned y = __shfl_up_sync(0xffffffffu, inc, off);
+    if (L >= off) inc += y;
   }
+  if (L == 31) wsum[w] = inc;
+  __syncthreads();
+  if (w == 0) {
+    unsigned t = L < NBUCKET / 32 ? wsum[L] : 0u;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const unsigned y = __shfl_up_sync(0xffffffffu, t, off);
+      if (L >= off) t += y;
+    }
+    if (L < NBUCKET / 32) wsum[L] = t;   // inclusive totals through warp L
+  }
+  __syncthreads();
+  a.cursor[b] = (w > 0 ? wsum[w - 1] : 0u) + inc - x;
 }
 
 static __global__ void plan_scatter_kernel(PlanArgs a) {
-  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < a.n_pairs; k += (int64_t)gridDim.x * blockDim.x) {
-    const unsigned pos = atomicAdd(&a.cursor[a.bucket[k]], 1u);
+  const int L = threadIdx.x & 31;
+  const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t wstride = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t k0 = 32 * w0; k0 < a.n_pairs; k0 += 32 * wstride) {
+    const int64_t k = k0 + L;
+    const int b = k < a.n_pairs ? (int)a.bucket[k] : -1;
+    const unsigned peers = __match_any_sync(0xffffffffu, b);
+    const int leader = __ffs(peers) - 1;
+    unsigned pos = 0;
+    if (b >= 0 && L == leader) pos = atomicAdd(&a.cursor[b], (unsigned)__popc(peers));
+    pos = __shfl_sync(0xffffffffu, pos, leader) + __popc(peers & ((1u << L) - 1u));
+    if (b < 0) continue;
     const int32_t ia = a.pairs[2 * k], ib = a.pairs[2 * k + 1];
     unsigned swap = 0;
     if (ia >= 0 && ib >= 0 && ia < a.n_curves && ib < a.n_curves) {
       const int64_t na = a.offsets[ia + 1] - a.offsets[ia], nb = a.offsets[ib + 1] - a.offsets[ib];
       swap = na > nb ? 1u : 0u;   // rows = the shorter curve
     }
-    const unsigned narrow = a.bucket[k] >= NBUCKET1 ? kNarrowBit : 0u;
+    const unsigned narrow = b >= NBUCKET1 ? kNarrowBit : 0u;
     a.worklist[pos] = (unsigned)k | narrow | (swap << 31);
   }
 }

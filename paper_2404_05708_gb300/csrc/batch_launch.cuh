@@ -51,10 +51,14 @@ void launch_curve_bbox(dfd_context* ctx, const void* points, const int64_t* offs
   const int64_t warps_needed = n_curves - first;
   if (warps_needed < 1) return;
   const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((warps_needed + 7) / 8, 16 * (int64_t)ctx->num_sms));
-  batch::curve_bbox_kernel<DK><<<blocks, 256, 0, s>>>(static_cast<const int32_t*>(points), offsets, first, n_curves,
-                                                      dim, vector_loads_ok<DK>(points, dim),
-                                                      ctx->opt.check_inputs ? 1 : 0, int32_coord_limit(dim), bbox,
-                                                      ctx->d_err);
+  const int32_t* pts = static_cast<const int32_t*>(points);
+  const int check = ctx->opt.check_inputs ? 1 : 0;
+  if (vector_loads_ok<DK>(points, dim))
+    batch::curve_bbox_kernel<DK, true><<<blocks, 256, 0, s>>>(pts, offsets, first, n_curves, dim, check,
+                                                              int32_coord_limit(dim), bbox, ctx->d_err);
+  else
+    batch::curve_bbox_kernel<DK, false><<<blocks, 256, 0, s>>>(pts, offsets, first, n_curves, dim, check,
+                                                               int32_coord_limit(dim), bbox, ctx->d_err);
 }
 
 template <class K>
@@ -118,7 +122,7 @@ dfd_status batch_prepare(dfd_context* ctx, int dim, const void* points, const in
   pa.order = ctx->batch_order[std::is_same<V, F32>::value ? 0 : 1][dim_class_index(DK)];
   const int pblocks = (int)std::min<int64_t>((n_pairs + 255) / 256, 8 * (int64_t)ctx->num_sms);
   batch::plan_hist_kernel<<<pblocks, 256, 0, s>>>(pa);
-  batch::plan_scan_kernel<<<1, 32, 0, s>>>(pa);
+  batch::plan_scan_kernel<<<1, batch::NBUCKET, 0, s>>>(pa);
   batch::plan_scatter_kernel<<<pblocks, 256, 0, s>>>(pa);
   ba->rowbuf = base + off_buf;
   ba->points = points;

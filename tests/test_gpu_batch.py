@@ -247,6 +247,37 @@ def test_batch_invalid_ids_are_reported(dctx):
     assert dctx.get_error() == 0
 
 
+@pytest.mark.parametrize("dim", [2, 3, 8])
+def test_batch_int_range_check(dctx, dim):
+    # |c| <= 2^30 - 1 (dim 2) or less is required of every coordinate; the
+    # per-curve boxes decide it, so a coordinate outside must be reported
+    # wherever it sits: the first point, past the first load round of a long
+    # curve, the last point, either sign.
+    lens = np.array([5, 300, 700, 33, 1000], np.int64)
+    off = np.concatenate([[0], np.cumsum(lens)]).astype(np.int64)
+    rng = np.random.default_rng(60 + dim)
+    base = np.cumsum(rng.integers(-64, 65, size=(off[-1], dim)), axis=0).astype(np.int32)
+    pairs = np.array([[0, 1], [2, 3], [4, 0], [1, 2]], np.int32)
+    outside = (1 << 30) + 5
+    for row, k, val in [(0, 0, outside), (off[1] + 299, dim - 1, -outside), (off[2] + 650, 1, outside),
+                        (off[-1] - 1, 0, -outside), (off[4] + 513, dim - 1, 2 ** 31 - 1)]:
+        pts = base.copy()
+        pts[row, k] = val
+        dctx.batch(dev(pts), dev(off), dev(pairs))
+        torch.cuda.synchronize()
+        assert dctx.get_error() == 2, (row, k, val)   # DFD_ERR_RANGE, then cleared
+        assert dctx.get_error() == 0
+    # large coordinates inside the limit run (int64 class) and stay exact
+    pts = base.copy()
+    pts[off[1] + 299, 0] = 1 << 28
+    pts[off[4] + 999, dim - 1] = -(1 << 28)
+    b = workloads.Batch(points=pts, offsets=off, pairs=pairs)
+    d, d2 = run_batch(dctx, b)
+    assert dctx.get_error() == 0
+    want, _ = oracle.batch(b.points, b.offsets, b.pairs)
+    assert np.array_equal(d2, want)
+
+
 # ----------------------------------------------------------------- matrix
 
 def condensed_oracle(b):
