@@ -514,6 +514,9 @@ __device__ __forceinline__ bool narrow_pair(const int* __restrict__ bbox, int dk
 // changes neither the box nor the check), and the next curve's offsets are
 // read while the current curve is reduced.  (A loop of one load per
 // iteration left each warp waiting on DRAM for every 32 points: 2 TB/s.)
+// The range check reads the box, not every point: all |c| <= lim exactly
+// when the box lies within [-lim, lim] (a check per coordinate against the
+// 64-bit limit kept the kernel issue-bound, at a third of DRAM bandwidth).
 template <int DK>
 struct BoxLoads {
   static constexpr int value = DK <= 2 ? 8 : DK <= 4 ? 4 : DK <= 8 ? 2 : 1;
@@ -560,10 +563,14 @@ __global__ void curve_bbox_kernel(const int32_t* __restrict__ pts, const int64_t
           for (int k = 0; k < DK; ++k) {
             lo[k] = min(lo[k], qk[u][k]);
             hi[k] = max(hi[k], qk[u][k]);
-            if (check && k < dim) bad |= qk[u][k] < -lim || qk[u][k] > lim;
           }
         }
       }
+    }
+    if (check) {
+#pragma unroll
+      for (int k = 0; k < DK; ++k)
+        if (k < dim) bad |= (long long)lo[k] < -lim || (long long)hi[k] > lim;   // empty: lo > hi, passes
     }
 #pragma unroll
     for (int k = 0; k < DK; ++k) {
