@@ -285,11 +285,14 @@ dfd_status dfd_batch_set_order(dfd_context* ctx, dfd_dtype dtype, int dim, int o
 /*
  * dfd_batch with HOST buffers (points, offsets, pairs and the outputs are
  * host pointers; outputs may be NULL, not both): synchronous.  The points
- * are copied to the device in up to 8 slices of curves (about 128 MiB each)
+ * are copied to the device in up to 8 slices of curves (about 64 MiB each)
  * on a copy stream, directly when they are page-locked and through the
  * context's pinned staging area otherwise; the pairs are grouped by the
  * slice of their later curve and each group runs as soon as its slice has
- * landed, so the copies overlap the computation.  Results are bit-identical
+ * landed, so the copies overlap the computation (launches alternate between
+ * two internal streams, so one launch's start overlaps the end of the one
+ * before).  The device staging holds the points, the results and two batch
+ * scratch areas (grow-only, freed at destroy).  Results are bit-identical
  * to dfd_batch on the same data.  Offsets must be nondecreasing and every
  * id in [0, n_curves) (checked on the host: DFD_ERR_INVALID_ARG); the
  * device-side checks are dfd_batch's, returned directly.  Uses the context's

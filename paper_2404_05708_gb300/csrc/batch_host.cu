@@ -6,13 +6,18 @@
 // The pairs are grouped by the slice of their later curve (a counting sort
 // on the host); slice k's group runs as one batch launch over curves
 // [0, end_k) as soon as slice k has landed, so the copy of slice k+1 overlaps
-// it.  Each launch boxes and checks only the curves no earlier launch
-// covered (the int32 bounding boxes live in one buffer for the whole
-// batch), and the last launch waits for every slice and covers all curves,
-// so the input checks are those of dfd_batch.  Results are bit-identical to
-// dfd_batch on the same data: each pair is computed by the same engine.
+// it.  Launches alternate between two streams, each with its own scratch
+// area, so a launch's bounding boxes, work list and first pairs start while
+// the one before finishes its longest pairs.  Each launch boxes and checks
+// only the curves no earlier launch covered (the int32 bounding boxes live
+// in one buffer for the whole batch, and a launch waits until the one before
+// has built its boxes), and the last launch waits for every slice and covers
+// all curves, so the input checks are those of dfd_batch.  Results are
+// bit-identical to dfd_batch on the same data: each pair is computed by the
+// same engine.
 #include <algorithm>
 #include <cstring>
+#include <memory>
 #include <vector>
 
 #include "batch_launch.cuh"
@@ -22,7 +27,8 @@ namespace dfd {
 #define DFD_RANGE_EXTERN(V, DK)                                                                                 \
   extern template dfd_status batch_launch_range<V, DK>(dfd_context*, int, const void*, const int64_t*, int64_t, \
                                                        const int32_t*, int64_t, void*, void*, cudaStream_t,     \
-                                                       int64_t, int*);
+                                                       int64_t, int*, char*, size_t, cudaEvent_t);              \
+  extern template size_t batch_scratch_bytes<V, DK>(dfd_context*, int64_t, int64_t, bool);
 DFD_RANGE_EXTERN(F32, 2)
 DFD_RANGE_EXTERN(F32, 3)
 DFD_RANGE_EXTERN(F32, 4)
@@ -37,28 +43,29 @@ DFD_RANGE_EXTERN(I32, 16)
 
 namespace {
 
-// Points per copy slice (about).  Every slice's launch ends on the tail of
-// its longest pairs, and the first slice's copy is not overlapped: on the
-// 65,536-pair int32 batch (277 MB) 3 slices of 128 MB ran at 1.75 Tcell/s
-// end to end, 6 of 48 MB at 1.67 (one launch after one copy: 1.52).
-constexpr size_t kSliceBytes = (size_t)128 << 20;
+// Points per copy slice (about).  The first slice's copy is not overlapped,
+// and each launch adds its pre-pass and the tail of its longest pairs (half
+// hidden by the next launch on the other stream): on the 65,536-pair int32
+// batch (277 MB) slices of 128, 64, 48 and 32 MB ran at 1.94, 1.95, 1.92
+// and 1.84 Tcell/s end to end.
+constexpr size_t kSliceBytes = (size_t)64 << 20;
 
 dfd_status range_run(dfd_context* ctx, dfd_dtype dtype, int dim, const void* points, const int64_t* offsets,
                      int64_t n_curves, const int32_t* pairs, int64_t n_pairs, void* out_dist, void* out_dist2,
-                     cudaStream_t s, int64_t first, int* bbox) {
-#define DFD_R_DK(V)                                                                                              \
-  switch (dim_class(dim)) {                                                                                      \
-    case 2: return batch_launch_range<V, 2>(ctx, dim, points, offsets, n_curves, pairs, n_pairs, out_dist,       \
-                                            out_dist2, s, first, bbox);                                          \
-    case 3: return batch_launch_range<V, 3>(ctx, dim, points, offsets, n_curves, pairs, n_pairs, out_dist,       \
-                                            out_dist2, s, first, bbox);                                          \
-    case 4: return batch_launch_range<V, 4>(ctx, dim, points, offsets, n_curves, pairs, n_pairs, out_dist,       \
-                                            out_dist2, s, first, bbox);                                          \
-    case 8: return batch_launch_range<V, 8>(ctx, dim, points, offsets, n_curves, pairs, n_pairs, out_dist,       \
-                                            out_dist2, s, first, bbox);                                          \
-    case 16: return batch_launch_range<V, 16>(ctx, dim, points, offsets, n_curves, pairs, n_pairs, out_dist,     \
-                                              out_dist2, s, first, bbox);                                        \
-    default: return DFD_ERR_UNSUPPORTED;                                                                         \
+                     cudaStream_t s, int64_t first, int* bbox, char* scratch, size_t scratch_bytes,
+                     cudaEvent_t prepared) {
+#define DFD_R_CASE(V, DK)                                                                                       \
+  case DK:                                                                                                      \
+    return batch_launch_range<V, DK>(ctx, dim, points, offsets, n_curves, pairs, n_pairs, out_dist, out_dist2, s, \
+                                     first, bbox, scratch, scratch_bytes, prepared);
+#define DFD_R_DK(V)                                                                                          \
+  switch (dim_class(dim)) {                                                                                  \
+    DFD_R_CASE(V, 2)                                                                                         \
+    DFD_R_CASE(V, 3)                                                                                         \
+    DFD_R_CASE(V, 4)                                                                                         \
+    DFD_R_CASE(V, 8)                                                                                         \
+    DFD_R_CASE(V, 16)                                                                                        \
+    default: return DFD_ERR_UNSUPPORTED;                                                                     \
   }
   if (dtype == DFD_F32) {
     DFD_R_DK(F32)
@@ -66,6 +73,29 @@ dfd_status range_run(dfd_context* ctx, dfd_dtype dtype, int dim, const void* poi
     DFD_R_DK(I32)
   }
 #undef DFD_R_DK
+#undef DFD_R_CASE
+}
+
+// Scratch bytes of one slice launch (at most n_pairs pairs); 0: unsupported.
+size_t range_scratch(dfd_context* ctx, dfd_dtype dtype, int dim, int64_t n_curves, int64_t n_pairs) {
+#define DFD_S_CASE(V, DK) \
+  case DK: return batch_scratch_bytes<V, DK>(ctx, n_curves, n_pairs, true);
+#define DFD_S_DK(V)          \
+  switch (dim_class(dim)) {  \
+    DFD_S_CASE(V, 2)         \
+    DFD_S_CASE(V, 3)         \
+    DFD_S_CASE(V, 4)         \
+    DFD_S_CASE(V, 8)         \
+    DFD_S_CASE(V, 16)        \
+    default: return 0;       \
+  }
+  if (dtype == DFD_F32) {
+    DFD_S_DK(F32)
+  } else {
+    DFD_S_DK(I32)
+  }
+#undef DFD_S_DK
+#undef DFD_S_CASE
 }
 
 bool page_locked(const void* x) {
@@ -109,21 +139,25 @@ extern "C" dfd_status dfd_batch_host(dfd_context* ctx, dfd_dtype dtype, int dim,
     bound[k] = std::min(std::max(bound[k], bound[k - 1]), n_curves);
   }
 
-  // pinned staging: [offsets | pairs (grouped) | dist | dist2 | points if pageable]
+  // pinned staging: [offsets | pairs (grouped) | dist | dist2 | error word | points if pageable]
   const bool pts_locked = page_locked(points);
   const size_t off_b = align_up((size_t)(n_curves + 1) * 8, 256);
   const size_t pair_b = align_up((size_t)n_pairs * 8, 256);
   const size_t dist_b = align_up((size_t)n_pairs * d1, 256), dist2_b = align_up((size_t)n_pairs * d2, 256);
-  const size_t host_bytes = off_b + pair_b + dist_b + dist2_b + (pts_locked ? 0 : align_up(pts_bytes, 256));
+  const size_t host_bytes = off_b + pair_b + dist_b + dist2_b + 256 + (pts_locked ? 0 : align_up(pts_bytes, 256));
   if ((st = ensure_pinned(ctx, host_bytes)) != DFD_OK) return st;
   char* h = static_cast<char*>(ctx->pinned);
-  char* h_pts = pts_locked ? nullptr : h + off_b + pair_b + dist_b + dist2_b;
+  int* h_err = reinterpret_cast<int*>(h + off_b + pair_b + dist_b + dist2_b);
+  char* h_pts = pts_locked ? nullptr : h + off_b + pair_b + dist_b + dist2_b + 256;
   if (!pts_locked) std::memcpy(h_pts, points, pts_bytes);
   const char* src_pts = pts_locked ? static_cast<const char*>(points) : h_pts;
 
-  // device (the context's staging buffer): [points | offsets | pairs | bbox | dist | dist2]
+  // device (the context's staging buffer):
+  //   [points | offsets | pairs | bbox | dist | dist2 | scratch 0 | scratch 1]
   const size_t bbox_b = f32 ? 0 : align_up((size_t)n_curves * dim_class(dim) * 2 * 4, 256);
-  const size_t dev_bytes = align_up(pts_bytes, 256) + off_b + pair_b + bbox_b + dist_b + dist2_b;
+  const size_t scr_b = align_up(range_scratch(ctx, dtype, dim, n_curves, n_pairs), 256);
+  if (scr_b == 0) return DFD_ERR_UNSUPPORTED;
+  const size_t dev_bytes = align_up(pts_bytes, 256) + off_b + pair_b + bbox_b + dist_b + dist2_b + 2 * scr_b;
   if ((st = ensure_io(ctx, dev_bytes)) != DFD_OK) return st;
   char* d = static_cast<char*>(ctx->io);
   char* d_pts = d;
@@ -132,6 +166,7 @@ extern "C" dfd_status dfd_batch_host(dfd_context* ctx, dfd_dtype dtype, int dim,
   int* d_bbox = f32 ? nullptr : reinterpret_cast<int*>(reinterpret_cast<char*>(d_pairs) + pair_b);
   char* d_dist = reinterpret_cast<char*>(d_pairs) + pair_b + bbox_b;
   char* d_dist2 = d_dist + dist_b;
+  char* d_scr[2] = {d_dist2 + dist2_b, d_dist2 + dist2_b + scr_b};
   cudaStream_t s = ctx->stream;
   if (!ctx->copy_stream) {
     if (cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking) != cudaSuccess) {
@@ -146,6 +181,20 @@ extern "C" dfd_status dfd_batch_host(dfd_context* ctx, dfd_dtype dtype, int dim,
       }
     }
   }
+  if (!ctx->launch_stream2) {
+    if (cudaStreamCreateWithFlags(&ctx->launch_stream2, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaGetLastError();
+      ctx->launch_stream2 = nullptr;
+      return DFD_ERR_CUDA;
+    }
+    for (cudaEvent_t* e : {&ctx->prep_ev[0], &ctx->prep_ev[1], &ctx->join_ev}) {
+      if (cudaEventCreateWithFlags(e, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        return DFD_ERR_CUDA;
+      }
+    }
+  }
+  cudaStream_t ls[2] = {s, ctx->launch_stream2};
 
   // Every host-to-device copy goes through the copy stream, in the order
   // the launches need it (copies in one direction are served in order):
@@ -165,7 +214,7 @@ extern "C" dfd_status dfd_batch_host(dfd_context* ctx, dfd_dtype dtype, int dim,
 
   // 2. on the host meanwhile: check the ids and group the pairs by the slice
   // of their later curve (stable counting sort)
-  std::vector<int> slice_of(n_pairs);
+  std::unique_ptr<int[]> slice_of(new int[n_pairs]);   // (no zero fill: every entry is written)
   std::vector<int64_t> start(K + 1, 0);
   bool bad_id = false;
   for (int64_t i = 0; i < n_pairs; ++i) {
@@ -189,7 +238,7 @@ extern "C" dfd_status dfd_batch_host(dfd_context* ctx, dfd_dtype dtype, int dim,
   for (int k = 0; k < K; ++k) start[k + 1] += start[k];
   std::memcpy(h, offsets, (size_t)(n_curves + 1) * 8);
   int32_t* hp = reinterpret_cast<int32_t*>(h + off_b);
-  std::vector<int32_t> perm(n_pairs);   // grouped position -> caller's pair index
+  std::unique_ptr<int32_t[]> perm(new int32_t[n_pairs]);   // grouped position -> caller's pair index
   {
     std::vector<int64_t> cur(start.begin(), start.end() - 1);
     for (int64_t i = 0; i < n_pairs; ++i) {
@@ -207,23 +256,30 @@ extern "C" dfd_status dfd_batch_host(dfd_context* ctx, dfd_dtype dtype, int dim,
   cudaMemcpyAsync(d_pairs, hp, (size_t)n_pairs * 8, cudaMemcpyHostToDevice, cs);
   cudaEventRecord(ctx->slice_ev[kMaxSlices], cs);
   cudaStreamWaitEvent(s, ctx->slice_ev[kMaxSlices], 0);
+  cudaStreamWaitEvent(ls[1], ctx->slice_ev[kMaxSlices], 0);
   for (int k = 1; k < K; ++k) copy_slice(k);
   int last = 0;   // the last slice with pairs: it waits for every slice and covers all curves
   for (int k = 0; k < K; ++k)
     if (start[k + 1] > start[k]) last = k;
   int64_t covered = 0;   // curves boxed / checked so far
+  int li = 0;            // launches issued: launch li runs on ls[li & 1] with scratch d_scr[li & 1]
   for (int k = 0; k <= last && st == DFD_OK; ++k) {
     const int64_t cnt = start[k + 1] - start[k];
     if (cnt == 0) continue;
     const bool final_launch = k == last;
+    cudaStream_t sk = ls[li & 1];
     for (int j = (final_launch ? 0 : k); j <= (final_launch ? K - 1 : k); ++j)
-      cudaStreamWaitEvent(s, ctx->slice_ev[j], 0);
+      cudaStreamWaitEvent(sk, ctx->slice_ev[j], 0);
+    if (li > 0) cudaStreamWaitEvent(sk, ctx->prep_ev[(li - 1) & 1], 0);   // boxes of the earlier curves
     const int64_t upto = final_launch ? n_curves : bound[k + 1];
     st = range_run(ctx, dtype, dim, d_pts, d_off, upto, d_pairs + 2 * start[k], cnt,
-                   out_dist ? d_dist + start[k] * d1 : nullptr, out_dist2 ? d_dist2 + start[k] * d2 : nullptr, s,
-                   covered, d_bbox);
+                   out_dist ? d_dist + start[k] * d1 : nullptr, out_dist2 ? d_dist2 + start[k] * d2 : nullptr, sk,
+                   covered, d_bbox, d_scr[li & 1], scr_b, ctx->prep_ev[li & 1]);
     covered = upto;
+    ++li;
   }
+  cudaEventRecord(ctx->join_ev, ls[1]);
+  cudaStreamWaitEvent(s, ctx->join_ev, 0);
   if (st == DFD_OK) {
     if (out_dist) cudaMemcpyAsync(h + off_b + pair_b, d_dist, (size_t)n_pairs * d1, cudaMemcpyDeviceToHost, s);
     if (out_dist2)
@@ -232,16 +288,16 @@ extern "C" dfd_status dfd_batch_host(dfd_context* ctx, dfd_dtype dtype, int dim,
   // s is ordered after every slice copy, whether or not a launch ran, so
   // the synchronisation below covers the copy stream too
   for (int k = 0; k < K; ++k) cudaStreamWaitEvent(s, ctx->slice_ev[k], 0);
+  *h_err = 0;
+  cudaMemcpyAsync(h_err, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost, s);
   if (cudaStreamSynchronize(s) != cudaSuccess) {
     cudaGetLastError();
     return DFD_ERR_CUDA;
   }
   if (st != DFD_OK) return st;
-  int err = 0;
-  cudaMemcpy(&err, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost);
-  if (err != 0) {
+  if (*h_err != 0) {
     cudaMemset(ctx->d_err, 0, sizeof(int));
-    return (dfd_status)err;
+    return (dfd_status)*h_err;
   }
   // 4. results back in the caller's pair order
   const char* r1 = h + off_b + pair_b;

@@ -78,25 +78,48 @@ int resident_blocks(const dfd_context* ctx, K kernel, int threads) {
 // buffer and only curves [first_curve, n_curves) are boxed and checked
 // (float32: only their points are checked): a batch run in slices of
 // curves, each slice covering the curves no earlier slice covered.
+// Scratch of one batch launch: [counter | hist | cursor] [bucket] [worklist]
+// [bbox] [row buffers].
+struct BatchLayout {
+  size_t off_hist, off_cursor, off_bucket, off_work, off_bbox, off_buf, total;
+};
+template <class V, int DK>
+BatchLayout batch_layout(int64_t n_curves, int64_t n_pairs, int blocks, bool bbox_ext) {
+  constexpr int THREADS = 256;
+  constexpr bool kInt = std::is_same<V, I32>::value;
+  BatchLayout l;
+  l.off_hist = 256;
+  l.off_cursor = l.off_hist + batch::NBUCKET * 4;
+  l.off_bucket = align_up(l.off_cursor + batch::NBUCKET * 4, 256);
+  l.off_work = align_up(l.off_bucket + (size_t)n_pairs * 2, 256);
+  l.off_bbox = align_up(l.off_work + (size_t)n_pairs * 4, 256);
+  l.off_buf = align_up(l.off_bbox + (kInt && !bbox_ext ? (size_t)n_curves * DK * 2 * 4 : 0), 256);
+  l.total = l.off_buf + (size_t)blocks * (THREADS / 32) * batch::BUF_COLS * sizeof(typename V::value);
+  return l;
+}
+
+// With `scratch_ext` the launch uses the caller's scratch area (at least
+// batch_scratch_bytes) instead of the context's, so launches on different
+// streams can run side by side.
 template <class V, int DK>
 dfd_status batch_prepare(dfd_context* ctx, int dim, const void* points, const int64_t* offsets, int64_t n_curves,
                          const int32_t* pairs, int64_t n_pairs, cudaStream_t s, int blocks, batch::BatchArgs* ba,
-                         int64_t first_curve = 0, int* bbox_ext = nullptr) {
-  using T = typename V::value;
-  constexpr int THREADS = 256;
-  const size_t warps = (size_t)blocks * (THREADS / 32);
+                         int64_t first_curve = 0, int* bbox_ext = nullptr, char* scratch_ext = nullptr,
+                         size_t scratch_ext_bytes = 0) {
   constexpr bool kInt = std::is_same<V, I32>::value;
   if (n_pairs >= (int64_t)batch::kNarrowBit) return DFD_ERR_UNSUPPORTED;
-  // scratch: [counter | hist | cursor] [bucket] [worklist] [bbox] [row buffers]
-  const size_t off_hist = 256, off_cursor = off_hist + batch::NBUCKET * 4;
-  const size_t off_bucket = align_up(off_cursor + batch::NBUCKET * 4, 256);
-  const size_t off_work = align_up(off_bucket + (size_t)n_pairs * 2, 256);
-  const size_t off_bbox = align_up(off_work + (size_t)n_pairs * 4, 256);
-  const size_t off_buf = align_up(off_bbox + (kInt && !bbox_ext ? (size_t)n_curves * DK * 2 * 4 : 0), 256);
-  const size_t total = off_buf + warps * batch::BUF_COLS * sizeof(T);
-  dfd_status st = ensure_scratch(ctx, total);
-  if (st != DFD_OK) return st;
-  char* base = static_cast<char*>(ctx->scratch);
+  const BatchLayout lay = batch_layout<V, DK>(n_curves, n_pairs, blocks, bbox_ext != nullptr);
+  const size_t off_cursor = lay.off_cursor, off_bucket = lay.off_bucket, off_work = lay.off_work;
+  const size_t off_bbox = lay.off_bbox, off_buf = lay.off_buf;
+  char* base = scratch_ext;
+  if (scratch_ext) {
+    if (lay.total > scratch_ext_bytes) return DFD_ERR_OOM;
+  } else {
+    const dfd_status st = ensure_scratch(ctx, lay.total);
+    if (st != DFD_OK) return st;
+    base = static_cast<char*>(ctx->scratch);
+  }
+  const size_t off_hist = lay.off_hist;
   cudaError_t e = cudaMemsetAsync(base, 0, off_bucket, s);
   if (e != cudaSuccess) return cuda_status(e);
   int* bbox = kInt ? (bbox_ext ? bbox_ext : reinterpret_cast<int*>(base + off_bbox)) : nullptr;
@@ -140,15 +163,26 @@ dfd_status batch_prepare(dfd_context* ctx, int dim, const void* points, const in
   return cuda_status(cudaGetLastError());
 }
 
+// Scratch bytes of one batch launch over `n_pairs` pairs of `n_curves`
+// curves (bounding boxes in the caller's buffer when `bbox_ext`).
+template <class V, int DK>
+size_t batch_scratch_bytes(dfd_context* ctx, int64_t n_curves, int64_t n_pairs, bool bbox_ext) {
+  return batch_layout<V, DK>(n_curves, n_pairs, resident_blocks(ctx, batch::batch_kernel<V, DK>, 256), bbox_ext).total;
+}
+
+// `prepared` (optional) is recorded on s once the bounding boxes and the
+// work list are built, before the batch kernel.
 template <class V, int DK>
 dfd_status batch_launch_range(dfd_context* ctx, int dim, const void* points, const int64_t* offsets,
                               int64_t n_curves, const int32_t* pairs, int64_t n_pairs, void* out_dist,
-                              void* out_dist2, cudaStream_t s, int64_t first_curve, int* bbox_ext) {
+                              void* out_dist2, cudaStream_t s, int64_t first_curve, int* bbox_ext,
+                              char* scratch_ext, size_t scratch_ext_bytes, cudaEvent_t prepared) {
   const int blocks = resident_blocks(ctx, batch::batch_kernel<V, DK>, 256);
   batch::BatchArgs ba;
   dfd_status st = batch_prepare<V, DK>(ctx, dim, points, offsets, n_curves, pairs, n_pairs, s, blocks, &ba,
-                                       first_curve, bbox_ext);
+                                       first_curve, bbox_ext, scratch_ext, scratch_ext_bytes);
   if (st != DFD_OK) return st;
+  if (prepared) cudaEventRecord(prepared, s);
   ba.out_dist = out_dist;
   ba.out_dist2 = out_dist2;
   timing_begin(ctx, s);
@@ -161,7 +195,7 @@ template <class V, int DK>
 dfd_status batch_launch(dfd_context* ctx, int dim, const void* points, const int64_t* offsets, int64_t n_curves,
                         const int32_t* pairs, int64_t n_pairs, void* out_dist, void* out_dist2, cudaStream_t s) {
   return batch_launch_range<V, DK>(ctx, dim, points, offsets, n_curves, pairs, n_pairs, out_dist, out_dist2, s, 0,
-                                   nullptr);
+                                   nullptr, nullptr, 0, nullptr);
 }
 
 template <class V, int DK>
@@ -234,7 +268,8 @@ dfd_status matrix_launch(dfd_context* ctx, int dim, const void* points, const in
                                                       const int32_t*, int64_t, void*, void*, cudaStream_t);        \
   template dfd_status dfd::batch_launch_range<dfd::V, DK>(dfd_context*, int, const void*, const int64_t*, int64_t, \
                                                             const int32_t*, int64_t, void*, void*, cudaStream_t,      \
-                                                            int64_t, int*);                                           \
+                                                            int64_t, int*, char*, size_t, cudaEvent_t);               \
+  template size_t dfd::batch_scratch_bytes<dfd::V, DK>(dfd_context*, int64_t, int64_t, bool);                       \
   template dfd_status dfd::decide_launch<dfd::V, DK>(dfd_context*, int, const void*, const int64_t*, int64_t,      \
                                                        const int32_t*, int64_t, const void*, double, void*, int32_t*, \
                                                        unsigned long long*, cudaStream_t);                            \

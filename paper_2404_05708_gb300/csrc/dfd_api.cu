@@ -438,6 +438,10 @@ dfd_status dfd_context_destroy(dfd_context* ctx) {
   if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
   for (cudaEvent_t e : ctx->slice_ev)
     if (e) cudaEventDestroy(e);
+  if (ctx->launch_stream2) cudaStreamDestroy(ctx->launch_stream2);
+  for (cudaEvent_t e : ctx->prep_ev)
+    if (e) cudaEventDestroy(e);
+  if (ctx->join_ev) cudaEventDestroy(ctx->join_ev);
   if (ctx->ev0) cudaEventDestroy(ctx->ev0);
   if (ctx->ev1) cudaEventDestroy(ctx->ev1);
   if (ctx->scratch) cudaFree(ctx->scratch);

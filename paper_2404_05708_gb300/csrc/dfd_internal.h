@@ -47,6 +47,9 @@ struct dfd_context {
   signed char batch_order[2][5] = {};         // batch packing order per (float32 / int32, dim class 2,3,4,8,16)
   cudaStream_t copy_stream = nullptr;         // dfd_batch_host: point slices (created on first use)
   cudaEvent_t slice_ev[dfd::kMaxSlices + 1] = {};   // one per slice, and one for the allocation
+  cudaStream_t launch_stream2 = nullptr;      // dfd_batch_host: every other slice launch
+  cudaEvent_t prep_ev[2] = {};                // dfd_batch_host: a launch's boxes and work list built
+  cudaEvent_t join_ev = nullptr;              // dfd_batch_host: launch_stream2's work done
 };
 
 namespace dfd {

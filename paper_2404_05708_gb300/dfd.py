@@ -585,14 +585,15 @@ class Context:
         offsets = np.ascontiguousarray(offsets, dtype=np.int64)
         pairs = np.ascontiguousarray(pairs, dtype=np.int32)
         n_pairs = pairs.size // 2
+        # (outputs need no zero fill: every entry is written)
         if points.dtype == np.float32:
             dt = DFD_F32
-            d1 = out_dist if out_dist is not None else np.zeros(n_pairs, np.float32)
-            d2 = out_dist2 if out_dist2 is not None else np.zeros(n_pairs, np.float32)
+            d1 = out_dist if out_dist is not None else np.empty(n_pairs, np.float32)
+            d2 = out_dist2 if out_dist2 is not None else np.empty(n_pairs, np.float32)
         elif points.dtype == np.int32:
             dt = DFD_I32
-            d1 = out_dist if out_dist is not None else np.zeros(n_pairs, np.float64)
-            d2 = out_dist2 if out_dist2 is not None else np.zeros(n_pairs, np.int64)
+            d1 = out_dist if out_dist is not None else np.empty(n_pairs, np.float64)
+            d2 = out_dist2 if out_dist2 is not None else np.empty(n_pairs, np.int64)
         else:
             raise TypeError("curves must be float32 or int32")
         _check(dfd_batch_host(self.handle, dt, points.shape[1], points.ctypes.data, offsets.ctypes.data,
