@@ -156,13 +156,43 @@ def test_batch_ragged_int_full_size(dctx):
 def test_batch_host_equals_device_batch(dctx):
     """dfd_batch_host (points copied in slices, pairs run per slice) equals
     dfd_batch bit for bit, from page-locked and from pageable points."""
-    b = workloads.ragged_int_batch()   # 277 MB of points: 8 copy slices
+    b = workloads.ragged_int_batch()   # 277 MB of points: several copy slices
     d_dev, d2_dev = run_batch(dctx, b)
     pinned = torch.from_numpy(b.points).pin_memory().numpy()
     for pts in (pinned, b.points):
         d, d2 = dctx.batch_host(pts, b.offsets, b.pairs)
         assert np.array_equal(d2, d2_dev), np.nonzero(d2 != d2_dev)[0][:10]
         assert np.array_equal(d, d_dev)
+
+
+def test_batch_host_boxes_across_slices(dctx):
+    """A pair whose curves sit in two copy slices takes its int32 value class
+    from boxes that two launches build (on two streams).  The same context
+    first runs small coordinates (every pair narrow), then the same curves
+    with every third one scaled by 4096 (pairs with it need the int64 class):
+    a launch that read the first call's boxes would take the narrow class and
+    overflow."""
+    b = workloads.ragged_int_batch(n_pairs=32768)   # 138 MB of points: three copy slices
+    n = b.n_curves
+    pairs = np.stack([np.arange(0, n - 1), np.arange(1, n)], 1).astype(np.int32)   # neighbours: every boundary
+    d, d2 = dctx.batch_host(b.points, b.offsets, pairs)
+    d_dev, d2_dev = run_batch(dctx, workloads.Batch(points=b.points, offsets=b.offsets, pairs=pairs))
+    assert np.array_equal(d2, d2_dev)
+    big = b.points.copy()
+    ln = np.diff(b.offsets)
+    scale = np.repeat(np.where(np.arange(n) % 3 == 0, 4096, 1), ln).astype(np.int32)
+    big *= scale[:, None]
+    bb = workloads.Batch(points=big, offsets=b.offsets, pairs=pairs)
+    d, d2 = dctx.batch_host(big, b.offsets, pairs)
+    d_dev, d2_dev = run_batch(dctx, bb)
+    assert np.array_equal(d2, d2_dev), np.nonzero(d2 != d2_dev)[0][:10]
+    # the pairs across each third of the points, against the oracle
+    cuts = np.searchsorted(b.offsets, [b.offsets[-1] * k // 3 for k in (1, 2)])
+    idx = np.unique(np.concatenate([np.arange(c - 3, c + 3) for c in cuts]))
+    want, _ = oracle.batch(big, b.offsets, pairs[idx])
+    assert np.array_equal(d2[idx], want)
+    scaled = (pairs[idx] % 3 == 0).any(axis=1)
+    assert scaled.any() and np.all(want[scaled] > 2 ** 31)   # these need the int64 class
 
 
 def test_batch_host_slices_without_pairs_and_checks():
