@@ -51,7 +51,7 @@ REF_SAMPLE = 20_000          # --impl reference: prefix per step
 # was taken on; any later source change reports null.
 TRAFFIC_BY_KERNEL_SHA: dict = {
     "9799fd99282b0741": 15759897,    # wave_kernel<F32, 3, 6>, long pair 200,000^2 (two fronts, 512-column q chunks)
-    "09fe397efc17d52f": 289231155,   # batch_kernel<I32, 2>, ragged batch of 65,536 pairs (graph launches)
+    "44f0d2c7b58cb5a2": 289341082,   # batch_kernel<I32, 2>, ragged batch of 65,536 pairs (graph launches)
 }
 
 
@@ -80,7 +80,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="long", choices=["long", "batch", "matrix", "pair2k", "serve", "knn", "next"])
+    ap.add_argument("--workload", default="long",
+                    choices=["long", "batch", "matrix", "pair2k", "serve", "knn", "next", "paper"])
     ap.add_argument("--rates", default="100,1000,3000,10000,20000,30000")
     ap.add_argument("--serve-seconds", type=float, default=2.0)
     ap.add_argument("--tick-cells", type=float, default=4e9, help="serve: cell budget of one tick")
@@ -739,6 +740,106 @@ def run_next(args):
     return 0
 
 
+def run_paper(args):
+    """The paper's own experiment shape (Sec. 4, Experiment 1), as context:
+    N pairs of 2-D float32 walks with steps uniform in {-1,0,1}^2, (i)
+    P = Q = 2^10 points with N = 2^5 ... 2^14 pairs, (ii) N = 2^10 pairs with
+    P = Q = 2^5 ... 2^14 points.  Each point runs as one dfd_batch launch
+    (one warp per pair; for P > 4096 with the row buffer widened to P).
+    From P = 2^12 on the same pairs also run through dfd_pair (the band
+    wavefront), one launch per pair, spread over 16 contexts each on its own
+    stream so that several pairs share the GPU.  L2 is flushed before each
+    step (untimed); CUDA events time each step after --warmup; the first
+    pairs of every point are checked bit-exact against the oracle's float32
+    mirror.
+    """
+    import torch
+    import oracle
+    from paper_2404_05708_gb300 import build, dfd, workloads
+    build.build()
+    oracle.load()
+    torch.cuda.set_device(0)
+    steps, warmup = max(args.steps, 3), max(args.warmup, 3)
+    ctx = dfd.Context(0)
+    n_ctx = 16
+    side = [dfd.Context(0) for _ in range(n_ctx)]
+    streams = [torch.cuda.Stream() for _ in range(n_ctx)]
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    mix_rate, mix_mhz = dfd.dfd_microbench(ctx.handle, dfd.MICRO_OPS["cell_f32_d2"])
+    peak = mix_rate * sms * mix_mhz * 1e6 / 1e9
+
+    def timed(fn):
+        for _ in range(warmup):
+            fn()
+        total = 0.0
+        for _ in range(steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            torch.cuda.synchronize()
+            total += e0.elapsed_time(e1)
+        return total / steps
+
+    rows = []
+    points = [("i", 1 << 10, 1 << k) for k in (5, 7, 9, 11, 13, 14)] + \
+             [("ii", 1 << k, 1 << 10) for k in (5, 7, 9, 11, 12, 13, 14)]
+    for sweep, P, N in points:
+        b = workloads.paper_walks(N, P)
+        cells = N * P * P
+        pts = torch.from_numpy(b.points).cuda()
+        O, Q = torch.from_numpy(b.offsets).cuda(), torch.from_numpy(b.pairs).cuda()
+        nchk = 8 if P <= 4096 else 1
+        mirror, _ = oracle.batch(b.points, b.offsets, b.pairs[:nchk], mirror=True)
+        if P > 4096:
+            ctx.set_batch_row_buffer(P)
+        out = {}
+        ms = timed(lambda: out.__setitem__("r", ctx.batch(pts, O, Q)))
+        d2 = out["r"][1][:nchk].cpu().numpy()
+        rows.append({"sweep": sweep, "P": P, "N": N, "cells_per_step": cells, "ms": ms,
+                     "gcups": cells / (ms * 1e-3) / 1e9, "engine": "dfd_batch, one launch (one warp per pair)",
+                     "roofline_frac": cells / (ms * 1e-3) / 1e9 / peak,
+                     "verified_vs_oracle": bool(np.array_equal(d2, mirror)) and ctx.get_error() == 0})
+        if P >= 4096:
+            curves = [pts[b.offsets[c]:b.offsets[c + 1]] for c in range(2 * N)]
+            od = torch.empty(N, dtype=torch.float32, device="cuda")
+            od2 = torch.empty(N, dtype=torch.float32, device="cuda")
+            cur = torch.cuda.current_stream()
+
+            def wave_all():
+                for s in streams:
+                    s.wait_stream(cur)
+                for i in range(N):
+                    k = i % n_ctx
+                    side[k].pair(curves[2 * i], curves[2 * i + 1], out_dist=od[i:i + 1], out_dist2=od2[i:i + 1],
+                                 stream=streams[k].cuda_stream)
+                for s in streams:
+                    cur.wait_stream(s)
+            ms = timed(wave_all)
+            rows.append({"sweep": sweep, "P": P, "N": N, "cells_per_step": cells, "ms": ms,
+                         "gcups": cells / (ms * 1e-3) / 1e9,
+                         "engine": f"dfd_pair per pair (band wavefront), {n_ctx} contexts on their own streams",
+                         "verified_vs_oracle": bool(np.array_equal(od2[:nchk].cpu().numpy(), mirror))})
+        del pts, O, Q
+    for c in side:
+        c.close()
+    ctx.close()
+    out_line = {"metric": METRIC, "value": max(r["gcups"] for r in rows), "unit": UNIT, "n_gpus": 1, "steps": steps,
+                "warmup": warmup, "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": "the paper's Experiment 1 shape: N pairs of 2-D walks, steps in {-1,0,1}^2, "
+                                       "(i) P=Q=2^10, N=2^5..2^14, (ii) N=2^10, P=Q=2^5..2^14 (value: best point)",
+                           "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MB write)",
+                           "roofline_peak": {"value": peak, "unit": "Gcell/s",
+                                             "basis": f"measured mix cell_f32_d2 {mix_rate:.2f} cells/clk/SM x "
+                                                      f"{sms} SMs x {mix_mhz:.0f} MHz"}},
+                "rows": rows}
+    print(json.dumps(out_line))
+    return 0
+
+
 # -------------------------------------------------------------- reference
 def run_reference(args):
     """CPU oracle on host cores, bounded sample per step."""
@@ -815,6 +916,8 @@ def main():
         return run_serving(args)
     if args.workload == "next":
         return run_next(args)
+    if args.workload == "paper":
+        return run_paper(args)
 
     import torch
     import torch.distributed as dist

@@ -153,8 +153,11 @@ dfd_status dfd_pair_host(dfd_context* ctx, dfd_dtype dtype, int dim, const void*
  * taken by persistent warps from an atomic counter.  Invalid curve ids or
  * empty curves put DFD_ERR_INVALID_ARG in the error word and leave that
  * pair's outputs unwritten.  A pair whose two curves both exceed 32*Rmax
- * points (Rmax = 8, 4, 2 for dim <= 4, <= 8, <= 16) needs its longer curve
- * <= 4096 points, else DFD_ERR_UNSUPPORTED for that pair.
+ * points (Rmax = 8 for dim <= 4, else 4) runs several stripes and hands a
+ * row of its longer curve's length between them through a per-warp row
+ * buffer: its longer curve must fit the buffer (4096 points unless
+ * dfd_batch_set_row_buffer widened it), else DFD_ERR_UNSUPPORTED for that
+ * pair.
  */
 dfd_status dfd_batch(dfd_context* ctx, dfd_dtype dtype, int dim, const void* points, const int64_t* offsets,
                      int64_t n_curves, const int32_t* pairs, int64_t n_pairs, void* out_dist, void* out_dist2,
@@ -283,6 +286,19 @@ dfd_status dfd_batch_autotune(dfd_context* ctx, dfd_dtype dtype, int dim, const 
 dfd_status dfd_batch_set_order(dfd_context* ctx, dfd_dtype dtype, int dim, int order);
 
 /*
+ * Row buffer width (columns per warp) of the ragged batch on this context:
+ * pairs that run several stripes may have up to `cols` points in their
+ * longer curve.  cols in [4096, 2^28], rounded up to a multiple of 32,
+ * else DFD_ERR_INVALID_ARG; the default is 4096.  The batch's scratch holds
+ * one buffer per resident warp (2432 on 152 SMs): cols * 4 bytes each for
+ * float32, cols * 8 for int32.  Applies to later dfd_batch and
+ * dfd_batch_capture calls; dfd_batch_host widens its buffers by itself to
+ * the widest pair it is given.  The decider, matrix, k-NN and variant
+ * kernels keep 4096.
+ */
+dfd_status dfd_batch_set_row_buffer(dfd_context* ctx, int cols);
+
+/*
  * dfd_batch with HOST buffers (points, offsets, pairs and the outputs are
  * host pointers; outputs may be NULL, not both): synchronous.  The points
  * are copied to the device in up to 8 slices of curves (about 64 MiB each)
@@ -292,7 +308,9 @@ dfd_status dfd_batch_set_order(dfd_context* ctx, dfd_dtype dtype, int dim, int o
  * landed, so the copies overlap the computation (launches alternate between
  * two internal streams, so one launch's start overlaps the end of the one
  * before).  The device staging holds the points, the results and two batch
- * scratch areas (grow-only, freed at destroy).  Results are bit-identical
+ * scratch areas (grow-only, freed at destroy), whose row buffers are as wide
+ * as the widest multi-stripe pair given (at least the context's width), so
+ * any pair lengths run.  Results are bit-identical
  * to dfd_batch on the same data.  Offsets must be nondecreasing and every
  * id in [0, n_curves) (checked on the host: DFD_ERR_INVALID_ARG); the
  * device-side checks are dfd_batch's, returned directly.  Uses the context's

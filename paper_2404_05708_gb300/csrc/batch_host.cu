@@ -27,8 +27,8 @@ namespace dfd {
 #define DFD_RANGE_EXTERN(V, DK)                                                                                 \
   extern template dfd_status batch_launch_range<V, DK>(dfd_context*, int, const void*, const int64_t*, int64_t, \
                                                        const int32_t*, int64_t, void*, void*, cudaStream_t,     \
-                                                       int64_t, int*, char*, size_t, cudaEvent_t);              \
-  extern template size_t batch_scratch_bytes<V, DK>(dfd_context*, int64_t, int64_t, bool);
+                                                       int64_t, int*, char*, size_t, cudaEvent_t, int);         \
+  extern template size_t batch_scratch_bytes<V, DK>(dfd_context*, int64_t, int64_t, bool, int);
 DFD_RANGE_EXTERN(F32, 2)
 DFD_RANGE_EXTERN(F32, 3)
 DFD_RANGE_EXTERN(F32, 4)
@@ -53,11 +53,11 @@ constexpr size_t kSliceBytes = (size_t)64 << 20;
 dfd_status range_run(dfd_context* ctx, dfd_dtype dtype, int dim, const void* points, const int64_t* offsets,
                      int64_t n_curves, const int32_t* pairs, int64_t n_pairs, void* out_dist, void* out_dist2,
                      cudaStream_t s, int64_t first, int* bbox, char* scratch, size_t scratch_bytes,
-                     cudaEvent_t prepared) {
+                     cudaEvent_t prepared, int buf_cols) {
 #define DFD_R_CASE(V, DK)                                                                                       \
   case DK:                                                                                                      \
     return batch_launch_range<V, DK>(ctx, dim, points, offsets, n_curves, pairs, n_pairs, out_dist, out_dist2, s, \
-                                     first, bbox, scratch, scratch_bytes, prepared);
+                                     first, bbox, scratch, scratch_bytes, prepared, buf_cols);
 #define DFD_R_DK(V)                                                                                          \
   switch (dim_class(dim)) {                                                                                  \
     DFD_R_CASE(V, 2)                                                                                         \
@@ -77,9 +77,9 @@ dfd_status range_run(dfd_context* ctx, dfd_dtype dtype, int dim, const void* poi
 }
 
 // Scratch bytes of one slice launch (at most n_pairs pairs); 0: unsupported.
-size_t range_scratch(dfd_context* ctx, dfd_dtype dtype, int dim, int64_t n_curves, int64_t n_pairs) {
+size_t range_scratch(dfd_context* ctx, dfd_dtype dtype, int dim, int64_t n_curves, int64_t n_pairs, int buf_cols) {
 #define DFD_S_CASE(V, DK) \
-  case DK: return batch_scratch_bytes<V, DK>(ctx, n_curves, n_pairs, true);
+  case DK: return batch_scratch_bytes<V, DK>(ctx, n_curves, n_pairs, true, buf_cols);
 #define DFD_S_DK(V)          \
   switch (dim_class(dim)) {  \
     DFD_S_CASE(V, 2)         \
@@ -96,6 +96,29 @@ size_t range_scratch(dfd_context* ctx, dfd_dtype dtype, int dim, int64_t n_curve
   }
 #undef DFD_S_DK
 #undef DFD_S_CASE
+}
+
+// Rows per lane of a full stripe (batch::Rmax) for a dimension class.
+int rmax_of(int dk) { return dk <= 4 ? 8 : 4; }
+static_assert(batch::Rmax<2>::value == 8 && batch::Rmax<4>::value == 8 && batch::Rmax<8>::value == 4 &&
+                  batch::Rmax<16>::value == 4,
+              "rmax_of mirrors batch::Rmax");
+
+// Device scratch of the two launch streams (grow-only; cudaFree on growth
+// synchronises the device, so no launch still uses the old area).
+dfd_status ensure_host_scratch(dfd_context* ctx, size_t bytes) {
+  if (bytes <= ctx->host_scr_bytes) return DFD_OK;
+  if (ctx->opt.mem_budget_bytes && bytes > ctx->opt.mem_budget_bytes) return DFD_ERR_OOM;
+  if (ctx->host_scr) cudaFree(ctx->host_scr);
+  ctx->host_scr = nullptr;
+  ctx->host_scr_bytes = 0;
+  if (cudaMalloc(&ctx->host_scr, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    ctx->host_scr = nullptr;
+    return DFD_ERR_OOM;
+  }
+  ctx->host_scr_bytes = bytes;
+  return DFD_OK;
 }
 
 bool page_locked(const void* x) {
@@ -117,10 +140,15 @@ extern "C" dfd_status dfd_batch_host(dfd_context* ctx, dfd_dtype dtype, int dim,
   if (st != DFD_OK) return st;
   if (!pairs || n_pairs < 0 || n_pairs > INT32_MAX) return DFD_ERR_INVALID_ARG;
   if (n_pairs == 0) return DFD_OK;
-  // host-side check the slicing relies on: monotone offsets
+  // host-side check the slicing relies on: monotone offsets (and the
+  // longest curve, which bounds the row buffers' width)
   if (offsets[0] < 0) return DFD_ERR_INVALID_ARG;
-  for (int64_t c = 0; c < n_curves; ++c)
-    if (offsets[c + 1] < offsets[c]) return DFD_ERR_INVALID_ARG;
+  int64_t len_max = 0;
+  for (int64_t c = 0; c < n_curves; ++c) {
+    const int64_t len = offsets[c + 1] - offsets[c];
+    if (len < 0) return DFD_ERR_INVALID_ARG;
+    len_max = std::max(len_max, len);
+  }
   if ((st = set_device(ctx)) != DFD_OK) return st;
 
   const int64_t n_pts = offsets[n_curves];
@@ -152,12 +180,10 @@ extern "C" dfd_status dfd_batch_host(dfd_context* ctx, dfd_dtype dtype, int dim,
   if (!pts_locked) std::memcpy(h_pts, points, pts_bytes);
   const char* src_pts = pts_locked ? static_cast<const char*>(points) : h_pts;
 
-  // device (the context's staging buffer):
-  //   [points | offsets | pairs | bbox | dist | dist2 | scratch 0 | scratch 1]
+  // device (the context's staging buffer): [points | offsets | pairs | bbox | dist | dist2];
+  // the launches' scratch is sized once the pairs are known (their row buffers)
   const size_t bbox_b = f32 ? 0 : align_up((size_t)n_curves * dim_class(dim) * 2 * 4, 256);
-  const size_t scr_b = align_up(range_scratch(ctx, dtype, dim, n_curves, n_pairs), 256);
-  if (scr_b == 0) return DFD_ERR_UNSUPPORTED;
-  const size_t dev_bytes = align_up(pts_bytes, 256) + off_b + pair_b + bbox_b + dist_b + dist2_b + 2 * scr_b;
+  const size_t dev_bytes = align_up(pts_bytes, 256) + off_b + pair_b + bbox_b + dist_b + dist2_b;
   if ((st = ensure_io(ctx, dev_bytes)) != DFD_OK) return st;
   char* d = static_cast<char*>(ctx->io);
   char* d_pts = d;
@@ -166,7 +192,6 @@ extern "C" dfd_status dfd_batch_host(dfd_context* ctx, dfd_dtype dtype, int dim,
   int* d_bbox = f32 ? nullptr : reinterpret_cast<int*>(reinterpret_cast<char*>(d_pairs) + pair_b);
   char* d_dist = reinterpret_cast<char*>(d_pairs) + pair_b + bbox_b;
   char* d_dist2 = d_dist + dist_b;
-  char* d_scr[2] = {d_dist2 + dist2_b, d_dist2 + dist2_b + scr_b};
   cudaStream_t s = ctx->stream;
   if (!ctx->copy_stream) {
     if (cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking) != cudaSuccess) {
@@ -212,16 +237,24 @@ extern "C" dfd_status dfd_batch_host(dfd_context* ctx, dfd_dtype dtype, int dim,
   cudaStreamWaitEvent(cs, ctx->slice_ev[kMaxSlices], 0);
   copy_slice(0);
 
-  // 2. on the host meanwhile: check the ids and group the pairs by the slice
-  // of their later curve (stable counting sort)
+  // 2. on the host meanwhile: check the ids, group the pairs by the slice
+  // of their later curve (stable counting sort), and find the widest row
+  // a multi-stripe pair hands between its stripes (the row buffers)
   std::unique_ptr<int[]> slice_of(new int[n_pairs]);   // (no zero fill: every entry is written)
   std::vector<int64_t> start(K + 1, 0);
   bool bad_id = false;
+  const int64_t stripe_rows = 32 * (int64_t)rmax_of(dim_class(dim));
+  const bool any_wide = len_max > ctx->batch_buf_cols;   // else no pair can outgrow the buffers
+  int64_t wide = 0;
   for (int64_t i = 0; i < n_pairs; ++i) {
     const int32_t ia = pairs[2 * i], ib = pairs[2 * i + 1];
     if (ia < 0 || ib < 0 || ia >= n_curves || ib >= n_curves) {
       bad_id = true;
       break;
+    }
+    if (any_wide) {
+      const int64_t na = offsets[ia + 1] - offsets[ia], nb = offsets[ib + 1] - offsets[ib];
+      if (std::min(na, nb) > stripe_rows) wide = std::max(wide, std::max(na, nb));
     }
     const int64_t c = std::max(ia, ib);
     int k = 0;
@@ -236,6 +269,19 @@ extern "C" dfd_status dfd_batch_host(dfd_context* ctx, dfd_dtype dtype, int dim,
     return DFD_ERR_INVALID_ARG;
   }
   for (int k = 0; k < K; ++k) start[k + 1] += start[k];
+  // row buffers as wide as the widest such pair needs (at least the context's width)
+  const int buf_cols =
+      (int)std::min<int64_t>(1 << 28, std::max<int64_t>(ctx->batch_buf_cols, (wide + 31) / 32 * 32));
+  if (wide > (1 << 28)) st = DFD_ERR_UNSUPPORTED;
+  const size_t scr_b = align_up(range_scratch(ctx, dtype, dim, n_curves, n_pairs, buf_cols), 256);
+  if (st == DFD_OK && scr_b == 0) st = DFD_ERR_UNSUPPORTED;
+  if (st == DFD_OK) st = ensure_host_scratch(ctx, 2 * scr_b);
+  if (st != DFD_OK) {
+    cudaStreamSynchronize(cs);   // the copy reads the caller's buffer
+    cudaGetLastError();
+    return st;
+  }
+  char* d_scr[2] = {static_cast<char*>(ctx->host_scr), static_cast<char*>(ctx->host_scr) + scr_b};
   std::memcpy(h, offsets, (size_t)(n_curves + 1) * 8);
   int32_t* hp = reinterpret_cast<int32_t*>(h + off_b);
   std::unique_ptr<int32_t[]> perm(new int32_t[n_pairs]);   // grouped position -> caller's pair index
@@ -274,7 +320,7 @@ extern "C" dfd_status dfd_batch_host(dfd_context* ctx, dfd_dtype dtype, int dim,
     const int64_t upto = final_launch ? n_curves : bound[k + 1];
     st = range_run(ctx, dtype, dim, d_pts, d_off, upto, d_pairs + 2 * start[k], cnt,
                    out_dist ? d_dist + start[k] * d1 : nullptr, out_dist2 ? d_dist2 + start[k] * d2 : nullptr, sk,
-                   covered, d_bbox, d_scr[li & 1], scr_b, ctx->prep_ev[li & 1]);
+                   covered, d_bbox, d_scr[li & 1], scr_b, ctx->prep_ev[li & 1], buf_cols);
     covered = upto;
     ++li;
   }

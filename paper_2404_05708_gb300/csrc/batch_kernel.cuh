@@ -98,7 +98,10 @@ __device__ __forceinline__ uint4 make_qrec(const typename V::coord (&q)[DK], int
   }
   return r;
 }
-constexpr int BUF_COLS = 4096;    // per-warp row buffer (columns) for multi-stripe pairs
+// Per-warp row buffer (columns) of multi-stripe pairs: the default width,
+// and the fixed one of the decider, matrix, k-NN and variant kernels; the
+// ragged batch takes a wider one per launch (BatchArgs::buf_cols).
+constexpr int BUF_COLS = 4096;
 
 // Rows per lane chosen for a pair with `rows` rows: the fewest stripes
 // (one when rows <= 32 * Rmax), with the rows spread evenly over them, so a
@@ -471,8 +474,8 @@ __host__ __device__ __forceinline__ int num_stripes(int rows) {
 
 // A pair needs the row buffer when its rows span several stripes.
 template <int DK>
-__device__ __forceinline__ bool fits_buffer(int rows, int cols) {
-  return rows <= 32 * Rmax<DK>::value || cols <= BUF_COLS;
+__device__ __forceinline__ bool fits_buffer(int rows, int cols, int buf_cols = BUF_COLS) {
+  return rows <= 32 * Rmax<DK>::value || cols <= buf_cols;
 }
 
 template <class V>
@@ -732,7 +735,8 @@ static __global__ void plan_scatter_kernel(PlanArgs a) {
 
 // ------------------------------------------------------------ batch kernel
 struct BatchArgs {
-  void* rowbuf;        // per-warp BUF_COLS values (multi-stripe pairs)
+  void* rowbuf;        // per-warp buf_cols values (multi-stripe pairs)
+  int buf_cols;        // row buffer columns per warp (>= BUF_COLS; the decider uses BUF_COLS)
   const void* points;
   const int64_t* offsets;
   const int32_t* pairs;
@@ -755,7 +759,7 @@ __global__ void __launch_bounds__(256, kBlocksPerSM<DK>::value) batch_kernel(Bat
   uint4* stage = stage_sm[threadIdx.x >> 5];
   const int L = threadIdx.x & 31;
   const int64_t gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  T* buf = static_cast<T*>(a.rowbuf) + gw * BUF_COLS;
+  T* buf = static_cast<T*>(a.rowbuf) + gw * (int64_t)a.buf_cols;
   const Cd* pts = static_cast<const Cd*>(a.points);
   const int64_t total = a.offsets[a.n_curves];
   if (ld_relaxed_i32(a.err) != 0) return;
@@ -778,7 +782,7 @@ __global__ void __launch_bounds__(256, kBlocksPerSM<DK>::value) batch_kernel(Bat
     if (oa < 0 || ob < 0 || ea > total || eb > total) continue;             // reported by the plan
     const int n = (int)(ea - oa), m = (int)(eb - ob);
     if (n < 1 || m < 1) continue;                                            // reported by the plan
-    if (!fits_buffer<DK>(n, m)) {
+    if (!fits_buffer<DK>(n, m, a.buf_cols)) {
       if (L == 0) raise_error(a.err, DFD_ERR_UNSUPPORTED);
       continue;
     }

@@ -10,6 +10,8 @@
 
 namespace dfd {
 
+static_assert(batch::BUF_COLS == kDefaultBatchBufCols, "the context's default row buffer is the kernels' fixed one");
+
 // float32 input check over CSR points [begin[0], end[0]) (point indices on
 // the device: offsets[first], offsets[n]); int32 batches are checked by the
 // bounding-box kernel.
@@ -84,7 +86,7 @@ struct BatchLayout {
   size_t off_hist, off_cursor, off_bucket, off_work, off_bbox, off_buf, total;
 };
 template <class V, int DK>
-BatchLayout batch_layout(int64_t n_curves, int64_t n_pairs, int blocks, bool bbox_ext) {
+BatchLayout batch_layout(int64_t n_curves, int64_t n_pairs, int blocks, bool bbox_ext, int buf_cols) {
   constexpr int THREADS = 256;
   constexpr bool kInt = std::is_same<V, I32>::value;
   BatchLayout l;
@@ -94,21 +96,21 @@ BatchLayout batch_layout(int64_t n_curves, int64_t n_pairs, int blocks, bool bbo
   l.off_work = align_up(l.off_bucket + (size_t)n_pairs * 2, 256);
   l.off_bbox = align_up(l.off_work + (size_t)n_pairs * 4, 256);
   l.off_buf = align_up(l.off_bbox + (kInt && !bbox_ext ? (size_t)n_curves * DK * 2 * 4 : 0), 256);
-  l.total = l.off_buf + (size_t)blocks * (THREADS / 32) * batch::BUF_COLS * sizeof(typename V::value);
+  l.total = l.off_buf + (size_t)blocks * (THREADS / 32) * (size_t)buf_cols * sizeof(typename V::value);
   return l;
 }
 
 // With `scratch_ext` the launch uses the caller's scratch area (at least
 // batch_scratch_bytes) instead of the context's, so launches on different
-// streams can run side by side.
+// streams can run side by side.  `buf_cols`: row buffer columns per warp.
 template <class V, int DK>
 dfd_status batch_prepare(dfd_context* ctx, int dim, const void* points, const int64_t* offsets, int64_t n_curves,
                          const int32_t* pairs, int64_t n_pairs, cudaStream_t s, int blocks, batch::BatchArgs* ba,
                          int64_t first_curve = 0, int* bbox_ext = nullptr, char* scratch_ext = nullptr,
-                         size_t scratch_ext_bytes = 0) {
+                         size_t scratch_ext_bytes = 0, int buf_cols = batch::BUF_COLS) {
   constexpr bool kInt = std::is_same<V, I32>::value;
   if (n_pairs >= (int64_t)batch::kNarrowBit) return DFD_ERR_UNSUPPORTED;
-  const BatchLayout lay = batch_layout<V, DK>(n_curves, n_pairs, blocks, bbox_ext != nullptr);
+  const BatchLayout lay = batch_layout<V, DK>(n_curves, n_pairs, blocks, bbox_ext != nullptr, buf_cols);
   const size_t off_cursor = lay.off_cursor, off_bucket = lay.off_bucket, off_work = lay.off_work;
   const size_t off_bbox = lay.off_bbox, off_buf = lay.off_buf;
   char* base = scratch_ext;
@@ -148,6 +150,7 @@ dfd_status batch_prepare(dfd_context* ctx, int dim, const void* points, const in
   batch::plan_scan_kernel<<<1, batch::NBUCKET, 0, s>>>(pa);
   batch::plan_scatter_kernel<<<pblocks, 256, 0, s>>>(pa);
   ba->rowbuf = base + off_buf;
+  ba->buf_cols = buf_cols;
   ba->points = points;
   ba->offsets = offsets;
   ba->pairs = pairs;
@@ -164,10 +167,13 @@ dfd_status batch_prepare(dfd_context* ctx, int dim, const void* points, const in
 }
 
 // Scratch bytes of one batch launch over `n_pairs` pairs of `n_curves`
-// curves (bounding boxes in the caller's buffer when `bbox_ext`).
+// curves (bounding boxes in the caller's buffer when `bbox_ext`) with row
+// buffers of `buf_cols` columns.
 template <class V, int DK>
-size_t batch_scratch_bytes(dfd_context* ctx, int64_t n_curves, int64_t n_pairs, bool bbox_ext) {
-  return batch_layout<V, DK>(n_curves, n_pairs, resident_blocks(ctx, batch::batch_kernel<V, DK>, 256), bbox_ext).total;
+size_t batch_scratch_bytes(dfd_context* ctx, int64_t n_curves, int64_t n_pairs, bool bbox_ext, int buf_cols) {
+  return batch_layout<V, DK>(n_curves, n_pairs, resident_blocks(ctx, batch::batch_kernel<V, DK>, 256), bbox_ext,
+                             buf_cols)
+      .total;
 }
 
 // `prepared` (optional) is recorded on s once the bounding boxes and the
@@ -176,11 +182,11 @@ template <class V, int DK>
 dfd_status batch_launch_range(dfd_context* ctx, int dim, const void* points, const int64_t* offsets,
                               int64_t n_curves, const int32_t* pairs, int64_t n_pairs, void* out_dist,
                               void* out_dist2, cudaStream_t s, int64_t first_curve, int* bbox_ext,
-                              char* scratch_ext, size_t scratch_ext_bytes, cudaEvent_t prepared) {
+                              char* scratch_ext, size_t scratch_ext_bytes, cudaEvent_t prepared, int buf_cols) {
   const int blocks = resident_blocks(ctx, batch::batch_kernel<V, DK>, 256);
   batch::BatchArgs ba;
   dfd_status st = batch_prepare<V, DK>(ctx, dim, points, offsets, n_curves, pairs, n_pairs, s, blocks, &ba,
-                                       first_curve, bbox_ext, scratch_ext, scratch_ext_bytes);
+                                       first_curve, bbox_ext, scratch_ext, scratch_ext_bytes, buf_cols);
   if (st != DFD_OK) return st;
   if (prepared) cudaEventRecord(prepared, s);
   ba.out_dist = out_dist;
@@ -195,7 +201,7 @@ template <class V, int DK>
 dfd_status batch_launch(dfd_context* ctx, int dim, const void* points, const int64_t* offsets, int64_t n_curves,
                         const int32_t* pairs, int64_t n_pairs, void* out_dist, void* out_dist2, cudaStream_t s) {
   return batch_launch_range<V, DK>(ctx, dim, points, offsets, n_curves, pairs, n_pairs, out_dist, out_dist2, s, 0,
-                                   nullptr, nullptr, 0, nullptr);
+                                   nullptr, nullptr, 0, nullptr, ctx->batch_buf_cols);
 }
 
 template <class V, int DK>
@@ -268,8 +274,8 @@ dfd_status matrix_launch(dfd_context* ctx, int dim, const void* points, const in
                                                       const int32_t*, int64_t, void*, void*, cudaStream_t);        \
   template dfd_status dfd::batch_launch_range<dfd::V, DK>(dfd_context*, int, const void*, const int64_t*, int64_t, \
                                                             const int32_t*, int64_t, void*, void*, cudaStream_t,      \
-                                                            int64_t, int*, char*, size_t, cudaEvent_t);               \
-  template size_t dfd::batch_scratch_bytes<dfd::V, DK>(dfd_context*, int64_t, int64_t, bool);                       \
+                                                            int64_t, int*, char*, size_t, cudaEvent_t, int);          \
+  template size_t dfd::batch_scratch_bytes<dfd::V, DK>(dfd_context*, int64_t, int64_t, bool, int);                  \
   template dfd_status dfd::decide_launch<dfd::V, DK>(dfd_context*, int, const void*, const int64_t*, int64_t,      \
                                                        const int32_t*, int64_t, const void*, double, void*, int32_t*, \
                                                        unsigned long long*, cudaStream_t);                            \

@@ -446,6 +446,7 @@ dfd_status dfd_context_destroy(dfd_context* ctx) {
   if (ctx->ev1) cudaEventDestroy(ctx->ev1);
   if (ctx->scratch) cudaFree(ctx->scratch);
   if (ctx->io) cudaFree(ctx->io);
+  if (ctx->host_scr) cudaFree(ctx->host_scr);
   if (ctx->pinned) cudaFreeHost(ctx->pinned);
   if (ctx->d_err) cudaFree(ctx->d_err);
   cudaGetLastError();
@@ -788,6 +789,13 @@ dfd_status dfd_batch_set_order(dfd_context* ctx, dfd_dtype dtype, int dim, int o
     return DFD_ERR_INVALID_ARG;
   if (dim > 16) return DFD_ERR_UNSUPPORTED;
   ctx->batch_order[dtype == DFD_F32 ? 0 : 1][dim_class_index(dim_class(dim))] = (signed char)order;
+  return DFD_OK;
+}
+
+dfd_status dfd_batch_set_row_buffer(dfd_context* ctx, int cols) {
+  // whole 32-column blocks; the widest a warp's row index reaches is INT32_MAX
+  if (!ctx || cols < kDefaultBatchBufCols || cols > (1 << 28)) return DFD_ERR_INVALID_ARG;
+  ctx->batch_buf_cols = (cols + 31) / 32 * 32;
   return DFD_OK;
 }
 

@@ -25,6 +25,7 @@ inline uint64_t tune_key(int dtype, int dk, int64_t n, int64_t m) {
 
 namespace dfd {
 constexpr int kMaxSlices = 8;   // dfd_batch_host: copy slices of the points
+constexpr int kDefaultBatchBufCols = 4096;   // batch::BUF_COLS (checked in batch_launch.cuh)
 }
 
 struct dfd_context {
@@ -47,6 +48,9 @@ struct dfd_context {
   signed char batch_order[2][5] = {};         // batch packing order per (float32 / int32, dim class 2,3,4,8,16)
   cudaStream_t copy_stream = nullptr;         // dfd_batch_host: point slices (created on first use)
   cudaEvent_t slice_ev[dfd::kMaxSlices + 1] = {};   // one per slice, and one for the allocation
+  int batch_buf_cols = dfd::kDefaultBatchBufCols;   // ragged batch: row buffer columns per warp
+  void* host_scr = nullptr;                   // dfd_batch_host: scratch of its two launch streams (grow-only)
+  size_t host_scr_bytes = 0;
   cudaStream_t launch_stream2 = nullptr;      // dfd_batch_host: every other slice launch
   cudaEvent_t prep_ev[2] = {};                // dfd_batch_host: a launch's boxes and work list built
   cudaEvent_t join_ev = nullptr;              // dfd_batch_host: launch_stream2's work done

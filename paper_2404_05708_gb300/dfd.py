@@ -83,6 +83,7 @@ _SIGS = {
     "dfd_batch_host": [_VP, _INT, _INT, _VP, _VP, _I64, _VP, _I64, _VP, _VP],
     "dfd_batch_autotune": [_VP, _INT, _INT, _VP, _VP, _I64, _VP, _I64, _VP, _VP, ctypes.POINTER(ctypes.c_int), _VP],
     "dfd_batch_set_order": [_VP, _INT, _INT, _INT],
+    "dfd_batch_set_row_buffer": [_VP, _INT],
     "dfd_matrix": [_VP, _INT, _INT, _VP, _VP, _I64, _VP, _VP, _VP],
     "dfd_batch_decide": [_VP, _INT, _INT, _VP, _VP, _I64, _VP, _I64, _VP, ctypes.c_double, _VP, _VP, _VP, _VP],
     "dfd_mc_pair": [_VP, _INT, _VP, _I64, _VP, _I64, _VP, _VP, ctypes.c_float, ctypes.c_float, _I64, _VP, _VP, _VP],
@@ -573,6 +574,11 @@ class Context:
     def set_batch_order(self, dtype: int, dim: int, order: int):
         """Set the ragged batch's packing order (0 variant-major, 1 cost-descending)."""
         _check(load_library().dfd_batch_set_order(self.handle, dtype, dim, order), "dfd_batch_set_order")
+
+    def set_batch_row_buffer(self, cols: int):
+        """Widen the ragged batch's per-warp row buffer (columns, >= 4096): pairs
+        that run several stripes may then have longer curves of up to `cols` points."""
+        _check(load_library().dfd_batch_set_row_buffer(self.handle, cols), "dfd_batch_set_row_buffer")
 
     def batch_host(self, points, offsets, pairs, out_dist=None, out_dist2=None):
         """dfd_batch on host (numpy) arrays, synchronous; returns (dist, dist2).

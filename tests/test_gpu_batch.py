@@ -195,6 +195,45 @@ def test_batch_host_boxes_across_slices(dctx):
     assert scaled.any() and np.all(want[scaled] > 2 ** 31)   # these need the int64 class
 
 
+@pytest.mark.parametrize("dtype", ["f32", "i32"])
+def test_batch_wide_pairs_row_buffer(dtype):
+    """Pairs that run several stripes (both curves longer than 256 points,
+    2-D) hand a row of their longer curve's length between stripes through a
+    per-warp buffer.  With the default 4096 columns dfd_batch reports
+    DFD_ERR_UNSUPPORTED for the wider ones and still computes the rest;
+    once the buffer is widened every pair equals the oracle; dfd_batch_host
+    widens it by itself."""
+    from paper_2404_05708_gb300 import dfd
+    ctx = dfd.Context(0)
+    rng = np.random.default_rng(31)
+    lens = np.array([300, 5000, 6100, 280, 100, 9000, 700, 4096, 4097, 520])
+    off = np.concatenate([[0], np.cumsum(lens)]).astype(np.int64)
+    if dtype == "f32":
+        pts = np.cumsum(rng.normal(0, 1, size=(int(off[-1]), 2)), axis=0).astype(np.float32)
+    else:
+        pts = np.cumsum(rng.integers(-64, 65, size=(int(off[-1]), 2)), axis=0).astype(np.int32)
+    pairs = np.array([[0, 1], [1, 2], [3, 5], [4, 5], [6, 7], [6, 8], [8, 9], [2, 1], [7, 9]], np.int32)
+    ln = lens[pairs]
+    wide = (ln.min(axis=1) > 256) & (ln.max(axis=1) > 4096)   # several stripes, a row wider than 4096
+    assert wide.sum() == 6 and (~wide).sum() == 3
+    b = workloads.Batch(points=pts, offsets=off, pairs=pairs)
+    want, _ = oracle.batch(pts, off, pairs, mirror=(dtype == "f32"))
+    d, d2 = run_batch(ctx, b)
+    assert ctx.get_error() == dfd.STATUS_CODE["DFD_ERR_UNSUPPORTED"]
+    assert np.array_equal(d2[~wide], want[~wide])
+    with pytest.raises(dfd.DFDError):
+        ctx.set_batch_row_buffer(1000)
+    ctx.set_batch_row_buffer(9000)
+    d, d2 = run_batch(ctx, b)
+    assert ctx.get_error() == 0
+    assert np.array_equal(d2, want)
+    ctx.close()
+    ctx = dfd.Context(0)
+    d, d2 = ctx.batch_host(pts, off, pairs)
+    assert np.array_equal(d2, want)
+    ctx.close()
+
+
 def test_batch_host_slices_without_pairs_and_checks():
     """Pairs that reference only late curves (early copy slices run no
     launch) still see every curve boxed and checked: results equal
