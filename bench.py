@@ -93,6 +93,8 @@ def parse():
     ap.add_argument("--shape", default="", help="long pair: fixed launch shape R,W,ctas (no autotune)")
     ap.add_argument("--pairs", type=int, default=0, help="batch: number of pairs (default 65,536)")
     ap.add_argument("--curves", type=int, default=0, help="matrix: number of curves (default 4096)")
+    ap.add_argument("--paper-points", default="",
+                    help="paper: only these points, comma-separated PxN (e.g. 1024x512); default all")
     return ap.parse_args()
 
 
@@ -787,6 +789,9 @@ def run_paper(args):
     rows = []
     points = [("i", 1 << 10, 1 << k) for k in (5, 7, 9, 11, 13, 14)] + \
              [("ii", 1 << k, 1 << 10) for k in (5, 7, 9, 11, 12, 13, 14)]
+    if args.paper_points:
+        keep = {tuple(int(x) for x in pn.split("x")) for pn in args.paper_points.split(",")}
+        points = [pt for pt in points if (pt[1], pt[2]) in keep]
     for sweep, P, N in points:
         b = workloads.paper_walks(N, P)
         cells = N * P * P

@@ -83,7 +83,7 @@ int resident_blocks(const dfd_context* ctx, K kernel, int threads) {
 // Scratch of one batch launch: [counter | hist | cursor] [bucket] [worklist]
 // [bbox] [row buffers].
 struct BatchLayout {
-  size_t off_hist, off_cursor, off_bucket, off_work, off_bbox, off_buf, total;
+  size_t off_hist, off_cursor, off_smrank, off_bucket, off_work, off_bbox, off_buf, total;
 };
 template <class V, int DK>
 BatchLayout batch_layout(int64_t n_curves, int64_t n_pairs, int blocks, bool bbox_ext, int buf_cols) {
@@ -92,7 +92,8 @@ BatchLayout batch_layout(int64_t n_curves, int64_t n_pairs, int blocks, bool bbo
   BatchLayout l;
   l.off_hist = 256;
   l.off_cursor = l.off_hist + batch::NBUCKET * 4;
-  l.off_bucket = align_up(l.off_cursor + batch::NBUCKET * 4, 256);
+  l.off_smrank = align_up(l.off_cursor + batch::NBUCKET * 4, 256);
+  l.off_bucket = align_up(l.off_smrank + batch::kSmSlots * 4, 256);
   l.off_work = align_up(l.off_bucket + (size_t)n_pairs * 2, 256);
   l.off_bbox = align_up(l.off_work + (size_t)n_pairs * 4, 256);
   l.off_buf = align_up(l.off_bbox + (kInt && !bbox_ext ? (size_t)n_curves * DK * 2 * 4 : 0), 256);
@@ -151,6 +152,8 @@ dfd_status batch_prepare(dfd_context* ctx, int dim, const void* points, const in
   batch::plan_scatter_kernel<<<pblocks, 256, 0, s>>>(pa);
   ba->rowbuf = base + off_buf;
   ba->buf_cols = buf_cols;
+  ba->sm_rank = reinterpret_cast<unsigned*>(base + lay.off_smrank);   // zeroed with the header
+  ba->n_sm = std::min(blocks, ctx->num_sms);
   ba->points = points;
   ba->offsets = offsets;
   ba->pairs = pairs;

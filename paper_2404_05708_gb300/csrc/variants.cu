@@ -261,9 +261,9 @@ __global__ void __launch_bounds__(256, batch::kBlocksPerSM<DK>::value) variant_k
   const Cd* pts = static_cast<const Cd*>(a.points);
   const int64_t total = a.offsets[a.n_curves];
   if (ld_relaxed_i32(a.err) != 0) return;
-  for (;;) {
+  for (bool first = true;; first = false) {
     int item = 0;
-    if (L == 0) item = atomicAdd(a.counter, 1);
+    if (L == 0) item = first ? batch::pop_first(a.counter, a.sm_rank, a.n_sm, a.n_items) : atomicAdd(a.counter, 1);
     item = __shfl_sync(0xffffffffu, item, 0);
     if (item >= a.n_items) break;
     const unsigned w = a.worklist[item];
