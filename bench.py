@@ -874,8 +874,19 @@ def run_reference(args):
             oracle.dfd2_linear(ps, qs)
         dt = time.perf_counter() - t0
         cores, dtype = 1, "f64"
+    elif args.workload not in ("batch", "matrix", "paper"):
+        print(json.dumps({"impl": "reference", "unavailable": f"no oracle arm for --workload {args.workload}: it "
+                                                              "covers long, pair2k, batch, matrix and paper"}))
+        return 0
     else:
-        if args.workload == "batch":
+        if args.workload == "paper":
+            b = workloads.paper_walks(1 << 10, 1 << 10)
+            pairs = b.pairs[:64]
+            dtype = "f64"
+            cfg = {"workload": "the paper's Experiment 1 shape, point P=Q=2^10, N=2^10 pairs of 2-D walks",
+                   "P": 1024, "N": 1024, "cells_per_step": 1024 * 1024 * 1024}
+            sample = "first 64 pairs of the point per step (Alg. 5, float64, all host threads)"
+        elif args.workload == "batch":
             b = workloads.ragged_int_batch()
             pairs = b.pairs[:4096]
             dtype = "int64"
