@@ -77,8 +77,6 @@ struct ServeArgs {
   const int64_t* offsets; // candidate c spans points [offsets[c], offsets[c + 1])
   int dim, vec;
   int* counter;
-  unsigned* sm_rank;      // batch::kSmSlots counters, zeroed per launch (batch::pop_first)
-  int n_sm;               // SMs the grid covers
   float* out;
   float* rowbuf;          // batch::BUF_COLS values per warp (multi-stripe short pairs)
 };
@@ -92,9 +90,9 @@ __global__ void __launch_bounds__(256, batch::kBlocksPerSM<DK>::value) serve_ker
   float* buf = a.rowbuf + gw * batch::BUF_COLS;
   const int base = a.n_slices > 0 ? a.prefix[0] : 0;
   const int total = a.n_items + (a.n_slices > 0 ? a.prefix[a.n_slices] - base : 0);
-  for (bool first = true;; first = false) {
+  for (;;) {
     int i = 0;
-    if (L == 0) i = first ? batch::pop_first(a.counter, a.sm_rank, a.n_sm, total) : atomicAdd(a.counter, 1);
+    if (L == 0) i = atomicAdd(a.counter, 1);
     i = __shfl_sync(0xffffffffu, i, 0);
     if (i >= total) break;
     const float *P, *Q;
@@ -286,7 +284,6 @@ struct Tick {
   float* d_out = nullptr;
   size_t cap_out = 0;
   int* d_counter = nullptr;   // one counter per launch (one launch per dim)
-  unsigned* d_smrank = nullptr;   // batch::kSmSlots per-SM rank counters per launch
   char* h_stage = nullptr;    // pinned staging of the queries and ids admitted with this tick
   size_t stage_used = 0;
   struct Upload {
@@ -652,7 +649,6 @@ void launch_tick(dfd_server* s, Tick& t) {
   cudaEventRecord(t.ev_up, st);
   if (n_it || n_sl) cudaMemcpyAsync(t.d_desc, t.h_desc, t.desc_bytes, cudaMemcpyHostToDevice, st);
   cudaMemsetAsync(t.d_counter, 0, (MAX_DIM + 1) * sizeof(int), st);
-  cudaMemsetAsync(t.d_smrank, 0, (size_t)(MAX_DIM + 1) * batch::kSmSlots * sizeof(unsigned), st);
   cudaEventRecord(t.ev_fork, st);   // the tick's inputs are in place
   const Item* d_items = reinterpret_cast<const Item*>(t.d_desc);
   const Slice* d_slices = reinterpret_cast<const Slice*>(t.d_desc + t.off_slices);
@@ -683,14 +679,10 @@ void launch_tick(dfd_server* s, Tick& t) {
     const int dk = dim_class(dim);
     a.vec = (dim == dk && dk != 3) ? 1 : 0;
     a.counter = t.d_counter + dim;
-    a.sm_rank = t.d_smrank + (size_t)dim * batch::kSmSlots;
     a.out = t.d_out;
     a.rowbuf = t.rowbuf[lane];
     const int64_t count = (int64_t)a.n_items + (t.prefix[se] - t.prefix[sb]);
-    // one CTA per pair up to the SM count, so a small tick's pairs each get
-    // an SM (their first pops go one per SM), at most two CTAs per SM
-    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(count, 2 * (int64_t)s->ctx->num_sms));
-    a.n_sm = std::min(blocks, s->ctx->num_sms);
+    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((count + 7) / 8, 2 * (int64_t)s->ctx->num_sms));
 #define DFD_SERVE_CASE(K)                                 \
   case K:                                                 \
     serve_kernel<K><<<blocks, 256, 0, ls>>>(a);           \
@@ -854,7 +846,6 @@ dfd_status dfd_server_create(dfd_context* ctx, const dfd_server_options* opt, df
     ok = ok && cudaEventCreate(&t.ev0) == cudaSuccess && cudaEventCreate(&t.ev1) == cudaSuccess;
     ok = ok && cudaEventCreateWithFlags(&t.ev_up, cudaEventDisableTiming) == cudaSuccess;
     ok = ok && cudaMalloc(&t.d_counter, (MAX_DIM + 1) * sizeof(int)) == cudaSuccess;
-    ok = ok && cudaMalloc(&t.d_smrank, (size_t)(MAX_DIM + 1) * batch::kSmSlots * sizeof(unsigned)) == cudaSuccess;
     ok = ok && cudaMallocHost(&t.h_stage, STAGE_BYTES) == cudaSuccess;
     // descriptors and results for ticks of up to ~256K pairs from the start:
     // growing them later allocates (synchronising) inside a tick's latency
@@ -888,7 +879,6 @@ dfd_status dfd_server_destroy(dfd_server* s) {
     if (t.d_desc) cudaFree(t.d_desc);
     if (t.d_out) cudaFree(t.d_out);
     if (t.d_counter) cudaFree(t.d_counter);
-    if (t.d_smrank) cudaFree(t.d_smrank);
     if (t.h_stage) cudaFreeHost(t.h_stage);
     if (t.ev0) cudaEventDestroy(t.ev0);
     if (t.ev1) cudaEventDestroy(t.ev1);
