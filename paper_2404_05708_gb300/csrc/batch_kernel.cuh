@@ -119,6 +119,7 @@ constexpr int BUF_COLS = 4096;
 // `sm_rank`: kSmSlots counters, zeroed per launch.
 constexpr int kSmSlots = 1024;
 constexpr unsigned long long kSpreadWaitNs = 20000;
+constexpr int kSpreadPolls = 64;
 __device__ __forceinline__ int pop_first(int* counter, unsigned* sm_rank, int n_sm, long long total) {
   if (sm_rank && total <= 4LL * n_sm) {
     unsigned sm, slot;
@@ -127,8 +128,12 @@ __device__ __forceinline__ int pop_first(int* counter, unsigned* sm_rank, int n_
     const unsigned q = sm * 4u + (slot & 3u);
     const unsigned r = q < (unsigned)kSmSlots ? atomicAdd(&sm_rank[q], 1u) : 0u;
     if (r > 0) {
+      // bounded twice: by the timer, and by a count of L2 round trips
+      // (kSpreadPolls) that holds even if the timer does not advance
       const unsigned long long t0 = globaltimer_ns();
-      while ((long long)ld_relaxed_i32(counter) < total && globaltimer_ns() - t0 < kSpreadWaitNs) {
+      for (int it = 0; it < kSpreadPolls && (long long)ld_relaxed_i32(counter) < total &&
+                       globaltimer_ns() - t0 < kSpreadWaitNs;
+           ++it) {
       }
     }
   }
