@@ -52,7 +52,7 @@ REF_SAMPLE = 20_000          # --impl reference: prefix per step
 # was taken on; any later source change reports null.
 TRAFFIC_BY_KERNEL_SHA: dict = {
     "9799fd99282b0741": 15759897,    # wave_kernel<F32, 3, 6>, long pair 200,000^2 (two fronts, 512-column q chunks)
-    "bbb4cc37a747c8a4": 289322701,   # batch_kernel<I32, 2>, ragged batch of 65,536 pairs (graph launches)
+    "27aa8e25b42fbf75": 289363200,   # batch_kernel<I32, 2>, ragged batch of 65,536 pairs (graph launches)
 }
 
 
