@@ -40,7 +40,8 @@
  *   dfo_dtw_f32mirror  DTW in float32, one rounding per cell (GPU selection mirror)
  *   dfo_perturb_f32    x + sigma * z with one rounding (Monte Carlo samples)
  *   dfo_levenshtein Wagner-Fischer edit distance (the appendix's third
- *                   variant; textbook definition, see DESIGN notes)
+ *                   variant, read as the textbook definition: unit insert,
+ *                   delete and substitute costs, D[i][0] = i, D[0][j] = j)
  *
  * Parity pins: every function above except the mirror is checked against
  * brute-force enumeration of monotone couplings, closed forms and the
