@@ -286,6 +286,9 @@ double dfo_hausdorff_f64(const float* p, int64_t n, const float* q, int64_t m, i
         for (int64_t j = 0; j < m; ++j) best = dmin(best, d2_f64(p + i * dim, q + j * dim, dim));
         h = dmax(h, best);
     }
+#if DFO_MUTANT == 6
+    m = 0;   /* planted mistake: one-sided (p -> q only) */
+#endif
     for (int64_t j = 0; j < m; ++j) {
         double best = INFINITY;
         for (int64_t i = 0; i < n; ++i) best = dmin(best, d2_f64(p + i * dim, q + j * dim, dim));
@@ -301,6 +304,9 @@ int64_t dfo_hausdorff_i64(const int32_t* p, int64_t n, const int32_t* q, int64_t
         for (int64_t j = 0; j < m; ++j) best = imin(best, d2_i64(p + i * dim, q + j * dim, dim));
         h = imax(h, best);
     }
+#if DFO_MUTANT == 6
+    m = 0;   /* planted mistake: one-sided (p -> q only) */
+#endif
     for (int64_t j = 0; j < m; ++j) {
         int64_t best = INT64_MAX;
         for (int64_t i = 0; i < n; ++i) best = imin(best, d2_i64(p + i * dim, q + j * dim, dim));

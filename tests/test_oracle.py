@@ -156,6 +156,86 @@ def test_lower_bounds_and_triangle():
         assert a <= b + 1e-12
 
 
+# ------------------------------------------------ discrete Hausdorff (Sec. 2)
+# The Frechet distance is never below the Hausdorff distance of the two point
+# sets (Sec. 2).  The oracle's Hausdorff routine is pinned here by closed
+# forms that separate it from the Frechet distance and from its one-sided
+# half, by the set properties it must have, and by a threshold search.
+
+def _as(kind, pts):
+    return np.array(pts, np.int32 if kind == "i32" else np.float32)
+
+
+@pytest.mark.parametrize("kind", ["i32", "f32"])
+def test_hausdorff_closed_forms(kind):
+    # a curve and its reverse: the same point set, so Hausdorff 0, while a
+    # coupling must pair (0,0) with (2,0) at an end, so delta^2 = 4
+    p = _as(kind, [[0, 0], [1, 0], [2, 0]])
+    q = p[::-1].copy()
+    assert oracle.hausdorff2(p, q) == 0
+    assert oracle.dfd2_linear(p, q) == 4
+    # one point against a curve that also reaches a far point: the one-sided
+    # distance from p is 0, the symmetric one is 5^2
+    p1 = _as(kind, [[0, 0]])
+    q1 = _as(kind, [[0, 0], [5, 0]])
+    assert oracle.hausdorff2(p1, q1) == 25
+    assert oracle.hausdorff2(q1, p1) == 25
+    # both directions nonzero and different: p = {(0,0), (10,0)},
+    # q = {(1,0), (2,0), (9,0)}; p -> q: max(1, 1) = 1; q -> p: max(1, 4, 1) = 4
+    p2 = _as(kind, [[0, 0], [10, 0]])
+    q2 = _as(kind, [[1, 0], [2, 0], [9, 0]])
+    assert oracle.hausdorff2(p2, q2) == 4
+    assert oracle.hausdorff2(q2, p2) == 4
+
+
+@pytest.mark.parametrize("kind", ["i32", "f32"])
+def test_hausdorff_one_point_curve_equals_frechet(kind):
+    """For a one-point curve both distances are the largest distance from
+    that point to the other curve (the fold over an empty sequence)."""
+    rng = np.random.default_rng(17)
+    for _ in range(30):
+        m = int(rng.integers(1, 30))
+        a = rand_int_curve(rng, 1, 2) if kind == "i32" else rand_f32_curve(rng, 1, 2)
+        q = rand_int_curve(rng, m, 2) if kind == "i32" else rand_f32_curve(rng, m, 2)
+        far = max(float(np.sum((a[0].astype(np.float64) - q[j]) ** 2)) for j in range(m))
+        assert oracle.hausdorff2(a, q) == far
+        assert oracle.hausdorff2(q, a) == far
+        assert oracle.hausdorff2(a, q) == oracle.dfd2_linear(a, q)
+
+
+@pytest.mark.parametrize("kind", ["i32", "f32"])
+def test_hausdorff_is_a_set_distance(kind):
+    """Hausdorff depends on the point sets only: symmetric, unchanged by any
+    reordering or duplication of points, zero on equal sets, and equal to the
+    smallest squared distance t at which every point of either curve has a
+    point of the other within t (a threshold search, not the max-min loops)."""
+    rng = np.random.default_rng(18)
+    for _ in range(40):
+        n, m = int(rng.integers(1, 25)), int(rng.integers(1, 25))
+        mk = rand_int_curve if kind == "i32" else rand_f32_curve
+        p, q = mk(rng, n, 3), mk(rng, m, 3)
+        h = oracle.hausdorff2(p, q)
+        assert oracle.hausdorff2(q, p) == h
+        pp = p[rng.permutation(n)]
+        qq = np.concatenate([q, q[rng.integers(0, m, size=3)]])[rng.permutation(m + 3)]
+        assert oracle.hausdorff2(pp, qq) == h
+        assert oracle.hausdorff2(p, pp) == 0
+        d2 = ((p[:, None, :].astype(np.float64) - q[None, :, :].astype(np.float64)) ** 2).sum(-1)
+        t = next(v for v in np.unique(d2) if (d2 <= v).any(1).all() and (d2 <= v).any(0).all())
+        assert h == t
+        assert oracle.dfd2_linear(p, q) >= h
+
+
+def test_hausdorff_pins_catch_the_one_sided_mistake(tmp_path):
+    """A Hausdorff that drops the second direction must fail a pin."""
+    path = oracle.build(str(tmp_path / "mut6.so"), mutant=6, force=True)
+    lib = oracle.load(path)
+    p1 = np.array([[0, 0]], np.int32)
+    q1 = np.array([[0, 0], [5, 0]], np.int32)
+    assert oracle.hausdorff2(p1, q1, lib=lib) != 25
+    assert oracle.hausdorff2(p1.astype(np.float32), q1.astype(np.float32), lib=lib) != 25
+
+
 def test_int_extremes_no_overflow():
     # precondition: dim * (2 * max|c|)^2 < 2^63
     big = (1 << 29) - 1
