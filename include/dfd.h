@@ -429,9 +429,10 @@ dfd_status dfd_pair_shaped(dfd_context* ctx, dfd_dtype dtype, int dim, const voi
  * DFD_NOALLOC_SCRATCH_BYTES in the library's device image, present on
  * every GPU that loads the library until the process exits.  Scratch needed
  * (bytes): 1024 + 8*ceil(n / 64) + m * (4 for float32, 8 for int32) +
- * (m + 288) * Q, where Q = 32 (float32, dim <= 4), 64 (float32, dim 5..8),
+ * (m + 1024) * Q, where Q = 32 (float32, dim <= 4), 64 (float32, dim 5..8),
  * 128 (float32, dim 9..16), 16 (int32, dim <= 4), 32 (int32, dim 5..8),
- * 64 (int32, dim 9..16).  Larger inputs return DFD_ERR_CAPACITY before
+ * 64 (int32, dim 9..16).  This is an upper bound of one front's layout;
+ * inputs whose bound exceeds the array return DFD_ERR_CAPACITY before
  * anything is enqueued (e.g. float32 3-D: m up to ~460,000).
  *
  * Arguments and results as dfd_pair, on CUDA device `device` (made current
@@ -442,8 +443,9 @@ dfd_status dfd_pair_shaped(dfd_context* ctx, dfd_dtype dtype, int dim, const voi
  * keeps only the last call's contents: calls whose work overlaps on the
  * GPU (on different streams, or from different threads) share the array
  * and race -- serialise them.  On a device-side error (invalid coordinates,
- * a bounded wait that ran out) the outputs are left as NaN (float, double)
- * / -1 (int64); there is no context to read the error code from.
+ * a bounded wait that ran out) the call still returns DFD_OK and the
+ * outputs are left as NaN (float, double) / -1 (int64); there is no context
+ * to read the error code from, so check the outputs.
  */
 #define DFD_NOALLOC_SCRATCH_BYTES (16u << 20)
 dfd_status dfd_pair_noalloc(int device, dfd_dtype dtype, int dim, const void* p, int64_t n, const void* q,

@@ -36,23 +36,26 @@ DeviceSetup g_setup[kMaxDevices];
 
 // Once per device, with that device current: the array's device address
 // (in host code its name is only a host-side stand-in) and the SM count.
+// Only a successful look-up is remembered; a failed one (for example a
+// first call made inside a stream capture) is retried by the next call.
 dfd_status setup_device(int device, DeviceSetup* out) {
   std::lock_guard<std::mutex> lock(g_setup_mu);
   DeviceSetup& s = g_setup[device];
   if (!s.done) {
     void* ptr = nullptr;
+    int sms = 0, optin = 0;
     cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
-    cudaDeviceProp prop;
-    if (e == cudaSuccess) e = cudaGetDeviceProperties(&prop, device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
     if (e != cudaSuccess) {
       cudaGetLastError();
-      s.status = DFD_ERR_CUDA;
-    } else {
-      s.scratch = static_cast<unsigned char*>(ptr);
-      s.num_sms = prop.multiProcessorCount;
-      s.smem_optin = prop.sharedMemPerBlockOptin;
-      s.status = DFD_OK;
+      *out = s;
+      return DFD_ERR_CUDA;
     }
+    s.scratch = static_cast<unsigned char*>(ptr);
+    s.num_sms = sms;
+    s.smem_optin = (size_t)optin;
+    s.status = DFD_OK;
     s.done = true;
   }
   *out = s;

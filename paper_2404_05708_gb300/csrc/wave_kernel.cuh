@@ -914,10 +914,13 @@ __global__ void pack_q_kernel(const typename V::coord* q, int64_t m, int dim, in
 // Each CTA reduces a stretch of columns; the values are non-negative, so
 // their bit patterns order like the values and the CTAs merge by an atomic
 // max of the complemented bits in `word` (zero before the launch); the last
-// CTA to finish (`count`, zero before the launch) writes the result.
+// CTA to finish (`count`, zero before the launch) writes the result, unless
+// the error word is set: an input check that failed or a wait that ran out
+// made the wavefront skip its bands, so the row buffers hold no result and
+// the outputs keep whatever the caller put there.
 template <class V>
 __global__ void combine_kernel(const void* rowbuf_f, const void* rowbuf_b, int64_t m, unsigned long long* word,
-                               unsigned* count, void* out_dist, void* out_dist2) {
+                               unsigned* count, const int* err, void* out_dist, void* out_dist2) {
   using T = typename V::value;
   const T* F = static_cast<const T*>(rowbuf_f);
   const T* B = static_cast<const T*>(rowbuf_b);
@@ -945,7 +948,7 @@ __global__ void combine_kernel(const void* rowbuf_f, const void* rowbuf_b, int64
         bits = (unsigned long long)(long long)x;
       atomicMax(word, ~bits);
       __threadfence();
-      if (atomicAdd(count, 1u) == gridDim.x - 1) {
+      if (atomicAdd(count, 1u) == gridDim.x - 1 && *(volatile const int*)err == 0) {
         const unsigned long long mb = ~atomicAdd(word, 0ull);
         if constexpr (sizeof(T) == 4) {
           const float r = __uint_as_float((unsigned)mb);

@@ -115,7 +115,8 @@ dfd_status wave_launch(dfd_context* ctx, int dim, const void* p, int64_t n, cons
     const int cblocks = (int)std::max<int64_t>(1, std::min<int64_t>((m + 1023) / 1024, ctx->num_sms));
     wave::combine_kernel<V><<<cblocks, 256, 0, s>>>(a.rowbuf, a.rowbuf_b, m,
                                                     reinterpret_cast<unsigned long long*>(base + 16),
-                                                    reinterpret_cast<unsigned*>(base + 8), out_dist, out_dist2);
+                                                    reinterpret_cast<unsigned*>(base + 8), a.err, out_dist,
+                                                    out_dist2);
   }
   timing_end(ctx, s);
   return cuda_status(cudaGetLastError());

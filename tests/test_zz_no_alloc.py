@@ -91,3 +91,38 @@ def test_noalloc_rejects_inputs_beyond_its_fixed_capacity():
     d = torch.empty(1, dtype=torch.float32, device="cuda")
     d2 = torch.empty(1, dtype=torch.float32, device="cuda")
     assert _noalloc(p, q, dfd.DFD_F32, d, d2) == dfd.STATUS_CODE["DFD_ERR_CAPACITY"]
+
+
+def test_noalloc_device_error_leaves_outputs_unset_after_a_good_call(dctx):
+    """A rejected coordinate found on the device must not yield a distance.
+    The caller has no context to read the error from, so the outputs keep
+    their NaN / -1 fill -- also on a pair of several bands (two fronts and
+    the combine pass), right after a good call left its rows in the array."""
+    p, q = workloads.warped_long_pair(3001, 2500, dim=3, seed=73)
+    P, Q = torch.from_numpy(p).cuda(), torch.from_numpy(q).cuda()
+    d = torch.empty(1, dtype=torch.float32, device="cuda")
+    d2 = torch.empty(1, dtype=torch.float32, device="cuda")
+    assert _noalloc(P, Q, dfd.DFD_F32, d, d2) == 0
+    want_d, want_d2 = _existing(dctx, P, Q)
+    assert d2.item() == want_d2 and d.item() == want_d
+    bad = p.copy()
+    bad[1700, 2] = np.nan
+    assert _noalloc(torch.from_numpy(bad).cuda(), Q, dfd.DFD_F32, d, d2) == 0
+    assert np.isnan(d.item()) and np.isnan(d2.item())
+
+    rng = np.random.default_rng(74)
+    pi = np.cumsum(rng.integers(-64, 65, size=(1800, 2)), axis=0).astype(np.int32)
+    qi = np.cumsum(rng.integers(-64, 65, size=(2200, 2)), axis=0).astype(np.int32)
+    Pi, Qi = torch.from_numpy(pi).cuda(), torch.from_numpy(qi).cuda()
+    di = torch.empty(1, dtype=torch.float64, device="cuda")
+    d2i = torch.empty(1, dtype=torch.int64, device="cuda")
+    assert _noalloc(Pi, Qi, dfd.DFD_I32, di, d2i) == 0
+    want_d, want_d2 = _existing(dctx, Pi, Qi)
+    assert d2i.item() == want_d2 and di.item() == want_d
+    badi = qi.copy()
+    badi[5, 1] = 1 << 30   # outside the exact int32 range
+    assert _noalloc(Pi, torch.from_numpy(badi).cuda(), dfd.DFD_I32, di, d2i) == 0
+    assert np.isnan(di.item()) and d2i.item() == -1
+    # and the next good call is unaffected
+    assert _noalloc(Pi, Qi, dfd.DFD_I32, di, d2i) == 0
+    assert d2i.item() == want_d2 and di.item() == want_d
