@@ -1,23 +1,34 @@
 #!/usr/bin/env python3
 """Benchmark of the discrete Frechet distance hot path on GB300.
 
-Default workload (the single-GPU configuration the headline metric is quoted
-on): one long pair of 3-D float32 curves, n = m = 200,000, q a time-warped,
-jittered copy of the Gaussian random walk p (seeded, synthetic).  A step is
-one complete distance computation through ``dfd_pair`` (the band wavefront,
-all 4.0e10 cells of Eq. 1).  ``value`` = cells / second / 1e9 (GCUPS) with
-the curves already resident in HBM; ``e2e`` = the same metric through
-``dfd_pair_host`` with host buffers (host->device copies and the result read
-inside the timed region).
+The headline metric is the batched / served rate against per-pair launches,
+so the default workload is the ragged batch: 65,536 pairs of int32 2-D
+random walks, lengths U{16..512} drawn per curve (seeded, synthetic).  A step
+is one complete batch through ``dfd_batch`` (input checks, the device-built
+work list and the persistent batch kernel, one captured CUDA graph launch).
+``value`` = cells / second / 1e9 (GCUPS) with the curves resident in HBM;
+``e2e`` = the same metric through ``dfd_batch_host`` with host buffers (the
+host->device copies and the result read inside the timed region).
+
+The same line carries, on one GPU:
+  config.per_pair  the same pairs (a 512-pair sample) one launch each through
+                   dfd_pair (band wavefront) and dfd_pair_reference (the
+                   plain per-pair form), back to back on one stream;
+  serving          p50 / p99 latency and rates of the continuous-batching
+                   server under open-loop Poisson streams (1,000 and 10,000
+                   requests/s, 2 s of arrivals, three sweeps each);
+  long_pair        the 200,000 x 200,000 3-D float32 pair through dfd_pair
+                   (rate, roofline fraction, oracle check).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
-    python bench.py --workload batch    # 65,536 ragged int32 2-D pairs, one graph launch per step
+    python bench.py --workload long     # only the 200,000^2 pair
     python bench.py --workload matrix   # all pairs of 4096 16-D AR(1) curves, one graph launch per step
     python bench.py --workload pair2k   # one 2000 x 1500 2-D pair
+    python bench.py --workload serve    # the serving sweep alone (more rates)
 
-Under torchrun (N > 1) the single long pair runs as replicas (one per rank);
-the batch and matrix workloads shard their pairs across ranks (no
-collective).  value = all ranks' cells / the slowest rank's time.
+Under torchrun (N > 1) the batch and matrix workloads shard their pairs
+across ranks (no collective) and the single long pair runs as replicas
+(one per rank); value = all ranks' cells / the slowest rank's time.
 ``--impl reference`` times the CPU oracle (float64 / int64 Alg. 5) on host
 cores on a bounded sample of the same workload.
 """
@@ -81,7 +92,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="long",
+    ap.add_argument("--workload", default="batch",
                     choices=["long", "batch", "matrix", "pair2k", "serve", "knn", "next", "paper"])
     ap.add_argument("--rates", default="100,1000,3000,10000,20000,30000")
     ap.add_argument("--serve-seconds", type=float, default=2.0)
@@ -94,6 +105,10 @@ def parse():
     ap.add_argument("--shape", default="", help="long pair: fixed launch shape R,W,ctas (no autotune)")
     ap.add_argument("--pairs", type=int, default=0, help="batch: number of pairs (default 65,536)")
     ap.add_argument("--curves", type=int, default=0, help="matrix: number of curves (default 4096)")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="batch: leave out the serving sweep and the long pair of the default line")
+    ap.add_argument("--extra-rates", default="1000,10000", help="batch line: serving rates (req/s)")
+    ap.add_argument("--serve-repeats", type=int, default=3, help="batch line: sweeps per serving rate")
     ap.add_argument("--paper-points", default="",
                     help="paper: only these points, comma-separated PxN (e.g. 1024x512); default all")
     return ap.parse_args()
@@ -347,6 +362,21 @@ class Batch(_Many):
         d, d2 = self.ctx.batch_host(self.pts_pinned_np, self.b.offsets, self.pairs_np)
         return d2
 
+    def kernel_ms(self, steps, flush):
+        """Duration of the batch kernel alone: the graph's launches carry no
+        readable library events, so the same call runs uncaptured (same
+        pairs, same kernel) with the library's event pair around the
+        kernel on the launching stream, L2 flushed before each."""
+        from paper_2404_05708_gb300 import dfd
+        out = []
+        for k in range(steps + 2):
+            flush.zero_()
+            self.ctx.batch(self.pts_dev, self.off, self.pairs, self.out, self.out2)
+            ms = dfd.dfd_timing_last(self.ctx.handle)
+            if k >= 2:
+                out.append(ms)
+        return out
+
     def micro_mix(self):
         mix = [("cell_i32b_d2", self.cells_narrow), ("cell_i32_d2", self.cells - self.cells_narrow)]
         return [(op, c) for op, c in mix if c > 0]
@@ -358,16 +388,18 @@ class Batch(_Many):
         return bool(np.array_equal(self.out2.cpu().numpy()[idx], ref))
 
     def cpu_baseline(self):
+        """The oracle over the whole batch, repeated for about 10 s of host time."""
         import oracle
         oracle.load()
-        n = 8192
         t0 = time.perf_counter()
-        _, used = oracle.batch(self.b.points, self.b.offsets, self.pairs_np[:n])
+        reps = 0
+        while time.perf_counter() - t0 < 10.0:
+            _, used = oracle.batch(self.b.points, self.b.offsets, self.pairs_np)
+            reps += 1
         dt = time.perf_counter() - t0
-        ln = self.b.lengths()
-        cells = int(np.sum(ln[self.pairs_np[:n, 0]] * ln[self.pairs_np[:n, 1]]))
-        return {"value": cells / dt / 1e9, "unit": UNIT, "cores": used, "kind": "oracle",
-                "sample": f"first {n} pairs of the batch, Alg. 5 int64, {used} threads, {dt:.1f} s"}
+        return {"value": reps * self.cells / dt / 1e9, "unit": UNIT, "cores": used, "kind": "oracle",
+                "sample": f"all {self.pairs_np.shape[0]} pairs of the batch, {reps} times, Alg. 5 int64, "
+                          f"{used} threads, {dt:.1f} s"}
 
     def per_pair(self):
         """The same pairs one launch each, back to back on one stream (sample of 512)."""
@@ -565,66 +597,77 @@ class Knn:
 WORKLOADS = {"long": LongPair, "pair2k": Pair2k, "batch": Batch, "matrix": Matrix, "knn": Knn}
 
 
-def run_serving(args):
-    """Open-loop Poisson request stream against the continuous-batching server.
+def serve_sweep(ctx, rates, seconds, repeats, tick_cells, stripes_per_tick):
+    """Open-loop Poisson request streams against the continuous-batching server.
 
     Pools: 2^16 float32 Gaussian-walk candidates per dim (2 and 3), lognormal
     lengths (median 256, sigma 0.75, clipped to [32, 4096]).  Requests: dim 2
     or 3, lognormal query length, k ~ U{1..1024} candidates.  For each rate
     the client submits every request at its scheduled arrival time (latency
     is measured from that time, so a late client cannot hide queueing) for
-    `--serve-seconds` seconds of arrivals, then waits for all of them.
+    `seconds` seconds of arrivals, then waits for all of them; each rate runs
+    `repeats` times with fresh arrival draws.
     """
-    import torch
-    from paper_2404_05708_gb300 import build, dfd, workloads
-    build.build()
-    torch.cuda.set_device(0)
-    ctx = dfd.Context(0)
+    from paper_2404_05708_gb300 import dfd, workloads
     pools = {d: workloads.serving_pool(dim=d, seed=6 + d) for d in (2, 3)}
-    srv = dfd.Server(ctx, mem_budget_bytes=4 << 30, max_slots=512, tick_cells=args.tick_cells,
-                     stripes_per_tick=args.stripes_per_tick)
+    srv = dfd.Server(ctx, mem_budget_bytes=4 << 30, max_slots=512, tick_cells=tick_cells,
+                     stripes_per_tick=stripes_per_tick)
     for d in (2, 3):
         srv.add_candidates(pools[d].points, pools[d].offsets)
-    rates = [float(r) for r in args.rates.split(",")]
     sweep = []
     # warm-up
     w = workloads.serving_requests(20, 1000.0, {2: 1 << 16, 3: 1 << 16}, seed=99)
     for t in [srv.submit(r.query, r.cand_ids) for r in w]:
         srv.wait(t)
     for rate in rates:
-        n_req = max(20, int(rate * args.serve_seconds))
-        reqs = workloads.serving_requests(n_req, rate, {2: 1 << 16, 3: 1 << 16}, seed=int(rate))
-        srv.reset_stats()
-        # no garbage-collector pass inside the open loop: a full pass over the
-        # request objects delays submissions (latency counts from the
-        # scheduled arrival)
-        gc.collect()
-        gc.disable()
-        t0 = srv.now() + 0.05
-        tickets = []
-        for r in reqs:
-            due = t0 + r.arrival_s
-            while True:
-                d = due - srv.now()
-                if d <= 0:
-                    break
-                time.sleep(min(d, 0.002))
-            tickets.append(srv.submit(r.query, r.cand_ids, arrival_s=due))
-        for t in tickets:
-            srv.wait(t)
-        gc.enable()
-        s = srv.stats()
-        sweep.append({"rate_req_s": rate, "requests": n_req, "p50_ms": s["p50_ms"], "p99_ms": s["p99_ms"],
-                      "gcups_wall": s["gcups_wall"], "gcups_busy": s["gcups_busy"], "ticks": s["ticks"],
-                      "cells": s["cells"]})
+        for rep in range(repeats):
+            n_req = max(20, int(rate * seconds))
+            reqs = workloads.serving_requests(n_req, rate, {2: 1 << 16, 3: 1 << 16}, seed=int(rate) + 7919 * rep)
+            srv.reset_stats()
+            # no garbage-collector pass inside the open loop: a full pass over the
+            # request objects delays submissions (latency counts from the
+            # scheduled arrival)
+            gc.collect()
+            gc.disable()
+            t0 = srv.now() + 0.05
+            tickets = []
+            for r in reqs:
+                due = t0 + r.arrival_s
+                while True:
+                    d = due - srv.now()
+                    if d <= 0:
+                        break
+                    time.sleep(min(d, 0.002))
+                tickets.append(srv.submit(r.query, r.cand_ids, arrival_s=due))
+            for t in tickets:
+                srv.wait(t)
+            gc.enable()
+            st = srv.stats()
+            sweep.append({"rate_req_s": rate, "repeat": rep, "requests": n_req, "p50_ms": st["p50_ms"],
+                          "p99_ms": st["p99_ms"], "gcups_wall": st["gcups_wall"], "gcups_busy": st["gcups_busy"],
+                          "ticks": st["ticks"], "cells": st["cells"]})
     srv.close()
+    return sweep
+
+
+SERVE_WORKLOAD = ("serving: Poisson stream of query-vs-k-candidates requests (dims 2, 3; lognormal lengths "
+                  "median 256 clipped [32, 4096]; k ~ U{1..1024}) against 2^16 resident candidates per dim")
+
+
+def run_serving(args):
+    """The serving sweep alone (see serve_sweep), over --rates."""
+    import torch
+    from paper_2404_05708_gb300 import build, dfd
+    build.build()
+    torch.cuda.set_device(0)
+    ctx = dfd.Context(0)
+    rates = [float(r) for r in args.rates.split(",")]
+    sweep = serve_sweep(ctx, rates, args.serve_seconds, 1, args.tick_cells, args.stripes_per_tick)
     ctx.close()
     best = max(sweep, key=lambda x: x["gcups_wall"])
     out = {"metric": METRIC, "value": best["gcups_wall"], "unit": UNIT, "n_gpus": 1,
            "higher_is_better": True, "dtype": "f32", "data": "synthetic",
-           "config": {"workload": "serving: Poisson stream of query-vs-k-candidates requests (dims 2, 3; "
-                                  "lognormal lengths median 256 clipped [32, 4096]; k ~ U{1..1024}) against "
-                                  "2^16 resident candidates per dim",
+           "config": {"workload": SERVE_WORKLOAD,
                       "tick_cells": args.tick_cells, "stripes_per_tick": args.stripes_per_tick},
            "serving": sweep}
     print(json.dumps(out))
@@ -923,7 +966,8 @@ def run_reference(args):
         "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": dtype, "data": "synthetic", "config": cfg,
         "impl": "reference",
-        "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "host_cores": os.cpu_count(), "kind": "oracle",
+                         "sample": sample},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(out))
@@ -931,6 +975,98 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------------ ours
+def timed_steps(wl, ctx, dfd, torch, steps, warmup, flush, world, kernel_timed):
+    """W untimed steps, then K steps each bracketed by CUDA events on the
+    launching stream, L2 flushed before each (outside the events); the
+    library's own event pair around the main kernel when `kernel_timed`.
+    Returns (total device ms, per-step kernel ms, clocks sampled meanwhile)."""
+    import torch.distributed as dist
+    stream = torch.cuda.current_stream()
+    for _ in range(warmup):
+        flush.zero_()
+        wl.step()
+    torch.cuda.synchronize()
+    try:
+        gpu_id = "GPU-" + str(torch.cuda.get_device_properties(torch.cuda.current_device()).uuid).replace("GPU-", "")
+    except Exception:
+        gpu_id = None
+    sampler = ClockSampler(gpu_id)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    time.sleep(0.3)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    kernel_ms = []
+    for k in range(steps):
+        flush.zero_()                       # L2 flush outside the timed events
+        ev[k][0].record(stream)
+        wl.step()
+        ev[k][1].record(stream)
+        if kernel_timed:
+            try:
+                kernel_ms.append(dfd.dfd_timing_last(ctx.handle))
+            except dfd.DFDError:
+                kernel_timed = False        # the step has no readable pair of library events
+                kernel_ms = []
+    torch.cuda.synchronize()
+    step_ms = [x.elapsed_time(y) for x, y in ev]
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    # the library's kernel events must sit inside the step's (a graph
+    # captured without them, or a failed read, falls back to the whole step)
+    if kernel_ms and not all(0 < km <= sm * 1.0001 for km, sm in zip(kernel_ms, step_ms)):
+        kernel_ms = []
+    return total_ms, kernel_ms, clocks
+
+
+def alu_roofline(wl, ctx, dfd, sms, clocks, kernel_ms, total_ms, steps):
+    """ALU roofline: measured issue rate of the workload's cell instruction
+    mix (cell-weighted over the mixes it runs: time adds per cell)."""
+    mixes = wl.micro_mix() if hasattr(wl, "micro_mix") else [(wl.micro_op, wl.cells)]
+    inv, basis, mb_mhz = 0.0, [], 0.0
+    tot = max(sum(c for _, c in mixes), 1)
+    for op, cells in mixes:
+        cell_rate, mb_mhz = dfd.dfd_microbench(ctx.handle, dfd.MICRO_OPS[op])
+        inv += cells / tot / cell_rate
+        basis.append(f"{op} {cell_rate:.2f} cells/clk/SM on {cells / tot:.1%} of cells")
+    clk = clocks["sm_mhz"] if clocks else mb_mhz
+    peak = (1.0 / inv) * sms * clk * 1e6 / 1e9
+    kern_avg = (sum(kernel_ms) / len(kernel_ms)) if kernel_ms else total_ms / steps
+    work_cells = wl.evaluated_cells() if hasattr(wl, "evaluated_cells") else wl.cells
+    achieved = work_cells / (kern_avg * 1e-3) / 1e9
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gcell/s", "frac": achieved / peak,
+                "traffic": TRAFFIC_BY_KERNEL_SHA.get(wl.config.get("kernel_sha")),
+                "peak_basis": f"measured mix ({'; '.join(basis)}) x {sms} SMs x {clk:.0f} MHz"}
+    roofline["timing"] = ("main kernel, the library's CUDA events on the launching stream" if kernel_ms
+                          else "whole step (all launches of the step)")
+    if hasattr(wl, "evaluated_cells"):
+        roofline["achieved_basis"] = (f"recurrence cells actually evaluated ({work_cells:.3e} per step; "
+                                      f"value counts all {wl.cells:.3e} candidate cells)")
+    return roofline
+
+
+def long_pair_summary(args, ctx, dfd, torch, workloads, flush, sms):
+    """The 200,000^2 3-D float32 pair through dfd_pair, for the batch line."""
+    la = argparse.Namespace(**vars(args))
+    la.n, la.m, la.shape, la.no_autotune = N_POINTS, N_POINTS, "", False
+    wl = LongPair(la, ctx, dfd, torch, workloads, 0, 1)
+    steps, warmup = 5, 3
+    total_ms, kernel_ms, clocks = timed_steps(wl, ctx, dfd, torch, steps, warmup, flush, 1, True)
+    roof = alu_roofline(wl, ctx, dfd, sms, clocks, kernel_ms, total_ms, steps)
+    out = {"workload": wl.config["workload"], "value": wl.cells * steps / (total_ms * 1e-3) / 1e9, "unit": UNIT,
+           "steps": steps, "warmup": warmup, "ms_per_step": total_ms / steps,
+           "launch_shape": wl.config["launch_shape"], "fronts": wl.config["fronts"],
+           "roofline": roof, "verified_vs_oracle": wl.verify(), "clocks": clocks}
+    del wl
+    return out
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -962,47 +1098,16 @@ def main():
     dfd.dfd_timing_enable(ctx.handle, True)
     wl = WORKLOADS[args.workload](args, ctx, dfd, torch, workloads, rank, world)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
-    stream = torch.cuda.current_stream()
-
-    for _ in range(args.warmup):
-        flush.zero_()
-        wl.step()
-    torch.cuda.synchronize()
-
-    try:
-        gpu_id = "GPU-" + str(torch.cuda.get_device_properties(local).uuid).replace("GPU-", "")
-    except Exception:
-        gpu_id = None
-    sampler = ClockSampler(gpu_id)
+    kernel_timed = args.workload in ("long", "pair2k", "batch")
+    total_ms, kernel_ms, clocks = timed_steps(wl, ctx, dfd, torch, args.steps, args.warmup, flush, world,
+                                              kernel_timed)
     if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
-    sampler.start()
-    time.sleep(0.3)
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    kernel_ms = []
-    for k in range(args.steps):
-        flush.zero_()                       # L2 flush outside the timed events
-        ev[k][0].record(stream)
-        wl.step()
-        ev[k][1].record(stream)
-        if args.workload in ("long", "pair2k"):
-            kernel_ms.append(dfd.dfd_timing_last(ctx.handle))
-    torch.cuda.synchronize()
-    step_ms = [a.elapsed_time(b) for a, b in ev]
-    total_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
         c = torch.tensor([wl.cells], device="cuda", dtype=torch.float64)
         dist.all_reduce(c, op=dist.ReduceOp.SUM)
         total_cells = float(c.item())
         dist.barrier()
     else:
         total_cells = float(wl.cells)
-    torch.cuda.synchronize()
-    clocks = sampler.stop()
     value = total_cells * args.steps / (total_ms * 1e-3) / 1e9
     verified = wl.verify()
 
@@ -1020,52 +1125,45 @@ def main():
         e2e_total = float(t.item())
     e2e_value = total_cells * args.steps / e2e_total / 1e9
 
-    # ALU roofline: measured issue rate of the workload's cell instruction
-    # mix (cell-weighted over the mixes it runs: time adds per cell)
     sms = torch.cuda.get_device_properties(local).multi_processor_count
-    mixes = wl.micro_mix() if hasattr(wl, "micro_mix") else [(wl.micro_op, wl.cells)]
-    inv, basis, mb_mhz = 0.0, [], 0.0
-    for op, cells in mixes:
-        cell_rate, mb_mhz = dfd.dfd_microbench(ctx.handle, dfd.MICRO_OPS[op])
-        inv += cells / max(sum(c for _, c in mixes), 1) / cell_rate
-        basis.append(f"{op} {cell_rate:.2f} cells/clk/SM on {cells / max(sum(c for _, c in mixes), 1):.1%} of cells")
-    clk = clocks["sm_mhz"] if clocks else mb_mhz
-    peak = (1.0 / inv) * sms * clk * 1e6 / 1e9
-    kern_avg = (sum(kernel_ms) / len(kernel_ms)) if kernel_ms else total_ms / args.steps
-    work_cells = wl.evaluated_cells() if hasattr(wl, "evaluated_cells") else wl.cells
-    achieved = work_cells / (kern_avg * 1e-3) / 1e9
-    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gcell/s", "frac": achieved / peak,
-                "traffic": TRAFFIC_BY_KERNEL_SHA.get(wl.config.get("kernel_sha")),
-                "peak_basis": f"measured mix ({'; '.join(basis)}) x {sms} SMs x {clk:.0f} MHz"}
-    if not kernel_ms:
-        roofline["timing"] = "whole step (all launches of the step)"
-    if hasattr(wl, "evaluated_cells"):
-        roofline["achieved_basis"] = (f"recurrence cells actually evaluated ({work_cells:.3e} per step; "
-                                      f"value counts all {wl.cells:.3e} candidate cells)")
+    if not kernel_ms and hasattr(wl, "kernel_ms"):
+        kernel_ms = wl.kernel_ms(args.steps, flush)
+    roofline = alu_roofline(wl, ctx, dfd, sms, clocks, kernel_ms, total_ms, args.steps)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = wl.cpu_baseline()
+        cpu["host_cores"] = os.cpu_count()
     extra = wl.per_pair() if rank == 0 else None
 
     cfg = dict(wl.config)
-    cfg.update({"parallelism": (f"dp{world} (pairs sharded)" if args.workload == "batch" else "replicas")
-                if world > 1 else "single",
+    cfg.update({"parallelism": (f"dp{world} (pairs sharded)" if args.workload in ("batch", "matrix")
+                                else "replicas") if world > 1 else "single",
                 "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MB write)", "verified_vs_oracle": verified})
     if extra:
         cfg["per_pair"] = extra
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-        "scaling": "strong" if args.workload == "batch" else "weak", "vs_baseline": None, "dtype": wl.dtype,
-        "data": "synthetic", "config": cfg, "roofline": roofline, "cpu_baseline": cpu,
+        "scaling": "strong" if args.workload in ("batch", "matrix") else "weak", "vs_baseline": None,
+        "dtype": wl.dtype, "data": "synthetic", "config": cfg, "roofline": roofline, "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": wl.h2d, "d2h_bytes_per_step": wl.d2h},
         "gpu_launches": wl.launches_per_step * args.steps,
         "clocks": clocks,
     }
+    del wl
+    if args.workload == "batch" and world == 1 and not args.no_extras:
+        # the served form and the long pair on the same GPU, after the batch
+        rates = [float(r) for r in args.extra_rates.split(",") if r]
+        if rates:
+            out["serving"] = serve_sweep(ctx, rates, args.serve_seconds, args.serve_repeats, args.tick_cells,
+                                         args.stripes_per_tick)
+            out["serving_config"] = {"workload": SERVE_WORKLOAD, "tick_cells": args.tick_cells,
+                                     "stripes_per_tick": args.stripes_per_tick,
+                                     "seconds_of_arrivals": args.serve_seconds}
+        out["long_pair"] = long_pair_summary(args, ctx, dfd, torch, workloads, flush, sms)
     if rank == 0:
         print(json.dumps(out))
-    del wl
     ctx.close()
     if world > 1:
         dist.destroy_process_group()

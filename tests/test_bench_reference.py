@@ -31,3 +31,13 @@ def test_reference_arm_line():
 def test_reference_arm_unavailable_for_uncovered_workload():
     d = run("--impl", "reference", "--workload", "serve")
     assert d["impl"] == "reference" and "serve" in d["unavailable"]
+
+
+def test_reference_arm_default_is_the_ragged_batch():
+    """With no --workload the arm times the same workload as the default
+    line (the 65,536-pair ragged int32 batch) and states the host's cores."""
+    d = run("--impl", "reference", "--steps", "1", "--warmup", "1")
+    assert d["impl"] == "reference" and d["dtype"] == "int64"
+    assert d["config"]["n_pairs"] == 65536 and "ragged batch" in d["config"]["workload"]
+    cb = d["cpu_baseline"]
+    assert cb["host_cores"] == os.cpu_count() and 1 <= cb["cores"] <= cb["host_cores"]
