@@ -796,8 +796,9 @@ def run_paper(args):
     """The paper's own experiment shape (Sec. 4, Experiment 1), as context:
     N pairs of 2-D float32 walks with steps uniform in {-1,0,1}^2, (i)
     P = Q = 2^10 points with N = 2^5 ... 2^14 pairs, (ii) N = 2^10 pairs with
-    P = Q = 2^5 ... 2^14 points.  Each point runs as one dfd_batch launch
-    (one warp per pair; for P > 4096 with the row buffer widened to P).
+    P = Q = 2^5 ... 2^14 points.  Each point runs as one dfd_batch launch,
+    once with one warp per pair (for P > 4096 with the row buffer widened to
+    P) and once with CTA teams for the pairs of several stripes.
     From P = 2^12 on the same pairs also run through dfd_pair (the band
     wavefront), one launch per pair, spread over 16 contexts each on its own
     stream so that several pairs share the GPU.  L2 is flushed before each
@@ -850,14 +851,21 @@ def run_paper(args):
         nchk = 8 if P <= 4096 else 1
         mirror, _ = oracle.batch(b.points, b.offsets, b.pairs[:nchk], mirror=True)
         if P > 4096:
-            ctx.set_batch_row_buffer(P)
+            ctx.set_batch_row_buffer(P)   # one warp per pair needs a row of P columns per warp
         out = {}
-        ms = timed(lambda: out.__setitem__("r", ctx.batch(pts, O, Q)))
-        d2 = out["r"][1][:nchk].cpu().numpy()
-        rows.append({"sweep": sweep, "P": P, "N": N, "cells_per_step": cells, "ms": ms,
-                     "gcups": cells / (ms * 1e-3) / 1e9, "engine": "dfd_batch, one launch (one warp per pair)",
-                     "roofline_frac": cells / (ms * 1e-3) / 1e9 / peak,
-                     "verified_vs_oracle": bool(np.array_equal(d2, mirror)) and ctx.get_error() == 0})
+        for mode, engine in ((0, "dfd_batch, one launch, size classes chosen by the plan (default)"),
+                             (1, "dfd_batch, one launch, one warp per pair"),
+                             (2, "dfd_batch, one launch, CTA teams for pairs of several stripes")):
+            if mode != 1 and P <= 256:
+                continue                  # one stripe: no team pairs
+            ctx.set_batch_team(dfd.DFD_F32, 2, mode)
+            ms = timed(lambda: out.__setitem__("r", ctx.batch(pts, O, Q)))
+            d2 = out["r"][1][:nchk].cpu().numpy()
+            rows.append({"sweep": sweep, "P": P, "N": N, "cells_per_step": cells, "ms": ms,
+                         "gcups": cells / (ms * 1e-3) / 1e9, "engine": engine, "team_mode": mode,
+                         "roofline_frac": cells / (ms * 1e-3) / 1e9 / peak,
+                         "verified_vs_oracle": bool(np.array_equal(d2, mirror)) and ctx.get_error() == 0})
+        ctx.set_batch_team(dfd.DFD_F32, 2, 0)
         if P >= 4096:
             curves = [pts[b.offsets[c]:b.offsets[c + 1]] for c in range(2 * N)]
             od = torch.empty(N, dtype=torch.float32, device="cuda")

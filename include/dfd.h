@@ -147,17 +147,23 @@ dfd_status dfd_pair_host(dfd_context* ctx, dfd_dtype dtype, int dim, const void*
  *   offsets: int64[n_curves + 1], device, non-decreasing, offsets[0] = 0.
  *   pairs:   int32[2 * n_pairs] curve ids (a, b), device.
  *   out_dist / out_dist2: n_pairs elements each (types as for dfd_pair).
- * One warp computes one pair (rows = the shorter curve, 32*R rows per
- * stripe, systolic over the columns); pairs are ordered by cost n*m,
- * largest first (a device-side counting sort, no host synchronisation) and
- * taken by persistent warps from an atomic counter.  Invalid curve ids or
- * empty curves put DFD_ERR_INVALID_ARG in the error word and leave that
- * pair's outputs unwritten.  A pair whose two curves both exceed 32*Rmax
- * points (Rmax = 8 for dim <= 4, else 4) runs several stripes and hands a
- * row of its longer curve's length between them through a per-warp row
- * buffer: its longer curve must fit the buffer (4096 points unless
- * dfd_batch_set_row_buffer widened it), else DFD_ERR_UNSUPPORTED for that
- * pair.
+ * A pair's rows are its shorter curve, cut into stripes of 32*R rows
+ * (R <= Rmax = 8 for dim <= 4, else 4), each a systolic array over the
+ * columns.  Pairs are sorted by cost on the device (a counting sort, no host
+ * synchronisation) and taken by persistent CTAs and warps from atomic
+ * counters, in two size classes (dfd_batch_set_team): pairs of several
+ * stripes that are too wide for one warp's row buffer (4096 columns unless
+ * dfd_batch_set_row_buffer widened it) -- and those for which a team is
+ * expected to finish sooner, as when a launch has fewer long pairs than the
+ * GPU has warps -- run first, each on the 8 warps of one CTA as a pipeline
+ * of stripes; the others run one warp per pair, costliest first.  A team pair with more than 8 stripes keeps a
+ * row of its longer curve in the CTA's eight warp buffers; one wider still
+ * runs after all others, in the last CTA, with every warp buffer of the
+ * launch as its row (2432 x the per-warp width on 152 SMs); a pair wider
+ * than that gets NaN (float, double) / -1 (int64) outputs and
+ * DFD_ERR_UNSUPPORTED in the error word.  Invalid curve ids or empty curves
+ * put DFD_ERR_INVALID_ARG in the error word and leave that pair's outputs
+ * unwritten.
  */
 dfd_status dfd_batch(dfd_context* ctx, dfd_dtype dtype, int dim, const void* points, const int64_t* offsets,
                      int64_t n_curves, const int32_t* pairs, int64_t n_pairs, void* out_dist, void* out_dist2,
@@ -284,6 +290,29 @@ dfd_status dfd_batch_autotune(dfd_context* ctx, dfd_dtype dtype, int dim, const 
                               int64_t n_curves, const int32_t* pairs, int64_t n_pairs, void* out_dist,
                               void* out_dist2, int* best_order, void* stream);
 dfd_status dfd_batch_set_order(dfd_context* ctx, dfd_dtype dtype, int dim, int order);
+
+/*
+ * Which pairs of a ragged batch run as CTA teams (no counterpart in the
+ * paper, whose batches pad every curve to one length and give each lane one
+ * curve, Sec. 4).  A team is the 8 warps of one CTA on one pair of several
+ * stripes (more rows in its shorter curve than one warp holds): warp w runs
+ * stripes w, w + 8, ... as a pipeline over the columns, handing each
+ * stripe's bottom row to the next through shared memory (and, from the last
+ * warp back to the first, through the CTA's eight warp row buffers, 8 x the
+ * per-warp width).  mode 1: only pairs too wide for one warp's row buffer;
+ * mode 2: every pair of several stripes; mode 0 (default): the wide pairs,
+ * and each pair of several stripes for which a latency model of the two
+ * schedules (the launch's pairs in rounds of resident warps or of CTAs,
+ * steps x cycles per step) expects the team to finish sooner -- on a few
+ * hundred long pairs, teams; on thousands of pairs that already fill every
+ * warp, one warp each.  Team pairs go first (costliest first), then the
+ * one-warp pairs.  Every mode computes
+ * every pair's value bit for bit as the others.  dfd_batch_autotune tunes
+ * the mode with the packing order; dfd_batch_tuned reads both back.
+ * DFD_ERR_INVALID_ARG for a mode outside 0..2.
+ */
+dfd_status dfd_batch_set_team(dfd_context* ctx, dfd_dtype dtype, int dim, int mode);
+dfd_status dfd_batch_tuned(dfd_context* ctx, dfd_dtype dtype, int dim, int* order, int* team);
 
 /*
  * Row buffer width (columns per warp) of the ragged batch on this context:

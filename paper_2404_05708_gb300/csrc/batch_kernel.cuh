@@ -140,6 +140,39 @@ __device__ __forceinline__ int pop_first(int* counter, unsigned* sm_rank, int n_
   return atomicAdd(counter, 1);
 }
 
+// Progress words of a team (shared memory, CTA scope): release store by
+// the producer's lane 0 after its lanes' stores, acquire load by the
+// consumer's lane 0 before its lanes' loads.
+__device__ __forceinline__ unsigned long long ld_acquire_cta_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.cta.shared::cta.u64 %0, [%1];" : "=l"(v) : "r"(smem_addr(p)) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_cta_u64(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.release.cta.shared::cta.u64 [%0], %1;" ::"r"(smem_addr(p)), "l"(v) : "memory");
+}
+// Bounded wait until *p >= need: by the timer and by a count of polls that
+// holds even if the timer does not advance; gives up at once when the
+// error word is set.  On expiry it records DFD_ERR_TIMEOUT and returns, and
+// the team goes on without waiting (its results are then not to be used:
+// the error word says so).
+constexpr long long kTeamPolls = 1LL << 26;
+__device__ __forceinline__ void team_wait(const unsigned long long* p, unsigned long long need, int* err,
+                                          unsigned long long timeout_ns) {
+  if (ld_acquire_cta_u64(p) >= need) return;
+  const unsigned long long t0 = globaltimer_ns();
+  for (long long it = 1;; ++it) {
+    if (ld_acquire_cta_u64(p) >= need) return;
+    if ((it & 255) == 0) {
+      if (ld_relaxed_i32(err) != 0) return;
+      if (it >= kTeamPolls || globaltimer_ns() - t0 > timeout_ns) {
+        raise_error(err, DFD_ERR_TIMEOUT);
+        return;
+      }
+    }
+  }
+}
+
 // Rows per lane chosen for a pair with `rows` rows: the fewest stripes
 // (one when rows <= 32 * Rmax), with the rows spread evenly over them, so a
 // pair of 300 rows runs two stripes of 160 rows rather than two of 256.
@@ -243,17 +276,100 @@ struct AbandonAbove {
   }
 };
 
-template <class V, int DK, int R, class AB = NoAbandon<V>>
+// Where a stripe reads its top row (the bottom row of the stripe above) and
+// writes its bottom row, per 32-column block.
+// SoloIO: one warp runs all stripes of the pair in order, through its own
+// row buffer in global memory (in place: a column is read for stripe k+1
+// before stripe k+1 overwrites it).
+struct SoloIO {
+  static constexpr bool kTeam = false;
+  template <class T>
+  __device__ __forceinline__ static T top(SoloIO*, const T* buf, int, int c0, int L, int m) {
+    return buf[min(c0 + L, m - 1)];
+  }
+  template <class T>
+  __device__ __forceinline__ static void bottom(SoloIO*, T* buf, int, int c0, int L, int m, const T* outb) {
+    const int oc = c0 + L - 31;
+    if (oc >= 0 && oc < m) buf[oc] = outb[L];
+  }
+};
+
+// Team of the CTA's warps on one pair: warp w runs stripes w, w + nw,
+// w + 2 nw, ... as a pipeline over the columns.  Stripe s hands its bottom
+// row to stripe s + 1 through warp w's shared-memory ring of RING slots,
+// or, from the last warp to warp 0 of the next cycle, through the CTA's row
+// buffer in global memory (m columns, in place).  Positions count over a
+// warp's stripes: column c of its stripe in cycle k is position k * m + c,
+// kept in ring slot (k * m + c) mod RING, so the ring is one FIFO across
+// cycles.  prog[w] counts the positions of warp w's bottom rows published,
+// cons[w] the positions of its top rows read (both in shared memory).  A
+// consumer waits for the producer before each block; a producer waits
+// before overwriting slots the consumer has not read (position - RING).
+// The global buffer needs no such wait: the last warp writes column c of a
+// later cycle only after that column has passed down through every stripe
+// in between, each of which read it after warp 0 did.  Every wait is
+// bounded.
+template <int RING>
+struct TeamIO {
+  static constexpr bool kTeam = true;
+  static_assert((RING & (RING - 1)) == 0 && RING >= 128, "ring: a power of two of at least 128 columns");
+  void* gbuf;                  // the CTA's row buffer (global), >= m values when the pair has more stripes than warps
+  void* ring;                  // shared: nw rings of RING values of up to 8 bytes
+  unsigned long long* prog;    // shared [nw]
+  unsigned long long* cons;    // shared [nw]
+  int w, nw;
+  int* err;
+  unsigned long long timeout_ns;
+
+  template <class T>
+  __device__ __forceinline__ static T top(TeamIO* io, const T*, int st, int c0, int L, int m) {
+    const int wp = io->w == 0 ? io->nw - 1 : io->w - 1;   // the warp of stripe st - 1
+    const unsigned long long kp = (unsigned long long)((st - 1) / io->nw);
+    const int need = min(c0 + 32, m);
+    if (L == 0) team_wait(&io->prog[wp], kp * (unsigned long long)m + need, io->err, io->timeout_ns);
+    __syncwarp();
+    const int c = min(c0 + L, m - 1);
+    const T v = wp == io->nw - 1
+                    ? static_cast<const T*>(io->gbuf)[c]
+                    : reinterpret_cast<const T*>(static_cast<const unsigned long long*>(io->ring) +
+                                                 wp * RING)[(kp * (unsigned long long)m + c) & (RING - 1)];
+    __syncwarp();
+    if (L == 0) st_release_cta_u64(&io->cons[io->w], (unsigned long long)(st / io->nw) * m + need);
+    return v;
+  }
+  template <class T>
+  __device__ __forceinline__ static void bottom(TeamIO* io, T*, int st, int c0, int L, int m, const T* outb) {
+    const int oc = c0 + L - 31;
+    const unsigned long long k = (unsigned long long)(st / io->nw);
+    if (io->w == io->nw - 1) {
+      if (oc >= 0 && oc < m) static_cast<T*>(io->gbuf)[oc] = outb[L];
+    } else {
+      // the slots of positions k*m + c0-31 .. k*m + c0 last held positions up
+      // to k*m + c0 - RING: the consumer (stripe st + 1, same cycle) must have read them
+      const long long need = (long long)(k * (unsigned long long)m) + c0 + 1 - RING;
+      if (need > 0 && L == 0) team_wait(&io->cons[io->w + 1], (unsigned long long)need, io->err, io->timeout_ns);
+      __syncwarp();
+      if (oc >= 0 && oc < m)
+        reinterpret_cast<T*>(static_cast<unsigned long long*>(io->ring) +
+                             io->w * RING)[(k * (unsigned long long)m + oc) & (RING - 1)] = outb[L];
+    }
+    __syncwarp();
+    if (L == 0) st_release_cta_u64(&io->prog[io->w], k * m + min(c0 + 1, m));   // columns 0 .. c0
+  }
+};
+
+template <class V, int DK, int R, class AB = NoAbandon<V>, class IO = SoloIO>
 __device__ __forceinline__ typename V::value warp_dfd(const typename V::coord* __restrict__ P, int n,
                                                       const typename V::coord* __restrict__ Q, int m, int dim,
                                                       bool vec, typename V::value* buf, int L, int st_begin = 0,
                                                       int st_end = 1 << 30, AB* ab = nullptr,
-                                                      uint4* stage = nullptr) {
+                                                      uint4* stage = nullptr, IO* io = nullptr,
+                                                      int st_step = 1) {
   using T = typename V::value;
   using Cd = typename V::coord;
   const int nstripes = (n + 32 * R - 1) / (32 * R);
   T res = V::inf();
-  for (int st = st_begin; st < min(st_end, nstripes); ++st) {
+  for (int st = st_begin; st < min(st_end, nstripes); st += st_step) {
     Cd pr[R][DK];
 #pragma unroll
     for (int r = 0; r < R; ++r) {
@@ -335,7 +451,7 @@ __device__ __forceinline__ typename V::value warp_dfd(const typename V::coord* _
     const uint4* sb = stage + (32 - L);   // column c0 + s - L of the window is sb[s]
     T* outb = reinterpret_cast<T*>(stage + NPL * 64);
     for (int c0 = 0; c0 < nsteps; c0 += 32) {
-      const T top_blk = has_top ? buf[min(c0 + L, m - 1)] : V::inf();
+      const T top_blk = has_top ? IO::top(io, buf, st, c0, L, m) : V::inf();
       // slide the window: the block before's columns (slot 32 + L, written
       // by this lane) move to slot L, this block's column to slot 32 + L
       __syncwarp();
@@ -436,10 +552,7 @@ __device__ __forceinline__ typename V::value warp_dfd(const typename V::coord* _
         for (int c = 0; c < NPL; ++c) qr[c] = qn[c];
       }
       __syncwarp();
-      if (has_bottom) {
-        const int oc = c0 + L - 31;
-        if (oc >= 0 && oc < m) buf[oc] = outb[L];
-      }
+      if (has_bottom) IO::bottom(io, buf, st, c0, L, m, outb);
       if constexpr (AB::on) {
         if (c0 + 31 <= m - 1) {
           T cut = upp;
@@ -641,8 +754,21 @@ __global__ void curve_bbox_kernel(const int32_t* __restrict__ pts, const int64_t
 // buckets of 256 per value class; int32 pairs come in two value classes
 // (exact int64 first, then exact uint32 bits, I32B).
 constexpr int NBUCKET1 = 256;
-constexpr int NBUCKET = 2 * NBUCKET1;
+// Team buckets come first: pairs of several stripes that a whole CTA runs
+// together (see batch_kernel), 16 cost buckets per value class, costliest
+// first.  The warp buckets follow.
+constexpr int NTB1 = 16;
+constexpr int NTB = 2 * NTB1;
+constexpr int NBUCKET = NTB + 2 * NBUCKET1;
 constexpr unsigned kNarrowBit = 1u << 30;   // worklist: pair index | narrow << 30 | swap << 31
+
+// Team bucket of a pair: floor(log2(rows * (cols + 31))) from 2^16 (15) up
+// to 2^31 and beyond (0), so the costliest team pairs start first.
+__device__ __forceinline__ int team_bucket(int64_t rows, int64_t cols) {
+  const unsigned long long cost = (unsigned long long)rows * (unsigned long long)(cols + 31);
+  const int msb = 63 - __clzll((long long)cost);
+  return 15 - min(15, max(0, msb - 16));
+}
 
 __device__ __forceinline__ int cost_bucket(int64_t rows, int64_t cols, int rmax) {
   const int64_t per_stripe = 32 * (int64_t)rmax;
@@ -667,8 +793,39 @@ __device__ __forceinline__ int cost_bucket_lpt(int64_t rows, int64_t cols, int r
   return NBUCKET1 - 1 - min(NBUCKET1 - 1, b);
 }
 
+// Whether a pair of several stripes should run as a CTA team (mode 3), from
+// a latency model of the two schedules in steps x cycles per step (a step
+// of R rows per lane costs about 24 + 8 R cycles: the shuffle from the lane
+// above, then R dependent cells), with the launch's pairs taking rounds of
+// the resident warps (one warp per pair) or CTAs (one team per pair):
+//   one warp:  ceil(N / (8 C)) * stripes * (cols + 31) * (24 + 8 Rmax)
+//   team:      ceil(N / C) * (cycles * (cols + 31) + (warps used - 1) * 64) * (24 + 8 Rt)
+// where a team spreads its rows over 8 warps with Rt rows per lane and the
+// hand-off between consecutive stripes lags 64 steps.  On the paper's
+// Experiment 1 shapes this picks teams for 32 .. 512 pairs of 1,024 points
+// and for 1,024 pairs of 2,048 points and more, one warp otherwise (measured
+// both ways).
+__device__ __forceinline__ bool team_pays(int64_t rows, int64_t cols, int rmax, int64_t n_pairs, int ctas) {
+  const double c = (double)cols + 31.0;
+  const int64_t sw = (rows + 32 * rmax - 1) / (32 * rmax);
+  const double warp_rounds = (double)((n_pairs + 8LL * ctas - 1) / (8LL * ctas));
+  const double warp_cost = warp_rounds * (double)sw * c * (24.0 + 8.0 * rmax);
+  int64_t rt = (rows + 32 * 8 - 1) / (32 * 8);
+  rt = rt < 1 ? 1 : (rt > rmax ? rmax : rt);
+  const int64_t st = (rows + 32 * rt - 1) / (32 * rt);
+  const int64_t cyc = (st + 7) / 8;
+  const int64_t used = st < 8 ? st : 8;
+  const double team_rounds = (double)((n_pairs + ctas - 1) / ctas);
+  const double team_cost = team_rounds * ((double)cyc * c + (double)(used - 1) * 64.0) * (24.0 + 8.0 * (double)rt);
+  return team_cost < warp_cost;
+}
+
 struct PlanArgs {
   int order;           // 0: variant-major buckets (cost_bucket), 1: cost-descending (cost_bucket_lpt)
+  int team;            // 0: no team buckets; 1: pairs of several stripes wider than buf_cols; 2: every pair of
+                       // several stripes; 3: those, when team_pays says so, and the wide ones
+  int buf_cols;        // row buffer columns of one warp
+  int ctas;            // persistent CTAs of the batch kernel (8 warps each)
   const int64_t* offsets;
   const int32_t* pairs;
   int64_t n_pairs;
@@ -698,7 +855,7 @@ static __global__ void plan_hist_kernel(PlanArgs a) {
     int b = -1;
     if (k < a.n_pairs) {
       const int32_t ia = a.pairs[2 * k], ib = a.pairs[2 * k + 1];
-      b = NBUCKET1 - 1;   // invalid pairs: last of the int64 class (skipped by the kernel)
+      b = NTB + NBUCKET1 - 1;   // invalid pairs: last of the int64 warp class (skipped by the kernel)
       if (ia < 0 || ib < 0 || ia >= a.n_curves || ib >= a.n_curves) {
         raise_error(a.err, DFD_ERR_INVALID_ARG);
       } else {
@@ -708,8 +865,15 @@ static __global__ void plan_hist_kernel(PlanArgs a) {
         if (na < 1 || nb < 1 || oa < 0 || ob < 0 || ea > total || eb > total || na > INT32_MAX || nb > INT32_MAX)
           raise_error(a.err, DFD_ERR_INVALID_ARG);
         const int64_t rows = max(min(na, nb), (int64_t)1), cols = max(max(na, nb), (int64_t)1);
-        b = a.order ? cost_bucket_lpt(rows, cols, a.rmax) : cost_bucket(rows, cols, a.rmax);
-        if (a.bbox && narrow_pair(a.bbox, a.dk, ia, ib)) b += NBUCKET1;
+        const bool narrow = a.bbox && narrow_pair(a.bbox, a.dk, ia, ib);
+        const bool multi = rows > 32 * (int64_t)a.rmax;
+        if (a.team && multi &&
+            (a.team == 2 || cols > a.buf_cols || (a.team == 3 && team_pays(rows, cols, a.rmax, a.n_pairs, a.ctas)))) {
+          b = team_bucket(rows, cols) + (narrow ? NTB1 : 0);
+        } else {
+          b = NTB + (a.order ? cost_bucket_lpt(rows, cols, a.rmax) : cost_bucket(rows, cols, a.rmax));
+          if (narrow) b += NBUCKET1;
+        }
       }
       a.bucket[k] = (unsigned short)b;
     }
@@ -765,16 +929,16 @@ static __global__ void plan_scatter_kernel(PlanArgs a) {
       const int64_t na = a.offsets[ia + 1] - a.offsets[ia], nb = a.offsets[ib + 1] - a.offsets[ib];
       swap = na > nb ? 1u : 0u;   // rows = the shorter curve
     }
-    const unsigned narrow = b >= NBUCKET1 ? kNarrowBit : 0u;
+    const unsigned narrow = (b < NTB ? b >= NTB1 : b - NTB >= NBUCKET1) ? kNarrowBit : 0u;
     a.worklist[pos] = (unsigned)k | narrow | (swap << 31);
   }
 }
 
 // ------------------------------------------------------------ batch kernel
 struct BatchArgs {
-  unsigned* sm_rank;   // kSmSlots counters, zeroed per launch (pop_first)
+  unsigned* sm_rank;   // kSmSlots counters, zeroed per launch (pop_first, team_pop_first)
   int n_sm;            // SMs the grid covers
-  void* rowbuf;        // per-warp buf_cols values (multi-stripe pairs)
+  void* rowbuf;        // per-warp buf_cols values (multi-stripe pairs); a CTA's eight are contiguous
   int buf_cols;        // row buffer columns per warp (>= BUF_COLS; the decider uses BUF_COLS)
   const void* points;
   const int64_t* offsets;
@@ -788,26 +952,197 @@ struct BatchArgs {
   int* err;
   void* out_dist;
   void* out_dist2;
+  // CTA teams (batch kernel only; null n_team: none)
+  const unsigned* n_team;   // items at the front of the worklist run by CTA teams (written by the plan)
+  int* team_counter;
+  unsigned* done_ctas;      // CTAs finished with the team and warp items
+  unsigned* deferred;       // worklist entries of team pairs wider than one CTA's row buffers
+  unsigned* n_deferred;
+  unsigned long long timeout_ns;
 };
 
+// Ring columns of a team's shared-memory hand-off (per warp, 8 bytes a slot).
+template <int DK>
+struct TeamRing {
+  static constexpr int value = DK >= 16 ? 128 : 256;
+};
+constexpr int kTeamWarps = 8;   // a team is the CTA's 8 warps
+
+// Rows per lane of a team pair: the rows spread over all the team's warps
+// (one stripe each) when they fit, else the largest stripes, cycling.
+template <int DK>
+__host__ __device__ __forceinline__ int team_rows_per_lane(int rows) {
+  constexpr int RM = Rmax<DK>::value;
+  if (rows <= 32) return 1;
+  const int r = (rows + 32 * kTeamWarps - 1) / (32 * kTeamWarps);
+  return r > RM ? RM : r;
+}
+
+template <class V, int DK, class IO>
+__device__ __forceinline__ typename V::value team_dfd_any(const typename V::coord* P, int n,
+                                                          const typename V::coord* Q, int m, int dim, bool vec,
+                                                          int L, int w, uint4* stage, IO* io) {
+  constexpr int RM = Rmax<DK>::value;
+  using T = typename V::value;
+  switch (team_rows_per_lane<DK>(n)) {
+#define DFD_T_CASE(RR)                                                                                         \
+  case RR:                                                                                                     \
+    if constexpr (RR < RM)                                                                                     \
+      return warp_dfd<V, DK, RR, NoAbandon<V>, IO>(P, n, Q, m, dim, vec, static_cast<T*>(nullptr), L, w,       \
+                                                   1 << 30, static_cast<NoAbandon<V>*>(nullptr), stage, io,    \
+                                                   kTeamWarps);                                                \
+    break;
+    DFD_T_CASE(1)
+    DFD_T_CASE(2)
+    DFD_T_CASE(3)
+    DFD_T_CASE(4)
+    DFD_T_CASE(5)
+    DFD_T_CASE(6)
+    DFD_T_CASE(7)
+    default:
+      break;
+#undef DFD_T_CASE
+  }
+  return warp_dfd<V, DK, RM, NoAbandon<V>, IO>(P, n, Q, m, dim, vec, static_cast<T*>(nullptr), L, w, 1 << 30,
+                                               static_cast<NoAbandon<V>*>(nullptr), stage, io, kTeamWarps);
+}
+
+// First team pop of a CTA: when every team item fits one round of the SMs,
+// a CTA that is not the first on its SM waits (bounded, placement only)
+// until every item is taken, so the teams spread one per SM.
+__device__ __forceinline__ int team_pop_first(int* counter, unsigned* sm_rank, int n_sm, long long total) {
+  if (sm_rank && total <= n_sm) {
+    unsigned sm;
+    asm volatile("mov.u32 %0, %%smid;" : "=r"(sm));
+    const unsigned q = 640u + sm;
+    const unsigned r = q < (unsigned)kSmSlots ? atomicAdd(&sm_rank[q], 1u) : 0u;
+    if (r > 0) {
+      const unsigned long long t0 = globaltimer_ns();
+      for (int it = 0; it < kSpreadPolls && (long long)ld_relaxed_i32(counter) < total &&
+                       globaltimer_ns() - t0 < kSpreadWaitNs;
+           ++it) {
+      }
+    }
+  }
+  return atomicAdd(counter, 1);
+}
+
+// One team pair (all 256 threads of the CTA call it): the rows of the
+// shorter curve in stripes over the 8 warps (TeamIO), the result written by
+// the warp that runs the last stripe.  `gbuf` holds `gcols` values; a pair
+// with more stripes than warps needs m of them, else it is not run here and
+// false is returned (CTA-uniform).
+template <class V, int DK>
+__device__ __forceinline__ bool run_team_pair(const BatchArgs& a, unsigned wentry, void* gbuf, long long gcols,
+                                              uint4* stage, unsigned long long* ring, unsigned long long* prog,
+                                              unsigned long long* cons) {
+  using Cd = typename V::coord;
+  const int L = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int64_t k = wentry & (kNarrowBit - 1);
+  int32_t ia = a.pairs[2 * k], ib = a.pairs[2 * k + 1];
+  if (wentry >> 31) {
+    const int32_t t = ia;
+    ia = ib;
+    ib = t;
+  }
+  if (ia < 0 || ib < 0 || ia >= a.n_curves || ib >= a.n_curves) return true;   // reported by the plan
+  const int64_t total = a.offsets[a.n_curves];
+  const int64_t oa = a.offsets[ia], ob = a.offsets[ib];
+  const int64_t ea = a.offsets[ia + 1], eb = a.offsets[ib + 1];
+  if (oa < 0 || ob < 0 || ea > total || eb > total) return true;                // reported by the plan
+  const int n = (int)(ea - oa), m = (int)(eb - ob);
+  if (n < 1 || m < 1) return true;                                               // reported by the plan
+  const int R = team_rows_per_lane<DK>(n);
+  const int S = (n + 32 * R - 1) / (32 * R);
+  if (S > kTeamWarps && (long long)m > gcols) return false;
+  if (threadIdx.x < kTeamWarps) {
+    prog[threadIdx.x] = 0;
+    cons[threadIdx.x] = 0;
+  }
+  __syncthreads();
+  TeamIO<TeamRing<DK>::value> io;
+  io.gbuf = gbuf;
+  io.ring = ring;
+  io.prog = prog;
+  io.cons = cons;
+  io.w = w;
+  io.nw = kTeamWarps;
+  io.err = a.err;
+  io.timeout_ns = a.timeout_ns;
+  const Cd* pts = static_cast<const Cd*>(a.points);
+  const bool last_warp = w == (S - 1) % kTeamWarps;
+  if constexpr (std::is_same<V, I32>::value) {
+    if (wentry & kNarrowBit) {
+      const float r = team_dfd_any<I32B, DK>(pts + oa * a.dim, n, pts + ob * a.dim, m, a.dim, a.vec != 0, L, w,
+                                             stage, &io);
+      if (last_warp && L == 0) write_result<I32B>(a.out_dist, a.out_dist2, k, r);
+      __syncthreads();
+      return true;
+    }
+  }
+  const typename V::value r =
+      team_dfd_any<V, DK>(pts + oa * a.dim, n, pts + ob * a.dim, m, a.dim, a.vec != 0, L, w, stage, &io);
+  if (last_warp && L == 0) write_result<V>(a.out_dist, a.out_dist2, k, r);
+  __syncthreads();
+  return true;
+}
+
+// Persistent CTAs in three phases:
+//  1. team items (the front of the worklist): the CTA's 8 warps run one
+//     pair of several stripes together, as a pipeline over the columns --
+//     pairs too long for one warp to finish early, or too wide for one
+//     warp's row buffer; their wrap-around row lives in the CTA's eight
+//     contiguous warp buffers (8 * buf_cols columns);
+//  2. warp items: one warp per pair (warp_dfd), as many at a time as warps;
+//  3. the last CTA to finish runs the team pairs that were wider than a
+//     CTA's buffers, with every warp buffer of the launch as one row buffer
+//     (all other CTAs are done with theirs); a pair wider still gets NaN /
+//     -1 outputs and DFD_ERR_UNSUPPORTED in the error word.
 template <class V, int DK>
 __global__ void __launch_bounds__(256, kBlocksPerSM<DK>::value) batch_kernel(BatchArgs a) {
   using T = typename V::value;
   using Cd = typename V::coord;
   __shared__ uint4 stage_sm[8][QStage<DK>::RECS];
+  __shared__ unsigned long long team_ring[kTeamWarps * TeamRing<DK>::value];
+  __shared__ unsigned long long team_prog[kTeamWarps], team_cons[kTeamWarps];
+  __shared__ int cta_word;
   uint4* stage = stage_sm[threadIdx.x >> 5];
   const int L = threadIdx.x & 31;
   const int64_t gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   T* buf = static_cast<T*>(a.rowbuf) + gw * (int64_t)a.buf_cols;
   const Cd* pts = static_cast<const Cd*>(a.points);
   const int64_t total = a.offsets[a.n_curves];
-  if (ld_relaxed_i32(a.err) != 0) return;
+  if (threadIdx.x == 0) cta_word = ld_relaxed_i32(a.err);
+  __syncthreads();
+  if (cta_word != 0) return;   // CTA-uniform
+  const long long n_team = a.n_team ? (long long)*a.n_team : 0;
+
+  // 1. team items
+  if (n_team > 0) {
+    void* gbuf = static_cast<T*>(a.rowbuf) + (int64_t)blockIdx.x * kTeamWarps * a.buf_cols;
+    for (bool first = true;; first = false) {
+      __syncthreads();
+      if (threadIdx.x == 0)
+        cta_word = first ? team_pop_first(a.team_counter, a.sm_rank, a.n_sm, n_team) : atomicAdd(a.team_counter, 1);
+      __syncthreads();
+      const int item = cta_word;
+      if (item >= n_team) break;
+      const unsigned we = a.worklist[item];
+      if (!run_team_pair<V, DK>(a, we, gbuf, (long long)kTeamWarps * a.buf_cols, stage, team_ring, team_prog,
+                                team_cons) &&
+          threadIdx.x == 0)
+        a.deferred[atomicAdd(a.n_deferred, 1u)] = we;
+    }
+  }
+
+  // 2. warp items
+  const long long n_warp = a.n_items - n_team;
   for (bool first = true;; first = false) {
     int item = 0;
-    if (L == 0) item = first ? pop_first(a.counter, a.sm_rank, a.n_sm, a.n_items) : atomicAdd(a.counter, 1);
+    if (L == 0) item = first ? pop_first(a.counter, a.sm_rank, a.n_sm, n_warp) : atomicAdd(a.counter, 1);
     item = __shfl_sync(0xffffffffu, item, 0);
-    if (item >= a.n_items) break;
-    const unsigned w = a.worklist[item];
+    if (item >= n_warp) break;
+    const unsigned w = a.worklist[n_team + item];
     const int64_t k = w & (kNarrowBit - 1);
     int32_t ia = a.pairs[2 * k], ib = a.pairs[2 * k + 1];
     if (w >> 31) {
@@ -822,6 +1157,7 @@ __global__ void __launch_bounds__(256, kBlocksPerSM<DK>::value) batch_kernel(Bat
     const int n = (int)(ea - oa), m = (int)(eb - ob);
     if (n < 1 || m < 1) continue;                                            // reported by the plan
     if (!fits_buffer<DK>(n, m, a.buf_cols)) {
+      // only when the plan made no team items (decider-style launches)
       if (L == 0) raise_error(a.err, DFD_ERR_UNSUPPORTED);
       continue;
     }
@@ -837,6 +1173,33 @@ __global__ void __launch_bounds__(256, kBlocksPerSM<DK>::value) batch_kernel(Bat
     const T r = warp_dfd_any<V, DK>(pts + oa * a.dim, n, pts + ob * a.dim, m, a.dim, a.vec != 0, buf, L, 0, 1 << 30,
                                     static_cast<NoAbandon<V>*>(nullptr), stage);
     if (L == 0) write_result<V>(a.out_dist, a.out_dist2, k, r);
+  }
+
+  // 3. the last CTA: team pairs wider than one CTA's buffers
+  if (n_team == 0) return;   // uniform: nothing was deferred
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    cta_word = atomicAdd(a.done_ctas, 1u) == gridDim.x - 1 ? 1 : 0;
+  }
+  __syncthreads();
+  if (cta_word == 0) return;
+  __threadfence();
+  const unsigned nd = *static_cast<volatile unsigned*>(a.n_deferred);
+  const long long pool = (long long)gridDim.x * kTeamWarps * a.buf_cols;
+  for (unsigned d = 0; d < nd; ++d) {
+    const unsigned we = static_cast<volatile unsigned*>(a.deferred)[d];
+    if (!run_team_pair<V, DK>(a, we, a.rowbuf, pool, stage, team_ring, team_prog, team_cons) && threadIdx.x == 0) {
+      const int64_t k = we & (kNarrowBit - 1);
+      if constexpr (std::is_same<V, F32>::value) {
+        if (a.out_dist2) static_cast<float*>(a.out_dist2)[k] = __int_as_float(0x7fffffff);
+        if (a.out_dist) static_cast<float*>(a.out_dist)[k] = __int_as_float(0x7fffffff);
+      } else {
+        if (a.out_dist2) static_cast<long long*>(a.out_dist2)[k] = -1;
+        if (a.out_dist) static_cast<double*>(a.out_dist)[k] = __longlong_as_double(0x7fffffffffffffffLL);
+      }
+      raise_error(a.err, DFD_ERR_UNSUPPORTED);
+    }
   }
 }
 

@@ -83,7 +83,7 @@ int resident_blocks(const dfd_context* ctx, K kernel, int threads) {
 // Scratch of one batch launch: [counter | hist | cursor] [bucket] [worklist]
 // [bbox] [row buffers].
 struct BatchLayout {
-  size_t off_hist, off_cursor, off_smrank, off_bucket, off_work, off_bbox, off_buf, total;
+  size_t off_hist, off_cursor, off_smrank, off_bucket, off_work, off_defer, off_bbox, off_buf, total;
 };
 template <class V, int DK>
 BatchLayout batch_layout(int64_t n_curves, int64_t n_pairs, int blocks, bool bbox_ext, int buf_cols) {
@@ -95,7 +95,8 @@ BatchLayout batch_layout(int64_t n_curves, int64_t n_pairs, int blocks, bool bbo
   l.off_smrank = align_up(l.off_cursor + batch::NBUCKET * 4, 256);
   l.off_bucket = align_up(l.off_smrank + batch::kSmSlots * 4, 256);
   l.off_work = align_up(l.off_bucket + (size_t)n_pairs * 2, 256);
-  l.off_bbox = align_up(l.off_work + (size_t)n_pairs * 4, 256);
+  l.off_defer = align_up(l.off_work + (size_t)n_pairs * 4, 256);
+  l.off_bbox = align_up(l.off_defer + (size_t)n_pairs * 4, 256);
   l.off_buf = align_up(l.off_bbox + (kInt && !bbox_ext ? (size_t)n_curves * DK * 2 * 4 : 0), 256);
   l.total = l.off_buf + (size_t)blocks * (THREADS / 32) * (size_t)buf_cols * sizeof(typename V::value);
   return l;
@@ -108,7 +109,7 @@ template <class V, int DK>
 dfd_status batch_prepare(dfd_context* ctx, int dim, const void* points, const int64_t* offsets, int64_t n_curves,
                          const int32_t* pairs, int64_t n_pairs, cudaStream_t s, int blocks, batch::BatchArgs* ba,
                          int64_t first_curve = 0, int* bbox_ext = nullptr, char* scratch_ext = nullptr,
-                         size_t scratch_ext_bytes = 0, int buf_cols = batch::BUF_COLS) {
+                         size_t scratch_ext_bytes = 0, int buf_cols = batch::BUF_COLS, int team = 0) {
   constexpr bool kInt = std::is_same<V, I32>::value;
   if (n_pairs >= (int64_t)batch::kNarrowBit) return DFD_ERR_UNSUPPORTED;
   const BatchLayout lay = batch_layout<V, DK>(n_curves, n_pairs, blocks, bbox_ext != nullptr, buf_cols);
@@ -146,6 +147,9 @@ dfd_status batch_prepare(dfd_context* ctx, int dim, const void* points, const in
   pa.err = ctx->d_err;
   pa.rmax = batch::Rmax<DK>::value;
   pa.order = ctx->batch_order[std::is_same<V, F32>::value ? 0 : 1][dim_class_index(DK)];
+  pa.team = team;
+  pa.buf_cols = buf_cols;
+  pa.ctas = blocks;
   const int pblocks = (int)std::min<int64_t>((n_pairs + 255) / 256, 8 * (int64_t)ctx->num_sms);
   batch::plan_hist_kernel<<<pblocks, 256, 0, s>>>(pa);
   batch::plan_scan_kernel<<<1, batch::NBUCKET, 0, s>>>(pa);
@@ -166,7 +170,25 @@ dfd_status batch_prepare(dfd_context* ctx, int dim, const void* points, const in
   ba->err = ctx->d_err;
   ba->out_dist = nullptr;
   ba->out_dist2 = nullptr;
+  // CTA teams: header words after the warp counter (zeroed above); the
+  // number of team items is the end of the last team bucket after the scatter
+  ba->n_team = team ? pa.cursor + (batch::NTB - 1) : nullptr;
+  ba->team_counter = reinterpret_cast<int*>(base + 4);
+  ba->done_ctas = reinterpret_cast<unsigned*>(base + 8);
+  ba->n_deferred = reinterpret_cast<unsigned*>(base + 12);
+  ba->deferred = reinterpret_cast<unsigned*>(base + lay.off_defer);
+  ba->timeout_ns = timeout_ns(ctx);
   return cuda_status(cudaGetLastError());
+}
+
+// Team mode of a ragged batch launch (see batch_kernel and team_pays): the
+// context's setting for (dtype, dim class) -- 1 only the pairs too wide for
+// one warp's row buffer, 2 every pair of several stripes -- or by default
+// (3) those for which the plan's latency model expects a team to finish
+// sooner, and the wide ones.
+inline int batch_team_mode(const dfd_context* ctx, bool f32, int dk) {
+  const int set = ctx->batch_team[f32 ? 0 : 1][dim_class_index(dk)];
+  return set > 0 ? set : 3;
 }
 
 // Scratch bytes of one batch launch over `n_pairs` pairs of `n_curves`
@@ -188,8 +210,9 @@ dfd_status batch_launch_range(dfd_context* ctx, int dim, const void* points, con
                               char* scratch_ext, size_t scratch_ext_bytes, cudaEvent_t prepared, int buf_cols) {
   const int blocks = resident_blocks(ctx, batch::batch_kernel<V, DK>, 256);
   batch::BatchArgs ba;
+  const int team = batch_team_mode(ctx, std::is_same<V, F32>::value, DK);
   dfd_status st = batch_prepare<V, DK>(ctx, dim, points, offsets, n_curves, pairs, n_pairs, s, blocks, &ba,
-                                       first_curve, bbox_ext, scratch_ext, scratch_ext_bytes, buf_cols);
+                                       first_curve, bbox_ext, scratch_ext, scratch_ext_bytes, buf_cols, team);
   if (st != DFD_OK) return st;
   if (prepared) cudaEventRecord(prepared, s);
   ba.out_dist = out_dist;

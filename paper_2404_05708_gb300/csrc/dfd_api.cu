@@ -792,6 +792,13 @@ dfd_status dfd_batch_set_order(dfd_context* ctx, dfd_dtype dtype, int dim, int o
   return DFD_OK;
 }
 
+dfd_status dfd_batch_set_team(dfd_context* ctx, dfd_dtype dtype, int dim, int mode) {
+  if (!ctx || (dtype != DFD_F32 && dtype != DFD_I32) || dim < 1 || mode < 0 || mode > 2) return DFD_ERR_INVALID_ARG;
+  if (dim > 16) return DFD_ERR_UNSUPPORTED;
+  ctx->batch_team[dtype == DFD_F32 ? 0 : 1][dim_class_index(dim_class(dim))] = (signed char)mode;
+  return DFD_OK;
+}
+
 dfd_status dfd_batch_set_row_buffer(dfd_context* ctx, int cols) {
   // whole 32-column blocks; the widest a warp's row index reaches is INT32_MAX
   if (!ctx || cols < kDefaultBatchBufCols || cols > (1 << 28)) return DFD_ERR_INVALID_ARG;
@@ -808,7 +815,8 @@ dfd_status dfd_batch_autotune(dfd_context* ctx, dfd_dtype dtype, int dim, const 
   if ((st = set_device(ctx)) != DFD_OK) return st;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   signed char& slot = ctx->batch_order[dtype == DFD_F32 ? 0 : 1][dim_class_index(dim_class(dim))];
-  const signed char keep = slot;
+  signed char& tslot = ctx->batch_team[dtype == DFD_F32 ? 0 : 1][dim_class_index(dim_class(dim))];
+  const signed char keep = slot, tkeep = tslot;
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess) {
     cudaGetLastError();
@@ -820,9 +828,13 @@ dfd_status dfd_batch_autotune(dfd_context* ctx, dfd_dtype dtype, int dim, const 
     return DFD_ERR_CUDA;
   }
   float best_ms = 0.f;
-  int best = keep;
-  for (int order = 0; order < 2 && st == DFD_OK && n_pairs > 0; ++order) {
+  int best = keep, best_team = tkeep;
+  // packing order x team mode (1: only pairs too wide for a warp's buffer
+  // run as CTA teams, 2: every pair of several stripes does)
+  for (int c = 0; c < 4 && st == DFD_OK && n_pairs > 0; ++c) {
+    const int order = c & 1, team = 1 + (c >> 1);
     slot = (signed char)order;
+    tslot = (signed char)team;
     // one untimed run (sizes the scratch), then three timed
     st = batch_run(ctx, dtype, dim, points, offsets, n_curves, pairs, n_pairs, out_dist, out_dist2, s);
     if (st != DFD_OK) break;
@@ -833,17 +845,28 @@ dfd_status dfd_batch_autotune(dfd_context* ctx, dfd_dtype dtype, int dim, const 
     float ms = 0.f;
     if (st == DFD_OK && (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
       st = DFD_ERR_CUDA;
-    if (st == DFD_OK && (order == 0 || ms < best_ms)) {
+    if (st == DFD_OK && (c == 0 || ms < best_ms)) {
       best_ms = ms;
       best = order;
+      best_team = team;
     }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   cudaGetLastError();
   slot = (signed char)(st == DFD_OK ? best : keep);
+  tslot = (signed char)(st == DFD_OK ? best_team : tkeep);
   if (best_order) *best_order = slot;
   return st;
+}
+
+dfd_status dfd_batch_tuned(dfd_context* ctx, dfd_dtype dtype, int dim, int* order, int* team) {
+  if (!ctx || (dtype != DFD_F32 && dtype != DFD_I32) || dim < 1) return DFD_ERR_INVALID_ARG;
+  if (dim > 16) return DFD_ERR_UNSUPPORTED;
+  const int t = dtype == DFD_F32 ? 0 : 1, d = dim_class_index(dim_class(dim));
+  if (order) *order = ctx->batch_order[t][d];
+  if (team) *team = ctx->batch_team[t][d];
+  return DFD_OK;
 }
 
 dfd_status dfd_batch_decide(dfd_context* ctx, dfd_dtype dtype, int dim, const void* points, const int64_t* offsets,

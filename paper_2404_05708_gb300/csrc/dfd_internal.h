@@ -46,6 +46,7 @@ struct dfd_context {
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   std::map<uint64_t, dfd::WaveShape> tuned;   // autotuned wavefront shapes
   signed char batch_order[2][5] = {};         // batch packing order per (float32 / int32, dim class 2,3,4,8,16)
+  signed char batch_team[2][5] = {};          // batch team mode per (dtype, dim class): 0 auto, 1 wide pairs, 2 all multi-stripe
   cudaStream_t copy_stream = nullptr;         // dfd_batch_host: point slices (created on first use)
   cudaEvent_t slice_ev[dfd::kMaxSlices + 1] = {};   // one per slice, and one for the allocation
   int batch_buf_cols = dfd::kDefaultBatchBufCols;   // ragged batch: row buffer columns per warp

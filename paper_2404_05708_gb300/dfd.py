@@ -84,6 +84,8 @@ _SIGS = {
     "dfd_batch_autotune": [_VP, _INT, _INT, _VP, _VP, _I64, _VP, _I64, _VP, _VP, ctypes.POINTER(ctypes.c_int), _VP],
     "dfd_batch_set_order": [_VP, _INT, _INT, _INT],
     "dfd_batch_set_row_buffer": [_VP, _INT],
+    "dfd_batch_set_team": [_VP, _INT, _INT, _INT],
+    "dfd_batch_tuned": [_VP, _INT, _INT, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)],
     "dfd_matrix": [_VP, _INT, _INT, _VP, _VP, _I64, _VP, _VP, _VP],
     "dfd_batch_decide": [_VP, _INT, _INT, _VP, _VP, _I64, _VP, _I64, _VP, ctypes.c_double, _VP, _VP, _VP, _VP],
     "dfd_mc_pair": [_VP, _INT, _VP, _I64, _VP, _I64, _VP, _VP, ctypes.c_float, ctypes.c_float, _I64, _VP, _VP, _VP],
@@ -574,6 +576,18 @@ class Context:
     def set_batch_order(self, dtype: int, dim: int, order: int):
         """Set the ragged batch's packing order (0 variant-major, 1 cost-descending)."""
         _check(load_library().dfd_batch_set_order(self.handle, dtype, dim, order), "dfd_batch_set_order")
+
+    def set_batch_team(self, dtype: int, dim: int, mode: int):
+        """Which ragged-batch pairs run as CTA teams: 0 auto, 1 only pairs too wide
+        for one warp's row buffer, 2 every pair of several stripes."""
+        _check(load_library().dfd_batch_set_team(self.handle, dtype, dim, mode), "dfd_batch_set_team")
+
+    def batch_tuned(self, dtype: int, dim: int):
+        """(packing order, team mode) recorded for (dtype, dim class)."""
+        o, t = ctypes.c_int(0), ctypes.c_int(0)
+        _check(load_library().dfd_batch_tuned(self.handle, dtype, dim, ctypes.byref(o), ctypes.byref(t)),
+               "dfd_batch_tuned")
+        return o.value, t.value
 
     def set_batch_row_buffer(self, cols: int):
         """Widen the ragged batch's per-warp row buffer (columns, >= 4096): pairs

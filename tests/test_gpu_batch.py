@@ -198,11 +198,11 @@ def test_batch_host_boxes_across_slices(dctx):
 @pytest.mark.parametrize("dtype", ["f32", "i32"])
 def test_batch_wide_pairs_row_buffer(dtype):
     """Pairs that run several stripes (both curves longer than 256 points,
-    2-D) hand a row of their longer curve's length between stripes through a
-    per-warp buffer.  With the default 4096 columns dfd_batch reports
-    DFD_ERR_UNSUPPORTED for the wider ones and still computes the rest;
-    once the buffer is widened every pair equals the oracle; dfd_batch_host
-    widens it by itself."""
+    2-D) and whose longer curve is wider than one warp's row buffer (4096
+    columns by default) run as CTA teams, whose wrap-around row has the
+    CTA's eight warp buffers: with the default buffer every pair equals the
+    oracle and the error word stays clear; widened buffers (the pairs then
+    run one warp each) and dfd_batch_host give the same bits."""
     from paper_2404_05708_gb300 import dfd
     ctx = dfd.Context(0)
     rng = np.random.default_rng(31)
@@ -218,9 +218,13 @@ def test_batch_wide_pairs_row_buffer(dtype):
     assert wide.sum() == 6 and (~wide).sum() == 3
     b = workloads.Batch(points=pts, offsets=off, pairs=pairs)
     want, _ = oracle.batch(pts, off, pairs, mirror=(dtype == "f32"))
-    d, d2 = run_batch(ctx, b)
-    assert ctx.get_error() == dfd.STATUS_CODE["DFD_ERR_UNSUPPORTED"]
-    assert np.array_equal(d2[~wide], want[~wide])
+    code = dfd.DFD_F32 if dtype == "f32" else dfd.DFD_I32
+    for mode in (1, 2):   # only the wide pairs as teams / every multi-stripe pair
+        ctx.set_batch_team(code, 2, mode)
+        d, d2 = run_batch(ctx, b)
+        assert ctx.get_error() == 0
+        assert np.array_equal(d2, want)
+    ctx.set_batch_team(code, 2, 0)
     with pytest.raises(dfd.DFDError):
         ctx.set_batch_row_buffer(1000)
     ctx.set_batch_row_buffer(9000)
@@ -232,6 +236,76 @@ def test_batch_wide_pairs_row_buffer(dtype):
     d, d2 = ctx.batch_host(pts, off, pairs)
     assert np.array_equal(d2, want)
     ctx.close()
+
+
+def team_edges(dtype, dim, seed):
+    """Pairs on both sides of every size-class edge of the ragged batch
+    (2-D: 32 * Rmax = 256 rows per stripe; a team of 8 warps spreads up to
+    8 stripes of up to 256 rows, 2048 rows, one stripe each, and cycles
+    beyond; one warp's row buffer holds 4096 columns, a CTA's 32,768):
+    rows 255 / 256 (one stripe), 257 (two), 1024 (8 stripes of 128), 2047,
+    2048 (8 of 256), 2049 and 2600 (cycling through the CTA buffer), against
+    columns 260 .. 40,000; 2049 x 33,000 and 2600 x 40,000 are wider than a
+    CTA's buffers and run last, on every buffer of the launch."""
+    rng = np.random.default_rng(seed)
+    rows = [255, 256, 257, 1024, 2047, 2048, 2049, 2600]
+    cols = [260, 1500, 4095, 4097, 9000]
+    shapes = [(r, c) for r in rows for c in cols if c >= r] + [(2048, 2049), (2049, 2049), (2600, 2601),
+                                                                  (257, 32768), (2049, 33000), (2600, 40000)]
+    lens, pairs = [], []
+    for k, (r, c) in enumerate(shapes):
+        a, bb = (r, c) if k % 2 == 0 else (c, r)   # both orders of (rows, cols)
+        pairs.append((len(lens), len(lens) + 1))
+        lens += [a, bb]
+    lens = np.array(lens, np.int64)
+    off = np.zeros(len(lens) + 1, np.int64)
+    np.cumsum(lens, out=off[1:])
+    if dtype == "i32":
+        pts = np.cumsum(rng.integers(-64, 65, size=(off[-1], dim)), axis=0).astype(np.int32)
+        # two pairs in the exact int64 value class: 255 x 1500 (one warp) and 1024 x 4097 (a team)
+        for k in (1, shapes.index((1024, 4097))):
+            pts[off[2 * k]:off[2 * k + 2]] *= 4096
+    else:
+        pts = np.cumsum(rng.normal(0, 1, size=(off[-1], dim)), axis=0).astype(np.float32)
+    return workloads.Batch(points=pts, offsets=off, pairs=np.array(pairs, np.int32))
+
+
+@pytest.mark.parametrize("dtype,dim", [("i32", 2), ("f32", 2), ("f32", 3)])
+def test_batch_team_modes_bit_identical(dctx, dtype, dim):
+    """Every team mode (auto; only wide pairs; every multi-stripe pair)
+    gives every pair the oracle's value bit for bit (float32: the selection
+    mirror), on both sides of each size-class edge, with a clear error word."""
+    from paper_2404_05708_gb300 import dfd
+    code = dfd.DFD_I32 if dtype == "i32" else dfd.DFD_F32
+    b = team_edges(dtype, dim, 150 + dim)
+    want, _ = oracle.batch(b.points, b.offsets, b.pairs, mirror=(dtype == "f32"))
+    outs = []
+    for mode in (0, 1, 2):
+        dctx.set_batch_team(code, dim, mode)
+        d, d2 = run_batch(dctx, b)
+        assert dctx.get_error() == 0
+        assert np.array_equal(d2, want), (mode, np.nonzero(d2 != want)[0][:10])
+        outs.append(d)
+    assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[0], outs[2])
+    dctx.set_batch_team(code, dim, 0)
+
+
+def test_batch_team_16d_float(dctx):
+    """16-D points (4 rows per lane, 128-column team rings): a team of 8
+    stripes of 128 rows, one cycling through 9 stripes, and one wide pair."""
+    from paper_2404_05708_gb300 import dfd
+    rng = np.random.default_rng(160)
+    lens = np.array([1024, 1100, 1025, 1200, 300, 5000, 130, 700])
+    off = np.concatenate([[0], np.cumsum(lens)]).astype(np.int64)
+    pts = np.cumsum(rng.normal(0, 1, size=(int(off[-1]), 16)), axis=0).astype(np.float32)
+    pairs = np.array([[0, 1], [2, 3], [4, 5], [6, 7], [1, 2]], np.int32)
+    b = workloads.Batch(points=pts, offsets=off, pairs=pairs)
+    for mode in (1, 2):
+        dctx.set_batch_team(dfd.DFD_F32, 16, mode)
+        d, d2 = run_batch(dctx, b)
+        assert dctx.get_error() == 0
+        check_f32(d, d2, b)
+    dctx.set_batch_team(dfd.DFD_F32, 16, 0)
 
 
 def test_batch_host_slices_without_pairs_and_checks():
