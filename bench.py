@@ -615,6 +615,26 @@ def serve_sweep(ctx, rates, seconds, repeats, tick_cells, stripes_per_tick):
     for d in (2, 3):
         srv.add_candidates(pools[d].points, pools[d].offsets)
     sweep = []
+    # A separate process that sleeps 1 ms at a time and reports every sleep that
+    # overran by more than 5 ms: a pause of the whole host (seen by this
+    # process and the watcher alike) shows there, so a latency outlier can be
+    # told apart from a stall of the server.  Times are CLOCK_MONOTONIC, the
+    # server's clock.
+    watch_s = 60.0 + sum(max(20, int(r * seconds)) / r + 2.0 for r in rates) * repeats
+    watcher = subprocess.Popen(
+        [sys.executable, "-c",
+         "import sys,time\n"
+         "end=time.monotonic()+float(sys.argv[1])\n"
+         "while time.monotonic()<end:\n"
+         "    a=time.monotonic(); time.sleep(0.001); d=time.monotonic()-a\n"
+         "    if d>0.006: print(f'{a:.6f} {d*1e3:.2f}', flush=True)\n",
+         str(watch_s)], stdout=subprocess.PIPE, text=True)
+    gaps = []
+
+    def read_gaps():
+        for ln in watcher.stdout:
+            gaps.append(tuple(float(x) for x in ln.split()))
+    threading.Thread(target=read_gaps, daemon=True).start()
     # warm-up
     w = workloads.serving_requests(20, 1000.0, {2: 1 << 16, 3: 1 << 16}, seed=99)
     for t in [srv.submit(r.query, r.cand_ids) for r in w]:
@@ -643,10 +663,13 @@ def serve_sweep(ctx, rates, seconds, repeats, tick_cells, stripes_per_tick):
                 srv.wait(t)
             gc.enable()
             st = srv.stats()
+            t_end = srv.now()
+            stalls = [round(d, 1) for a, d in list(gaps) if t0 <= a <= t_end]
             sweep.append({"rate_req_s": rate, "repeat": rep, "requests": n_req, "p50_ms": st["p50_ms"],
                           "p99_ms": st["p99_ms"], "gcups_wall": st["gcups_wall"], "gcups_busy": st["gcups_busy"],
-                          "ticks": st["ticks"], "cells": st["cells"]})
+                          "ticks": st["ticks"], "cells": st["cells"], "host_stalls_ms": stalls})
     srv.close()
+    watcher.terminate()
     return sweep
 
 

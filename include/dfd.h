@@ -425,6 +425,37 @@ dfd_status dfd_server_wait(dfd_server* server, uint64_t ticket, double timeout_m
 dfd_status dfd_server_cancel(dfd_server* server, uint64_t ticket);
 dfd_status dfd_server_stats(dfd_server* server, dfd_serving_stats* out);
 dfd_status dfd_server_stats_reset(dfd_server* server);
+/* Per-request record of each request completed since the last stats reset
+   (at most 2^22), in completion order, times on the dfd_server_now clock:
+   where a request's latency went -- waiting to be submitted (submit_s -
+   arrival_s), queued for admission (admit_s - submit_s), for its first tick
+   (launch_s - admit_s), and on the GPU (done_s - launch_s).  Copies up to
+   cap records to out; *n receives the number recorded. */
+typedef struct dfd_request_record {
+  uint64_t ticket;
+  double arrival_s, submit_s, admit_s, launch_s, done_s;
+  double cells;
+  int n, k, dim, pad;
+  double locked_s;           /* submission took the server's lock */
+} dfd_request_record;
+dfd_status dfd_server_request_log(dfd_server* server, dfd_request_record* out, int64_t cap, int64_t* n);
+/* Per-tick record of each tick retired since the last stats reset (at most
+   2^20): when the scheduler began building it and returned from launching it,
+   when it was retired, its device time (first to last event of the tick),
+   its cells, long-pair items, short-pair slices, results and newly admitted
+   requests; of the host time before the launch, the admission and tick
+   building shares, and the slowest single CUDA call of the launch (which:
+   1 event record, 2 stream wait, 3 query / id upload, 4 descriptor copy,
+   5 counter reset, 6 kernel launch, 7 stream join, 8 result copy, 9 final
+   event).  Copies up to cap records to out; *n receives the number. */
+typedef struct dfd_tick_record {
+  double build_s, launched_s, retired_s, gpu_ms, cells;
+  int n_items, n_slices, n_outs, n_admitted;
+  double admit_ms, build_ms, slow_call_ms;
+  int slow_call, pad;
+  double sync_s, synced_s, locked_s;   /* scheduler: began waiting for the tick, saw it done, retook the lock */
+} dfd_tick_record;
+dfd_status dfd_server_tick_log(dfd_server* server, dfd_tick_record* out, int64_t cap, int64_t* n);
 /* The server's clock in seconds (monotonic). */
 double dfd_server_now(dfd_server* server);
 

@@ -237,6 +237,8 @@ struct Request {
   std::vector<int64_t> ids;
   float* host_out = nullptr;
   double t_arrival = 0, t_done = 0;
+  double t_submit = 0, t_admit = 0, t_launch = 0;   // submission, admission, first tick launch
+  double t_locked = 0;                                // submission: server lock taken
   dfd_status status = DFD_ERR_NOT_READY;
   bool cancelled = false;
   size_t q_off = SIZE_MAX;
@@ -266,6 +268,12 @@ struct SliceRec {
 constexpr int NSTREAM = 2;
 
 struct Tick {
+  double t_build = 0, t_launched = 0;   // host: build began, launch calls returned
+  double t_admitted = 0, t_built = 0;   // host: admission and tick building done
+  double t_sync0 = 0, t_sync1 = 0, t_locked = 0;   // host: wait for the tick's last event, lock retaken
+  double slow_call_ms = 0;              // the slowest CUDA call of the launch, and which (1-9)
+  int slow_call = 0;
+  int n_admitted = 0;
   cudaStream_t stream[NSTREAM] = {};
   float* rowbuf[NSTREAM] = {};   // per-warp row buffers of the launches on each stream
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
@@ -336,6 +344,8 @@ struct dfd_server {
   std::atomic<bool> stop{false};
   // statistics
   std::vector<double> latencies_ms;
+  std::vector<dfd_request_record> log;   // completed requests (since the last stats reset)
+  std::vector<dfd_tick_record> tick_log; // retired ticks (since the last stats reset)
   double busy_ms = 0, cells_done = 0, t_first = -1, t_last = 0;
   uint64_t completed = 0, n_cancelled = 0, n_ticks = 0;
   dfd_status fatal = DFD_OK;
@@ -412,6 +422,22 @@ void finish_request(dfd_server* s, Request* r, dfd_status st, double t) {
   if (st == DFD_OK) {
     s->completed++;
     s->latencies_ms.push_back((t - r->t_arrival) * 1e3);
+    if (s->log.size() < ((size_t)1 << 22)) {
+      dfd_request_record rec;
+      rec.ticket = r->ticket;
+      rec.arrival_s = r->t_arrival;
+      rec.submit_s = r->t_submit;
+      rec.admit_s = r->t_admit;
+      rec.launch_s = r->t_launch;
+      rec.done_s = t;
+      rec.cells = r->cells;
+      rec.locked_s = r->t_locked;
+      rec.n = r->n;
+      rec.k = (int)r->ids.size();
+      rec.dim = r->dim;
+      rec.pad = 0;
+      s->log.push_back(rec);
+    }
     s->cells_done += r->cells;
     s->t_last = t;
   } else {
@@ -494,6 +520,7 @@ void admit(dfd_server* s, Tick& t) {
       break;
     }
     s->pending.pop_front();
+    r->t_admit = now_s();
     r->q_off = off;
     r->cid_off = coff;
     r->cid_bytes = ib;
@@ -635,21 +662,42 @@ void build_tick(dfd_server* s, Tick& t) {
 
 void launch_tick(dfd_server* s, Tick& t) {
   const size_t n_it = t.items.size(), n_sl = t.slices.size();
+  t.slow_call_ms = 0;
+  t.slow_call = 0;
+  double tc = now_s();
+  // the slowest CUDA call of the launch (host time), for the tick log
+  auto mark = [&](int id) {
+    const double x = now_s();
+    if ((x - tc) * 1e3 > t.slow_call_ms) {
+      t.slow_call_ms = (x - tc) * 1e3;
+      t.slow_call = id;
+    }
+    tc = x;
+  };
   if (n_it) std::memcpy(t.h_desc, t.items.data(), n_it * sizeof(Item));
   Slice* hs = reinterpret_cast<Slice*>(t.h_desc + t.off_slices);
   for (size_t j = 0; j < n_sl; ++j) hs[j] = t.slices[j].d;
   std::memcpy(t.h_desc + t.off_prefix, t.prefix.data(), (n_sl + 1) * sizeof(int));
   cudaStream_t st = t.stream[0];
+  tc = now_s();
   cudaEventRecord(t.ev0, st);
+  mark(1);
   // queries and ids admitted with earlier ticks were uploaded on their
   // streams: order this tick after those copies (not after their kernels)
   if (s->last_launched) cudaStreamWaitEvent(st, s->last_launched->ev_up, 0);
-  for (const auto& u : t.uploads)
+  mark(2);
+  for (const auto& u : t.uploads) {
     cudaMemcpyAsync(s->arena.ptr(u.arena_off), t.h_stage + u.stage_off, u.bytes, cudaMemcpyHostToDevice, st);
+    mark(3);
+  }
   cudaEventRecord(t.ev_up, st);
+  mark(1);
   if (n_it || n_sl) cudaMemcpyAsync(t.d_desc, t.h_desc, t.desc_bytes, cudaMemcpyHostToDevice, st);
+  mark(4);
   cudaMemsetAsync(t.d_counter, 0, (MAX_DIM + 1) * sizeof(int), st);
+  mark(5);
   cudaEventRecord(t.ev_fork, st);   // the tick's inputs are in place
+  mark(1);
   const Item* d_items = reinterpret_cast<const Item*>(t.d_desc);
   const Slice* d_slices = reinterpret_cast<const Slice*>(t.d_desc + t.off_slices);
   const int* d_prefix = reinterpret_cast<const int*>(t.d_desc + t.off_prefix);
@@ -666,6 +714,7 @@ void launch_tick(dfd_server* s, Tick& t) {
     const int lane = n_launch++ % NSTREAM;
     cudaStream_t ls = t.stream[lane];
     if (n_launch == 2) cudaStreamWaitEvent(ls, t.ev_fork, 0);
+    mark(2);
     ServeArgs a;
     a.items = d_items + ib;
     a.n_items = (int)(ie - ib);
@@ -697,17 +746,26 @@ void launch_tick(dfd_server* s, Tick& t) {
         break;
     }
 #undef DFD_SERVE_CASE
+    mark(6);
     ib = ie;
     sb = se;
   }
   if (n_launch > 1) {
     cudaEventRecord(t.ev_join, t.stream[1]);
     cudaStreamWaitEvent(st, t.ev_join, 0);
+    mark(7);
   }
   if (t.n_outs)
     cudaMemcpyAsync(t.h_out, t.d_out, t.n_outs * sizeof(float), cudaMemcpyDeviceToHost, st);
+  mark(8);
   cudaEventRecord(t.ev1, st);
+  mark(9);
   s->last_launched = &t;
+  const double now = now_s();
+  for (Request* r : t.members)
+    if (r->t_launch == 0) r->t_launch = now;
+  for (const SliceRec& sr : t.slices)
+    if (sr.r->t_launch == 0) sr.r->t_launch = now;
   if (cudaGetLastError() != cudaSuccess) s->fatal = DFD_ERR_CUDA;
 }
 
@@ -724,6 +782,27 @@ void retire_tick(dfd_server* s, Tick& t) {
   cudaGetLastError();
   s->last_retired = &t;
   s->n_ticks++;
+  if (s->tick_log.size() < ((size_t)1 << 20)) {
+    dfd_tick_record tr;
+    tr.build_s = t.t_build;
+    tr.launched_s = t.t_launched;
+    tr.retired_s = now;
+    tr.gpu_ms = ms;
+    tr.cells = t.cells;
+    tr.n_items = (int)t.items.size();
+    tr.n_slices = (int)t.slices.size();
+    tr.n_outs = (int)t.n_outs;
+    tr.n_admitted = t.n_admitted;
+    tr.admit_ms = (t.t_admitted - t.t_build) * 1e3;
+    tr.build_ms = (t.t_built - t.t_admitted) * 1e3;
+    tr.slow_call_ms = t.slow_call_ms;
+    tr.slow_call = t.slow_call;
+    tr.pad = 0;
+    tr.sync_s = t.t_sync0;
+    tr.synced_s = t.t_sync1;
+    tr.locked_s = t.t_locked;
+    s->tick_log.push_back(tr);
+  }
   for (LongPair* p : t.longs_issued) p->busy = false;
   for (size_t i = 0; i < t.outs.size(); ++i) {
     Request* r = t.outs[i].first;
@@ -761,13 +840,19 @@ void worker_loop(dfd_server* s) {
     Tick& t = s->ticks[s->next_tick];
     bool launched = false;
     if (s->inflight.size() < NTICK - 1) {
+      t.t_build = now_s();
+      const size_t before = s->active.size();
       admit(s, t);
+      t.t_admitted = now_s();
+      t.n_admitted = (int)(s->active.size() - before);
       build_tick(s, t);
+      t.t_built = now_s();
       if (!t.items.empty() || !t.slices.empty() || !t.uploads.empty()) {
         if (!ensure_tick_capacity(t, t.desc_bytes, t.n_outs)) {
           s->fatal = DFD_ERR_OOM;
         } else {
           launch_tick(s, t);
+          t.t_launched = now_s();
           s->inflight.push_back(&t);
           s->next_tick = (s->next_tick + 1) % NTICK;
           launched = true;
@@ -777,8 +862,13 @@ void worker_loop(dfd_server* s) {
     if (!s->inflight.empty() && (s->inflight.size() >= NTICK - 1 || !launched)) {
       Tick* old = s->inflight.front();
       lk.unlock();
+      const double w0 = now_s();
       cudaEventSynchronize(old->ev1);
+      const double w1 = now_s();
       lk.lock();
+      old->t_sync0 = w0;
+      old->t_sync1 = w1;
+      old->t_locked = now_s();
       s->inflight.pop_front();
       retire_tick(s, *old);
       continue;
@@ -957,8 +1047,10 @@ dfd_status dfd_server_submit(dfd_server* s, int dim, const float* host_query, in
   r->query.assign(host_query, host_query + n * dim);
   r->ids.assign(cand_ids, cand_ids + k);
   r->host_out = host_out;
-  r->t_arrival = arrival_s >= 0 ? arrival_s : now_s();
+  r->t_submit = now_s();
+  r->t_arrival = arrival_s >= 0 ? arrival_s : r->t_submit;
   std::lock_guard<std::mutex> lk(s->mu);
+  r->t_locked = now_s();
   if (s->fatal != DFD_OK) return s->fatal;
   auto pit = s->pools.find(dim);
   if (pit == s->pools.end()) return DFD_ERR_INVALID_ARG;
@@ -1049,6 +1141,26 @@ dfd_status dfd_server_stats_reset(dfd_server* s) {
   s->completed = 0;
   s->n_cancelled = 0;
   s->n_ticks = 0;
+  s->log.clear();
+  s->tick_log.clear();
+  return DFD_OK;
+}
+
+dfd_status dfd_server_tick_log(dfd_server* s, dfd_tick_record* out, int64_t cap, int64_t* n) {
+  if (!s || !n || cap < 0 || (cap > 0 && !out)) return DFD_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(s->mu);
+  const int64_t m = std::min<int64_t>(cap, (int64_t)s->tick_log.size());
+  if (m > 0) std::memcpy(out, s->tick_log.data(), (size_t)m * sizeof(dfd_tick_record));
+  *n = (int64_t)s->tick_log.size();
+  return DFD_OK;
+}
+
+dfd_status dfd_server_request_log(dfd_server* s, dfd_request_record* out, int64_t cap, int64_t* n) {
+  if (!s || !n || cap < 0 || (cap > 0 && !out)) return DFD_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(s->mu);
+  const int64_t m = std::min<int64_t>(cap, (int64_t)s->log.size());
+  if (m > 0) std::memcpy(out, s->log.data(), (size_t)m * sizeof(dfd_request_record));
+  *n = (int64_t)s->log.size();
   return DFD_OK;
 }
 

@@ -48,6 +48,13 @@ class ServerOptions(ctypes.Structure):
                 ("tick_cells", ctypes.c_double), ("stripes_per_tick", ctypes.c_int)]
 
 
+class RequestRecord(ctypes.Structure):
+    _fields_ = [("ticket", ctypes.c_uint64), ("arrival_s", ctypes.c_double), ("submit_s", ctypes.c_double),
+                ("admit_s", ctypes.c_double), ("launch_s", ctypes.c_double), ("done_s", ctypes.c_double),
+                ("cells", ctypes.c_double), ("n", ctypes.c_int), ("k", ctypes.c_int), ("dim", ctypes.c_int),
+                ("pad", ctypes.c_int), ("locked_s", ctypes.c_double)]
+
+
 class ServingStats(ctypes.Structure):
     _fields_ = [("completed", ctypes.c_uint64), ("cancelled", ctypes.c_uint64), ("ticks", ctypes.c_uint64),
                 ("cells", ctypes.c_double), ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double),
@@ -104,6 +111,8 @@ _SIGS = {
     "dfd_server_cancel": [_VP, ctypes.c_uint64],
     "dfd_server_stats": [_VP, ctypes.POINTER(ServingStats)],
     "dfd_server_stats_reset": [_VP],
+    "dfd_server_request_log": [_VP, _VP, _I64, ctypes.POINTER(_I64)],
+    "dfd_server_tick_log": [_VP, _VP, _I64, ctypes.POINTER(_I64)],
     "dfd_server_now": [_VP],
     "dfd_timing_enable": [_VP, _INT],
     "dfd_timing_last": [_VP, ctypes.POINTER(ctypes.c_double)],
@@ -425,6 +434,41 @@ class Server:
 
     def reset_stats(self):
         dfd_server_stats_reset(self.handle)
+
+    def request_log(self):
+        """Per-request times of the requests completed since the last reset: a
+        numpy structured array (ticket, arrival_s, submit_s, admit_s, launch_s,
+        done_s, cells, n, k, dim)."""
+        import numpy as np
+        lib = load_library()
+        n = _I64(0)
+        _check(lib.dfd_server_request_log(self.handle, None, 0, ctypes.byref(n)), "dfd_server_request_log")
+        recs = (RequestRecord * max(n.value, 1))()
+        _check(lib.dfd_server_request_log(self.handle, ctypes.cast(recs, _VP), n.value, ctypes.byref(n)),
+               "dfd_server_request_log")
+        dt = np.dtype([("ticket", "<u8"), ("arrival_s", "<f8"), ("submit_s", "<f8"), ("admit_s", "<f8"),
+                       ("launch_s", "<f8"), ("done_s", "<f8"), ("cells", "<f8"), ("n", "<i4"), ("k", "<i4"),
+                       ("dim", "<i4"), ("pad", "<i4"), ("locked_s", "<f8")])
+        return np.frombuffer(bytes(recs), dtype=dt, count=n.value).copy()
+
+    def tick_log(self):
+        """Per-tick record of the ticks retired since the last reset: a numpy
+        structured array (build_s, launched_s, retired_s, gpu_ms, cells,
+        n_items, n_slices, n_outs, n_admitted, admit_ms, build_ms,
+        slow_call_ms, slow_call)."""
+        import numpy as np
+        lib = load_library()
+        dt = np.dtype([("build_s", "<f8"), ("launched_s", "<f8"), ("retired_s", "<f8"), ("gpu_ms", "<f8"),
+                       ("cells", "<f8"), ("n_items", "<i4"), ("n_slices", "<i4"), ("n_outs", "<i4"),
+                       ("n_admitted", "<i4"), ("admit_ms", "<f8"), ("build_ms", "<f8"), ("slow_call_ms", "<f8"),
+                       ("slow_call", "<i4"), ("pad", "<i4"), ("sync_s", "<f8"), ("synced_s", "<f8"),
+                       ("locked_s", "<f8")])
+        n = _I64(0)
+        _check(lib.dfd_server_tick_log(self.handle, None, 0, ctypes.byref(n)), "dfd_server_tick_log")
+        buf = np.zeros(max(n.value, 1), dtype=dt)
+        _check(lib.dfd_server_tick_log(self.handle, buf.ctypes.data, n.value, ctypes.byref(n)),
+               "dfd_server_tick_log")
+        return buf[: n.value].copy()
 
     def now(self) -> float:
         return dfd_server_now(self.handle)

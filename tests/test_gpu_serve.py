@@ -172,3 +172,41 @@ def test_invalid_requests_rejected(dctx):
     with pytest.raises(dfd.DFDError):
         srv.submit(bad, np.array([0], np.int64))
     srv.close()
+
+
+def test_request_and_tick_logs(dctx):
+    """The per-request log has one record per completed request, its times
+    in order (arrival <= submit <= lock <= admission <= first launch <=
+    completion) and its cells; the per-tick log covers every tick, with
+    device time and the cells of the completed requests; a stats reset
+    clears both."""
+    pl = pools(n=200, seed=130)
+    srv = make_server(dctx, pl, tick_cells=2e6)
+    reqs = requests(pl, 12, seed=131, kmax=40, qhi=600)
+    t0 = srv.now()
+    tickets = [srv.submit(q, ids, arrival_s=t0) for q, ids in reqs]
+    for t in tickets:
+        assert srv.wait(t)[0] == 0
+    st = srv.stats()
+    log = srv.request_log()
+    assert len(log) == 12 == st["completed"]
+    assert sorted(log["ticket"].tolist()) == sorted(tickets)
+    eps = 1e-9
+    assert np.all(log["arrival_s"] <= log["submit_s"] + eps)
+    assert np.all(log["submit_s"] <= log["locked_s"] + eps)
+    assert np.all(log["locked_s"] <= log["admit_s"] + eps)
+    assert np.all(log["admit_s"] <= log["launch_s"] + eps)
+    assert np.all(log["launch_s"] <= log["done_s"] + eps)
+    by_ticket = {int(r["ticket"]): r for r in log}
+    for t, (q, ids) in zip(tickets, reqs):
+        r = by_ticket[t]
+        lens = np.diff(pl[q.shape[1]].offsets)[ids]
+        assert r["cells"] == float(np.sum(q.shape[0] * lens)) and r["k"] == len(ids) and r["n"] == q.shape[0]
+    ticks = srv.tick_log()
+    assert len(ticks) == st["ticks"] >= 1
+    assert np.all(ticks["gpu_ms"] > 0) and np.all(ticks["build_s"] <= ticks["launched_s"])
+    assert np.all(ticks["launched_s"] <= ticks["retired_s"])
+    assert abs(ticks["cells"].sum() - st["cells"]) <= 1e-6 * st["cells"]
+    srv.reset_stats()
+    assert len(srv.request_log()) == 0 and len(srv.tick_log()) == 0
+    srv.close()
