@@ -176,7 +176,7 @@ class LongPair:
     """One long 3-D float32 pair through dfd_pair (band wavefront)."""
     micro_op = "cell_f32_d3"
     dtype = "f32"
-    launches_per_step = 4          # 2 input checks, q packing, wavefront (one front; set per shape below)
+    launches_per_step = 4          # input check, q packing, wavefront, combine (two fronts; set per shape below)
 
     def __init__(self, args, ctx, dfd, torch, workloads, rank, world):
         self.n, self.m = args.n, args.m
@@ -204,9 +204,9 @@ class LongPair:
                        "launch_shape": {"rows_per_lane": shape[0], "warps": shape[1], "ctas": shape[2],
                                         "autotuned": tuned},
                        "kernel_sha": kernel_sha()}
-        # two fronts (a pair of two bands or more): q packed twice and a combine kernel
+        # two fronts (a pair of two bands or more): a combine kernel after the wavefront
         bands = -(-self.n // (32 * shape[0] * shape[1]))
-        self.launches_per_step = 6 if bands >= 2 else 4
+        self.launches_per_step = 4 if bands >= 2 else 3
         self.config["fronts"] = 2 if bands >= 2 else 1
         self.h2d = (self.n + self.m) * DIM * 4
         self.d2h = 16

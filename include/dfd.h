@@ -463,7 +463,9 @@ double dfd_server_now(dfd_server* server);
  * Explicit launch shape for the band wavefront of dfd_pair (for tuning and
  * measurement).  rows_per_lane in {2, 4, 6, 8}, warps in 1..16 (compute
  * warps per CTA; one more communication warp is added), ctas in 1..#SMs
- * (0 = min(#bands, #SMs)).  Unsupported shapes return DFD_ERR_UNSUPPORTED.
+ * times the CTAs an SM holds (two for points of up to 4 coordinates, else
+ * one; 0 = min(#bands, resident CTAs)).  Unsupported shapes return
+ * DFD_ERR_UNSUPPORTED.
  */
 typedef struct dfd_wave_shape {
   int rows_per_lane;

@@ -124,35 +124,43 @@ dfd_status ensure_pinned(dfd_context* ctx, size_t bytes) {
 }
 
 // ------------------------------------------------------ input check kernels
-__global__ void check_f32_kernel(const float* x, int64_t count, int* err) {
+// Both arrays in one launch: indices below nx read x, the rest y.
+__global__ void check_f32_kernel(const float* x, int64_t nx, const float* y, int64_t ny, int* err) {
   bool bad = false;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x)
-    bad |= !isfinite(x[i]);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nx + ny; i += (int64_t)gridDim.x * blockDim.x)
+    bad |= !isfinite(i < nx ? x[i] : y[i - nx]);
   if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) raise_error(err, DFD_ERR_NONFINITE);
 }
 
-__global__ void check_i32_kernel(const int32_t* x, int64_t count, long long lim, int* err) {
+__global__ void check_i32_kernel(const int32_t* x, int64_t nx, const int32_t* y, int64_t ny, long long lim, int* err) {
   // |c| <= lim = min(2^30 - 1, sqrt((2^63 - 1) / dim) / 2), computed on the host
   bool bad = false;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
-    const long long v = x[i] < 0 ? -(long long)x[i] : (long long)x[i];
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nx + ny; i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t c = i < nx ? x[i] : y[i - nx];
+    const long long v = c < 0 ? -(long long)c : (long long)c;
     bad |= v > lim;
   }
   if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) raise_error(err, DFD_ERR_RANGE);
 }
 
-dfd_status launch_check_inputs(dfd_dtype dtype, int dim, const void* x, int64_t count, int* err, cudaStream_t s) {
-  if (count <= 0) return DFD_OK;
+dfd_status launch_check_inputs2(dfd_dtype dtype, int dim, const void* x, int64_t nx, const void* y, int64_t ny,
+                                int* err, cudaStream_t s) {
+  if (nx + ny <= 0) return DFD_OK;
   const int threads = 256;
-  const int blocks = (int)std::min<int64_t>((count + threads - 1) / threads, 1024);
+  const int blocks = (int)std::min<int64_t>((nx + ny + threads - 1) / threads, 1024);
   if (dtype == DFD_F32)
-    check_f32_kernel<<<blocks, threads, 0, s>>>(static_cast<const float*>(x), count, err);
+    check_f32_kernel<<<blocks, threads, 0, s>>>(static_cast<const float*>(x), nx, static_cast<const float*>(y), ny,
+                                                err);
   else
     check_i32_kernel<<<blocks, threads, 0, s>>>(
-        static_cast<const int32_t*>(x), count,
+        static_cast<const int32_t*>(x), nx, static_cast<const int32_t*>(y), ny,
         std::min<long long>((1LL << 30) - 1, (long long)std::floor(std::sqrt((double)LLONG_MAX / (double)dim) / 2.0)),
         err);
   return cuda_status(cudaGetLastError());
+}
+
+dfd_status launch_check_inputs(dfd_dtype dtype, int dim, const void* x, int64_t count, int* err, cudaStream_t s) {
+  return launch_check_inputs2(dtype, dim, x, count, x, 0, err, s);
 }
 
 // ------------------------------------------------------------- wave plans
@@ -180,6 +188,9 @@ dfd_status wave_plan(const dfd_context* ctx, dfd_dtype dtype, int dim, int64_t n
     return DFD_OK;
   }
   const double RSAT = dtype == DFD_F32 ? 24.0 : 48.0;
+  // one CTA per SM: bands of one chain sharing an SM slow each other down
+  // more than a second CTA hides (the 200,000^2 3-D pair: 2.63 Tcell/s with
+  // 152 CTAs, 1.87 with all 261 bands resident two to an SM)
   const int P = std::max(ctx->num_sms, 1);
   double best = 1e300;
   WaveShape bs;
@@ -349,9 +360,7 @@ dfd_status check_pair_args(dfd_context* ctx, dfd_dtype dtype, int dim, const voi
 dfd_status pre_checks(dfd_context* ctx, dfd_dtype dtype, int dim, const void* p, int64_t n, const void* q, int64_t m,
                       cudaStream_t s) {
   if (!ctx->opt.check_inputs) return DFD_OK;
-  dfd_status st = launch_check_inputs(dtype, dim, p, n * dim, ctx->d_err, s);
-  if (st != DFD_OK) return st;
-  return launch_check_inputs(dtype, dim, q, m * dim, ctx->d_err, s);
+  return launch_check_inputs2(dtype, dim, p, n * dim, q, m * dim, ctx->d_err, s);
 }
 
 }  // namespace
@@ -528,24 +537,29 @@ dfd_status dfd_pair_autotune(dfd_context* ctx, dfd_dtype dtype, int dim, const v
       if (!shape_ok(ctx, dtype, dim, R, W)) continue;
       const int64_t H = (int64_t)32 * W * R;
       const int64_t B = (n + H - 1) / H;
-      if (B > 2 * (int64_t)ctx->num_sms || (B < ctx->num_sms / 2 && W > 2)) continue;
-      WaveShape sh;
-      sh.R = R;
-      sh.W = W;
-      sh.ctas = 0;
-      cudaEventRecord(e0, s);
-      st = wave_run(ctx, dtype, dim, p, n, q, m, res, nullptr, s, sh);
-      cudaEventRecord(e1, s);
-      if (st != DFD_OK) continue;
-      if (cudaEventSynchronize(e1) != cudaSuccess) {
-        cudaGetLastError();
+      if (B > 2 * (int64_t)ctx->num_sms * wave::blocks_per_sm(dim_class(dim)) || (B < ctx->num_sms / 2 && W > 2))
         continue;
-      }
-      float ms = 0.f;
-      cudaEventElapsedTime(&ms, e0, e1);
-      if (ms < best_ms) {
-        best_ms = ms;
-        best = sh;
+      // one CTA per SM, and (bands permitting) every CTA that can be resident
+      const int grids[2] = {(int)std::min<int64_t>(B, ctx->num_sms), 0};
+      for (int g = 0; g < (B > ctx->num_sms ? 2 : 1); ++g) {
+        WaveShape sh;
+        sh.R = R;
+        sh.W = W;
+        sh.ctas = grids[g];
+        cudaEventRecord(e0, s);
+        st = wave_run(ctx, dtype, dim, p, n, q, m, res, nullptr, s, sh);
+        cudaEventRecord(e1, s);
+        if (st != DFD_OK) continue;
+        if (cudaEventSynchronize(e1) != cudaSuccess) {
+          cudaGetLastError();
+          continue;
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best_ms) {
+          best_ms = ms;
+          best = sh;
+        }
       }
     }
   }
@@ -628,7 +642,7 @@ dfd_status dfd_pair_shaped(dfd_context* ctx, dfd_dtype dtype, int dim, const voi
     sh.R = shape->rows_per_lane;
     sh.W = shape->warps;
     sh.ctas = shape->ctas;
-    if (sh.ctas < 0 || sh.ctas > ctx->num_sms) return DFD_ERR_UNSUPPORTED;
+    if (sh.ctas < 0 || sh.ctas > ctx->num_sms * wave::blocks_per_sm(dim_class(dim))) return DFD_ERR_UNSUPPORTED;
   } else {
     wave_plan(ctx, dtype, dim, n, m, &sh);
   }

@@ -112,6 +112,9 @@ dfd_status check_batch_args(dfd_context* ctx, dfd_dtype dtype, int dim, const vo
 // Input validation kernels: set DFD_ERR_NONFINITE / DFD_ERR_RANGE in *err.
 dfd_status launch_check_inputs(dfd_dtype dtype, int dim, const void* x, int64_t count, int* err,
                                cudaStream_t s);
+// Both curves of a pair in one launch.
+dfd_status launch_check_inputs2(dfd_dtype dtype, int dim, const void* x, int64_t nx, const void* y, int64_t ny,
+                                int* err, cudaStream_t s);
 
 // Band wavefront (K2).
 dfd_status wave_plan(const dfd_context* ctx, dfd_dtype dtype, int dim, int64_t n, int64_t m, WaveShape* shape);

@@ -123,8 +123,7 @@ extern "C" dfd_status dfd_pair_noalloc(int device, dfd_dtype dtype, int dim, con
     // The error word must start at zero for this call.
     if (e == cudaSuccess) e = cudaMemsetAsync(c.d_err, 0, sizeof(int), s);
     st = cuda_status(e);
-    if (st == DFD_OK) st = launch_check_inputs(dtype, dim, p, n * dim, c.d_err, s);
-    if (st == DFD_OK) st = launch_check_inputs(dtype, dim, q, m * dim, c.d_err, s);
+    if (st == DFD_OK) st = launch_check_inputs2(dtype, dim, p, n * dim, q, m * dim, c.d_err, s);
     if (st == DFD_OK) {
       WaveShape sh;
       wave_plan(&c, dtype, dim, n, m, &sh);

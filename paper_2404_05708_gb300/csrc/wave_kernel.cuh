@@ -319,6 +319,7 @@ constexpr int kQMirror = 64;
 // addresses its record at a fixed offset from the block's base.
 template <int C, int TR>
 struct QRow {
+  static constexpr int NQ = nq_slots(C);
   static constexpr int RING_LEN = NQ * C / TR;      // records of the ring proper
   static constexpr int LEN = RING_LEN + kQMirror;   // records per row
   static constexpr int PLANE = TR * LEN;            // records per plane
@@ -335,6 +336,7 @@ struct Layout {
   using QR = QRow<C, TR>;
   static constexpr size_t q_bytes = (size_t)NPL * QR::PLANE * sizeof(Rec);
   static constexpr size_t bar_off = q_bytes;
+  static constexpr int NQ = nq_slots(C);
   static constexpr size_t ring_off = bar_off + 2 * NQ * sizeof(uint64_t);
   static __host__ __device__ size_t ctl_off(int W) { return ring_off + (size_t)(W + 1) * RING * sizeof(T); }
   static __host__ __device__ size_t bytes(int W) { return ctl_off(W) + sizeof(Ctl); }
@@ -476,6 +478,7 @@ __device__ __forceinline__ void compute_stripe(const Args& a, const Prob& pb, in
   using Rec = typename Lay::Rec;
   constexpr int C = Lay::C;
   constexpr int NPL = Lay::NPL;
+  constexpr int NQ = Lay::NQ;
   constexpr int NQC = NQ * C;
   constexpr int K = Skew<V, R>::value;
   constexpr int SK = 32 * K - 1;
@@ -652,6 +655,7 @@ __device__ __forceinline__ void comm_warp(const Args& a, const Prob& pb, int64_t
   constexpr int C = Lay::C;
   constexpr int NPL = Lay::NPL;
   constexpr unsigned CHUNK_BYTES = (unsigned)(NPL * C * sizeof(Rec));
+  constexpr int NQ = Lay::NQ;
   constexpr int TR = Lay::TR;
   using QR = typename Lay::QR;
   static_assert(QTrans<V, R>::value == TR, "q ring residue split");
@@ -801,9 +805,10 @@ __device__ __forceinline__ void comm_warp(const Args& a, const Prob& pb, int64_t
 
 // ------------------------------------------------------------------ kernel
 template <class V, int DK, int R>
-__global__ void __launch_bounds__((kMaxWarps<V, DK, R>::value + 1) * 32, 1) wave_kernel(Args a) {
+__global__ void __launch_bounds__((kMaxWarps<V, DK, R>::value + 1) * 32, blocks_per_sm(DK)) wave_kernel(Args a) {
   using Lay = Layout<V, DK, R>;
   using T = typename V::value;
+  constexpr int NQ = Lay::NQ;
   extern __shared__ __align__(128) unsigned char smem[];
   const int W = (int)(blockDim.x >> 5) - 1;
   const int warp = threadIdx.x >> 5;
@@ -870,7 +875,11 @@ __global__ void __launch_bounds__((kMaxWarps<V, DK, R>::value + 1) * 32, 1) wave
 // footnote; they are never read into the result).  With `rev` the stream is
 // that of q reversed (column j is q_{m-1-j}).
 template <class V, int DK>
-__global__ void pack_q_kernel(const typename V::coord* q, int64_t m, int dim, int nch, int TR, int rev, void* out) {
+__global__ void pack_q_kernel(const typename V::coord* q, int64_t m, int dim, int nch, int TR, void* out0,
+                              void* out1) {
+  // blockIdx.y: 0 the forward stream (to out0), 1 q reversed (to out1)
+  const int rev = (int)blockIdx.y;
+  void* out = rev ? out1 : out0;
   constexpr int C = ChunkCols<DK>::value;
   using Rows_ = Rows<V, DK, 2>;
   constexpr int NPL = Rows_::NPL;

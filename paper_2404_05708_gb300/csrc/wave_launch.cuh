@@ -70,9 +70,9 @@ dfd_status wave_launch(dfd_context* ctx, int dim, const void* p, int64_t n, cons
     const int64_t recs = (int64_t)nch * C * Lay::NPL;
     const int threads = 256;
     const int blocks = (int)std::min<int64_t>((recs + threads - 1) / threads, 4 * (int64_t)ctx->num_sms);
-    for (int r = 0; r < (two ? 2 : 1); ++r)
-      wave::pack_q_kernel<V, DK><<<blocks, threads, 0, s>>>(static_cast<const typename V::coord*>(q), m, dim, nch,
-                                                           wave::QTrans<V, R>::value, r, base + (r ? off_q_b : off_q));
+    wave::pack_q_kernel<V, DK><<<dim3(blocks, two ? 2 : 1), threads, 0, s>>>(
+        static_cast<const typename V::coord*>(q), m, dim, nch, wave::QTrans<V, R>::value, base + off_q,
+        base + off_q_b);
   }
   const size_t smem = Lay::bytes(W);
   if (smem > ctx->smem_optin) return DFD_ERR_UNSUPPORTED;
@@ -106,7 +106,16 @@ dfd_status wave_launch(dfd_context* ctx, int dim, const void* p, int64_t n, cons
   a.rowbuf_b = two ? base + off_row_b : nullptr;
   a.progress_b = reinterpret_cast<unsigned long long*>(base + off_prog_b);
   const int64_t nbands = nb0 + nb1;
-  int grid = ctas > 0 ? ctas : ctx->num_sms;
+  // persistent grid: every CTA that can be resident (a band is only ever
+  // awaited by a later ticket, so CTAs that are not resident wait harmlessly)
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, wave::wave_kernel<V, DK, R>, (W + 1) * 32, smem) !=
+          cudaSuccess ||
+      per_sm < 1) {
+    cudaGetLastError();
+    per_sm = 1;
+  }
+  int grid = ctas > 0 ? ctas : per_sm * ctx->num_sms;
   grid = (int)std::min<int64_t>(grid, nbands);
   timing_begin(ctx, s);
   wave::wave_kernel<V, DK, R><<<grid, (W + 1) * 32, smem, s>>>(a);

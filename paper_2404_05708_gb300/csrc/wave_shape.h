@@ -7,7 +7,6 @@ namespace wave {
 
 constexpr int G = 32;        // systolic steps between synchronisations
 constexpr int RING = 256;    // columns held by each inter-warp ring (power of 2)
-constexpr int NQ = 8;        // q chunk slots (power of 2)
 
 // q columns per TMA chunk.  A compute warp checks a chunk's barrier once per
 // chunk, and the warp that paces the band pays a few hundred cycles for it:
@@ -15,6 +14,14 @@ constexpr int NQ = 8;        // q chunk slots (power of 2)
 // shared memory for 3-D points) made the 200,000^2 pair 2.5% faster than
 // 128-column ones (16 slots).
 constexpr int chunk_cols(int dk) { return dk <= 4 ? 512 : 128; }
+
+// q chunk slots (a power of 2).  Points of up to 4 coordinates keep 4 slots
+// of 512 columns (about 70 KB of shared memory a CTA for 3-D points), so two
+// CTAs fit an SM and each SM sub-partition holds two compute warps (one
+// compute warp per sub-partition left the step's dependent chain exposed);
+// larger points keep 8 slots of 128 columns and one CTA per SM.
+constexpr int nq_slots(int C) { return C >= 512 ? 4 : 8; }
+constexpr int blocks_per_sm(int dk) { return dk <= 4 ? 2 : 1; }
 
 // Column skew between neighbouring lanes: float32 lanes hold R/2 skewed row
 // pairs, int32 lanes keep their R rows in one column.
@@ -28,7 +35,7 @@ constexpr int skew(bool f32, int R) { return f32 ? R / 2 : 1; }
 // wait for must fit in the ring beside the oldest one the last warp may
 // still read:
 //   (NQ - 1) * C >= (W - 1) * (32*K + G) + 31*K + G + 2.
-constexpr int max_warps_ring(int C, int K) { return ((NQ - 1) * C - 31 * K - G - 2) / (32 * K + G) + 1; }
+constexpr int max_warps_ring(int C, int K) { return ((nq_slots(C) - 1) * C - 31 * K - G - 2) / (32 * K + G) + 1; }
 
 // Registers a compute lane needs (points, row state, q records in flight,
 // the block's ring inputs, addressing), an estimate calibrated on ptxas.
@@ -38,12 +45,13 @@ constexpr int reg_estimate(bool f32, int dk, int R) {
 }
 
 // Compute warps per CTA the register file allows (with the communication
-// warp, one CTA per SM); 0 if even one warp would not fit in 255 registers.
+// warp, blocks_per_sm CTAs per SM); 0 if even one warp would not fit in 255
+// registers.
 constexpr int max_warps_regs(bool f32, int dk, int R) {
   return reg_estimate(f32, dk, R) > 248 ? 0
-         : (65536 / (32 * ((reg_estimate(f32, dk, R) + 7) / 8 * 8)) - 1) > 16
+         : (65536 / blocks_per_sm(dk) / (32 * ((reg_estimate(f32, dk, R) + 7) / 8 * 8)) - 1) > 16
              ? 16
-             : 65536 / (32 * ((reg_estimate(f32, dk, R) + 7) / 8 * 8)) - 1;
+             : 65536 / blocks_per_sm(dk) / (32 * ((reg_estimate(f32, dk, R) + 7) / 8 * 8)) - 1;
 }
 
 constexpr bool shape_supported(bool f32, int dk, int R, int W) {

@@ -1,0 +1,120 @@
+"""Small, seeded cases that launch one kernel each, for profiler captures.
+
+    python -m paper_2404_05708_gb300.profile_cases <case> [--reps N]
+
+Each case builds its inputs, runs the entry point once untimed (so lazy
+loading and scratch growth happen first), synchronises, then runs it
+``--reps`` more times (default 1), so a capture of the case's kernel with
+``-s 1 -c 1`` profiles a warm launch.  Cases:
+
+  rowscan   dfd_pair_reference (the per-pair form, rowscan_kernel), 2000 x 1500 2-D float32 walks
+  wave      dfd_pair (wave_kernel), 2000 x 1500 2-D float32 walks
+  wave3d    dfd_pair (wave_kernel), 20,000 x 20,000 3-D float32 warped walk
+  batch     dfd_batch (batch_kernel), 32,768 ragged int32 2-D pairs, lengths U{16..512}
+  team      dfd_batch (batch_kernel, CTA teams), 32 pairs of 1,024-point 2-D walks
+  decide    dfd_batch_decide (decide_kernel), 16,384 ragged int32 2-D pairs
+  lev       Levenshtein (variant_kernel<LevOp>), 16,384 pairs of symbols over {0..3}
+  knn       dfd_knn (knn_kernel), a 2-D query against 16,384 resident candidates, k = 10
+  serve     one serving tick (serve_kernel): 8 requests of 2-D queries, k = 512
+  micro8    dfd_microbench op 8 (micro_kernel<8>: the 3-D float32 cell mix)
+  matrix    dfd_matrix (matrix_kernel), 512 16-D AR(1) curves
+"""
+from __future__ import annotations
+
+import argparse
+import sys
+
+import numpy as np
+
+
+def _walks(rng, lens, dim, kind="f32"):
+    off = np.concatenate([[0], np.cumsum(lens)]).astype(np.int64)
+    if kind == "i32":
+        pts = np.cumsum(rng.integers(-64, 65, size=(int(off[-1]), dim)), axis=0).astype(np.int32)
+    else:
+        pts = np.cumsum(rng.normal(0, 1, size=(int(off[-1]), dim)), axis=0).astype(np.float32)
+    return pts, off
+
+
+def main(argv=None) -> int:
+    ap = argparse.ArgumentParser()
+    ap.add_argument("case")
+    ap.add_argument("--reps", type=int, default=1)
+    a = ap.parse_args(argv)
+    import torch
+    from paper_2404_05708_gb300 import build, dfd, workloads
+    build.build()
+    torch.cuda.set_device(0)
+    ctx = dfd.Context(0)
+    dev = lambda x: torch.from_numpy(np.ascontiguousarray(x)).cuda()   # noqa: E731
+    rng = np.random.default_rng(17)
+    case = a.case
+
+    if case in ("rowscan", "wave"):
+        p, q = workloads.gaussian_walk_pair(2000, 1500, dim=2)
+        P, Q = dev(p), dev(q)
+        fn = lambda: ctx.pair(P, Q, reference=(case == "rowscan"))   # noqa: E731
+    elif case == "wave3d":
+        p, q = workloads.warped_long_pair(20000, 20000, dim=3, seed=3)
+        P, Q = dev(p), dev(q)
+        fn = lambda: ctx.pair(P, Q)   # noqa: E731
+    elif case in ("batch", "decide"):
+        b = workloads.ragged_int_batch(n_pairs=32768 if case == "batch" else 16384, seed=4)
+        PT, O, PR = dev(b.points), dev(b.offsets), dev(b.pairs)
+        if case == "batch":
+            fn = lambda: ctx.batch(PT, O, PR)   # noqa: E731
+        else:
+            fn = lambda: ctx.decide(PT, O, PR, 2.0e7)   # noqa: E731
+    elif case == "team":
+        b = workloads.paper_walks(32, 1024)
+        PT, O, PR = dev(b.points), dev(b.offsets), dev(b.pairs)
+        fn = lambda: ctx.batch(PT, O, PR)   # noqa: E731
+    elif case == "lev":
+        lens = rng.integers(16, 513, size=2 * 16384)
+        off = np.concatenate([[0], np.cumsum(lens)]).astype(np.int64)
+        sym = rng.integers(0, 4, size=(int(off[-1]), 1)).astype(np.int32)
+        pairs = np.arange(2 * 16384, dtype=np.int32).reshape(-1, 2)
+        PT, O, PR = dev(sym), dev(off), dev(pairs)
+        fn = lambda: ctx.levenshtein(PT, O, PR)   # noqa: E731
+    elif case == "knn":
+        pool = workloads.serving_pool(n_curves=16384, dim=2, seed=8)
+        qs = workloads.serving_pool(n_curves=1, dim=2, seed=99)
+        PT, O, QD = dev(pool.points), dev(pool.offsets), dev(qs.curve(0).copy())
+        fn = lambda: ctx.knn(QD, PT, O, 10)   # noqa: E731
+    elif case == "serve":
+        pool = workloads.serving_pool(n_curves=8192, dim=2, seed=8)
+        srv = dfd.Server(ctx, mem_budget_bytes=1 << 30, max_slots=64, tick_cells=4e9)
+        srv.add_candidates(pool.points, pool.offsets)
+        reqs = []
+        for i in range(8):
+            q = np.cumsum(rng.normal(0, 1, size=(256, 2)), axis=0).astype(np.float32)
+            reqs.append((q, rng.integers(0, 8192, size=512).astype(np.int64)))
+
+        def fn():
+            ts = [srv.submit(q, ids) for q, ids in reqs]
+            for t in ts:
+                srv.wait(t)
+    elif case == "micro8":
+        fn = lambda: dfd.dfd_microbench(ctx.handle, dfd.MICRO_OPS["cell_f32_d3"])   # noqa: E731
+    elif case == "matrix":
+        b = workloads.ar1_curves(n_curves=512)
+        PT, O = dev(b.points), dev(b.offsets)
+        fn = lambda: ctx.matrix(PT, O)   # noqa: E731
+    else:
+        print(f"unknown case {case}", file=sys.stderr)
+        return 2
+    fn()
+    torch.cuda.synchronize()
+    for _ in range(a.reps):
+        fn()
+    torch.cuda.synchronize()
+    err = ctx.get_error()
+    if case == "serve":
+        srv.close()
+    ctx.close()
+    print(f"{case} ok (error word {err})")
+    return 0 if err == 0 else 1
+
+
+if __name__ == "__main__":
+    sys.exit(main())
