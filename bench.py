@@ -1056,6 +1056,19 @@ def timed_steps(wl, ctx, dfd, torch, steps, warmup, flush, world, kernel_timed):
     return total_ms, kernel_ms, clocks
 
 
+# Instructions per cell of each measured cell mix (warp-instructions of one
+# lane's cell): the stricter roofline from the unit counts alone is
+# 4 sub-partitions x 32 lanes = 128 lane-instructions per clock per SM over
+# these.  float32 cells run two rows per f32x2 instruction.
+MIX_INSTR_PER_CELL = {
+    "cell_f32_d3": 5.0,      # (3 sub + mul + 2 fma) / 2 rows, min3, max
+    "cell_f32_d2": 4.0,      # (2 sub + mul + fma) / 2 rows, min3, max
+    "cell_i32b_d2": 5.0,     # 3 integer instructions (|p|^2 + |q|^2 - 2 p.q), min3, max
+    "cell_f32_d16": 18.0,    # (16 sub + mul + 15 fma) / 2 rows, min3, max
+    "cell_dtw_f32_d2": 6.0,  # sub, sub, mul, fma, min3, add
+}
+
+
 def alu_roofline(wl, ctx, dfd, sms, clocks, kernel_ms, total_ms, steps):
     """ALU roofline: measured issue rate of the workload's cell instruction
     mix (cell-weighted over the mixes it runs: time adds per cell)."""
@@ -1079,6 +1092,12 @@ def alu_roofline(wl, ctx, dfd, sms, clocks, kernel_ms, total_ms, steps):
     if hasattr(wl, "evaluated_cells"):
         roofline["achieved_basis"] = (f"recurrence cells actually evaluated ({work_cells:.3e} per step; "
                                       f"value counts all {wl.cells:.3e} candidate cells)")
+    if all(op in MIX_INSTR_PER_CELL for op, _ in mixes):
+        ipc = sum(c / tot * MIX_INSTR_PER_CELL[op] for op, c in mixes)
+        ib = 128.0 / ipc * sms * clk * 1e6 / 1e9
+        roofline["issue_bound"] = {"peak": ib, "frac": achieved / ib,
+                                   "basis": f"128 lane-instructions/clk/SM / {ipc:.2f} instructions per cell x {sms} SMs "
+                                            f"x {clk:.0f} MHz"}
     return roofline
 
 

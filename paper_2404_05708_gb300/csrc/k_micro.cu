@@ -217,6 +217,11 @@ __global__ void __launch_bounds__(MB_THREADS) micro_kernel(float seed, unsigned 
       }
     }
   }
+  // every warp of the block has finished its loop before the end stamp:
+  // warps of one sub-partition are not issued evenly (the first may finish
+  // well ahead of the others), so a stamp taken when thread 0 alone is done
+  // would undercount the block's cycles and overstate the rate
+  __syncthreads();
   const unsigned long long g1 = globaltimer_ns();
   const unsigned long long t1 = clock64();
   if (threadIdx.x == 0) {
