@@ -278,9 +278,11 @@ dfd_status dfd_matrix(dfd_context* ctx, dfd_dtype dtype, int dim, const void* po
  * and, inside a variant, by columns, largest first; order 1 hands them out by
  * estimated cost alone (stripes x rows per lane x (columns + 31)), largest
  * first.  Both compute every pair identically; only the timing differs.
- * dfd_batch_autotune runs dfd_batch on the arguments with each order (one
- * untimed and three timed runs, CUDA events on `stream`, synchronous),
- * records the faster for (dtype, dim class) in the context -- later
+ * dfd_batch_autotune runs dfd_batch on the arguments with each order x
+ * team mode (1, 2) x tile shape (rows per lane cap Rmax or Rmax / 2, CTAs
+ * per SM all or 1; see dfd_batch_set_shape) (one untimed and three timed
+ * runs each, CUDA events on `stream`, synchronous), records the fastest
+ * combination for (dtype, dim class) in the context -- later
  * dfd_batch, dfd_batch_capture, dfd_batch_host and dfd_batch_decide calls
  * of that class use it -- and writes it to *best_order (may be NULL).  The
  * outputs hold the batch's results afterwards.  dfd_batch_set_order sets
@@ -308,11 +310,38 @@ dfd_status dfd_batch_set_order(dfd_context* ctx, dfd_dtype dtype, int dim, int o
  * warp, one warp each.  Team pairs go first (costliest first), then the
  * one-warp pairs.  Every mode computes
  * every pair's value bit for bit as the others.  dfd_batch_autotune tunes
- * the mode with the packing order; dfd_batch_tuned reads both back.
+ * the mode with the packing order and the tile shape (below);
+ * dfd_batch_tuned reads them back (NULL outputs are skipped; 0 = default).
  * DFD_ERR_INVALID_ARG for a mode outside 0..2.
  */
 dfd_status dfd_batch_set_team(dfd_context* ctx, dfd_dtype dtype, int dim, int mode);
-dfd_status dfd_batch_tuned(dfd_context* ctx, dfd_dtype dtype, int dim, int* order, int* team);
+dfd_status dfd_batch_tuned(dfd_context* ctx, dfd_dtype dtype, int dim, int* order, int* team, int* rows_per_lane,
+                           int* ctas_per_sm);
+
+/*
+ * Tile shape of the ragged batch's one-warp pairs and of the all-pairs
+ * matrix (no counterpart in the paper), per (dtype, dim class):
+ * rows_per_lane caps the rows a lane holds (1..8; the stripes of a pair
+ * are at most 32 x this tall; 0 = the largest, 8 for dim <= 4, 4 above): a
+ * lane's rows form one dependent chain per step, so fewer rows shorten the
+ * step and more rows amortise its fixed instructions.  ctas_per_sm (1 or 2;
+ * 0 = every resident CTA) sets the persistent grid.  Every shape computes
+ * the same bits; pairs the cap would leave wider than the row buffer run
+ * with the largest cap (matrix) or as CTA teams (batch), so the shape never
+ * changes which pairs run.  dfd_batch_autotune and dfd_matrix_autotune time
+ * the shapes on the caller's data and keep the fastest.
+ */
+dfd_status dfd_batch_set_shape(dfd_context* ctx, dfd_dtype dtype, int dim, int rows_per_lane, int ctas_per_sm);
+dfd_status dfd_matrix_set_shape(dfd_context* ctx, dfd_dtype dtype, int dim, int rows_per_lane, int ctas_per_sm);
+dfd_status dfd_matrix_tuned(dfd_context* ctx, dfd_dtype dtype, int dim, int* rows_per_lane, int* ctas_per_sm);
+/* Times dfd_matrix on the arguments with rows per lane cap {Rmax, Rmax/2,
+   Rmax/4} x CTAs per SM {all, 1} (one untimed and two timed runs each, CUDA
+   events on `stream`, synchronous), records the fastest for (dtype, dim
+   class) and writes it out (pointers may be NULL).  The outputs hold the
+   matrix afterwards. */
+dfd_status dfd_matrix_autotune(dfd_context* ctx, dfd_dtype dtype, int dim, const void* points, const int64_t* offsets,
+                               int64_t n_curves, void* out_condensed, void* out_dist2, int* best_rows_per_lane,
+                               int* best_ctas_per_sm, void* stream);
 
 /*
  * Row buffer width (columns per warp) of the ragged batch on this context:

@@ -176,9 +176,10 @@ __device__ __forceinline__ void team_wait(const unsigned long long* p, unsigned 
 // Rows per lane chosen for a pair with `rows` rows: the fewest stripes
 // (one when rows <= 32 * Rmax), with the rows spread evenly over them, so a
 // pair of 300 rows runs two stripes of 160 rows rather than two of 256.
+// `rmax` (at most Rmax, a launch's tuned cap) bounds the rows per lane.
 template <int DK>
-__host__ __device__ __forceinline__ int rows_per_lane(int rows) {
-  constexpr int RM = Rmax<DK>::value;
+__host__ __device__ __forceinline__ int rows_per_lane(int rows, int rmax = Rmax<DK>::value) {
+  const int RM = rmax < 1 ? 1 : (rmax > Rmax<DK>::value ? Rmax<DK>::value : rmax);
   if (rows <= 32) return 1;
   const int st = (rows + 32 * RM - 1) / (32 * RM);
   const int r = (rows + 32 * st - 1) / (32 * st);
@@ -594,9 +595,9 @@ __device__ __forceinline__ typename V::value warp_dfd_any(const typename V::coor
                                                           const typename V::coord* Q, int m, int dim, bool vec,
                                                           typename V::value* buf, int L, int st_begin = 0,
                                                           int st_end = 1 << 30, AB* ab = nullptr,
-                                                          uint4* stage = nullptr) {
+                                                          uint4* stage = nullptr, int rmax = Rmax<DK>::value) {
   constexpr int RM = Rmax<DK>::value;
-  switch (rows_per_lane<DK>(n)) {
+  switch (rows_per_lane<DK>(n, rmax)) {
 #define DFD_B_CASE(RR)                                                                                       \
   case RR:                                                                                                   \
     if constexpr (RR < RM) return warp_dfd<V, DK, RR, AB>(P, n, Q, m, dim, vec, buf, L, st_begin, st_end, ab, stage); \
@@ -617,15 +618,16 @@ __device__ __forceinline__ typename V::value warp_dfd_any(const typename V::coor
 
 // Number of stripes warp_dfd_any uses for a pair with `rows` rows.
 template <int DK>
-__host__ __device__ __forceinline__ int num_stripes(int rows) {
-  const int r = rows_per_lane<DK>(rows);
+__host__ __device__ __forceinline__ int num_stripes(int rows, int rmax = Rmax<DK>::value) {
+  const int r = rows_per_lane<DK>(rows, rmax);
   return (rows + 32 * r - 1) / (32 * r);
 }
 
 // A pair needs the row buffer when its rows span several stripes.
 template <int DK>
-__device__ __forceinline__ bool fits_buffer(int rows, int cols, int buf_cols = BUF_COLS) {
-  return rows <= 32 * Rmax<DK>::value || cols <= buf_cols;
+__device__ __forceinline__ bool fits_buffer(int rows, int cols, int buf_cols = BUF_COLS,
+                                            int rmax = Rmax<DK>::value) {
+  return num_stripes<DK>(rows, rmax) <= 1 || cols <= buf_cols;
 }
 
 template <class V>
@@ -959,6 +961,7 @@ struct BatchArgs {
   unsigned* deferred;       // worklist entries of team pairs wider than one CTA's row buffers
   unsigned* n_deferred;
   unsigned long long timeout_ns;
+  int rmax;                 // rows per lane cap of one-warp pairs (<= Rmax; the launch's tuned shape)
 };
 
 // Ring columns of a team's shared-memory hand-off (per warp, 8 bytes a slot).
@@ -1156,7 +1159,7 @@ __global__ void __launch_bounds__(256, kBlocksPerSM<DK>::value) batch_kernel(Bat
     if (oa < 0 || ob < 0 || ea > total || eb > total) continue;             // reported by the plan
     const int n = (int)(ea - oa), m = (int)(eb - ob);
     if (n < 1 || m < 1) continue;                                            // reported by the plan
-    if (!fits_buffer<DK>(n, m, a.buf_cols)) {
+    if (!fits_buffer<DK>(n, m, a.buf_cols, a.rmax)) {
       // only when the plan made no team items (decider-style launches)
       if (L == 0) raise_error(a.err, DFD_ERR_UNSUPPORTED);
       continue;
@@ -1165,13 +1168,13 @@ __global__ void __launch_bounds__(256, kBlocksPerSM<DK>::value) batch_kernel(Bat
       if (w & kNarrowBit) {
         const float r = warp_dfd_any<I32B, DK>(pts + oa * a.dim, n, pts + ob * a.dim, m, a.dim, a.vec != 0,
                                                reinterpret_cast<float*>(buf), L, 0, 1 << 30,
-                                               static_cast<NoAbandon<I32B>*>(nullptr), stage);
+                                               static_cast<NoAbandon<I32B>*>(nullptr), stage, a.rmax);
         if (L == 0) write_result<I32B>(a.out_dist, a.out_dist2, k, r);
         continue;
       }
     }
     const T r = warp_dfd_any<V, DK>(pts + oa * a.dim, n, pts + ob * a.dim, m, a.dim, a.vec != 0, buf, L, 0, 1 << 30,
-                                    static_cast<NoAbandon<V>*>(nullptr), stage);
+                                    static_cast<NoAbandon<V>*>(nullptr), stage, a.rmax);
     if (L == 0) write_result<V>(a.out_dist, a.out_dist2, k, r);
   }
 
@@ -1330,6 +1333,8 @@ struct MatrixArgs {
   int dim;
   int vec;             // 1: vector point loads allowed (dim == DK, 16-byte aligned points)
   int chunk;        // pairs per pop
+  int rmax;         // rows per lane cap (<= Rmax; the tuned shape); a pair it would leave wider than the
+                    // row buffer runs with Rmax
   const int* bbox;  // int32 matrices: per curve and coordinate (min, max); else null
   int* counter;
   int* err;
@@ -1366,6 +1371,7 @@ __global__ void __launch_bounds__(256, kBlocksPerSM<DK>::value) matrix_kernel(Ma
       if (rows < 1) {
         if (L == 0) raise_error(a.err, DFD_ERR_INVALID_ARG);
       } else if (fits_buffer<DK>(rows, cols)) {
+        const int rm = fits_buffer<DK>(rows, cols, BUF_COLS, a.rmax) ? a.rmax : Rmax<DK>::value;
         const int64_t ia = ni <= nj ? i : j, ib = ni <= nj ? j : i;
         const int64_t oa = ni <= nj ? oi : oj, ob = ni <= nj ? oj : oi;
         bool narrow = false;
@@ -1374,12 +1380,12 @@ __global__ void __launch_bounds__(256, kBlocksPerSM<DK>::value) matrix_kernel(Ma
           if constexpr (std::is_same<V, I32>::value) {
             const float r = warp_dfd_any<I32B, DK>(pts + oa * a.dim, rows, pts + ob * a.dim, cols, a.dim,
                                                    a.vec != 0, reinterpret_cast<float*>(buf), L, 0, 1 << 30,
-                                                   static_cast<NoAbandon<I32B>*>(nullptr), stage);
+                                                   static_cast<NoAbandon<I32B>*>(nullptr), stage, rm);
             if (L == 0) write_result<I32B>(a.out_dist, a.out_dist2, k, r);
           }
         } else {
           const T r = warp_dfd_any<V, DK>(pts + oa * a.dim, rows, pts + ob * a.dim, cols, a.dim, a.vec != 0, buf, L,
-                                          0, 1 << 30, static_cast<NoAbandon<V>*>(nullptr), stage);
+                                          0, 1 << 30, static_cast<NoAbandon<V>*>(nullptr), stage, rm);
           if (L == 0) write_result<V>(a.out_dist, a.out_dist2, k, r);
         }
       } else if (L == 0) {

@@ -109,7 +109,8 @@ template <class V, int DK>
 dfd_status batch_prepare(dfd_context* ctx, int dim, const void* points, const int64_t* offsets, int64_t n_curves,
                          const int32_t* pairs, int64_t n_pairs, cudaStream_t s, int blocks, batch::BatchArgs* ba,
                          int64_t first_curve = 0, int* bbox_ext = nullptr, char* scratch_ext = nullptr,
-                         size_t scratch_ext_bytes = 0, int buf_cols = batch::BUF_COLS, int team = 0) {
+                         size_t scratch_ext_bytes = 0, int buf_cols = batch::BUF_COLS, int team = 0,
+                         int rmax = batch::Rmax<DK>::value) {
   constexpr bool kInt = std::is_same<V, I32>::value;
   if (n_pairs >= (int64_t)batch::kNarrowBit) return DFD_ERR_UNSUPPORTED;
   const BatchLayout lay = batch_layout<V, DK>(n_curves, n_pairs, blocks, bbox_ext != nullptr, buf_cols);
@@ -145,7 +146,7 @@ dfd_status batch_prepare(dfd_context* ctx, int dim, const void* points, const in
   pa.bbox = bbox;
   pa.dk = DK;
   pa.err = ctx->d_err;
-  pa.rmax = batch::Rmax<DK>::value;
+  pa.rmax = rmax;
   pa.order = ctx->batch_order[std::is_same<V, F32>::value ? 0 : 1][dim_class_index(DK)];
   pa.team = team;
   pa.buf_cols = buf_cols;
@@ -178,7 +179,28 @@ dfd_status batch_prepare(dfd_context* ctx, int dim, const void* points, const in
   ba->n_deferred = reinterpret_cast<unsigned*>(base + 12);
   ba->deferred = reinterpret_cast<unsigned*>(base + lay.off_defer);
   ba->timeout_ns = timeout_ns(ctx);
+  ba->rmax = rmax;
   return cuda_status(cudaGetLastError());
+}
+
+// Tile shape of a batch or matrix launch, tuned per (dtype, dim class): the
+// cap on rows per lane (a lane's rows are one dependent chain per step, so
+// fewer rows shorten the step; more rows amortise its fixed instructions)
+// and the CTAs per SM (more CTAs hide latency; fewer leave registers and
+// issue slots to each).  0 = the defaults: Rmax, every resident CTA.
+struct TileShape {
+  int rmax;
+  int blocks;
+};
+template <int DK, class K>
+TileShape tile_shape(const dfd_context* ctx, K kernel, const signed char (&rm)[2][5], const signed char (&cp)[2][5],
+                     bool f32) {
+  const int t = f32 ? 0 : 1, d = dim_class_index(DK);
+  TileShape sh;
+  sh.rmax = rm[t][d] > 0 ? std::min<int>(rm[t][d], batch::Rmax<DK>::value) : batch::Rmax<DK>::value;
+  const int resident = resident_blocks(ctx, kernel, 256);
+  sh.blocks = cp[t][d] > 0 ? std::min(resident, cp[t][d] * ctx->num_sms) : resident;
+  return sh;
 }
 
 // Team mode of a ragged batch launch (see batch_kernel and team_pays): the
@@ -208,11 +230,14 @@ dfd_status batch_launch_range(dfd_context* ctx, int dim, const void* points, con
                               int64_t n_curves, const int32_t* pairs, int64_t n_pairs, void* out_dist,
                               void* out_dist2, cudaStream_t s, int64_t first_curve, int* bbox_ext,
                               char* scratch_ext, size_t scratch_ext_bytes, cudaEvent_t prepared, int buf_cols) {
-  const int blocks = resident_blocks(ctx, batch::batch_kernel<V, DK>, 256);
+  const TileShape ts = tile_shape<DK>(ctx, batch::batch_kernel<V, DK>, ctx->batch_rmax, ctx->batch_cpsm,
+                                      std::is_same<V, F32>::value);
+  const int blocks = ts.blocks;
   batch::BatchArgs ba;
   const int team = batch_team_mode(ctx, std::is_same<V, F32>::value, DK);
   dfd_status st = batch_prepare<V, DK>(ctx, dim, points, offsets, n_curves, pairs, n_pairs, s, blocks, &ba,
-                                       first_curve, bbox_ext, scratch_ext, scratch_ext_bytes, buf_cols, team);
+                                       first_curve, bbox_ext, scratch_ext, scratch_ext_bytes, buf_cols, team,
+                                       ts.rmax);
   if (st != DFD_OK) return st;
   if (prepared) cudaEventRecord(prepared, s);
   ba.out_dist = out_dist;
@@ -255,7 +280,9 @@ dfd_status matrix_launch(dfd_context* ctx, int dim, const void* points, const in
                          void* out_dist, void* out_dist2, cudaStream_t s, int chunk) {
   using T = typename V::value;
   constexpr int THREADS = 256;
-  const int blocks = resident_blocks(ctx, batch::matrix_kernel<V, DK>, THREADS);
+  const TileShape ts = tile_shape<DK>(ctx, batch::matrix_kernel<V, DK>, ctx->matrix_rmax, ctx->matrix_cpsm,
+                                      std::is_same<V, F32>::value);
+  const int blocks = ts.blocks;
   const size_t warps = (size_t)blocks * (THREADS / 32);
   constexpr bool kInt = std::is_same<V, I32>::value;
   const size_t off_bbox = 256;
@@ -282,6 +309,7 @@ dfd_status matrix_launch(dfd_context* ctx, int dim, const void* points, const in
   ma.dim = dim;
   ma.vec = vector_loads_ok<DK>(points, dim);
   ma.chunk = chunk > 0 ? chunk : 8;
+  ma.rmax = ts.rmax;
   ma.bbox = bbox;
   ma.counter = reinterpret_cast<int*>(base);
   ma.err = ctx->d_err;

@@ -828,9 +828,14 @@ dfd_status dfd_batch_autotune(dfd_context* ctx, dfd_dtype dtype, int dim, const 
   if (!pairs || n_pairs < 0 || n_pairs > INT32_MAX) return DFD_ERR_INVALID_ARG;
   if ((st = set_device(ctx)) != DFD_OK) return st;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  signed char& slot = ctx->batch_order[dtype == DFD_F32 ? 0 : 1][dim_class_index(dim_class(dim))];
-  signed char& tslot = ctx->batch_team[dtype == DFD_F32 ? 0 : 1][dim_class_index(dim_class(dim))];
-  const signed char keep = slot, tkeep = tslot;
+  const int ti = dtype == DFD_F32 ? 0 : 1, di = dim_class_index(dim_class(dim));
+  signed char& slot = ctx->batch_order[ti][di];
+  signed char& tslot = ctx->batch_team[ti][di];
+  signed char& rslot = ctx->batch_rmax[ti][di];
+  signed char& cslot = ctx->batch_cpsm[ti][di];
+  const signed char keep = slot, tkeep = tslot, rkeep = rslot, ckeep = cslot;
+  const int rm_full = dim_class(dim) <= 4 ? 8 : 4;   // batch::Rmax of the dim class
+  const int cp_full = dim_class(dim) >= 16 ? 1 : 2;  // CTAs per SM of its launch bounds
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess) {
     cudaGetLastError();
@@ -842,13 +847,18 @@ dfd_status dfd_batch_autotune(dfd_context* ctx, dfd_dtype dtype, int dim, const 
     return DFD_ERR_CUDA;
   }
   float best_ms = 0.f;
-  int best = keep, best_team = tkeep;
+  int best = keep, best_team = tkeep, best_rm = rkeep, best_cp = ckeep;
   // packing order x team mode (1: only pairs too wide for a warp's buffer
-  // run as CTA teams, 2: every pair of several stripes does)
-  for (int c = 0; c < 4 && st == DFD_OK && n_pairs > 0; ++c) {
-    const int order = c & 1, team = 1 + (c >> 1);
+  // run as CTA teams, 2: every pair of several stripes does) x tile shape
+  // (rows per lane cap Rmax or Rmax / 2, CTAs per SM 1 or all)
+  for (int c = 0; c < 16 && st == DFD_OK && n_pairs > 0; ++c) {
+    const int order = c & 1, team = 1 + ((c >> 1) & 1);
+    const int rm = (c >> 2) & 1 ? rm_full / 2 : rm_full, cp = (c >> 3) & 1 ? 1 : cp_full;
+    if (cp_full == 1 && cp == 1 && (c >> 3) & 1) continue;   // one CTA per SM is the only shape
     slot = (signed char)order;
     tslot = (signed char)team;
+    rslot = (signed char)rm;
+    cslot = (signed char)cp;
     // one untimed run (sizes the scratch), then three timed
     st = batch_run(ctx, dtype, dim, points, offsets, n_curves, pairs, n_pairs, out_dist, out_dist2, s);
     if (st != DFD_OK) break;
@@ -863,23 +873,62 @@ dfd_status dfd_batch_autotune(dfd_context* ctx, dfd_dtype dtype, int dim, const 
       best_ms = ms;
       best = order;
       best_team = team;
+      best_rm = rm;
+      best_cp = cp;
     }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   cudaGetLastError();
-  slot = (signed char)(st == DFD_OK ? best : keep);
-  tslot = (signed char)(st == DFD_OK ? best_team : tkeep);
+  const bool ok = st == DFD_OK;
+  slot = (signed char)(ok ? best : keep);
+  tslot = (signed char)(ok ? best_team : tkeep);
+  rslot = (signed char)(ok ? best_rm : rkeep);
+  cslot = (signed char)(ok ? best_cp : ckeep);
   if (best_order) *best_order = slot;
   return st;
 }
 
-dfd_status dfd_batch_tuned(dfd_context* ctx, dfd_dtype dtype, int dim, int* order, int* team) {
+dfd_status dfd_batch_tuned(dfd_context* ctx, dfd_dtype dtype, int dim, int* order, int* team, int* rows_per_lane,
+                           int* ctas_per_sm) {
   if (!ctx || (dtype != DFD_F32 && dtype != DFD_I32) || dim < 1) return DFD_ERR_INVALID_ARG;
   if (dim > 16) return DFD_ERR_UNSUPPORTED;
   const int t = dtype == DFD_F32 ? 0 : 1, d = dim_class_index(dim_class(dim));
   if (order) *order = ctx->batch_order[t][d];
   if (team) *team = ctx->batch_team[t][d];
+  if (rows_per_lane) *rows_per_lane = ctx->batch_rmax[t][d];
+  if (ctas_per_sm) *ctas_per_sm = ctx->batch_cpsm[t][d];
+  return DFD_OK;
+}
+
+dfd_status dfd_batch_set_shape(dfd_context* ctx, dfd_dtype dtype, int dim, int rows_per_lane, int ctas_per_sm) {
+  if (!ctx || (dtype != DFD_F32 && dtype != DFD_I32) || dim < 1 || rows_per_lane < 0 || rows_per_lane > 8 ||
+      ctas_per_sm < 0 || ctas_per_sm > 2)
+    return DFD_ERR_INVALID_ARG;
+  if (dim > 16) return DFD_ERR_UNSUPPORTED;
+  const int t = dtype == DFD_F32 ? 0 : 1, d = dim_class_index(dim_class(dim));
+  ctx->batch_rmax[t][d] = (signed char)rows_per_lane;
+  ctx->batch_cpsm[t][d] = (signed char)ctas_per_sm;
+  return DFD_OK;
+}
+
+dfd_status dfd_matrix_set_shape(dfd_context* ctx, dfd_dtype dtype, int dim, int rows_per_lane, int ctas_per_sm) {
+  if (!ctx || (dtype != DFD_F32 && dtype != DFD_I32) || dim < 1 || rows_per_lane < 0 || rows_per_lane > 8 ||
+      ctas_per_sm < 0 || ctas_per_sm > 2)
+    return DFD_ERR_INVALID_ARG;
+  if (dim > 16) return DFD_ERR_UNSUPPORTED;
+  const int t = dtype == DFD_F32 ? 0 : 1, d = dim_class_index(dim_class(dim));
+  ctx->matrix_rmax[t][d] = (signed char)rows_per_lane;
+  ctx->matrix_cpsm[t][d] = (signed char)ctas_per_sm;
+  return DFD_OK;
+}
+
+dfd_status dfd_matrix_tuned(dfd_context* ctx, dfd_dtype dtype, int dim, int* rows_per_lane, int* ctas_per_sm) {
+  if (!ctx || (dtype != DFD_F32 && dtype != DFD_I32) || dim < 1) return DFD_ERR_INVALID_ARG;
+  if (dim > 16) return DFD_ERR_UNSUPPORTED;
+  const int t = dtype == DFD_F32 ? 0 : 1, d = dim_class_index(dim_class(dim));
+  if (rows_per_lane) *rows_per_lane = ctx->matrix_rmax[t][d];
+  if (ctas_per_sm) *ctas_per_sm = ctx->matrix_cpsm[t][d];
   return DFD_OK;
 }
 
@@ -913,6 +962,60 @@ dfd_status dfd_matrix(dfd_context* ctx, dfd_dtype dtype, int dim, const void* po
   if ((st = set_device(ctx)) != DFD_OK) return st;
   return matrix_run(ctx, dtype, dim, points, offsets, n_curves, out_condensed, out_dist2,
                     static_cast<cudaStream_t>(stream), 0);
+}
+
+dfd_status dfd_matrix_autotune(dfd_context* ctx, dfd_dtype dtype, int dim, const void* points, const int64_t* offsets,
+                               int64_t n_curves, void* out_condensed, void* out_dist2, int* best_rows_per_lane,
+                               int* best_ctas_per_sm, void* stream) {
+  dfd_status st = check_batch_args(ctx, dtype, dim, points, offsets, n_curves, out_condensed, out_dist2);
+  if (st != DFD_OK) return st;
+  if ((st = set_device(ctx)) != DFD_OK) return st;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int ti = dtype == DFD_F32 ? 0 : 1, di = dim_class_index(dim_class(dim));
+  signed char& rslot = ctx->matrix_rmax[ti][di];
+  signed char& cslot = ctx->matrix_cpsm[ti][di];
+  const signed char rkeep = rslot, ckeep = cslot;
+  const int rm_full = dim_class(dim) <= 4 ? 8 : 4;
+  const int cp_full = dim_class(dim) >= 16 ? 1 : 2;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    cudaGetLastError();
+    if (e0) cudaEventDestroy(e0);
+    return DFD_ERR_CUDA;
+  }
+  float best_ms = 0.f;
+  int best_rm = rkeep, best_cp = ckeep;
+  bool any = false;
+  // rows per lane cap Rmax, Rmax / 2, Rmax / 4 x CTAs per SM (all, 1)
+  for (int c = 0; c < 6 && st == DFD_OK && n_curves >= 2; ++c) {
+    const int rm = rm_full >> (c % 3), cp = c < 3 ? cp_full : 1;
+    if (rm < 1 || (c >= 3 && cp_full == 1)) continue;
+    rslot = (signed char)rm;
+    cslot = (signed char)cp;
+    st = matrix_run(ctx, dtype, dim, points, offsets, n_curves, out_condensed, out_dist2, s, 0);
+    if (st != DFD_OK) break;
+    cudaEventRecord(e0, s);
+    for (int r = 0; r < 2 && st == DFD_OK; ++r)
+      st = matrix_run(ctx, dtype, dim, points, offsets, n_curves, out_condensed, out_dist2, s, 0);
+    cudaEventRecord(e1, s);
+    float ms = 0.f;
+    if (st == DFD_OK && (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+      st = DFD_ERR_CUDA;
+    if (st == DFD_OK && (!any || ms < best_ms)) {
+      best_ms = ms;
+      best_rm = rm;
+      best_cp = cp;
+      any = true;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaGetLastError();
+  rslot = (signed char)(st == DFD_OK ? best_rm : rkeep);
+  cslot = (signed char)(st == DFD_OK ? best_cp : ckeep);
+  if (best_rows_per_lane) *best_rows_per_lane = rslot;
+  if (best_ctas_per_sm) *best_ctas_per_sm = cslot;
+  return st;
 }
 
 dfd_status dfd_batch_capture(dfd_context* ctx, dfd_dtype dtype, int dim, const void* points, const int64_t* offsets,

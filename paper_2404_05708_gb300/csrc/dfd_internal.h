@@ -47,6 +47,10 @@ struct dfd_context {
   std::map<uint64_t, dfd::WaveShape> tuned;   // autotuned wavefront shapes
   signed char batch_order[2][5] = {};         // batch packing order per (float32 / int32, dim class 2,3,4,8,16)
   signed char batch_team[2][5] = {};          // batch team mode per (dtype, dim class): 0 auto, 1 wide pairs, 2 all multi-stripe
+  signed char batch_rmax[2][5] = {};          // batch tile shape: rows per lane cap (0 = Rmax)
+  signed char batch_cpsm[2][5] = {};          //   and CTAs per SM (0 = every resident CTA)
+  signed char matrix_rmax[2][5] = {};         // matrix tile shape, likewise
+  signed char matrix_cpsm[2][5] = {};
   cudaStream_t copy_stream = nullptr;         // dfd_batch_host: point slices (created on first use)
   cudaEvent_t slice_ev[dfd::kMaxSlices + 1] = {};   // one per slice, and one for the allocation
   int batch_buf_cols = dfd::kDefaultBatchBufCols;   // ragged batch: row buffer columns per warp

@@ -92,7 +92,13 @@ _SIGS = {
     "dfd_batch_set_order": [_VP, _INT, _INT, _INT],
     "dfd_batch_set_row_buffer": [_VP, _INT],
     "dfd_batch_set_team": [_VP, _INT, _INT, _INT],
-    "dfd_batch_tuned": [_VP, _INT, _INT, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)],
+    "dfd_batch_tuned": [_VP, _INT, _INT, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                        ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)],
+    "dfd_batch_set_shape": [_VP, _INT, _INT, _INT, _INT],
+    "dfd_matrix_set_shape": [_VP, _INT, _INT, _INT, _INT],
+    "dfd_matrix_tuned": [_VP, _INT, _INT, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)],
+    "dfd_matrix_autotune": [_VP, _INT, _INT, _VP, _VP, _I64, _VP, _VP, ctypes.POINTER(ctypes.c_int),
+                            ctypes.POINTER(ctypes.c_int), _VP],
     "dfd_matrix": [_VP, _INT, _INT, _VP, _VP, _I64, _VP, _VP, _VP],
     "dfd_batch_decide": [_VP, _INT, _INT, _VP, _VP, _I64, _VP, _I64, _VP, ctypes.c_double, _VP, _VP, _VP, _VP],
     "dfd_mc_pair": [_VP, _INT, _VP, _I64, _VP, _I64, _VP, _VP, ctypes.c_float, ctypes.c_float, _I64, _VP, _VP, _VP],
@@ -627,11 +633,45 @@ class Context:
         _check(load_library().dfd_batch_set_team(self.handle, dtype, dim, mode), "dfd_batch_set_team")
 
     def batch_tuned(self, dtype: int, dim: int):
-        """(packing order, team mode) recorded for (dtype, dim class)."""
-        o, t = ctypes.c_int(0), ctypes.c_int(0)
-        _check(load_library().dfd_batch_tuned(self.handle, dtype, dim, ctypes.byref(o), ctypes.byref(t)),
-               "dfd_batch_tuned")
-        return o.value, t.value
+        """(packing order, team mode, rows per lane cap, CTAs per SM) recorded for
+        (dtype, dim class); 0 = the default."""
+        o, t, r, c = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int(0)
+        _check(load_library().dfd_batch_tuned(self.handle, dtype, dim, ctypes.byref(o), ctypes.byref(t),
+                                              ctypes.byref(r), ctypes.byref(c)), "dfd_batch_tuned")
+        return o.value, t.value, r.value, c.value
+
+    def set_batch_shape(self, dtype: int, dim: int, rows_per_lane: int, ctas_per_sm: int):
+        """Tile shape of the ragged batch's one-warp pairs (0, 0 = defaults)."""
+        _check(load_library().dfd_batch_set_shape(self.handle, dtype, dim, rows_per_lane, ctas_per_sm),
+               "dfd_batch_set_shape")
+
+    def set_matrix_shape(self, dtype: int, dim: int, rows_per_lane: int, ctas_per_sm: int):
+        """Tile shape of the all-pairs matrix (0, 0 = defaults)."""
+        _check(load_library().dfd_matrix_set_shape(self.handle, dtype, dim, rows_per_lane, ctas_per_sm),
+               "dfd_matrix_set_shape")
+
+    def matrix_tuned(self, dtype: int, dim: int):
+        r, c = ctypes.c_int(0), ctypes.c_int(0)
+        _check(load_library().dfd_matrix_tuned(self.handle, dtype, dim, ctypes.byref(r), ctypes.byref(c)),
+               "dfd_matrix_tuned")
+        return r.value, c.value
+
+    def matrix_autotune(self, points, offsets, stream=None):
+        """Time the matrix's tile shapes on these curves (device tensors), keep
+        the fastest; returns (rows per lane cap, CTAs per SM)."""
+        torch = _torch()
+        points = _curve(points)
+        dt = _dtype_code(points)
+        offsets = offsets.contiguous()
+        n = offsets.numel() - 1
+        npairs = n * (n - 1) // 2
+        od, od2 = self._batch_outs(dt, npairs, None, None)
+        r, c = ctypes.c_int(0), ctypes.c_int(0)
+        s = stream if stream is not None else torch.cuda.current_stream(self.device).cuda_stream
+        _check(load_library().dfd_matrix_autotune(self.handle, dt, points.shape[1], points.data_ptr(),
+                                                  offsets.data_ptr(), n, od.data_ptr(), od2.data_ptr(),
+                                                  ctypes.byref(r), ctypes.byref(c), s), "dfd_matrix_autotune")
+        return r.value, c.value
 
     def set_batch_row_buffer(self, cols: int):
         """Widen the ragged batch's per-warp row buffer (columns, >= 4096): pairs

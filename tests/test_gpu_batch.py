@@ -452,6 +452,67 @@ def test_matrix_small_int(dctx):
     assert np.array_equal(d2.cpu().numpy(), ref)
 
 
+@pytest.mark.parametrize("dtype,dim", [("i32", 2), ("f32", 3), ("f32", 16)])
+def test_batch_tile_shapes_bit_identical(dctx, dtype, dim):
+    """Every tile shape of the one-warp pairs (rows per lane cap 1 .. Rmax,
+    CTAs per SM 1 or all) gives every pair the same bits, on both sides of
+    the stripe edges; the autotuner records a valid shape that reproduces them."""
+    from paper_2404_05708_gb300 import dfd
+    code = dfd.DFD_I32 if dtype == "i32" else dfd.DFD_F32
+    b = ragged_edges(dtype, dim, 170 + dim)
+    want, _ = oracle.batch(b.points, b.offsets, b.pairs, mirror=(dtype == "f32"))
+    rm_full = 8 if dim <= 4 else 4
+    for rm in (1, 2, 3, rm_full):
+        for cp in (0, 1):
+            dctx.set_batch_shape(code, dim, rm, cp)
+            for team in (1, 2):
+                dctx.set_batch_team(code, dim, team)
+                _, d2 = run_batch(dctx, b)
+                assert dctx.get_error() == 0
+                assert np.array_equal(d2, want), (rm, cp, team, np.nonzero(d2 != want)[0][:10])
+    dctx.set_batch_shape(code, dim, 0, 0)
+    dctx.set_batch_team(code, dim, 0)
+    order = dctx.batch_autotune(dev(b.points), dev(b.offsets), dev(b.pairs))
+    o, team, rm, cp = dctx.batch_tuned(code, dim)
+    assert o == order and team in (1, 2) and rm in (rm_full // 2, rm_full) and cp in (1, 2)
+    _, d2 = run_batch(dctx, b)
+    assert np.array_equal(d2, want)
+    dctx.set_batch_shape(code, dim, 0, 0)
+    dctx.set_batch_team(code, dim, 0)
+    dctx.set_batch_order(code, dim, 0)
+
+
+def test_matrix_tile_shapes_bit_identical(dctx):
+    """The matrix under every tile shape equals the oracle bit for bit
+    (float32 16-D: the selection mirror; int32 3-D: exact), including curves
+    of 300 points that a cap of one row per lane splits into 10 stripes,
+    and the autotuner records a shape."""
+    from paper_2404_05708_gb300 import dfd
+    bf = workloads.ar1_curves(n_curves=40, seed=53)
+    _, mirror_f = condensed_oracle(bf)
+    rng = np.random.default_rng(54)
+    lens = rng.integers(1, 300, size=36)
+    off = np.zeros(37, np.int64)
+    np.cumsum(lens, out=off[1:])
+    pts = np.cumsum(rng.integers(-100, 101, size=(off[-1], 3)), axis=0).astype(np.int32)
+    bi = workloads.Batch(points=pts, offsets=off, pairs=np.zeros((0, 2), np.int32))
+    (ref_i, _), _ = condensed_oracle(bi)
+    for rm in (1, 2, 4, 8):
+        for cp in (0, 1):
+            dctx.set_matrix_shape(dfd.DFD_F32, 16, min(rm, 4), cp)
+            dctx.set_matrix_shape(dfd.DFD_I32, 3, rm, cp)
+            _, d2 = dctx.matrix(dev(bf.points), dev(bf.offsets))
+            _, e2 = dctx.matrix(dev(pts), dev(off))
+            torch.cuda.synchronize()
+            assert dctx.get_error() == 0
+            assert np.array_equal(d2.cpu().numpy(), mirror_f[0]), (rm, cp)
+            assert np.array_equal(e2.cpu().numpy(), ref_i), (rm, cp)
+    rm, cp = dctx.matrix_autotune(dev(pts), dev(off))
+    assert (rm, cp) == dctx.matrix_tuned(dfd.DFD_I32, 3) and rm in (2, 4, 8) and cp in (1, 2)
+    for code, dim in ((dfd.DFD_F32, 16), (dfd.DFD_I32, 3)):
+        dctx.set_matrix_shape(code, dim, 0, 0)
+
+
 def test_matrix_full_size_sampled(dctx):
     """4096 curves, 16-D AR(1), lengths U{64..256}: 8,386,560 pairs, 400 sampled entries vs the oracle."""
     b = workloads.ar1_curves()
