@@ -805,7 +805,7 @@ __device__ __forceinline__ void comm_warp(const Args& a, const Prob& pb, int64_t
 
 // ------------------------------------------------------------------ kernel
 template <class V, int DK, int R>
-__global__ void __launch_bounds__((kMaxWarps<V, DK, R>::value + 1) * 32, blocks_per_sm(DK)) wave_kernel(Args a) {
+__global__ void __launch_bounds__((kMaxWarps<V, DK, R>::value + 1) * 32, 1) wave_kernel(Args a) {
   using Lay = Layout<V, DK, R>;
   using T = typename V::value;
   constexpr int NQ = Lay::NQ;

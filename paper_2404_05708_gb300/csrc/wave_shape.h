@@ -21,6 +21,9 @@ constexpr int chunk_cols(int dk) { return dk <= 4 ? 512 : 128; }
 // compute warp per sub-partition left the step's dependent chain exposed);
 // larger points keep 8 slots of 128 columns and one CTA per SM.
 constexpr int nq_slots(int C) { return C >= 512 ? 4 : 8; }
+// CTAs an SM can hold at the planner's shapes (the occupancy query decides
+// at launch; the kernel is compiled for one CTA per SM, so a CTA may also
+// have as many warps as the register file allows).
 constexpr int blocks_per_sm(int dk) { return dk <= 4 ? 2 : 1; }
 
 // Column skew between neighbouring lanes: float32 lanes hold R/2 skewed row
@@ -45,13 +48,12 @@ constexpr int reg_estimate(bool f32, int dk, int R) {
 }
 
 // Compute warps per CTA the register file allows (with the communication
-// warp, blocks_per_sm CTAs per SM); 0 if even one warp would not fit in 255
-// registers.
+// warp, one CTA per SM); 0 if even one warp would not fit in 255 registers.
 constexpr int max_warps_regs(bool f32, int dk, int R) {
   return reg_estimate(f32, dk, R) > 248 ? 0
-         : (65536 / blocks_per_sm(dk) / (32 * ((reg_estimate(f32, dk, R) + 7) / 8 * 8)) - 1) > 16
+         : (65536 / (32 * ((reg_estimate(f32, dk, R) + 7) / 8 * 8)) - 1) > 16
              ? 16
-             : 65536 / blocks_per_sm(dk) / (32 * ((reg_estimate(f32, dk, R) + 7) / 8 * 8)) - 1;
+             : 65536 / (32 * ((reg_estimate(f32, dk, R) + 7) / 8 * 8)) - 1;
 }
 
 constexpr bool shape_supported(bool f32, int dk, int R, int W) {
