@@ -909,10 +909,18 @@ def run_paper(args):
             ctx.set_batch_team(dfd.DFD_F32, 2, mode)
             ms = timed(lambda: out.__setitem__("r", ctx.batch(pts, O, Q)))
             d2 = out["r"][1][:nchk].cpu().numpy()
+            ok = bool(np.array_equal(d2, mirror)) and ctx.get_error() == 0
+            # the same call captured once in a CUDA graph (the batch API's hot path:
+            # one graph launch per step instead of the call's six launches)
+            graph, _, g2 = ctx.batch(pts, O, Q, capture=True)
+            ms_g = timed(graph.launch)
+            ok_g = bool(np.array_equal(g2[:nchk].cpu().numpy(), mirror)) and ctx.get_error() == 0
+            graph.close()
             rows.append({"sweep": sweep, "P": P, "N": N, "cells_per_step": cells, "ms": ms,
                          "gcups": cells / (ms * 1e-3) / 1e9, "engine": engine, "team_mode": mode,
                          "roofline_frac": cells / (ms * 1e-3) / 1e9 / peak,
-                         "verified_vs_oracle": bool(np.array_equal(d2, mirror)) and ctx.get_error() == 0})
+                         "graph_ms": ms_g, "graph_gcups": cells / (ms_g * 1e-3) / 1e9,
+                         "verified_vs_oracle": ok and ok_g})
         ctx.set_batch_team(dfd.DFD_F32, 2, 0)
         if P >= 4096:
             curves = [pts[b.offsets[c]:b.offsets[c + 1]] for c in range(2 * N)]
