@@ -175,8 +175,10 @@ dfd_status dfd_batch(dfd_context* ctx, dfd_dtype dtype, int dim, const void* poi
  * along a monotone path's prefix bottleneck, so delta^2 >= min of M over any
  * set of cells every path must enter; once such a set of the running
  * recurrence exceeds eps^2 the pair is abandoned (the heuristics that avoid
- * full computations, Sec. 5).  Same inputs, engine and limits as dfd_batch,
- * plus:
+ * full computations, Sec. 5).  Same inputs and engine as dfd_batch, one
+ * warp per pair (no CTA teams): a pair of several stripes whose longer curve
+ * is wider than 4096 points gets within = 0, out_dist2 NaN (float) / -1
+ * (int64) and DFD_ERR_UNSUPPORTED in the error word.  Plus:
  *   eps2:       per-pair squared thresholds, device (float for DFD_F32,
  *               int64 for DFD_I32), or NULL to use eps2_all for every pair
  *               (compared as: float32 delta^2 <= the largest float <=
@@ -225,8 +227,10 @@ dfd_status dfd_knn(dfd_context* ctx, int dim, const float* query, int64_t n, con
 
 /*
  * The appendix variants of the recurrence (DTW and the Levenshtein
- * distance), many pairs per launch on the batch engine (same inputs, order
- * and limits as dfd_batch):
+ * distance), many pairs per launch on the batch engine (same inputs and
+ * order as dfd_batch, one warp per pair: a pair of several stripes whose
+ * longer curve is wider than 4096 points gets NaN / -1 and
+ * DFD_ERR_UNSUPPORTED in the error word):
  *   DFD_VARIANT_DTW: dtype DFD_F32, 1 <= dim <= 16; out = float[n_pairs],
  *     D_{n,m} of D_ij = fl(min(D_{i-1,j}, D_{i-1,j-1}, D_{i,j-1}) + c_ij)
  *     with c_ij the float32 squared distance of dfd_pair and the first row /
@@ -265,8 +269,10 @@ dfd_status dfd_mc_pair(dfd_context* ctx, int dim, const float* p, int64_t n, con
  * clustering and distance matrices of trajectories, Sec. 2), condensed upper
  * triangle: entry k = i*(2N - i - 1)/2 + (j - i - 1) for i < j (N =
  * n_curves), N*(N-1)/2 elements in out_condensed (distances) and/or
- * out_dist2.  Pairs are decoded from k on the device; same engine and
- * limits as dfd_batch.
+ * out_dist2.  Pairs are decoded from k on the device; the batch engine, one
+ * warp per pair, tile shape per dfd_matrix_set_shape.  A pair of several
+ * stripes whose longer curve is wider than 4096 points gets NaN (float,
+ * double) / -1 (int64) and DFD_ERR_UNSUPPORTED in the error word.
  */
 dfd_status dfd_matrix(dfd_context* ctx, dfd_dtype dtype, int dim, const void* points, const int64_t* offsets,
                       int64_t n_curves, void* out_condensed, void* out_dist2, void* stream);

@@ -648,6 +648,19 @@ __device__ __forceinline__ void write_result(void* out_dist, void* out_dist2, in
   }
 }
 
+// Outputs of a pair the kernel cannot run (a row wider than its buffer):
+// NaN (float, double) / -1 (int64), beside DFD_ERR_UNSUPPORTED in the error word.
+template <class V>
+__device__ __forceinline__ void write_unsupported(void* out_dist, void* out_dist2, int64_t k) {
+  if constexpr (std::is_same<V, F32>::value) {
+    if (out_dist2) static_cast<float*>(out_dist2)[k] = __int_as_float(0x7fffffff);
+    if (out_dist) static_cast<float*>(out_dist)[k] = __int_as_float(0x7fffffff);
+  } else {
+    if (out_dist2) static_cast<long long*>(out_dist2)[k] = -1;
+    if (out_dist) static_cast<double*>(out_dist)[k] = __longlong_as_double(0x7fffffffffffffffLL);
+  }
+}
+
 // int32 pairs whose bounding boxes keep every squared distance exact in
 // uint32 (below the first float NaN pattern) run as I32B.  bbox holds per
 // curve and coordinate (min, max).
@@ -1163,7 +1176,10 @@ __global__ void __launch_bounds__(256, kBlocksPerSM<DK>::value) batch_kernel(Bat
     if (n < 1 || m < 1) continue;                                            // reported by the plan
     if (!fits_buffer<DK>(n, m, a.buf_cols, a.rmax)) {
       // only when the plan made no team items (decider-style launches)
-      if (L == 0) raise_error(a.err, DFD_ERR_UNSUPPORTED);
+      if (L == 0) {
+        raise_error(a.err, DFD_ERR_UNSUPPORTED);
+        write_unsupported<V>(a.out_dist, a.out_dist2, k);
+      }
       continue;
     }
     if constexpr (std::is_same<V, I32>::value) {
@@ -1195,14 +1211,7 @@ __global__ void __launch_bounds__(256, kBlocksPerSM<DK>::value) batch_kernel(Bat
   for (unsigned d = 0; d < nd; ++d) {
     const unsigned we = static_cast<volatile unsigned*>(a.deferred)[d];
     if (!run_team_pair<V, DK>(a, we, a.rowbuf, pool, stage, team_ring, team_prog, team_cons) && threadIdx.x == 0) {
-      const int64_t k = we & (kNarrowBit - 1);
-      if constexpr (std::is_same<V, F32>::value) {
-        if (a.out_dist2) static_cast<float*>(a.out_dist2)[k] = __int_as_float(0x7fffffff);
-        if (a.out_dist) static_cast<float*>(a.out_dist)[k] = __int_as_float(0x7fffffff);
-      } else {
-        if (a.out_dist2) static_cast<long long*>(a.out_dist2)[k] = -1;
-        if (a.out_dist) static_cast<double*>(a.out_dist)[k] = __longlong_as_double(0x7fffffffffffffffLL);
-      }
+      write_unsupported<V>(a.out_dist, a.out_dist2, we & (kNarrowBit - 1));
       raise_error(a.err, DFD_ERR_UNSUPPORTED);
     }
   }
@@ -1262,7 +1271,12 @@ __global__ void __launch_bounds__(256, kBlocksPerSM<DK>::value) decide_kernel(De
     const int n = (int)(ea - oa), m = (int)(eb - ob);
     if (n < 1 || m < 1) continue;
     if (!fits_buffer<DK>(n, m)) {
-      if (L == 0) raise_error(a.err, DFD_ERR_UNSUPPORTED);
+      // no decision: not within, delta^2 NaN / -1, and the error word says so
+      if (L == 0) {
+        raise_error(a.err, DFD_ERR_UNSUPPORTED);
+        if (d.within) d.within[k] = 0;
+        write_unsupported<V>(nullptr, a.out_dist2, k);
+      }
       continue;
     }
     bool hit = false, within = false;
@@ -1392,6 +1406,7 @@ __global__ void __launch_bounds__(256, kBlocksPerSM<DK>::value) matrix_kernel(Ma
         }
       } else if (L == 0) {
         raise_error(a.err, DFD_ERR_UNSUPPORTED);
+        write_unsupported<V>(a.out_dist, a.out_dist2, k);
       }
       if (++j == a.n_curves) {
         ++i;

@@ -281,7 +281,14 @@ __global__ void __launch_bounds__(256, batch::kBlocksPerSM<DK>::value) variant_k
     const int n = (int)(ea - oa), m = (int)(eb - ob);
     if (n < 1 || m < 1) continue;
     if (!batch::fits_buffer<DK>(n, m)) {
-      if (L == 0) raise_error(a.err, DFD_ERR_UNSUPPORTED);
+      // longer curve wider than a warp's row buffer: no value; NaN / -1 and the error word say so
+      if (L == 0) {
+        raise_error(a.err, DFD_ERR_UNSUPPORTED);
+        if constexpr (Op::lev)
+          static_cast<long long*>(a.out_dist2)[k] = -1;
+        else
+          static_cast<float*>(a.out_dist2)[k] = __int_as_float(0x7fffffff);
+      }
       continue;
     }
     const T r = warp_var_any<Op, DK>(pts + oa * a.dim, n, pts + ob * a.dim, m, a.dim, a.vec != 0, buf, L, stage);

@@ -532,3 +532,56 @@ def test_matrix_full_size_sampled(dctx):
     got = d.cpu().numpy()[ks]
     assert np.array_equal(got2, mirror)
     assert np.all(np.abs(got - np.sqrt(ref)) <= REL_TOL * np.sqrt(ref))
+
+
+def test_wide_pairs_outside_the_batch_get_nan_and_an_error(dctx):
+    """The decider, the DTW / Levenshtein variants and the matrix run one warp
+    per pair with a 4096-column row buffer: a pair of several stripes whose
+    longer curve is wider gets NaN (float) / -1 (int64) outputs, never stale
+    memory, and DFD_ERR_UNSUPPORTED in the error word; the other pairs are
+    exact."""
+    from paper_2404_05708_gb300 import dfd
+    rng = np.random.default_rng(180)
+    lens = np.array([300, 5000, 100, 260])
+    off = np.concatenate([[0], np.cumsum(lens)]).astype(np.int64)
+    pts = np.cumsum(rng.normal(0, 1, size=(int(off[-1]), 2)), axis=0).astype(np.float32)
+    pairs = np.array([[0, 1], [0, 2], [2, 3], [3, 1]], np.int32)   # 0 and 3 are wide
+    wide = np.array([True, False, False, True])
+    P, O, Q = dev(pts), dev(off), dev(pairs)
+    mirror, _ = oracle.batch(pts, off, pairs, mirror=True)
+    unsupported = dfd.STATUS_CODE["DFD_ERR_UNSUPPORTED"]
+
+    d2, within, _ = dctx.decide(P, O, Q, 1e12)
+    torch.cuda.synchronize()
+    assert dctx.get_error() == unsupported
+    d2, within = d2.cpu().numpy(), within.cpu().numpy()
+    assert np.all(np.isnan(d2[wide])) and np.all(within[wide] == 0)
+    assert np.array_equal(d2[~wide], mirror[~wide]) and np.all(within[~wide] == 1)
+
+    out = dctx.dtw(P, O, Q)
+    torch.cuda.synchronize()
+    assert dctx.get_error() == unsupported
+    out = out.cpu().numpy()
+    want = np.array([oracle.dtw_f32mirror(pts[off[a]:off[a + 1]], pts[off[b]:off[b + 1]]) for a, b in pairs],
+                    np.float32)
+    assert np.all(np.isnan(out[wide])) and np.array_equal(out[~wide], want[~wide])
+
+    sym = rng.integers(0, 4, size=(int(off[-1]), 1)).astype(np.int32)
+    lev = dctx.levenshtein(dev(sym), O, Q)
+    torch.cuda.synchronize()
+    assert dctx.get_error() == unsupported
+    lev = lev.cpu().numpy()
+    assert np.all(lev[wide] == -1)
+    for k in np.nonzero(~wide)[0]:
+        a, b = pairs[k]
+        assert lev[k] == oracle.levenshtein(sym[off[a]:off[a + 1], 0], sym[off[b]:off[b + 1], 0])
+
+    d, dm2 = dctx.matrix(P, O)
+    torch.cuda.synchronize()
+    assert dctx.get_error() == unsupported
+    ii, jj = np.triu_indices(4, k=1)
+    mat_pairs = np.stack([ii, jj], 1).astype(np.int32)
+    mwant, _ = oracle.batch(pts, off, mat_pairs, mirror=True)
+    mwide = (np.minimum(lens[ii], lens[jj]) > 256) & (np.maximum(lens[ii], lens[jj]) > 4096)
+    dm2 = dm2.cpu().numpy()
+    assert mwide.sum() == 2 and np.all(np.isnan(dm2[mwide])) and np.array_equal(dm2[~mwide], mwant[~mwide])
