@@ -44,12 +44,14 @@ struct kBlocksPerSM {
 // stored plane-major ([plane][64 slots]) so lanes one column apart read
 // consecutive records.  (Per-lane loads left lane 0 waiting on L2 for every
 // new point.)  After the planes, 16 records hold the stripe's bottom row of
-// the current block (lane 31 stores one value per step).
+// the current block (lane 31 stores four values at a time), and 16 more the
+// stripe above's values for the block's columns (lane 0 reads eight at a
+// time).
 template <int DK>
 struct QStage {
   static constexpr bool on = true;
   static constexpr int NPL = (DK + 3) / 4;
-  static constexpr int RECS = NPL * 64 + 16;   // uint4 records per warp
+  static constexpr int RECS = NPL * 64 + 32;   // uint4 records per warp
 };
 
 // Form of a column's record in the window.
@@ -169,6 +171,41 @@ __device__ __forceinline__ void team_wait(const unsigned long long* p, unsigned 
         raise_error(err, DFD_ERR_TIMEOUT);
         return;
       }
+    }
+  }
+}
+
+// Eight values of a warp's staging area into registers (16-byte loads), and
+// four out of them (16-byte stores); the addresses are 16-byte aligned.
+template <class T>
+__device__ __forceinline__ void load8(const T* p, T (&v)[8]) {
+  const uint4* q = reinterpret_cast<const uint4*>(p);
+#pragma unroll
+  for (int i = 0; i < (int)(8 * sizeof(T) / 16); ++i) {
+    const uint4 x = q[i];
+    const unsigned w[4] = {x.x, x.y, x.z, x.w};
+    if constexpr (sizeof(T) == 4) {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) v[4 * i + j] = __uint_as_float(w[j]);
+    } else {
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        const unsigned long long z = ((unsigned long long)w[2 * j + 1] << 32) | w[2 * j];
+        v[2 * i + j] = (T)(long long)z;
+      }
+    }
+  }
+}
+template <class T>
+__device__ __forceinline__ void store4(T* p, const T (&v)[4]) {
+  uint4* q = reinterpret_cast<uint4*>(p);
+  if constexpr (sizeof(T) == 4) {
+    q[0] = make_uint4(__float_as_uint(v[0]), __float_as_uint(v[1]), __float_as_uint(v[2]), __float_as_uint(v[3]));
+  } else {
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+      const unsigned long long a = (unsigned long long)(long long)v[2 * i], b = (unsigned long long)(long long)v[2 * i + 1];
+      q[i] = make_uint4((unsigned)a, (unsigned)(a >> 32), (unsigned)b, (unsigned)(b >> 32));
     }
   }
 }
@@ -451,6 +488,7 @@ __device__ __forceinline__ typename V::value warp_dfd(const typename V::coord* _
     load_point<Cd, DK>(Q, min(L, m - 1), dim, vec, qpre);
     const uint4* sb = stage + (32 - L);   // column c0 + s - L of the window is sb[s]
     T* outb = reinterpret_cast<T*>(stage + NPL * 64);
+    T* topb = reinterpret_cast<T*>(stage + NPL * 64 + 16);
     for (int c0 = 0; c0 < nsteps; c0 += 32) {
       const T top_blk = has_top ? IO::top(io, buf, st, c0, L, m) : V::inf();
       // slide the window: the block before's columns (slot 32 + L, written
@@ -461,98 +499,110 @@ __device__ __forceinline__ typename V::value warp_dfd(const typename V::coord* _
         stage[c * 64 + L] = c0 > 0 ? stage[c * 64 + 32 + L] : make_qrec<V, DK>(qpre, c);
         stage[c * 64 + 32 + L] = make_qrec<V, DK>(qpre, c);
       }
+      topb[L] = top_blk;   // the stripe above's columns c0 .. c0 + 31, read by lane 0 eight at a time
       __syncwarp();
       load_point<Cd, DK>(Q, min(c0 + 32 + L, m - 1), dim, vec, qpre);   // next block, in flight
       uint4 qr[NPL];
 #pragma unroll
       for (int c = 0; c < NPL; ++c) qr[c] = sb[c * 64];
-      // 8 steps unrolled (not 32): a kernel holds every R variant, and warps
-      // running different variants side by side must not thrash the
-      // instruction cache (the ragged int32 batch: 2.86 Tcell/s unrolled by
-      // 4, 3.04 by 8, 2.78 fully).  The next step's record is read
-      // unconditionally: at the block's last step that read lands on the
-      // next plane's (or the bottom row's) first slots of this warp's
-      // window, inside the array, and is never used.
-#pragma unroll 8
-      for (int s = 0; s < 32; ++s) {
-        uint4 qn[NPL];   // the next step's record, read one step ahead
+      // Groups of 8 steps unrolled (not 32): a kernel holds every R variant,
+      // and warps running different variants side by side must not thrash
+      // the instruction cache (the ragged int32 batch: 2.86 Tcell/s unrolled
+      // by 4, 3.04 by 8, 2.78 fully).  Per group, lane 0's inputs from the
+      // stripe above come from the staging area in two or four 16-byte loads
+      // (was a shuffle per step) and lane 31's bottom values leave in
+      // 16-byte stores of four (was a store per step): 3.04 -> 3.26.  The
+      // next step's record is read unconditionally: at the block's last step
+      // that read lands on the next plane's (or the bottom row's) first
+      // slots of this warp's window, inside the array, and is never used.
+#pragma unroll 1
+      for (int s8 = 0; s8 < 32; s8 += 8) {
+        T tv[8];
+        load8<T>(topb + s8, tv);
+        T ob[4];
 #pragma unroll
-        for (int c = 0; c < NPL; ++c) qn[c] = sb[c * 64 + s + 1];
-        T d[R];
-        if constexpr (QR::kind == kNorm) {
-#pragma unroll
-          for (int r = 0; r < R; ++r) {
-            unsigned acc = pn[r] + qr[0].w;
-            acc += (unsigned)pr[r][0] * qr[0].x;
-            if (DK > 1) acc += (unsigned)pr[r][1] * qr[0].y;
-            if (DK > 2) acc += (unsigned)pr[r][2 < DK ? 2 : 0] * qr[0].z;
-            d[r] = __uint_as_float(acc);
-          }
-        } else if constexpr (QR::kind == kDup) {
-          unsigned long long qd[2];
-          qd[0] = ((unsigned long long)qr[0].y << 32) | qr[0].x;
-          qd[1] = ((unsigned long long)qr[0].w << 32) | qr[0].z;
-#pragma unroll
-          for (int h = 0; h < R / 2; ++h) {
-            const unsigned long long t0 = sub2(pp[h][0], qd[0]);
-            const unsigned long long t1 = sub2(pp[h][1], qd[1]);
-            const unsigned long long acc = fma2(t1, t1, mul2(t0, t0));
-            d[2 * h] = lo2(acc);
-            d[2 * h + 1] = hi2(acc);
-          }
-          if constexpr ((R & 1) != 0) {
-            const Cd qk[DK] = {__uint_as_float(qr[0].x), __uint_as_float(qr[0].z)};
-            d[R - 1] = vdist2<V, DK>(pr[R - 1], qk);
-          }
-        } else {
-          Cd qk[DK];
-#pragma unroll
-          for (int c = 0; c < NPL; ++c) {
-            qk[4 * c] = *reinterpret_cast<const Cd*>(&qr[c].x);
-            if (4 * c + 1 < DK) qk[4 * c + 1] = *reinterpret_cast<const Cd*>(&qr[c].y);
-            if (4 * c + 2 < DK) qk[4 * c + 2] = *reinterpret_cast<const Cd*>(&qr[c].z);
-            if (4 * c + 3 < DK) qk[4 * c + 3] = *reinterpret_cast<const Cd*>(&qr[c].w);
-          }
-          if constexpr (kPack) {
-            unsigned long long qd[DK];
-#pragma unroll
-            for (int k = 0; k < DK; ++k) qd[k] = pack2(qk[k], qk[k]);
-#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+          const int s = s8 + t;
+          uint4 qn[NPL];   // the next step's record, read one step ahead
+  #pragma unroll
+          for (int c = 0; c < NPL; ++c) qn[c] = sb[c * 64 + s + 1];
+          T d[R];
+          if constexpr (QR::kind == kNorm) {
+  #pragma unroll
+            for (int r = 0; r < R; ++r) {
+              unsigned acc = pn[r] + qr[0].w;
+              acc += (unsigned)pr[r][0] * qr[0].x;
+              if (DK > 1) acc += (unsigned)pr[r][1] * qr[0].y;
+              if (DK > 2) acc += (unsigned)pr[r][2 < DK ? 2 : 0] * qr[0].z;
+              d[r] = __uint_as_float(acc);
+            }
+          } else if constexpr (QR::kind == kDup) {
+            unsigned long long qd[2];
+            qd[0] = ((unsigned long long)qr[0].y << 32) | qr[0].x;
+            qd[1] = ((unsigned long long)qr[0].w << 32) | qr[0].z;
+  #pragma unroll
             for (int h = 0; h < R / 2; ++h) {
               const unsigned long long t0 = sub2(pp[h][0], qd[0]);
-              unsigned long long acc = mul2(t0, t0);
-#pragma unroll
-              for (int k = 1; k < DK; ++k) {
-                const unsigned long long t = sub2(pp[h][k], qd[k]);
-                acc = fma2(t, t, acc);
-              }
+              const unsigned long long t1 = sub2(pp[h][1], qd[1]);
+              const unsigned long long acc = fma2(t1, t1, mul2(t0, t0));
               d[2 * h] = lo2(acc);
               d[2 * h + 1] = hi2(acc);
             }
-            if constexpr ((R & 1) != 0) d[R - 1] = vdist2<V, DK>(pr[R - 1], qk);
+            if constexpr ((R & 1) != 0) {
+              const Cd qk[DK] = {__uint_as_float(qr[0].x), __uint_as_float(qr[0].z)};
+              d[R - 1] = vdist2<V, DK>(pr[R - 1], qk);
+            }
           } else {
-#pragma unroll
-            for (int r = 0; r < R; ++r) d[r] = vdist2<V, DK>(pr[r], qk);
+            Cd qk[DK];
+  #pragma unroll
+            for (int c = 0; c < NPL; ++c) {
+              qk[4 * c] = *reinterpret_cast<const Cd*>(&qr[c].x);
+              if (4 * c + 1 < DK) qk[4 * c + 1] = *reinterpret_cast<const Cd*>(&qr[c].y);
+              if (4 * c + 2 < DK) qk[4 * c + 2] = *reinterpret_cast<const Cd*>(&qr[c].z);
+              if (4 * c + 3 < DK) qk[4 * c + 3] = *reinterpret_cast<const Cd*>(&qr[c].w);
+            }
+            if constexpr (kPack) {
+              unsigned long long qd[DK];
+  #pragma unroll
+              for (int k = 0; k < DK; ++k) qd[k] = pack2(qk[k], qk[k]);
+  #pragma unroll
+              for (int h = 0; h < R / 2; ++h) {
+                const unsigned long long t0 = sub2(pp[h][0], qd[0]);
+                unsigned long long acc = mul2(t0, t0);
+  #pragma unroll
+                for (int k = 1; k < DK; ++k) {
+                  const unsigned long long t = sub2(pp[h][k], qd[k]);
+                  acc = fma2(t, t, acc);
+                }
+                d[2 * h] = lo2(acc);
+                d[2 * h + 1] = hi2(acc);
+              }
+              if constexpr ((R & 1) != 0) d[R - 1] = vdist2<V, DK>(pr[R - 1], qk);
+            } else {
+  #pragma unroll
+              for (int r = 0; r < R; ++r) d[r] = vdist2<V, DK>(pr[r], qk);
+            }
           }
+          T u = __shfl_up_sync(0xffffffffu, bout, 1);
+          u = (L == 0) ? tv[t] : u;
+          T up = u, dg = upp;
+  #pragma unroll
+          for (int r = 0; r < R; ++r) {
+            const T l = v[r];
+            const T nv = V::vmax(V::vmin3(l, dg, up), d[r]);
+            dg = l;
+            v[r] = nv;
+            up = nv;
+          }
+          upp = u;
+          bout = up;
+          if constexpr (AB::on) bmin = V::vmin(bmin, bout);
+          ob[t & 3] = bout;   // column c0 + s - 31 of the stripe's bottom row
+          if ((t & 3) == 3 && has_bottom && L == 31) store4<T>(outb + (s - 3), ob);
+  #pragma unroll
+          for (int c = 0; c < NPL; ++c) qr[c] = qn[c];
+
         }
-        const T tin = __shfl_sync(0xffffffffu, top_blk, s);
-        T u = __shfl_up_sync(0xffffffffu, bout, 1);
-        u = (L == 0) ? tin : u;
-        T up = u, dg = upp;
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-          const T l = v[r];
-          const T nv = V::vmax(V::vmin3(l, dg, up), d[r]);
-          dg = l;
-          v[r] = nv;
-          up = nv;
-        }
-        upp = u;
-        bout = up;
-        if constexpr (AB::on) bmin = V::vmin(bmin, bout);
-        if (has_bottom && L == 31) outb[s] = bout;   // column c0 + s - 31 of the stripe's bottom row
-#pragma unroll
-        for (int c = 0; c < NPL; ++c) qr[c] = qn[c];
       }
       __syncwarp();
       if (has_bottom) IO::bottom(io, buf, st, c0, L, m, outb);
