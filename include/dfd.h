@@ -147,9 +147,11 @@ dfd_status dfd_pair_host(dfd_context* ctx, dfd_dtype dtype, int dim, const void*
  *   offsets: int64[n_curves + 1], device, non-decreasing, offsets[0] = 0.
  *   pairs:   int32[2 * n_pairs] curve ids (a, b), device.
  *   out_dist / out_dist2: n_pairs elements each (types as for dfd_pair).
- * A pair's rows are its shorter curve, cut into stripes of 32*R rows
- * (R <= Rmax = 8 for dim <= 4, else 4), each a systolic array over the
- * columns.  Pairs are sorted by cost on the device (a counting sort, no host
+ * A pair's rows are the curve that needs fewer systolic steps (usually the
+ * shorter; delta is symmetric), cut into stripes of 32*R rows (R <= Rmax =
+ * 8 for dim <= 4, else 4), each a systolic array over the columns; of the
+ * two orientations the one whose columns fit one warp's row buffer is taken
+ * when only one does.  Pairs are sorted by cost on the device (a counting sort, no host
  * synchronisation) and taken by persistent CTAs and warps from atomic
  * counters, in two size classes (dfd_batch_set_team): pairs of several
  * stripes that are too wide for one warp's row buffer (4096 columns unless
@@ -303,7 +305,7 @@ dfd_status dfd_batch_set_order(dfd_context* ctx, dfd_dtype dtype, int dim, int o
  * Which pairs of a ragged batch run as CTA teams (no counterpart in the
  * paper, whose batches pad every curve to one length and give each lane one
  * curve, Sec. 4).  A team is the 8 warps of one CTA on one pair of several
- * stripes (more rows in its shorter curve than one warp holds): warp w runs
+ * stripes (more rows than one warp holds): warp w runs
  * stripes w, w + 8, ... as a pipeline over the columns, handing each
  * stripe's bottom row to the next through shared memory (and, from the last
  * warp back to the first, through the CTA's eight warp row buffers, 8 x the

@@ -254,7 +254,9 @@ extern "C" dfd_status dfd_batch_host(dfd_context* ctx, dfd_dtype dtype, int dim,
     }
     if (any_wide) {
       const int64_t na = offsets[ia + 1] - offsets[ia], nb = offsets[ib + 1] - offsets[ib];
-      if (std::min(na, nb) > stripe_rows) wide = std::max(wide, std::max(na, nb));
+      const bool sw = batch::plan_rows_from_b(na, nb, dim_class(dim), rmax_of(dim_class(dim)),
+                                              ctx->batch_buf_cols);   // the plan's orientation
+      if ((sw ? nb : na) > stripe_rows) wide = std::max(wide, sw ? na : nb);
     }
     const int64_t c = std::max(ia, ib);
     int k = 0;

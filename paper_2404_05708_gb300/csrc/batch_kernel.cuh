@@ -1,7 +1,8 @@
 // batch_kernel.cuh -- K4 (ragged batch) and K5 (all-pairs matrix).
 //
 // Many independent pairs: one warp per pair.  The rows of the recurrence of
-// Eq. 1 are the shorter curve (delta(p,q) = delta(q,p)), split into stripes
+// Eq. 1 are the curve that costs fewer steps (delta(p,q) = delta(q,p); see
+// orient_cost: usually the shorter one), split into stripes
 // of 32*R rows; lane L holds R consecutive rows in registers and the stripe
 // runs as a systolic array over the columns (lane L at step s updates column
 // s - L).  Rows past the curve's end repeat its last point (a repeated point
@@ -829,6 +830,43 @@ constexpr int NTB = 2 * NTB1;
 constexpr int NBUCKET = NTB + 2 * NBUCKET1;
 constexpr unsigned kNarrowBit = 1u << 30;   // worklist: pair index | narrow << 30 | swap << 31
 
+// Orientation of a pair (delta(p, q) = delta(q, p), bit for bit: the ground
+// distance is symmetric in every value class).  A warp spends about
+// stripes x (cols + 31) steps on a pair -- the 31 being the systolic ramp --
+// and a step costs a cell's instructions per row of a lane (5 for points of
+// up to 4 coordinates, 10 for 8, 18 for 16) and about eight more (the
+// shuffle from the lane above, the column record's load, lane 0's select,
+// the loop), measured on uniform int32 2-D batches (47.9 per step at R = 8,
+// 27.7 at R = 4).  The rows are the curve for which that estimate is lower,
+// with Rmax rows per lane whatever the launch's cap, so that the host can
+// repeat the choice: e.g. 100 x 500 2-D points run as two stripes of 8 rows
+// a lane over 131 steps each (12.6k instructions) rather than one stripe of
+// 4 rows over 531 steps (14.9k).  Ties keep rows = the shorter curve.
+__host__ __device__ __forceinline__ int rmax_of_class(int dk) { return dk <= 4 ? 8 : 4; }
+__host__ __device__ __forceinline__ long long orient_cost(int64_t rows, int64_t cols, int dk) {
+  const int rmax = rmax_of_class(dk);
+  const int cell = dk <= 4 ? 5 : dk <= 8 ? 10 : 18;
+  const int64_t st = (rows + 32 * rmax - 1) / (32 * rmax);
+  const int64_t r = rows <= 32 ? 1 : (rows + 32 * st - 1) / (32 * st);
+  return (long long)(st * (cols + 31)) * (cell * r + 8);
+}
+// Whether curve b supplies the rows of pair (a, b) (a has na points, b nb;
+// dk = the dimension class).
+__host__ __device__ __forceinline__ bool rows_from_b(int64_t na, int64_t nb, int dk) {
+  const long long ca = orient_cost(na, nb, dk), cb = orient_cost(nb, na, dk);
+  return cb < ca || (cb == ca && nb < na);
+}
+// The plan's choice: the cheaper orientation, unless only the other one
+// keeps a pair of several stripes (of 32 * rmax rows) within a warp's row
+// buffer (buf_cols columns).
+__host__ __device__ __forceinline__ bool plan_rows_from_b(int64_t na, int64_t nb, int dk, int rmax, int64_t buf_cols) {
+  const bool sw = rows_from_b(na, nb, dk);
+  const int64_t rows = sw ? nb : na, cols = sw ? na : nb;
+  const bool fits = rows <= 32 * (int64_t)rmax || cols <= buf_cols;
+  const bool fits_other = cols <= 32 * (int64_t)rmax || rows <= buf_cols;
+  return (!fits && fits_other) ? !sw : sw;
+}
+
 // Team bucket of a pair: floor(log2(rows * (cols + 31))) from 2^16 (15) up
 // to 2^31 and beyond (0), so the costliest team pairs start first.
 __device__ __forceinline__ int team_bucket(int64_t rows, int64_t cols) {
@@ -931,7 +969,8 @@ static __global__ void plan_hist_kernel(PlanArgs a) {
         const int64_t na = ea - oa, nb = eb - ob;
         if (na < 1 || nb < 1 || oa < 0 || ob < 0 || ea > total || eb > total || na > INT32_MAX || nb > INT32_MAX)
           raise_error(a.err, DFD_ERR_INVALID_ARG);
-        const int64_t rows = max(min(na, nb), (int64_t)1), cols = max(max(na, nb), (int64_t)1);
+        const bool sw = plan_rows_from_b(na, nb, a.dk, a.rmax, a.buf_cols);
+        const int64_t rows = max(sw ? nb : na, (int64_t)1), cols = max(sw ? na : nb, (int64_t)1);
         const bool narrow = a.bbox && narrow_pair(a.bbox, a.dk, ia, ib);
         const bool multi = rows > 32 * (int64_t)a.rmax;
         if (a.team && multi &&
@@ -994,7 +1033,7 @@ static __global__ void plan_scatter_kernel(PlanArgs a) {
     unsigned swap = 0;
     if (ia >= 0 && ib >= 0 && ia < a.n_curves && ib < a.n_curves) {
       const int64_t na = a.offsets[ia + 1] - a.offsets[ia], nb = a.offsets[ib + 1] - a.offsets[ib];
-      swap = na > nb ? 1u : 0u;   // rows = the shorter curve
+      swap = plan_rows_from_b(na, nb, a.dk, a.rmax, a.buf_cols) ? 1u : 0u;   // as in plan_hist_kernel
     }
     const unsigned narrow = (b < NTB ? b >= NTB1 : b - NTB >= NBUCKET1) ? kNarrowBit : 0u;
     a.worklist[pos] = (unsigned)k | narrow | (swap << 31);
@@ -1095,8 +1134,8 @@ __device__ __forceinline__ int team_pop_first(int* counter, unsigned* sm_rank, i
   return atomicAdd(counter, 1);
 }
 
-// One team pair (all 256 threads of the CTA call it): the rows of the
-// shorter curve in stripes over the 8 warps (TeamIO), the result written by
+// One team pair (all 256 threads of the CTA call it): the rows (the plan's
+// orientation) in stripes over the 8 warps (TeamIO), the result written by
 // the warp that runs the last stripe.  `gbuf` holds `gcols` values; a pair
 // with more stripes than warps needs m of them, else it is not run here and
 // false is returned (CTA-uniform).
@@ -1433,13 +1472,16 @@ __global__ void __launch_bounds__(256, kBlocksPerSM<DK>::value) matrix_kernel(Ma
       const bool ok = oi >= 0 && oj >= 0 && ei <= total && ej <= total && ei - oi <= INT32_MAX &&
                       ej - oj <= INT32_MAX;
       const int ni = ok ? (int)(ei - oi) : 0, nj = ok ? (int)(ej - oj) : 0;
-      const int rows = min(ni, nj), cols = max(ni, nj);
-      if (rows < 1) {
+      // the cheaper orientation, unless only the other one fits the row buffer
+      bool sw = rows_from_b(ni, nj, DK);
+      if (!fits_buffer<DK>(sw ? nj : ni, sw ? ni : nj) && fits_buffer<DK>(sw ? ni : nj, sw ? nj : ni)) sw = !sw;
+      const int rows = sw ? nj : ni, cols = sw ? ni : nj;
+      if (rows < 1 || cols < 1) {
         if (L == 0) raise_error(a.err, DFD_ERR_INVALID_ARG);
       } else if (fits_buffer<DK>(rows, cols)) {
         const int rm = fits_buffer<DK>(rows, cols, BUF_COLS, a.rmax) ? a.rmax : Rmax<DK>::value;
-        const int64_t ia = ni <= nj ? i : j, ib = ni <= nj ? j : i;
-        const int64_t oa = ni <= nj ? oi : oj, ob = ni <= nj ? oj : oi;
+        const int64_t ia = sw ? j : i, ib = sw ? i : j;
+        const int64_t oa = sw ? oj : oi, ob = sw ? oi : oj;
         bool narrow = false;
         if constexpr (std::is_same<V, I32>::value) narrow = a.bbox && narrow_pair(a.bbox, DK, ia, ib);
         if (narrow) {

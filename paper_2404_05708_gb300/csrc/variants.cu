@@ -3,7 +3,8 @@
 // Levenshtein distance (unit-cost edit distance), many pairs per launch.
 //
 // Same lane layout as the Frechet batch kernel (one warp per pair, rows =
-// the shorter sequence in stripes of 32*R, lane L at step s on column
+// the plan's orientation, usually the shorter sequence, in stripes of 32*R,
+// lane L at step s on column
 // s - L, stripes handing their bottom row through a per-warp buffer) and
 // the same device-built LPT work list; only the cell rule and the
 // boundaries differ:

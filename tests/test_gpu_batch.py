@@ -197,12 +197,14 @@ def test_batch_host_boxes_across_slices(dctx):
 
 @pytest.mark.parametrize("dtype", ["f32", "i32"])
 def test_batch_wide_pairs_row_buffer(dtype):
-    """Pairs that run several stripes (both curves longer than 256 points,
-    2-D) and whose longer curve is wider than one warp's row buffer (4096
-    columns by default) run as CTA teams, whose wrap-around row has the
-    CTA's eight warp buffers: with the default buffer every pair equals the
-    oracle and the error word stays clear; widened buffers (the pairs then
-    run one warp each) and dfd_batch_host give the same bits."""
+    """Pairs that run several stripes (2-D: more than 256 rows) with a row
+    wider than one warp's buffer (4096 columns by default) in both
+    orientations run as CTA teams, whose wrap-around row has the CTA's eight
+    warp buffers; the other long pairs take the long curve as their rows,
+    so that their columns fit (e.g. 300 x 5000, 4097 x 520).  With the
+    default buffer every pair equals the oracle and the error word stays
+    clear; widened buffers (the pairs then run one warp each) and
+    dfd_batch_host give the same bits."""
     from paper_2404_05708_gb300 import dfd
     ctx = dfd.Context(0)
     rng = np.random.default_rng(31)
@@ -214,8 +216,9 @@ def test_batch_wide_pairs_row_buffer(dtype):
         pts = np.cumsum(rng.integers(-64, 65, size=(int(off[-1]), 2)), axis=0).astype(np.int32)
     pairs = np.array([[0, 1], [1, 2], [3, 5], [4, 5], [6, 7], [6, 8], [8, 9], [2, 1], [7, 9]], np.int32)
     ln = lens[pairs]
-    wide = (ln.min(axis=1) > 256) & (ln.max(axis=1) > 4096)   # several stripes, a row wider than 4096
-    assert wide.sum() == 6 and (~wide).sum() == 3
+    long_ = (ln.min(axis=1) > 256) & (ln.max(axis=1) > 4096)   # several stripes, one curve wider than 4096
+    wide = ln.min(axis=1) > 4096                                # wider than 4096 both ways
+    assert long_.sum() == 6 and wide.sum() == 2
     b = workloads.Batch(points=pts, offsets=off, pairs=pairs)
     want, _ = oracle.batch(pts, off, pairs, mirror=(dtype == "f32"))
     code = dfd.DFD_F32 if dtype == "f32" else dfd.DFD_I32
@@ -245,13 +248,16 @@ def team_edges(dtype, dim, seed):
     beyond; one warp's row buffer holds 4096 columns, a CTA's 32,768):
     rows 255 / 256 (one stripe), 257 (two), 1024 (8 stripes of 128), 2047,
     2048 (8 of 256), 2049 and 2600 (cycling through the CTA buffer), against
-    columns 260 .. 40,000; 2049 x 33,000 and 2600 x 40,000 are wider than a
-    CTA's buffers and run last, on every buffer of the launch."""
+    columns 260 .. 40,000; 2049 x 33,000 and 2600 x 40,000 run with the long
+    curve as their rows (129 and 157 stripes of one warp), and 32,800 x
+    33,000 is wider than a CTA's buffers both ways: it runs last, on every
+    buffer of the launch."""
     rng = np.random.default_rng(seed)
     rows = [255, 256, 257, 1024, 2047, 2048, 2049, 2600]
     cols = [260, 1500, 4095, 4097, 9000]
     shapes = [(r, c) for r in rows for c in cols if c >= r] + [(2048, 2049), (2049, 2049), (2600, 2601),
-                                                                  (257, 32768), (2049, 33000), (2600, 40000)]
+                                                                  (257, 32768), (2049, 33000), (2600, 40000),
+                                                                  (32800, 33000)]
     lens, pairs = [], []
     for k, (r, c) in enumerate(shapes):
         a, bb = (r, c) if k % 2 == 0 else (c, r)   # both orders of (rows, cols)
@@ -292,10 +298,11 @@ def test_batch_team_modes_bit_identical(dctx, dtype, dim):
 
 def test_batch_team_16d_float(dctx):
     """16-D points (4 rows per lane, 128-column team rings): a team of 8
-    stripes of 128 rows, one cycling through 9 stripes, and one wide pair."""
+    stripes of 128 rows, one cycling through 9 stripes, and one pair wider
+    than a warp's row buffer both ways (4200 x 5000)."""
     from paper_2404_05708_gb300 import dfd
     rng = np.random.default_rng(160)
-    lens = np.array([1024, 1100, 1025, 1200, 300, 5000, 130, 700])
+    lens = np.array([1024, 1100, 1025, 1200, 4200, 5000, 130, 700])
     off = np.concatenate([[0], np.cumsum(lens)]).astype(np.int64)
     pts = np.cumsum(rng.normal(0, 1, size=(int(off[-1]), 16)), axis=0).astype(np.float32)
     pairs = np.array([[0, 1], [2, 3], [4, 5], [6, 7], [1, 2]], np.int32)
@@ -536,17 +543,18 @@ def test_matrix_full_size_sampled(dctx):
 
 def test_wide_pairs_outside_the_batch_get_nan_and_an_error(dctx):
     """The decider, the DTW / Levenshtein variants and the matrix run one warp
-    per pair with a 4096-column row buffer: a pair of several stripes whose
-    longer curve is wider gets NaN (float) / -1 (int64) outputs, never stale
-    memory, and DFD_ERR_UNSUPPORTED in the error word; the other pairs are
-    exact."""
+    per pair with a 4096-column row buffer: a pair of several stripes that is
+    wider than the buffer in both orientations gets NaN (float) / -1 (int64)
+    outputs, never stale memory, and DFD_ERR_UNSUPPORTED in the error word;
+    the other pairs are exact, among them 260 x 5000 points, which runs with
+    the long curve as its rows (its columns then fit)."""
     from paper_2404_05708_gb300 import dfd
     rng = np.random.default_rng(180)
-    lens = np.array([300, 5000, 100, 260])
+    lens = np.array([4200, 5000, 100, 260])
     off = np.concatenate([[0], np.cumsum(lens)]).astype(np.int64)
     pts = np.cumsum(rng.normal(0, 1, size=(int(off[-1]), 2)), axis=0).astype(np.float32)
-    pairs = np.array([[0, 1], [0, 2], [2, 3], [3, 1]], np.int32)   # 0 and 3 are wide
-    wide = np.array([True, False, False, True])
+    pairs = np.array([[0, 1], [0, 2], [2, 3], [3, 1]], np.int32)   # pair 0 is wide both ways
+    wide = np.array([True, False, False, False])
     P, O, Q = dev(pts), dev(off), dev(pairs)
     mirror, _ = oracle.batch(pts, off, pairs, mirror=True)
     unsupported = dfd.STATUS_CODE["DFD_ERR_UNSUPPORTED"]
@@ -582,6 +590,6 @@ def test_wide_pairs_outside_the_batch_get_nan_and_an_error(dctx):
     ii, jj = np.triu_indices(4, k=1)
     mat_pairs = np.stack([ii, jj], 1).astype(np.int32)
     mwant, _ = oracle.batch(pts, off, mat_pairs, mirror=True)
-    mwide = (np.minimum(lens[ii], lens[jj]) > 256) & (np.maximum(lens[ii], lens[jj]) > 4096)
+    mwide = np.minimum(lens[ii], lens[jj]) > 4096
     dm2 = dm2.cpu().numpy()
-    assert mwide.sum() == 2 and np.all(np.isnan(dm2[mwide])) and np.array_equal(dm2[~mwide], mwant[~mwide])
+    assert mwide.sum() == 1 and np.all(np.isnan(dm2[mwide])) and np.array_equal(dm2[~mwide], mwant[~mwide])
