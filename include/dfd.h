@@ -369,11 +369,13 @@ dfd_status dfd_batch_set_row_buffer(dfd_context* ctx, int cols);
  * host pointers; outputs may be NULL, not both): synchronous.  The points
  * are copied to the device in up to 8 slices of curves (about 64 MiB each)
  * on a copy stream, directly when they are page-locked and through the
- * context's pinned staging area otherwise; the pairs are grouped by the
- * slice of their later curve and each group runs as soon as its slice has
- * landed, so the copies overlap the computation (launches alternate between
- * two internal streams, so one launch's start overlaps the end of the one
- * before).  The device staging holds the points, the results and two batch
+ * context's pinned staging area otherwise (the offsets and pairs first,
+ * as given); one launch per slice takes, from the whole pair list, the
+ * pairs whose later curve lies in that slice (a filter in its device-side
+ * plan) as soon as the slice has landed, so the copies overlap the
+ * computation and results land at the pairs' own indices (launches
+ * alternate between two internal streams, so one launch's start overlaps
+ * the end of the one before).  The device staging holds the points, the results and two batch
  * scratch areas (grow-only, freed at destroy), whose row buffers are as wide
  * as the widest multi-stripe pair given (at least the context's width), so
  * any pair lengths run.  Results are bit-identical

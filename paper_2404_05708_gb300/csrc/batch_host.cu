@@ -3,16 +3,18 @@
 // curves on a copy stream while the batch engine runs the pairs whose
 // curves have arrived, then copies the distances back.
 //
-// The pairs are grouped by the slice of their later curve (a counting sort
-// on the host); slice k's group runs as one batch launch over curves
-// [0, end_k) as soon as slice k has landed, so the copy of slice k+1 overlaps
-// it.  Launches alternate between two streams, each with its own scratch
-// area, so a launch's bounding boxes, work list and first pairs start while
-// the one before finishes its longest pairs.  Each launch boxes and checks
-// only the curves no earlier launch covered (the int32 bounding boxes live
-// in one buffer for the whole batch, and a launch waits until the one before
-// has built its boxes), and the last launch waits for every slice and covers
-// all curves, so the input checks are those of dfd_batch.  Results are
+// The offsets and the pair list go first, as given; then the point slices.
+// Slice k's launch runs over curves [0, end_k) and takes from the whole pair
+// list the pairs whose later curve lies in slice k (its plan filters them:
+// no grouping on the host), as soon as slice k has landed, so the copy of
+// slice k+1 overlaps it, and every result lands at the caller's pair index.
+// Launches alternate between two streams, each with its own scratch area,
+// so a launch's bounding boxes, work list and first pairs start while the
+// one before finishes its longest pairs.  Each launch boxes and checks only
+// the curves no earlier launch covered (the int32 bounding boxes live in one
+// buffer for the whole batch, and a launch waits until the one before has
+// built its boxes), and the last launch waits for every slice and covers all
+// curves, so the input checks are those of dfd_batch.  Results are
 // bit-identical to dfd_batch on the same data: each pair is computed by the
 // same engine.
 #include <algorithm>
@@ -27,7 +29,8 @@ namespace dfd {
 #define DFD_RANGE_EXTERN(V, DK)                                                                                 \
   extern template dfd_status batch_launch_range<V, DK>(dfd_context*, int, const void*, const int64_t*, int64_t, \
                                                        const int32_t*, int64_t, void*, void*, cudaStream_t,     \
-                                                       int64_t, int*, char*, size_t, cudaEvent_t, int);         \
+                                                       int64_t, int*, char*, size_t, cudaEvent_t, int,          \
+                                                       const SliceFilter*);                                     \
   extern template size_t batch_scratch_bytes<V, DK>(dfd_context*, int64_t, int64_t, bool, int);
 DFD_RANGE_EXTERN(F32, 2)
 DFD_RANGE_EXTERN(F32, 3)
@@ -46,18 +49,19 @@ namespace {
 // Points per copy slice (about).  The first slice's copy is not overlapped,
 // and each launch adds its pre-pass and the tail of its longest pairs (half
 // hidden by the next launch on the other stream): on the 65,536-pair int32
-// batch (277 MB) slices of 128, 64, 48 and 32 MB ran at 1.94, 1.95, 1.92
-// and 1.84 Tcell/s end to end.
+// batch (279 MB) slices of 64 and 36 MB ran at 2.25 and 2.13 Tcell/s end to
+// end; a first and a last slice of 16 MB (8 MB) with three even ones between
+// ran at 2.13 (2.08).
 constexpr size_t kSliceBytes = (size_t)64 << 20;
 
 dfd_status range_run(dfd_context* ctx, dfd_dtype dtype, int dim, const void* points, const int64_t* offsets,
                      int64_t n_curves, const int32_t* pairs, int64_t n_pairs, void* out_dist, void* out_dist2,
                      cudaStream_t s, int64_t first, int* bbox, char* scratch, size_t scratch_bytes,
-                     cudaEvent_t prepared, int buf_cols) {
+                     cudaEvent_t prepared, int buf_cols, const SliceFilter* slice) {
 #define DFD_R_CASE(V, DK)                                                                                       \
   case DK:                                                                                                      \
     return batch_launch_range<V, DK>(ctx, dim, points, offsets, n_curves, pairs, n_pairs, out_dist, out_dist2, s, \
-                                     first, bbox, scratch, scratch_bytes, prepared, buf_cols);
+                                     first, bbox, scratch, scratch_bytes, prepared, buf_cols, slice);
 #define DFD_R_DK(V)                                                                                          \
   switch (dim_class(dim)) {                                                                                  \
     DFD_R_CASE(V, 2)                                                                                         \
@@ -140,15 +144,7 @@ extern "C" dfd_status dfd_batch_host(dfd_context* ctx, dfd_dtype dtype, int dim,
   if (st != DFD_OK) return st;
   if (!pairs || n_pairs < 0 || n_pairs > INT32_MAX) return DFD_ERR_INVALID_ARG;
   if (n_pairs == 0) return DFD_OK;
-  // host-side check the slicing relies on: monotone offsets (and the
-  // longest curve, which bounds the row buffers' width)
-  if (offsets[0] < 0) return DFD_ERR_INVALID_ARG;
-  int64_t len_max = 0;
-  for (int64_t c = 0; c < n_curves; ++c) {
-    const int64_t len = offsets[c + 1] - offsets[c];
-    if (len < 0) return DFD_ERR_INVALID_ARG;
-    len_max = std::max(len_max, len);
-  }
+  if (offsets[0] < 0 || offsets[n_curves] < 0) return DFD_ERR_INVALID_ARG;
   if ((st = set_device(ctx)) != DFD_OK) return st;
 
   const int64_t n_pts = offsets[n_curves];
@@ -166,8 +162,18 @@ extern "C" dfd_status dfd_batch_host(dfd_context* ctx, dfd_dtype dtype, int dim,
     bound[k] = std::lower_bound(offsets, offsets + n_curves + 1, target) - offsets;
     bound[k] = std::min(std::max(bound[k], bound[k - 1]), n_curves);
   }
+  // byte range of each slice's copy: the slice's curves when the offsets are
+  // valid (checked below, while the copies run), and in any case a partition
+  // of the caller's buffer, so no copy reads outside it
+  std::vector<size_t> cut(K + 1, pts_bytes);
+  cut[0] = 0;
+  for (int k = 1; k < K; ++k) {
+    const int64_t o = offsets[bound[k]];
+    const size_t b = o < 0 ? 0 : (size_t)o * dim * elem;
+    cut[k] = std::min(std::max(b, cut[k - 1]), pts_bytes);
+  }
 
-  // pinned staging: [offsets | pairs (grouped) | dist | dist2 | error word | points if pageable]
+  // pinned staging: [offsets | pairs | dist | dist2 | error word | points if pageable]
   const bool pts_locked = page_locked(points);
   const size_t off_b = align_up((size_t)(n_curves + 1) * 8, 256);
   const size_t pair_b = align_up((size_t)n_pairs * 8, 256);
@@ -177,7 +183,6 @@ extern "C" dfd_status dfd_batch_host(dfd_context* ctx, dfd_dtype dtype, int dim,
   char* h = static_cast<char*>(ctx->pinned);
   int* h_err = reinterpret_cast<int*>(h + off_b + pair_b + dist_b + dist2_b);
   char* h_pts = pts_locked ? nullptr : h + off_b + pair_b + dist_b + dist2_b + 256;
-  if (!pts_locked) std::memcpy(h_pts, points, pts_bytes);
   const char* src_pts = pts_locked ? static_cast<const char*>(points) : h_pts;
 
   // device (the context's staging buffer): [points | offsets | pairs | bbox | dist | dist2];
@@ -221,29 +226,49 @@ extern "C" dfd_status dfd_batch_host(dfd_context* ctx, dfd_dtype dtype, int dim,
   }
   cudaStream_t ls[2] = {s, ctx->launch_stream2};
 
-  // Every host-to-device copy goes through the copy stream, in the order
-  // the launches need it (copies in one direction are served in order):
-  // slice 0, then the offsets and the grouped pairs, then the other slices.
+  // 1. every host-to-device copy on the copy stream, in the order the
+  // launches need it (copies in one direction are served in order): point
+  // slice 0, the offsets and the pairs as given (1.5 MB for 65,536 pairs),
+  // then the other slices.  Nothing is regrouped on the host: each launch's
+  // plan picks its own pairs from the whole list, and results land at the
+  // caller's indices.
   cudaStream_t cs = ctx->copy_stream;
-  auto copy_slice = [&](int k) {
-    const size_t b0 = (size_t)(k == 0 ? 0 : offsets[bound[k]]) * dim * elem;
-    const size_t b1 = (size_t)(k + 1 == K ? n_pts : offsets[bound[k + 1]]) * dim * elem;
-    if (b1 > b0) cudaMemcpyAsync(d_pts + b0, src_pts + b0, b1 - b0, cudaMemcpyHostToDevice, cs);
-    cudaEventRecord(ctx->slice_ev[k], cs);
-  };
-  // 1. slice 0 first (after the previous work on s, which may still read
-  // the staging buffer's earlier contents)
-  cudaEventRecord(ctx->slice_ev[kMaxSlices], s);
+  cudaEventRecord(ctx->slice_ev[kMaxSlices], s);   // after the previous work on s (the staging areas)
   cudaStreamWaitEvent(cs, ctx->slice_ev[kMaxSlices], 0);
-  copy_slice(0);
+  for (int k = 0; k < K; ++k) {
+    const size_t b0 = cut[k], b1 = cut[k + 1];
+    if (b1 > b0) {
+      if (!pts_locked) std::memcpy(h_pts + b0, static_cast<const char*>(points) + b0, b1 - b0);
+      cudaMemcpyAsync(d_pts + b0, src_pts + b0, b1 - b0, cudaMemcpyHostToDevice, cs);
+    }
+    if (k == 0) {   // the offsets and pairs right after the first slice (host copies while it is in flight)
+      std::memcpy(h, offsets, (size_t)(n_curves + 1) * 8);
+      std::memcpy(h + off_b, pairs, (size_t)n_pairs * 8);
+      cudaMemcpyAsync(d_off, h, (size_t)(n_curves + 1) * 8, cudaMemcpyHostToDevice, cs);
+      cudaMemcpyAsync(d_pairs, h + off_b, (size_t)n_pairs * 8, cudaMemcpyHostToDevice, cs);
+    }
+    cudaEventRecord(ctx->slice_ev[k], cs);
+  }
 
-  // 2. on the host meanwhile: check the ids, group the pairs by the slice
-  // of their later curve (stable counting sort), and find the widest row
-  // a multi-stripe pair hands between its stripes (the row buffers)
-  std::unique_ptr<int[]> slice_of(new int[n_pairs]);   // (no zero fill: every entry is written)
-  std::vector<int64_t> start(K + 1, 0);
+  // 2. on the host meanwhile: check the offsets (nondecreasing; the longest
+  // curve bounds the row buffers' width) and the ids, and find the widest
+  // row a multi-stripe pair hands between its stripes (the row buffers)
+  int64_t len_max = 0;
+  bool bad = false;
+  for (int64_t c = 0; c < n_curves; ++c) {
+    const int64_t len = offsets[c + 1] - offsets[c];
+    bad |= len < 0;
+    len_max = std::max(len_max, len);
+  }
+  if (bad) {
+    // the copies read the caller's buffers: let them finish before returning
+    cudaStreamSynchronize(cs);
+    cudaGetLastError();
+    return DFD_ERR_INVALID_ARG;
+  }
   bool bad_id = false;
-  const int64_t stripe_rows = 32 * (int64_t)rmax_of(dim_class(dim));
+  const int dk = dim_class(dim);
+  const int64_t stripe_rows = 32 * (int64_t)rmax_of(dk);
   const bool any_wide = len_max > ctx->batch_buf_cols;   // else no pair can outgrow the buffers
   int64_t wide = 0;
   for (int64_t i = 0; i < n_pairs; ++i) {
@@ -254,23 +279,16 @@ extern "C" dfd_status dfd_batch_host(dfd_context* ctx, dfd_dtype dtype, int dim,
     }
     if (any_wide) {
       const int64_t na = offsets[ia + 1] - offsets[ia], nb = offsets[ib + 1] - offsets[ib];
-      const bool sw = batch::plan_rows_from_b(na, nb, dim_class(dim), rmax_of(dim_class(dim)),
-                                              ctx->batch_buf_cols);   // the plan's orientation
+      const bool sw = batch::plan_rows_from_b(na, nb, dk, rmax_of(dk), ctx->batch_buf_cols);   // the plan's orientation
       if ((sw ? nb : na) > stripe_rows) wide = std::max(wide, sw ? na : nb);
     }
-    const int64_t c = std::max(ia, ib);
-    int k = 0;
-    while (k + 1 < K && c >= bound[k + 1]) ++k;
-    slice_of[i] = k;
-    ++start[k + 1];
   }
   if (bad_id) {
-    // the copy reads the caller's buffer: let it finish before returning
+    // the copies read the caller's buffers: let them finish before returning
     cudaStreamSynchronize(cs);
     cudaGetLastError();
     return DFD_ERR_INVALID_ARG;
   }
-  for (int k = 0; k < K; ++k) start[k + 1] += start[k];
   // row buffers as wide as the widest such pair needs (at least the context's width)
   const int buf_cols =
       (int)std::min<int64_t>(1 << 28, std::max<int64_t>(ctx->batch_buf_cols, (wide + 31) / 32 * 32));
@@ -279,52 +297,28 @@ extern "C" dfd_status dfd_batch_host(dfd_context* ctx, dfd_dtype dtype, int dim,
   if (st == DFD_OK && scr_b == 0) st = DFD_ERR_UNSUPPORTED;
   if (st == DFD_OK) st = ensure_host_scratch(ctx, 2 * scr_b);
   if (st != DFD_OK) {
-    cudaStreamSynchronize(cs);   // the copy reads the caller's buffer
+    cudaStreamSynchronize(cs);   // the copies read the caller's buffers
     cudaGetLastError();
     return st;
   }
   char* d_scr[2] = {static_cast<char*>(ctx->host_scr), static_cast<char*>(ctx->host_scr) + scr_b};
-  std::memcpy(h, offsets, (size_t)(n_curves + 1) * 8);
-  int32_t* hp = reinterpret_cast<int32_t*>(h + off_b);
-  std::unique_ptr<int32_t[]> perm(new int32_t[n_pairs]);   // grouped position -> caller's pair index
-  {
-    std::vector<int64_t> cur(start.begin(), start.end() - 1);
-    for (int64_t i = 0; i < n_pairs; ++i) {
-      const int64_t pos = cur[slice_of[i]]++;
-      perm[pos] = (int32_t)i;
-      hp[2 * pos] = pairs[2 * i];
-      hp[2 * pos + 1] = pairs[2 * i + 1];
-    }
-  }
 
-  // 3. the offsets and pairs, then the other slices; each slice's pairs run
-  // as soon as the slice has landed (slice k's event follows the offsets
-  // and pairs for k >= 1; slice 0's launch also waits for them)
-  cudaMemcpyAsync(d_off, h, (size_t)(n_curves + 1) * 8, cudaMemcpyHostToDevice, cs);
-  cudaMemcpyAsync(d_pairs, hp, (size_t)n_pairs * 8, cudaMemcpyHostToDevice, cs);
-  cudaEventRecord(ctx->slice_ev[kMaxSlices], cs);
-  cudaStreamWaitEvent(s, ctx->slice_ev[kMaxSlices], 0);
-  cudaStreamWaitEvent(ls[1], ctx->slice_ev[kMaxSlices], 0);
-  for (int k = 1; k < K; ++k) copy_slice(k);
-  int last = 0;   // the last slice with pairs: it waits for every slice and covers all curves
-  for (int k = 0; k < K; ++k)
-    if (start[k + 1] > start[k]) last = k;
+  // 3. one launch per slice, over the whole pair list: slice k's launch
+  // takes the pairs whose later curve lies in slice k, as soon as the slice
+  // has landed; the last launch waits for every slice, covers all curves and
+  // also takes any pair with an id out of range (its plan reports it).
   int64_t covered = 0;   // curves boxed / checked so far
-  int li = 0;            // launches issued: launch li runs on ls[li & 1] with scratch d_scr[li & 1]
-  for (int k = 0; k <= last && st == DFD_OK; ++k) {
-    const int64_t cnt = start[k + 1] - start[k];
-    if (cnt == 0) continue;
-    const bool final_launch = k == last;
-    cudaStream_t sk = ls[li & 1];
-    for (int j = (final_launch ? 0 : k); j <= (final_launch ? K - 1 : k); ++j)
-      cudaStreamWaitEvent(sk, ctx->slice_ev[j], 0);
-    if (li > 0) cudaStreamWaitEvent(sk, ctx->prep_ev[(li - 1) & 1], 0);   // boxes of the earlier curves
+  for (int k = 0; k < K && st == DFD_OK; ++k) {
+    const bool final_launch = k + 1 == K;
+    cudaStream_t sk = ls[k & 1];
+    for (int j = (final_launch ? 0 : k); j <= k; ++j) cudaStreamWaitEvent(sk, ctx->slice_ev[j], 0);
+    if (k > 0) cudaStreamWaitEvent(sk, ctx->prep_ev[(k - 1) & 1], 0);   // boxes of the earlier curves
     const int64_t upto = final_launch ? n_curves : bound[k + 1];
-    st = range_run(ctx, dtype, dim, d_pts, d_off, upto, d_pairs + 2 * start[k], cnt,
-                   out_dist ? d_dist + start[k] * d1 : nullptr, out_dist2 ? d_dist2 + start[k] * d2 : nullptr, sk,
-                   covered, d_bbox, d_scr[li & 1], scr_b, ctx->prep_ev[li & 1], buf_cols);
+    const SliceFilter filt{n_curves, bound[k], upto, final_launch};
+    st = range_run(ctx, dtype, dim, d_pts, d_off, upto, d_pairs, n_pairs, out_dist ? d_dist : nullptr,
+                   out_dist2 ? d_dist2 : nullptr, sk, covered, d_bbox, d_scr[k & 1], scr_b, ctx->prep_ev[k & 1],
+                   buf_cols, &filt);
     covered = upto;
-    ++li;
   }
   cudaEventRecord(ctx->join_ev, ls[1]);
   cudaStreamWaitEvent(s, ctx->join_ev, 0);
@@ -347,31 +341,8 @@ extern "C" dfd_status dfd_batch_host(dfd_context* ctx, dfd_dtype dtype, int dim,
     cudaMemset(ctx->d_err, 0, sizeof(int));
     return (dfd_status)*h_err;
   }
-  // 4. results back in the caller's pair order
-  const char* r1 = h + off_b + pair_b;
-  const char* r2 = r1 + dist_b;
-  if (f32) {
-    if (out_dist) {
-      const float* a = reinterpret_cast<const float*>(r1);
-      float* o = static_cast<float*>(out_dist);
-      for (int64_t pos = 0; pos < n_pairs; ++pos) o[perm[pos]] = a[pos];
-    }
-    if (out_dist2) {
-      const float* a = reinterpret_cast<const float*>(r2);
-      float* o = static_cast<float*>(out_dist2);
-      for (int64_t pos = 0; pos < n_pairs; ++pos) o[perm[pos]] = a[pos];
-    }
-  } else {
-    if (out_dist) {
-      const double* a = reinterpret_cast<const double*>(r1);
-      double* o = static_cast<double*>(out_dist);
-      for (int64_t pos = 0; pos < n_pairs; ++pos) o[perm[pos]] = a[pos];
-    }
-    if (out_dist2) {
-      const long long* a = reinterpret_cast<const long long*>(r2);
-      long long* o = static_cast<long long*>(out_dist2);
-      for (int64_t pos = 0; pos < n_pairs; ++pos) o[perm[pos]] = a[pos];
-    }
-  }
+  // 4. results, already in the caller's pair order
+  if (out_dist) std::memcpy(out_dist, h + off_b + pair_b, (size_t)n_pairs * d1);
+  if (out_dist2) std::memcpy(out_dist2, h + off_b + pair_b + dist_b, (size_t)n_pairs * d2);
   return DFD_OK;
 }

@@ -943,7 +943,16 @@ struct PlanArgs {
   int dk;              // coordinates per bbox entry
   int* err;
   int rmax;            // rows per lane of one stripe for this dimension class
+  // Pairs this launch takes (a host-buffer call runs one launch per copy
+  // slice over the whole pair list): those whose later curve id lies in
+  // [lo_curve, hi_curve), and the pairs with an id outside [0, n_ids) when
+  // take_invalid is set (they only raise DFD_ERR_INVALID_ARG).  The others
+  // get bucket kNoBucket and no work-list slot.
+  int64_t n_ids;
+  int64_t lo_curve, hi_curve;
+  int take_invalid;
 };
+constexpr unsigned short kNoBucket = 0xFFFF;
 
 // The counting sort's atomics are aggregated per warp: the lanes of a warp
 // that fall in one bucket add their count with one atomic (hist) or take
@@ -958,7 +967,14 @@ static __global__ void plan_hist_kernel(PlanArgs a) {
   for (int64_t k0 = 32 * w0; k0 < a.n_pairs; k0 += 32 * wstride) {
     const int64_t k = k0 + L;
     int b = -1;
+    bool mine = false;
     if (k < a.n_pairs) {
+      const int32_t ia = a.pairs[2 * k], ib = a.pairs[2 * k + 1];
+      const bool valid_id = ia >= 0 && ib >= 0 && ia < a.n_ids && ib < a.n_ids;
+      const int64_t c = max(ia, ib);
+      mine = valid_id ? (c >= a.lo_curve && c < a.hi_curve) : a.take_invalid != 0;
+    }
+    if (mine) {
       const int32_t ia = a.pairs[2 * k], ib = a.pairs[2 * k + 1];
       b = NTB + NBUCKET1 - 1;   // invalid pairs: last of the int64 warp class (skipped by the kernel)
       if (ia < 0 || ib < 0 || ia >= a.n_curves || ib >= a.n_curves) {
@@ -982,6 +998,8 @@ static __global__ void plan_hist_kernel(PlanArgs a) {
         }
       }
       a.bucket[k] = (unsigned short)b;
+    } else if (k < a.n_pairs) {
+      a.bucket[k] = kNoBucket;
     }
     const unsigned peers = __match_any_sync(0xffffffffu, b);
     if (b >= 0 && L == __ffs(peers) - 1) atomicAdd(&a.hist[b], (unsigned)__popc(peers));
@@ -1022,7 +1040,7 @@ static __global__ void plan_scatter_kernel(PlanArgs a) {
   const int64_t wstride = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t k0 = 32 * w0; k0 < a.n_pairs; k0 += 32 * wstride) {
     const int64_t k = k0 + L;
-    const int b = k < a.n_pairs ? (int)a.bucket[k] : -1;
+    const int b = k < a.n_pairs && a.bucket[k] != kNoBucket ? (int)a.bucket[k] : -1;
     const unsigned peers = __match_any_sync(0xffffffffu, b);
     const int leader = __ffs(peers) - 1;
     unsigned pos = 0;
@@ -1051,6 +1069,7 @@ struct BatchArgs {
   const int32_t* pairs;
   const unsigned* worklist;
   int64_t n_items;
+  const unsigned* n_items_dev;   // batch kernel: items of the work list, written by the plan (null: n_items)
   int64_t n_curves;
   int dim;
   int vec;             // 1: vector point loads allowed (dim == DK, 16-byte aligned points)
@@ -1243,7 +1262,8 @@ __global__ void __launch_bounds__(256, kBlocksPerSM<DK>::value) batch_kernel(Bat
   }
 
   // 2. warp items
-  const long long n_warp = a.n_items - n_team;
+  const long long n_items = a.n_items_dev ? (long long)*a.n_items_dev : a.n_items;
+  const long long n_warp = n_items - n_team;
   for (bool first = true;; first = false) {
     int item = 0;
     if (L == 0) item = first ? pop_first(a.counter, a.sm_rank, a.n_sm, n_warp) : atomicAdd(a.counter, 1);

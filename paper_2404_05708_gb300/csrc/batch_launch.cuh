@@ -105,12 +105,20 @@ BatchLayout batch_layout(int64_t n_curves, int64_t n_pairs, int blocks, bool bbo
 // With `scratch_ext` the launch uses the caller's scratch area (at least
 // batch_scratch_bytes) instead of the context's, so launches on different
 // streams can run side by side.  `buf_cols`: row buffer columns per warp.
+// The pairs one launch of a host-buffer batch takes (PlanArgs): later
+// curve id in [lo, hi), and those with an id outside [0, n_ids) when
+// take_invalid is set.
+struct SliceFilter {
+  int64_t n_ids, lo, hi;
+  bool take_invalid;
+};
+
 template <class V, int DK>
 dfd_status batch_prepare(dfd_context* ctx, int dim, const void* points, const int64_t* offsets, int64_t n_curves,
                          const int32_t* pairs, int64_t n_pairs, cudaStream_t s, int blocks, batch::BatchArgs* ba,
                          int64_t first_curve = 0, int* bbox_ext = nullptr, char* scratch_ext = nullptr,
                          size_t scratch_ext_bytes = 0, int buf_cols = batch::BUF_COLS, int team = 0,
-                         int rmax = batch::Rmax<DK>::value) {
+                         int rmax = batch::Rmax<DK>::value, const SliceFilter* slice = nullptr) {
   constexpr bool kInt = std::is_same<V, I32>::value;
   if (n_pairs >= (int64_t)batch::kNarrowBit) return DFD_ERR_UNSUPPORTED;
   const BatchLayout lay = batch_layout<V, DK>(n_curves, n_pairs, blocks, bbox_ext != nullptr, buf_cols);
@@ -151,6 +159,10 @@ dfd_status batch_prepare(dfd_context* ctx, int dim, const void* points, const in
   pa.team = team;
   pa.buf_cols = buf_cols;
   pa.ctas = blocks;
+  pa.n_ids = slice ? slice->n_ids : n_curves;
+  pa.lo_curve = slice ? slice->lo : 0;
+  pa.hi_curve = slice ? slice->hi : n_curves;
+  pa.take_invalid = slice ? (int)slice->take_invalid : 1;
   const int pblocks = (int)std::min<int64_t>((n_pairs + 255) / 256, 8 * (int64_t)ctx->num_sms);
   batch::plan_hist_kernel<<<pblocks, 256, 0, s>>>(pa);
   batch::plan_scan_kernel<<<1, batch::NBUCKET, 0, s>>>(pa);
@@ -164,6 +176,8 @@ dfd_status batch_prepare(dfd_context* ctx, int dim, const void* points, const in
   ba->pairs = pairs;
   ba->worklist = pa.worklist;
   ba->n_items = n_pairs;
+  // a filtered launch's items: the end of the last bucket after the scatter
+  ba->n_items_dev = slice ? pa.cursor + (batch::NBUCKET - 1) : nullptr;
   ba->n_curves = n_curves;
   ba->dim = dim;
   ba->vec = vector_loads_ok<DK>(points, dim);
@@ -229,7 +243,8 @@ template <class V, int DK>
 dfd_status batch_launch_range(dfd_context* ctx, int dim, const void* points, const int64_t* offsets,
                               int64_t n_curves, const int32_t* pairs, int64_t n_pairs, void* out_dist,
                               void* out_dist2, cudaStream_t s, int64_t first_curve, int* bbox_ext,
-                              char* scratch_ext, size_t scratch_ext_bytes, cudaEvent_t prepared, int buf_cols) {
+                              char* scratch_ext, size_t scratch_ext_bytes, cudaEvent_t prepared, int buf_cols,
+                              const SliceFilter* slice = nullptr) {
   const TileShape ts = tile_shape<DK>(ctx, batch::batch_kernel<V, DK>, ctx->batch_rmax, ctx->batch_cpsm,
                                       std::is_same<V, F32>::value);
   const int blocks = ts.blocks;
@@ -237,7 +252,7 @@ dfd_status batch_launch_range(dfd_context* ctx, int dim, const void* points, con
   const int team = batch_team_mode(ctx, std::is_same<V, F32>::value, DK);
   dfd_status st = batch_prepare<V, DK>(ctx, dim, points, offsets, n_curves, pairs, n_pairs, s, blocks, &ba,
                                        first_curve, bbox_ext, scratch_ext, scratch_ext_bytes, buf_cols, team,
-                                       ts.rmax);
+                                       ts.rmax, slice);
   if (st != DFD_OK) return st;
   if (prepared) cudaEventRecord(prepared, s);
   ba.out_dist = out_dist;
@@ -328,7 +343,8 @@ dfd_status matrix_launch(dfd_context* ctx, int dim, const void* points, const in
                                                       const int32_t*, int64_t, void*, void*, cudaStream_t);        \
   template dfd_status dfd::batch_launch_range<dfd::V, DK>(dfd_context*, int, const void*, const int64_t*, int64_t, \
                                                             const int32_t*, int64_t, void*, void*, cudaStream_t,      \
-                                                            int64_t, int*, char*, size_t, cudaEvent_t, int);          \
+                                                            int64_t, int*, char*, size_t, cudaEvent_t, int,           \
+                                                            const dfd::SliceFilter*);                                 \
   template size_t dfd::batch_scratch_bytes<dfd::V, DK>(dfd_context*, int64_t, int64_t, bool, int);                  \
   template dfd_status dfd::decide_launch<dfd::V, DK>(dfd_context*, int, const void*, const int64_t*, int64_t,      \
                                                        const int32_t*, int64_t, const void*, double, void*, int32_t*, \
