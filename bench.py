@@ -69,6 +69,10 @@ TRAFFIC_BY_KERNEL_SHA: dict = {
     # 32,768-pair batch (139.0 MB of inputs), scaled by the inputs (the points are read once) to the
     # 65,536-pair batch's 278.6 MB
     "46c1e1b19151a973": 295400000,
+    # the same after the grouped staging loads / stores, the cost-based orientation and the
+    # slice filter of the plan: 145.60 MB per launch on the 32,768-pair batch (138.2 MB of
+    # points), scaled by the points to the 65,536-pair batch's 277.0 MB
+    "cb7f3699e1ec87c1": 291797623,
 }
 
 

@@ -11,6 +11,7 @@ loading and scratch growth happen first), synchronises, then runs it
   wave      dfd_pair (wave_kernel), 2000 x 1500 2-D float32 walks
   wave3d    dfd_pair (wave_kernel), 20,000 x 20,000 3-D float32 warped walk
   batch     dfd_batch (batch_kernel), 32,768 ragged int32 2-D pairs, lengths U{16..512}
+  uniform   dfd_batch (batch_kernel), 32,768 int32 2-D pairs of --n x --m points (instruction mix per step)
   team      dfd_batch (batch_kernel, CTA teams), 32 pairs of 1,024-point 2-D walks
   decide    dfd_batch_decide (decide_kernel), 16,384 ragged int32 2-D pairs
   lev       Levenshtein (variant_kernel<LevOp>), 16,384 pairs of symbols over {0..3}
@@ -40,6 +41,8 @@ def main(argv=None) -> int:
     ap = argparse.ArgumentParser()
     ap.add_argument("case")
     ap.add_argument("--reps", type=int, default=1)
+    ap.add_argument("--n", type=int, default=256, help="uniform: points of each pair's first curve")
+    ap.add_argument("--m", type=int, default=256, help="uniform: points of each pair's second curve")
     a = ap.parse_args(argv)
     import torch
     from paper_2404_05708_gb300 import build, dfd, workloads
@@ -65,6 +68,13 @@ def main(argv=None) -> int:
             fn = lambda: ctx.batch(PT, O, PR)   # noqa: E731
         else:
             fn = lambda: ctx.decide(PT, O, PR, 2.0e7)   # noqa: E731
+    elif case == "uniform":
+        lens = np.tile(np.array([a.n, a.m], dtype=np.int64), 32768)
+        off = np.concatenate([[0], np.cumsum(lens)]).astype(np.int64)
+        pts = np.cumsum(rng.integers(-64, 65, size=(int(off[-1]), 2)), axis=0).astype(np.int32)
+        pairs = np.arange(2 * 32768, dtype=np.int32).reshape(-1, 2)
+        PT, O, PR = dev(pts), dev(off), dev(pairs)
+        fn = lambda: ctx.batch(PT, O, PR)   # noqa: E731
     elif case == "team":
         b = workloads.paper_walks(32, 1024)
         PT, O, PR = dev(b.points), dev(b.offsets), dev(b.pairs)
