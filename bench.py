@@ -185,7 +185,7 @@ class LongPair:
     """One long 3-D float32 pair through dfd_pair (band wavefront)."""
     micro_op = "cell_f32_d3"
     dtype = "f32"
-    launches_per_step = 4          # input check, q packing, wavefront, combine (two fronts; set per shape below)
+    launches_per_step = 3          # prep (check + q packing), wavefront, combine (set per shape below)
 
     def __init__(self, args, ctx, dfd, torch, workloads, rank, world):
         self.n, self.m = args.n, args.m
@@ -213,9 +213,11 @@ class LongPair:
                        "launch_shape": {"rows_per_lane": shape[0], "warps": shape[1], "ctas": shape[2],
                                         "autotuned": tuned},
                        "kernel_sha": kernel_sha()}
-        # two fronts (a pair of two bands or more): a combine kernel after the wavefront
+        # prep kernel + wavefront; two fronts (a pair of two bands or more) on a
+        # row of more than 65,536 columns add a combine kernel (shorter rows are
+        # met by the wavefront's last CTA)
         bands = -(-self.n // (32 * shape[0] * shape[1]))
-        self.launches_per_step = 4 if bands >= 2 else 3
+        self.launches_per_step = 3 if bands >= 2 and self.m > 65536 else 2
         self.config["fronts"] = 2 if bands >= 2 else 1
         self.h2d = (self.n + self.m) * DIM * 4
         self.d2h = 16
@@ -258,7 +260,8 @@ class LongPair:
 
 class Pair2k(LongPair):
     """One 2000 x 1500 2-D float32 pair (Gaussian walks)."""
-    micro_op = "cell_f32_d3"
+    micro_op = "cell_f32_d2"
+    launches_per_step = 2          # prep (check + q packing), wavefront (its last CTA meets the two fronts)
 
     def __init__(self, args, ctx, dfd, torch, workloads, rank, world):
         self.n, self.m = 2000, 1500

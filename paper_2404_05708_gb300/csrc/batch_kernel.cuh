@@ -143,37 +143,43 @@ __device__ __forceinline__ int pop_first(int* counter, unsigned* sm_rank, int n_
   return atomicAdd(counter, 1);
 }
 
-// Progress words of a team (shared memory, CTA scope): release store by
-// the producer's lane 0 after its lanes' stores, acquire load by the
-// consumer's lane 0 before its lanes' loads.
-__device__ __forceinline__ unsigned long long ld_acquire_cta_u64(const unsigned long long* p) {
-  unsigned long long v;
-  asm volatile("ld.acquire.cta.shared::cta.u64 %0, [%1];" : "=l"(v) : "r"(smem_addr(p)) : "memory");
-  return v;
-}
-__device__ __forceinline__ void st_release_cta_u64(unsigned long long* p, unsigned long long v) {
-  asm volatile("st.release.cta.shared::cta.u64 [%0], %1;" ::"r"(smem_addr(p)), "l"(v) : "memory");
-}
+// Progress words of a team (shared memory, CTA scope): the producer's lane
+// 0 publishes after its lanes' stores (__syncwarp, then a fence and a
+// relaxed store: a release), the consumer's lane 0 polls relaxed and fences
+// once the value is there (an acquire) before its lanes' loads.
 // Bounded wait until *p >= need: by the timer and by a count of polls that
 // holds even if the timer does not advance; gives up at once when the
 // error word is set.  On expiry it records DFD_ERR_TIMEOUT and returns, and
 // the team goes on without waiting (its results are then not to be used:
 // the error word says so).
 constexpr long long kTeamPolls = 1LL << 26;
+__device__ __forceinline__ unsigned long long ld_relaxed_cta_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.cta.shared::cta.u64 %0, [%1];" : "=l"(v) : "r"(smem_addr(p)) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_relaxed_cta_u64(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.relaxed.cta.shared::cta.u64 [%0], %1;" ::"r"(smem_addr(p)), "l"(v) : "memory");
+}
+__device__ __forceinline__ void fence_acq_rel_cta_team() { asm volatile("fence.acq_rel.cta;" ::: "memory"); }
+// Relaxed polls, then one fence: with the producer's fence before its
+// relaxed store, an acquire of what it published.
 __device__ __forceinline__ void team_wait(const unsigned long long* p, unsigned long long need, int* err,
                                           unsigned long long timeout_ns) {
-  if (ld_acquire_cta_u64(p) >= need) return;
-  const unsigned long long t0 = globaltimer_ns();
-  for (long long it = 1;; ++it) {
-    if (ld_acquire_cta_u64(p) >= need) return;
-    if ((it & 255) == 0) {
-      if (ld_relaxed_i32(err) != 0) return;
-      if (it >= kTeamPolls || globaltimer_ns() - t0 > timeout_ns) {
-        raise_error(err, DFD_ERR_TIMEOUT);
-        return;
+  if (ld_relaxed_cta_u64(p) < need) {
+    const unsigned long long t0 = globaltimer_ns();
+    for (long long it = 1;; ++it) {
+      if (ld_relaxed_cta_u64(p) >= need) break;
+      if ((it & 255) == 0) {
+        if (ld_relaxed_i32(err) != 0) break;
+        if (it >= kTeamPolls || globaltimer_ns() - t0 > timeout_ns) {
+          raise_error(err, DFD_ERR_TIMEOUT);
+          break;
+        }
       }
     }
   }
+  fence_acq_rel_cta_team();
 }
 
 // Eight values of a warp's staging area into registers (16-byte loads), and
@@ -331,6 +337,7 @@ struct SoloIO {
     const int oc = c0 + L - 31;
     if (oc >= 0 && oc < m) buf[oc] = outb[L];
   }
+  __device__ __forceinline__ static void end_block(SoloIO*, int, int, int, int, bool, bool) {}
 };
 
 // Team of the CTA's warps on one pair: warp w runs stripes w, w + nw,
@@ -372,9 +379,7 @@ struct TeamIO {
                     ? static_cast<const T*>(io->gbuf)[c]
                     : reinterpret_cast<const T*>(static_cast<const unsigned long long*>(io->ring) +
                                                  wp * RING)[(kp * (unsigned long long)m + c) & (RING - 1)];
-    __syncwarp();
-    if (L == 0) st_release_cta_u64(&io->cons[io->w], (unsigned long long)(st / io->nw) * m + need);
-    return v;
+    return v;   // the read is published (cons) with the block's output, in end_block
   }
   template <class T>
   __device__ __forceinline__ static void bottom(TeamIO* io, T*, int st, int c0, int L, int m, const T* outb) {
@@ -392,8 +397,23 @@ struct TeamIO {
         reinterpret_cast<T*>(static_cast<unsigned long long*>(io->ring) +
                              io->w * RING)[(k * (unsigned long long)m + oc) & (RING - 1)] = outb[L];
     }
+  }
+  // After each block: one release for both progress words -- the block's
+  // bottom row (columns 0 .. c0 of stripe st) and the top row it read
+  // (columns up to c0 + 31).  A fence, then relaxed stores, where a release
+  // store per word took two fences; holding the read back to here delays the
+  // producer's flow control by one block, well within the ring (the producer
+  // waits for positions RING behind its own, the consumer trails it by about
+  // two blocks).
+  __device__ __forceinline__ static void end_block(TeamIO* io, int st, int c0, int L, int m, bool has_top,
+                                                   bool has_bottom) {
     __syncwarp();
-    if (L == 0) st_release_cta_u64(&io->prog[io->w], k * m + min(c0 + 1, m));   // columns 0 .. c0
+    if (L == 0) {
+      fence_acq_rel_cta_team();
+      const unsigned long long k = (unsigned long long)(st / io->nw);
+      if (has_bottom) st_relaxed_cta_u64(&io->prog[io->w], k * m + min(c0 + 1, m));
+      if (has_top) st_relaxed_cta_u64(&io->cons[io->w], k * m + min(c0 + 32, m));
+    }
   }
 };
 
@@ -607,6 +627,7 @@ __device__ __forceinline__ typename V::value warp_dfd(const typename V::coord* _
       }
       __syncwarp();
       if (has_bottom) IO::bottom(io, buf, st, c0, L, m, outb);
+      IO::end_block(io, st, c0, L, m, has_top, has_bottom);
       if constexpr (AB::on) {
         if (c0 + 31 <= m - 1) {
           T cut = upp;

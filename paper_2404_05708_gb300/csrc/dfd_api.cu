@@ -14,11 +14,11 @@ namespace dfd {
 // ------------------------------------------------------------ declarations
 template <class V, int DK, int R>
 dfd_status wave_launch(dfd_context* ctx, int dim, const void* p, int64_t n, const void* q, int64_t m,
-                       void* out_dist, void* out_dist2, cudaStream_t s, int W, int ctas);
+                       void* out_dist, void* out_dist2, cudaStream_t s, int W, int ctas, bool check);
 
 #define DFD_WAVE_EXTERN(V, DK, R)                                                                              \
   extern template dfd_status wave_launch<V, DK, R>(dfd_context*, int, const void*, int64_t, const void*, int64_t, \
-                                                   void*, void*, cudaStream_t, int, int);
+                                                   void*, void*, cudaStream_t, int, int, bool);
 #define DFD_WAVE_EXTERN_R(V, DK) \
   DFD_WAVE_EXTERN(V, DK, 2) DFD_WAVE_EXTERN(V, DK, 4) DFD_WAVE_EXTERN(V, DK, 6) DFD_WAVE_EXTERN(V, DK, 8)
 DFD_WAVE_EXTERN_R(F32, 2)
@@ -228,15 +228,15 @@ dfd_status wave_plan(const dfd_context* ctx, dfd_dtype dtype, int dim, int64_t n
 }
 
 dfd_status wave_run(dfd_context* ctx, dfd_dtype dtype, int dim, const void* p, int64_t n, const void* q, int64_t m,
-                    void* out_dist, void* out_dist2, cudaStream_t s, const WaveShape& sh) {
+                    void* out_dist, void* out_dist2, cudaStream_t s, const WaveShape& sh, bool check) {
   if (!shape_ok(ctx, dtype, dim, sh.R, sh.W)) return DFD_ERR_UNSUPPORTED;
   const int dk = dim_class(dim);
 #define DFD_W_R(V, DK)                                                                       \
   switch (sh.R) {                                                                            \
-    case 2: return wave_launch<V, DK, 2>(ctx, dim, p, n, q, m, out_dist, out_dist2, s, sh.W, sh.ctas); \
-    case 4: return wave_launch<V, DK, 4>(ctx, dim, p, n, q, m, out_dist, out_dist2, s, sh.W, sh.ctas); \
-    case 6: return wave_launch<V, DK, 6>(ctx, dim, p, n, q, m, out_dist, out_dist2, s, sh.W, sh.ctas); \
-    case 8: return wave_launch<V, DK, 8>(ctx, dim, p, n, q, m, out_dist, out_dist2, s, sh.W, sh.ctas); \
+    case 2: return wave_launch<V, DK, 2>(ctx, dim, p, n, q, m, out_dist, out_dist2, s, sh.W, sh.ctas, check); \
+    case 4: return wave_launch<V, DK, 4>(ctx, dim, p, n, q, m, out_dist, out_dist2, s, sh.W, sh.ctas, check); \
+    case 6: return wave_launch<V, DK, 6>(ctx, dim, p, n, q, m, out_dist, out_dist2, s, sh.W, sh.ctas, check); \
+    case 8: return wave_launch<V, DK, 8>(ctx, dim, p, n, q, m, out_dist, out_dist2, s, sh.W, sh.ctas, check); \
     default: return DFD_ERR_UNSUPPORTED;                                                     \
   }
 #define DFD_W_DK(V)              \
@@ -547,7 +547,7 @@ dfd_status dfd_pair_autotune(dfd_context* ctx, dfd_dtype dtype, int dim, const v
         sh.W = W;
         sh.ctas = grids[g];
         cudaEventRecord(e0, s);
-        st = wave_run(ctx, dtype, dim, p, n, q, m, res, nullptr, s, sh);
+        st = wave_run(ctx, dtype, dim, p, n, q, m, res, nullptr, s, sh, false);
         cudaEventRecord(e1, s);
         if (st != DFD_OK) continue;
         if (cudaEventSynchronize(e1) != cudaSuccess) {
@@ -648,8 +648,8 @@ dfd_status dfd_pair_shaped(dfd_context* ctx, dfd_dtype dtype, int dim, const voi
   }
   if ((st = set_device(ctx)) != DFD_OK) return st;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  if ((st = pre_checks(ctx, dtype, dim, p, n, q, m, s)) != DFD_OK) return st;
-  return wave_run(ctx, dtype, dim, p, n, q, m, out_dist, out_dist2, s, sh);
+  // the input checks run in the wavefront's prep kernel
+  return wave_run(ctx, dtype, dim, p, n, q, m, out_dist, out_dist2, s, sh, ctx->opt.check_inputs != 0);
 }
 
 dfd_status dfd_pair(dfd_context* ctx, dfd_dtype dtype, int dim, const void* p, int64_t n, const void* q, int64_t m,
@@ -697,9 +697,9 @@ dfd_status dfd_pair_host(dfd_context* ctx, dfd_dtype dtype, int dim, const void*
   cudaMemcpyAsync(d + pb, q_locked ? q : h + pb, (size_t)m * dim * 4, cudaMemcpyHostToDevice, s);
   WaveShape sh;
   wave_plan(ctx, dtype, dim, n, m, &sh);
-  if ((st = pre_checks(ctx, dtype, dim, d, n, d + pb, m, s)) == DFD_OK) {
+  {
     char* dres = d + pb + qb;
-    st = wave_run(ctx, dtype, dim, d, n, d + pb, m, dres, dres + 8, s, sh);
+    st = wave_run(ctx, dtype, dim, d, n, d + pb, m, dres, dres + 8, s, sh, ctx->opt.check_inputs != 0);
     if (st == DFD_OK) {
       cudaMemcpyAsync(h + pb + qb, dres, 16, cudaMemcpyDeviceToHost, s);
     }

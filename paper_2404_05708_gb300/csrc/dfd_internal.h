@@ -4,6 +4,7 @@
 #include <cstdint>
 #include <map>
 #include <mutex>
+#include <utility>
 #include <cuda_runtime.h>
 
 #include "dfd.h"
@@ -14,6 +15,12 @@ struct WaveShape {
   int R = 4;      // rows per lane
   int W = 4;      // compute warps per CTA
   int ctas = 0;   // persistent CTAs (0 = auto)
+};
+// Launch attributes of one wavefront kernel at W compute warps, queried
+// once per context: the dynamic shared memory it needs and the CTAs per SM.
+struct WaveAttr {
+  size_t smem = 0;
+  int per_sm = 1;
 };
 // Autotuning key: dtype, dimension class and the size classes of n and m
 // (floor(log2)), packed in 64 bits.
@@ -45,6 +52,8 @@ struct dfd_context {
   bool timed = false;                 // ev0/ev1 hold a recorded pair
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   std::map<uint64_t, dfd::WaveShape> tuned;   // autotuned wavefront shapes
+  std::map<std::pair<const void*, int>, dfd::WaveAttr> wave_attr;   // per (wavefront kernel, warps)
+  bool attr_cache = true;                     // keep wave_attr (off in the no-allocation entry point)
   signed char batch_order[2][5] = {};         // batch packing order per (float32 / int32, dim class 2,3,4,8,16)
   signed char batch_team[2][5] = {};          // batch team mode per (dtype, dim class): 0 auto, 1 wide pairs, 2 all multi-stripe
   signed char batch_rmax[2][5] = {};          // batch tile shape: rows per lane cap (0 = Rmax)
@@ -122,8 +131,11 @@ dfd_status launch_check_inputs2(dfd_dtype dtype, int dim, const void* x, int64_t
 
 // Band wavefront (K2).
 dfd_status wave_plan(const dfd_context* ctx, dfd_dtype dtype, int dim, int64_t n, int64_t m, WaveShape* shape);
+// check: the launch's prep kernel also runs the input checks (dfd_pair's
+// check_inputs); callers that checked already pass false.
 dfd_status wave_run(dfd_context* ctx, dfd_dtype dtype, int dim, const void* p, int64_t n, const void* q,
-                    int64_t m, void* out_dist, void* out_dist2, cudaStream_t s, const WaveShape& shape);
+                    int64_t m, void* out_dist, void* out_dist2, cudaStream_t s, const WaveShape& shape,
+                    bool check);
 
 // Ragged batch (K4) and all-pairs matrix (K5).
 dfd_status batch_run(dfd_context* ctx, dfd_dtype dtype, int dim, const void* points, const int64_t* offsets,

@@ -114,6 +114,7 @@ extern "C" dfd_status dfd_pair_noalloc(int device, dfd_dtype dtype, int dim, con
     c.d_err = reinterpret_cast<int*>(dev.scratch);
     c.scratch = dev.scratch + kErrBytes;
     c.scratch_bytes = DFD_NOALLOC_SCRATCH_BYTES - kErrBytes;
+    c.attr_cache = false;   // no host-side cache either: nothing allocated
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     // Outputs start as NaN (float, double) / -1 (int64): all-ones bytes.
     const size_t vb = dtype == DFD_F32 ? 4 : 8;
@@ -127,7 +128,7 @@ extern "C" dfd_status dfd_pair_noalloc(int device, dfd_dtype dtype, int dim, con
     if (st == DFD_OK) {
       WaveShape sh;
       wave_plan(&c, dtype, dim, n, m, &sh);
-      st = wave_run(&c, dtype, dim, p, n, q, m, out_dist, out_dist2, s, sh);
+      st = wave_run(&c, dtype, dim, p, n, q, m, out_dist, out_dist2, s, sh, false);   // checked above
       if (st == DFD_ERR_OOM) st = DFD_ERR_CAPACITY;
     }
     c.scratch = nullptr;   // not owned: nothing to release

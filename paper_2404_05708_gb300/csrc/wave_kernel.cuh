@@ -88,6 +88,13 @@ struct Args {
   const void* qpk_b;
   void* rowbuf_b;
   unsigned long long* progress_b;
+  // Two fronts on a row short enough (combine != 0): the last CTA to leave
+  // meets them itself (combine_block) and writes res_dist / res_dist2;
+  // `done` counts the CTAs that have left (zero before the launch).
+  int combine;
+  unsigned* done;
+  void* res_dist;
+  void* res_dist2;
 };
 
 // The fields of Args that differ between the two problems of a launch.
@@ -803,6 +810,43 @@ __device__ __forceinline__ void comm_warp(const Args& a, const Prob& pb, int64_t
   }
 }
 
+// The meeting of the two fronts (see combine_kernel) by one CTA, at the end
+// of the wavefront launch when the row is short: every other CTA has left,
+// so both row buffers are final.  Loads bypass L1 (the rows were written by
+// other SMs).  Nothing is written when the error word is set.
+template <class V>
+__device__ __forceinline__ void combine_block(const void* rowbuf_f, const void* rowbuf_b, int64_t m, const int* err,
+                                              void* out_dist, void* out_dist2, typename V::value* part) {
+  using T = typename V::value;
+  const T* F = static_cast<const T*>(rowbuf_f);
+  const T* B = static_cast<const T*>(rowbuf_b);
+  T best = V::inf();
+  for (int64_t j = threadIdx.x; j < m; j += blockDim.x) {
+    const T bj = __ldcg(B + (m - 1 - j));
+    const T bj1 = j + 1 < m ? __ldcg(B + (m - 2 - j)) : V::inf();
+    best = V::vmin(best, V::vmax(__ldcg(F + j), V::vmin(bj, bj1)));
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) best = V::vmin(best, __shfl_xor_sync(0xffffffffu, best, off));
+  const int warp = threadIdx.x >> 5, L = threadIdx.x & 31;
+  if (L == 0) part[warp] = best;   // part: one value per warp (shared memory the caller no longer uses)
+  __syncthreads();
+  if (warp == 0) {
+    T x = L < (int)(blockDim.x >> 5) ? part[L] : V::inf();
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) x = V::vmin(x, __shfl_xor_sync(0xffffffffu, x, off));
+    if (L == 0 && *(volatile const int*)err == 0) {
+      if constexpr (sizeof(T) == 4) {
+        if (out_dist2) static_cast<float*>(out_dist2)[0] = (float)x;
+        if (out_dist) static_cast<float*>(out_dist)[0] = sqrtf((float)x);
+      } else {
+        if (out_dist2) static_cast<long long*>(out_dist2)[0] = (long long)x;
+        if (out_dist) static_cast<double*>(out_dist)[0] = sqrt((double)(long long)x);
+      }
+    }
+  }
+}
+
 // ------------------------------------------------------------------ kernel
 template <class V, int DK, int R>
 __global__ void __launch_bounds__((kMaxWarps<V, DK, R>::value + 1) * 32, 1) wave_kernel(Args a) {
@@ -866,19 +910,59 @@ __global__ void __launch_bounds__((kMaxWarps<V, DK, R>::value + 1) * 32, 1) wave
     __syncthreads();
     if (ctl->abort) break;
   }
+  if (a.combine) {
+    // (no static shared memory: the control block and the rings are free now)
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence();   // this CTA's row-buffer stores before its count
+      ctl->band = atomicAdd(a.done, 1u) == gridDim.x - 1 ? 1 : 0;
+    }
+    __syncthreads();
+    if (ctl->band) {
+      __threadfence();
+      combine_block<V>(a.rowbuf, a.rowbuf_b, a.m, a.err, a.res_dist, a.res_dist2, rings);
+    }
+  }
 }
 
-// --------------------------------------------------------- q packing kernel
-// Writes the per-band q stream: nch chunks of C columns, NPL 16-byte planes
-// per column, each plane in the column order qpos(., TR, C); columns past m
-// repeat q_{m-1} (a repeated point does not change the distance, Sec. 4
-// footnote; they are never read into the result).  With `rev` the stream is
-// that of q reversed (column j is q_{m-1-j}).
+// --------------------------------------------------------- prep kernel
+// Everything the wavefront needs before its first band, in one launch:
+//   * the scratch header (ticket, merge words, progress words) zeroed by
+//     block (0, 0);
+//   * the input check, when `check` is set (blockIdx.y == 0): every float32
+//     coordinate of p and q finite (DFD_ERR_NONFINITE), every int32 one
+//     within +-lim (DFD_ERR_RANGE), raised in the error word, which makes the
+//     wavefront skip its bands;
+//   * the per-band q stream: nch chunks of C columns, NPL 16-byte planes per
+//     column, each plane in the column order qpos(., TR, C); columns past m
+//     repeat q_{m-1} (a repeated point does not change the distance, Sec. 4
+//     footnote; they are never read into the result).  blockIdx.y == 1 writes
+//     the stream of q reversed (column j is q_{m-1-j}) for the backward front.
+// (Was a memset, a check kernel and a packing kernel: on the 2000 x 1500
+// pair, three launches whose gaps cost more than their work.)
 template <class V, int DK>
-__global__ void pack_q_kernel(const typename V::coord* q, int64_t m, int dim, int nch, int TR, void* out0,
-                              void* out1) {
-  // blockIdx.y: 0 the forward stream (to out0), 1 q reversed (to out1)
+__global__ void wave_prep_kernel(const typename V::coord* q, int64_t m, int dim, int nch, int TR, void* out0,
+                                 void* out1, unsigned* header, int header_words, const typename V::coord* p,
+                                 int64_t p_elems, int check, long long lim, int* err) {
   const int rev = (int)blockIdx.y;
+  if (blockIdx.x == 0 && rev == 0)
+    for (int i = threadIdx.x; i < header_words; i += blockDim.x) header[i] = 0u;
+  if (check && rev == 0) {
+    const int64_t q_elems = m * dim;
+    bool bad = false;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < p_elems + q_elems;
+         i += (int64_t)gridDim.x * blockDim.x) {
+      const typename V::coord c = i < p_elems ? p[i] : q[i - p_elems];
+      if constexpr (std::is_same<V, F32>::value) {
+        bad |= !isfinite(c);
+      } else {
+        const long long v = c < 0 ? -(long long)c : (long long)c;
+        bad |= v > lim;
+      }
+    }
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0)
+      raise_error(err, std::is_same<V, F32>::value ? DFD_ERR_NONFINITE : DFD_ERR_RANGE);
+  }
   void* out = rev ? out1 : out0;
   constexpr int C = ChunkCols<DK>::value;
   using Rows_ = Rows<V, DK, 2>;

@@ -2,15 +2,23 @@
 // per (value type, dimension class, rows per lane) in wave_*.cu.
 #pragma once
 #include <algorithm>
+#include <climits>
+#include <cmath>
+#include <mutex>
 #include <type_traits>
 #include "dfd_internal.h"
 #include "wave_kernel.cuh"
 
 namespace dfd {
 
+// Rows of at most this many columns meet the two fronts inside the
+// wavefront launch (its last CTA); longer ones launch combine_kernel, whose
+// many CTAs read the rows in parallel.
+constexpr int64_t kFusedCombineCols = 65536;
+
 template <class V, int DK, int R>
 dfd_status wave_launch(dfd_context* ctx, int dim, const void* p, int64_t n, const void* q, int64_t m,
-                       void* out_dist, void* out_dist2, cudaStream_t s, int W, int ctas) {
+                       void* out_dist, void* out_dist2, cudaStream_t s, int W, int ctas, bool check) {
   using Lay = wave::Layout<V, DK, R>;
   using T = typename V::value;
   using Rec = typename Lay::Rec;
@@ -64,20 +72,58 @@ dfd_status wave_launch(dfd_context* ctx, int dim, const void* p, int64_t n, cons
   const int64_t nb1 = (n2 + H - 1) / H;
   char* base = static_cast<char*>(ctx->scratch);
 
-  cudaError_t e = cudaMemsetAsync(base, 0, off_row, s);
-  if (e != cudaSuccess) return cuda_status(e);
-  {
-    const int64_t recs = (int64_t)nch * C * Lay::NPL;
-    const int threads = 256;
-    const int blocks = (int)std::min<int64_t>((recs + threads - 1) / threads, 4 * (int64_t)ctx->num_sms);
-    wave::pack_q_kernel<V, DK><<<dim3(blocks, two ? 2 : 1), threads, 0, s>>>(
-        static_cast<const typename V::coord*>(q), m, dim, nch, wave::QTrans<V, R>::value, base + off_q,
-        base + off_q_b);
-  }
   const size_t smem = Lay::bytes(W);
   if (smem > ctx->smem_optin) return DFD_ERR_UNSUPPORTED;
-  e = cudaFuncSetAttribute(wave::wave_kernel<V, DK, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return cuda_status(e);
+  // one launch before the wavefront: the header zeroed, the inputs checked
+  // (check), q packed for each front
+  {
+    const int64_t recs = (int64_t)nch * C * Lay::NPL;
+    const int64_t elems = check ? (n + m) * (int64_t)dim : 0;
+    const int threads = 256;
+    const int blocks = (int)std::max<int64_t>(
+        1, std::min<int64_t>((std::max(recs, elems) + threads - 1) / threads, 4 * (int64_t)ctx->num_sms));
+    const long long lim =
+        std::min<long long>((1LL << 30) - 1, (long long)std::floor(std::sqrt((double)LLONG_MAX / (double)dim) / 2.0));
+    wave::wave_prep_kernel<V, DK><<<dim3(blocks, two ? 2 : 1), threads, 0, s>>>(
+        static_cast<const typename V::coord*>(q), m, dim, nch, wave::QTrans<V, R>::value, base + off_q,
+        base + off_q_b, reinterpret_cast<unsigned*>(base), (int)(off_row / 4),
+        static_cast<const typename V::coord*>(p), n * (int64_t)dim, check ? 1 : 0, lim, ctx->d_err);
+  }
+  // Launch attributes.  The kernel's dynamic shared memory allowance is a
+  // property of the function on the device (not of a context), so it is kept
+  // process-wide and only ever raised: the largest size set so far, per
+  // device.  The CTAs per SM are kept per context and (kernel, warps).
+  const void* kfn = reinterpret_cast<const void*>(wave::wave_kernel<V, DK, R>);
+  int per_sm = 0;
+  {
+    static std::mutex smem_mu;
+    static size_t smem_set[64] = {};
+    const int dev = ctx->device >= 0 && ctx->device < 64 ? ctx->device : 0;
+    {
+      std::lock_guard<std::mutex> lock(smem_mu);
+      if (smem_set[dev] < smem || ctx->device != dev) {
+        cudaError_t e =
+            cudaFuncSetAttribute(wave::wave_kernel<V, DK, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) {
+          cudaGetLastError();   // leave no error behind for later calls
+          return cuda_status(e);
+        }
+        if (ctx->device == dev) smem_set[dev] = smem;
+      }
+    }
+    auto it = ctx->attr_cache ? ctx->wave_attr.find({kfn, W}) : ctx->wave_attr.end();
+    if (it != ctx->wave_attr.end()) {
+      per_sm = it->second.per_sm;
+    } else {
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, wave::wave_kernel<V, DK, R>, (W + 1) * 32, smem) !=
+              cudaSuccess ||
+          per_sm < 1) {
+        cudaGetLastError();
+        per_sm = 1;
+      }
+      if (ctx->attr_cache) ctx->wave_attr[{kfn, W}] = WaveAttr{smem, per_sm};
+    }
+  }
 
   using Coord = typename V::coord;
   wave::Args a;
@@ -94,8 +140,13 @@ dfd_status wave_launch(dfd_context* ctx, int dim, const void* p, int64_t n, cons
   a.progress = reinterpret_cast<unsigned long long*>(base + 256);
   a.ticket = reinterpret_cast<int*>(base);
   a.err = ctx->d_err;
-  a.out_dist = two ? nullptr : out_dist;     // two fronts: combine_kernel writes the result
+  a.out_dist = two ? nullptr : out_dist;     // two fronts: the combine writes the result
   a.out_dist2 = two ? nullptr : out_dist2;
+  const bool fused = two && m <= kFusedCombineCols;
+  a.combine = fused ? 1 : 0;
+  a.done = reinterpret_cast<unsigned*>(base + 24);   // zeroed header word after the merge words
+  a.res_dist = out_dist;
+  a.res_dist2 = out_dist2;
   a.timeout_ns = timeout_ns(ctx);
   a.pstep = dim;
   a.nprob = two ? 2 : 1;
@@ -108,18 +159,11 @@ dfd_status wave_launch(dfd_context* ctx, int dim, const void* p, int64_t n, cons
   const int64_t nbands = nb0 + nb1;
   // persistent grid: every CTA that can be resident (a band is only ever
   // awaited by a later ticket, so CTAs that are not resident wait harmlessly)
-  int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, wave::wave_kernel<V, DK, R>, (W + 1) * 32, smem) !=
-          cudaSuccess ||
-      per_sm < 1) {
-    cudaGetLastError();
-    per_sm = 1;
-  }
   int grid = ctas > 0 ? ctas : per_sm * ctx->num_sms;
   grid = (int)std::min<int64_t>(grid, nbands);
   timing_begin(ctx, s);
   wave::wave_kernel<V, DK, R><<<grid, (W + 1) * 32, smem, s>>>(a);
-  if (two) {
+  if (two && !fused) {
     // the merge words sit after the ticket in the zeroed scratch header
     const int cblocks = (int)std::max<int64_t>(1, std::min<int64_t>((m + 1023) / 1024, ctx->num_sms));
     wave::combine_kernel<V><<<cblocks, 256, 0, s>>>(a.rowbuf, a.rowbuf_b, m,
@@ -136,4 +180,4 @@ dfd_status wave_launch(dfd_context* ctx, int dim, const void* p, int64_t n, cons
 
 #define DFD_WAVE_INSTANTIATE(V, DK, R)                                                                     \
   template dfd_status dfd::wave_launch<dfd::V, DK, R>(dfd_context*, int, const void*, int64_t, const void*, \
-                                                        int64_t, void*, void*, cudaStream_t, int, int);
+                                                        int64_t, void*, void*, cudaStream_t, int, int, bool);
