@@ -64,6 +64,7 @@ REF_SAMPLE = 20_000          # --impl reference: prefix per step
 TRAFFIC_BY_KERNEL_SHA: dict = {
     "9799fd99282b0741": 15759897,    # wave_kernel<F32, 3, 6>, long pair 200,000^2 (two fronts, 512-column q chunks)
     "4da739c00f897e73": 16059648,    # the same with a 4-chunk q ring (15.40 MB read, 0.66 MB written)
+    "336ce32a9a0f5945": 16327168,    # the same after the prep kernel and the fused combine (15.73 MB read, 0.59 MB written)
     "27aa8e25b42fbf75": 289363200,   # batch_kernel<I32, 2>, ragged batch of 65,536 pairs (graph launches)
     # batch_kernel<I32, 2> with size classes and the 8-step loop: 147.41 MB per launch captured on the
     # 32,768-pair batch (139.0 MB of inputs), scaled by the inputs (the points are read once) to the
