@@ -981,6 +981,49 @@ constexpr unsigned short kNoBucket = 0xFFFF;
 // few buckets.  Each warp walks the pairs 32 at a time with all lanes
 // together, so the match covers the whole warp.
 // (static: this header is compiled into several translation units)
+// Bucket of pair k (k < n_pairs), or -1 when the pair belongs to another
+// launch; also raises the plan's input errors.
+__device__ __forceinline__ int plan_bucket(const PlanArgs& a, int64_t k) {
+  const int32_t ia = a.pairs[2 * k], ib = a.pairs[2 * k + 1];
+  const bool valid_id = ia >= 0 && ib >= 0 && ia < a.n_ids && ib < a.n_ids;
+  const int64_t c = max(ia, ib);
+  if (!(valid_id ? (c >= a.lo_curve && c < a.hi_curve) : a.take_invalid != 0)) return -1;
+  int b = NTB + NBUCKET1 - 1;   // invalid pairs: last of the int64 warp class (skipped by the kernel)
+  if (ia < 0 || ib < 0 || ia >= a.n_curves || ib >= a.n_curves) {
+    raise_error(a.err, DFD_ERR_INVALID_ARG);
+  } else {
+    const int64_t total = a.offsets[a.n_curves];
+    const int64_t oa = a.offsets[ia], ob = a.offsets[ib], ea = a.offsets[ia + 1], eb = a.offsets[ib + 1];
+    const int64_t na = ea - oa, nb = eb - ob;
+    if (na < 1 || nb < 1 || oa < 0 || ob < 0 || ea > total || eb > total || na > INT32_MAX || nb > INT32_MAX)
+      raise_error(a.err, DFD_ERR_INVALID_ARG);
+    const bool sw = plan_rows_from_b(na, nb, a.dk, a.rmax, a.buf_cols);
+    const int64_t rows = max(sw ? nb : na, (int64_t)1), cols = max(sw ? na : nb, (int64_t)1);
+    const bool narrow = a.bbox && narrow_pair(a.bbox, a.dk, ia, ib);
+    const bool multi = rows > 32 * (int64_t)a.rmax;
+    if (a.team && multi &&
+        (a.team == 2 || cols > a.buf_cols || (a.team == 3 && team_pays(rows, cols, a.rmax, a.n_pairs, a.ctas)))) {
+      b = team_bucket(rows, cols) + (narrow ? NTB1 : 0);
+    } else {
+      b = NTB + (a.order ? cost_bucket_lpt(rows, cols, a.rmax) : cost_bucket(rows, cols, a.rmax));
+      if (narrow) b += NBUCKET1;
+    }
+  }
+  return b;
+}
+
+// Work-list entry of pair k in bucket b: index | narrow << 30 | swap << 31.
+__device__ __forceinline__ unsigned plan_entry(const PlanArgs& a, int64_t k, int b) {
+  const int32_t ia = a.pairs[2 * k], ib = a.pairs[2 * k + 1];
+  unsigned swap = 0;
+  if (ia >= 0 && ib >= 0 && ia < a.n_curves && ib < a.n_curves) {
+    const int64_t na = a.offsets[ia + 1] - a.offsets[ia], nb = a.offsets[ib + 1] - a.offsets[ib];
+    swap = plan_rows_from_b(na, nb, a.dk, a.rmax, a.buf_cols) ? 1u : 0u;   // as in plan_bucket
+  }
+  const unsigned narrow = (b < NTB ? b >= NTB1 : b - NTB >= NBUCKET1) ? kNarrowBit : 0u;
+  return (unsigned)k | narrow | (swap << 31);
+}
+
 static __global__ void plan_hist_kernel(PlanArgs a) {
   const int L = threadIdx.x & 31;
   const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -988,39 +1031,9 @@ static __global__ void plan_hist_kernel(PlanArgs a) {
   for (int64_t k0 = 32 * w0; k0 < a.n_pairs; k0 += 32 * wstride) {
     const int64_t k = k0 + L;
     int b = -1;
-    bool mine = false;
     if (k < a.n_pairs) {
-      const int32_t ia = a.pairs[2 * k], ib = a.pairs[2 * k + 1];
-      const bool valid_id = ia >= 0 && ib >= 0 && ia < a.n_ids && ib < a.n_ids;
-      const int64_t c = max(ia, ib);
-      mine = valid_id ? (c >= a.lo_curve && c < a.hi_curve) : a.take_invalid != 0;
-    }
-    if (mine) {
-      const int32_t ia = a.pairs[2 * k], ib = a.pairs[2 * k + 1];
-      b = NTB + NBUCKET1 - 1;   // invalid pairs: last of the int64 warp class (skipped by the kernel)
-      if (ia < 0 || ib < 0 || ia >= a.n_curves || ib >= a.n_curves) {
-        raise_error(a.err, DFD_ERR_INVALID_ARG);
-      } else {
-        const int64_t total = a.offsets[a.n_curves];
-        const int64_t oa = a.offsets[ia], ob = a.offsets[ib], ea = a.offsets[ia + 1], eb = a.offsets[ib + 1];
-        const int64_t na = ea - oa, nb = eb - ob;
-        if (na < 1 || nb < 1 || oa < 0 || ob < 0 || ea > total || eb > total || na > INT32_MAX || nb > INT32_MAX)
-          raise_error(a.err, DFD_ERR_INVALID_ARG);
-        const bool sw = plan_rows_from_b(na, nb, a.dk, a.rmax, a.buf_cols);
-        const int64_t rows = max(sw ? nb : na, (int64_t)1), cols = max(sw ? na : nb, (int64_t)1);
-        const bool narrow = a.bbox && narrow_pair(a.bbox, a.dk, ia, ib);
-        const bool multi = rows > 32 * (int64_t)a.rmax;
-        if (a.team && multi &&
-            (a.team == 2 || cols > a.buf_cols || (a.team == 3 && team_pays(rows, cols, a.rmax, a.n_pairs, a.ctas)))) {
-          b = team_bucket(rows, cols) + (narrow ? NTB1 : 0);
-        } else {
-          b = NTB + (a.order ? cost_bucket_lpt(rows, cols, a.rmax) : cost_bucket(rows, cols, a.rmax));
-          if (narrow) b += NBUCKET1;
-        }
-      }
-      a.bucket[k] = (unsigned short)b;
-    } else if (k < a.n_pairs) {
-      a.bucket[k] = kNoBucket;
+      b = plan_bucket(a, k);
+      a.bucket[k] = b >= 0 ? (unsigned short)b : kNoBucket;
     }
     const unsigned peers = __match_any_sync(0xffffffffu, b);
     if (b >= 0 && L == __ffs(peers) - 1) atomicAdd(&a.hist[b], (unsigned)__popc(peers));
@@ -1068,15 +1081,61 @@ static __global__ void plan_scatter_kernel(PlanArgs a) {
     if (b >= 0 && L == leader) pos = atomicAdd(&a.cursor[b], (unsigned)__popc(peers));
     pos = __shfl_sync(0xffffffffu, pos, leader) + __popc(peers & ((1u << L) - 1u));
     if (b < 0) continue;
-    const int32_t ia = a.pairs[2 * k], ib = a.pairs[2 * k + 1];
-    unsigned swap = 0;
-    if (ia >= 0 && ib >= 0 && ia < a.n_curves && ib < a.n_curves) {
-      const int64_t na = a.offsets[ia + 1] - a.offsets[ia], nb = a.offsets[ib + 1] - a.offsets[ib];
-      swap = plan_rows_from_b(na, nb, a.dk, a.rmax, a.buf_cols) ? 1u : 0u;   // as in plan_hist_kernel
-    }
-    const unsigned narrow = (b < NTB ? b >= NTB1 : b - NTB >= NBUCKET1) ? kNarrowBit : 0u;
-    a.worklist[pos] = (unsigned)k | narrow | (swap << 31);
+    a.worklist[pos] = plan_entry(a, k, b);
   }
+}
+
+// The whole plan of a launch of at most kSmallPlanPairs pairs in one block
+// of 1024 threads: the scratch header (zero_words words: counters, bucket
+// counts, cursors, SM slots) zeroed, the bucket counts and their scan in
+// shared memory, the scatter, and the final cursors (read by the batch
+// kernel) stored.  The general plan takes a memset and three kernels, whose
+// launch gaps dominate a small launch (32 pairs of 1,024 points).
+constexpr int64_t kSmallPlanPairs = 2048;
+static __global__ void __launch_bounds__(1024) plan_small_kernel(PlanArgs a, unsigned* zero_base, int zero_words) {
+  static_assert(NBUCKET <= 1024, "one bucket per thread");
+  __shared__ unsigned cnt[NBUCKET];
+  __shared__ unsigned wsum[32];
+  const int t = threadIdx.x, L = t & 31, w = t >> 5;
+  for (int i = t; i < zero_words; i += blockDim.x) zero_base[i] = 0u;
+  for (int i = t; i < NBUCKET; i += blockDim.x) cnt[i] = 0u;
+  __syncthreads();
+  for (int64_t k = t; k < a.n_pairs; k += blockDim.x) {
+    const int b = plan_bucket(a, k);
+    a.bucket[k] = b >= 0 ? (unsigned short)b : kNoBucket;
+    if (b >= 0) atomicAdd(&cnt[b], 1u);
+  }
+  __syncthreads();
+  // exclusive scan of the counts: a shuffle scan per warp, then over the warp totals
+  const unsigned x = t < NBUCKET ? cnt[t] : 0u;
+  unsigned inc = x;
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const unsigned y = __shfl_up_sync(0xffffffffu, inc, off);
+    if (L >= off) inc += y;
+  }
+  if (L == 31) wsum[w] = inc;
+  __syncthreads();
+  if (w == 0) {
+    unsigned v = wsum[L];
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const unsigned y = __shfl_up_sync(0xffffffffu, v, off);
+      if (L >= off) v += y;
+    }
+    wsum[L] = v;   // inclusive totals through warp L
+  }
+  __syncthreads();
+  if (t < NBUCKET) cnt[t] = (w > 0 ? wsum[w - 1] : 0u) + inc - x;
+  __syncthreads();
+  for (int64_t k = t; k < a.n_pairs; k += blockDim.x) {
+    const unsigned short bb = a.bucket[k];
+    if (bb == kNoBucket) continue;
+    const unsigned pos = atomicAdd(&cnt[bb], 1u);
+    a.worklist[pos] = plan_entry(a, k, (int)bb);
+  }
+  __syncthreads();
+  for (int i = t; i < NBUCKET; i += blockDim.x) a.cursor[i] = cnt[i];
 }
 
 // ------------------------------------------------------------ batch kernel

@@ -133,8 +133,12 @@ dfd_status batch_prepare(dfd_context* ctx, int dim, const void* points, const in
     base = static_cast<char*>(ctx->scratch);
   }
   const size_t off_hist = lay.off_hist;
-  cudaError_t e = cudaMemsetAsync(base, 0, off_bucket, s);
-  if (e != cudaSuccess) return cuda_status(e);
+  // a small launch zeroes its header in its one-block plan kernel
+  const bool small_plan = n_pairs <= batch::kSmallPlanPairs;
+  if (!small_plan) {
+    cudaError_t e = cudaMemsetAsync(base, 0, off_bucket, s);
+    if (e != cudaSuccess) return cuda_status(e);
+  }
   int* bbox = kInt ? (bbox_ext ? bbox_ext : reinterpret_cast<int*>(base + off_bbox)) : nullptr;
   if constexpr (kInt) {
     launch_curve_bbox<DK>(ctx, points, offsets, n_curves, dim, bbox, s, bbox_ext ? first_curve : 0);
@@ -164,9 +168,13 @@ dfd_status batch_prepare(dfd_context* ctx, int dim, const void* points, const in
   pa.hi_curve = slice ? slice->hi : n_curves;
   pa.take_invalid = slice ? (int)slice->take_invalid : 1;
   const int pblocks = (int)std::min<int64_t>((n_pairs + 255) / 256, 8 * (int64_t)ctx->num_sms);
-  batch::plan_hist_kernel<<<pblocks, 256, 0, s>>>(pa);
-  batch::plan_scan_kernel<<<1, batch::NBUCKET, 0, s>>>(pa);
-  batch::plan_scatter_kernel<<<pblocks, 256, 0, s>>>(pa);
+  if (small_plan) {
+    batch::plan_small_kernel<<<1, 1024, 0, s>>>(pa, reinterpret_cast<unsigned*>(base), (int)(off_bucket / 4));
+  } else {
+    batch::plan_hist_kernel<<<pblocks, 256, 0, s>>>(pa);
+    batch::plan_scan_kernel<<<1, batch::NBUCKET, 0, s>>>(pa);
+    batch::plan_scatter_kernel<<<pblocks, 256, 0, s>>>(pa);
+  }
   ba->rowbuf = base + off_buf;
   ba->buf_cols = buf_cols;
   ba->sm_rank = reinterpret_cast<unsigned*>(base + lay.off_smrank);   // zeroed with the header
