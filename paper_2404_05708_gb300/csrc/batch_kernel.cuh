@@ -338,6 +338,7 @@ struct SoloIO {
     if (oc >= 0 && oc < m) buf[oc] = outb[L];
   }
   __device__ __forceinline__ static void end_block(SoloIO*, int, int, int, int, bool, bool) {}
+  __device__ __forceinline__ static bool final_row(const SoloIO*) { return false; }
 };
 
 // Team of the CTA's warps on one pair: warp w runs stripes w, w + nw,
@@ -366,6 +367,9 @@ struct TeamIO {
   int w, nw;
   int* err;
   unsigned long long timeout_ns;
+  void* final_out;             // global, m values: stripe last_st's bottom row (a half-pair), or null
+  int last_st;
+  __device__ __forceinline__ static bool final_row(const TeamIO* io) { return io->final_out != nullptr; }
 
   template <class T>
   __device__ __forceinline__ static T top(TeamIO* io, const T*, int st, int c0, int L, int m) {
@@ -384,6 +388,10 @@ struct TeamIO {
   template <class T>
   __device__ __forceinline__ static void bottom(TeamIO* io, T*, int st, int c0, int L, int m, const T* outb) {
     const int oc = c0 + L - 31;
+    if (io->final_out && st == io->last_st) {   // the half-pair's last row: no consumer but the meeting
+      if (oc >= 0 && oc < m) static_cast<T*>(io->final_out)[oc] = outb[L];
+      return;
+    }
     const unsigned long long k = (unsigned long long)(st / io->nw);
     if (io->w == io->nw - 1) {
       if (oc >= 0 && oc < m) static_cast<T*>(io->gbuf)[oc] = outb[L];
@@ -423,7 +431,10 @@ __device__ __forceinline__ typename V::value warp_dfd(const typename V::coord* _
                                                       bool vec, typename V::value* buf, int L, int st_begin = 0,
                                                       int st_end = 1 << 30, AB* ab = nullptr,
                                                       uint4* stage = nullptr, IO* io = nullptr,
-                                                      int st_step = 1) {
+                                                      int st_step = 1, int pstep = 0, int qsign = 1) {
+  // pstep: elements from one row of P to the next (0: dim; -dim runs the rows
+  // backwards from P); qsign = -1 runs the columns backwards from Q.
+  const int64_t prow = pstep ? pstep : dim;
   using T = typename V::value;
   using Cd = typename V::coord;
   const int nstripes = (n + 32 * R - 1) / (32 * R);
@@ -434,7 +445,7 @@ __device__ __forceinline__ typename V::value warp_dfd(const typename V::coord* _
     for (int r = 0; r < R; ++r) {
       const int i = min(st * 32 * R + L * R + r, n - 1);
 #pragma unroll
-      for (int k = 0; k < DK; ++k) pr[r][k] = k < dim ? __ldg(P + (int64_t)i * dim + k) : (Cd)0;
+      for (int k = 0; k < DK; ++k) pr[r][k] = k < dim ? __ldg(P + (int64_t)i * prow + k) : (Cd)0;
     }
     // float32: rows packed in pairs, two cells per f32x2 instruction (the
     // same per-element rounding as the scalar order; odd R: last row scalar)
@@ -447,7 +458,8 @@ __device__ __forceinline__ typename V::value warp_dfd(const typename V::coord* _
         for (int k = 0; k < DK; ++k) pp[h][k] = pack2(pr[2 * h][k], pr[2 * h + 1][k]);
       }
     }
-    const bool has_top = st > 0, has_bottom = st + 1 < nstripes, last = !has_bottom;
+    // (a team half-pair also hands its last stripe's bottom row out: IO::final_row)
+    const bool has_top = st > 0, has_bottom = st + 1 < nstripes || IO::final_row(io), last = st + 1 >= nstripes;
     T v[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) v[r] = V::inf();
@@ -506,7 +518,7 @@ __device__ __forceinline__ typename V::value warp_dfd(const typename V::coord* _
     }
     // this lane's point of the coming block (in flight during the block before)
     Cd qpre[DK];
-    load_point<Cd, DK>(Q, min(L, m - 1), dim, vec, qpre);
+    load_point<Cd, DK>(Q, min(L, m - 1) * qsign, dim, vec, qpre);
     const uint4* sb = stage + (32 - L);   // column c0 + s - L of the window is sb[s]
     T* outb = reinterpret_cast<T*>(stage + NPL * 64);
     T* topb = reinterpret_cast<T*>(stage + NPL * 64 + 16);
@@ -522,7 +534,7 @@ __device__ __forceinline__ typename V::value warp_dfd(const typename V::coord* _
       }
       topb[L] = top_blk;   // the stripe above's columns c0 .. c0 + 31, read by lane 0 eight at a time
       __syncwarp();
-      load_point<Cd, DK>(Q, min(c0 + 32 + L, m - 1), dim, vec, qpre);   // next block, in flight
+      load_point<Cd, DK>(Q, min(c0 + 32 + L, m - 1) * qsign, dim, vec, qpre);   // next block, in flight
       uint4 qr[NPL];
 #pragma unroll
       for (int c = 0; c < NPL; ++c) qr[c] = sb[c * 64];
@@ -1177,26 +1189,27 @@ constexpr int kTeamWarps = 8;   // a team is the CTA's 8 warps
 // Rows per lane of a team pair: the rows spread over all the team's warps
 // (one stripe each) when they fit, else the largest stripes, cycling.
 template <int DK>
-__host__ __device__ __forceinline__ int team_rows_per_lane(int rows) {
+__host__ __device__ __forceinline__ int team_rows_per_lane(int rows, int nw = kTeamWarps) {
   constexpr int RM = Rmax<DK>::value;
   if (rows <= 32) return 1;
-  const int r = (rows + 32 * kTeamWarps - 1) / (32 * kTeamWarps);
+  const int r = (rows + 32 * nw - 1) / (32 * nw);
   return r > RM ? RM : r;
 }
 
 template <class V, int DK, class IO>
 __device__ __forceinline__ typename V::value team_dfd_any(const typename V::coord* P, int n,
                                                           const typename V::coord* Q, int m, int dim, bool vec,
-                                                          int L, int w, uint4* stage, IO* io) {
+                                                          int L, int w, uint4* stage, IO* io, int nw = kTeamWarps,
+                                                          int pstep = 0, int qsign = 1) {
   constexpr int RM = Rmax<DK>::value;
   using T = typename V::value;
-  switch (team_rows_per_lane<DK>(n)) {
+  switch (team_rows_per_lane<DK>(n, nw)) {
 #define DFD_T_CASE(RR)                                                                                         \
   case RR:                                                                                                     \
     if constexpr (RR < RM)                                                                                     \
       return warp_dfd<V, DK, RR, NoAbandon<V>, IO>(P, n, Q, m, dim, vec, static_cast<T*>(nullptr), L, w,       \
-                                                   1 << 30, static_cast<NoAbandon<V>*>(nullptr), stage, io,    \
-                                                   kTeamWarps);                                                \
+                                                   1 << 30, static_cast<NoAbandon<V>*>(nullptr), stage, io, nw, \
+                                                   pstep, qsign);                                              \
     break;
     DFD_T_CASE(1)
     DFD_T_CASE(2)
@@ -1210,7 +1223,7 @@ __device__ __forceinline__ typename V::value team_dfd_any(const typename V::coor
 #undef DFD_T_CASE
   }
   return warp_dfd<V, DK, RM, NoAbandon<V>, IO>(P, n, Q, m, dim, vec, static_cast<T*>(nullptr), L, w, 1 << 30,
-                                               static_cast<NoAbandon<V>*>(nullptr), stage, io, kTeamWarps);
+                                               static_cast<NoAbandon<V>*>(nullptr), stage, io, nw, pstep, qsign);
 }
 
 // First team pop of a CTA: when every team item fits one round of the SMs,
@@ -1231,6 +1244,34 @@ __device__ __forceinline__ int team_pop_first(int* counter, unsigned* sm_rank, i
     }
   }
   return atomicAdd(counter, 1);
+}
+
+// Meeting of a split team pair's halves (see combine_kernel): F is the
+// forward half's last row (row h - 1), B the backward half's (row h, taken
+// with q reversed, so B[m-1-j] is column j); every monotone path steps from
+// row h - 1 to row h once, so delta^2 = min_j max(F[j], min(B at j, B at
+// j + 1)) -- a selection among the same values, bit for bit the one-front
+// result.  All threads of the CTA call it; thread 0 gets the result.
+// `scratch`: 8 shared-memory words the CTA no longer uses (its rings).
+template <class V>
+__device__ __forceinline__ typename V::value meet_rows(const typename V::value* F, const typename V::value* B, int m,
+                                                       unsigned long long* scratch) {
+  using T = typename V::value;
+  T best = V::inf();
+  for (int j = threadIdx.x; j < m; j += blockDim.x) {
+    const T bj = B[m - 1 - j];
+    const T bj1 = j + 1 < m ? B[m - 2 - j] : V::inf();
+    best = V::vmin(best, V::vmax(F[j], V::vmin(bj, bj1)));
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) best = V::vmin(best, __shfl_xor_sync(0xffffffffu, best, off));
+  T* part = reinterpret_cast<T*>(scratch);
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = best;
+  __syncthreads();
+  T r = V::inf();
+  if (threadIdx.x == 0)
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) r = V::vmin(r, part[k]);
+  return r;
 }
 
 // One team pair (all 256 threads of the CTA call it): the rows (the plan's
@@ -1258,6 +1299,58 @@ __device__ __forceinline__ bool run_team_pair(const BatchArgs& a, unsigned wentr
   if (oa < 0 || ob < 0 || ea > total || eb > total) return true;                // reported by the plan
   const int n = (int)(ea - oa), m = (int)(eb - ob);
   if (n < 1 || m < 1) return true;                                               // reported by the plan
+  const Cd* pts = static_cast<const Cd*>(a.points);
+  // Two fronts (as the band wavefront's): when each half of the rows fits
+  // kHalf stripes, warps 0..3 run the first h rows forward and warps 4..7 the
+  // other n - h rows backwards against q reversed, each half a pipeline of
+  // its own, and their last rows meet in the CTA (meet_rows): the pipeline
+  // is half as deep.  The halves' last rows sit in the CTA's row buffer.
+  constexpr int kHalf = kTeamWarps / 2;
+  const int h = (n + 1) / 2;
+  if (n >= 64 && h <= kHalf * 32 * Rmax<DK>::value && 2LL * m <= gcols) {
+    if (threadIdx.x < kTeamWarps) {
+      prog[threadIdx.x] = 0;
+      cons[threadIdx.x] = 0;
+    }
+    __syncthreads();
+    const int half = w / kHalf;
+    const int nh = half == 0 ? h : n - h;
+    const int Rh = team_rows_per_lane<DK>(nh, kHalf);
+    TeamIO<TeamRing<DK>::value> io;
+    io.gbuf = gbuf;   // (no wrap-around: a half has at most kHalf stripes)
+    io.ring = ring + (size_t)half * kHalf * TeamRing<DK>::value;
+    io.prog = prog + half * kHalf;
+    io.cons = cons + half * kHalf;
+    io.w = w % kHalf;
+    io.nw = kHalf;
+    io.err = a.err;
+    io.timeout_ns = a.timeout_ns;
+    io.last_st = (nh + 32 * Rh - 1) / (32 * Rh) - 1;
+    const Cd* P = pts + (half == 0 ? oa : oa + n - 1) * a.dim;
+    const Cd* Q = pts + (half == 0 ? ob : ob + m - 1) * a.dim;
+    const int ps = half == 0 ? a.dim : -a.dim, qs = half == 0 ? 1 : -1;
+    if constexpr (std::is_same<V, I32>::value) {
+      if (wentry & kNarrowBit) {
+        float* rows = static_cast<float*>(gbuf);
+        io.final_out = rows + (size_t)half * m;
+        team_dfd_any<I32B, DK>(P, nh, Q, m, a.dim, a.vec != 0, L, io.w, stage, &io, kHalf, ps, qs);
+        __syncthreads();
+        const float r = meet_rows<I32B>(rows, rows + m, m, ring);
+        if (threadIdx.x == 0) write_result<I32B>(a.out_dist, a.out_dist2, k, r);
+        __syncthreads();
+        return true;
+      }
+    }
+    using T = typename V::value;
+    T* rows = static_cast<T*>(gbuf);
+    io.final_out = rows + (size_t)half * m;
+    team_dfd_any<V, DK>(P, nh, Q, m, a.dim, a.vec != 0, L, io.w, stage, &io, kHalf, ps, qs);
+    __syncthreads();
+    const T r = meet_rows<V>(rows, rows + m, m, ring);
+    if (threadIdx.x == 0) write_result<V>(a.out_dist, a.out_dist2, k, r);
+    __syncthreads();
+    return true;
+  }
   const int R = team_rows_per_lane<DK>(n);
   const int S = (n + 32 * R - 1) / (32 * R);
   if (S > kTeamWarps && (long long)m > gcols) return false;
@@ -1275,7 +1368,8 @@ __device__ __forceinline__ bool run_team_pair(const BatchArgs& a, unsigned wentr
   io.nw = kTeamWarps;
   io.err = a.err;
   io.timeout_ns = a.timeout_ns;
-  const Cd* pts = static_cast<const Cd*>(a.points);
+  io.final_out = nullptr;
+  io.last_st = S - 1;
   const bool last_warp = w == (S - 1) % kTeamWarps;
   if constexpr (std::is_same<V, I32>::value) {
     if (wentry & kNarrowBit) {
