@@ -74,6 +74,8 @@ TRAFFIC_BY_KERNEL_SHA: dict = {
     # slice filter of the plan: 145.60 MB per launch on the 32,768-pair batch (138.2 MB of
     # points), scaled by the points to the 65,536-pair batch's 277.0 MB
     "cb7f3699e1ec87c1": 291797623,
+    # the same after the one-block plan and the two-front teams: 145.70 MB per launch on 32,768 pairs
+    "4e3a53f28fbbf8b0": 291998225,
 }
 
 
