@@ -379,9 +379,12 @@ dfd_status dfd_batch_set_row_buffer(dfd_context* ctx, int cols);
  * scratch areas (grow-only, freed at destroy), whose row buffers are as wide
  * as the widest multi-stripe pair given (at least the context's width), so
  * any pair lengths run.  Results are bit-identical
- * to dfd_batch on the same data.  Offsets must be nondecreasing and every
- * id in [0, n_curves) (checked on the host: DFD_ERR_INVALID_ARG); the
- * device-side checks are dfd_batch's, returned directly.  Uses the context's
+ * to dfd_batch on the same data.  Offsets must be nondecreasing (checked on
+ * the host: DFD_ERR_INVALID_ARG) and every id in [0, n_curves)
+ * (DFD_ERR_INVALID_ARG: checked on the host when some curve is longer than
+ * the context's row buffers, else by the last launch's device-side plan,
+ * the other pairs' outputs then being written); the device-side checks are
+ * dfd_batch's, returned directly.  Uses the context's
  * internal streams and staging: one host-buffer call per context at a time.
  */
 dfd_status dfd_batch_host(dfd_context* ctx, dfd_dtype dtype, int dim, const void* points, const int64_t* offsets,

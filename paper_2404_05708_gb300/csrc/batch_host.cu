@@ -251,8 +251,9 @@ extern "C" dfd_status dfd_batch_host(dfd_context* ctx, dfd_dtype dtype, int dim,
   }
 
   // 2. on the host meanwhile: check the offsets (nondecreasing; the longest
-  // curve bounds the row buffers' width) and the ids, and find the widest
-  // row a multi-stripe pair hands between its stripes (the row buffers)
+  // curve bounds the row buffers' width) and, when a curve is wider than the
+  // buffers, the ids and the widest row a multi-stripe pair hands between its
+  // stripes (the row buffers)
   int64_t len_max = 0;
   bool bad = false;
   for (int64_t c = 0; c < n_curves; ++c) {
@@ -266,22 +267,24 @@ extern "C" dfd_status dfd_batch_host(dfd_context* ctx, dfd_dtype dtype, int dim,
     cudaGetLastError();
     return DFD_ERR_INVALID_ARG;
   }
+  // Unless some curve is longer than the row buffers are wide, the pair list
+  // needs no host pass at all: the launches go out at once, and an id out of
+  // range is reported by the last launch's plan (DFD_ERR_INVALID_ARG, as the
+  // host check would).
   bool bad_id = false;
   const int dk = dim_class(dim);
   const int64_t stripe_rows = 32 * (int64_t)rmax_of(dk);
   const bool any_wide = len_max > ctx->batch_buf_cols;   // else no pair can outgrow the buffers
   int64_t wide = 0;
-  for (int64_t i = 0; i < n_pairs; ++i) {
+  for (int64_t i = 0; any_wide && i < n_pairs; ++i) {
     const int32_t ia = pairs[2 * i], ib = pairs[2 * i + 1];
     if (ia < 0 || ib < 0 || ia >= n_curves || ib >= n_curves) {
       bad_id = true;
       break;
     }
-    if (any_wide) {
-      const int64_t na = offsets[ia + 1] - offsets[ia], nb = offsets[ib + 1] - offsets[ib];
-      const bool sw = batch::plan_rows_from_b(na, nb, dk, rmax_of(dk), ctx->batch_buf_cols);   // the plan's orientation
-      if ((sw ? nb : na) > stripe_rows) wide = std::max(wide, sw ? na : nb);
-    }
+    const int64_t na = offsets[ia + 1] - offsets[ia], nb = offsets[ib + 1] - offsets[ib];
+    const bool sw = batch::plan_rows_from_b(na, nb, dk, rmax_of(dk), ctx->batch_buf_cols);   // the plan's orientation
+    if ((sw ? nb : na) > stripe_rows) wide = std::max(wide, sw ? na : nb);
   }
   if (bad_id) {
     // the copies read the caller's buffers: let them finish before returning

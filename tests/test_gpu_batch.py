@@ -397,6 +397,33 @@ def test_batch_invalid_ids_are_reported(dctx):
     assert dctx.get_error() == 0
 
 
+def test_batch_host_invalid_ids_are_reported():
+    """dfd_batch_host returns DFD_ERR_INVALID_ARG for an id out of range:
+    found by the last launch's device-side plan when every curve fits the
+    row buffers, and by the host pass when one is longer; a good call after
+    either returns the oracle's values."""
+    from paper_2404_05708_gb300 import dfd
+    ctx = dfd.Context(0)
+    try:
+        b = ragged_edges("i32", 2, 9)
+        want, _ = oracle.batch(b.points, b.offsets, b.pairs)
+        for lens_long in (False, True):
+            off, pts = b.offsets, b.points
+            if lens_long:   # one extra curve of 5,000 points (> 4,096 columns), not in any pair
+                extra = np.cumsum(np.ones((5000, 2), np.int64), axis=0).astype(np.int32)
+                pts = np.concatenate([pts, extra])
+                off = np.concatenate([off, [off[-1] + 5000]]).astype(np.int64)
+            pairs = b.pairs.copy()
+            pairs[3, 0] = len(off) + 7
+            with pytest.raises(dfd.DFDError) as e:
+                ctx.batch_host(pts, off, pairs)
+            assert e.value.status == dfd.STATUS_CODE["DFD_ERR_INVALID_ARG"], lens_long
+            d, d2 = ctx.batch_host(pts, off, b.pairs)
+            assert np.array_equal(d2, want), lens_long
+    finally:
+        ctx.close()
+
+
 @pytest.mark.parametrize("dim", [2, 3, 8])
 def test_batch_int_range_check(dctx, dim):
     # |c| <= 2^30 - 1 (dim 2) or less is required of every coordinate; the
