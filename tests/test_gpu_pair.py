@@ -206,6 +206,20 @@ def test_reference_kernel_matches_oracle_int(dctx):
 
 # ------------------------------------------------------------ edge cases
 
+@pytest.mark.parametrize("m", [65536, 65537])
+def test_two_fronts_met_in_the_launch_or_by_the_combine_kernel(dctx, m):
+    """A pair of two bands or more runs as two fronts; rows of at most
+    65,536 columns are met by the wavefront's last CTA, longer ones by the
+    combine kernel.  Both sides of the edge, float32 and int32, equal the
+    oracle bit for bit, with explicit shapes of two and three bands."""
+    rng = np.random.default_rng(90 + m % 7)
+    p, q = f32_walk(rng, 900, 2), f32_walk(rng, m, 2)
+    check_f32(dctx, p, q)
+    check_f32(dctx, p, q, shape=(4, 2, 0))   # 256-row bands: four, two fronts of two
+    pi, qi = i32_walk(rng, 700, 2), i32_walk(rng, m, 2)
+    check_i32(dctx, pi, qi)
+
+
 def test_identity_symmetry_reversal_duplication(dctx):
     rng = np.random.default_rng(51)
     p, q = f32_walk(rng, 1500, 3), f32_walk(rng, 1100, 3)
