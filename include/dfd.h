@@ -111,6 +111,14 @@ dfd_status dfd_get_error(dfd_context* ctx);
  * half of the bands and backward over the rest (both curves reversed) --
  * whose last rows a final pass combines (min over the crossing steps of the
  * max of both sides): the same value, bit for bit.
+ * int32 pairs whose bounding box (over p and q) keeps every squared distance
+ * below 0x7F800000 (each coordinate's range at most 46,340, the squared
+ * ranges summing to at most 0x7F7FFFFF) carry their exact squared distances
+ * as uint32 bits in float registers (float min / max order them as
+ * integers); the others carry exact int64 values.  The choice is made on the
+ * device (the call launches a kernel for each class; the one that does not
+ * apply returns at once), so the call stays asynchronous; both give the
+ * exact int64 result.
  *   p: n x dim, q: m x dim (device, dtype), n >= 1, m >= 1, 1 <= dim <= 16.
  *   out_dist / out_dist2: device pointers to one element each (see top).
  */
@@ -532,12 +540,14 @@ dfd_status dfd_pair_shaped(dfd_context* ctx, dfd_dtype dtype, int dim, const voi
  * packed q) and the device error word live in one fixed array of
  * DFD_NOALLOC_SCRATCH_BYTES in the library's device image, present on
  * every GPU that loads the library until the process exits.  Scratch needed
- * (bytes): 1024 + 8*ceil(n / 64) + m * (4 for float32, 8 for int32) +
+ * (bytes): 2048 + B + 8*ceil(n / 64) + m * (4 for float32, 8 for int32) +
  * (m + 1024) * Q, where Q = 32 (float32, dim <= 4), 64 (float32, dim 5..8),
- * 128 (float32, dim 9..16), 16 (int32, dim <= 4), 32 (int32, dim 5..8),
- * 64 (int32, dim 9..16).  This is an upper bound of one front's layout;
- * inputs whose bound exceeds the array return DFD_ERR_CAPACITY before
- * anything is enqueued (e.g. float32 3-D: m up to ~460,000).
+ * 128 (float32, dim 9..16), 48 (int32, dim <= 4), 96 (int32, dim 5..8),
+ * 192 (int32, dim 9..16: int32 packs q for both of its value classes), and
+ * B = 0 (float32) or 16,640 (int32: the bounding-box partials).  This is an
+ * upper bound of one front's layout; inputs whose bound exceeds the array
+ * return DFD_ERR_CAPACITY before anything is enqueued (e.g. float32 3-D: m
+ * up to ~460,000; int32 2-D: m up to ~300,000).
  *
  * Arguments and results as dfd_pair, on CUDA device `device` (made current
  * for the call, then restored).  The input checks always run.  The first

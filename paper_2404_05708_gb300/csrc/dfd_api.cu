@@ -166,10 +166,11 @@ dfd_status launch_check_inputs(dfd_dtype dtype, int dim, const void* x, int64_t 
 // ------------------------------------------------------------- wave plans
 static bool shape_ok(const dfd_context* ctx, dfd_dtype dtype, int dim, int R, int W) {
   // The q ring bounds how far the last warp may trail warp 0, the register
-  // file how many warps of R rows a CTA can hold (wave_shape.h).
+  // file how many warps of R rows a CTA can hold (wave_shape.h); an int32
+  // pair's shape must suit both of its kernels.
   (void)ctx;
   const int dk = dim_class(dim);
-  return dk > 0 && wave::shape_supported(dtype == DFD_F32, dk, R, W);
+  return dk > 0 && (dtype == DFD_F32 ? wave::shape_supported(true, dk, R, W) : wave::int_shape_supported(dk, R, W));
 }
 
 dfd_status wave_plan(const dfd_context* ctx, dfd_dtype dtype, int dim, int64_t n, int64_t m, WaveShape* shape) {
@@ -177,17 +178,17 @@ dfd_status wave_plan(const dfd_context* ctx, dfd_dtype dtype, int dim, int64_t n
   // sweeps m columns plus its internal skew; bands start one inter-band lag
   // apart (W warps, each trailing the one above by 32*K + G columns), and a
   // pair of two bands or more runs as two fronts, each its own chain of
-  // bands.  float32: a step costs the cycles measured for one band of each R
+  // bands.  A step costs the cycles measured for one float32 band of each R
   // alone (in place, one compute warp per SM sub-partition: 73, 69, 74, 117
-  // for R = 2, 4, 6, 8), times the compute warps sharing a sub-partition;
-  // int32: an SM reaches its issue limit once W*R >= 48 rows.  Minimise the
-  // modelled completion time.
+  // for R = 2, 4, 6, 8), times the compute warps sharing a sub-partition.
+  // int32 pairs are planned the same way: the shape serves both of their
+  // kernels, and the narrow class (the float32 stripe) is the common one.
+  // Minimise the modelled completion time.
   auto hit = ctx->tuned.find(tune_key(dtype, dim_class(dim), n, m));
   if (hit != ctx->tuned.end()) {
     *shape = hit->second;
     return DFD_OK;
   }
-  const double RSAT = dtype == DFD_F32 ? 24.0 : 48.0;
   // one CTA per SM: bands of one chain sharing an SM slow each other down
   // more than a second CTA hides (the 200,000^2 3-D pair: 2.63 Tcell/s with
   // 152 CTAs, 1.87 with all 261 bands resident two to an SM)
@@ -201,20 +202,14 @@ dfd_status wave_plan(const dfd_context* ctx, dfd_dtype dtype, int dim, int64_t n
       const double H = 32.0 * W * R;
       const double B = std::ceil((double)n / H);
       const double waves = std::ceil(B / P);
-      const double K = dtype == DFD_F32 ? R / 2 : 1;
+      const double K = R / 2;
       const double wlag = 32.0 * K + 32.0;
       const double lag = wlag * W + 96.0;
       const double conc = std::min(B, (double)P);
       const double chain = B >= 2 ? std::ceil(conc / 2.0) - 1.0 : 0.0;   // bands of one front started in turn
       const double cols = waves * ((double)m + wlag * W) + chain * lag;
-      double t;
-      if (dtype == DFD_F32) {
-        const double step = R == 2 ? 73.0 : R == 4 ? 69.0 : R == 6 ? 74.0 : 117.0;
-        t = cols * step * std::ceil(W / 4.0);
-      } else {
-        const double sat = std::min(1.0, W * R / RSAT);
-        t = cols * H / sat;
-      }
+      const double step = R == 2 ? 73.0 : R == 4 ? 69.0 : R == 6 ? 74.0 : 117.0;
+      const double t = cols * step * std::ceil(W / 4.0);
       if (t < best * 0.999) {
         best = t;
         bs.R = R;

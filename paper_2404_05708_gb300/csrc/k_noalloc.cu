@@ -65,16 +65,19 @@ dfd_status setup_device(int device, DeviceSetup* out) {
 // Upper bound of the wavefront's scratch for (n, m) in this dtype / dim.
 size_t scratch_needed(dfd_dtype dtype, int dim, int64_t n, int64_t m) {
   const int dk = dim_class(dim);
-  size_t q_per_col;
-  if (dtype == DFD_F32)
-    q_per_col = dk <= 4 ? 32 : dk == 8 ? 64 : 128;
-  else
-    q_per_col = dk <= 4 ? 16 : dk == 8 ? 32 : 64;
+  // packed q bytes per column: float32 (and the narrow int32 class) 16-byte
+  // planes of two coordinates, the exact int32 class planes of four; an
+  // int32 pair packs both streams, and its prep kernel's bounding-box
+  // partials (at most 128 blocks of dk (min, max) int pairs) sit beside them
+  const size_t q_f = dk <= 4 ? 32 : dk == 8 ? 64 : 128;
+  const size_t q_i = dk <= 4 ? 16 : dk == 8 ? 32 : 64;
+  const size_t q_per_col = dtype == DFD_F32 ? q_f : q_f + q_i;
+  const size_t box = dtype == DFD_F32 ? 0 : 128 * 2 * 16 * sizeof(int) + 256;
   const size_t vbytes = dtype == DFD_F32 ? 4 : 8;
   // packed q: m columns plus the skew and block padding, rounded up to whole
   // chunks of up to 512 columns (one front; two fronts are used only when
   // their doubled scratch also fits, else the wavefront runs one)
-  return 1024 + 8 * (size_t)((n + 63) / 64) + (size_t)m * vbytes + ((size_t)m + 1024) * q_per_col;
+  return 2048 + box + 8 * (size_t)((n + 63) / 64) + (size_t)m * vbytes + ((size_t)m + 1024) * q_per_col;
 }
 
 }  // namespace

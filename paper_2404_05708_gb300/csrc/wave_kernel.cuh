@@ -34,20 +34,25 @@ struct ChunkCols {
   static constexpr int value = chunk_cols(DK);
 };
 
-// Column skew between neighbouring lanes.  float32 lanes hold K = R/2 row
-// pairs and pair h runs h columns behind pair 0, so the K pairs of one step
-// are independent (the "up" of pair h is pair h-1's value from the step
-// before); lane L+1 runs K columns behind lane L.  int32 lanes keep all R
-// rows in one column (K = 1).
+// Column skew between neighbouring lanes.  float32 lanes (and the narrow
+// int32 class, whose values are floats) hold K = R/2 row pairs and pair h
+// runs h columns behind pair 0, so the K pairs of one step are independent
+// (the "up" of pair h is pair h-1's value from the step before); lane L+1
+// runs K columns behind lane L.  Exact int64 lanes keep all R rows in one
+// column (K = 1).
+template <class V>
+struct Skewed {
+  static constexpr bool value = !std::is_same<V, I32>::value;
+};
 template <class V, int R>
 struct Skew {
-  static constexpr int value = skew(std::is_same<V, F32>::value, R);
+  static constexpr int value = skew(Skewed<V>::value, R);
 };
 
 // Compute warps per CTA the register file allows (the kernel's launch bound).
 template <class V, int DK, int R>
 struct kMaxWarps {
-  static constexpr int value = max_warps_regs(std::is_same<V, F32>::value, DK, R);
+  static constexpr int value = max_warps_regs(Skewed<V>::value, DK, R, std::is_same<V, I32B>::value);
 };
 
 // Position of column cc (0 <= cc < C) inside a packed q chunk plane: lanes
@@ -95,6 +100,13 @@ struct Args {
   unsigned* done;
   void* res_dist;
   void* res_dist2;
+  // int32 pairs launch a narrow-class and an exact-class kernel back to
+  // back; each CTA reduces the prep kernel's bounding-box partials (box:
+  // nbox blocks of DK (min, max) pairs) and leaves at once unless the pair's
+  // class is its own (want: 1 narrow, 0 exact).  box == nullptr: no choice.
+  const int* box;
+  int nbox;
+  int want;
 };
 
 // The fields of Args that differ between the two problems of a launch.
@@ -216,6 +228,120 @@ struct Rows<I32, DK, R> {
     }
   }
 };
+
+// Narrow int32 class (values are the exact uint32 squared distances carried
+// as float bits, see I32B): the float32 stripe's row pairs and q ring
+// geometry (NPL 16-byte planes a column), with the q record holding the
+// words (-2 q_0, ..., -2 q_{DK-1}, |q|^2, 0...) and each row its int32
+// coordinates and |p|^2.  d^2 = |p|^2 + |q|^2 + sum_k p_k (-2 q_k) in uint32
+// arithmetic: every term wraps mod 2^32 and the true value lies below
+// 0x7F800000, so the wrapped sum is that value exactly.
+template <int DK, int R>
+struct Rows<I32B, DK, R> {
+  static_assert(R % 2 == 0, "rows are processed in pairs");
+  static constexpr int NPL = (DK + 1) / 2;
+  using Rec = float4;
+  int pr[R][DK];
+  unsigned pn[R];
+
+  __device__ __forceinline__ void load(const int32_t* P, int64_t r0, int64_t rlast, int dim, int64_t pstep) {
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int64_t i = min(r0 + r, rlast);
+      unsigned n2 = 0;
+#pragma unroll
+      for (int k = 0; k < DK; ++k) {
+        pr[r][k] = k < dim ? P[i * pstep + k] : 0;
+        n2 += (unsigned)pr[r][k] * (unsigned)pr[r][k];
+      }
+      pn[r] = n2;
+    }
+  }
+
+  // word w of a record given as its NPL planes (w a compile-time constant
+  // after unrolling)
+  static __device__ __forceinline__ unsigned word(const float4 (&t)[NPL], int w) {
+    const float4 v = t[w >> 2];
+    const float x = (w & 3) == 0 ? v.x : (w & 3) == 1 ? v.y : (w & 3) == 2 ? v.z : v.w;
+    return __float_as_uint(x);
+  }
+
+  __device__ __forceinline__ void dist_pair(int h, const float4 (&t)[NPL], float& d0, float& d1) const {
+    const unsigned qn = word(t, DK);
+    unsigned a0 = pn[2 * h] + qn, a1 = pn[2 * h + 1] + qn;
+#pragma unroll
+    for (int k = 0; k < DK; ++k) {
+      const unsigned w = word(t, k);
+      a0 += (unsigned)pr[2 * h][k] * w;
+      a1 += (unsigned)pr[2 * h + 1][k] * w;
+    }
+    d0 = __uint_as_float(a0);
+    d1 = __uint_as_float(a1);
+  }
+};
+
+// One pair's result from its squared distance in the value type: float32
+// as is; int32 as int64 delta^2 and double delta (the narrow class's float
+// bits are the uint32 value).
+template <class V>
+__device__ __forceinline__ void write_pair_result(void* out_dist, void* out_dist2, typename V::value x) {
+  if constexpr (std::is_same<V, F32>::value) {
+    if (out_dist2) static_cast<float*>(out_dist2)[0] = x;
+    if (out_dist) static_cast<float*>(out_dist)[0] = sqrtf(x);
+  } else {
+    long long v;
+    if constexpr (std::is_same<V, I32B>::value)
+      v = (long long)__float_as_uint(x);
+    else
+      v = (long long)x;
+    if (out_dist2) static_cast<long long*>(out_dist2)[0] = v;
+    if (out_dist) static_cast<double*>(out_dist)[0] = sqrt((double)v);
+  }
+}
+
+// Whether an int32 pair is narrow: every coordinate's range over p and q at
+// most 46340 and the sum of the squared ranges at most 0x7F7FFFFF, so that
+// every squared distance is exact in uint32 below the first float NaN
+// pattern.  box holds nbox partial boxes of DK (min, max) pairs (the prep
+// kernel's blocks; coordinates past dim are zero).  Called by every thread
+// of the block; sh: 2 * DK + 1 ints of shared memory, free on return.
+template <int DK>
+__device__ __forceinline__ bool box_narrow_block(const int* box, int nbox, int* sh) {
+  if (threadIdx.x < 2 * DK) sh[threadIdx.x] = (threadIdx.x & 1) ? INT_MIN : INT_MAX;
+  __syncthreads();
+  // one coordinate at a time: two values live, whatever DK
+#pragma unroll 1
+  for (int k = 0; k < DK; ++k) {
+    int lo = INT_MAX, hi = INT_MIN;
+    for (int b = threadIdx.x; b < nbox; b += blockDim.x) {
+      lo = min(lo, __ldcg(box + (b * DK + k) * 2));
+      hi = max(hi, __ldcg(box + (b * DK + k) * 2 + 1));
+    }
+    lo = __reduce_min_sync(0xffffffffu, lo);
+    hi = __reduce_max_sync(0xffffffffu, hi);
+    if ((threadIdx.x & 31) == 0) {
+      atomicMin(&sh[2 * k], lo);
+      atomicMax(&sh[2 * k + 1], hi);
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    bool narrow = true;
+    unsigned long long s2 = 0;
+    for (int k = 0; k < DK; ++k) {
+      const long long r = (long long)sh[2 * k + 1] - (long long)sh[2 * k];
+      if (r < 0 || r > (long long)kI32BMaxRange)
+        narrow = false;
+      else
+        s2 += (unsigned long long)(r * r);
+    }
+    sh[2 * DK] = narrow && s2 <= kI32BMaxD2 ? 1 : 0;
+  }
+  __syncthreads();
+  const bool narrow = sh[2 * DK] != 0;
+  __syncthreads();
+  return narrow;
+}
 
 // --------------------------------------------------- shared-memory counters
 __device__ __forceinline__ int ld_acquire_cta(const int* p) {
@@ -388,8 +514,8 @@ struct SkewState {
   float ush;                    // lane L-1's bottom value, shuffled for the coming step
 };
 
-template <int DK, int R>
-__device__ __forceinline__ void skew_block(const Rows<F32, DK, R>& rows, SkewState<DK, R>& st, const float* ring_in,
+template <class RowsT, int DK, int R>
+__device__ __forceinline__ void skew_block(const RowsT& rows, SkewState<DK, R>& st, const float* ring_in,
                                            float* ring_out, const float4* qring, unsigned xbase, int c0, int L) {
   constexpr int K = R / 2;
   constexpr int NPL = (DK + 1) / 2;
@@ -489,7 +615,7 @@ __device__ __forceinline__ void compute_stripe(const Args& a, const Prob& pb, in
   constexpr int NQC = NQ * C;
   constexpr int K = Skew<V, R>::value;
   constexpr int SK = 32 * K - 1;
-  constexpr bool kSkew = std::is_same<V, F32>::value;
+  constexpr bool kSkew = Skewed<V>::value;
   const int L = threadIdx.x & 31;
   const int W = (int)(blockDim.x >> 5) - 1;
   const Rec* qring = reinterpret_cast<const Rec*>(smem);
@@ -593,9 +719,8 @@ __device__ __forceinline__ void compute_stripe(const Args& a, const Prob& pb, in
     }
 
     if constexpr (kSkew) {
-      skew_block<DK, (kSkew ? R : 2)>(reinterpret_cast<const Rows<F32, DK, (kSkew ? R : 2)>&>(rows), ss,
-                                      reinterpret_cast<const float*>(ring_in), reinterpret_cast<float*>(ring_out),
-                                      qr, xbase, c0, L);
+      skew_block<Rows<V, DK, R>, DK, R>(rows, ss, reinterpret_cast<const float*>(ring_in),
+                                        reinterpret_cast<float*>(ring_out), qr, xbase, c0, L);
     } else {
       auto qaddr = [&](int cq) { return qring + ((xbase + (unsigned)cq) & (unsigned)(NQC - 1)); };
       // The block's 32 ring inputs, one per lane (lane s holds column c0 + s);
@@ -760,15 +885,7 @@ __device__ __forceinline__ void comm_warp(const Args& a, const Prob& pb, int64_t
           if (k < units && col < m) {
             const T val = ringW[ridx(col)];
             st_cg(rowbuf + col, val);
-            if (band == pb.nbands - 1 && col == m - 1) {
-              if constexpr (sizeof(T) == 4) {
-                if (a.out_dist2) static_cast<float*>(a.out_dist2)[0] = (float)val;
-                if (a.out_dist) static_cast<float*>(a.out_dist)[0] = sqrtf((float)val);
-              } else {
-                if (a.out_dist2) static_cast<long long*>(a.out_dist2)[0] = (long long)val;
-                if (a.out_dist) static_cast<double*>(a.out_dist)[0] = sqrt((double)val);
-              }
-            }
+            if (band == pb.nbands - 1 && col == m - 1) write_pair_result<V>(a.out_dist, a.out_dist2, val);
           }
         }
         __syncwarp();
@@ -835,15 +952,7 @@ __device__ __forceinline__ void combine_block(const void* rowbuf_f, const void* 
     T x = L < (int)(blockDim.x >> 5) ? part[L] : V::inf();
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) x = V::vmin(x, __shfl_xor_sync(0xffffffffu, x, off));
-    if (L == 0 && *(volatile const int*)err == 0) {
-      if constexpr (sizeof(T) == 4) {
-        if (out_dist2) static_cast<float*>(out_dist2)[0] = (float)x;
-        if (out_dist) static_cast<float*>(out_dist)[0] = sqrtf((float)x);
-      } else {
-        if (out_dist2) static_cast<long long*>(out_dist2)[0] = (long long)x;
-        if (out_dist) static_cast<double*>(out_dist)[0] = sqrt((double)(long long)x);
-      }
-    }
+    if (L == 0 && *(volatile const int*)err == 0) write_pair_result<V>(out_dist, out_dist2, x);
   }
 }
 
@@ -860,6 +969,9 @@ __global__ void __launch_bounds__((kMaxWarps<V, DK, R>::value + 1) * 32, 1) wave
   uint64_t* empty = full + NQ;
   T* rings = reinterpret_cast<T*>(smem + Lay::ring_off);
   Ctl* ctl = reinterpret_cast<Ctl*>(smem + Lay::ctl_off(W));
+
+  // an int32 pair's other class: leave before touching anything
+  if (a.box && box_narrow_block<DK>(a.box, a.nbox, reinterpret_cast<int*>(smem)) != (a.want != 0)) return;
 
   // zero the q ring once (never-read slots stay finite), rings to +inf
   {
@@ -929,10 +1041,9 @@ __global__ void __launch_bounds__((kMaxWarps<V, DK, R>::value + 1) * 32, 1) wave
 // Everything the wavefront needs before its first band, in one launch:
 //   * the scratch header (ticket, merge words, progress words) zeroed by
 //     block (0, 0);
-//   * the input check, when `check` is set (blockIdx.y == 0): every float32
-//     coordinate of p and q finite (DFD_ERR_NONFINITE), every int32 one
-//     within +-lim (DFD_ERR_RANGE), raised in the error word, which makes the
-//     wavefront skip its bands;
+//   * the input check, when `check` is set (blockIdx.y == 0): every
+//     coordinate of p and q finite (DFD_ERR_NONFINITE), raised in the error
+//     word, which makes the wavefront skip its bands;
 //   * the per-band q stream: nch chunks of C columns, NPL 16-byte planes per
 //     column, each plane in the column order qpos(., TR, C); columns past m
 //     repeat q_{m-1} (a repeated point does not change the distance, Sec. 4
@@ -940,10 +1051,13 @@ __global__ void __launch_bounds__((kMaxWarps<V, DK, R>::value + 1) * 32, 1) wave
 //     the stream of q reversed (column j is q_{m-1-j}) for the backward front.
 // (Was a memset, a check kernel and a packing kernel: on the 2000 x 1500
 // pair, three launches whose gaps cost more than their work.)
+// (float32; int32 pairs use wave_prep_int_kernel)
 template <class V, int DK>
 __global__ void wave_prep_kernel(const typename V::coord* q, int64_t m, int dim, int nch, int TR, void* out0,
                                  void* out1, unsigned* header, int header_words, const typename V::coord* p,
                                  int64_t p_elems, int check, long long lim, int* err) {
+  static_assert(std::is_same<V, F32>::value, "float32 prep");
+  (void)lim;
   const int rev = (int)blockIdx.y;
   if (blockIdx.x == 0 && rev == 0)
     for (int i = threadIdx.x; i < header_words; i += blockDim.x) header[i] = 0u;
@@ -952,16 +1066,10 @@ __global__ void wave_prep_kernel(const typename V::coord* q, int64_t m, int dim,
     bool bad = false;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < p_elems + q_elems;
          i += (int64_t)gridDim.x * blockDim.x) {
-      const typename V::coord c = i < p_elems ? p[i] : q[i - p_elems];
-      if constexpr (std::is_same<V, F32>::value) {
-        bad |= !isfinite(c);
-      } else {
-        const long long v = c < 0 ? -(long long)c : (long long)c;
-        bad |= v > lim;
-      }
+      const float c = i < p_elems ? p[i] : q[i - p_elems];
+      bad |= !isfinite(c);
     }
-    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0)
-      raise_error(err, std::is_same<V, F32>::value ? DFD_ERR_NONFINITE : DFD_ERR_RANGE);
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) raise_error(err, DFD_ERR_NONFINITE);
   }
   void* out = rev ? out1 : out0;
   constexpr int C = ChunkCols<DK>::value;
@@ -978,21 +1086,114 @@ __global__ void wave_prep_kernel(const typename V::coord* q, int64_t m, int dim,
     const int jj = rem % C;
     const int64_t jc = min(chunk * C + jj, m - 1);
     const int64_t j = rev ? m - 1 - jc : jc;   // the reversed problem's column jc is q's column m-1-jc
-    const typename V::coord* qj = q + j * dim;
-    Rec r;
-    if constexpr (std::is_same<V, F32>::value) {
-      const int k0 = 2 * plane, k1 = 2 * plane + 1;
-      const float x0 = k0 < dim ? qj[k0] : 0.f;
-      const float x1 = k1 < dim ? qj[k1] : 0.f;
-      r = make_float4(x0, x0, x1, x1);
-    } else {
-      const int k = 4 * plane;
-      r.x = k < dim ? qj[k] : 0;
-      r.y = k + 1 < dim ? qj[k + 1] : 0;
-      r.z = k + 2 < dim ? qj[k + 2] : 0;
-      r.w = k + 3 < dim ? qj[k + 3] : 0;
+    const float* qj = q + j * dim;
+    const int k0 = 2 * plane, k1 = 2 * plane + 1;
+    const float x0 = k0 < dim ? qj[k0] : 0.f;
+    const float x1 = k1 < dim ? qj[k1] : 0.f;
+    o[chunk * (C * NPL) + plane * C + qpos(jj, TR, C)] = make_float4(x0, x0, x1, x1);
+  }
+}
+
+// The int32 form of the prep kernel.  Besides the header and the range
+// check it reduces the bounding box of p and q: blocks blockIdx.x < nbox of
+// blockIdx.y == 0 take points in a grid stride of nbox blocks and write their
+// (min, max) per coordinate (zero past dim) to box[blockIdx.x], which every
+// CTA of the launches that follow reduces to choose the value class.  It
+// packs q for both classes, each front its own streams: the narrow class's
+// (out_n0 / out_n1: nch_n chunks of NPL = (DK+1)/2 planes, words
+// (-2 q_0, ..., -2 q_{DK-1}, |q|^2, 0...), order qpos(., TR_n, C)) and the
+// exact class's (out_w0 / out_w1: nch_w chunks of (DK+3)/4 int4 planes).
+template <int DK>
+__global__ void wave_prep_int_kernel(const int32_t* q, int64_t m, int dim, const int32_t* p, int64_t n,
+                                     unsigned* header, int header_words, int check, long long lim, int* err,
+                                     int* box, int nbox, int nch_n, int TR_n, void* out_n0, void* out_n1, int nch_w,
+                                     void* out_w0, void* out_w1) {
+  const int rev = (int)blockIdx.y;
+  if (blockIdx.x == 0 && rev == 0)
+    for (int i = threadIdx.x; i < header_words; i += blockDim.x) header[i] = 0u;
+  if (rev == 0 && (int)blockIdx.x < nbox) {
+    __shared__ int sh[2 * DK];
+    if (threadIdx.x < 2 * DK) sh[threadIdx.x] = (threadIdx.x & 1) ? INT_MIN : INT_MAX;
+    __syncthreads();
+    int lo[DK], hi[DK];
+#pragma unroll
+    for (int k = 0; k < DK; ++k) {
+      lo[k] = INT_MAX;
+      hi[k] = INT_MIN;
     }
-    o[chunk * (C * NPL) + plane * C + qpos(jj, TR, C)] = r;
+    bool bad = false;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n + m; i += (int64_t)nbox * blockDim.x) {
+      const int32_t* x = i < n ? p + i * dim : q + (i - n) * dim;
+#pragma unroll
+      for (int k = 0; k < DK; ++k) {
+        const int c = k < dim ? x[k] : 0;
+        lo[k] = min(lo[k], c);
+        hi[k] = max(hi[k], c);
+        if (check && k < dim) {
+          const long long v = c < 0 ? -(long long)c : (long long)c;
+          bad |= v > lim;
+        }
+      }
+    }
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) raise_error(err, DFD_ERR_RANGE);
+#pragma unroll
+    for (int k = 0; k < DK; ++k) {
+      lo[k] = __reduce_min_sync(0xffffffffu, lo[k]);
+      hi[k] = __reduce_max_sync(0xffffffffu, hi[k]);
+    }
+    if ((threadIdx.x & 31) == 0) {
+#pragma unroll
+      for (int k = 0; k < DK; ++k) {
+        atomicMin(&sh[2 * k], lo[k]);
+        atomicMax(&sh[2 * k + 1], hi[k]);
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x < 2 * DK) box[blockIdx.x * 2 * DK + threadIdx.x] = sh[threadIdx.x];
+  }
+  constexpr int C = ChunkCols<DK>::value;
+  constexpr int NPL_N = Rows<I32B, DK, 2>::NPL;
+  constexpr int NPL_W = Rows<I32, DK, 2>::NPL;
+  const int64_t total_n = (int64_t)nch_n * C * NPL_N;
+  const int64_t total_w = (int64_t)nch_w * C * NPL_W;
+  int4* on = static_cast<int4*>(rev ? out_n1 : out_n0);
+  int4* ow = static_cast<int4*>(rev ? out_w1 : out_w0);
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total_n + total_w;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const bool nar = idx < total_n;
+    const int64_t id = nar ? idx : idx - total_n;
+    const int npl = nar ? NPL_N : NPL_W;
+    const int64_t chunk = id / (C * npl);
+    const int rem = (int)(id % (C * npl));
+    const int plane = rem / C;
+    const int jj = rem % C;
+    const int64_t jc = min(chunk * C + jj, m - 1);
+    const int64_t j = rev ? m - 1 - jc : jc;   // the reversed problem's column jc is q's column m-1-jc
+    const int32_t* qj = q + j * dim;
+    int w[4];
+    if (nar) {
+      unsigned n2 = 0;
+      if (4 * plane <= DK && DK < 4 * plane + 4) {
+#pragma unroll
+        for (int k = 0; k < DK; ++k) {
+          const unsigned c = k < dim ? (unsigned)qj[k] : 0u;
+          n2 += c * c;
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int k = 4 * plane + i;
+        w[i] = k < DK ? (k < dim ? (int)(0u - 2u * (unsigned)qj[k]) : 0) : k == DK ? (int)n2 : 0;
+      }
+      on[chunk * (C * NPL_N) + plane * C + qpos(jj, TR_n, C)] = make_int4(w[0], w[1], w[2], w[3]);
+    } else {
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int k = 4 * plane + i;
+        w[i] = k < dim ? qj[k] : 0;
+      }
+      ow[chunk * (C * NPL_W) + plane * C + jj] = make_int4(w[0], w[1], w[2], w[3]);
+    }
   }
 }
 
@@ -1011,10 +1212,13 @@ __global__ void wave_prep_kernel(const typename V::coord* q, int64_t m, int dim,
 // the error word is set: an input check that failed or a wait that ran out
 // made the wavefront skip its bands, so the row buffers hold no result and
 // the outputs keep whatever the caller put there.
-template <class V>
+template <class V, int DK>
 __global__ void combine_kernel(const void* rowbuf_f, const void* rowbuf_b, int64_t m, unsigned long long* word,
-                               unsigned* count, const int* err, void* out_dist, void* out_dist2) {
+                               unsigned* count, const int* err, void* out_dist, void* out_dist2, const int* box,
+                               int nbox, int want) {
   using T = typename V::value;
+  __shared__ int sel[2 * DK + 1];
+  if (box && box_narrow_block<DK>(box, nbox, sel) != (want != 0)) return;   // the other class's launch
   const T* F = static_cast<const T*>(rowbuf_f);
   const T* B = static_cast<const T*>(rowbuf_b);
   T best = V::inf();
@@ -1043,15 +1247,10 @@ __global__ void combine_kernel(const void* rowbuf_f, const void* rowbuf_b, int64
       __threadfence();
       if (atomicAdd(count, 1u) == gridDim.x - 1 && *(volatile const int*)err == 0) {
         const unsigned long long mb = ~atomicAdd(word, 0ull);
-        if constexpr (sizeof(T) == 4) {
-          const float r = __uint_as_float((unsigned)mb);
-          if (out_dist2) static_cast<float*>(out_dist2)[0] = r;
-          if (out_dist) static_cast<float*>(out_dist)[0] = sqrtf(r);
-        } else {
-          const long long r = (long long)mb;
-          if (out_dist2) static_cast<long long*>(out_dist2)[0] = r;
-          if (out_dist) static_cast<double*>(out_dist)[0] = sqrt((double)r);
-        }
+        if constexpr (sizeof(T) == 4)
+          write_pair_result<V>(out_dist, out_dist2, __uint_as_float((unsigned)mb));
+        else
+          write_pair_result<V>(out_dist, out_dist2, (T)(long long)mb);
       }
     }
   }

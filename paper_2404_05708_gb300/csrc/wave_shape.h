@@ -42,23 +42,35 @@ constexpr int max_warps_ring(int C, int K) { return ((nq_slots(C) - 1) * C - 31 
 
 // Registers a compute lane needs (points, row state, q records in flight,
 // the block's ring inputs, addressing), an estimate calibrated on ptxas.
-constexpr int reg_estimate(bool f32, int dk, int R) {
-  return f32 ? 48 + R * dk + (R / 2) * ((dk + 1) / 2) * 4 + 2 * R + 3 * (R / 2) + G
+// The narrow int32 class (uint32 bits carried as floats) runs the float32
+// stripe with integer coordinates and one |p|^2 more per row.
+constexpr int reg_estimate(bool f32, int dk, int R, bool narrow = false) {
+  return f32 ? 48 + R * dk + (R / 2) * ((dk + 1) / 2) * 4 + 2 * R + 3 * (R / 2) + G + (narrow ? R : 0)
              : 48 + R * dk + 4 * R + ((dk + 3) / 4) * 4;
 }
 
 // Compute warps per CTA the register file allows (with the communication
 // warp, one CTA per SM); 0 if even one warp would not fit in 255 registers.
-constexpr int max_warps_regs(bool f32, int dk, int R) {
-  return reg_estimate(f32, dk, R) > 248 ? 0
-         : (65536 / (32 * ((reg_estimate(f32, dk, R) + 7) / 8 * 8)) - 1) > 16
+constexpr int max_warps_regs(bool f32, int dk, int R, bool narrow = false) {
+  return reg_estimate(f32, dk, R, narrow) > 248 ? 0
+         : (65536 / (32 * ((reg_estimate(f32, dk, R, narrow) + 7) / 8 * 8)) - 1) > 16
              ? 16
-             : 65536 / (32 * ((reg_estimate(f32, dk, R) + 7) / 8 * 8)) - 1;
+             : 65536 / (32 * ((reg_estimate(f32, dk, R, narrow) + 7) / 8 * 8)) - 1;
 }
 
 constexpr bool shape_supported(bool f32, int dk, int R, int W) {
   return (R == 2 || R == 4 || R == 6 || R == 8) && W >= 1 && W <= max_warps_regs(f32, dk, R) &&
          W <= max_warps_ring(chunk_cols(dk), skew(f32, R));
+}
+
+// An int32 pair launches both its kernels with one shape: the narrow one
+// (float32 stripe and skew) and the exact int64 one.
+constexpr bool narrow_shape_supported(int dk, int R, int W) {
+  return (R == 2 || R == 4 || R == 6 || R == 8) && W >= 1 && W <= max_warps_regs(true, dk, R, true) &&
+         W <= max_warps_ring(chunk_cols(dk), skew(true, R));
+}
+constexpr bool int_shape_supported(int dk, int R, int W) {
+  return shape_supported(false, dk, R, W) && narrow_shape_supported(dk, R, W);
 }
 
 }  // namespace wave

@@ -220,6 +220,49 @@ def test_two_fronts_met_in_the_launch_or_by_the_combine_kernel(dctx, m):
     check_i32(dctx, pi, qi)
 
 
+@pytest.mark.parametrize("m", [1500, 70000])
+def test_int_value_class_boundary(dctx, m):
+    """int32 pairs carry uint32 bits in float registers only while every
+    squared distance stays below the first NaN pattern: the squared ranges
+    of the bounding box summing to at most 0x7F7FFFFF.  p at the origin and
+    q at (r, s) repeated give delta^2 = r^2 + s^2, the largest squared
+    distance of the pair, on both sides of the bound: 46,250^2 and
+    32,000^2 + 33,393^2 fit, 46,251^2 and 32,000^2 + 33,394^2 do not.  A
+    boundary one off would turn the last into a NaN pattern.  Two fronts
+    met in the launch (m = 1,500) and by the combine kernel (m = 70,000);
+    the classes alternate on one context."""
+    n = 2000
+    rng = np.random.default_rng(95)
+    for r, s in ((46250, 0), (46251, 0), (32000, 33393), (32000, 33394), (46250, 0)):
+        p = np.zeros((n, 2), np.int32)
+        q = np.tile(np.array([[r, s]], np.int32), (m, 1))
+        d, d2 = run(dctx, p, q)
+        assert d2 == r * r + s * s, (r, s, d2)
+        assert d == math.sqrt(float(r * r + s * s))
+        # a walk inside the same box (its corners pinned), against the oracle
+        w = i32_walk(rng, n, 2, 200)
+        w = (w - w.min(axis=0)) % np.array([r + 1, s + 1])
+        w[0], w[-1] = (0, 0), (r, s)
+        qw = np.tile(np.array([[r // 2, s // 2]], np.int32), (m, 1)) + i32_walk(rng, m, 2, 3) % 7
+        check_i32(dctx, w.astype(np.int32), qw.astype(np.int32))
+    assert dctx.get_error() == 0
+
+
+def test_int_value_classes_in_explicit_shapes(dctx):
+    """Both int32 classes in every rows-per-lane shape (their skews differ:
+    R/2 columns a lane for the narrow class, 1 for the exact one)."""
+    rng = np.random.default_rng(96)
+    narrow = (i32_walk(rng, 1700, 3, 40), i32_walk(rng, 1300, 3, 40))
+    wide = (i32_walk(rng, 1700, 3, 4000), i32_walk(rng, 1300, 3, 4000))
+    box = np.ptp(np.concatenate(wide[:2]).astype(np.int64), axis=0)
+    assert int((box * box).sum()) > 0x7F7FFFFF
+    for p, q in (narrow, wide):
+        want = oracle.dfd2_linear(p, q)
+        for R in (2, 4, 6, 8):
+            for W in (1, 2, 4):
+                assert run(dctx, p, q, shape=(R, W, 0))[1] == want, (R, W)
+
+
 def test_identity_symmetry_reversal_duplication(dctx):
     rng = np.random.default_rng(51)
     p, q = f32_walk(rng, 1500, 3), f32_walk(rng, 1100, 3)
