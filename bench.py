@@ -60,11 +60,14 @@ REF_SAMPLE = 20_000          # --impl reference: prefix per step
 # DRAM bytes (read + write) per launch of the main kernel, from an ncu launch
 # list of the benchmark command (gpu__time_duration.sum, dram__bytes_read.sum,
 # dram__bytes_write.sum: one pass), keyed by the hash of the kernel sources it
-# was taken on; any later source change reports null.
+# was taken on (and "/<workload>" where two workloads share those sources);
+# any later source change reports null.
 TRAFFIC_BY_KERNEL_SHA: dict = {
     "9799fd99282b0741": 15759897,    # wave_kernel<F32, 3, 6>, long pair 200,000^2 (two fronts, 512-column q chunks)
     "4da739c00f897e73": 16059648,    # the same with a 4-chunk q ring (15.40 MB read, 0.66 MB written)
     "336ce32a9a0f5945": 16327168,    # the same after the prep kernel and the fused combine (15.73 MB read, 0.59 MB written)
+    "b1c84c88a75cca4c": 16335104,    # the same with the int32 value classes beside it (15.68 MB read, 0.66 MB written)
+    "b1c84c88a75cca4c/pair2k": 138906,   # wave_kernel<F32, 2, 4>, pair 2000 x 1500 (mean of 10 launches, reads only)
     "27aa8e25b42fbf75": 289363200,   # batch_kernel<I32, 2>, ragged batch of 65,536 pairs (graph launches)
     # batch_kernel<I32, 2> with size classes and the 8-step loop: 147.41 MB per launch captured on the
     # 32,768-pair batch (139.0 MB of inputs), scaled by the inputs (the points are read once) to the
@@ -276,7 +279,8 @@ class Pair2k(LongPair):
         self.d2 = torch.empty(1, dtype=torch.float32, device="cuda")
         self.cells = self.n * self.m
         self.config = {"workload": PAIR2K_WORKLOAD, "n": self.n,
-                       "m": self.m, "dim": 2, "cells_per_step": self.cells}
+                       "m": self.m, "dim": 2, "cells_per_step": self.cells, "kernel_sha": kernel_sha()}
+        self.traffic_tag = "pair2k"   # same kernel sources as the long pair, another workload
         self.h2d = (self.n + self.m) * 2 * 4
         self.d2h = 16
 
@@ -1142,7 +1146,9 @@ def alu_roofline(wl, ctx, dfd, sms, clocks, kernel_ms, total_ms, steps):
     else:
         peak, peak_basis = mix_peak, mix_basis
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gcell/s", "frac": achieved / peak,
-                "traffic": TRAFFIC_BY_KERNEL_SHA.get(wl.config.get("kernel_sha")), "peak_basis": peak_basis,
+                "traffic": TRAFFIC_BY_KERNEL_SHA.get(
+                    wl.config.get("kernel_sha", "") + (f"/{wl.traffic_tag}" if getattr(wl, "traffic_tag", None) else "")),
+                "peak_basis": peak_basis,
                 "measured_mix": {"peak": mix_peak, "frac": achieved / mix_peak, "basis": mix_basis}}
     roofline["timing"] = ("main kernel, the library's CUDA events on the launching stream" if kernel_ms
                           else "whole step (all launches of the step)")
