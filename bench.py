@@ -191,6 +191,9 @@ class LongPair:
     """One long 3-D float32 pair through dfd_pair (band wavefront)."""
     micro_op = "cell_f32_d3"
     dtype = "f32"
+    # the wavefront starts on the prep kernel's tail (programmatic launch), so
+    # the library's events bracket both
+    kernel_timing = "prep and wavefront kernels"
     launches_per_step = 3          # prep (check + q packing), wavefront, combine (set per shape below)
 
     def __init__(self, args, ctx, dfd, torch, workloads, rank, world):
@@ -1150,8 +1153,8 @@ def alu_roofline(wl, ctx, dfd, sms, clocks, kernel_ms, total_ms, steps):
                     wl.config.get("kernel_sha", "") + (f"/{wl.traffic_tag}" if getattr(wl, "traffic_tag", None) else "")),
                 "peak_basis": peak_basis,
                 "measured_mix": {"peak": mix_peak, "frac": achieved / mix_peak, "basis": mix_basis}}
-    roofline["timing"] = ("main kernel, the library's CUDA events on the launching stream" if kernel_ms
-                          else "whole step (all launches of the step)")
+    roofline["timing"] = (getattr(wl, "kernel_timing", "main kernel") + ", the library's CUDA events on the launching stream"
+                          if kernel_ms else "whole step (all launches of the step)")
     if hasattr(wl, "evaluated_cells"):
         roofline["achieved_basis"] = (f"recurrence cells actually evaluated ({work_cells:.3e} per step; "
                                       f"value counts all {wl.cells:.3e} candidate cells)")

@@ -586,9 +586,11 @@ dfd_status dfd_pair_plan(dfd_context* ctx, dfd_dtype dtype, int dim, int64_t n, 
 /*
  * Measurement hooks (no counterpart in the paper).  With timing enabled the
  * context records a CUDA event pair around the main kernel launch of every
- * computing call, on that call's stream.  dfd_timing_last waits for the
- * latest pair and returns its duration in milliseconds (DFD_ERR_NOT_READY
- * if none was recorded since enabling).
+ * computing call, on that call's stream (for the band wavefront of dfd_pair:
+ * around its prep kernel and the wavefront kernels, which start early on the
+ * prep kernel's tail and would not with an event between them).
+ * dfd_timing_last waits for the latest pair and returns its duration in
+ * milliseconds (DFD_ERR_NOT_READY if none was recorded since enabling).
  */
 dfd_status dfd_timing_enable(dfd_context* ctx, int on);
 dfd_status dfd_timing_last(dfd_context* ctx, double* ms);

@@ -343,6 +343,16 @@ __device__ __forceinline__ bool box_narrow_block(const int* box, int nbox, int* 
   return narrow;
 }
 
+// Programmatic dependent launch: a kernel launched with programmatic stream
+// serialisation may start while the kernel before it in the stream runs, as
+// soon as every CTA of that kernel has called launch_dependents (or exited);
+// griddep_wait then blocks until that kernel has completed and its memory
+// operations are visible.  Without the launch attribute both are no-ops.
+__device__ __forceinline__ void griddep_launch_dependents() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 // --------------------------------------------------- shared-memory counters
 __device__ __forceinline__ int ld_acquire_cta(const int* p) {
   int v;
@@ -970,14 +980,14 @@ __global__ void __launch_bounds__((kMaxWarps<V, DK, R>::value + 1) * 32, 1) wave
   T* rings = reinterpret_cast<T*>(smem + Lay::ring_off);
   Ctl* ctl = reinterpret_cast<Ctl*>(smem + Lay::ctl_off(W));
 
-  // an int32 pair's other class: leave before touching anything
-  if (a.box && box_narrow_block<DK>(a.box, a.nbox, reinterpret_cast<int*>(smem)) != (a.want != 0)) return;
-
-  // zero the q ring once (never-read slots stay finite), rings to +inf
+  // The kernel that follows in the stream (an int32 pair's other class) may
+  // start its prologue now; it waits for this one to finish.
+  griddep_launch_dependents();
+  // zero the q ring once (never-read slots stay finite); this needs nothing
+  // from the kernel before, so it overlaps that kernel's tail
   {
     uint4* q4 = reinterpret_cast<uint4*>(smem);
     for (size_t i = threadIdx.x; i < Lay::q_bytes / 16; i += blockDim.x) q4[i] = make_uint4(0, 0, 0, 0);
-    for (size_t i = threadIdx.x; i < (size_t)(W + 1) * RING; i += blockDim.x) rings[i] = V::inf();
   }
   if (threadIdx.x == 0) {
     for (int s = 0; s < NQ; ++s) {
@@ -987,6 +997,12 @@ __global__ void __launch_bounds__((kMaxWarps<V, DK, R>::value + 1) * 32, 1) wave
     fence_mbar_init();
     ctl->abort = 0;
   }
+  // the prep kernel's header, box and packed q from here on
+  griddep_wait();
+  // an int32 pair's other class: leave before touching the header (the
+  // rings serve as the reduction's scratch; no bulk copy has been issued)
+  if (a.box && box_narrow_block<DK>(a.box, a.nbox, reinterpret_cast<int*>(rings)) != (a.want != 0)) return;
+  for (size_t i = threadIdx.x; i < (size_t)(W + 1) * RING; i += blockDim.x) rings[i] = V::inf();
   __syncthreads();
 
   unsigned gbase = 0;
@@ -1058,6 +1074,7 @@ __global__ void wave_prep_kernel(const typename V::coord* q, int64_t m, int dim,
                                  int64_t p_elems, int check, long long lim, int* err) {
   static_assert(std::is_same<V, F32>::value, "float32 prep");
   (void)lim;
+  griddep_launch_dependents();   // the wavefront may start its prologue
   const int rev = (int)blockIdx.y;
   if (blockIdx.x == 0 && rev == 0)
     for (int i = threadIdx.x; i < header_words; i += blockDim.x) header[i] = 0u;
@@ -1108,6 +1125,7 @@ __global__ void wave_prep_int_kernel(const int32_t* q, int64_t m, int dim, const
                                      unsigned* header, int header_words, int check, long long lim, int* err,
                                      int* box, int nbox, int nch_n, int TR_n, void* out_n0, void* out_n1, int nch_w,
                                      void* out_w0, void* out_w1) {
+  griddep_launch_dependents();   // the wavefronts may start their prologue
   const int rev = (int)blockIdx.y;
   if (blockIdx.x == 0 && rev == 0)
     for (int i = threadIdx.x; i < header_words; i += blockDim.x) header[i] = 0u;

@@ -163,7 +163,10 @@ dfd_status wave_launch(dfd_context* ctx, int dim, const void* p, int64_t n, cons
   const size_t smem_n = LayN::bytes(W), smem_w = LayW::bytes(W);
   if (smem_n > ctx->smem_optin || (kInt && smem_w > ctx->smem_optin)) return DFD_ERR_UNSUPPORTED;
   // one launch before the wavefront: the header zeroed, the inputs checked
-  // (check), q packed for each front (int32: also the bounding box)
+  // (check), q packed for each front (int32: also the bounding box).  The
+  // measurement events bracket it too: an event between it and the
+  // wavefront would keep the wavefront from starting early (below).
+  timing_begin(ctx, s);
   const long long lim =
       std::min<long long>((1LL << 30) - 1, (long long)std::floor(std::sqrt((double)LLONG_MAX / (double)dim) / 2.0));
   if constexpr (kInt) {
@@ -225,12 +228,30 @@ dfd_status wave_launch(dfd_context* ctx, int dim, const void* p, int64_t n, cons
     const int g = ctas > 0 ? ctas : per_sm * ctx->num_sms;
     return (int)std::min<int64_t>(g, nbands);
   };
-  timing_begin(ctx, s);
-  wave::wave_kernel<VN, DK, R><<<grid_of(per_sm_n), (W + 1) * 32, smem_n, s>>>(
-      args(gn.nblk, gn.nch, off.qn, off.qn_b, 1));
-  if constexpr (kInt)
-    wave::wave_kernel<V, DK, R><<<grid_of(per_sm_w), (W + 1) * 32, smem_w, s>>>(
-        args(gw.nblk, gw.nch, off.qw, off.qw_b, 0));
+  // The wavefronts are launched with programmatic stream serialisation: their
+  // CTAs may become resident and run their prologue (q ring zeroed, barriers
+  // initialised) while the kernel before them finishes, then wait for it in
+  // griddep_wait, which hides most of a launch gap per kernel.
+  cudaLaunchAttribute pdl[1];
+  pdl[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  pdl[0].val.programmaticStreamSerializationAllowed = 1;
+  auto launch = [&](auto kernel, int per_sm, size_t smem, const wave::Args& a) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid_of(per_sm));
+    cfg.blockDim = dim3((unsigned)((W + 1) * 32));
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cfg.attrs = pdl;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, a);
+  };
+  cudaError_t le = launch(wave::wave_kernel<VN, DK, R>, per_sm_n, smem_n, args(gn.nblk, gn.nch, off.qn, off.qn_b, 1));
+  if (le == cudaSuccess && kInt)
+    le = launch(wave::wave_kernel<V, DK, R>, per_sm_w, smem_w, args(gw.nblk, gw.nch, off.qw, off.qw_b, 0));
+  if (le != cudaSuccess) {
+    cudaGetLastError();
+    return cuda_status(le);
+  }
   if (two && !fused) {
     // the merge words sit after the ticket in the zeroed scratch header
     const int cblocks = (int)std::max<int64_t>(1, std::min<int64_t>((m + 1023) / 1024, ctx->num_sms));
