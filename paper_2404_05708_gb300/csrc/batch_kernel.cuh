@@ -780,6 +780,7 @@ template <int DK, bool VEC>
 __global__ void curve_bbox_kernel(const int32_t* __restrict__ pts, const int64_t* __restrict__ offsets,
                                   int64_t first, int64_t n_curves, int dim, int check, long long lim, int* bbox,
                                   int* err) {
+  griddep_launch_dependents();   // the plan may start (it waits for the boxes)
   constexpr int NL = BoxLoads<DK>::value;
   const int L = threadIdx.x & 31;
   const int64_t total = offsets[n_curves];
@@ -1036,7 +1037,14 @@ __device__ __forceinline__ unsigned plan_entry(const PlanArgs& a, int64_t k, int
   return (unsigned)k | narrow | (swap << 31);
 }
 
+// Plan kernels run with programmatic stream serialisation (launch_pdl) right
+// after the call's own check or box kernel: an int32 plan waits for the
+// bounding boxes before it classifies; a float32 plan needs nothing from the
+// input check, runs beside it and waits for it only before it finishes, so
+// that the batch kernel, which waits for the plan, also finds the check done.
 static __global__ void plan_hist_kernel(PlanArgs a) {
+  griddep_launch_dependents();
+  if (a.bbox) griddep_wait();
   const int L = threadIdx.x & 31;
   const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t wstride = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -1050,6 +1058,7 @@ static __global__ void plan_hist_kernel(PlanArgs a) {
     const unsigned peers = __match_any_sync(0xffffffffu, b);
     if (b >= 0 && L == __ffs(peers) - 1) atomicAdd(&a.hist[b], (unsigned)__popc(peers));
   }
+  griddep_wait();
 }
 
 // One block of NBUCKET threads: exclusive scan of the bucket counts into
@@ -1057,6 +1066,8 @@ static __global__ void plan_hist_kernel(PlanArgs a) {
 static __global__ void plan_scan_kernel(PlanArgs a) {
   static_assert(NBUCKET % 32 == 0 && NBUCKET / 32 <= 32 && NBUCKET <= 1024, "one block, one warp of warp totals");
   __shared__ unsigned wsum[NBUCKET / 32];
+  griddep_launch_dependents();
+  griddep_wait();   // the counts
   const int b = threadIdx.x, L = b & 31, w = b >> 5;
   const unsigned x = a.hist[b];
   unsigned inc = x;
@@ -1081,6 +1092,8 @@ static __global__ void plan_scan_kernel(PlanArgs a) {
 }
 
 static __global__ void plan_scatter_kernel(PlanArgs a) {
+  griddep_launch_dependents();
+  griddep_wait();   // the cursors (and, through the scan, the buckets)
   const int L = threadIdx.x & 31;
   const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t wstride = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -1108,6 +1121,8 @@ static __global__ void __launch_bounds__(1024) plan_small_kernel(PlanArgs a, uns
   static_assert(NBUCKET <= 1024, "one bucket per thread");
   __shared__ unsigned cnt[NBUCKET];
   __shared__ unsigned wsum[32];
+  griddep_launch_dependents();
+  if (a.bbox) griddep_wait();   // int32: the bounding boxes (see plan_hist_kernel)
   const int t = threadIdx.x, L = t & 31, w = t >> 5;
   for (int i = t; i < zero_words; i += blockDim.x) zero_base[i] = 0u;
   for (int i = t; i < NBUCKET; i += blockDim.x) cnt[i] = 0u;
@@ -1148,6 +1163,7 @@ static __global__ void __launch_bounds__(1024) plan_small_kernel(PlanArgs a, uns
   }
   __syncthreads();
   for (int i = t; i < NBUCKET; i += blockDim.x) a.cursor[i] = cnt[i];
+  griddep_wait();
 }
 
 // ------------------------------------------------------------ batch kernel
@@ -1411,6 +1427,8 @@ __global__ void __launch_bounds__(256, kBlocksPerSM<DK>::value) batch_kernel(Bat
   const int64_t gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   T* buf = static_cast<T*>(a.rowbuf) + gw * (int64_t)a.buf_cols;
   const Cd* pts = static_cast<const Cd*>(a.points);
+  // the plan (and through it the input check) is done from here on
+  griddep_wait();
   const int64_t total = a.offsets[a.n_curves];
   if (threadIdx.x == 0) cta_word = ld_relaxed_i32(a.err);
   __syncthreads();

@@ -19,6 +19,7 @@ template <class V>
 __global__ void check_points_kernel(const typename V::coord* x, const int64_t* begin, const int64_t* end, int dim,
                                     int* err) {
   static_assert(std::is_same<V, F32>::value, "float32 only");
+  griddep_launch_dependents();   // the plan may start beside it
   const int64_t count = end[0] * dim;
   bool bad = false;
   for (int64_t i = begin[0] * dim + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count;
@@ -46,12 +47,13 @@ inline long long int32_coord_limit(int dim) {
 }
 
 // Per-curve bounding boxes (and, with input checks on, the coordinate
-// range check) of curves [first, n_curves) of an int32 CSR batch.
+// range check) of curves [first, n_curves) of an int32 CSR batch.  Returns
+// whether a kernel was launched (none when the range is empty).
 template <int DK>
-void launch_curve_bbox(dfd_context* ctx, const void* points, const int64_t* offsets, int64_t n_curves, int dim,
+bool launch_curve_bbox(dfd_context* ctx, const void* points, const int64_t* offsets, int64_t n_curves, int dim,
                        int* bbox, cudaStream_t s, int64_t first = 0) {
   const int64_t warps_needed = n_curves - first;
-  if (warps_needed < 1) return;
+  if (warps_needed < 1) return false;
   const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((warps_needed + 7) / 8, 16 * (int64_t)ctx->num_sms));
   const int32_t* pts = static_cast<const int32_t*>(points);
   const int check = ctx->opt.check_inputs ? 1 : 0;
@@ -61,6 +63,7 @@ void launch_curve_bbox(dfd_context* ctx, const void* points, const int64_t* offs
   else
     batch::curve_bbox_kernel<DK, false><<<blocks, 256, 0, s>>>(pts, offsets, first, n_curves, dim, check,
                                                                int32_coord_limit(dim), bbox, ctx->d_err);
+  return true;
 }
 
 template <class K>
@@ -140,11 +143,17 @@ dfd_status batch_prepare(dfd_context* ctx, int dim, const void* points, const in
     if (e != cudaSuccess) return cuda_status(e);
   }
   int* bbox = kInt ? (bbox_ext ? bbox_ext : reinterpret_cast<int*>(base + off_bbox)) : nullptr;
+  // The plan starts early (programmatic launch) only right after this call's
+  // own check or box kernel, an ordinary launch that waited for everything
+  // before it: a float32 plan writes the header before it waits, and the
+  // scratch may still be in use by whatever ran before the call.
+  bool lead = false;
   if constexpr (kInt) {
-    launch_curve_bbox<DK>(ctx, points, offsets, n_curves, dim, bbox, s, bbox_ext ? first_curve : 0);
+    lead = launch_curve_bbox<DK>(ctx, points, offsets, n_curves, dim, bbox, s, bbox_ext ? first_curve : 0);
   } else if (ctx->opt.check_inputs && n_curves > first_curve) {
     check_points_kernel<V><<<std::min(4 * ctx->num_sms, 1024), 256, 0, s>>>(
         static_cast<const typename V::coord*>(points), offsets + first_curve, offsets + n_curves, dim, ctx->d_err);
+    lead = true;
   }
   batch::PlanArgs pa;
   pa.offsets = offsets;
@@ -168,12 +177,24 @@ dfd_status batch_prepare(dfd_context* ctx, int dim, const void* points, const in
   pa.hi_curve = slice ? slice->hi : n_curves;
   pa.take_invalid = slice ? (int)slice->take_invalid : 1;
   const int pblocks = (int)std::min<int64_t>((n_pairs + 255) / 256, 8 * (int64_t)ctx->num_sms);
+  cudaError_t le = cudaSuccess;
   if (small_plan) {
-    batch::plan_small_kernel<<<1, 1024, 0, s>>>(pa, reinterpret_cast<unsigned*>(base), (int)(off_bucket / 4));
+    if (lead)
+      le = launch_pdl(batch::plan_small_kernel, dim3(1), dim3(1024), 0, s, pa, reinterpret_cast<unsigned*>(base),
+                      (int)(off_bucket / 4));
+    else
+      batch::plan_small_kernel<<<1, 1024, 0, s>>>(pa, reinterpret_cast<unsigned*>(base), (int)(off_bucket / 4));
   } else {
-    batch::plan_hist_kernel<<<pblocks, 256, 0, s>>>(pa);
-    batch::plan_scan_kernel<<<1, batch::NBUCKET, 0, s>>>(pa);
-    batch::plan_scatter_kernel<<<pblocks, 256, 0, s>>>(pa);
+    if (lead)
+      le = launch_pdl(batch::plan_hist_kernel, dim3(pblocks), dim3(256), 0, s, pa);
+    else
+      batch::plan_hist_kernel<<<pblocks, 256, 0, s>>>(pa);
+    if (le == cudaSuccess) le = launch_pdl(batch::plan_scan_kernel, dim3(1), dim3(batch::NBUCKET), 0, s, pa);
+    if (le == cudaSuccess) le = launch_pdl(batch::plan_scatter_kernel, dim3(pblocks), dim3(256), 0, s, pa);
+  }
+  if (le != cudaSuccess) {
+    cudaGetLastError();
+    return cuda_status(le);
   }
   ba->rowbuf = base + off_buf;
   ba->buf_cols = buf_cols;
@@ -266,8 +287,14 @@ dfd_status batch_launch_range(dfd_context* ctx, int dim, const void* points, con
   ba.out_dist = out_dist;
   ba.out_dist2 = out_dist2;
   timing_begin(ctx, s);
-  batch::batch_kernel<V, DK><<<blocks, 256, 0, s>>>(ba);
+  // programmatic launch: the CTAs become resident while the plan finishes
+  // and wait for it (griddep_wait) before reading the work list
+  const cudaError_t le = launch_pdl(batch::batch_kernel<V, DK>, dim3(blocks), dim3(256), 0, s, ba);
   timing_end(ctx, s);
+  if (le != cudaSuccess) {
+    cudaGetLastError();
+    return cuda_status(le);
+  }
   return cuda_status(cudaGetLastError());
 }
 

@@ -101,6 +101,16 @@ __device__ __forceinline__ long long dist2(const int32_t* p, const int32_t* q) {
   return acc;
 }
 
+// Programmatic dependent launch: a kernel launched with programmatic stream
+// serialisation may start while the kernel before it in the stream runs, as
+// soon as every CTA of that kernel has called launch_dependents (or exited);
+// griddep_wait then blocks until that kernel has completed and its memory
+// operations are visible.  Without the launch attribute both are no-ops.
+__device__ __forceinline__ void griddep_launch_dependents() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 // Squared distance in the value type of V (F32: float, I32: exact int64,
 // I32B: exact uint32 bits as a float).
 template <class V, int D>

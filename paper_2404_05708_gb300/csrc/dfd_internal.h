@@ -97,6 +97,27 @@ inline void timing_end(dfd_context* ctx, cudaStream_t s) {
 
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
+// Launch with programmatic stream serialisation: the kernel's CTAs may start
+// while the kernel before it in the stream finishes (once every CTA of that
+// one has called griddepcontrol.launch_dependents or exited); the kernel
+// calls griddepcontrol.wait before it reads anything that kernel (or one
+// before it) wrote.  Between two kernels this hides most of a launch gap.
+template <class... KArgs, class... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                       Args&&... args) {
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
+
 inline unsigned long long timeout_ns(const dfd_context* ctx) {
   double ms = ctx->opt.wait_timeout_ms > 0 ? ctx->opt.wait_timeout_ms : 2000.0;
   return (unsigned long long)(ms * 1.0e6);

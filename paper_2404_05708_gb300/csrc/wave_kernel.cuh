@@ -343,16 +343,6 @@ __device__ __forceinline__ bool box_narrow_block(const int* box, int nbox, int* 
   return narrow;
 }
 
-// Programmatic dependent launch: a kernel launched with programmatic stream
-// serialisation may start while the kernel before it in the stream runs, as
-// soon as every CTA of that kernel has called launch_dependents (or exited);
-// griddep_wait then blocks until that kernel has completed and its memory
-// operations are visible.  Without the launch attribute both are no-ops.
-__device__ __forceinline__ void griddep_launch_dependents() {
-  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-}
-__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
-
 // --------------------------------------------------- shared-memory counters
 __device__ __forceinline__ int ld_acquire_cta(const int* p) {
   int v;

@@ -232,18 +232,8 @@ dfd_status wave_launch(dfd_context* ctx, int dim, const void* p, int64_t n, cons
   // CTAs may become resident and run their prologue (q ring zeroed, barriers
   // initialised) while the kernel before them finishes, then wait for it in
   // griddep_wait, which hides most of a launch gap per kernel.
-  cudaLaunchAttribute pdl[1];
-  pdl[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  pdl[0].val.programmaticStreamSerializationAllowed = 1;
   auto launch = [&](auto kernel, int per_sm, size_t smem, const wave::Args& a) {
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)grid_of(per_sm));
-    cfg.blockDim = dim3((unsigned)((W + 1) * 32));
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = s;
-    cfg.attrs = pdl;
-    cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, kernel, a);
+    return launch_pdl(kernel, dim3((unsigned)grid_of(per_sm)), dim3((unsigned)((W + 1) * 32)), smem, s, a);
   };
   cudaError_t le = launch(wave::wave_kernel<VN, DK, R>, per_sm_n, smem_n, args(gn.nblk, gn.nch, off.qn, off.qn_b, 1));
   if (le == cudaSuccess && kInt)
