@@ -1193,7 +1193,12 @@ struct BatchArgs {
   unsigned* n_deferred;
   unsigned long long timeout_ns;
   int rmax;                 // rows per lane cap of one-warp pairs (<= Rmax; the launch's tuned shape)
+  unsigned* meet;           // kMeetItems x 4 words, zeroed per launch: team pairs split over two CTAs
 };
+
+// Team pairs run as two halves on two CTAs (see run_team_pair) when at most
+// this many team items exist and their halves fit one per SM.
+constexpr int kMeetItems = 128;
 
 // Ring columns of a team's shared-memory hand-off (per warp, 8 bytes a slot).
 template <int DK>
@@ -1269,15 +1274,17 @@ __device__ __forceinline__ int team_pop_first(int* counter, unsigned* sm_rank, i
 // j + 1)) -- a selection among the same values, bit for bit the one-front
 // result.  All threads of the CTA call it; thread 0 gets the result.
 // `scratch`: 8 shared-memory words the CTA no longer uses (its rings).
-template <class V>
+// Rows written by another SM are read through L2 (CG).
+template <class V, bool CG = false>
 __device__ __forceinline__ typename V::value meet_rows(const typename V::value* F, const typename V::value* B, int m,
                                                        unsigned long long* scratch) {
   using T = typename V::value;
+  auto ld = [](const T* p) { return CG ? __ldcg(p) : *p; };
   T best = V::inf();
   for (int j = threadIdx.x; j < m; j += blockDim.x) {
-    const T bj = B[m - 1 - j];
-    const T bj1 = j + 1 < m ? B[m - 2 - j] : V::inf();
-    best = V::vmin(best, V::vmax(F[j], V::vmin(bj, bj1)));
+    const T bj = ld(B + (m - 1 - j));
+    const T bj1 = j + 1 < m ? ld(B + (m - 2 - j)) : V::inf();
+    best = V::vmin(best, V::vmax(ld(F + j), V::vmin(bj, bj1)));
   }
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) best = V::vmin(best, __shfl_xor_sync(0xffffffffu, best, off));
@@ -1295,10 +1302,16 @@ __device__ __forceinline__ typename V::value meet_rows(const typename V::value* 
 // the warp that runs the last stripe.  `gbuf` holds `gcols` values; a pair
 // with more stripes than warps needs m of them, else it is not run here and
 // false is returned (CTA-uniform).
+// With only_half = 0 or 1 the CTA runs one half of a two-front pair (below)
+// and another CTA the other: `meet` is the pair's 4 words (count, the two
+// halves' CTAs + 1), `xw` a shared word, and *hold is set when this CTA
+// finished first, so its row buffer holds its half's row until the other
+// CTA has read it.  A pair that does not split runs whole in half 0's CTA.
 template <class V, int DK>
 __device__ __forceinline__ bool run_team_pair(const BatchArgs& a, unsigned wentry, void* gbuf, long long gcols,
                                               uint4* stage, unsigned long long* ring, unsigned long long* prog,
-                                              unsigned long long* cons) {
+                                              unsigned long long* cons, int only_half = -1,
+                                              unsigned* meet = nullptr, int* xw = nullptr, bool* hold = nullptr) {
   using Cd = typename V::coord;
   const int L = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int64_t k = wentry & (kNarrowBit - 1);
@@ -1321,9 +1334,14 @@ __device__ __forceinline__ bool run_team_pair(const BatchArgs& a, unsigned wentr
   // other n - h rows backwards against q reversed, each half a pipeline of
   // its own, and their last rows meet in the CTA (meet_rows): the pipeline
   // is half as deep.  The halves' last rows sit in the CTA's row buffer.
+  // With only_half set, the CTA's warps of that half run it (one warp per
+  // SM sub-partition, the others wait at the barrier) and the CTA that
+  // finishes second meets the two rows, the other's read through L2.
   constexpr int kHalf = kTeamWarps / 2;
   const int h = (n + 1) / 2;
-  if (n >= 64 && h <= kHalf * 32 * Rmax<DK>::value && 2LL * m <= gcols) {
+  const bool split = n >= 64 && h <= kHalf * 32 * Rmax<DK>::value && 2LL * m <= gcols;
+  if (only_half == 1 && !split) return true;   // half 0's CTA runs the whole pair
+  if (split) {
     if (threadIdx.x < kTeamWarps) {
       prog[threadIdx.x] = 0;
       cons[threadIdx.x] = 0;
@@ -1345,26 +1363,56 @@ __device__ __forceinline__ bool run_team_pair(const BatchArgs& a, unsigned wentr
     const Cd* P = pts + (half == 0 ? oa : oa + n - 1) * a.dim;
     const Cd* Q = pts + (half == 0 ? ob : ob + m - 1) * a.dim;
     const int ps = half == 0 ? a.dim : -a.dim, qs = half == 0 ? 1 : -1;
+    const bool mine = only_half < 0 || half == only_half;
+    auto run = [&](auto cls) {
+      using VV = decltype(cls);
+      using TT = typename VV::value;
+      TT* rows = static_cast<TT*>(gbuf);
+      io.final_out = rows + (size_t)half * m;
+      if (mine) team_dfd_any<VV, DK>(P, nh, Q, m, a.dim, a.vec != 0, L, io.w, stage, &io, kHalf, ps, qs);
+      __syncthreads();
+      if (only_half < 0) {
+        const TT r = meet_rows<VV>(rows, rows + m, m, ring);
+        if (threadIdx.x == 0) write_result<VV>(a.out_dist, a.out_dist2, k, r);
+        __syncthreads();
+        return;
+      }
+      // publish this half's row (every writer's stores before the count),
+      // then count; the second CTA reads the first's CTA index and meets
+      __threadfence();
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        *reinterpret_cast<volatile unsigned*>(&meet[1 + only_half]) = blockIdx.x + 1u;
+        __threadfence();
+        const unsigned before = atomicAdd(&meet[0], 1u);
+        int other = -1;
+        if (before == 1) {
+          other = (int)*reinterpret_cast<volatile unsigned*>(&meet[2 - only_half]) - 1;
+          __threadfence();
+        }
+        *xw = before == 0 ? -2 : other;
+      }
+      __syncthreads();
+      const int other = *xw;
+      *hold = other == -2;
+      if (other >= 0) {
+        // the other CTA's row buffer, offset as gbuf is (in the launch's value type)
+        const TT* orow = reinterpret_cast<const TT*>(static_cast<const typename V::value*>(a.rowbuf) +
+                                                     (int64_t)other * kTeamWarps * a.buf_cols);
+        const TT* F = only_half == 0 ? rows : orow;
+        const TT* B = only_half == 1 ? rows + m : orow + m;
+        const TT r = meet_rows<VV, true>(F, B, m, ring);
+        if (threadIdx.x == 0) write_result<VV>(a.out_dist, a.out_dist2, k, r);
+      }
+      __syncthreads();
+    };
     if constexpr (std::is_same<V, I32>::value) {
       if (wentry & kNarrowBit) {
-        float* rows = static_cast<float*>(gbuf);
-        io.final_out = rows + (size_t)half * m;
-        team_dfd_any<I32B, DK>(P, nh, Q, m, a.dim, a.vec != 0, L, io.w, stage, &io, kHalf, ps, qs);
-        __syncthreads();
-        const float r = meet_rows<I32B>(rows, rows + m, m, ring);
-        if (threadIdx.x == 0) write_result<I32B>(a.out_dist, a.out_dist2, k, r);
-        __syncthreads();
+        run(I32B{});
         return true;
       }
     }
-    using T = typename V::value;
-    T* rows = static_cast<T*>(gbuf);
-    io.final_out = rows + (size_t)half * m;
-    team_dfd_any<V, DK>(P, nh, Q, m, a.dim, a.vec != 0, L, io.w, stage, &io, kHalf, ps, qs);
-    __syncthreads();
-    const T r = meet_rows<V>(rows, rows + m, m, ring);
-    if (threadIdx.x == 0) write_result<V>(a.out_dist, a.out_dist2, k, r);
-    __syncthreads();
+    run(V{});
     return true;
   }
   const int R = team_rows_per_lane<DK>(n);
@@ -1435,27 +1483,35 @@ __global__ void __launch_bounds__(256, kBlocksPerSM<DK>::value) batch_kernel(Bat
   if (cta_word != 0) return;   // CTA-uniform
   const long long n_team = a.n_team ? (long long)*a.n_team : 0;
 
-  // 1. team items
+  // 1. team items.  When every team pair's two halves fit one per SM, the
+  // items are halves (2t: pair t's first half, 2t + 1 its second), each CTA
+  // runs one with one warp per SM sub-partition, and the CTA that finishes
+  // a half first keeps its row buffer (hold): no more items for it.
+  bool hold = false;
   if (n_team > 0) {
     void* gbuf = static_cast<T*>(a.rowbuf) + (int64_t)blockIdx.x * kTeamWarps * a.buf_cols;
-    for (bool first = true;; first = false) {
+    const bool halves = a.meet && n_team <= kMeetItems && 2 * n_team <= a.n_sm;
+    const long long n_pop = halves ? 2 * n_team : n_team;
+    for (bool first = true; !hold; first = false) {
       __syncthreads();
       if (threadIdx.x == 0)
-        cta_word = first ? team_pop_first(a.team_counter, a.sm_rank, a.n_sm, n_team) : atomicAdd(a.team_counter, 1);
+        cta_word = first ? team_pop_first(a.team_counter, a.sm_rank, a.n_sm, n_pop) : atomicAdd(a.team_counter, 1);
       __syncthreads();
       const int item = cta_word;
-      if (item >= n_team) break;
-      const unsigned we = a.worklist[item];
-      if (!run_team_pair<V, DK>(a, we, gbuf, (long long)kTeamWarps * a.buf_cols, stage, team_ring, team_prog,
-                                team_cons) &&
-          threadIdx.x == 0)
-        a.deferred[atomicAdd(a.n_deferred, 1u)] = we;
+      if (item >= n_pop) break;
+      const int ti = halves ? item >> 1 : item;
+      const unsigned we = a.worklist[ti];
+      const bool ran = halves ? run_team_pair<V, DK>(a, we, gbuf, (long long)kTeamWarps * a.buf_cols, stage, team_ring,
+                                                     team_prog, team_cons, item & 1, a.meet + 4 * ti, &cta_word, &hold)
+                              : run_team_pair<V, DK>(a, we, gbuf, (long long)kTeamWarps * a.buf_cols, stage, team_ring,
+                                                     team_prog, team_cons);
+      if (!ran && threadIdx.x == 0) a.deferred[atomicAdd(a.n_deferred, 1u)] = we;
     }
   }
 
-  // 2. warp items
+  // 2. warp items (none for a CTA whose row buffer holds a half's row)
   const long long n_items = a.n_items_dev ? (long long)*a.n_items_dev : a.n_items;
-  const long long n_warp = n_items - n_team;
+  const long long n_warp = hold ? 0 : n_items - n_team;
   for (bool first = true;; first = false) {
     int item = 0;
     if (L == 0) item = first ? pop_first(a.counter, a.sm_rank, a.n_sm, n_warp) : atomicAdd(a.counter, 1);

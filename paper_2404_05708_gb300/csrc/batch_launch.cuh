@@ -83,10 +83,11 @@ int resident_blocks(const dfd_context* ctx, K kernel, int threads) {
 // buffer and only curves [first_curve, n_curves) are boxed and checked
 // (float32: only their points are checked): a batch run in slices of
 // curves, each slice covering the curves no earlier slice covered.
-// Scratch of one batch launch: [counter | hist | cursor] [bucket] [worklist]
+// Scratch of one batch launch: [counter | hist | cursor | SM slots | meet
+// words] (zeroed per launch) [bucket] [worklist]
 // [bbox] [row buffers].
 struct BatchLayout {
-  size_t off_hist, off_cursor, off_smrank, off_bucket, off_work, off_defer, off_bbox, off_buf, total;
+  size_t off_hist, off_cursor, off_smrank, off_meet, off_bucket, off_work, off_defer, off_bbox, off_buf, total;
 };
 template <class V, int DK>
 BatchLayout batch_layout(int64_t n_curves, int64_t n_pairs, int blocks, bool bbox_ext, int buf_cols) {
@@ -96,7 +97,8 @@ BatchLayout batch_layout(int64_t n_curves, int64_t n_pairs, int blocks, bool bbo
   l.off_hist = 256;
   l.off_cursor = l.off_hist + batch::NBUCKET * 4;
   l.off_smrank = align_up(l.off_cursor + batch::NBUCKET * 4, 256);
-  l.off_bucket = align_up(l.off_smrank + batch::kSmSlots * 4, 256);
+  l.off_meet = align_up(l.off_smrank + batch::kSmSlots * 4, 256);
+  l.off_bucket = align_up(l.off_meet + batch::kMeetItems * 4 * 4, 256);
   l.off_work = align_up(l.off_bucket + (size_t)n_pairs * 2, 256);
   l.off_defer = align_up(l.off_work + (size_t)n_pairs * 4, 256);
   l.off_bbox = align_up(l.off_defer + (size_t)n_pairs * 4, 256);
@@ -199,6 +201,7 @@ dfd_status batch_prepare(dfd_context* ctx, int dim, const void* points, const in
   ba->rowbuf = base + off_buf;
   ba->buf_cols = buf_cols;
   ba->sm_rank = reinterpret_cast<unsigned*>(base + lay.off_smrank);   // zeroed with the header
+  ba->meet = reinterpret_cast<unsigned*>(base + lay.off_meet);        // zeroed with the header
   ba->n_sm = std::min(blocks, ctx->num_sms);
   ba->points = points;
   ba->offsets = offsets;

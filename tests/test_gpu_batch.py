@@ -296,6 +296,38 @@ def test_batch_team_modes_bit_identical(dctx, dtype, dim):
     dctx.set_batch_team(code, dim, 0)
 
 
+@pytest.mark.parametrize("n_team", [32, 76, 77])
+def test_batch_team_halves_on_two_ctas(dctx, n_team):
+    """When every team pair's two halves fit one per SM (at most 76 team
+    pairs on 152 SMs), each half runs on its own CTA and the CTA that
+    finishes second meets the rows; 77 team pairs run whole in one CTA
+    each.  Team pairs (every multi-stripe pair: 600 to 1,100 rows) beside
+    one-warp pairs (40 to 250 rows), float32 against the selection mirror
+    and int32 (both value classes) against the oracle, bit for bit."""
+    from paper_2404_05708_gb300 import dfd
+    rng = np.random.default_rng(170 + n_team)
+    team_lens = rng.integers(600, 1101, size=2 * n_team)
+    warp_lens = rng.integers(40, 251, size=2 * 200)
+    lens = np.concatenate([team_lens, warp_lens]).astype(np.int64)
+    off = np.concatenate([[0], np.cumsum(lens)]).astype(np.int64)
+    pairs = np.arange(len(lens), dtype=np.int32).reshape(-1, 2)
+    for dtype in ("f32", "i32"):
+        if dtype == "f32":
+            pts = np.cumsum(rng.normal(0, 1, size=(int(off[-1]), 2)), axis=0).astype(np.float32)
+        else:
+            pts = np.cumsum(rng.integers(-64, 65, size=(int(off[-1]), 2)), axis=0).astype(np.int32)
+            pts[off[2]:off[4]] *= 4096   # team pair 1 in the exact int64 class
+        b = workloads.Batch(points=pts, offsets=off, pairs=pairs)
+        want, _ = oracle.batch(pts, off, pairs, mirror=(dtype == "f32"))
+        code = dfd.DFD_F32 if dtype == "f32" else dfd.DFD_I32
+        dctx.set_batch_team(code, 2, 2)
+        for _ in range(2):   # the meet words start at zero in every launch
+            d, d2 = run_batch(dctx, b)
+            assert dctx.get_error() == 0
+            assert np.array_equal(d2, want), np.nonzero(d2 != want)[0][:10]
+        dctx.set_batch_team(code, 2, 0)
+
+
 def test_batch_team_16d_float(dctx):
     """16-D points (4 rows per lane, 128-column team rings): a team of 8
     stripes of 128 rows, one cycling through 9 stripes, and one pair wider
