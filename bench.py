@@ -79,6 +79,8 @@ TRAFFIC_BY_KERNEL_SHA: dict = {
     "cb7f3699e1ec87c1": 291797623,
     # the same after the one-block plan and the two-front teams: 145.70 MB per launch on 32,768 pairs
     "4e3a53f28fbbf8b0": 291998225,
+    # the same with programmatic launches and team halves on two CTAs: 146.02 MB per launch on 32,768 pairs
+    "be9bbfac9032b6ac": 292637166,
 }
 
 
