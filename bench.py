@@ -81,6 +81,8 @@ TRAFFIC_BY_KERNEL_SHA: dict = {
     "4e3a53f28fbbf8b0": 291998225,
     # the same with programmatic launches and team halves on two CTAs: 146.02 MB per launch on 32,768 pairs
     "be9bbfac9032b6ac": 292637166,
+    # the same with the plan's cost models in 32-bit and float32 arithmetic: 145.68 MB per launch on 32,768 pairs
+    "d222274be6df4291": 291956860,
 }
 
 

@@ -877,12 +877,16 @@ constexpr unsigned kNarrowBit = 1u << 30;   // worklist: pair index | narrow << 
 // a lane over 131 steps each (12.6k instructions) rather than one stripe of
 // 4 rows over 531 steps (14.9k).  Ties keep rows = the shorter curve.
 __host__ __device__ __forceinline__ int rmax_of_class(int dk) { return dk <= 4 ? 8 : 4; }
+// (32-bit divisions: a 64-bit one is a long software routine on the GPU,
+// and the one-block plan of a small launch waits on it; lengths past 2^30,
+// which no curve here reaches, count as 2^30.)
 __host__ __device__ __forceinline__ long long orient_cost(int64_t rows, int64_t cols, int dk) {
-  const int rmax = rmax_of_class(dk);
-  const int cell = dk <= 4 ? 5 : dk <= 8 ? 10 : 18;
-  const int64_t st = (rows + 32 * rmax - 1) / (32 * rmax);
-  const int64_t r = rows <= 32 ? 1 : (rows + 32 * st - 1) / (32 * st);
-  return (long long)(st * (cols + 31)) * (cell * r + 8);
+  const unsigned rmax = (unsigned)rmax_of_class(dk);
+  const unsigned cell = dk <= 4 ? 5u : dk <= 8 ? 10u : 18u;
+  const unsigned R = (unsigned)(rows < (1LL << 30) ? rows : (1LL << 30));
+  const unsigned st = (R + 32u * rmax - 1u) / (32u * rmax);
+  const unsigned r = R <= 32u ? 1u : (R + 32u * st - 1u) / (32u * st);
+  return (long long)st * (long long)(cols + 31) * (long long)(cell * r + 8u);
 }
 // Whether curve b supplies the rows of pair (a, b) (a has na points, b nb;
 // dk = the dimension class).
@@ -944,18 +948,24 @@ __device__ __forceinline__ int cost_bucket_lpt(int64_t rows, int64_t cols, int r
 // Experiment 1 shapes this picks teams for 32 .. 512 pairs of 1,024 points
 // and for 1,024 pairs of 2,048 points and more, one warp otherwise (measured
 // both ways).
-__device__ __forceinline__ bool team_pays(int64_t rows, int64_t cols, int rmax, int64_t n_pairs, int ctas) {
-  const double c = (double)cols + 31.0;
-  const int64_t sw = (rows + 32 * rmax - 1) / (32 * rmax);
-  const double warp_rounds = (double)((n_pairs + 8LL * ctas - 1) / (8LL * ctas));
-  const double warp_cost = warp_rounds * (double)sw * c * (24.0 + 8.0 * rmax);
-  int64_t rt = (rows + 32 * 8 - 1) / (32 * 8);
-  rt = rt < 1 ? 1 : (rt > rmax ? rmax : rt);
-  const int64_t st = (rows + 32 * rt - 1) / (32 * rt);
-  const int64_t cyc = (st + 7) / 8;
-  const int64_t used = st < 8 ? st : 8;
-  const double team_rounds = (double)((n_pairs + ctas - 1) / ctas);
-  const double team_cost = team_rounds * ((double)cyc * c + (double)(used - 1) * 64.0) * (24.0 + 8.0 * (double)rt);
+// (float32 and 32-bit divisions: the decision changes no result, and FP64
+// arithmetic and 64-bit division are slow paths that the one-block plan of a
+// small launch would wait on; lengths and counts past 2^30 count as 2^30.)
+__device__ __forceinline__ bool team_pays(int64_t rows64, int64_t cols, int rmax, int64_t n_pairs, int ctas) {
+  const unsigned rows = (unsigned)min(rows64, (int64_t)1 << 30);
+  const unsigned np = (unsigned)min(n_pairs, (int64_t)1 << 30);
+  const unsigned rm = (unsigned)rmax, cs = (unsigned)max(ctas, 1);
+  const float c = (float)cols + 31.0f;
+  const unsigned sw = (rows + 32u * rm - 1u) / (32u * rm);
+  const float warp_rounds = (float)((np + 8u * cs - 1u) / (8u * cs));
+  const float warp_cost = warp_rounds * (float)sw * c * (24.0f + 8.0f * (float)rm);
+  unsigned rt = (rows + 32u * 8u - 1u) / (32u * 8u);
+  rt = rt < 1u ? 1u : (rt > rm ? rm : rt);
+  const unsigned st = (rows + 32u * rt - 1u) / (32u * rt);
+  const unsigned cyc = (st + 7u) / 8u;
+  const unsigned used = st < 8u ? st : 8u;
+  const float team_rounds = (float)((np + cs - 1u) / cs);
+  const float team_cost = team_rounds * ((float)cyc * c + (float)(used - 1u) * 64.0f) * (24.0f + 8.0f * (float)rt);
   return team_cost < warp_cost;
 }
 
